@@ -1,0 +1,234 @@
+"""Synthetic workloads shaped like the paper's (Section 3.1), carried onto the
+HEALPix sphere.
+
+The paper simulates flat-sky T/Q/U maps from CAMB spectra with a Cholesky draw
+of (T, E, B) harmonic coefficients, adds correlated noise and applies T and P
+masks (Section 3.1).  None of those data exist here, so this module stands in
+for them with analytic spectra, an inhomogeneous diagonal noise model and
+band-plus-disk masks.  Nothing here is part of the method: the transforms, the
+filter and the messenger loop live in the CUDA library (product) and in the
+oracle (test infrastructure).  Both receive these arrays as plain data.
+
+Recipe (all seeded through numpy's PCG64 via SeedSequence):
+
+* spectra: C_l^TT = exp(-(l/40)^2) / (l(l+1)) for l >= 1, C_0^TT = 0;
+  C^EE = 0.05 C^TT, C^BB = 0.01 C^EE, C^TE = 0.3 sqrt(C^TT C^EE), polarisation
+  only from l = 2;
+* signal: a_lm drawn from the per-l 2x2 TE block by Cholesky, B independent;
+  m = 0 real, m > 0 with re and im at half variance;
+* noise: sigma_T = s0 (1 + 2|cos theta|)(0.5 + U(0,1)) per pixel with s0 = 10 %
+  of the analytic T rms sqrt(sum (2l+1) C_l^TT / 4pi); sigma_Q = sigma_U =
+  sqrt(2) sigma_T; an optional (1 + cos^2 theta) scan-depth factor;
+* mask: |z| < band removed, plus disks (centres uniform on the sphere), a pixel
+  is masked when its centre lies inside a disk.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ARCMIN = np.pi / (180.0 * 60.0)
+DEG = np.pi / 180.0
+
+
+def cl_analytic(lmax: int, lscale: float = 40.0) -> np.ndarray:
+    """[4, lmax+1] = TT, EE, BB, TE."""
+    ell = np.arange(lmax + 1, dtype=np.float64)
+    tt = np.zeros(lmax + 1)
+    tt[1:] = np.exp(-(ell[1:] / lscale) ** 2) / (ell[1:] * (ell[1:] + 1.0))
+    ee = 0.05 * tt
+    bb = 0.01 * ee
+    te = 0.3 * np.sqrt(tt * ee)
+    ee[:2] = 0.0
+    bb[:2] = 0.0
+    te[:2] = 0.0
+    return np.stack([tt, ee, bb, te])
+
+
+def signal_rms(cl: np.ndarray) -> float:
+    ell = np.arange(cl.shape[1])
+    return float(np.sqrt(np.sum((2 * ell + 1) * cl[0]) / (4 * np.pi)))
+
+
+def pixel_centers(nside: int):
+    """(z, phi) of every HEALPix pixel in RING order (Gorski et al. 2005)."""
+    ns = nside
+    npix = 12 * ns * ns
+    p = np.arange(npix, dtype=np.int64)
+    z = np.empty(npix)
+    phi = np.empty(npix)
+    ncap = 2 * ns * (ns - 1)
+    # north cap
+    north = p < ncap
+    pn = p[north]
+    i = ((1 + np.sqrt(1 + 2 * pn)) / 2).astype(np.int64)
+    i = np.where(2 * i * (i - 1) > pn, i - 1, i)
+    i = np.where(2 * (i + 1) * i <= pn, i + 1, i)
+    j = pn - 2 * i * (i - 1)
+    z[north] = 1 - i * i / (3.0 * ns * ns)
+    phi[north] = (j + 0.5) * np.pi / (2.0 * i)
+    # equatorial belt
+    eq = (p >= ncap) & (p < npix - ncap)
+    pe = p[eq] - ncap
+    i = pe // (4 * ns) + ns
+    j = pe % (4 * ns)
+    shift = ((i - ns + 1) % 2 == 1).astype(np.float64) * 0.5
+    z[eq] = 4.0 / 3.0 - 2.0 * i / (3.0 * ns)
+    phi[eq] = (j + shift) * np.pi / (2.0 * ns)
+    # south cap (mirror)
+    south = p >= npix - ncap
+    ps = npix - 1 - p[south]
+    i = ((1 + np.sqrt(1 + 2 * ps)) / 2).astype(np.int64)
+    i = np.where(2 * i * (i - 1) > ps, i - 1, i)
+    i = np.where(2 * (i + 1) * i <= ps, i + 1, i)
+    jr = ps - 2 * i * (i - 1)  # counted from the end of the ring
+    j = 4 * i - 1 - jr
+    z[south] = -(1 - i * i / (3.0 * ns * ns))
+    phi[south] = (j + 0.5) * np.pi / (2.0 * i)
+    return z, phi
+
+
+def noise_sigma(nside: int, cl: np.ndarray, rng: np.random.Generator, scan_depth: bool = False,
+                level: float = 0.1) -> np.ndarray:
+    """[3, npix] per-pixel noise std-dev (I, Q, U)."""
+    z, _ = pixel_centers(nside)
+    s0 = level * signal_rms(cl)
+    st = s0 * (1.0 + 2.0 * np.abs(z)) * (0.5 + rng.random(z.size))
+    if scan_depth:
+        st = st * (1.0 + z * z)
+    return np.stack([st, np.sqrt(2.0) * st, np.sqrt(2.0) * st])
+
+
+def mask_band_disks(nside: int, rng: np.random.Generator, band: float, disks) -> np.ndarray:
+    """uint8 [npix], 1 = observed.  disks: list of (count, radius_rad) or
+    (count, (rmin, rmax)) with radii uniform in [rmin, rmax]."""
+    z, phi = pixel_centers(nside)
+    obs = np.abs(z) >= band
+    sth = np.sqrt(np.maximum(0.0, 1 - z * z))
+    vx, vy, vz = sth * np.cos(phi), sth * np.sin(phi), z
+    for count, rad in disks:
+        cz = rng.uniform(-1.0, 1.0, count)
+        cphi = rng.uniform(0.0, 2 * np.pi, count)
+        if np.isscalar(rad):
+            radii = np.full(count, float(rad))
+        else:
+            radii = rng.uniform(rad[0], rad[1], count)
+        cs = np.sqrt(1 - cz * cz)
+        cx, cy = cs * np.cos(cphi), cs * np.sin(cphi)
+        for k in range(count):
+            cosd = vx * cx[k] + vy * cy[k] + vz * cz[k]
+            obs &= cosd < np.cos(radii[k])
+    return obs.astype(np.uint8)
+
+
+def draw_alm(lmax: int, cl: np.ndarray, rng: np.random.Generator) -> np.ndarray:
+    """Gaussian (T, E, B) harmonic coefficients [3, nalm] complex128, m-major."""
+    tt, ee, bb, te = cl
+    nalm = (lmax + 1) * (lmax + 2) // 2
+    ls = np.concatenate([np.arange(m, lmax + 1) for m in range(lmax + 1)])
+    ms = np.concatenate([np.full(lmax + 1 - m, m) for m in range(lmax + 1)])
+    zr = rng.standard_normal((3, nalm))
+    zi = rng.standard_normal((3, nalm))
+    l11 = np.sqrt(np.maximum(tt, 0.0))
+    l21 = np.where(l11 > 0, te / np.where(l11 > 0, l11, 1.0), 0.0)
+    l22 = np.sqrt(np.maximum(ee - l21 ** 2, 0.0))
+    lbb = np.sqrt(np.maximum(bb, 0.0))
+    scale = np.where(ms == 0, 1.0, np.sqrt(0.5))
+    zc = zr + 1j * np.where(ms == 0, 0.0, zi)
+    alm = np.empty((3, nalm), dtype=np.complex128)
+    alm[0] = scale * l11[ls] * zc[0]
+    alm[1] = scale * (l21[ls] * zc[0] + l22[ls] * zc[1])
+    alm[2] = scale * lbb[ls] * zc[2]
+    return alm
+
+
+def draw_noise(sigma: np.ndarray, mask: np.ndarray, rng: np.random.Generator) -> np.ndarray:
+    return sigma * rng.standard_normal(sigma.shape) * mask[None, :]
+
+
+@dataclass
+class Workload:
+    """One synthetic problem: spectra, noise, mask and the true signal alm."""
+    name: str
+    nside: int
+    lmax: int
+    cl: np.ndarray
+    sigma: np.ndarray
+    mask: np.ndarray
+    alm_true: list = field(default_factory=list)   # per RHS [3, nalm]
+    noise: list = field(default_factory=list)      # per RHS [3, npix]
+    seeds: list = field(default_factory=list)
+
+    @property
+    def npix(self):
+        return 12 * self.nside * self.nside
+
+    def data(self, signal_maps):
+        """d = s + n on observed pixels, 0 on masked ones (Eq. 1)."""
+        return [(s + n) * self.mask[None, :] for s, n in zip(signal_maps, self.noise)]
+
+
+def _streams(seed: int, n: int):
+    return [np.random.default_rng(s) for s in np.random.SeedSequence(seed).spawn(n)]
+
+
+# Workload recipes.  Sizes follow the five benchmark configurations: nside 16 /
+# 256 / 512 / 2048 and the serving mix.
+CONFIGS = {
+    "nside16": dict(nside=16, lmax=47, band=0.2, disks=[(10, 3.0 * DEG)], scan=False),
+    "nside256": dict(nside=256, lmax=512, band=0.2, disks=[(10, 3.0 * DEG), (50, 0.5 * DEG)], scan=False),
+    "nside512": dict(nside=512, lmax=1024, band=0.2, disks=[(10, 3.0 * DEG), (50, 0.5 * DEG)], scan=False),
+    "nside2048": dict(nside=2048, lmax=4096, band=0.3, disks=[(2000, (5 * ARCMIN, 30 * ARCMIN))], scan=True),
+}
+
+
+def make_workload(name: str, seeds, nside: int | None = None, lmax: int | None = None,
+                  with_signal: bool = True) -> Workload:
+    """Spectra, noise sigma and mask from the first seed; per-RHS signal alm and
+    noise realisation from each seed."""
+    cfg = dict(CONFIGS[name])
+    if nside is not None:
+        cfg["nside"] = nside
+        cfg["lmax"] = lmax if lmax is not None else 2 * nside
+    ns, lm = cfg["nside"], cfg["lmax"]
+    seeds = list(seeds)
+    cl = cl_analytic(lm)
+    r_sigma, r_mask = _streams(seeds[0] * 7919 + 1, 2)
+    sigma = noise_sigma(ns, cl, r_sigma, scan_depth=cfg["scan"])
+    mask = mask_band_disks(ns, r_mask, cfg["band"], cfg["disks"])
+    wl = Workload(name=name, nside=ns, lmax=lm, cl=cl, sigma=sigma, mask=mask, seeds=seeds)
+    for sd in seeds:
+        r_sig, r_noise = _streams(sd, 2)
+        wl.alm_true.append(draw_alm(lm, cl, r_sig) if with_signal else None)
+        wl.noise.append(draw_noise(sigma, mask, r_noise))
+    return wl
+
+
+def lambda_schedule(lambda0: float = 1000.0, nlev: int = 10) -> np.ndarray:
+    """Geometric cooling 1000 -> 1 over nlev levels (last exactly 1)."""
+    lam = np.array([lambda0 ** (1.0 - k / (nlev - 1)) for k in range(nlev)])
+    lam[-1] = 1.0
+    return lam
+
+
+def eps_schedule(nlev: int, eps0: float = 1e-4, eps_final: float = 1e-6) -> np.ndarray:
+    """Cauchy thresholds cooled geometrically from eps0 to eps_final."""
+    return np.array([eps0 * (eps_final / eps0) ** (k / (nlev - 1)) for k in range(nlev)])
+
+
+def random_maps(nside: int, nmaps: int, seed: int) -> np.ndarray:
+    """Unstructured N(0,1) test maps [nmaps, 3, npix] (transform parity inputs)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((nmaps, 3, 12 * nside * nside))
+
+
+def random_alm(lmax: int, nalm_sets: int, seed: int, cl: np.ndarray | None = None) -> np.ndarray:
+    """Random harmonic coefficients [n, 3, nalm] (real-field valid: m = 0 real,
+    E/B zero for l < 2).  White unless cl is given."""
+    rng = np.random.default_rng(seed)
+    if cl is None:
+        cl = np.ones((4, lmax + 1))
+        cl[3] = 0.0
+        cl[1:3, :2] = 0.0
+    return np.stack([draw_alm(lmax, cl, rng) for _ in range(nalm_sets)])
