@@ -1,0 +1,200 @@
+/*
+ * dmwf.h -- C ABI of the GB300 (sm_103a) dual messenger Wiener filter for joint
+ * T/Q/U CMB maps on the HEALPix sphere.
+ *
+ * Method: Kodi Ramanah, Lavaux & Wandelt, "Optimal and fast E/B separation with
+ * a dual messenger field" (arXiv:1801.05358), Section 2 and Algorithm 1; the
+ * constrained realisations of Section 2.2.  The paper is flat-sky; this library
+ * carries it onto the HEALPix sphere with spin-0 and spin-2 harmonic transforms.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pixelisation: HEALPix RING order, npix = 12 nside^2, rings 1..4nside-1.
+ *  - Maps: [batch][3][npix] float64, components I (T), Q, U.
+ *  - Harmonic coefficients: [batch][3][nalm] complex128 (interleaved re, im),
+ *    fields T, E, B, m-major: index(l, m) = m (2 lmax + 1 - m) / 2 + l,
+ *    0 <= m <= l <= lmax, nalm = (lmax + 1)(lmax + 2) / 2.  Real fields: the
+ *    m < 0 coefficients are a_{l,-m} = (-1)^m conj(a_lm) and are not stored.
+ *  - Harmonics: Goldberg et al. (1967) spin-weighted harmonics
+ *    sY_lm = sqrt((2l+1)/4pi) d^l_{m,-s}(theta) e^{i m phi}; polarisation
+ *    (Q + iU) = sum a_{2,lm} 2Y_lm, (Q - iU) = sum a_{-2,lm} -2Y_lm,
+ *    a_{+-2} = -(a_E +- i a_B)  (the sphere form of Eqs. 12-16).
+ *  - Synthesis Y: alm -> map.  Analysis A = Omega Y^dagger with
+ *    Omega = 4 pi / npix (no ring weights).
+ *  - Spectra: cl[4][lmax+1] float64 = C^TT, C^EE, C^BB, C^TE (Eq. 10).
+ *  - Noise: diagonal N = sigma^2 per pixel and component; masked pixels have
+ *    N^{-1} = 0 (Appendix B).  T = alpha 1 with alpha = min N over observed
+ *    pixel-components (Section 2), w = alpha / N.
+ *  - Device pointers are CUDA device addresses on the plan's device; `stream`
+ *    is a cudaStream_t (NULL = legacy default stream).  Calls are ordered on
+ *    that stream; a call returns once its work is enqueued unless it says it
+ *    synchronises.  The caller owns every buffer it passes; the plan owns its
+ *    workspace.  A plan is not thread-safe: one host thread at a time.
+ *
+ * Errors: every call returns a dm_status.  DM_EINVAL for bad arguments (the
+ * plan is left unchanged), DM_ECUDA for a CUDA failure, DM_ENOMEM when device
+ * memory runs out, DM_ENOTCONV when max_iter was reached before the last level
+ * converged (the last iterate is still written).  dm_last_error() returns a
+ * message for the last failure on that plan.
+ */
+#ifndef DMWF_H
+#define DMWF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dm_plan dm_plan;
+
+typedef enum {
+  DM_OK = 0,
+  DM_EINVAL = 1,
+  DM_ENOMEM = 2,
+  DM_ECUDA = 3,
+  DM_ENOTCONV = 4,
+  DM_ETIMEOUT = 5,
+  DM_EAGAIN = 6,
+  DM_EBUSY = 7
+} dm_status;
+
+/* Arithmetic of the Legendre contraction and of map storage.
+ * DM_FP64: everything in FP64.
+ * DM_MIXED_FP32: FP64 recurrence (Legendre/Wigner values generated in FP64),
+ *   FP32 contraction, FP32 ring FFTs and maps on the device; FP64 per-l 3x3
+ *   filter, FP64 harmonic state and FP64 convergence norms. */
+typedef enum { DM_FP64 = 0, DM_MIXED_FP32 = 1 } dm_precision;
+
+/* Cooling and stopping schedule of Algorithm 1 (Section 3.2).
+ * Levels: lambda_k = xi_k / T_h = lambda0^(1 - k/(n_levels-1)), k = 0..n_levels-1,
+ * the last level exactly 1 (mu = 0: the Wiener filter itself).
+ * iters_per_level > 0: exactly that many iterations per level (no test).
+ * Otherwise a level ends when ||s_i - s_{i-1}|| / ||s_i|| < eps_k with
+ *   eta > 0 : eps_k = max(eps_final, eps0 * eta^-k), eps_final at the last level;
+ *   eta == 0: eps_k = eps0 (eps_final/eps0)^(k/(n_levels-1)).
+ * max_iter caps the total; check_every is how often (in iterations) the host
+ * reads the device-side convergence state (>= 1). */
+typedef struct {
+  double lambda0;
+  int n_levels;
+  int iters_per_level;
+  double eps0;
+  double eps_final;
+  double eta;
+  int max_iter;
+  int check_every;
+} dm_schedule;
+
+#define DM_MAX_LEVELS 64
+
+/* Per-RHS statistics, valid after the call returns. */
+typedef struct {
+  int iters_total;
+  int levels_done;
+  int iters_per_level[DM_MAX_LEVELS];
+  double cauchy_final;
+} dm_stats;
+
+/* --- plan ------------------------------------------------------------------ */
+
+/* Create a plan for `batch` right-hand sides of one geometry on the current
+ * CUDA device.  1 <= nside <= 1024 (a power of two is not required),
+ * 2 <= lmax <= 4 nside, 1 <= batch <= 4096.  Builds the ring geometry, the
+ * FFT chirps, the recurrence coefficient and seed tables, and allocates the
+ * workspace (DM_ENOMEM if it does not fit). */
+dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out);
+void dm_plan_destroy(dm_plan *plan);
+const char *dm_last_error(const dm_plan *plan);
+/* Sizes of the plan: npix, nalm, nrings, device bytes held. */
+dm_status dm_plan_info(const dm_plan *plan, int64_t *npix, int64_t *nalm, int *nrings, int64_t *workspace_bytes);
+
+/* Arithmetic mode (default DM_FP64). */
+dm_status dm_set_precision(dm_plan *plan, dm_precision prec);
+
+/* Signal covariance, Eq. 10: host array cl[4][lmax+1] (TT, EE, BB, TE).
+ * Each per-l TE block must be positive semi-definite (DM_EINVAL otherwise). */
+dm_status dm_set_spectra(dm_plan *plan, const double *cl);
+
+/* Noise and mask (shared by every RHS of the plan), host arrays:
+ * sigma[3][npix] per-pixel noise std-dev of I, Q, U (> 0 and finite on
+ * observed pixels); mask[npix], 1 = observed, 0 = masked; NULL = full sky.
+ * Computes alpha = min sigma^2 over observed pixel-components, T_h = alpha
+ * Omega and w = alpha / sigma^2 on the device. */
+dm_status dm_set_noise_mask(dm_plan *plan, const double *sigma, const uint8_t *mask);
+
+/* Schedule (defaults: lambda0 1000, 10 levels, 10 iterations per level). */
+dm_status dm_set_schedule(dm_plan *plan, const dm_schedule *sched);
+
+/* Force the per-level iteration counts (length n_levels of the schedule),
+ * overriding iters_per_level and the Cauchy test; NULL clears it.  Used to
+ * replay a recorded run. */
+dm_status dm_set_forced_iters(dm_plan *plan, const int *iters);
+
+/* --- the hot path -------------------------------------------------------- */
+
+/* Wiener filter by the dual messenger iteration (Algorithm 1).
+ * d: device [batch][3][npix] data maps (masked pixels ignored).
+ * s_out: device [batch][3][npix] Wiener-filtered maps (s = Y a).
+ * alm_out: device [batch][3][nalm] complex128 or NULL.
+ * stats: host [batch] or NULL.  Synchronises the stream before returning. */
+dm_status dm_wiener_filter(dm_plan *plan, const double *d, double *s_out, double *alm_out,
+                           dm_stats *stats, void *stream);
+
+/* Same, with HOST buffers (pinned memory recommended): copies d in, runs,
+ * copies s_out (and alm_out if non-NULL) back. */
+dm_status dm_wiener_filter_host(dm_plan *plan, const double *d_host, double *s_host, double *alm_host,
+                                dm_stats *stats, void *stream);
+
+/* Constrained realisations, Section 2.2, Eq. 19:
+ * s_CR = W(d - dhat) + shat with shat = Y ahat, ahat ~ S, dhat = shat + nhat,
+ * nhat ~ N on observed pixels, drawn from seeds[batch] (host) with the
+ * Philox4x32-10 generator described at dm_draw_cr_inputs.  One dual messenger
+ * run per realisation.  Buffers as in dm_wiener_filter; s_cr_out device. */
+dm_status dm_constrained_realization(dm_plan *plan, const double *d, const uint64_t *seeds,
+                                     double *s_cr_out, double *alm_cr_out, dm_stats *stats, void *stream);
+
+/* The random inputs of a constrained realisation (step a9), per RHS b with
+ * key = (seed_b low 32 bits, seed_b high 32 bits):
+ *  ahat: for alm index i, Philox counters (i, j, 0, 0), j = 0, 1, 2 give unit
+ *   normals for T, E, B: two 53-bit uniforms u1 = words 0,1 and u2 = words 2,3
+ *   ((hi >> 5) * 2^26 + (lo >> 6) + 0.5) * 2^-53, Box-Muller z0 = r cos(2 pi u2),
+ *   z1 = r sin(2 pi u2), r = sqrt(-2 ln u1); re from z0, im from z1.  ahat = L z
+ *   with L the Cholesky factor of [[TT, TE], [TE, EE]] and sqrt(BB); m = 0 real
+ *   (full variance), m > 0 re and im each at half variance.
+ *  nhat: for pixel p, counters (p, 0, 1, 0) -> (I, Q), (p, 1, 1, 0) -> (U, -),
+ *   times sigma, zero on masked pixels.
+ * Outputs (device, any may be NULL): ahat [batch][3][nalm] complex128,
+ * shat = Y ahat and dhat = (shat + nhat) on observed pixels, [batch][3][npix]. */
+dm_status dm_draw_cr_inputs(dm_plan *plan, const uint64_t *seeds, double *ahat, double *shat, double *dhat,
+                            void *stream);
+
+/* --- transform stages (the steps of the iteration, exposed for testing) ---- */
+
+/* Synthesis map = Y alm (Legendre synthesis + inverse ring FFT), device buffers. */
+dm_status dm_alm2map(dm_plan *plan, const double *alm, double *map, void *stream);
+/* Analysis alm = A map = Omega Y^dagger map (ring FFT + Legendre analysis). */
+dm_status dm_map2alm(dm_plan *plan, const double *map, double *alm, void *stream);
+/* Ring DFTs alone: rc[batch][3][nrings][lmax+1] complex128,
+ * rc = sum_j f_j e^{-i m phi_j} per ring (forward); inverse is the real map
+ * f_j = Re rc_0 + 2 sum_{m>0} Re(rc_m e^{i m phi_j}). */
+dm_status dm_ring_fft_forward(dm_plan *plan, const double *map, double *rc, void *stream);
+dm_status dm_ring_fft_inverse(dm_plan *plan, const double *rc, double *map, void *stream);
+/* Legendre stages alone, rc in the layout above:
+ * synthesis rc^T = sum_l aT lambda, rc^Q = -sum_l (aE lam+ + i aB lam-),
+ * rc^U = -sum_l (aB lam+ - i aE lam-), lam+- = (2lambda +- -2lambda)/2;
+ * analysis is its Omega-scaled adjoint (ring sums). */
+dm_status dm_legendre_synthesis(dm_plan *plan, const double *alm, double *rc, void *stream);
+dm_status dm_legendre_analysis(dm_plan *plan, const double *rc, double *alm, void *stream);
+/* Per-l filter of level lambda (Eq. 8): alm_out = F alm_in with
+ * F = V diag(f_e) V^T, f_e = max(S_e, mu)/(max(S_e, mu) + T_h), mu = (lambda-1) T_h. */
+dm_status dm_apply_filter(dm_plan *plan, double lambda, const double *alm_in, double *alm_out, void *stream);
+/* alpha and T_h of the current noise model (host outputs). */
+dm_status dm_noise_info(const dm_plan *plan, double *alpha, double *t_h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMWF_H */

@@ -1,0 +1,468 @@
+// dm_api.cu -- the extern "C" entry points of include/dmwf.h: plan lifecycle,
+// argument validation, and the host driver of Algorithm 1 that enqueues the
+// device stages and polls the device-side convergence state.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "dm_internal.h"
+
+using namespace dmwf;
+
+namespace {
+
+dm_status fail(dm_plan *p, dm_status s, const std::string &msg) {
+  if (p) p->err = msg;
+  return s;
+}
+
+dm_status cuda_fail(dm_plan *p, cudaError_t e, const char *where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (p) p->err = m;
+  return e == cudaErrorMemoryAllocation ? DM_ENOMEM : DM_ECUDA;
+}
+
+#define DM_CU(call, where)                          \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(p, e_, where); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(dm_plan *p, T **ptr, size_t count) {
+  size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+  cudaError_t e = cudaMalloc((void **)ptr, bytes);
+  if (e == cudaSuccess) p->bytes += (int64_t)bytes;
+  return e;
+}
+
+void free_all(dm_plan *p) {
+  void *ptrs[] = {p->rings, p->pairs, p->phase, p->bhat, p->twid, p->rec, p->seed, p->seed_exp, p->cl,
+                  p->filt, p->w, p->mask, p->sigma, p->rc, p->a, p->apart, p->wd, p->norms, p->state,
+                  p->lev, p->tmpmap, p->tmpmap2, p->tmpalm, p->seeds_dev, p->coef_tmp};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+}
+
+void default_schedule(dm_schedule *s) {
+  s->lambda0 = 1000.0;
+  s->n_levels = 10;
+  s->iters_per_level = 10;
+  s->eps0 = 1e-4;
+  s->eps_final = 1e-6;
+  s->eta = 0.0;
+  s->max_iter = 100000;
+  s->check_every = 8;
+}
+
+// Host copy of the level table; the device copy drives k_control_step.
+dm_status upload_levels(dm_plan *p) {
+  const dm_schedule &s = p->sched;
+  LevelDev L{};
+  L.n_levels = s.n_levels;
+  L.max_iter = s.max_iter;
+  p->lambdas.assign(s.n_levels, 1.0);
+  for (int k = 0; k < s.n_levels; ++k) {
+    p->lambdas[k] = (s.n_levels == 1) ? 1.0 : pow(s.lambda0, 1.0 - (double)k / (double)(s.n_levels - 1));
+    double e;
+    if (s.eta > 0.0)
+      e = std::max(s.eps_final, s.eps0 * pow(s.eta, -(double)k));
+    else
+      e = (s.n_levels == 1) ? s.eps_final
+                            : s.eps0 * pow(s.eps_final / s.eps0, (double)k / (double)(s.n_levels - 1));
+    L.eps[k] = e;
+  }
+  p->lambdas[s.n_levels - 1] = 1.0;
+  L.eps[s.n_levels - 1] = s.eps_final;
+  if (!p->forced.empty()) {
+    L.forced = 1;
+    for (int k = 0; k < s.n_levels; ++k) L.fixed_iters[k] = p->forced[k];
+  } else if (s.iters_per_level > 0) {
+    L.forced = 1;
+    for (int k = 0; k < s.n_levels; ++k) L.fixed_iters[k] = s.iters_per_level;
+  }
+  DM_CU(cudaMemcpy(p->lev, &L, sizeof(LevelDev), cudaMemcpyHostToDevice), "upload levels");
+  return DM_OK;
+}
+
+dm_status refresh_filters(dm_plan *p) {
+  if (!p->have_cl || !p->have_noise) return DM_OK;
+  DM_CU(build_filters(p, 0), "build filters");
+  DM_CU(cudaDeviceSynchronize(), "build filters");
+  return DM_OK;
+}
+
+dm_status check_ready(dm_plan *p) {
+  if (!p) return DM_EINVAL;
+  if (!p->have_cl) return fail(p, DM_EINVAL, "spectra not set (dm_set_spectra)");
+  if (!p->have_noise) return fail(p, DM_EINVAL, "noise not set (dm_set_noise_mask)");
+  return DM_OK;
+}
+
+// The iteration driver.  Device stages per iteration:
+//   analysis + harmonic step  a <- F_k [a + A (t - s)]      (k_leg_ana64 + k_ana_reduce)
+//   synthesis                 F_m(theta) from a             (k_leg_syn64)
+//   ring stage                s, Cauchy partials, t - s, G_m (k_ring<RING_ITER>)
+//   control                   Cauchy ratio, level, stop     (k_control_step)
+dm_status run_dm(dm_plan *p, const double *d, double *s_out, cudaStream_t st) {
+  const int64_t n3 = 3 * p->npix;
+  DM_CU(cudaMemsetAsync(p->a, 0, sizeof(double2) * 3 * p->nalm * p->batch, st), "zero a");
+  DM_CU(cudaMemsetAsync(s_out, 0, sizeof(double) * n3 * p->batch, st), "zero s");
+  DM_CU(prepare_wd(p, d, st), "w d");
+  DM_CU(control_init(p, st), "control init");
+  p->state_active = true;
+  DM_CU(ring_stage(p, RING_INIT, d, nullptr, st), "ring init");
+  std::vector<SolveState> hs(p->batch);
+  int launched = 0;
+  const dm_schedule &S = p->sched;
+  long cap = (long)S.max_iter + 4;
+  if (S.iters_per_level > 0 || !p->forced.empty()) {
+    long tot = 0;
+    for (int k = 0; k < S.n_levels; ++k) tot += p->forced.empty() ? S.iters_per_level : p->forced[k];
+    cap = tot + 4;
+  }
+  const int every = std::max(1, S.check_every);
+  dm_status rs = DM_OK;
+  for (;;) {
+    for (int k = 0; k < every; ++k) {
+      cudaError_t e;
+      if ((e = legendre_analysis(p, ANA_DM_STEP, p->a, st))) { rs = cuda_fail(p, e, "analysis"); break; }
+      if ((e = legendre_synthesis(p, p->a, st))) { rs = cuda_fail(p, e, "synthesis"); break; }
+      if ((e = ring_stage(p, RING_ITER, nullptr, s_out, st))) { rs = cuda_fail(p, e, "ring"); break; }
+      if ((e = control_step(p, st))) { rs = cuda_fail(p, e, "control"); break; }
+    }
+    if (rs != DM_OK) break;
+    launched += every;
+    cudaError_t e = cudaMemcpyAsync(hs.data(), p->state, sizeof(SolveState) * p->batch, cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) { rs = cuda_fail(p, e, "poll state"); break; }
+    bool all = true;
+    for (auto &s : hs) all = all && s.done;
+    if (all) break;
+    if (launched > cap) { rs = fail(p, DM_ENOTCONV, "iteration cap reached"); break; }
+  }
+  p->state_active = false;
+  return rs;
+}
+
+void fill_stats(dm_plan *p, dm_stats *stats, dm_status *rs) {
+  std::vector<SolveState> hs(p->batch);
+  cudaMemcpy(hs.data(), p->state, sizeof(SolveState) * p->batch, cudaMemcpyDeviceToHost);
+  bool notconv = false;
+  for (int b = 0; b < p->batch; ++b) {
+    notconv = notconv || hs[b].notconv;
+    if (!stats) continue;
+    dm_stats &o = stats[b];
+    memset(&o, 0, sizeof(o));
+    o.iters_total = hs[b].iters_total;
+    o.levels_done = hs[b].done ? p->sched.n_levels : hs[b].level;
+    for (int k = 0; k < DM_MAX_LEVELS; ++k) o.iters_per_level[k] = hs[b].iters_per_level[k];
+    o.cauchy_final = hs[b].cauchy;
+  }
+  if (notconv && *rs == DM_OK) *rs = fail(p, DM_ENOTCONV, "max_iter reached before the last level converged");
+}
+
+}  // namespace
+
+extern "C" {
+
+dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out) {
+  if (!out) return DM_EINVAL;
+  *out = nullptr;
+  if (nside < 1 || nside > 1024 || lmax < 2 || lmax > 4 * nside || batch < 1 || batch > 4096) return DM_EINVAL;
+  dm_plan *p = new dm_plan();
+  cudaGetDevice(&p->device);
+  p->nside = nside;
+  p->lmax = lmax;
+  p->mmax = lmax;
+  p->batch = batch;
+  p->npix = 12LL * nside * nside;
+  p->nalm = (int64_t)(lmax + 1) * (lmax + 2) / 2;
+  p->nrings = 4 * nside - 1;
+  p->npairs = 2 * nside;
+  p->nchunk = (p->npairs + 63) / 64;
+  default_schedule(&p->sched);
+  cudaError_t e = build_tables(p);
+  auto bad = [&](cudaError_t err, const char *w) {
+    dm_status s = cuda_fail(p, err, w);
+    fprintf(stderr, "dm_plan_create: %s\n", p->err.c_str());
+    free_all(p);
+    delete p;
+    return s;
+  };
+  if (e) return bad(e, "build tables");
+  const int64_t B = batch, n3 = 3 * p->npix;
+  if ((e = dalloc(p, &p->cl, 4 * (size_t)(lmax + 1)))) return bad(e, "alloc");
+  if ((e = dalloc(p, &p->w, n3))) return bad(e, "alloc");
+  if ((e = dalloc(p, &p->mask, p->npix))) return bad(e, "alloc");
+  if ((e = dalloc(p, &p->sigma, n3))) return bad(e, "alloc");
+  if ((e = dalloc(p, &p->rc, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return bad(e, "alloc rc");
+  if ((e = dalloc(p, &p->a, (size_t)B * 3 * p->nalm))) return bad(e, "alloc a");
+  if ((e = dalloc(p, &p->apart, (size_t)B * p->nchunk * 3 * p->nalm))) return bad(e, "alloc apart");
+  if ((e = dalloc(p, &p->wd, (size_t)B * n3))) return bad(e, "alloc wd");
+  if ((e = dalloc(p, &p->norms, (size_t)B * 3 * p->nrings * 2))) return bad(e, "alloc norms");
+  if ((e = dalloc(p, &p->state, (size_t)B))) return bad(e, "alloc state");
+  if ((e = dalloc(p, &p->lev, 1))) return bad(e, "alloc lev");
+  if ((e = dalloc(p, &p->tmpmap, (size_t)B * n3))) return bad(e, "alloc tmp");
+  if ((e = dalloc(p, &p->tmpmap2, (size_t)B * n3))) return bad(e, "alloc tmp");
+  if ((e = dalloc(p, &p->tmpalm, (size_t)B * 3 * p->nalm))) return bad(e, "alloc tmp");
+  if ((e = dalloc(p, &p->seeds_dev, (size_t)B))) return bad(e, "alloc seeds");
+  if ((e = dalloc(p, &p->coef_tmp, 4 * (size_t)(lmax + 1)))) return bad(e, "alloc coef");
+  cudaMemset(p->rc, 0, sizeof(double2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
+  cudaMemset(p->mask, 1, p->npix);
+  dm_status s = upload_levels(p);
+  if (s != DM_OK) {
+    free_all(p);
+    delete p;
+    return s;
+  }
+  if ((e = cudaDeviceSynchronize())) return bad(e, "create");
+  *out = p;
+  return DM_OK;
+}
+
+void dm_plan_destroy(dm_plan *p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  free_all(p);
+  delete p;
+}
+
+const char *dm_last_error(const dm_plan *p) { return p ? p->err.c_str() : "null plan"; }
+
+dm_status dm_plan_info(const dm_plan *p, int64_t *npix, int64_t *nalm, int *nrings, int64_t *ws) {
+  if (!p) return DM_EINVAL;
+  if (npix) *npix = p->npix;
+  if (nalm) *nalm = p->nalm;
+  if (nrings) *nrings = p->nrings;
+  if (ws) *ws = p->bytes;
+  return DM_OK;
+}
+
+dm_status dm_set_precision(dm_plan *p, dm_precision prec) {
+  if (!p) return DM_EINVAL;
+  if (prec != DM_FP64) return fail(p, DM_EINVAL, "precision mode not available in this build");
+  p->prec = prec;
+  return DM_OK;
+}
+
+dm_status dm_set_spectra(dm_plan *p, const double *cl) {
+  if (!p || !cl) return DM_EINVAL;
+  const int L = p->lmax + 1;
+  for (int l = 0; l < L; ++l) {
+    double tt = cl[l], ee = cl[L + l], bb = cl[2 * L + l], te = cl[3 * L + l];
+    if (!std::isfinite(tt) || !std::isfinite(ee) || !std::isfinite(bb) || !std::isfinite(te))
+      return fail(p, DM_EINVAL, "non-finite spectrum");
+    if (tt < 0 || ee < 0 || bb < 0 || te * te > tt * ee * (1.0 + 1e-12))
+      return fail(p, DM_EINVAL, "spectrum block not positive semi-definite at l = " + std::to_string(l));
+  }
+  p->cl_h.assign(cl, cl + 4 * L);
+  DM_CU(cudaMemcpy(p->cl, cl, sizeof(double) * 4 * L, cudaMemcpyHostToDevice), "upload cl");
+  p->have_cl = true;
+  return refresh_filters(p);
+}
+
+dm_status dm_set_noise_mask(dm_plan *p, const double *sigma, const uint8_t *mask) {
+  if (!p || !sigma) return DM_EINVAL;
+  const int64_t np = p->npix;
+  int64_t nobs = 0;
+  for (int64_t i = 0; i < np; ++i) {
+    bool obs = !mask || mask[i];
+    if (!obs) continue;
+    ++nobs;
+    for (int f = 0; f < 3; ++f) {
+      double s = sigma[f * np + i];
+      if (!(s > 0.0) || !std::isfinite(s))
+        return fail(p, DM_EINVAL, "sigma must be finite and > 0 on observed pixels");
+    }
+  }
+  if (nobs == 0) return fail(p, DM_EINVAL, "mask leaves no observed pixel");
+  DM_CU(cudaMemcpy(p->sigma, sigma, sizeof(double) * 3 * np, cudaMemcpyHostToDevice), "upload sigma");
+  if (mask)
+    DM_CU(cudaMemcpy(p->mask, mask, np, cudaMemcpyHostToDevice), "upload mask");
+  else
+    DM_CU(cudaMemset(p->mask, 1, np), "mask");
+  DM_CU(build_noise(p, 0), "noise");
+  p->have_noise = true;
+  return refresh_filters(p);
+}
+
+dm_status dm_set_schedule(dm_plan *p, const dm_schedule *s) {
+  if (!p || !s) return DM_EINVAL;
+  if (s->n_levels < 1 || s->n_levels > DM_MAX_LEVELS || !(s->lambda0 >= 1.0) || s->max_iter < 1 ||
+      s->iters_per_level < 0)
+    return fail(p, DM_EINVAL, "bad schedule");
+  if (s->iters_per_level == 0 && (!(s->eps0 > 0) || !(s->eps_final > 0) || s->eta < 0))
+    return fail(p, DM_EINVAL, "bad Cauchy thresholds");
+  p->sched = *s;
+  if (p->sched.check_every < 1) p->sched.check_every = 1;
+  if (!p->forced.empty() && (int)p->forced.size() != s->n_levels) p->forced.clear();
+  dm_status r = upload_levels(p);
+  if (r != DM_OK) return r;
+  return refresh_filters(p);
+}
+
+dm_status dm_set_forced_iters(dm_plan *p, const int *iters) {
+  if (!p) return DM_EINVAL;
+  if (!iters) {
+    p->forced.clear();
+  } else {
+    for (int k = 0; k < p->sched.n_levels; ++k)
+      if (iters[k] < 0) return fail(p, DM_EINVAL, "negative iteration count");
+    p->forced.assign(iters, iters + p->sched.n_levels);
+  }
+  return upload_levels(p);
+}
+
+dm_status dm_wiener_filter(dm_plan *p, const double *d, double *s_out, double *alm_out, dm_stats *stats,
+                           void *stream) {
+  dm_status r = check_ready(p);
+  if (r != DM_OK) return r;
+  if (!d || !s_out) return fail(p, DM_EINVAL, "null buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  r = run_dm(p, d, s_out, st);
+  if (r != DM_OK && r != DM_ENOTCONV) return r;
+  if (alm_out)
+    DM_CU(cudaMemcpyAsync(alm_out, p->a, sizeof(double2) * 3 * p->nalm * p->batch, cudaMemcpyDeviceToDevice, st),
+          "copy alm");
+  DM_CU(cudaStreamSynchronize(st), "sync");
+  fill_stats(p, stats, &r);
+  return r;
+}
+
+dm_status dm_wiener_filter_host(dm_plan *p, const double *d_host, double *s_host, double *alm_host,
+                                dm_stats *stats, void *stream) {
+  dm_status r = check_ready(p);
+  if (r != DM_OK) return r;
+  if (!d_host || !s_host) return fail(p, DM_EINVAL, "null buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t mb = sizeof(double) * 3 * p->npix * p->batch;
+  // tmpmap2 holds d, tmpmap receives s
+  DM_CU(cudaMemcpyAsync(p->tmpmap2, d_host, mb, cudaMemcpyHostToDevice, st), "h2d");
+  r = run_dm(p, p->tmpmap2, p->tmpmap, st);
+  if (r != DM_OK && r != DM_ENOTCONV) return r;
+  DM_CU(cudaMemcpyAsync(s_host, p->tmpmap, mb, cudaMemcpyDeviceToHost, st), "d2h");
+  if (alm_host)
+    DM_CU(cudaMemcpyAsync(alm_host, p->a, sizeof(double2) * 3 * p->nalm * p->batch, cudaMemcpyDeviceToHost, st),
+          "d2h alm");
+  DM_CU(cudaStreamSynchronize(st), "sync");
+  fill_stats(p, stats, &r);
+  return r;
+}
+
+dm_status dm_draw_cr_inputs(dm_plan *p, const uint64_t *seeds, double *ahat, double *shat, double *dhat,
+                            void *stream) {
+  if (!p || !seeds) return DM_EINVAL;
+  if (!p->have_cl || !p->have_noise) return fail(p, DM_EINVAL, "spectra and noise must be set");
+  cudaStream_t st = (cudaStream_t)stream;
+  DM_CU(cudaMemcpyAsync(p->seeds_dev, seeds, sizeof(uint64_t) * p->batch, cudaMemcpyHostToDevice, st), "seeds");
+  DM_CU(draw_signal(p, p->seeds_dev, p->tmpalm, st), "draw signal");
+  DM_CU(legendre_synthesis(p, p->tmpalm, st), "synthesis");
+  DM_CU(ring_stage(p, RING_INV_MAP, nullptr, p->tmpmap, st), "ring inverse");
+  if (dhat) DM_CU(draw_noise_add(p, p->seeds_dev, p->tmpmap, dhat, st), "draw noise");
+  const size_t mb = sizeof(double) * 3 * p->npix * p->batch;
+  if (shat) DM_CU(cudaMemcpyAsync(shat, p->tmpmap, mb, cudaMemcpyDeviceToDevice, st), "copy shat");
+  if (ahat)
+    DM_CU(cudaMemcpyAsync(ahat, p->tmpalm, sizeof(double2) * 3 * p->nalm * p->batch, cudaMemcpyDeviceToDevice, st),
+          "copy ahat");
+  DM_CU(cudaStreamSynchronize(st), "sync");
+  return DM_OK;
+}
+
+dm_status dm_constrained_realization(dm_plan *p, const double *d, const uint64_t *seeds, double *s_cr_out,
+                                     double *alm_cr_out, dm_stats *stats, void *stream) {
+  dm_status r = check_ready(p);
+  if (r != DM_OK) return r;
+  if (!d || !seeds || !s_cr_out) return fail(p, DM_EINVAL, "null buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = 3 * p->npix * p->batch;
+  // shat -> tmpmap, ahat -> tmpalm, dhat -> tmpmap2, then tmpmap2 = d - dhat
+  DM_CU(cudaMemcpyAsync(p->seeds_dev, seeds, sizeof(uint64_t) * p->batch, cudaMemcpyHostToDevice, st), "seeds");
+  DM_CU(draw_signal(p, p->seeds_dev, p->tmpalm, st), "draw signal");
+  DM_CU(legendre_synthesis(p, p->tmpalm, st), "synthesis");
+  DM_CU(ring_stage(p, RING_INV_MAP, nullptr, p->tmpmap, st), "ring inverse");
+  DM_CU(draw_noise_add(p, p->seeds_dev, p->tmpmap, p->tmpmap2, st), "draw noise");
+  DM_CU(axpy_maps(n, p->tmpmap2, -2.0, p->tmpmap2, st), "negate");   // -dhat
+  DM_CU(axpy_maps(n, d, 1.0, p->tmpmap2, st), "d - dhat");
+  r = run_dm(p, p->tmpmap2, s_cr_out, st);
+  if (r != DM_OK && r != DM_ENOTCONV) return r;
+  DM_CU(axpy_maps(n, p->tmpmap, 1.0, s_cr_out, st), "+ shat");
+  if (alm_cr_out) {
+    DM_CU(cudaMemcpyAsync(alm_cr_out, p->a, sizeof(double2) * 3 * p->nalm * p->batch, cudaMemcpyDeviceToDevice, st),
+          "copy alm");
+    DM_CU(axpy_maps(6 * p->nalm * p->batch, (const double *)p->tmpalm, 1.0, alm_cr_out, st), "+ ahat");
+  }
+  DM_CU(cudaStreamSynchronize(st), "sync");
+  fill_stats(p, stats, &r);
+  return r;
+}
+
+dm_status dm_alm2map(dm_plan *p, const double *alm, double *map, void *stream) {
+  if (!p || !alm || !map) return DM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  DM_CU(legendre_synthesis(p, (const double2 *)alm, st), "synthesis");
+  DM_CU(ring_stage(p, RING_INV_MAP, nullptr, map, st), "ring inverse");
+  return DM_OK;
+}
+
+dm_status dm_map2alm(dm_plan *p, const double *map, double *alm, void *stream) {
+  if (!p || !alm || !map) return DM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  DM_CU(ring_stage(p, RING_FWD_MAP, map, nullptr, st), "ring forward");
+  DM_CU(legendre_analysis(p, ANA_PLAIN, (double2 *)alm, st), "analysis");
+  return DM_OK;
+}
+
+dm_status dm_ring_fft_forward(dm_plan *p, const double *map, double *rc, void *stream) {
+  if (!p || !map || !rc) return DM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  DM_CU(ring_stage(p, RING_FWD_MAP, map, nullptr, st), "ring forward");
+  DM_CU(rc_to_public(p, (double2 *)rc, st), "layout");
+  return DM_OK;
+}
+
+dm_status dm_ring_fft_inverse(dm_plan *p, const double *rc, double *map, void *stream) {
+  if (!p || !map || !rc) return DM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  DM_CU(rc_from_public(p, (const double2 *)rc, st), "layout");
+  DM_CU(ring_stage(p, RING_INV_MAP, nullptr, map, st), "ring inverse");
+  return DM_OK;
+}
+
+dm_status dm_legendre_synthesis(dm_plan *p, const double *alm, double *rc, void *stream) {
+  if (!p || !alm || !rc) return DM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  DM_CU(legendre_synthesis(p, (const double2 *)alm, st), "synthesis");
+  DM_CU(rc_to_public(p, (double2 *)rc, st), "layout");
+  return DM_OK;
+}
+
+dm_status dm_legendre_analysis(dm_plan *p, const double *rc, double *alm, void *stream) {
+  if (!p || !alm || !rc) return DM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  DM_CU(rc_from_public(p, (const double2 *)rc, st), "layout");
+  DM_CU(legendre_analysis(p, ANA_PLAIN, (double2 *)alm, st), "analysis");
+  return DM_OK;
+}
+
+dm_status dm_apply_filter(dm_plan *p, double lambda, const double *alm_in, double *alm_out, void *stream) {
+  if (!p || !alm_in || !alm_out) return DM_EINVAL;
+  if (!p->have_cl || !p->have_noise) return fail(p, DM_EINVAL, "spectra and noise must be set");
+  if (!(lambda >= 1.0)) return fail(p, DM_EINVAL, "lambda must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  DM_CU(build_filter_one(p, lambda, p->coef_tmp, st), "filter");
+  DM_CU(apply_filter_level(p, p->coef_tmp, (const double2 *)alm_in, (double2 *)alm_out, st), "apply filter");
+  return DM_OK;
+}
+
+dm_status dm_noise_info(const dm_plan *p, double *alpha, double *t_h) {
+  if (!p || !p->have_noise) return DM_EINVAL;
+  if (alpha) *alpha = p->alpha;
+  if (t_h) *t_h = p->t_h;
+  return DM_OK;
+}
+
+}  // extern "C"

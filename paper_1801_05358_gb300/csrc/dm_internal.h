@@ -1,0 +1,153 @@
+// dm_internal.h -- plan layout and kernel launchers shared by the CUDA
+// translation units of libdmwf.  Not part of the public ABI (include/dmwf.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dmwf.h"
+
+namespace dmwf {
+
+// Per-ring geometry and FFT plan (device array, one entry per ring).
+struct RingDev {
+  int64_t start;     // first pixel of the ring (RING order)
+  int n;             // pixels in the ring (4i or 4 nside)
+  int h;             // n / 2: length of the complex FFT of the packed real ring
+  int M;             // FFT size: h when h is a power of two, else the Bluestein size
+  int bluestein;     // 1 when h is not a power of two
+  int shift;         // 1 when the first pixel sits half a pixel east of phi = 0
+  int pair;          // ring-pair index (north ring index - 1)
+  int side;          // 0 = northern (or equatorial) member, 1 = southern member
+  int64_t ph_off;    // offset of e^{-i pi q / n}, q in [0, 2n), in the phase table
+  int64_t bh_off;    // offset of the Bluestein kernel spectrum (M entries), -1 if none
+};
+
+// Per-ring-pair data for the Legendre stages.
+struct PairDev {
+  double x;          // cos(theta) of the northern ring
+  double omz, opz;   // 1 - x and 1 + x without cancellation
+};
+
+// Per-(m, l) recurrence coefficients (m-major like the alm index).
+//  spin 0 : lam_l = al * x * lam_{l-1} - bl * lam_{l-2}
+//  spin 2 : lp_l = a x lp_{l-1} + ac lm_{l-1} - b lp_{l-2}
+//           lm_l = a x lm_{l-1} + ac lp_{l-1} - b lm_{l-2}
+// with lp/lm = (2lambda +- -2lambda)/2 and a, ac, b taken at the source l-1.
+struct RecCoef {
+  double al, bl, a, ac, b, pad;
+};
+
+// Device-side solver state of one RHS.
+struct SolveState {
+  int level;          // current cooling level
+  int iter_in_level;  // iterations done at this level
+  int iters_total;
+  int done;           // 1 once the last level met its stopping rule
+  int first;          // 1 before the first iteration (t_0 = d)
+  int notconv;        // 1 when max_iter was hit
+  double cauchy;      // last Cauchy ratio
+  int iters_per_level[DM_MAX_LEVELS];
+};
+
+struct LevelDev {
+  int n_levels;
+  int max_iter;
+  int forced;                         // 1: fixed counts per level
+  int fixed_iters[DM_MAX_LEVELS];     // counts when forced
+  double eps[DM_MAX_LEVELS];
+};
+
+}  // namespace dmwf
+
+struct dm_plan {
+  int device = 0;
+  int nside = 0, lmax = 0, mmax = 0, batch = 0;
+  int64_t npix = 0, nalm = 0;
+  int nrings = 0, npairs = 0;
+  int fft_M_max = 1;            // largest FFT size over rings
+  dm_precision prec = DM_FP64;
+  std::string err;
+
+  // host copies
+  std::vector<dmwf::RingDev> rings_h;
+  std::vector<double> cl_h;     // [4][lmax+1]
+  bool have_cl = false, have_noise = false;
+  double alpha = 0.0, t_h = 0.0;
+
+  // schedule
+  dm_schedule sched{};
+  std::vector<int> forced;      // empty = not forced
+  std::vector<double> lambdas;  // per level
+
+  // device tables
+  dmwf::RingDev *rings = nullptr;
+  dmwf::PairDev *pairs = nullptr;
+  double2 *phase = nullptr;     // e^{-i pi q / n} tables
+  double2 *bhat = nullptr;      // Bluestein kernel spectra
+  double2 *twid = nullptr;      // e^{-2 pi i k / fft_M_max}, k < fft_M_max / 2
+  dmwf::RecCoef *rec = nullptr; // [nalm]
+  double *seed = nullptr;       // [mmax+1][npairs][3] : lambda_mm, lp, lm at l0 = max(m, 2)
+  int *seed_exp = nullptr;      // [mmax+1][npairs] : scale S (true = v 2^-S), 0 = plain
+  double *cl = nullptr;         // [4][lmax+1]
+  double *filt = nullptr;       // [n_levels][lmax+1][4]
+  int filt_levels = 0;
+  double *w = nullptr;          // [3][npix] alpha / N (0 masked)
+  uint8_t *mask = nullptr;      // [npix]
+  double *sigma = nullptr;      // [3][npix]
+
+  // workspace (per batch)
+  double2 *rc = nullptr;        // [B][3][mmax+1][npairs][2] ring coefficients
+  double2 *a = nullptr;         // [B][3][nalm] harmonic iterate
+  double2 *apart = nullptr;     // [B][nchunk][3][nalm] analysis partial sums
+  int nchunk = 0;               // pair chunks of the analysis
+  double *wd = nullptr;         // [B][3][npix] w * d
+  double *norms = nullptr;      // [B][3][nrings][2] Cauchy partial sums
+  dmwf::SolveState *state = nullptr;   // [B]
+  dmwf::LevelDev *lev = nullptr;
+  double *tmpmap = nullptr;     // [B][3][npix] scratch map (CR, host-buffer entry)
+  double *tmpmap2 = nullptr;    // [B][3][npix] scratch map
+  double2 *tmpalm = nullptr;    // [B][3][nalm] scratch alm (CR)
+  uint64_t *seeds_dev = nullptr;  // [B]
+  double *coef_tmp = nullptr;   // [lmax+1][4] filter of dm_apply_filter
+  bool state_active = false;    // kernels consult state[] (skip finished RHS)
+  int64_t bytes = 0;
+};
+
+namespace dmwf {
+
+// ---- launchers (stream-ordered; return cudaGetLastError()) ----
+cudaError_t build_tables(dm_plan *p);                        // geometry, phases, chirps, coefficients, seeds
+cudaError_t build_filters(dm_plan *p, cudaStream_t st);      // per-level filter coefficients
+cudaError_t build_noise(dm_plan *p, cudaStream_t st);        // alpha (reduction) and w
+
+// ring stage: mode
+enum RingMode { RING_FWD_MAP = 0, RING_INV_MAP = 1, RING_ITER = 2, RING_INIT = 3 };
+cudaError_t ring_stage(dm_plan *p, int mode, const double *in_map, double *out_map, cudaStream_t st);
+// public-layout permutations of the ring coefficients
+cudaError_t rc_to_public(dm_plan *p, double2 *pub, cudaStream_t st);
+cudaError_t rc_from_public(dm_plan *p, const double2 *pub, cudaStream_t st);
+
+// Legendre stages on the plan's rc buffer
+cudaError_t legendre_synthesis(dm_plan *p, const double2 *alm, cudaStream_t st);
+// analysis into apart, then reduce: out = (accumulate ? a_prev : 0) + Omega sum, then filter
+enum AnaEpilogue { ANA_PLAIN = 0, ANA_DM_STEP = 1 };
+cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st);
+cudaError_t apply_filter_level(dm_plan *p, const double *coef, const double2 *in, double2 *out, cudaStream_t st);
+cudaError_t build_filter_one(dm_plan *p, double lambda, double *coef, cudaStream_t st);
+
+// solver control
+cudaError_t control_init(dm_plan *p, cudaStream_t st);
+cudaError_t control_step(dm_plan *p, cudaStream_t st);
+cudaError_t prepare_wd(dm_plan *p, const double *d, cudaStream_t st);
+
+// constrained realisations
+cudaError_t draw_signal(dm_plan *p, const uint64_t *seeds_dev, double2 *ahat, cudaStream_t st);
+cudaError_t draw_noise_add(dm_plan *p, const uint64_t *seeds_dev, const double *shat, double *dhat,
+                           cudaStream_t st);
+cudaError_t axpy_maps(int64_t n, const double *x, double alpha, double *y, cudaStream_t st);
+
+}  // namespace dmwf

@@ -1,0 +1,349 @@
+// dm_legendre.cu -- FP64 Legendre/Wigner-d stages of the spherical harmonic
+// transforms: the harmonic-space half of a dual messenger iteration.
+//
+// Synthesis (F in Algorithm 1), per order m and ring pair (theta, pi - theta):
+//   F^T = sum_l aT lambda,  F^Q = -sum_l (aE lam+ + i aB lam-),
+//   F^U = -sum_l (aB lam+ - i aE lam-),  lam+- = (2lambda +- -2lambda)/2.
+// Analysis (sigma^{-1} F^dagger), the Omega-scaled adjoint:
+//   aT = Omega sum_r lambda G^T,  aE = -Omega sum_r (lam+ G^Q + i lam- G^U),
+//   aB = -Omega sum_r (lam+ G^U - i lam- G^Q).
+// The recurrences (spin 0 and the lam+- pair of the k = -+2 Wigner-d
+// recurrence) run on the fly in FP64 from per-(m, pair) seeds, one ring pair
+// per thread; the mirror ring comes from the parities
+//   lambda(pi - theta) = (-1)^{l+m} lambda,  lam+(pi - theta) = (-1)^{l+m} lam+,
+//   lam-(pi - theta) = -(-1)^{l+m} lam-.
+// Seeds below 2^-600 are carried as v 2^-S (S >= 600) and advanced without
+// accumulation until they become representable (negligible region).
+#include "dm_fft.cuh"
+#include "dm_internal.h"
+
+namespace dmwf {
+
+__device__ __forceinline__ int64_t alm_base(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
+__device__ __forceinline__ int64_t rc_index2(int b, int f, int m, int mmax, int pair, int npairs) {
+  return ((((int64_t)b * 3 + f) * (mmax + 1) + m) * npairs + pair) * 2;
+}
+
+// Recurrence state of one ring pair: current and previous values.
+struct Rec {
+  double l0, l1;    // lambda_l, lambda_{l-1}
+  double p0, p1;    // lam+_l, lam+_{l-1}
+  double q0, q1;    // lam-_l, lam-_{l-1}
+  int S;            // scale: true = value * 2^-S (0 = plain)
+};
+
+// advance from l to l+1 with the coefficients of target l+1
+__device__ __forceinline__ void rec_step(Rec &s, const RecCoef &c, double x) {
+  double nl = fma(c.al * x, s.l0, -c.bl * s.l1);
+  double ax = c.a * x;
+  double np = fma(ax, s.p0, fma(c.ac, s.q0, -c.b * s.p1));
+  double nq = fma(ax, s.q0, fma(c.ac, s.p0, -c.b * s.q1));
+  s.l1 = s.l0;
+  s.l0 = nl;
+  s.p1 = s.p0;
+  s.p0 = np;
+  s.q1 = s.q0;
+  s.q0 = nq;
+}
+
+// negligible-region bookkeeping (only when S > 0)
+__device__ __forceinline__ void rec_rescale(Rec &s) {
+  const double big = 0x1p300;
+  if (fabs(s.l0) > big || fabs(s.p0) > big || fabs(s.q0) > big) {
+    s.l0 *= 0x1p-300; s.l1 *= 0x1p-300;
+    s.p0 *= 0x1p-300; s.p1 *= 0x1p-300;
+    s.q0 *= 0x1p-300; s.q1 *= 0x1p-300;
+    s.S -= 300;
+    if (s.S < 600) {
+      double f = ldexp(1.0, -s.S);
+      s.l0 *= f; s.l1 *= f; s.p0 *= f; s.p1 *= f; s.q0 *= f; s.q1 *= f;
+      s.S = 0;
+    }
+  }
+}
+
+// Initial state at l = m.  Spin 2 starts at l0 = max(m, 2); for m < 2 its
+// values are zero until the seed is injected when advancing to l = 2.
+__device__ __forceinline__ void rec_init(Rec &s, const double *seed, const int *seed_exp, int m, int p,
+                                         int npairs) {
+  int64_t o = (int64_t)m * npairs + p;
+  s.l0 = seed[3 * o];
+  s.l1 = 0.0;
+  s.S = seed_exp[o];
+  if (m >= 2) {
+    s.p0 = seed[3 * o + 1];
+    s.q0 = seed[3 * o + 2];
+  } else {
+    s.p0 = 0.0;
+    s.q0 = 0.0;
+  }
+  s.p1 = 0.0;
+  s.q1 = 0.0;
+}
+
+__device__ __forceinline__ void rec_advance(Rec &s, const RecCoef &c, double x, int m, int l, const double *seed,
+                                            int p, int npairs) {
+  // l -> l+1
+  if (m < 2 && l + 1 == 2) {
+    int64_t o = (int64_t)m * npairs + p;
+    double nl = fma(c.al * x, s.l0, -c.bl * s.l1);
+    s.l1 = s.l0;
+    s.l0 = nl;
+    s.p1 = 0.0;
+    s.q1 = 0.0;
+    s.p0 = seed[3 * o + 1];
+    s.q0 = seed[3 * o + 2];
+  } else {
+    rec_step(s, c, x);
+  }
+  if (s.S) rec_rescale(s);
+}
+
+// ------------------------------------------------------------- synthesis
+constexpr int SYN_THREADS = 128;
+constexpr int SYN_CH = 64;
+
+__global__ void __launch_bounds__(SYN_THREADS) k_leg_syn64(const PairDev *__restrict__ pairs,
+                                                           const RecCoef *__restrict__ rec,
+                                                           const double *__restrict__ seed,
+                                                           const int *__restrict__ seed_exp,
+                                                           const double2 *__restrict__ alm, double2 *__restrict__ rc,
+                                                           int lmax, int mmax, int npairs, int64_t nalm,
+                                                           const SolveState *__restrict__ state) {
+  __shared__ double2 sT[SYN_CH], sE[SYN_CH], sB[SYN_CH];
+  __shared__ RecCoef sc[SYN_CH];
+  const int m = blockIdx.y, b = blockIdx.z;
+  if (state != nullptr && state[b].done) return;
+  const int p = blockIdx.x * SYN_THREADS + threadIdx.x;
+  const bool act = p < npairs;
+  const int pp = act ? p : npairs - 1;
+  const double x = pairs[pp].x;
+  Rec s;
+  rec_init(s, seed, seed_exp, m, pp, npairs);
+  // accumulators: index 0 = parity of (l + m) even, 1 = odd
+  double2 T0 = {0, 0}, T1 = {0, 0}, Q0 = {0, 0}, Q1 = {0, 0}, U0 = {0, 0}, U1 = {0, 0};
+  const int64_t base = alm_base(lmax, m);
+  const double2 *aT = alm + ((int64_t)b * 3 + 0) * nalm + base;
+  const double2 *aE = alm + ((int64_t)b * 3 + 1) * nalm + base;
+  const double2 *aB = alm + ((int64_t)b * 3 + 2) * nalm + base;
+  for (int lc = m; lc <= lmax; lc += SYN_CH) {
+    const int cnt = min(SYN_CH, lmax + 1 - lc);
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += SYN_THREADS) {
+      const int l = lc + j;
+      sT[j] = aT[l];
+      double2 e = aE[l], bb = aB[l];
+      sE[j] = make_double2(-e.x, -e.y);   // -aE
+      sB[j] = make_double2(-bb.x, -bb.y); // -aB
+      sc[j] = rec[base + l + 1];          // coefficients of target l + 1
+    }
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      const int l = lc + j;
+      if (s.S == 0) {
+        const double2 t = sT[j], ne = sE[j], nb = sB[j];
+        const double lam = s.l0, lp = s.p0, lq = s.q0;
+        if (((l - m) & 1) == 0) {
+          T0.x = fma(t.x, lam, T0.x); T0.y = fma(t.y, lam, T0.y);
+          Q0.x = fma(ne.x, lp, Q0.x); Q0.y = fma(ne.y, lp, Q0.y);   // -aE lam+
+          U0.x = fma(nb.x, lp, U0.x); U0.y = fma(nb.y, lp, U0.y);   // -aB lam+
+          Q1.x = fma(-nb.y, lq, Q1.x); Q1.y = fma(nb.x, lq, Q1.y);  // -i aB lam-
+          U1.x = fma(ne.y, lq, U1.x); U1.y = fma(-ne.x, lq, U1.y);  // +i aE lam-
+        } else {
+          T1.x = fma(t.x, lam, T1.x); T1.y = fma(t.y, lam, T1.y);
+          Q1.x = fma(ne.x, lp, Q1.x); Q1.y = fma(ne.y, lp, Q1.y);
+          U1.x = fma(nb.x, lp, U1.x); U1.y = fma(nb.y, lp, U1.y);
+          Q0.x = fma(-nb.y, lq, Q0.x); Q0.y = fma(nb.x, lq, Q0.y);
+          U0.x = fma(ne.y, lq, U0.x); U0.y = fma(-ne.x, lq, U0.y);
+        }
+      }
+      if (l < lmax) rec_advance(s, sc[j], x, m, l, seed, pp, npairs);
+    }
+  }
+  if (!act) return;
+  const bool equator = (p == npairs - 1);
+  double2 *o0 = rc + rc_index2(b, 0, m, mmax, p, npairs);
+  double2 *o1 = rc + rc_index2(b, 1, m, mmax, p, npairs);
+  double2 *o2 = rc + rc_index2(b, 2, m, mmax, p, npairs);
+  o0[0] = cadd(T0, T1);
+  o1[0] = cadd(Q0, Q1);
+  o2[0] = cadd(U0, U1);
+  if (!equator) {
+    o0[1] = csub(T0, T1);
+    o1[1] = csub(Q0, Q1);
+    o2[1] = csub(U0, U1);
+  }
+}
+
+cudaError_t legendre_synthesis(dm_plan *p, const double2 *alm, cudaStream_t st) {
+  dim3 grid((p->npairs + SYN_THREADS - 1) / SYN_THREADS, p->mmax + 1, p->batch);
+  k_leg_syn64<<<grid, SYN_THREADS, 0, st>>>(p->pairs, p->rec, p->seed, p->seed_exp, alm, p->rc, p->lmax, p->mmax,
+                                           p->npairs, p->nalm, p->state_active ? p->state : nullptr);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- analysis
+// Block = ANA_P ring pairs x one m.  For each chunk of ANA_L multipoles:
+//  phase A: thread = pair, runs the recurrence, writes lambda, lam+, lam- to smem;
+//  phase B: thread = (l, half of the pairs), contracts over pairs in FP64.
+// Partial sums per pair chunk go to apart[b][chunk][f][alm]; k_ana_reduce
+// sums the chunks in a fixed order (deterministic).
+constexpr int ANA_P = 64;
+constexpr int ANA_L = 16;
+constexpr int ANA_PARTS = ANA_P / ANA_L;
+
+__global__ void __launch_bounds__(ANA_P) k_leg_ana64(const PairDev *__restrict__ pairs,
+                                                     const RecCoef *__restrict__ rec,
+                                                     const double *__restrict__ seed,
+                                                     const int *__restrict__ seed_exp,
+                                                     const double2 *__restrict__ rc, double2 *__restrict__ apart,
+                                                     int lmax, int mmax, int npairs, int64_t nalm, int nchunk,
+                                                     const SolveState *__restrict__ state) {
+  __shared__ double P0[ANA_P][ANA_L + 1], Pp[ANA_P][ANA_L + 1], Pq[ANA_P][ANA_L + 1];
+  // per pair: GT even, GT odd, GQ even, GQ odd, GU even, GU odd (complex)
+  __shared__ double2 G[ANA_P][6];
+  __shared__ double red[ANA_PARTS][ANA_L][6];
+  __shared__ RecCoef sc[ANA_L];
+  const int m = blockIdx.y, b = blockIdx.z, chunk = blockIdx.x;
+  if (state != nullptr && state[b].done) return;
+  const int t = threadIdx.x;
+  const int p = chunk * ANA_P + t;
+  const bool act = p < npairs;
+  const int pp = act ? p : npairs - 1;
+  const double x = pairs[pp].x;
+  {
+    double2 gn[3], gs[3];
+    for (int f = 0; f < 3; ++f) {
+      const double2 *g = rc + rc_index2(b, f, m, mmax, pp, npairs);
+      gn[f] = act ? g[0] : make_double2(0, 0);
+      gs[f] = (act && p != npairs - 1) ? g[1] : make_double2(0, 0);  // equator: no mirror ring
+    }
+    for (int f = 0; f < 3; ++f) {
+      G[t][2 * f] = cadd(gn[f], gs[f]);
+      G[t][2 * f + 1] = csub(gn[f], gs[f]);
+    }
+  }
+  Rec s;
+  rec_init(s, seed, seed_exp, m, pp, npairs);
+  const int64_t base = alm_base(lmax, m);
+  const int lj = t % ANA_L, part = t / ANA_L;
+  for (int lc = m; lc <= lmax; lc += ANA_L) {
+    const int cnt = min(ANA_L, lmax + 1 - lc);
+    __syncthreads();
+    if (t < cnt) sc[t] = rec[base + lc + t + 1];
+    __syncthreads();
+    // phase A
+    for (int j = 0; j < cnt; ++j) {
+      const int l = lc + j;
+      const bool live = (s.S == 0) && act;
+      P0[t][j] = live ? s.l0 : 0.0;
+      Pp[t][j] = live ? s.p0 : 0.0;
+      Pq[t][j] = live ? s.q0 : 0.0;
+      if (l < lmax) rec_advance(s, sc[j], x, m, l, seed, pp, npairs);
+    }
+    __syncthreads();
+    // phase B: thread (lj, part) sums pairs [part*ANA_L, part*ANA_L + ANA_L)
+    double aTr = 0, aTi = 0, aEr = 0, aEi = 0, aBr = 0, aBi = 0;
+    if (lj < cnt) {
+      const int l = lc + lj;
+      const int par = (l - m) & 1, opp = par ^ 1;
+      for (int q = part * ANA_L; q < (part + 1) * ANA_L; ++q) {
+        const double lam = P0[q][lj], lp = Pp[q][lj], lq = Pq[q][lj];
+        const double2 gt = G[q][par], gqp = G[q][2 + par], gup = G[q][4 + par];
+        const double2 gqo = G[q][2 + opp], guo = G[q][4 + opp];
+        aTr = fma(lam, gt.x, aTr);
+        aTi = fma(lam, gt.y, aTi);
+        // aE = -(lam+ GQ_par + i lam- GU_opp)
+        aEr = fma(-lp, gqp.x, fma(lq, guo.y, aEr));
+        aEi = fma(-lp, gqp.y, fma(-lq, guo.x, aEi));
+        // aB = -(lam+ GU_par - i lam- GQ_opp)
+        aBr = fma(-lp, gup.x, fma(-lq, gqo.y, aBr));
+        aBi = fma(-lp, gup.y, fma(lq, gqo.x, aBi));
+      }
+    }
+    red[part][lj][0] = aTr; red[part][lj][1] = aTi; red[part][lj][2] = aEr;
+    red[part][lj][3] = aEi; red[part][lj][4] = aBr; red[part][lj][5] = aBi;
+    __syncthreads();
+    if (part == 0 && lj < cnt) {
+      const int l = lc + lj;
+      double v[6];
+      for (int k = 0; k < 6; ++k) {
+        double a = red[0][lj][k];
+        for (int q = 1; q < ANA_PARTS; ++q) a += red[q][lj][k];
+        v[k] = a;
+      }
+      double2 *o = apart + ((int64_t)b * nchunk + chunk) * 3 * nalm + base + l;
+      o[0] = make_double2(v[0], v[1]);
+      o[nalm] = make_double2(v[2], v[3]);
+      o[2 * nalm] = make_double2(v[4], v[5]);
+    }
+  }
+}
+
+// Sum the pair chunks, scale by Omega; epilogue:
+//  ANA_PLAIN   : out = Omega sum
+//  ANA_DM_STEP : out = F_level (out + Omega sum)   (a <- F [a + A (t - s)])
+// grid: (l blocks, batch, m)
+__global__ void k_ana_reduce(const double2 *__restrict__ apart, double2 *out, int lmax, int64_t nalm, int nchunk,
+                             double omega, int epilogue, const double *__restrict__ filt,
+                             const SolveState *__restrict__ state) {
+  const int b = blockIdx.y, m = blockIdx.z;
+  if (state != nullptr && state[b].done) return;
+  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
+  if (l > lmax) return;
+  const int64_t i = alm_base(lmax, m) + l;
+  double2 acc[3];
+  for (int f = 0; f < 3; ++f) {
+    double2 a = make_double2(0, 0);
+    for (int c = 0; c < nchunk; ++c) a = cadd(a, apart[(((int64_t)b * nchunk + c) * 3 + f) * nalm + i]);
+    acc[f] = make_double2(omega * a.x, omega * a.y);
+  }
+  double2 *o = out + (int64_t)b * 3 * nalm + i;
+  if (epilogue == ANA_PLAIN) {
+    o[0] = acc[0];
+    o[nalm] = acc[1];
+    o[2 * nalm] = acc[2];
+    return;
+  }
+  const double *c = filt + ((int64_t)state[b].level * (lmax + 1) + l) * 4;
+  double2 t = cadd(o[0], acc[0]), e = cadd(o[nalm], acc[1]), bb = cadd(o[2 * nalm], acc[2]);
+  o[0] = make_double2(c[0] * t.x + c[1] * e.x, c[0] * t.y + c[1] * e.y);
+  o[nalm] = make_double2(c[1] * t.x + c[2] * e.x, c[1] * t.y + c[2] * e.y);
+  o[2 * nalm] = make_double2(c[3] * bb.x, c[3] * bb.y);
+}
+
+cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st) {
+  dim3 grid(p->nchunk, p->mmax + 1, p->batch);
+  const SolveState *stp = p->state_active ? p->state : nullptr;
+  k_leg_ana64<<<grid, ANA_P, 0, st>>>(p->pairs, p->rec, p->seed, p->seed_exp, p->rc, p->apart, p->lmax, p->mmax,
+                                      p->npairs, p->nalm, p->nchunk, stp);
+  double omega = 4.0 * M_PI / (double)p->npix;
+  dim3 g2((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
+  k_ana_reduce<<<g2, 128, 0, st>>>(p->apart, out, p->lmax, p->nalm, p->nchunk, omega, epilogue, p->filt,
+                                   epilogue == ANA_DM_STEP ? p->state : stp);
+  return cudaGetLastError();
+}
+
+// standalone filter (for testing the a3 step): out = F in, coefficients given
+__global__ void k_apply_filter(const double *__restrict__ coef, const double2 *in, double2 *out, int lmax,
+                               int64_t nalm) {
+  const int b = blockIdx.y;
+  const int m = blockIdx.z;
+  const int64_t base = alm_base(lmax, m);
+  for (int l = m + blockIdx.x * blockDim.x + threadIdx.x; l <= lmax; l += gridDim.x * blockDim.x) {
+    const double *c = coef + 4 * l;
+    const double2 *ip = in + (int64_t)b * 3 * nalm + base + l;
+    double2 *op = out + (int64_t)b * 3 * nalm + base + l;
+    double2 t = ip[0], e = ip[nalm], bb = ip[2 * nalm];
+    op[0] = make_double2(c[0] * t.x + c[1] * e.x, c[0] * t.y + c[1] * e.y);
+    op[nalm] = make_double2(c[1] * t.x + c[2] * e.x, c[1] * t.y + c[2] * e.y);
+    op[2 * nalm] = make_double2(c[3] * bb.x, c[3] * bb.y);
+  }
+}
+
+cudaError_t apply_filter_level(dm_plan *p, const double *coef, const double2 *in, double2 *out, cudaStream_t st) {
+  k_apply_filter<<<dim3(1, p->batch, p->mmax + 1), 128, 0, st>>>(coef, in, out, p->lmax, p->nalm);
+  return cudaGetLastError();
+}
+
+}  // namespace dmwf

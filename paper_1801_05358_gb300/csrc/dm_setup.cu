@@ -1,0 +1,396 @@
+// dm_setup.cu -- plan tables built once on the device: ring-pair latitudes,
+// FFT phase/chirp/twiddle tables, Wigner-d recurrence coefficients and seeds,
+// the per-level TEB filters (Eq. 8, Algorithm 1) and the noise weights
+// w = alpha / N (Section 2, Appendix B).
+#include <math.h>
+
+#include "dm_fft.cuh"
+#include "dm_internal.h"
+
+namespace dmwf {
+
+// ---------------------------------------------------------------- geometry
+// Pair p joins northern ring i = p + 1 (1 <= i <= 2 nside) with its mirror.
+__global__ void k_pairs(PairDev *pairs, int nside, int npairs) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  int i = p + 1;
+  double ns = nside;
+  PairDev q;
+  if (i < nside) {
+    q.omz = ((double)i * (double)i) / (3.0 * ns * ns);
+    q.opz = 2.0 - q.omz;
+    q.x = 1.0 - q.omz;
+  } else {
+    q.x = 4.0 / 3.0 - 2.0 * (double)i / (3.0 * ns);
+    q.omz = 1.0 - q.x;
+    q.opz = 1.0 + q.x;
+  }
+  pairs[p] = q;
+}
+
+// e^{-i pi q / n} for n = 4i, q < 2n; table of ring length n starts at 4 i (i - 1).
+__global__ void k_phase(double2 *ph, int nside) {
+  int i = blockIdx.y + 1;  // ring "radius" 1..nside
+  int n = 4 * i;
+  int64_t off = 4LL * i * (i - 1);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 2 * n; q += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(-(double)q / (double)n, &s, &c);
+    ph[off + q] = make_double2(c, s);
+  }
+}
+
+__global__ void k_twiddle(double2 *tw, int Mtab) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Mtab / 2) return;
+  double s, c;
+  sincospi(-2.0 * (double)k / (double)Mtab, &s, &c);
+  tw[k] = make_double2(c, s);
+}
+
+// Bluestein kernel spectrum for one ring length: FFT_M of b_j = e^{+i pi j^2/h}
+// placed at j and M - j (|j| < h), zero elsewhere.
+__global__ void k_bhat(const RingDev *rings, const int *ring_ids, const double2 *ph, double2 *bhat,
+                       const double2 *twid, int Mtab) {
+  extern __shared__ double2 sm_b[];
+  RingDev R = rings[ring_ids[blockIdx.x]];
+  const double2 *p = ph + R.ph_off;
+  int h = R.h, M = R.M;
+  int64_t n2 = 4LL * h;
+  for (int j = threadIdx.x; j < M; j += blockDim.x) sm_b[j] = make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int j = threadIdx.x; j < h; j += blockDim.x) {
+    double2 c = p[(2LL * j * j) % n2];
+    double2 b = make_double2(c.x, -c.y);
+    sm_b[j] = b;
+    if (j > 0) sm_b[M - j] = b;
+  }
+  __syncthreads();
+  fft_pow2(sm_b, M, twid, Mtab);
+  for (int k = threadIdx.x; k < M; k += blockDim.x) bhat[R.bh_off + k] = sm_b[k];
+}
+
+// --------------------------------------------------- recurrence coefficients
+// For target l and order m (entry idx(l, m)):
+//   spin 0 (l > m): al = sqrt((4l^2-1)/(l^2-m^2)),
+//                   bl = sqrt((2l+1)((l-1)^2-m^2) / ((2l-3)(l^2-m^2)))
+//   spin 2 (source L = l - 1 >= max(m, 2)), R(l) = sqrt((l^2-m^2)(l^2-4)):
+//     a  = sqrt((2L+3)/(2L+1)) (L+1)(2L+1) / R(L+1)
+//     ac = a * 2m / (L(L+1))
+//     b  = sqrt((2L+3)/(2L-1)) (L+1) R(L) / (L R(L+1))
+// (three-term Wigner-d recurrence with k = -+2 written for lam+- =
+//  (2lambda +- -2lambda)/2).
+__global__ void k_reccoef(RecCoef *rec, int lmax, int mmax) {
+  int m = blockIdx.y;
+  if (m > mmax) return;
+  int64_t base = (int64_t)m * (2 * lmax + 1 - m) / 2;
+  for (int l = m + blockIdx.x * blockDim.x + threadIdx.x; l <= lmax; l += gridDim.x * blockDim.x) {
+    RecCoef c = {0, 0, 0, 0, 0, 0};
+    double dl = l, dm = m;
+    if (l > m) {
+      double l2m2 = dl * dl - dm * dm;
+      c.al = sqrt((4.0 * dl * dl - 1.0) / l2m2);
+      c.bl = sqrt((2.0 * dl + 1.0) * ((dl - 1.0) * (dl - 1.0) - dm * dm) / ((2.0 * dl - 3.0) * l2m2));
+    }
+    int L = l - 1;
+    int l0 = m > 2 ? m : 2;
+    if (L >= l0) {
+      double dL = L;
+      double R1 = sqrt(((dL + 1) * (dL + 1) - dm * dm) * ((dL + 1) * (dL + 1) - 4.0));
+      double R0 = sqrt((dL * dL - dm * dm) * (dL * dL - 4.0));
+      c.a = sqrt((2.0 * dL + 3.0) / (2.0 * dL + 1.0)) * (dL + 1.0) * (2.0 * dL + 1.0) / R1;
+      c.ac = c.a * 2.0 * dm / (dL * (dL + 1.0));
+      c.b = (R0 == 0.0) ? 0.0 : sqrt((2.0 * dL + 3.0) / (2.0 * dL - 1.0)) * (dL + 1.0) * R0 / (dL * R1);
+    }
+    rec[base + l] = c;
+  }
+}
+
+// ------------------------------------------------------------------- seeds
+// Per pair and m: lambda_mm and lam+- at l0 = max(m, 2), carried as v * 2^-S.
+//   lambda_mm = prod_{j<=m} (-sqrt((2j+1)/(2j)) sin theta) / sqrt(4 pi)
+//   m >= 2: 2lambda_mm = lambda_mm r tan^2(theta/2), -2lambda_mm = lambda_mm r cot^2(theta/2),
+//           r = sqrt(m(m-1)/((m+1)(m+2)))
+//   m < 2 : closed forms of 2lambda_2m and -2lambda_2m.
+// S = 0 when the value is representable above 2^-600, else S >= 600.
+__global__ void k_seeds(const PairDev *pairs, double *seed, int *seed_exp, int mmax, int npairs) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  PairDev q = pairs[p];
+  double sth = sqrt(q.omz * q.opz);
+  double c2 = 0.5 * q.opz, s2 = 0.5 * q.omz;  // cos^2(theta/2), sin^2(theta/2)
+  double t2 = q.omz / q.opz;                   // tan^2(theta/2)
+  int e = 0;
+  double v = frexp(0.28209479177387814347403972578039 /* 1/sqrt(4pi) */, &e);
+  const double n2 = 0.63078313050504001190 /* sqrt(5/(4pi)) */;
+  double c = sqrt(c2), s = sqrt(s2);
+  for (int m = 0; m <= mmax; ++m) {
+    if (m > 0) {
+      int de;
+      v *= -sqrt((2.0 * m + 1.0) / (2.0 * m)) * sth;
+      v = frexp(v, &de);
+      e += de;
+    }
+    double l0, lp, lm;
+    int S;
+    if (m < 2) {
+      // lambda_mm plain (m = 0, 1 are O(1)); spin-2 seeds at l = 2
+      double pv, mv;
+      if (m == 0) {
+        pv = n2 * sqrt(6.0) * c2 * s2;          // 2lambda_20  (k = -2)
+        mv = n2 * sqrt(6.0) * c2 * s2;          // -2lambda_20 (k = +2)
+      } else {
+        pv = -n2 * 2.0 * c * s2 * s;            // 2lambda_21 = -N2 2 c s^3
+        mv = n2 * 2.0 * c2 * c * s;             // -2lambda_21 = N2 2 c^3 s
+      }
+      l0 = ldexp(v, e);
+      lp = 0.5 * (pv + mv);
+      lm = 0.5 * (pv - mv);
+      S = 0;
+    } else {
+      double r = sqrt((double)m * (m - 1) / ((double)(m + 1) * (m + 2)));
+      double pv = v * r * t2, mv = v * r / t2;
+      if (e >= -600) {
+        l0 = ldexp(v, e);
+        lp = ldexp(0.5 * (pv + mv), e);
+        lm = ldexp(0.5 * (pv - mv), e);
+        S = 0;
+      } else {
+        l0 = v;
+        lp = 0.5 * (pv + mv);
+        lm = 0.5 * (pv - mv);
+        S = -e;
+      }
+    }
+    int64_t o = (int64_t)m * npairs + p;
+    seed[3 * o + 0] = l0;
+    seed[3 * o + 1] = lp;
+    seed[3 * o + 2] = lm;
+    seed_exp[o] = S;
+  }
+}
+
+// ---------------------------------------------------------------- filters
+// Per l: eigen-decomposition of [[TT, TE], [TE, EE]] (closed form), BB apart;
+// f_e = max(S_e, mu) / (max(S_e, mu) + T_h); coef = (F_TT, F_TE, F_EE, F_BB).
+__device__ void filter_one_l(const double *cl, int lmax, int l, double mu, double th, double *out) {
+  double tt = cl[l], ee = cl[(lmax + 1) + l], bb = cl[2 * (lmax + 1) + l], te = cl[3 * (lmax + 1) + l];
+  double e1, e2, v1x, v1y;
+  if (te == 0.0) {
+    if (tt >= ee) { e1 = tt; e2 = ee; v1x = 1.0; v1y = 0.0; }
+    else { e1 = ee; e2 = tt; v1x = 0.0; v1y = 1.0; }
+  } else {
+    double hd = 0.5 * (tt - ee);
+    double disc = sqrt(hd * hd + te * te);
+    e1 = 0.5 * (tt + ee) + disc;
+    e2 = (tt * ee - te * te) / e1;
+    double ax = te, ay = e1 - tt, bx = e1 - ee, by = te;
+    double na = sqrt(ax * ax + ay * ay), nb = sqrt(bx * bx + by * by);
+    if (na >= nb) { v1x = ax / na; v1y = ay / na; }
+    else { v1x = bx / nb; v1y = by / nb; }
+  }
+  double v2x = -v1y, v2y = v1x;
+  e1 = fmax(e1, 0.0);
+  e2 = fmax(e2, 0.0);
+  double s1 = fmax(e1, mu), s2 = fmax(e2, mu), s3 = fmax(fmax(bb, 0.0), mu);
+  double f1 = s1 / (s1 + th), f2 = s2 / (s2 + th), f3 = s3 / (s3 + th);
+  out[0] = f1 * v1x * v1x + f2 * v2x * v2x;
+  out[1] = f1 * v1x * v1y + f2 * v2x * v2y;
+  out[2] = f1 * v1y * v1y + f2 * v2y * v2y;
+  out[3] = f3;
+}
+
+__global__ void k_filter(const double *cl, int lmax, double mu, double th, double *coef) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l > lmax) return;
+  filter_one_l(cl, lmax, l, mu, th, coef + 4 * l);
+}
+
+// ------------------------------------------------------------------- noise
+__global__ void k_min_n(const double *sigma, const uint8_t *mask, int64_t npix, double *partial) {
+  __shared__ double red[256];
+  double mn = INFINITY;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * npix;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = i % npix;
+    if (mask == nullptr || mask[p]) mn = fmin(mn, sigma[i] * sigma[i]);
+  }
+  red[threadIdx.x] = mn;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_min_final(double *partial, int n) {
+  __shared__ double red[256];
+  double mn = INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mn = fmin(mn, partial[i]);
+  red[threadIdx.x] = mn;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[0] = red[0];
+}
+
+__global__ void k_weights(const double *sigma, const uint8_t *mask, int64_t npix, const double *alpha_dev,
+                          double *w) {
+  double alpha = alpha_dev[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * npix;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = i % npix;
+    bool obs = (mask == nullptr) || mask[p];
+    w[i] = obs ? alpha / (sigma[i] * sigma[i]) : 0.0;
+  }
+}
+
+// ------------------------------------------------------------- launchers
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+static int next_pow2(int v) {
+  int r = 1;
+  while (r < v) r <<= 1;
+  return r;
+}
+
+cudaError_t build_tables(dm_plan *p) {
+  const int ns = p->nside;
+  // host-side ring metadata (integer geometry of the RING scheme)
+  p->rings_h.resize(p->nrings);
+  int Mmax = 1;
+  for (int r = 0; r < p->nrings; ++r) {
+    int i = r + 1;
+    RingDev R{};
+    int64_t n64 = ns;
+    if (i < ns) {
+      R.n = 4 * i;
+      R.start = 2LL * i * (i - 1);
+      R.shift = 1;
+      R.pair = i - 1;
+      R.side = 0;
+    } else if (i <= 3 * ns) {
+      R.n = 4 * ns;
+      R.start = 2LL * ns * (ns - 1) + (int64_t)(i - ns) * 4 * n64;
+      R.shift = ((i - ns + 1) % 2 == 1) ? 1 : 0;
+      if (i <= 2 * ns) {
+        R.pair = i - 1;
+        R.side = 0;
+      } else {
+        R.pair = 4 * ns - i - 1;
+        R.side = 1;
+      }
+    } else {
+      int ip = 4 * ns - i;
+      R.n = 4 * ip;
+      R.start = 12LL * n64 * n64 - 2LL * ip * (ip + 1);
+      R.shift = 1;
+      R.pair = ip - 1;
+      R.side = 1;
+    }
+    R.h = R.n / 2;
+    R.bluestein = is_pow2(R.h) ? 0 : 1;
+    R.M = R.bluestein ? next_pow2(2 * R.h - 1) : R.h;
+    int rad = R.n / 4;
+    R.ph_off = 4LL * rad * (rad - 1);
+    R.bh_off = -1;
+    Mmax = R.M > Mmax ? R.M : Mmax;
+    p->rings_h[r] = R;
+  }
+  p->fft_M_max = Mmax < 2 ? 2 : Mmax;
+  // Bluestein spectra: one per distinct ring radius (north and south share)
+  std::vector<int> bl_ring;  // representative ring per radius needing bluestein
+  std::vector<int64_t> bl_off_by_rad(ns + 1, -1);
+  int64_t bh_total = 0;
+  for (int r = 0; r < p->nrings; ++r) {
+    RingDev &R = p->rings_h[r];
+    if (!R.bluestein) continue;
+    int rad = R.n / 4;
+    if (bl_off_by_rad[rad] < 0) {
+      bl_off_by_rad[rad] = bh_total;
+      bh_total += R.M;
+      bl_ring.push_back(r);
+    }
+    R.bh_off = bl_off_by_rad[rad];
+  }
+  cudaError_t e;
+  size_t ph_n = 4ull * ns * (ns + 1);
+  if ((e = cudaMalloc(&p->rings, sizeof(RingDev) * p->nrings))) return e;
+  if ((e = cudaMalloc(&p->pairs, sizeof(PairDev) * p->npairs))) return e;
+  if ((e = cudaMalloc(&p->phase, sizeof(double2) * ph_n))) return e;
+  if ((e = cudaMalloc(&p->twid, sizeof(double2) * (p->fft_M_max / 2)))) return e;
+  if ((e = cudaMalloc(&p->bhat, sizeof(double2) * (bh_total > 0 ? bh_total : 1)))) return e;
+  if ((e = cudaMalloc(&p->rec, sizeof(RecCoef) * (p->nalm + 1)))) return e;
+  size_t nseed = (size_t)(p->mmax + 1) * p->npairs;
+  if ((e = cudaMalloc(&p->seed, sizeof(double) * 3 * nseed))) return e;
+  if ((e = cudaMalloc(&p->seed_exp, sizeof(int) * nseed))) return e;
+  p->bytes += sizeof(RingDev) * p->nrings + sizeof(PairDev) * p->npairs + sizeof(double2) * ph_n +
+              sizeof(double2) * (p->fft_M_max / 2 + bh_total) + sizeof(RecCoef) * (p->nalm + 1) +
+              (sizeof(double) * 3 + sizeof(int)) * nseed;
+  if ((e = cudaMemcpy(p->rings, p->rings_h.data(), sizeof(RingDev) * p->nrings, cudaMemcpyHostToDevice)))
+    return e;
+  cudaMemset(p->rec, 0, sizeof(RecCoef) * (p->nalm + 1));
+  k_pairs<<<(p->npairs + 127) / 128, 128>>>(p->pairs, ns, p->npairs);
+  k_phase<<<dim3(8, ns), 256>>>(p->phase, ns);
+  k_twiddle<<<(p->fft_M_max / 2 + 255) / 256, 256>>>(p->twid, p->fft_M_max);
+  if (!bl_ring.empty()) {
+    int *ids;
+    if ((e = cudaMalloc(&ids, sizeof(int) * bl_ring.size()))) return e;
+    cudaMemcpy(ids, bl_ring.data(), sizeof(int) * bl_ring.size(), cudaMemcpyHostToDevice);
+    size_t smem = sizeof(double2) * p->fft_M_max;
+    cudaFuncSetAttribute(k_bhat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_bhat<<<(unsigned)bl_ring.size(), 256, smem>>>(p->rings, ids, p->phase, p->bhat, p->twid, p->fft_M_max);
+    e = cudaDeviceSynchronize();
+    cudaFree(ids);
+    if (e) return e;
+  }
+  k_reccoef<<<dim3(4, p->mmax + 1), 256>>>(p->rec, p->lmax, p->mmax);
+  k_seeds<<<(p->npairs + 63) / 64, 64>>>(p->pairs, p->seed, p->seed_exp, p->mmax, p->npairs);
+  e = cudaGetLastError();
+  if (e) return e;
+  return cudaDeviceSynchronize();
+}
+
+cudaError_t build_filter_one(dm_plan *p, double lambda, double *coef, cudaStream_t st) {
+  double mu = (lambda - 1.0) * p->t_h;
+  k_filter<<<(p->lmax + 1 + 127) / 128, 128, 0, st>>>(p->cl, p->lmax, mu, p->t_h, coef);
+  return cudaGetLastError();
+}
+
+cudaError_t build_filters(dm_plan *p, cudaStream_t st) {
+  int nl = (int)p->lambdas.size();
+  if (p->filt == nullptr || p->filt_levels < nl) {
+    if (p->filt) cudaFree(p->filt);
+    cudaError_t e = cudaMalloc(&p->filt, sizeof(double) * 4 * (p->lmax + 1) * (size_t)(nl > 0 ? nl : 1));
+    if (e) return e;
+    p->filt_levels = nl;
+  }
+  for (int k = 0; k < nl; ++k) {
+    cudaError_t e = build_filter_one(p, p->lambdas[k], p->filt + (size_t)4 * (p->lmax + 1) * k, st);
+    if (e) return e;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t build_noise(dm_plan *p, cudaStream_t st) {
+  int nb = 256;
+  double *partial;
+  cudaError_t e = cudaMalloc(&partial, sizeof(double) * nb);
+  if (e) return e;
+  k_min_n<<<nb, 256, 0, st>>>(p->sigma, p->mask, p->npix, partial);
+  k_min_final<<<1, 256, 0, st>>>(partial, nb);
+  k_weights<<<1024, 256, 0, st>>>(p->sigma, p->mask, p->npix, partial, p->w);
+  double alpha = 0.0;
+  cudaMemcpyAsync(&alpha, partial, sizeof(double), cudaMemcpyDeviceToHost, st);
+  e = cudaStreamSynchronize(st);
+  cudaFree(partial);
+  if (e) return e;
+  p->alpha = alpha;
+  p->t_h = alpha * 4.0 * M_PI / (double)p->npix;
+  return cudaGetLastError();
+}
+
+}  // namespace dmwf

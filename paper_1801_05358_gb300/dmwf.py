@@ -1,0 +1,216 @@
+"""Thin Python binding of libdmwf (include/dmwf.h): argument marshalling only.
+
+Every step of the dual messenger path runs in the CUDA library; this module
+passes torch device pointers and CUDA streams through ctypes and converts the
+host-side arrays (spectra, noise, mask, schedule).  Importing it fails loudly
+when the library has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdmwf.so")
+
+DM_OK, DM_EINVAL, DM_ENOMEM, DM_ECUDA, DM_ENOTCONV, DM_ETIMEOUT, DM_EAGAIN, DM_EBUSY = range(8)
+DM_FP64, DM_MIXED_FP32 = 0, 1
+DM_MAX_LEVELS = 64
+
+EXPORTS = [
+    "dm_plan_create", "dm_plan_destroy", "dm_last_error", "dm_plan_info", "dm_set_precision", "dm_set_spectra",
+    "dm_set_noise_mask", "dm_set_schedule", "dm_set_forced_iters", "dm_wiener_filter", "dm_wiener_filter_host",
+    "dm_constrained_realization", "dm_draw_cr_inputs", "dm_alm2map", "dm_map2alm", "dm_ring_fft_forward",
+    "dm_ring_fft_inverse", "dm_legendre_synthesis", "dm_legendre_analysis", "dm_apply_filter", "dm_noise_info",
+]
+
+
+class DmSchedule(ctypes.Structure):
+    _fields_ = [("lambda0", ctypes.c_double), ("n_levels", ctypes.c_int), ("iters_per_level", ctypes.c_int),
+                ("eps0", ctypes.c_double), ("eps_final", ctypes.c_double), ("eta", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class DmStats(ctypes.Structure):
+    _fields_ = [("iters_total", ctypes.c_int), ("levels_done", ctypes.c_int),
+                ("iters_per_level", ctypes.c_int * DM_MAX_LEVELS), ("cauchy_final", ctypes.c_double)]
+
+
+class DmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"dmwf status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libdmwf.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} not built: run `python -m paper_1801_05358_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.dm_plan_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+        L.dm_plan_destroy.argtypes = [vp]
+        L.dm_plan_destroy.restype = None
+        L.dm_last_error.argtypes = [vp]
+        L.dm_last_error.restype = ctypes.c_char_p
+        L.dm_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]
+        L.dm_set_precision.argtypes = [vp, ctypes.c_int]
+        L.dm_set_spectra.argtypes = [vp, vp]
+        L.dm_set_noise_mask.argtypes = [vp, vp, vp]
+        L.dm_set_schedule.argtypes = [vp, ctypes.POINTER(DmSchedule)]
+        L.dm_set_forced_iters.argtypes = [vp, vp]
+        L.dm_wiener_filter.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.dm_wiener_filter_host.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.dm_constrained_realization.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.dm_draw_cr_inputs.argtypes = [vp, vp, vp, vp, vp, vp]
+        for name in ["dm_alm2map", "dm_map2alm", "dm_ring_fft_forward", "dm_ring_fft_inverse",
+                     "dm_legendre_synthesis", "dm_legendre_analysis"]:
+            getattr(L, name).argtypes = [vp, vp, vp, vp]
+        L.dm_apply_filter.argtypes = [vp, ctypes.c_double, vp, vp, vp]
+        L.dm_noise_info.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """One dm_plan: geometry (nside, lmax), batch of right-hand sides."""
+
+    def __init__(self, nside: int, lmax: int, batch: int = 1):
+        h = ctypes.c_void_p()
+        st = lib().dm_plan_create(nside, lmax, batch, ctypes.byref(h))
+        if st != DM_OK:
+            raise DmError(st, "dm_plan_create failed (nside, lmax, batch out of range or no memory)")
+        self.h = h
+        self.nside, self.lmax, self.batch = nside, lmax, batch
+        self.npix = 12 * nside * nside
+        self.nalm = (lmax + 1) * (lmax + 2) // 2
+        self.nrings = 4 * nside - 1
+        self._keep = []
+
+    def close(self):
+        if self.h:
+            lib().dm_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=()):
+        if st != DM_OK and st not in allow:
+            raise DmError(st, lib().dm_last_error(self.h).decode())
+        return st
+
+    # ---- set-up ----
+    def set_precision(self, prec):
+        self._check(lib().dm_set_precision(self.h, prec))
+
+    def set_spectra(self, cl):
+        c = np.ascontiguousarray(cl, dtype=np.float64)
+        self._check(lib().dm_set_spectra(self.h, _np_ptr(c)))
+
+    def set_noise_mask(self, sigma, mask=None):
+        s = np.ascontiguousarray(sigma, dtype=np.float64)
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        self._check(lib().dm_set_noise_mask(self.h, _np_ptr(s), _np_ptr(m)))
+
+    def set_schedule(self, lambda0=1000.0, n_levels=10, iters_per_level=10, eps0=1e-4, eps_final=1e-6, eta=0.0,
+                     max_iter=100000, check_every=8):
+        sc = DmSchedule(lambda0, n_levels, iters_per_level, eps0, eps_final, eta, max_iter, check_every)
+        self._check(lib().dm_set_schedule(self.h, ctypes.byref(sc)))
+
+    def set_forced_iters(self, iters):
+        if iters is None:
+            self._check(lib().dm_set_forced_iters(self.h, None))
+            return
+        a = np.ascontiguousarray(iters, dtype=np.int32)
+        self._check(lib().dm_set_forced_iters(self.h, _np_ptr(a)))
+
+    def noise_info(self):
+        a, t = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().dm_noise_info(self.h, ctypes.byref(a), ctypes.byref(t)))
+        return a.value, t.value
+
+    def info(self):
+        a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
+        self._check(lib().dm_plan_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+        return dict(npix=a.value, nalm=b.value, nrings=c.value, workspace_bytes=d.value)
+
+    # ---- hot path (torch CUDA tensors, float64 / complex128) ----
+    @staticmethod
+    def _stats_out(stats_arr):
+        return [dict(iters_total=s.iters_total, levels_done=s.levels_done,
+                     iters_per_level=list(s.iters_per_level), cauchy_final=s.cauchy_final) for s in stats_arr]
+
+    def wiener_filter(self, d, s_out, alm_out=None, stream=None):
+        stats = (DmStats * self.batch)()
+        st = lib().dm_wiener_filter(self.h, _ptr(d), _ptr(s_out), _ptr(alm_out), stats, _stream(stream))
+        self._check(st, allow=(DM_ENOTCONV,))
+        return st, self._stats_out(stats)
+
+    def wiener_filter_host(self, d_host, s_host, alm_host=None, stream=None):
+        stats = (DmStats * self.batch)()
+        st = lib().dm_wiener_filter_host(self.h, _ptr(d_host), _ptr(s_host), _ptr(alm_host), stats,
+                                         _stream(stream))
+        self._check(st, allow=(DM_ENOTCONV,))
+        return st, self._stats_out(stats)
+
+    def constrained_realization(self, d, seeds, s_out, alm_out=None, stream=None):
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        stats = (DmStats * self.batch)()
+        st = lib().dm_constrained_realization(self.h, _ptr(d), _np_ptr(sd), _ptr(s_out), _ptr(alm_out), stats,
+                                              _stream(stream))
+        self._check(st, allow=(DM_ENOTCONV,))
+        return st, self._stats_out(stats)
+
+    def draw_cr_inputs(self, seeds, ahat=None, shat=None, dhat=None, stream=None):
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        self._check(lib().dm_draw_cr_inputs(self.h, _np_ptr(sd), _ptr(ahat), _ptr(shat), _ptr(dhat),
+                                            _stream(stream)))
+
+    def alm2map(self, alm, out, stream=None):
+        self._check(lib().dm_alm2map(self.h, _ptr(alm), _ptr(out), _stream(stream)))
+
+    def map2alm(self, maps, out, stream=None):
+        self._check(lib().dm_map2alm(self.h, _ptr(maps), _ptr(out), _stream(stream)))
+
+    def ring_fft_forward(self, maps, rc, stream=None):
+        self._check(lib().dm_ring_fft_forward(self.h, _ptr(maps), _ptr(rc), _stream(stream)))
+
+    def ring_fft_inverse(self, rc, maps, stream=None):
+        self._check(lib().dm_ring_fft_inverse(self.h, _ptr(rc), _ptr(maps), _stream(stream)))
+
+    def legendre_synthesis(self, alm, rc, stream=None):
+        self._check(lib().dm_legendre_synthesis(self.h, _ptr(alm), _ptr(rc), _stream(stream)))
+
+    def legendre_analysis(self, rc, alm, stream=None):
+        self._check(lib().dm_legendre_analysis(self.h, _ptr(rc), _ptr(alm), _stream(stream)))
+
+    def apply_filter(self, lam, alm_in, alm_out, stream=None):
+        self._check(lib().dm_apply_filter(self.h, ctypes.c_double(lam), _ptr(alm_in), _ptr(alm_out),
+                                          _stream(stream)))
