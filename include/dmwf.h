@@ -193,6 +193,30 @@ dm_status dm_apply_filter(dm_plan *plan, double lambda, const double *alm_in, do
 /* alpha and T_h of the current noise model (host outputs). */
 dm_status dm_noise_info(const dm_plan *plan, double *alpha, double *t_h);
 
+/* --- measurement --------------------------------------------------------- */
+
+/* Per-stage device time of the dual messenger iterations, measured with CUDA
+ * events recorded on the caller's stream around every stage launch, and the
+ * number of kernels this library launched.  Enabling resets the counters. */
+typedef struct {
+  int64_t launches;        /* kernels launched by this plan since enabling */
+  int64_t iterations;      /* dual messenger iterations timed */
+  double ms_analysis;      /* Legendre analysis (a2) */
+  double ms_reduce;        /* chunk reduction + harmonic step + filter (a2/a3) */
+  double ms_synthesis;     /* Legendre synthesis (a4) */
+  double ms_ring;          /* inverse FFT, update, norms, forward FFT (a5, a6, a7, a1) */
+  double ms_control;       /* Cauchy ratio and level control (a7, a8) */
+} dm_profile;
+
+dm_status dm_profile_enable(dm_plan *plan, int on);
+dm_status dm_profile_read(const dm_plan *plan, dm_profile *out);
+
+/* ALU roofline denominators of the current device, measured with independent
+ * FMA chains on every SM (about 0.2 s): FP64 and FP32 TFLOP/s (FMA = 2 flops).
+ * The paper has no counterpart; it is the peak the FP64 Legendre stage is
+ * compared against. */
+dm_status dm_measure_alu_peaks(double *fp64_tflops, double *fp32_tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,8 @@ cudaError_t dalloc(dm_plan *p, T **ptr, size_t count) {
 }
 
 void free_all(dm_plan *p) {
+  for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+  p->ev.clear();
   void *ptrs[] = {p->rings, p->pairs, p->phase, p->bhat, p->twid, p->rec, p->seed, p->seed_exp, p->cl,
                   p->filt, p->w, p->mask, p->sigma, p->rc, p->a, p->apart, p->wd, p->norms, p->state,
                   p->lev, p->tmpmap, p->tmpmap2, p->tmpalm, p->seeds_dev, p->coef_tmp};
@@ -125,20 +127,45 @@ dm_status run_dm(dm_plan *p, const double *d, double *s_out, cudaStream_t st) {
     cap = tot + 4;
   }
   const int every = std::max(1, S.check_every);
+  if (p->prof_on && (int)p->ev.size() < 6 * every) {
+    int have = (int)p->ev.size();
+    p->ev.resize(6 * every);
+    for (int i = have; i < 6 * every; ++i) cudaEventCreate(&p->ev[i]);
+  }
+  p->launches += 3;
   dm_status rs = DM_OK;
   for (;;) {
     for (int k = 0; k < every; ++k) {
       cudaError_t e;
-      if ((e = legendre_analysis(p, ANA_DM_STEP, p->a, st))) { rs = cuda_fail(p, e, "analysis"); break; }
+      cudaEvent_t *E = p->prof_on ? &p->ev[6 * k] : nullptr;
+      if (E) cudaEventRecord(E[0], st);
+      if ((e = legendre_analysis(p, ANA_DM_STEP, p->a, st, E ? E[1] : nullptr))) { rs = cuda_fail(p, e, "analysis"); break; }
+      if (E) cudaEventRecord(E[2], st);
       if ((e = legendre_synthesis(p, p->a, st))) { rs = cuda_fail(p, e, "synthesis"); break; }
+      if (E) cudaEventRecord(E[3], st);
       if ((e = ring_stage(p, RING_ITER, nullptr, s_out, st))) { rs = cuda_fail(p, e, "ring"); break; }
+      if (E) cudaEventRecord(E[4], st);
       if ((e = control_step(p, st))) { rs = cuda_fail(p, e, "control"); break; }
+      if (E) cudaEventRecord(E[5], st);
+      p->launches += 5;
     }
     if (rs != DM_OK) break;
     launched += every;
     cudaError_t e = cudaMemcpyAsync(hs.data(), p->state, sizeof(SolveState) * p->batch, cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaStreamSynchronize(st);
     if (e) { rs = cuda_fail(p, e, "poll state"); break; }
+    if (p->prof_on) {
+      for (int k = 0; k < every; ++k) {
+        float t[5];
+        for (int j = 0; j < 5; ++j) cudaEventElapsedTime(&t[j], p->ev[6 * k + j], p->ev[6 * k + j + 1]);
+        p->prof.ms_analysis += t[0];
+        p->prof.ms_reduce += t[1];
+        p->prof.ms_synthesis += t[2];
+        p->prof.ms_ring += t[3];
+        p->prof.ms_control += t[4];
+        p->prof.iterations += 1;
+      }
+    }
     bool all = true;
     for (auto &s : hs) all = all && s.done;
     if (all) break;
@@ -455,6 +482,21 @@ dm_status dm_apply_filter(dm_plan *p, double lambda, const double *alm_in, doubl
   cudaStream_t st = (cudaStream_t)stream;
   DM_CU(build_filter_one(p, lambda, p->coef_tmp, st), "filter");
   DM_CU(apply_filter_level(p, p->coef_tmp, (const double2 *)alm_in, (double2 *)alm_out, st), "apply filter");
+  return DM_OK;
+}
+
+dm_status dm_profile_enable(dm_plan *p, int on) {
+  if (!p) return DM_EINVAL;
+  p->prof_on = on != 0;
+  memset(&p->prof, 0, sizeof(p->prof));
+  p->launches = 0;
+  return DM_OK;
+}
+
+dm_status dm_profile_read(const dm_plan *p, dm_profile *out) {
+  if (!p || !out) return DM_EINVAL;
+  *out = p->prof;
+  out->launches = p->launches;
   return DM_OK;
 }
 

@@ -206,4 +206,52 @@ cudaError_t draw_noise_add(dm_plan *p, const uint64_t *seeds_dev, const double *
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------- peak probe
+template <typename T>
+__global__ void k_fma_chain(T *out, int iters, T a, T b) {
+  T x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+      x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+template <typename T>
+static double time_fma(int blocks, int iters) {
+  T *out = nullptr;
+  if (cudaMalloc(&out, sizeof(T) * blocks * 256)) return -1.0;
+  k_fma_chain<T><<<blocks, 256>>>(out, 4, (T)0.999, (T)0.001);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int r = 0; r < 3; ++r) {
+    cudaEventRecord(e0);
+    k_fma_chain<T><<<blocks, 256>>>(out, iters, (T)0.999, (T)0.001);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = ms < best ? ms : best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  double flops = 2.0 * 64.0 * (double)blocks * 256.0 * (double)iters;
+  return flops / (best * 1e-3) / 1e12;
+}
+
 }  // namespace dmwf
+
+extern "C" dm_status dm_measure_alu_peaks(double *fp64_tflops, double *fp32_tflops) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (fp64_tflops) *fp64_tflops = dmwf::time_fma<double>(sms * 4, 1024);
+  if (fp32_tflops) *fp32_tflops = dmwf::time_fma<float>(sms * 8, 8192);
+  return cudaGetLastError() == cudaSuccess ? DM_OK : DM_ECUDA;
+}

@@ -115,6 +115,11 @@ struct dm_plan {
   double *coef_tmp = nullptr;   // [lmax+1][4] filter of dm_apply_filter
   bool state_active = false;    // kernels consult state[] (skip finished RHS)
   int64_t bytes = 0;
+  // measurement
+  bool prof_on = false;
+  dm_profile prof{};
+  std::vector<cudaEvent_t> ev;  // 6 per iteration of one poll window
+  int64_t launches = 0;
 };
 
 namespace dmwf {
@@ -135,7 +140,7 @@ cudaError_t rc_from_public(dm_plan *p, const double2 *pub, cudaStream_t st);
 cudaError_t legendre_synthesis(dm_plan *p, const double2 *alm, cudaStream_t st);
 // analysis into apart, then reduce: out = (accumulate ? a_prev : 0) + Omega sum, then filter
 enum AnaEpilogue { ANA_PLAIN = 0, ANA_DM_STEP = 1 };
-cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st);
+cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid = nullptr);
 cudaError_t apply_filter_level(dm_plan *p, const double *coef, const double2 *in, double2 *out, cudaStream_t st);
 cudaError_t build_filter_one(dm_plan *p, double lambda, double *coef, cudaStream_t st);
 

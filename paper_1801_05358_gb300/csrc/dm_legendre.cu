@@ -312,11 +312,12 @@ __global__ void k_ana_reduce(const double2 *__restrict__ apart, double2 *out, in
   o[2 * nalm] = make_double2(c[3] * bb.x, c[3] * bb.y);
 }
 
-cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st) {
+cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid) {
   dim3 grid(p->nchunk, p->mmax + 1, p->batch);
   const SolveState *stp = p->state_active ? p->state : nullptr;
   k_leg_ana64<<<grid, ANA_P, 0, st>>>(p->pairs, p->rec, p->seed, p->seed_exp, p->rc, p->apart, p->lmax, p->mmax,
                                       p->npairs, p->nalm, p->nchunk, stp);
+  if (mid) cudaEventRecord(mid, st);
   double omega = 4.0 * M_PI / (double)p->npix;
   dim3 g2((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
   k_ana_reduce<<<g2, 128, 0, st>>>(p->apart, out, p->lmax, p->nalm, p->nchunk, omega, epilogue, p->filt,

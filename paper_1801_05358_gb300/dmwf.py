@@ -24,6 +24,7 @@ EXPORTS = [
     "dm_set_noise_mask", "dm_set_schedule", "dm_set_forced_iters", "dm_wiener_filter", "dm_wiener_filter_host",
     "dm_constrained_realization", "dm_draw_cr_inputs", "dm_alm2map", "dm_map2alm", "dm_ring_fft_forward",
     "dm_ring_fft_inverse", "dm_legendre_synthesis", "dm_legendre_analysis", "dm_apply_filter", "dm_noise_info",
+    "dm_profile_enable", "dm_profile_read", "dm_measure_alu_peaks",
 ]
 
 
@@ -36,6 +37,12 @@ class DmSchedule(ctypes.Structure):
 class DmStats(ctypes.Structure):
     _fields_ = [("iters_total", ctypes.c_int), ("levels_done", ctypes.c_int),
                 ("iters_per_level", ctypes.c_int * DM_MAX_LEVELS), ("cauchy_final", ctypes.c_double)]
+
+
+class DmProfile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("iterations", ctypes.c_int64), ("ms_analysis", ctypes.c_double),
+                ("ms_reduce", ctypes.c_double), ("ms_synthesis", ctypes.c_double), ("ms_ring", ctypes.c_double),
+                ("ms_control", ctypes.c_double)]
 
 
 class DmError(RuntimeError):
@@ -76,6 +83,9 @@ def lib():
             getattr(L, name).argtypes = [vp, vp, vp, vp]
         L.dm_apply_filter.argtypes = [vp, ctypes.c_double, vp, vp, vp]
         L.dm_noise_info.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.dm_profile_enable.argtypes = [vp, ctypes.c_int]
+        L.dm_profile_read.argtypes = [vp, ctypes.POINTER(DmProfile)]
+        L.dm_measure_alu_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
 
@@ -93,6 +103,15 @@ def _stream(stream):
         import torch
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def measure_alu_peaks():
+    """(fp64, fp32) TFLOP/s of the current device from FMA chains."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = lib().dm_measure_alu_peaks(ctypes.byref(a), ctypes.byref(b))
+    if st != DM_OK:
+        raise DmError(st, "peak probe failed")
+    return a.value, b.value
 
 
 class Plan:
@@ -155,6 +174,14 @@ class Plan:
         a, t = ctypes.c_double(), ctypes.c_double()
         self._check(lib().dm_noise_info(self.h, ctypes.byref(a), ctypes.byref(t)))
         return a.value, t.value
+
+    def profile_enable(self, on=True):
+        self._check(lib().dm_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        pr = DmProfile()
+        self._check(lib().dm_profile_read(self.h, ctypes.byref(pr)))
+        return {k: getattr(pr, k) for k, _ in DmProfile._fields_}
 
     def info(self):
         a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
