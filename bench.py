@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--nside", type=int, default=512)
     ap.add_argument("--lmax", type=int, default=None)
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="iterations of the plain FP64 GPU path timed beside (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -203,6 +206,7 @@ def main():
     plan = dmwf.Plan(nside, lmax, B)
     plan.set_spectra(wl.cl)
     plan.set_noise_mask(wl.sigma, wl.mask)
+    prec = dmwf.DM_MIXED_FP32 if args.precision == "mixed" else dmwf.DM_FP64
     nalm = plan.nalm
     d = torch.zeros((B, 3, npix), dtype=torch.float64, device=dev)
     alm_in = torch.zeros((B, 3, nalm, 2), dtype=torch.float64, device=dev)
@@ -219,6 +223,24 @@ def main():
     del s_tmp, alm_in
     s_out = torch.zeros_like(d)
     torch.cuda.synchronize()
+
+    # ---- the plain FP64 GPU solve, timed beside (same batch, same API) ----
+    fp64_line = None
+    if args.fp64_steps > 0 and prec != dmwf.DM_FP64:
+        nf = args.fp64_steps
+        plan.set_schedule(lambda0=1000.0, n_levels=10, iters_per_level=1, check_every=nf)
+        plan.set_forced_iters(iters_split(nf))
+        plan.wiener_filter(d, s_out)   # warm
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        f0.record()
+        plan.wiener_filter(d, s_out)
+        f1.record()
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1)
+        fp64_line = {"value": B * nf / (fms * 1e-3), "unit": "DM iterations/s", "steps": nf,
+                     "ms_per_step": fms / nf}
+    plan.set_precision(prec)
 
     # ---- warm-up: W iterations through the public API ----
     plan.set_schedule(lambda0=1000.0, n_levels=10, iters_per_level=1, check_every=max(1, Wu))
@@ -253,25 +275,43 @@ def main():
     assert iters == K, f"timed {iters} iterations, expected {K}"
     value = B * K * ws / (ms_max * 1e-3)
 
-    # ---- dominant kernel roofline (FP64 Legendre stage) ----
+    # ---- dominant kernel roofline (Legendre stage) ----
     npairs = 2 * nside
     triples = nalm * npairs
-    flops_launch = FLOPS_PER_TRIPLE * triples * B
     ms_syn = prof["ms_synthesis"] / max(1, prof["iterations"])
     ms_ana = prof["ms_analysis"] / max(1, prof["iterations"])
+    suffix = "64" if prec == dmwf.DM_FP64 else "32"
     if ms_syn >= ms_ana:
-        kname, kms = "k_leg_syn64", ms_syn
+        kname, kms = "k_leg_syn" + suffix, ms_syn
     else:
-        kname, kms = "k_leg_ana64", ms_ana
-    achieved = flops_launch / (kms * 1e-3) / 1e12
+        kname, kms = "k_leg_ana" + suffix, ms_ana
     workload_name = f"nside{nside}_lmax{lmax}_B{B}"
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": traffic_for(kname, workload_name),
-                "kernel": kname, "ms_per_launch": kms,
-                "peak_source": "FP64 FMA-chain probe measured live on this GPU (dm_measure_alu_peaks)",
-                "stage_ms_per_iter": {k: prof[k] / max(1, prof["iterations"]) for k in
-                                      ["ms_analysis", "ms_reduce", "ms_synthesis", "ms_ring", "ms_control"]},
-                "fp32_peak_tflops": fp32_peak}
+    stage = {k: prof[k] / max(1, prof["iterations"]) for k in
+             ["ms_analysis", "ms_reduce", "ms_synthesis", "ms_ring", "ms_control"]}
+    if prec == dmwf.DM_FP64:
+        achieved = FLOPS_PER_TRIPLE * triples * B / (kms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak,
+                    "peak_source": "FP64 FMA-chain probe measured live on this GPU (dm_measure_alu_peaks)"}
+    else:
+        # FP32 contraction from FP32 tables: 20 flops per triple per RHS on the
+        # FP32 pipe; the 3 table values per triple are read once per launch.
+        flops = 20.0 * triples * B
+        tbytes = 12.0 * triples
+        ach_f = flops / (kms * 1e-3) / 1e12
+        ach_b = tbytes / (kms * 1e-3) / 1e9
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        if ach_f / fp32_peak >= ach_b / hbm:
+            roofline = {"bound": "alu", "achieved": ach_f, "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": ach_f / fp32_peak,
+                        "peak_source": "FP32 FMA-chain probe measured live on this GPU (dm_measure_alu_peaks)"}
+        else:
+            roofline = {"bound": "hbm", "achieved": ach_b, "peak": hbm, "unit": "GB/s", "frac": ach_b / hbm,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
+    roofline.update({"traffic": traffic_for(kname, workload_name), "kernel": kname, "ms_per_launch": kms,
+                     "stage_ms_per_iter": stage, "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak})
 
     # ---- end to end through the host-buffer entry point ----
     e2e = None
@@ -302,13 +342,15 @@ def main():
     if rank == 0:
         line = {"metric": "DM iterations/s", "value": value, "unit": "DM iterations/s", "n_gpus": ws,
                 "steps": K, "warmup": Wu, "ms_per_step": ms_max / K, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == dmwf.DM_FP64 else "f32+f64",
+                "data": "synthetic",
                 "config": {"workload": f"batched constrained realisations nside {nside} lmax {lmax}: "
                                        f"{nwf} WF + {B - nwf} fluctuation RHS per launch (seeds 100..{99 + B})",
-                           "nside": nside, "lmax": lmax, "batch": B, "precision": "fp64",
+                           "nside": nside, "lmax": lmax, "batch": B, "precision": args.precision,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "l2": "inputs larger than L2 (maps and ring coefficients exceed 129 MB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["launches"],
+                "fp64_gpu": fp64_line,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     plan.close()

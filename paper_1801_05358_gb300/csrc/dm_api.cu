@@ -44,7 +44,8 @@ void free_all(dm_plan *p) {
   p->ev.clear();
   void *ptrs[] = {p->rings, p->pairs, p->phase, p->bhat, p->twid, p->rec, p->seed, p->seed_exp, p->cl,
                   p->filt, p->w, p->mask, p->sigma, p->rc, p->a, p->apart, p->wd, p->norms, p->state,
-                  p->lev, p->tmpmap, p->tmpmap2, p->tmpalm, p->seeds_dev, p->coef_tmp};
+                  p->lev, p->tmpmap, p->tmpmap2, p->tmpalm, p->seeds_dev, p->coef_tmp,
+                  p->ptab, p->rc32, p->apart32, p->s32, p->w32, p->wd32, p->phase32, p->bhat32, p->twid32};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -112,7 +113,11 @@ dm_status check_ready(dm_plan *p) {
 dm_status run_dm(dm_plan *p, const double *d, double *s_out, cudaStream_t st) {
   const int64_t n3 = 3 * p->npix;
   DM_CU(cudaMemsetAsync(p->a, 0, sizeof(double2) * 3 * p->nalm * p->batch, st), "zero a");
-  DM_CU(cudaMemsetAsync(s_out, 0, sizeof(double) * n3 * p->batch, st), "zero s");
+  const bool fp32 = p->prec != DM_FP64;
+  if (fp32)
+    DM_CU(cudaMemsetAsync(p->s32, 0, sizeof(float) * n3 * p->batch, st), "zero s");
+  else
+    DM_CU(cudaMemsetAsync(s_out, 0, sizeof(double) * n3 * p->batch, st), "zero s");
   DM_CU(prepare_wd(p, d, st), "w d");
   DM_CU(control_init(p, st), "control init");
   p->state_active = true;
@@ -172,6 +177,10 @@ dm_status run_dm(dm_plan *p, const double *d, double *s_out, cudaStream_t st) {
     if (launched > cap) { rs = fail(p, DM_ENOTCONV, "iteration cap reached"); break; }
   }
   p->state_active = false;
+  if (rs == DM_OK && fp32) {
+    cudaError_t e = copy_s32_to_user(p, s_out, st);
+    if (e) rs = cuda_fail(p, e, "copy s");
+  }
   return rs;
 }
 
@@ -271,7 +280,8 @@ dm_status dm_plan_info(const dm_plan *p, int64_t *npix, int64_t *nalm, int *nrin
 
 dm_status dm_set_precision(dm_plan *p, dm_precision prec) {
   if (!p) return DM_EINVAL;
-  if (prec != DM_FP64) return fail(p, DM_EINVAL, "precision mode not available in this build");
+  if (prec != DM_FP64 && prec != DM_MIXED_FP32) return fail(p, DM_EINVAL, "unknown precision mode");
+  if (prec == DM_MIXED_FP32) DM_CU(setup_fp32(p), "mixed-precision tables");
   p->prec = prec;
   return DM_OK;
 }

@@ -105,8 +105,32 @@ __global__ void k_wd(const double *__restrict__ d, const double *__restrict__ w,
   }
 }
 
+// FP32 iteration maps: w32 = w and wd32 = w d, both rounded once from FP64
+__global__ void k_wd32(const double *__restrict__ d, const double *__restrict__ w, float *__restrict__ w32,
+                       float *__restrict__ wd32, int64_t n3, int batch) {
+  int64_t total = n3 * batch;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    double ww = w[i % n3];
+    wd32[i] = (ww > 0.0) ? (float)(ww * d[i]) : 0.0f;
+    if (i < n3) w32[i] = (float)ww;
+  }
+}
+
 cudaError_t prepare_wd(dm_plan *p, const double *d, cudaStream_t st) {
-  k_wd<<<2048, 256, 0, st>>>(d, p->w, p->wd, 3 * p->npix, p->batch);
+  if (p->prec == DM_FP64)
+    k_wd<<<2048, 256, 0, st>>>(d, p->w, p->wd, 3 * p->npix, p->batch);
+  else
+    k_wd32<<<2048, 256, 0, st>>>(d, p->w, p->w32, p->wd32, 3 * p->npix, p->batch);
+  return cudaGetLastError();
+}
+
+__global__ void k_f2d(const float *__restrict__ in, double *__restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+cudaError_t copy_s32_to_user(dm_plan *p, double *s_out, cudaStream_t st) {
+  k_f2d<<<2048, 256, 0, st>>>(p->s32, s_out, 3 * p->npix * p->batch);
   return cudaGetLastError();
 }
 

@@ -115,6 +115,15 @@ struct dm_plan {
   double *coef_tmp = nullptr;   // [lmax+1][4] filter of dm_apply_filter
   bool state_active = false;    // kernels consult state[] (skip finished RHS)
   int64_t bytes = 0;
+  // DM_MIXED_FP32 resources (allocated by dm_set_precision)
+  float *ptab = nullptr;        // [3][nalm][npairs] lambda, lam+, lam- in FP32 (FP64 recurrence)
+  float2 *rc32 = nullptr;       // [B][3][mmax+1][npairs][2]
+  float2 *apart32 = nullptr;    // [B][nchunk][3][nalm]
+  float *s32 = nullptr;         // [B][3][npix] iteration map
+  float *w32 = nullptr;         // [3][npix]
+  float *wd32 = nullptr;        // [B][3][npix]
+  float2 *phase32 = nullptr, *bhat32 = nullptr, *twid32 = nullptr;
+  int64_t bh_total = 0, ph_total = 0;
   // measurement
   bool prof_on = false;
   dm_profile prof{};
@@ -148,6 +157,8 @@ cudaError_t build_filter_one(dm_plan *p, double lambda, double *coef, cudaStream
 cudaError_t control_init(dm_plan *p, cudaStream_t st);
 cudaError_t control_step(dm_plan *p, cudaStream_t st);
 cudaError_t prepare_wd(dm_plan *p, const double *d, cudaStream_t st);
+cudaError_t setup_fp32(dm_plan *p);                          // tables and buffers of DM_MIXED_FP32
+cudaError_t copy_s32_to_user(dm_plan *p, double *s_out, cudaStream_t st);
 
 // constrained realisations
 cudaError_t draw_signal(dm_plan *p, const uint64_t *seeds_dev, double2 *ahat, cudaStream_t st);

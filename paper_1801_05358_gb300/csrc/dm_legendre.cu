@@ -175,7 +175,11 @@ __global__ void __launch_bounds__(SYN_THREADS) k_leg_syn64(const PairDev *__rest
   }
 }
 
+cudaError_t legendre_synthesis32(dm_plan *p, const double2 *alm, cudaStream_t st);
+cudaError_t legendre_analysis32(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid);
+
 cudaError_t legendre_synthesis(dm_plan *p, const double2 *alm, cudaStream_t st) {
+  if (p->prec != DM_FP64) return legendre_synthesis32(p, alm, st);
   dim3 grid((p->npairs + SYN_THREADS - 1) / SYN_THREADS, p->mmax + 1, p->batch);
   k_leg_syn64<<<grid, SYN_THREADS, 0, st>>>(p->pairs, p->rec, p->seed, p->seed_exp, alm, p->rc, p->lmax, p->mmax,
                                            p->npairs, p->nalm, p->state_active ? p->state : nullptr);
@@ -313,6 +317,7 @@ __global__ void k_ana_reduce(const double2 *__restrict__ apart, double2 *out, in
 }
 
 cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid) {
+  if (p->prec != DM_FP64) return legendre_analysis32(p, epilogue, out, st, mid);
   dim3 grid(p->nchunk, p->mmax + 1, p->batch);
   const SolveState *stp = p->state_active ? p->state : nullptr;
   k_leg_ana64<<<grid, ANA_P, 0, st>>>(p->pairs, p->rec, p->seed, p->seed_exp, p->rc, p->apart, p->lmax, p->mmax,
@@ -344,6 +349,292 @@ __global__ void k_apply_filter(const double *__restrict__ coef, const double2 *i
 
 cudaError_t apply_filter_level(dm_plan *p, const double *coef, const double2 *in, double2 *out, cudaStream_t st) {
   k_apply_filter<<<dim3(1, p->batch, p->mmax + 1), 128, 0, st>>>(coef, in, out, p->lmax, p->nalm);
+  return cudaGetLastError();
+}
+
+// ======================================================================
+// DM_MIXED_FP32: Legendre values from the FP64 recurrence, stored once in
+// FP32 tables ptab[f][idx(l, m)][pair] (f = lambda, lam+, lam-); FP32
+// contraction; FP32 ring coefficients; FP64 harmonic state and filter.
+// ======================================================================
+
+__global__ void __launch_bounds__(128) k_gen_tables(const PairDev *__restrict__ pairs, const RecCoef *__restrict__ rec,
+                                                    const double *__restrict__ seed, const int *__restrict__ seed_exp,
+                                                    float *__restrict__ ptab, int lmax, int npairs, int64_t nalm) {
+  __shared__ RecCoef sc[SYN_CH];
+  const int m = blockIdx.y;
+  const int p = blockIdx.x * 128 + threadIdx.x;
+  const bool act = p < npairs;
+  const int pp = act ? p : npairs - 1;
+  const double x = pairs[pp].x;
+  Rec s;
+  rec_init(s, seed, seed_exp, m, pp, npairs);
+  const int64_t base = alm_base(lmax, m);
+  const int64_t plane = nalm * (int64_t)npairs;
+  for (int lc = m; lc <= lmax; lc += SYN_CH) {
+    const int cnt = min(SYN_CH, lmax + 1 - lc);
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += 128) sc[j] = rec[base + lc + j + 1];
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      const int l = lc + j;
+      if (act) {
+        const int64_t o = (base + l) * (int64_t)npairs + p;
+        const bool live = (s.S == 0);
+        ptab[o] = live ? (float)s.l0 : 0.0f;
+        ptab[plane + o] = live ? (float)s.p0 : 0.0f;
+        ptab[2 * plane + o] = live ? (float)s.q0 : 0.0f;
+      }
+      if (l < lmax) rec_advance(s, sc[j], x, m, l, seed, pp, npairs);
+    }
+  }
+}
+
+cudaError_t gen_tables32(dm_plan *p) {
+  dim3 g((p->npairs + 127) / 128, p->mmax + 1);
+  k_gen_tables<<<g, 128>>>(p->pairs, p->rec, p->seed, p->seed_exp, p->ptab, p->lmax, p->npairs, p->nalm);
+  return cudaGetLastError();
+}
+
+// Synthesis, FP32 contraction over l; NB right-hand sides per thread.
+// grid: (batch / NB, pair blocks, m); consecutive blocks share the table tile in L2.
+template <int NB>
+__global__ void __launch_bounds__(SYN_THREADS) k_leg_syn32(const float *__restrict__ ptab,
+                                                           const double2 *__restrict__ alm,
+                                                           float2 *__restrict__ rc, int lmax, int mmax, int npairs,
+                                                           int64_t nalm, const SolveState *__restrict__ state) {
+  __shared__ float2 sT[NB][SYN_CH], sE[NB][SYN_CH], sB[NB][SYN_CH];
+  const int b0 = blockIdx.x * NB, m = blockIdx.z;
+  bool any = false;
+  for (int k = 0; k < NB; ++k) any = any || state == nullptr || !state[b0 + k].done;
+  if (!any) return;
+  const int p = blockIdx.y * SYN_THREADS + threadIdx.x;
+  const bool act = p < npairs;
+  const int pp = act ? p : npairs - 1;
+  float2 T0[NB], T1[NB], Q0[NB], Q1[NB], U0[NB], U1[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    T0[k] = T1[k] = Q0[k] = Q1[k] = U0[k] = U1[k] = make_float2(0.f, 0.f);
+  }
+  const int64_t base = alm_base(lmax, m);
+  const int64_t plane = nalm * (int64_t)npairs;
+  const float *P0 = ptab + base * npairs + pp, *Pp = P0 + plane, *Pq = P0 + 2 * plane;
+  for (int lc = m; lc <= lmax; lc += SYN_CH) {
+    const int cnt = min(SYN_CH, lmax + 1 - lc);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt * NB; i += SYN_THREADS) {
+      const int k = i / cnt, j = i % cnt;
+      const int64_t ob = (int64_t)(b0 + k) * 3 * nalm + base + lc + j;
+      const double2 t = alm[ob], e = alm[ob + nalm], bb = alm[ob + 2 * nalm];
+      sT[k][j] = make_float2((float)t.x, (float)t.y);
+      sE[k][j] = make_float2((float)-e.x, (float)-e.y);
+      sB[k][j] = make_float2((float)-bb.x, (float)-bb.y);
+    }
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      const int l = lc + j;
+      const int64_t o = (int64_t)l * npairs;  // table entry idx(l, m) = base + l
+      const float lam = P0[o], lp = Pp[o], lq = Pq[o];
+      if (((l - m) & 1) == 0) {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+          const float2 t = sT[k][j], ne = sE[k][j], nb = sB[k][j];
+          T0[k].x = fmaf(t.x, lam, T0[k].x); T0[k].y = fmaf(t.y, lam, T0[k].y);
+          Q0[k].x = fmaf(ne.x, lp, Q0[k].x); Q0[k].y = fmaf(ne.y, lp, Q0[k].y);
+          U0[k].x = fmaf(nb.x, lp, U0[k].x); U0[k].y = fmaf(nb.y, lp, U0[k].y);
+          Q1[k].x = fmaf(-nb.y, lq, Q1[k].x); Q1[k].y = fmaf(nb.x, lq, Q1[k].y);
+          U1[k].x = fmaf(ne.y, lq, U1[k].x); U1[k].y = fmaf(-ne.x, lq, U1[k].y);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+          const float2 t = sT[k][j], ne = sE[k][j], nb = sB[k][j];
+          T1[k].x = fmaf(t.x, lam, T1[k].x); T1[k].y = fmaf(t.y, lam, T1[k].y);
+          Q1[k].x = fmaf(ne.x, lp, Q1[k].x); Q1[k].y = fmaf(ne.y, lp, Q1[k].y);
+          U1[k].x = fmaf(nb.x, lp, U1[k].x); U1[k].y = fmaf(nb.y, lp, U1[k].y);
+          Q0[k].x = fmaf(-nb.y, lq, Q0[k].x); Q0[k].y = fmaf(nb.x, lq, Q0[k].y);
+          U0[k].x = fmaf(ne.y, lq, U0[k].x); U0[k].y = fmaf(-ne.x, lq, U0[k].y);
+        }
+      }
+    }
+  }
+  if (!act) return;
+  const bool equator = (p == npairs - 1);
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int b = b0 + k;
+    if (state != nullptr && state[b].done) continue;
+    float2 *o0 = rc + rc_index2(b, 0, m, mmax, p, npairs);
+    float2 *o1 = rc + rc_index2(b, 1, m, mmax, p, npairs);
+    float2 *o2 = rc + rc_index2(b, 2, m, mmax, p, npairs);
+    o0[0] = cadd(T0[k], T1[k]);
+    o1[0] = cadd(Q0[k], Q1[k]);
+    o2[0] = cadd(U0[k], U1[k]);
+    if (!equator) {
+      o0[1] = csub(T0[k], T1[k]);
+      o1[1] = csub(Q0[k], Q1[k]);
+      o2[1] = csub(U0[k], U1[k]);
+    }
+  }
+}
+
+// Analysis, FP32: P tile from the table into smem, then the per-l contraction
+// over the pairs of the chunk (same structure as k_leg_ana64), NB RHS per block.
+template <int NB>
+__global__ void __launch_bounds__(ANA_P) k_leg_ana32(const float *__restrict__ ptab, const float2 *__restrict__ rc,
+                                                     float2 *__restrict__ apart, int lmax, int mmax, int npairs,
+                                                     int64_t nalm, int nchunk, const SolveState *__restrict__ state) {
+  __shared__ float P0[ANA_P][ANA_L + 1], Pp[ANA_P][ANA_L + 1], Pq[ANA_P][ANA_L + 1];
+  __shared__ float4 G[ANA_P][NB][3];  // (GT_e, GT_o), (GQ_e, GQ_o), (GU_e, GU_o)
+  __shared__ float red[ANA_PARTS][ANA_L][NB][6];
+  const int b0 = blockIdx.x * NB, chunk = blockIdx.y, m = blockIdx.z;
+  bool any = false;
+  for (int k = 0; k < NB; ++k) any = any || state == nullptr || !state[b0 + k].done;
+  if (!any) return;
+  const int t = threadIdx.x;
+  const int p = chunk * ANA_P + t;
+  const bool act = p < npairs;
+  const int pp = act ? p : npairs - 1;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    float2 gn[3], gs[3];
+    for (int f = 0; f < 3; ++f) {
+      const float2 *g = rc + rc_index2(b0 + k, f, m, mmax, pp, npairs);
+      gn[f] = act ? g[0] : make_float2(0.f, 0.f);
+      gs[f] = (act && p != npairs - 1) ? g[1] : make_float2(0.f, 0.f);
+    }
+    for (int f = 0; f < 3; ++f) {
+      float2 e = cadd(gn[f], gs[f]), o = csub(gn[f], gs[f]);
+      G[t][k][f] = make_float4(e.x, e.y, o.x, o.y);
+    }
+  }
+  const int64_t base = alm_base(lmax, m);
+  const int64_t plane = nalm * (int64_t)npairs;
+  const int lj = t % ANA_L, part = t / ANA_L;
+  for (int lc = m; lc <= lmax; lc += ANA_L) {
+    const int cnt = min(ANA_L, lmax + 1 - lc);
+    __syncthreads();
+    // phase A: tile of the tables, coalesced over pairs
+    for (int j = 0; j < cnt; ++j) {
+      const int64_t o = (base + lc + j) * (int64_t)npairs + pp;
+      P0[t][j] = act ? ptab[o] : 0.f;
+      Pp[t][j] = act ? ptab[plane + o] : 0.f;
+      Pq[t][j] = act ? ptab[2 * plane + o] : 0.f;
+    }
+    __syncthreads();
+    float acc[NB][6];
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) acc[k][i] = 0.f;
+    if (lj < cnt) {
+      const int l = lc + lj;
+      const bool odd = ((l - m) & 1) != 0;
+      for (int q = part * ANA_L; q < (part + 1) * ANA_L; ++q) {
+        const float lam = P0[q][lj], lp = Pp[q][lj], lq = Pq[q][lj];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+          const float4 gt4 = G[q][k][0], gq4 = G[q][k][1], gu4 = G[q][k][2];
+          const float2 gt = odd ? make_float2(gt4.z, gt4.w) : make_float2(gt4.x, gt4.y);
+          const float2 gqp = odd ? make_float2(gq4.z, gq4.w) : make_float2(gq4.x, gq4.y);
+          const float2 gup = odd ? make_float2(gu4.z, gu4.w) : make_float2(gu4.x, gu4.y);
+          const float2 gqo = odd ? make_float2(gq4.x, gq4.y) : make_float2(gq4.z, gq4.w);
+          const float2 guo = odd ? make_float2(gu4.x, gu4.y) : make_float2(gu4.z, gu4.w);
+          acc[k][0] = fmaf(lam, gt.x, acc[k][0]);
+          acc[k][1] = fmaf(lam, gt.y, acc[k][1]);
+          acc[k][2] = fmaf(-lp, gqp.x, fmaf(lq, guo.y, acc[k][2]));
+          acc[k][3] = fmaf(-lp, gqp.y, fmaf(-lq, guo.x, acc[k][3]));
+          acc[k][4] = fmaf(-lp, gup.x, fmaf(-lq, gqo.y, acc[k][4]));
+          acc[k][5] = fmaf(-lp, gup.y, fmaf(lq, gqo.x, acc[k][5]));
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) red[part][lj][k][i] = acc[k][i];
+    __syncthreads();
+    if (part == 0 && lj < cnt) {
+      const int l = lc + lj;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        float v[6];
+        for (int i = 0; i < 6; ++i) {
+          float a = red[0][lj][k][i];
+          for (int q = 1; q < ANA_PARTS; ++q) a += red[q][lj][k][i];
+          v[i] = a;
+        }
+        float2 *o = apart + ((int64_t)(b0 + k) * nchunk + chunk) * 3 * nalm + base + l;
+        o[0] = make_float2(v[0], v[1]);
+        o[nalm] = make_float2(v[2], v[3]);
+        o[2 * nalm] = make_float2(v[4], v[5]);
+      }
+    }
+  }
+}
+
+// chunk sum in FP64, then the FP64 harmonic step and filter
+__global__ void k_ana_reduce32(const float2 *__restrict__ apart, double2 *out, int lmax, int64_t nalm, int nchunk,
+                               double omega, int epilogue, const double *__restrict__ filt,
+                               const SolveState *__restrict__ state) {
+  const int b = blockIdx.y, m = blockIdx.z;
+  if (state != nullptr && state[b].done) return;
+  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
+  if (l > lmax) return;
+  const int64_t i = alm_base(lmax, m) + l;
+  double2 acc[3];
+  for (int f = 0; f < 3; ++f) {
+    double ax = 0.0, ay = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      const float2 v = apart[(((int64_t)b * nchunk + c) * 3 + f) * nalm + i];
+      ax += v.x;
+      ay += v.y;
+    }
+    acc[f] = make_double2(omega * ax, omega * ay);
+  }
+  double2 *o = out + (int64_t)b * 3 * nalm + i;
+  if (epilogue == ANA_PLAIN) {
+    o[0] = acc[0];
+    o[nalm] = acc[1];
+    o[2 * nalm] = acc[2];
+    return;
+  }
+  const double *c = filt + ((int64_t)state[b].level * (lmax + 1) + l) * 4;
+  double2 t = cadd(o[0], acc[0]), e = cadd(o[nalm], acc[1]), bb = cadd(o[2 * nalm], acc[2]);
+  o[0] = make_double2(c[0] * t.x + c[1] * e.x, c[0] * t.y + c[1] * e.y);
+  o[nalm] = make_double2(c[1] * t.x + c[2] * e.x, c[1] * t.y + c[2] * e.y);
+  o[2 * nalm] = make_double2(c[3] * bb.x, c[3] * bb.y);
+}
+
+cudaError_t legendre_synthesis32(dm_plan *p, const double2 *alm, cudaStream_t st) {
+  const SolveState *stp = p->state_active ? p->state : nullptr;
+  const int pb = (p->npairs + SYN_THREADS - 1) / SYN_THREADS;
+  if (p->batch % 4 == 0) {
+    dim3 g(p->batch / 4, pb, p->mmax + 1);
+    k_leg_syn32<4><<<g, SYN_THREADS, 0, st>>>(p->ptab, alm, p->rc32, p->lmax, p->mmax, p->npairs, p->nalm, stp);
+  } else {
+    dim3 g(p->batch, pb, p->mmax + 1);
+    k_leg_syn32<1><<<g, SYN_THREADS, 0, st>>>(p->ptab, alm, p->rc32, p->lmax, p->mmax, p->npairs, p->nalm, stp);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t legendre_analysis32(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid) {
+  const SolveState *stp = p->state_active ? p->state : nullptr;
+  if (p->batch % 4 == 0) {
+    dim3 g(p->batch / 4, p->nchunk, p->mmax + 1);
+    k_leg_ana32<4><<<g, ANA_P, 0, st>>>(p->ptab, p->rc32, p->apart32, p->lmax, p->mmax, p->npairs, p->nalm,
+                                        p->nchunk, stp);
+  } else {
+    dim3 g(p->batch, p->nchunk, p->mmax + 1);
+    k_leg_ana32<1><<<g, ANA_P, 0, st>>>(p->ptab, p->rc32, p->apart32, p->lmax, p->mmax, p->npairs, p->nalm,
+                                        p->nchunk, stp);
+  }
+  if (mid) cudaEventRecord(mid, st);
+  double omega = 4.0 * M_PI / (double)p->npix;
+  dim3 g2((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
+  k_ana_reduce32<<<g2, 128, 0, st>>>(p->apart32, out, p->lmax, p->nalm, p->nchunk, omega, epilogue, p->filt,
+                                     epilogue == ANA_DM_STEP ? p->state : stp);
   return cudaGetLastError();
 }
 

@@ -17,37 +17,43 @@ __device__ __forceinline__ int64_t rc_index(int b, int f, int m, int mmax, int p
   return ((((int64_t)b * 3 + f) * (mmax + 1) + m) * npairs + pair) * 2 + side;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256) k_ring(const RingDev *__restrict__ rings, const double2 *__restrict__ phase,
-                                              const double2 *__restrict__ bhat, const double2 *__restrict__ twid,
-                                              int Mtab, double2 *__restrict__ rc, int mmax, int npairs, int64_t npix,
-                                              int nrings, const double *__restrict__ in_map, double *out_map,
-                                              const double *__restrict__ w, const double *__restrict__ wd,
+// R: real type of the FFT and of the iteration maps (double or float); C its
+// complex type.  User maps (in_map, out_user) are always FP64.
+template <typename R, typename C, int MODE>
+__global__ void __launch_bounds__(256) k_ring(const RingDev *__restrict__ rings, const C *__restrict__ phase,
+                                              const C *__restrict__ bhat, const C *__restrict__ twid, int Mtab,
+                                              C *__restrict__ rc, int mmax, int npairs, int64_t npix, int nrings,
+                                              const double *__restrict__ in_map, double *__restrict__ out_user,
+                                              R *s_state, const R *__restrict__ w, const R *__restrict__ wd,
                                               double *__restrict__ norms, const SolveState *__restrict__ state) {
-  extern __shared__ double2 sm[];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C *sm = reinterpret_cast<C *>(sm_raw);
   const int r = blockIdx.x, f = blockIdx.y, b = blockIdx.z;
   if ((MODE == RING_ITER || MODE == RING_INIT) && state != nullptr && state[b].done) return;
-  const RingDev R = rings[r];
-  const int n = R.n, h = R.h;
+  const RingDev Rg = rings[r];
+  const int n = Rg.n, h = Rg.h;
   const int64_t n2 = 2LL * n;
-  const double2 *ph = phase + R.ph_off;  // e^{-i pi q / n}, q < 2n
-  double2 *buf = sm;                     // FFT work area, M entries
-  double2 *cb = sm + Mtab;               // h + 1 <= Mtab + 1 spectrum entries
-  const int64_t moff = ((int64_t)b * 3 + f) * npix + R.start;
+  const C *ph = phase + Rg.ph_off;  // e^{-i pi q / n}, q < 2n
+  C *buf = sm;                      // FFT work area, M entries
+  C *cb = sm + Mtab;                // h + 1 <= Mtab + 1 spectrum entries
+  const int64_t moff = ((int64_t)b * 3 + f) * npix + Rg.start;
+  const C *bh = bhat + (Rg.bh_off < 0 ? 0 : Rg.bh_off);
 
   if (MODE == RING_INV_MAP || MODE == RING_ITER) {
     // Fold F_m (m = -mmax..mmax, F_{-m} = conj F_m) into C_k = sum_{m = k mod n} F_m e^{i m phi0}, k <= h.
     for (int k = threadIdx.x; k <= h; k += blockDim.x) {
-      double2 acc = make_double2(0.0, 0.0);
+      C acc;
+      acc.x = 0;
+      acc.y = 0;
       for (int m = k; m <= mmax; m += n) {
-        double2 F = rc[rc_index(b, f, m, mmax, R.pair, npairs, R.side)];
-        double2 e = cconj(ph[((int64_t)m * R.shift) % n2]);
+        C F = rc[rc_index(b, f, m, mmax, Rg.pair, npairs, Rg.side)];
+        C e = cconj(ph[((int64_t)m * Rg.shift) % n2]);
         acc = cadd(acc, cmul(F, e));
       }
       for (int m = n - k; m <= mmax; m += n) {
         if (m < 1) continue;
-        double2 F = rc[rc_index(b, f, m, mmax, R.pair, npairs, R.side)];
-        double2 e = cconj(ph[((int64_t)m * R.shift) % n2]);
+        C F = rc[rc_index(b, f, m, mmax, Rg.pair, npairs, Rg.side)];
+        C e = cconj(ph[((int64_t)m * Rg.shift) % n2]);
         acc = cadd(acc, cconj(cmul(F, e)));
       }
       cb[k] = acc;
@@ -57,37 +63,41 @@ __global__ void __launch_bounds__(256) k_ring(const RingDev *__restrict__ rings,
     // E_k = C_k + conj(C_{h-k}),  O_k = (C_k - conj(C_{h-k})) e^{2 pi i k/n}; stored conjugated
     // so that a forward FFT followed by conjugation gives the inverse.
     for (int k = threadIdx.x; k < h; k += blockDim.x) {
-      double2 ck = cb[k], cc = cconj(cb[h - k]);
-      double2 E = cadd(ck, cc);
-      double2 O = cmul(csub(ck, cc), cconj(ph[2 * k]));
-      double2 Z = make_double2(E.x - O.y, E.y + O.x);
+      C ck = cb[k], cc = cconj(cb[h - k]);
+      C E = cadd(ck, cc);
+      C O = cmul(csub(ck, cc), cconj(ph[2 * k]));
+      C Z;
+      Z.x = E.x - O.y;
+      Z.y = E.y + O.x;
       buf[k] = cconj(Z);
     }
     __syncthreads();
-    dft_forward(buf, h, R.M, R.bluestein, ph, bhat + (R.bh_off < 0 ? 0 : R.bh_off), twid, Mtab);
+    dft_forward(buf, h, Rg.M, Rg.bluestein, ph, bh, twid, Mtab);
     // z_j = conj(buf_j) = s_{2j} + i s_{2j+1}
     if (MODE == RING_INV_MAP) {
       for (int j = threadIdx.x; j < h; j += blockDim.x) {
-        double2 z = buf[j];
-        out_map[moff + 2 * j] = z.x;
-        out_map[moff + 2 * j + 1] = -z.y;
+        C z = buf[j];
+        out_user[moff + 2 * j] = (double)z.x;
+        out_user[moff + 2 * j + 1] = -(double)z.y;
       }
       return;
     }
-    // RING_ITER: Cauchy partials, store s, form t - s = w d - w s and pack it.
+    // RING_ITER: Cauchy partials (FP64), store s, form t - s = w d - w s and pack it.
     double dd = 0.0, ss = 0.0;
-    const int64_t wo = (int64_t)f * npix + R.start;
+    const int64_t wo = (int64_t)f * npix + Rg.start;
     for (int j = threadIdx.x; j < h; j += blockDim.x) {
-      double2 z = buf[j];
-      double s0 = z.x, s1 = -z.y;
-      double o0 = out_map[moff + 2 * j], o1 = out_map[moff + 2 * j + 1];
-      dd += (s0 - o0) * (s0 - o0) + (s1 - o1) * (s1 - o1);
-      ss += s0 * s0 + s1 * s1;
-      out_map[moff + 2 * j] = s0;
-      out_map[moff + 2 * j + 1] = s1;
-      double r0 = wd[moff + 2 * j] - w[wo + 2 * j] * s0;
-      double r1 = wd[moff + 2 * j + 1] - w[wo + 2 * j + 1] * s1;
-      buf[j] = make_double2(r0, r1);
+      C z = buf[j];
+      R s0 = z.x, s1 = -z.y;
+      R o0 = s_state[moff + 2 * j], o1 = s_state[moff + 2 * j + 1];
+      double d0 = (double)s0 - (double)o0, d1 = (double)s1 - (double)o1;
+      dd += d0 * d0 + d1 * d1;
+      ss += (double)s0 * (double)s0 + (double)s1 * (double)s1;
+      s_state[moff + 2 * j] = s0;
+      s_state[moff + 2 * j + 1] = s1;
+      C rr;
+      rr.x = wd[moff + 2 * j] - w[wo + 2 * j] * s0;
+      rr.y = wd[moff + 2 * j + 1] - w[wo + 2 * j + 1] * s1;
+      buf[j] = rr;
     }
     // block reduction of (dd, ss)
     __shared__ double red[2][32];
@@ -112,92 +122,126 @@ __global__ void __launch_bounds__(256) k_ring(const RingDev *__restrict__ rings,
     }
   } else {
     // forward only: load the real ring (RING_INIT: t_0 - s_0 = d on observed pixels)
-    const int64_t wo = (int64_t)f * npix + R.start;
+    const int64_t wo = (int64_t)f * npix + Rg.start;
     for (int j = threadIdx.x; j < h; j += blockDim.x) {
       double x0 = in_map[moff + 2 * j], x1 = in_map[moff + 2 * j + 1];
       if (MODE == RING_INIT) {
-        x0 = (w[wo + 2 * j] > 0.0) ? x0 : 0.0;
-        x1 = (w[wo + 2 * j + 1] > 0.0) ? x1 : 0.0;
+        x0 = (w[wo + 2 * j] > (R)0) ? x0 : 0.0;
+        x1 = (w[wo + 2 * j + 1] > (R)0) ? x1 : 0.0;
       }
-      buf[j] = make_double2(x0, x1);
+      C v;
+      v.x = (R)x0;
+      v.y = (R)x1;
+      buf[j] = v;
     }
   }
   __syncthreads();
   // forward: Z = FFT_h(z), X_k = E_k + e^{-2 pi i k/n} O_k, k = 0..h
-  dft_forward(buf, h, R.M, R.bluestein, ph, bhat + (R.bh_off < 0 ? 0 : R.bh_off), twid, Mtab);
+  dft_forward(buf, h, Rg.M, Rg.bluestein, ph, bh, twid, Mtab);
+  const R half = (R)0.5;
   for (int k = threadIdx.x; k <= h; k += blockDim.x) {
-    double2 zk = buf[k == h ? 0 : k], zc = cconj(buf[k == 0 ? 0 : h - k]);
+    C zk = buf[k == h ? 0 : k], zc = cconj(buf[k == 0 ? 0 : h - k]);
     if (k == h) zc = cconj(buf[0]);
-    double2 E = make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y));
-    double2 D = csub(zk, zc);                          // = 2i O_k
-    double2 O = make_double2(0.5 * D.y, -0.5 * D.x);   // D / (2i)
+    C E, O;
+    E.x = half * (zk.x + zc.x);
+    E.y = half * (zk.y + zc.y);
+    C D = csub(zk, zc);  // = 2i O_k
+    O.x = half * D.y;
+    O.y = -half * D.x;   // D / (2i)
     cb[k] = cadd(E, cmul(O, ph[2 * k]));
   }
   __syncthreads();
   for (int m = threadIdx.x; m <= mmax; m += blockDim.x) {
     int q = m % n;
-    double2 X = (q <= h) ? cb[q] : cconj(cb[n - q]);
-    rc[rc_index(b, f, m, mmax, R.pair, npairs, R.side)] = cmul(X, ph[((int64_t)m * R.shift) % n2]);
+    C X = (q <= h) ? cb[q] : cconj(cb[n - q]);
+    rc[rc_index(b, f, m, mmax, Rg.pair, npairs, Rg.side)] = cmul(X, ph[((int64_t)m * Rg.shift) % n2]);
   }
 }
 
-cudaError_t ring_stage(dm_plan *p, int mode, const double *in_map, double *out_map, cudaStream_t st) {
+template <typename R, typename C, int MODE>
+static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const C *twid, C *rc,
+                               const double *in_map, double *out_user, R *s_state, const R *w, const R *wd,
+                               cudaStream_t st) {
   dim3 grid(p->nrings, 3, p->batch);
-  size_t smem = sizeof(double2) * (2 * (size_t)p->fft_M_max + 1);
-  const SolveState *stp = p->state;
-  switch (mode) {
-    case RING_FWD_MAP:
-      cudaFuncSetAttribute(k_ring<RING_FWD_MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_ring<RING_FWD_MAP><<<grid, 256, smem, st>>>(p->rings, p->phase, p->bhat, p->twid, p->fft_M_max, p->rc,
-                                                    p->mmax, p->npairs, p->npix, p->nrings, in_map, out_map, p->w,
-                                                    p->wd, p->norms, nullptr);
-      break;
-    case RING_INV_MAP:
-      cudaFuncSetAttribute(k_ring<RING_INV_MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_ring<RING_INV_MAP><<<grid, 256, smem, st>>>(p->rings, p->phase, p->bhat, p->twid, p->fft_M_max, p->rc,
-                                                    p->mmax, p->npairs, p->npix, p->nrings, in_map, out_map, p->w,
-                                                    p->wd, p->norms, nullptr);
-      break;
-    case RING_ITER:
-      cudaFuncSetAttribute(k_ring<RING_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_ring<RING_ITER><<<grid, 256, smem, st>>>(p->rings, p->phase, p->bhat, p->twid, p->fft_M_max, p->rc,
-                                                 p->mmax, p->npairs, p->npix, p->nrings, in_map, out_map, p->w,
-                                                 p->wd, p->norms, stp);
-      break;
-    case RING_INIT:
-      cudaFuncSetAttribute(k_ring<RING_INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_ring<RING_INIT><<<grid, 256, smem, st>>>(p->rings, p->phase, p->bhat, p->twid, p->fft_M_max, p->rc,
-                                                 p->mmax, p->npairs, p->npix, p->nrings, in_map, out_map, p->w,
-                                                 p->wd, p->norms, stp);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
+  size_t smem = sizeof(C) * (2 * (size_t)p->fft_M_max + 1);
+  const SolveState *stp = (MODE == RING_ITER || MODE == RING_INIT) ? p->state : nullptr;
+  cudaFuncSetAttribute(k_ring<R, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_ring<R, C, MODE><<<grid, 256, smem, st>>>(p->rings, phase, bhat, twid, p->fft_M_max, rc, p->mmax, p->npairs,
+                                              p->npix, p->nrings, in_map, out_user, s_state, w, wd, p->norms, stp);
   return cudaGetLastError();
 }
 
-// public layout rc_pub[b][f][ring][m] <-> internal rc[b][f][m][pair][side]
-__global__ void k_rc_pub(const RingDev *rings, double2 *rc, double2 *pub, int mmax, int npairs, int nrings,
+// FP64 maps for the user-facing modes; the iteration state is s_iter (FP64:
+// the caller's s buffer; FP32: the plan's s32).
+cudaError_t ring_stage(dm_plan *p, int mode, const double *in_map, double *out_map, cudaStream_t st) {
+  if (p->prec == DM_FP64) {
+    switch (mode) {
+      case RING_FWD_MAP:
+        return launch_ring<double, double2, RING_FWD_MAP>(p, p->phase, p->bhat, p->twid, p->rc, in_map, nullptr,
+                                                          nullptr, p->w, p->wd, st);
+      case RING_INV_MAP:
+        return launch_ring<double, double2, RING_INV_MAP>(p, p->phase, p->bhat, p->twid, p->rc, nullptr, out_map,
+                                                          nullptr, p->w, p->wd, st);
+      case RING_ITER:
+        return launch_ring<double, double2, RING_ITER>(p, p->phase, p->bhat, p->twid, p->rc, nullptr, nullptr,
+                                                       out_map, p->w, p->wd, st);
+      case RING_INIT:
+        return launch_ring<double, double2, RING_INIT>(p, p->phase, p->bhat, p->twid, p->rc, in_map, nullptr,
+                                                       nullptr, p->w, p->wd, st);
+    }
+  } else {
+    switch (mode) {
+      case RING_FWD_MAP:
+        return launch_ring<float, float2, RING_FWD_MAP>(p, p->phase32, p->bhat32, p->twid32, p->rc32, in_map,
+                                                        nullptr, nullptr, p->w32, p->wd32, st);
+      case RING_INV_MAP:
+        return launch_ring<float, float2, RING_INV_MAP>(p, p->phase32, p->bhat32, p->twid32, p->rc32, nullptr,
+                                                        out_map, nullptr, p->w32, p->wd32, st);
+      case RING_ITER:
+        return launch_ring<float, float2, RING_ITER>(p, p->phase32, p->bhat32, p->twid32, p->rc32, nullptr,
+                                                     nullptr, p->s32, p->w32, p->wd32, st);
+      case RING_INIT:
+        return launch_ring<float, float2, RING_INIT>(p, p->phase32, p->bhat32, p->twid32, p->rc32, in_map,
+                                                     nullptr, nullptr, p->w32, p->wd32, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// public layout rc_pub[b][f][ring][m] (complex128) <-> internal rc[b][f][m][pair][side]
+template <typename C>
+__global__ void k_rc_pub(const RingDev *rings, C *rc, double2 *pub, int mmax, int npairs, int nrings,
                          int to_public) {
   int r = blockIdx.x, f = blockIdx.y, b = blockIdx.z;
   RingDev R = rings[r];
   for (int m = threadIdx.x; m <= mmax; m += blockDim.x) {
     int64_t pi = (((int64_t)b * 3 + f) * nrings + r) * (mmax + 1) + m;
     int64_t ii = rc_index(b, f, m, mmax, R.pair, npairs, R.side);
-    if (to_public)
-      pub[pi] = rc[ii];
-    else
-      rc[ii] = pub[pi];
+    if (to_public) {
+      pub[pi] = make_double2(rc[ii].x, rc[ii].y);
+    } else {
+      C v;
+      v.x = pub[pi].x;
+      v.y = pub[pi].y;
+      rc[ii] = v;
+    }
   }
 }
 
 cudaError_t rc_to_public(dm_plan *p, double2 *pub, cudaStream_t st) {
-  k_rc_pub<<<dim3(p->nrings, 3, p->batch), 128, 0, st>>>(p->rings, p->rc, pub, p->mmax, p->npairs, p->nrings, 1);
+  dim3 g(p->nrings, 3, p->batch);
+  if (p->prec == DM_FP64)
+    k_rc_pub<<<g, 128, 0, st>>>(p->rings, p->rc, pub, p->mmax, p->npairs, p->nrings, 1);
+  else
+    k_rc_pub<<<g, 128, 0, st>>>(p->rings, p->rc32, pub, p->mmax, p->npairs, p->nrings, 1);
   return cudaGetLastError();
 }
 cudaError_t rc_from_public(dm_plan *p, const double2 *pub, cudaStream_t st) {
-  k_rc_pub<<<dim3(p->nrings, 3, p->batch), 128, 0, st>>>(p->rings, p->rc, const_cast<double2 *>(pub), p->mmax,
-                                                          p->npairs, p->nrings, 0);
+  dim3 g(p->nrings, 3, p->batch);
+  if (p->prec == DM_FP64)
+    k_rc_pub<<<g, 128, 0, st>>>(p->rings, p->rc, const_cast<double2 *>(pub), p->mmax, p->npairs, p->nrings, 0);
+  else
+    k_rc_pub<<<g, 128, 0, st>>>(p->rings, p->rc32, const_cast<double2 *>(pub), p->mmax, p->npairs, p->nrings, 0);
   return cudaGetLastError();
 }
 

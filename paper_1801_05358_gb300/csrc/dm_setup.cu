@@ -323,6 +323,8 @@ cudaError_t build_tables(dm_plan *p) {
   if ((e = cudaMalloc(&p->phase, sizeof(double2) * ph_n))) return e;
   if ((e = cudaMalloc(&p->twid, sizeof(double2) * (p->fft_M_max / 2)))) return e;
   if ((e = cudaMalloc(&p->bhat, sizeof(double2) * (bh_total > 0 ? bh_total : 1)))) return e;
+  p->bh_total = bh_total;
+  p->ph_total = (int64_t)ph_n;
   if ((e = cudaMalloc(&p->rec, sizeof(RecCoef) * (p->nalm + 1)))) return e;
   size_t nseed = (size_t)(p->mmax + 1) * p->npairs;
   if ((e = cudaMalloc(&p->seed, sizeof(double) * 3 * nseed))) return e;
@@ -351,6 +353,42 @@ cudaError_t build_tables(dm_plan *p) {
   k_seeds<<<(p->npairs + 63) / 64, 64>>>(p->pairs, p->seed, p->seed_exp, p->mmax, p->npairs);
   e = cudaGetLastError();
   if (e) return e;
+  return cudaDeviceSynchronize();
+}
+
+__global__ void k_d2f2(const double2 *in, float2 *out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+cudaError_t gen_tables32(dm_plan *p);  // dm_legendre.cu
+
+// Tables and buffers of DM_MIXED_FP32: FP32 copies of the FFT tables, the FP32
+// Legendre tables (FP64 recurrence), FP32 ring coefficients and maps.
+cudaError_t setup_fp32(dm_plan *p) {
+  if (p->ptab) return cudaSuccess;
+  cudaError_t e;
+  const int64_t B = p->batch, n3 = 3 * p->npix;
+  auto al = [&](auto **ptr, size_t cnt) {
+    size_t bytes = sizeof(**ptr) * (cnt > 0 ? cnt : 1);
+    cudaError_t r = cudaMalloc((void **)ptr, bytes);
+    if (!r) p->bytes += (int64_t)bytes;
+    return r;
+  };
+  if ((e = al(&p->phase32, p->ph_total))) return e;
+  if ((e = al(&p->bhat32, p->bh_total))) return e;
+  if ((e = al(&p->twid32, p->fft_M_max / 2))) return e;
+  if ((e = al(&p->ptab, (size_t)3 * p->nalm * p->npairs))) return e;
+  if ((e = al(&p->rc32, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return e;
+  if ((e = al(&p->apart32, (size_t)B * p->nchunk * 3 * p->nalm))) return e;
+  if ((e = al(&p->s32, (size_t)B * n3))) return e;
+  if ((e = al(&p->w32, (size_t)n3))) return e;
+  if ((e = al(&p->wd32, (size_t)B * n3))) return e;
+  cudaMemset(p->rc32, 0, sizeof(float2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
+  k_d2f2<<<512, 256>>>(p->phase, p->phase32, p->ph_total);
+  if (p->bh_total > 0) k_d2f2<<<512, 256>>>(p->bhat, p->bhat32, p->bh_total);
+  k_d2f2<<<64, 256>>>(p->twid, p->twid32, p->fft_M_max / 2);
+  if ((e = gen_tables32(p))) return e;
   return cudaDeviceSynchronize();
 }
 

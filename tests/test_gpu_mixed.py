@@ -1,0 +1,89 @@
+"""DM_MIXED_FP32 (FP64 recurrence, FP32 contraction and ring FFTs, FP64
+harmonic state, filter and norms) against the FP64 oracle.
+
+Bound for the mixed mode: relative L2 map error <= 1e-5 for full solves;
+single FP32 transforms are held to 2e-6."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_helpers import alm_dev, alm_host, dev, make_plan, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1801_05358_gb300 import dmwf  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("nside,lmax,B", [(8, 16, 1), (12, 30, 4), (16, 47, 3), (64, 128, 4)])
+def test_mixed_transforms(orc, nside, lmax, B):
+    alm = W.random_alm(lmax, B, 8)
+    maps = W.random_maps(nside, B, 9)
+    p = dmwf.Plan(nside, lmax, B)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    m_out = torch.zeros((B, 3, 12 * nside * nside), dtype=torch.float64, device="cuda")
+    a_out = torch.zeros((B, 3, (lmax + 1) * (lmax + 2) // 2, 2), dtype=torch.float64, device="cuda")
+    p.alm2map(alm_dev(alm), m_out)
+    p.map2alm(dev(maps), a_out)
+    gm = m_out.cpu().numpy()
+    ga = a_out.cpu().numpy().view(np.complex128)[..., 0]
+    for b in range(B):
+        assert rel(gm[b], orc.alm2map(nside, lmax, alm[b])) < 2e-6
+        assert rel(ga[b], orc.map2alm(nside, lmax, maps[b])) < 2e-6
+
+
+def _data(orc, wl):
+    return np.stack([wl.data([orc.alm2map(wl.nside, wl.lmax, a)])[0] for a in wl.alm_true])
+
+
+def test_mixed_fixed_schedule_nside16(orc):
+    wl = W.make_workload("nside16", [0])
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(1000.0, 10)
+    ref = orc.dm_solve(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.mask, d[0], lam, forced_iters=[10] * 10)
+    p = make_plan(wl, 1, lambda0=1000.0, n_levels=10, iters_per_level=10)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    s = torch.zeros((1, 3, wl.npix), dtype=torch.float64, device="cuda")
+    a = torch.zeros((1, 3, ref["alm"].shape[-1], 2), dtype=torch.float64, device="cuda")
+    p.wiener_filter(dev(d), s, a)
+    assert rel(s.cpu().numpy()[0], ref["s"]) < 1e-5
+    assert rel(alm_host(a, (1, 3, -1))[0], ref["alm"]) < 1e-5
+
+
+@pytest.mark.slow
+def test_mixed_converged_solve_nside32(orc):
+    """Run to the Cauchy criterion 1e-6 at lambda = 1 (levels 1000 -> 1):
+    the mixed-mode map stays within 1e-5 of the oracle's converged map."""
+    wl = W.make_workload("nside16", [5], nside=32, lmax=64)
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(1000.0, 10)
+    eps = W.eps_schedule(10, 1e-4, 1e-6)
+    ref = orc.dm_solve(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.mask, d[0], lam, eps=eps)
+    p = make_plan(wl, 1, lambda0=1000.0, n_levels=10, iters_per_level=0, eps0=1e-4, eps_final=1e-6, eta=0.0,
+                  check_every=32)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    s = torch.zeros((1, 3, wl.npix), dtype=torch.float64, device="cuda")
+    st, stats = p.wiener_filter(dev(d), s)
+    err = rel(s.cpu().numpy()[0], ref["s"])
+    assert err < 1e-5, (err, stats[0]["iters_total"], ref["iters"])
+
+
+def test_mixed_first_iterations_nside256(orc):
+    """Configuration nside 256 / lmax 512, first 12 iterations (3 levels of 4),
+    mixed mode against the oracle."""
+    wl = W.make_workload("nside256", [1])
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(1000.0, 3)
+    ref = orc.dm_solve(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.mask, d[0], lam, forced_iters=[4, 4, 4])
+    p = make_plan(wl, 1, lambda0=1000.0, n_levels=3, iters_per_level=4)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    s = torch.zeros((1, 3, wl.npix), dtype=torch.float64, device="cuda")
+    p.wiener_filter(dev(d), s)
+    assert rel(s.cpu().numpy()[0], ref["s"]) < 1e-5
