@@ -224,33 +224,41 @@ def main():
     s_out = torch.zeros_like(d)
     torch.cuda.synchronize()
 
+    # Schedule of a real solve: lambda 1000 -> 1 over 10 levels, Cauchy eps
+    # cooled 1e-4 -> 1e-6; the timed steps are iterations of that solve.
+    def real_schedule(check):
+        plan.set_forced_iters(None)
+        plan.set_schedule(lambda0=1000.0, n_levels=10, iters_per_level=0, eps0=1e-4, eps_final=1e-6, eta=0.0,
+                          max_iter=1000000, check_every=check)
+
     # ---- the plain FP64 GPU solve, timed beside (same batch, same API) ----
     fp64_line = None
     if args.fp64_steps > 0 and prec != dmwf.DM_FP64:
         nf = args.fp64_steps
-        plan.set_schedule(lambda0=1000.0, n_levels=10, iters_per_level=1, check_every=nf)
-        plan.set_forced_iters(iters_split(nf))
-        plan.wiener_filter(d, s_out)   # warm
+        real_schedule(nf)
+        plan.solve_begin(d)
+        plan.solve_iterate(1)            # warm
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         f0.record()
-        plan.wiener_filter(d, s_out)
+        plan.solve_iterate(nf)
         f1.record()
         torch.cuda.synchronize()
+        plan.solve_end()
         fms = f0.elapsed_time(f1)
         fp64_line = {"value": B * nf / (fms * 1e-3), "unit": "DM iterations/s", "steps": nf,
                      "ms_per_step": fms / nf}
     plan.set_precision(prec)
 
-    # ---- warm-up: W iterations through the public API ----
-    plan.set_schedule(lambda0=1000.0, n_levels=10, iters_per_level=1, check_every=max(1, Wu))
-    plan.set_forced_iters(iters_split(Wu))
-    plan.wiener_filter(d, s_out)
+    # ---- warm-up: begin a solve and run W iterations through the public API ----
+    real_schedule(max(1, K))
+    plan.profile_enable(True)
+    plan.solve_begin(d)
+    plan.solve_iterate(Wu)
+    warm_prof = plan.profile_read()
     fp64_peak, fp32_peak = dmwf.measure_alu_peaks()
 
-    # ---- timed: exactly K iterations ----
-    plan.set_schedule(lambda0=1000.0, n_levels=10, iters_per_level=1, check_every=K)
-    plan.set_forced_iters(iters_split(K))
+    # ---- timed: exactly K further iterations of the same solve ----
     plan.profile_enable(True)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -259,7 +267,7 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         e0.record(stream)
-        st, stats = plan.wiener_filter(d, s_out)
+        plan.solve_iterate(K)
         e1.record(stream)
         torch.cuda.synchronize()
     if ws > 1:
@@ -267,13 +275,21 @@ def main():
     ms = e0.elapsed_time(e1)
     prof = plan.profile_read()
     plan.profile_enable(False)
+    st, stats = plan.solve_end(s_out)
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    iters = stats[0]["iters_total"]
+    iters = prof["iterations"]
     assert iters == K, f"timed {iters} iterations, expected {K}"
+    assert stats[0]["iters_total"] == Wu + K, stats[0]["iters_total"]
     value = B * K * ws / (ms_max * 1e-3)
+    anchor = None
+    if prec != dmwf.DM_FP64:
+        ams = warm_prof["ms_anchor"] / max(1, warm_prof["anchors"])
+        every = 256
+        anchor = {"ms_per_anchor": ams, "anchor_every": every, "anchors_in_timed_window": prof["anchors"],
+                  "amortized_value": B * K * ws / ((ms_max - prof["ms_anchor"] + ams * K / every) * 1e-3)}
 
     # ---- dominant kernel roofline (Legendre stage) ----
     npairs = 2 * nside
@@ -316,6 +332,8 @@ def main():
     # ---- end to end through the host-buffer entry point ----
     e2e = None
     if not args.no_e2e:
+        plan.set_schedule(lambda0=1000.0, n_levels=10, iters_per_level=1, check_every=max(1, K))
+        plan.set_forced_iters(iters_split(K))
         d_host = d.cpu().pin_memory()
         s_host = torch.empty_like(d_host).pin_memory()
         torch.cuda.synchronize()
@@ -330,7 +348,8 @@ def main():
         nbytes = d_host.numel() * 8
         e2e = {"value": B * K / (ems * 1e-3), "unit": "DM iterations/s",
                "h2d_bytes_per_step": nbytes / K, "d2h_bytes_per_step": nbytes / K,
-               "note": f"one dm_wiener_filter_host call of {K} iterations; d in and s out once per call"}
+               "note": f"one dm_wiener_filter_host call of {K} iterations (a whole solve: begin, {K} "
+                       f"iterations, end); d in and s out once per call"}
 
     # ---- CPU baseline (oracle), rank 0 at N = 1 only ----
     cpu = None
@@ -350,7 +369,7 @@ def main():
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "l2": "inputs larger than L2 (maps and ring coefficients exceed 129 MB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["launches"],
-                "fp64_gpu": fp64_line,
+                "fp64_gpu": fp64_line, "refinement": anchor,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     plan.close()

@@ -147,6 +147,25 @@ dm_status dm_wiener_filter(dm_plan *plan, const double *d, double *s_out, double
 dm_status dm_wiener_filter_host(dm_plan *plan, const double *d_host, double *s_host, double *alm_host,
                                 dm_stats *stats, void *stream);
 
+/* The same solve in three calls, so that a caller can advance it in pieces
+ * (serving, checkpointed runs, steady-state timing):
+ *  dm_solve_begin   sets s_0 = 0, t_0 = d (d must stay valid until the call
+ *                   returns; the plan keeps w d and its own iterate);
+ *  dm_solve_iterate runs up to max_iters iterations, stops early once every
+ *                   RHS met its stopping rule (*all_done = 1); synchronises;
+ *  dm_solve_end     writes s_out / alm_out (device, may be NULL) and stats.
+ * DM_EBUSY when a solve is already in progress on the plan. */
+dm_status dm_solve_begin(dm_plan *plan, const double *d, void *stream);
+dm_status dm_solve_iterate(dm_plan *plan, int max_iters, int *all_done, void *stream);
+dm_status dm_solve_end(dm_plan *plan, double *s_out, double *alm_out, dm_stats *stats, void *stream);
+
+/* Mixed precision refinement: the FP32 stages act on the correction
+ * e = a - a_hi around an FP64 anchor a_hi, and A W (d - Y a_hi) is recomputed
+ * with the FP64 transforms every anchor_every iterations (default 256) and at
+ * the end, so the iteration keeps the FP64 fixed point (classical mixed
+ * precision iterative refinement; no counterpart in the paper). */
+dm_status dm_set_refinement(dm_plan *plan, int anchor_every);
+
 /* Constrained realisations, Section 2.2, Eq. 19:
  * s_CR = W(d - dhat) + shat with shat = Y ahat, ahat ~ S, dhat = shat + nhat,
  * nhat ~ N on observed pixels, drawn from seeds[batch] (host) with the
@@ -206,6 +225,8 @@ typedef struct {
   double ms_synthesis;     /* Legendre synthesis (a4) */
   double ms_ring;          /* inverse FFT, update, norms, forward FFT (a5, a6, a7, a1) */
   double ms_control;       /* Cauchy ratio and level control (a7, a8) */
+  int64_t anchors;         /* FP64 anchors of the mixed mode */
+  double ms_anchor;        /* their total device time */
 } dm_profile;
 
 dm_status dm_profile_enable(dm_plan *plan, int on);

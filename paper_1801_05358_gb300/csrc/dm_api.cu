@@ -45,7 +45,8 @@ void free_all(dm_plan *p) {
   void *ptrs[] = {p->rings, p->pairs, p->phase, p->bhat, p->twid, p->rec, p->seed, p->seed_exp, p->cl,
                   p->filt, p->w, p->mask, p->sigma, p->rc, p->a, p->apart, p->wd, p->norms, p->state,
                   p->lev, p->tmpmap, p->tmpmap2, p->tmpalm, p->seeds_dev, p->coef_tmp,
-                  p->ptab, p->rc32, p->apart32, p->s32, p->w32, p->wd32, p->phase32, p->bhat32, p->twid32};
+                  p->ptab, p->rc32, p->apart32, p->s32, p->w32, p->wd32, p->phase32, p->bhat32, p->twid32,
+                  p->a_hi, p->g_hi, p->shi32, p->s64, p->rhi};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -106,61 +107,130 @@ dm_status check_ready(dm_plan *p) {
 }
 
 // The iteration driver.  Device stages per iteration:
-//   analysis + harmonic step  a <- F_k [a + A (t - s)]      (k_leg_ana64 + k_ana_reduce)
-//   synthesis                 F_m(theta) from a             (k_leg_syn64)
+//   analysis + harmonic step  a <- F_k [a + A (t - s)]      (k_leg_ana + k_ana_reduce)
+//   synthesis                 F_m(theta) from a             (k_leg_syn)
 //   ring stage                s, Cauchy partials, t - s, G_m (k_ring<RING_ITER>)
 //   control                   Cauchy ratio, level, stop     (k_control_step)
-dm_status run_dm(dm_plan *p, const double *d, double *s_out, cudaStream_t st) {
-  const int64_t n3 = 3 * p->npix;
+// Mixed precision adds FP64 anchors (iterative refinement): a = a_hi + e, the
+// FP32 stages transform e only, and g_hi = A W (d - Y a_hi) is recomputed in
+// FP64 every anchor_every iterations, so the fixed point is the FP64 one.
+cudaError_t enqueue_iteration(dm_plan *p, cudaStream_t st, cudaEvent_t *E) {
+  cudaError_t e;
+  if (E) cudaEventRecord(E[0], st);
+  if ((e = legendre_analysis(p, ANA_DM_STEP, p->a, st, E ? E[1] : nullptr))) return e;
+  if (E) cudaEventRecord(E[2], st);
+  if ((e = legendre_synthesis(p, p->a, st))) return e;
+  if (E) cudaEventRecord(E[3], st);
+  if ((e = ring_stage(p, RING_ITER, nullptr, p->s64, st))) return e;
+  if (E) cudaEventRecord(E[4], st);
+  if ((e = control_step(p, st))) return e;
+  if (E) cudaEventRecord(E[5], st);
+  p->launches += 5;
+  return cudaSuccess;
+}
+
+// FP64 anchor at the current iterate (all RHS): a_hi = a, s64 = Y a_hi,
+// rhi = w (d - s64), g_hi = A rhi; the FP32 correction restarts from e = 0.
+// initial: a_hi = 0 and rhi = d on observed pixels (Algorithm 1's t_0 = d).
+dm_status anchor(dm_plan *p, cudaStream_t st, bool initial, const double *d, bool need_g) {
+  const bool sa = p->state_active;
+  const size_t an = sizeof(double2) * 3 * p->nalm * p->batch;
+  const size_t mn = sizeof(double) * 3 * p->npix * p->batch;
+  p->state_active = false;
+  p->prec = DM_FP64;
+  cudaError_t e = cudaSuccess;
+  cudaEvent_t ta = nullptr, tb = nullptr;
+  if (p->prof_on) {
+    cudaEventCreate(&ta);
+    cudaEventCreate(&tb);
+    cudaEventRecord(ta, st);
+  }
+  if (initial) {
+    if (!e) e = cudaMemsetAsync(p->a_hi, 0, an, st);
+    if (!e) e = cudaMemsetAsync(p->s64, 0, mn, st);
+    if (!e) e = anchor_residual(p, d, nullptr, st);
+    p->launches += 1;
+  } else {
+    if (!e) e = cudaMemcpyAsync(p->a_hi, p->a, an, cudaMemcpyDeviceToDevice, st);
+    if (!e) e = legendre_synthesis(p, p->a_hi, st);
+    if (!e) e = ring_stage(p, RING_INV_MAP, nullptr, p->s64, st);
+    if (!e) e = anchor_residual_wd(p, p->s64, st);
+    p->launches += 3;
+  }
+  if (need_g) {
+    if (!e) e = ring_stage(p, RING_FWD_MAP, p->rhi, nullptr, st);
+    if (!e) e = legendre_analysis(p, ANA_PLAIN, p->g_hi, st);
+    p->launches += 3;
+  }
+  p->prec = DM_MIXED_FP32;
+  if (!e) e = cudaMemsetAsync(p->s32, 0, sizeof(float) * 3 * p->npix * p->batch, st);
+  if (!e)
+    e = cudaMemsetAsync(p->rc32, 0, sizeof(float2) * (size_t)p->batch * 3 * (p->mmax + 1) * p->npairs * 2, st);
+  p->state_active = sa;
+  p->since_anchor = 0;
+  if (p->prof_on) {
+    cudaEventRecord(tb, st);
+    cudaEventSynchronize(tb);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ta, tb);
+    p->prof.ms_anchor += ms;
+    p->prof.anchors += 1;
+    cudaEventDestroy(ta);
+    cudaEventDestroy(tb);
+  }
+  if (e) return cuda_fail(p, e, "anchor");
+  return DM_OK;
+}
+
+dm_status solve_begin(dm_plan *p, const double *d, cudaStream_t st) {
   DM_CU(cudaMemsetAsync(p->a, 0, sizeof(double2) * 3 * p->nalm * p->batch, st), "zero a");
-  const bool fp32 = p->prec != DM_FP64;
-  if (fp32)
-    DM_CU(cudaMemsetAsync(p->s32, 0, sizeof(float) * n3 * p->batch, st), "zero s");
-  else
-    DM_CU(cudaMemsetAsync(s_out, 0, sizeof(double) * n3 * p->batch, st), "zero s");
   DM_CU(prepare_wd(p, d, st), "w d");
   DM_CU(control_init(p, st), "control init");
-  p->state_active = true;
-  DM_CU(ring_stage(p, RING_INIT, d, nullptr, st), "ring init");
-  std::vector<SolveState> hs(p->batch);
-  int launched = 0;
-  const dm_schedule &S = p->sched;
-  long cap = (long)S.max_iter + 4;
-  if (S.iters_per_level > 0 || !p->forced.empty()) {
-    long tot = 0;
-    for (int k = 0; k < S.n_levels; ++k) tot += p->forced.empty() ? S.iters_per_level : p->forced[k];
-    cap = tot + 4;
+  p->launches += 2;
+  if (p->prec == DM_FP64) {
+    DM_CU(cudaMemsetAsync(p->s64, 0, sizeof(double) * 3 * p->npix * p->batch, st), "zero s");
+    p->state_active = true;
+    DM_CU(ring_stage(p, RING_INIT, d, nullptr, st), "ring init");
+    p->launches += 1;
+  } else {
+    p->anchor_active = true;
+    dm_status r = anchor(p, st, true, d, true);
+    if (r != DM_OK) return r;
   }
-  const int every = std::max(1, S.check_every);
+  p->state_active = true;
+  p->session = true;
+  p->iters_launched = 0;
+  return DM_OK;
+}
+
+// Up to max_iters iterations; *all_done = 1 once every RHS has stopped.
+dm_status solve_iterate(dm_plan *p, long max_iters, int *all_done, cudaStream_t st) {
+  if (!p->session) return fail(p, DM_EINVAL, "no solve in progress (dm_solve_begin)");
+  const int every = std::max(1, p->sched.check_every);
   if (p->prof_on && (int)p->ev.size() < 6 * every) {
     int have = (int)p->ev.size();
     p->ev.resize(6 * every);
     for (int i = have; i < 6 * every; ++i) cudaEventCreate(&p->ev[i]);
   }
-  p->launches += 3;
-  dm_status rs = DM_OK;
-  for (;;) {
-    for (int k = 0; k < every; ++k) {
-      cudaError_t e;
-      cudaEvent_t *E = p->prof_on ? &p->ev[6 * k] : nullptr;
-      if (E) cudaEventRecord(E[0], st);
-      if ((e = legendre_analysis(p, ANA_DM_STEP, p->a, st, E ? E[1] : nullptr))) { rs = cuda_fail(p, e, "analysis"); break; }
-      if (E) cudaEventRecord(E[2], st);
-      if ((e = legendre_synthesis(p, p->a, st))) { rs = cuda_fail(p, e, "synthesis"); break; }
-      if (E) cudaEventRecord(E[3], st);
-      if ((e = ring_stage(p, RING_ITER, nullptr, s_out, st))) { rs = cuda_fail(p, e, "ring"); break; }
-      if (E) cudaEventRecord(E[4], st);
-      if ((e = control_step(p, st))) { rs = cuda_fail(p, e, "control"); break; }
-      if (E) cudaEventRecord(E[5], st);
-      p->launches += 5;
+  std::vector<SolveState> hs(p->batch);
+  const bool mixed = p->prec != DM_FP64;
+  long done_iters = 0;
+  *all_done = 0;
+  while (done_iters < max_iters) {
+    long window = std::min<long>(every, max_iters - done_iters);
+    if (mixed && p->iters_launched == 0) window = 1;  // re-anchor after the t_0 = d step
+    for (long k = 0; k < window; ++k) {
+      cudaError_t e = enqueue_iteration(p, st, p->prof_on ? &p->ev[6 * k] : nullptr);
+      if (e) return cuda_fail(p, e, "iteration");
     }
-    if (rs != DM_OK) break;
-    launched += every;
+    done_iters += window;
+    p->iters_launched += window;
+    p->since_anchor += (int)window;
     cudaError_t e = cudaMemcpyAsync(hs.data(), p->state, sizeof(SolveState) * p->batch, cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaStreamSynchronize(st);
-    if (e) { rs = cuda_fail(p, e, "poll state"); break; }
+    if (e) return cuda_fail(p, e, "poll state");
     if (p->prof_on) {
-      for (int k = 0; k < every; ++k) {
+      for (long k = 0; k < window; ++k) {
         float t[5];
         for (int j = 0; j < 5; ++j) cudaEventElapsedTime(&t[j], p->ev[6 * k + j], p->ev[6 * k + j + 1]);
         p->prof.ms_analysis += t[0];
@@ -173,15 +243,49 @@ dm_status run_dm(dm_plan *p, const double *d, double *s_out, cudaStream_t st) {
     }
     bool all = true;
     for (auto &s : hs) all = all && s.done;
-    if (all) break;
-    if (launched > cap) { rs = fail(p, DM_ENOTCONV, "iteration cap reached"); break; }
+    if (all) {
+      *all_done = 1;
+      break;
+    }
+    if (mixed && (p->iters_launched == 1 || p->since_anchor >= p->anchor_every)) {
+      dm_status r = anchor(p, st, false, nullptr, true);
+      if (r != DM_OK) return r;
+    }
+  }
+  return DM_OK;
+}
+
+// Final iterate into s_out (mixed: one last FP64 synthesis of a).
+dm_status solve_end(dm_plan *p, double *s_out, double *alm_out, cudaStream_t st, bool to_host) {
+  if (!p->session) return fail(p, DM_EINVAL, "no solve in progress (dm_solve_begin)");
+  if (p->prec != DM_FP64) {
+    dm_status r = anchor(p, st, false, nullptr, false);
+    if (r != DM_OK) return r;
+    p->anchor_active = false;
   }
   p->state_active = false;
-  if (rs == DM_OK && fp32) {
-    cudaError_t e = copy_s32_to_user(p, s_out, st);
-    if (e) rs = cuda_fail(p, e, "copy s");
+  p->session = false;
+  const cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (s_out) DM_CU(cudaMemcpyAsync(s_out, p->s64, sizeof(double) * 3 * p->npix * p->batch, kind, st), "copy s");
+  if (alm_out) DM_CU(cudaMemcpyAsync(alm_out, p->a, sizeof(double2) * 3 * p->nalm * p->batch, kind, st), "copy alm");
+  return DM_OK;
+}
+
+dm_status run_dm(dm_plan *p, const double *d, cudaStream_t st) {
+  dm_status r = solve_begin(p, d, st);
+  if (r != DM_OK) return r;
+  const dm_schedule &S = p->sched;
+  long cap = (long)S.max_iter + 4;
+  if (S.iters_per_level > 0 || !p->forced.empty()) {
+    long tot = 0;
+    for (int k = 0; k < S.n_levels; ++k) tot += p->forced.empty() ? S.iters_per_level : p->forced[k];
+    cap = tot + 4;
   }
-  return rs;
+  int all = 0;
+  r = solve_iterate(p, cap, &all, st);
+  if (r != DM_OK) return r;
+  if (!all) return fail(p, DM_ENOTCONV, "iteration cap reached");
+  return DM_OK;
 }
 
 void fill_stats(dm_plan *p, dm_stats *stats, dm_status *rs) {
@@ -247,6 +351,8 @@ dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out) {
   if ((e = dalloc(p, &p->tmpalm, (size_t)B * 3 * p->nalm))) return bad(e, "alloc tmp");
   if ((e = dalloc(p, &p->seeds_dev, (size_t)B))) return bad(e, "alloc seeds");
   if ((e = dalloc(p, &p->coef_tmp, 4 * (size_t)(lmax + 1)))) return bad(e, "alloc coef");
+  if ((e = dalloc(p, &p->s64, (size_t)B * n3))) return bad(e, "alloc s");
+  if ((e = dalloc(p, &p->rhi, (size_t)B * n3))) return bad(e, "alloc rhi");
   cudaMemset(p->rc, 0, sizeof(double2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
   cudaMemset(p->mask, 1, p->npix);
   dm_status s = upload_levels(p);
@@ -360,11 +466,10 @@ dm_status dm_wiener_filter(dm_plan *p, const double *d, double *s_out, double *a
   if (r != DM_OK) return r;
   if (!d || !s_out) return fail(p, DM_EINVAL, "null buffer");
   cudaStream_t st = (cudaStream_t)stream;
-  r = run_dm(p, d, s_out, st);
+  r = run_dm(p, d, st);
   if (r != DM_OK && r != DM_ENOTCONV) return r;
-  if (alm_out)
-    DM_CU(cudaMemcpyAsync(alm_out, p->a, sizeof(double2) * 3 * p->nalm * p->batch, cudaMemcpyDeviceToDevice, st),
-          "copy alm");
+  dm_status r2 = solve_end(p, s_out, alm_out, st, false);
+  if (r2 != DM_OK) return r2;
   DM_CU(cudaStreamSynchronize(st), "sync");
   fill_stats(p, stats, &r);
   return r;
@@ -377,14 +482,12 @@ dm_status dm_wiener_filter_host(dm_plan *p, const double *d_host, double *s_host
   if (!d_host || !s_host) return fail(p, DM_EINVAL, "null buffer");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t mb = sizeof(double) * 3 * p->npix * p->batch;
-  // tmpmap2 holds d, tmpmap receives s
+  // tmpmap2 holds d
   DM_CU(cudaMemcpyAsync(p->tmpmap2, d_host, mb, cudaMemcpyHostToDevice, st), "h2d");
-  r = run_dm(p, p->tmpmap2, p->tmpmap, st);
+  r = run_dm(p, p->tmpmap2, st);
   if (r != DM_OK && r != DM_ENOTCONV) return r;
-  DM_CU(cudaMemcpyAsync(s_host, p->tmpmap, mb, cudaMemcpyDeviceToHost, st), "d2h");
-  if (alm_host)
-    DM_CU(cudaMemcpyAsync(alm_host, p->a, sizeof(double2) * 3 * p->nalm * p->batch, cudaMemcpyDeviceToHost, st),
-          "d2h alm");
+  dm_status r2 = solve_end(p, s_host, alm_host, st, true);
+  if (r2 != DM_OK) return r2;
   DM_CU(cudaStreamSynchronize(st), "sync");
   fill_stats(p, stats, &r);
   return r;
@@ -424,14 +527,12 @@ dm_status dm_constrained_realization(dm_plan *p, const double *d, const uint64_t
   DM_CU(draw_noise_add(p, p->seeds_dev, p->tmpmap, p->tmpmap2, st), "draw noise");
   DM_CU(axpy_maps(n, p->tmpmap2, -2.0, p->tmpmap2, st), "negate");   // -dhat
   DM_CU(axpy_maps(n, d, 1.0, p->tmpmap2, st), "d - dhat");
-  r = run_dm(p, p->tmpmap2, s_cr_out, st);
+  r = run_dm(p, p->tmpmap2, st);
   if (r != DM_OK && r != DM_ENOTCONV) return r;
+  dm_status r2 = solve_end(p, s_cr_out, alm_cr_out, st, false);
+  if (r2 != DM_OK) return r2;
   DM_CU(axpy_maps(n, p->tmpmap, 1.0, s_cr_out, st), "+ shat");
-  if (alm_cr_out) {
-    DM_CU(cudaMemcpyAsync(alm_cr_out, p->a, sizeof(double2) * 3 * p->nalm * p->batch, cudaMemcpyDeviceToDevice, st),
-          "copy alm");
-    DM_CU(axpy_maps(6 * p->nalm * p->batch, (const double *)p->tmpalm, 1.0, alm_cr_out, st), "+ ahat");
-  }
+  if (alm_cr_out) DM_CU(axpy_maps(6 * p->nalm * p->batch, (const double *)p->tmpalm, 1.0, alm_cr_out, st), "+ ahat");
   DM_CU(cudaStreamSynchronize(st), "sync");
   fill_stats(p, stats, &r);
   return r;
@@ -492,6 +593,36 @@ dm_status dm_apply_filter(dm_plan *p, double lambda, const double *alm_in, doubl
   cudaStream_t st = (cudaStream_t)stream;
   DM_CU(build_filter_one(p, lambda, p->coef_tmp, st), "filter");
   DM_CU(apply_filter_level(p, p->coef_tmp, (const double2 *)alm_in, (double2 *)alm_out, st), "apply filter");
+  return DM_OK;
+}
+
+dm_status dm_solve_begin(dm_plan *p, const double *d, void *stream) {
+  dm_status r = check_ready(p);
+  if (r != DM_OK) return r;
+  if (!d) return fail(p, DM_EINVAL, "null buffer");
+  if (p->session) return fail(p, DM_EBUSY, "a solve is already in progress on this plan");
+  return solve_begin(p, d, (cudaStream_t)stream);
+}
+
+dm_status dm_solve_iterate(dm_plan *p, int max_iters, int *all_done, void *stream) {
+  if (!p || max_iters < 0) return DM_EINVAL;
+  int dummy = 0;
+  return solve_iterate(p, max_iters, all_done ? all_done : &dummy, (cudaStream_t)stream);
+}
+
+dm_status dm_solve_end(dm_plan *p, double *s_out, double *alm_out, dm_stats *stats, void *stream) {
+  if (!p) return DM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  dm_status r = solve_end(p, s_out, alm_out, st, false);
+  if (r != DM_OK) return r;
+  DM_CU(cudaStreamSynchronize(st), "sync");
+  fill_stats(p, stats, &r);
+  return r;
+}
+
+dm_status dm_set_refinement(dm_plan *p, int anchor_every) {
+  if (!p || anchor_every < 1) return DM_EINVAL;
+  p->anchor_every = anchor_every;
   return DM_OK;
 }
 

@@ -117,10 +117,47 @@ __global__ void k_wd32(const double *__restrict__ d, const double *__restrict__ 
 }
 
 cudaError_t prepare_wd(dm_plan *p, const double *d, cudaStream_t st) {
-  if (p->prec == DM_FP64)
-    k_wd<<<2048, 256, 0, st>>>(d, p->w, p->wd, 3 * p->npix, p->batch);
-  else
-    k_wd32<<<2048, 256, 0, st>>>(d, p->w, p->w32, p->wd32, 3 * p->npix, p->batch);
+  k_wd<<<2048, 256, 0, st>>>(d, p->w, p->wd, 3 * p->npix, p->batch);
+  if (p->prec != DM_FP64) k_wd32<<<2048, 256, 0, st>>>(d, p->w, p->w32, p->wd32, 3 * p->npix, p->batch);
+  return cudaGetLastError();
+}
+
+__global__ void k_anchor_resid(const double *__restrict__ d, const double *__restrict__ s_hi,
+                               const double *__restrict__ w, double *__restrict__ r, float *__restrict__ shi32,
+                               int64_t n3, int batch) {
+  int64_t total = n3 * batch;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ww = w[i % n3];
+    if (s_hi == nullptr) {  // t_0 - s_0 = d on observed pixels (Algorithm 1 initial guess)
+      r[i] = (ww > 0.0) ? d[i] : 0.0;
+      shi32[i] = 0.0f;
+    } else {
+      const double sh = s_hi[i];
+      r[i] = (ww > 0.0) ? ww * (d[i] - sh) : 0.0;
+      shi32[i] = (float)sh;
+    }
+  }
+}
+
+cudaError_t anchor_residual(dm_plan *p, const double *d, const double *s_hi, cudaStream_t st) {
+  k_anchor_resid<<<2048, 256, 0, st>>>(d, s_hi, p->w, p->rhi, p->shi32, 3 * p->npix, p->batch);
+  return cudaGetLastError();
+}
+
+// r = w d - w s_hi from the stored w d (FP64), shi32 = s_hi in FP32
+__global__ void k_anchor_resid_wd(const double *__restrict__ wd, const double *__restrict__ s_hi,
+                                  const double *__restrict__ w, double *__restrict__ r, float *__restrict__ shi32,
+                                  int64_t n3, int batch) {
+  int64_t total = n3 * batch;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const double sh = s_hi[i];
+    r[i] = wd[i] - w[i % n3] * sh;
+    shi32[i] = (float)sh;
+  }
+}
+
+cudaError_t anchor_residual_wd(dm_plan *p, const double *s_hi, cudaStream_t st) {
+  k_anchor_resid_wd<<<2048, 256, 0, st>>>(p->wd, s_hi, p->w, p->rhi, p->shi32, 3 * p->npix, p->batch);
   return cudaGetLastError();
 }
 

@@ -123,6 +123,19 @@ struct dm_plan {
   float *w32 = nullptr;         // [3][npix]
   float *wd32 = nullptr;        // [B][3][npix]
   float2 *phase32 = nullptr, *bhat32 = nullptr, *twid32 = nullptr;
+  // FP64 anchor of the mixed iteration (iterative refinement):
+  //   a = a_hi + e;  FP32 stages act on e only; g_hi = A W (d - Y a_hi) in FP64
+  double2 *a_hi = nullptr;      // [B][3][nalm]
+  double2 *g_hi = nullptr;      // [B][3][nalm]
+  float *shi32 = nullptr;       // [B][3][npix] Y a_hi rounded to FP32 (for ||s||)
+  bool anchor_active = false;
+  int anchor_every = 256;
+  // solve session (dm_solve_begin / iterate / end)
+  double *s64 = nullptr;        // [B][3][npix] FP64 iterate s (FP64 mode) / Y a_hi (mixed)
+  double *rhi = nullptr;        // [B][3][npix] FP64 anchor residual w (d - Y a_hi)
+  bool session = false;
+  int since_anchor = 0;
+  int64_t iters_launched = 0;
   int64_t bh_total = 0, ph_total = 0;
   // measurement
   bool prof_on = false;
@@ -159,6 +172,10 @@ cudaError_t control_step(dm_plan *p, cudaStream_t st);
 cudaError_t prepare_wd(dm_plan *p, const double *d, cudaStream_t st);
 cudaError_t setup_fp32(dm_plan *p);                          // tables and buffers of DM_MIXED_FP32
 cudaError_t copy_s32_to_user(dm_plan *p, double *s_out, cudaStream_t st);
+// anchor residual: r = w (d - s_hi) (or d on observed pixels when s_hi == nullptr),
+// written to p->wd; shi32 = s_hi in FP32
+cudaError_t anchor_residual(dm_plan *p, const double *d, const double *s_hi, cudaStream_t st);
+cudaError_t anchor_residual_wd(dm_plan *p, const double *s_hi, cudaStream_t st);  // r = wd - w s_hi
 
 // constrained realisations
 cudaError_t draw_signal(dm_plan *p, const uint64_t *seeds_dev, double2 *ahat, cudaStream_t st);

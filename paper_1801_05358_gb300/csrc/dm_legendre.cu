@@ -401,6 +401,7 @@ cudaError_t gen_tables32(dm_plan *p) {
 template <int NB>
 __global__ void __launch_bounds__(SYN_THREADS) k_leg_syn32(const float *__restrict__ ptab,
                                                            const double2 *__restrict__ alm,
+                                                           const double2 *__restrict__ a_sub,
                                                            float2 *__restrict__ rc, int lmax, int mmax, int npairs,
                                                            int64_t nalm, const SolveState *__restrict__ state) {
   __shared__ float2 sT[NB][SYN_CH], sE[NB][SYN_CH], sB[NB][SYN_CH];
@@ -425,7 +426,12 @@ __global__ void __launch_bounds__(SYN_THREADS) k_leg_syn32(const float *__restri
     for (int i = threadIdx.x; i < cnt * NB; i += SYN_THREADS) {
       const int k = i / cnt, j = i % cnt;
       const int64_t ob = (int64_t)(b0 + k) * 3 * nalm + base + lc + j;
-      const double2 t = alm[ob], e = alm[ob + nalm], bb = alm[ob + 2 * nalm];
+      double2 t = alm[ob], e = alm[ob + nalm], bb = alm[ob + 2 * nalm];
+      if (a_sub != nullptr) {  // correction e = a - a_hi (FP64 difference, then FP32)
+        t = csub(t, a_sub[ob]);
+        e = csub(e, a_sub[ob + nalm]);
+        bb = csub(bb, a_sub[ob + 2 * nalm]);
+      }
       sT[k][j] = make_float2((float)t.x, (float)t.y);
       sE[k][j] = make_float2((float)-e.x, (float)-e.y);
       sB[k][j] = make_float2((float)-bb.x, (float)-bb.y);
@@ -576,7 +582,7 @@ __global__ void __launch_bounds__(ANA_P) k_leg_ana32(const float *__restrict__ p
 // chunk sum in FP64, then the FP64 harmonic step and filter
 __global__ void k_ana_reduce32(const float2 *__restrict__ apart, double2 *out, int lmax, int64_t nalm, int nchunk,
                                double omega, int epilogue, const double *__restrict__ filt,
-                               const SolveState *__restrict__ state) {
+                               const SolveState *__restrict__ state, const double2 *__restrict__ g_add) {
   const int b = blockIdx.y, m = blockIdx.z;
   if (state != nullptr && state[b].done) return;
   const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
@@ -599,6 +605,12 @@ __global__ void k_ana_reduce32(const float2 *__restrict__ apart, double2 *out, i
     o[2 * nalm] = acc[2];
     return;
   }
+  if (g_add != nullptr) {  // anchor term A W (d - Y a_hi), FP64
+    const double2 *g = g_add + (int64_t)b * 3 * nalm + i;
+    acc[0] = cadd(acc[0], g[0]);
+    acc[1] = cadd(acc[1], g[nalm]);
+    acc[2] = cadd(acc[2], g[2 * nalm]);
+  }
   const double *c = filt + ((int64_t)state[b].level * (lmax + 1) + l) * 4;
   double2 t = cadd(o[0], acc[0]), e = cadd(o[nalm], acc[1]), bb = cadd(o[2 * nalm], acc[2]);
   o[0] = make_double2(c[0] * t.x + c[1] * e.x, c[0] * t.y + c[1] * e.y);
@@ -611,10 +623,12 @@ cudaError_t legendre_synthesis32(dm_plan *p, const double2 *alm, cudaStream_t st
   const int pb = (p->npairs + SYN_THREADS - 1) / SYN_THREADS;
   if (p->batch % 4 == 0) {
     dim3 g(p->batch / 4, pb, p->mmax + 1);
-    k_leg_syn32<4><<<g, SYN_THREADS, 0, st>>>(p->ptab, alm, p->rc32, p->lmax, p->mmax, p->npairs, p->nalm, stp);
+    k_leg_syn32<4><<<g, SYN_THREADS, 0, st>>>(p->ptab, alm, p->anchor_active ? p->a_hi : nullptr, p->rc32, p->lmax,
+                                              p->mmax, p->npairs, p->nalm, stp);
   } else {
     dim3 g(p->batch, pb, p->mmax + 1);
-    k_leg_syn32<1><<<g, SYN_THREADS, 0, st>>>(p->ptab, alm, p->rc32, p->lmax, p->mmax, p->npairs, p->nalm, stp);
+    k_leg_syn32<1><<<g, SYN_THREADS, 0, st>>>(p->ptab, alm, p->anchor_active ? p->a_hi : nullptr, p->rc32, p->lmax,
+                                              p->mmax, p->npairs, p->nalm, stp);
   }
   return cudaGetLastError();
 }
@@ -634,7 +648,8 @@ cudaError_t legendre_analysis32(dm_plan *p, int epilogue, double2 *out, cudaStre
   double omega = 4.0 * M_PI / (double)p->npix;
   dim3 g2((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
   k_ana_reduce32<<<g2, 128, 0, st>>>(p->apart32, out, p->lmax, p->nalm, p->nchunk, omega, epilogue, p->filt,
-                                     epilogue == ANA_DM_STEP ? p->state : stp);
+                                     epilogue == ANA_DM_STEP ? p->state : stp,
+                                     (p->anchor_active && epilogue == ANA_DM_STEP) ? p->g_hi : nullptr);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(256) k_ring(const RingDev *__restrict__ rings,
                                               C *__restrict__ rc, int mmax, int npairs, int64_t npix, int nrings,
                                               const double *__restrict__ in_map, double *__restrict__ out_user,
                                               R *s_state, const R *__restrict__ w, const R *__restrict__ wd,
-                                              double *__restrict__ norms, const SolveState *__restrict__ state) {
+                                              double *__restrict__ norms, const SolveState *__restrict__ state,
+                                              const R *__restrict__ s_anchor) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C *sm = reinterpret_cast<C *>(sm_raw);
   const int r = blockIdx.x, f = blockIdx.y, b = blockIdx.z;
@@ -83,6 +84,8 @@ __global__ void __launch_bounds__(256) k_ring(const RingDev *__restrict__ rings,
       return;
     }
     // RING_ITER: Cauchy partials (FP64), store s, form t - s = w d - w s and pack it.
+    // With an anchor (mixed precision) the state is Y e, s = s_anchor + Y e, and
+    // the data part w (d - s_anchor) is carried in FP64 by the anchor: r = -w Y e.
     double dd = 0.0, ss = 0.0;
     const int64_t wo = (int64_t)f * npix + Rg.start;
     for (int j = threadIdx.x; j < h; j += blockDim.x) {
@@ -91,12 +94,20 @@ __global__ void __launch_bounds__(256) k_ring(const RingDev *__restrict__ rings,
       R o0 = s_state[moff + 2 * j], o1 = s_state[moff + 2 * j + 1];
       double d0 = (double)s0 - (double)o0, d1 = (double)s1 - (double)o1;
       dd += d0 * d0 + d1 * d1;
-      ss += (double)s0 * (double)s0 + (double)s1 * (double)s1;
       s_state[moff + 2 * j] = s0;
       s_state[moff + 2 * j + 1] = s1;
       C rr;
-      rr.x = wd[moff + 2 * j] - w[wo + 2 * j] * s0;
-      rr.y = wd[moff + 2 * j + 1] - w[wo + 2 * j + 1] * s1;
+      if (s_anchor != nullptr) {
+        const double f0 = (double)s_anchor[moff + 2 * j] + (double)s0;
+        const double f1 = (double)s_anchor[moff + 2 * j + 1] + (double)s1;
+        ss += f0 * f0 + f1 * f1;
+        rr.x = -w[wo + 2 * j] * s0;
+        rr.y = -w[wo + 2 * j + 1] * s1;
+      } else {
+        ss += (double)s0 * (double)s0 + (double)s1 * (double)s1;
+        rr.x = wd[moff + 2 * j] - w[wo + 2 * j] * s0;
+        rr.y = wd[moff + 2 * j + 1] - w[wo + 2 * j + 1] * s1;
+      }
       buf[j] = rr;
     }
     // block reduction of (dd, ss)
@@ -161,13 +172,14 @@ __global__ void __launch_bounds__(256) k_ring(const RingDev *__restrict__ rings,
 template <typename R, typename C, int MODE>
 static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const C *twid, C *rc,
                                const double *in_map, double *out_user, R *s_state, const R *w, const R *wd,
-                               cudaStream_t st) {
+                               cudaStream_t st, const R *s_anchor = nullptr) {
   dim3 grid(p->nrings, 3, p->batch);
   size_t smem = sizeof(C) * (2 * (size_t)p->fft_M_max + 1);
   const SolveState *stp = (MODE == RING_ITER || MODE == RING_INIT) ? p->state : nullptr;
   cudaFuncSetAttribute(k_ring<R, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_ring<R, C, MODE><<<grid, 256, smem, st>>>(p->rings, phase, bhat, twid, p->fft_M_max, rc, p->mmax, p->npairs,
-                                              p->npix, p->nrings, in_map, out_user, s_state, w, wd, p->norms, stp);
+                                              p->npix, p->nrings, in_map, out_user, s_state, w, wd, p->norms, stp,
+                                              s_anchor);
   return cudaGetLastError();
 }
 
@@ -199,7 +211,8 @@ cudaError_t ring_stage(dm_plan *p, int mode, const double *in_map, double *out_m
                                                         out_map, nullptr, p->w32, p->wd32, st);
       case RING_ITER:
         return launch_ring<float, float2, RING_ITER>(p, p->phase32, p->bhat32, p->twid32, p->rc32, nullptr,
-                                                     nullptr, p->s32, p->w32, p->wd32, st);
+                                                     nullptr, p->s32, p->w32, p->wd32, st,
+                                                     p->anchor_active ? p->shi32 : nullptr);
       case RING_INIT:
         return launch_ring<float, float2, RING_INIT>(p, p->phase32, p->bhat32, p->twid32, p->rc32, in_map,
                                                      nullptr, nullptr, p->w32, p->wd32, st);

@@ -24,7 +24,8 @@ EXPORTS = [
     "dm_set_noise_mask", "dm_set_schedule", "dm_set_forced_iters", "dm_wiener_filter", "dm_wiener_filter_host",
     "dm_constrained_realization", "dm_draw_cr_inputs", "dm_alm2map", "dm_map2alm", "dm_ring_fft_forward",
     "dm_ring_fft_inverse", "dm_legendre_synthesis", "dm_legendre_analysis", "dm_apply_filter", "dm_noise_info",
-    "dm_profile_enable", "dm_profile_read", "dm_measure_alu_peaks",
+    "dm_profile_enable", "dm_profile_read", "dm_measure_alu_peaks", "dm_solve_begin", "dm_solve_iterate",
+    "dm_solve_end", "dm_set_refinement",
 ]
 
 
@@ -42,7 +43,7 @@ class DmStats(ctypes.Structure):
 class DmProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("iterations", ctypes.c_int64), ("ms_analysis", ctypes.c_double),
                 ("ms_reduce", ctypes.c_double), ("ms_synthesis", ctypes.c_double), ("ms_ring", ctypes.c_double),
-                ("ms_control", ctypes.c_double)]
+                ("ms_control", ctypes.c_double), ("anchors", ctypes.c_int64), ("ms_anchor", ctypes.c_double)]
 
 
 class DmError(RuntimeError):
@@ -85,6 +86,10 @@ def lib():
         L.dm_noise_info.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.dm_profile_enable.argtypes = [vp, ctypes.c_int]
         L.dm_profile_read.argtypes = [vp, ctypes.POINTER(DmProfile)]
+        L.dm_solve_begin.argtypes = [vp, vp, vp]
+        L.dm_solve_iterate.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
+        L.dm_solve_end.argtypes = [vp, vp, vp, vp, vp]
+        L.dm_set_refinement.argtypes = [vp, ctypes.c_int]
         L.dm_measure_alu_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
@@ -199,6 +204,23 @@ class Plan:
         st = lib().dm_wiener_filter(self.h, _ptr(d), _ptr(s_out), _ptr(alm_out), stats, _stream(stream))
         self._check(st, allow=(DM_ENOTCONV,))
         return st, self._stats_out(stats)
+
+    def solve_begin(self, d, stream=None):
+        self._check(lib().dm_solve_begin(self.h, _ptr(d), _stream(stream)))
+
+    def solve_iterate(self, max_iters, stream=None):
+        done = ctypes.c_int(0)
+        self._check(lib().dm_solve_iterate(self.h, int(max_iters), ctypes.byref(done), _stream(stream)))
+        return bool(done.value)
+
+    def solve_end(self, s_out=None, alm_out=None, stream=None):
+        stats = (DmStats * self.batch)()
+        st = lib().dm_solve_end(self.h, _ptr(s_out), _ptr(alm_out), stats, _stream(stream))
+        self._check(st, allow=(DM_ENOTCONV,))
+        return st, self._stats_out(stats)
+
+    def set_refinement(self, anchor_every):
+        self._check(lib().dm_set_refinement(self.h, int(anchor_every)))
 
     def wiener_filter_host(self, d_host, s_host, alm_host=None, stream=None):
         stats = (DmStats * self.batch)()

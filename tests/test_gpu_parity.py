@@ -192,3 +192,26 @@ def test_constrained_realization(orc):
     s = torch.zeros((1, 3, wl.npix), dtype=torch.float64, device="cuda")
     p.constrained_realization(dev(d), [99], s)
     assert rel(s.cpu().numpy()[0], ref["s_cr"]) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [dmwf.DM_FP64, dmwf.DM_MIXED_FP32])
+def test_session_api_equals_one_call(orc, prec):
+    """dm_solve_begin + dm_solve_iterate in pieces + dm_solve_end gives the same
+    iterate as dm_wiener_filter (the pieces are the same device work)."""
+    wl = W.make_workload("nside16", [2], nside=8, lmax=16)
+    d = _data(orc, wl)
+    p = make_plan(wl, 1, lambda0=100.0, n_levels=3, iters_per_level=6, check_every=4)
+    p.set_precision(prec)
+    s1 = torch.zeros((1, 3, wl.npix), dtype=torch.float64, device="cuda")
+    p.wiener_filter(dev(d), s1)
+    s2 = torch.zeros_like(s1)
+    p.solve_begin(dev(d))
+    done = False
+    for chunk in [1, 3, 5, 100]:
+        done = p.solve_iterate(chunk)
+        if done:
+            break
+    assert done
+    st, stats = p.solve_end(s2)
+    assert stats[0]["iters_total"] == 18
+    assert rel(s2.cpu().numpy(), s1.cpu().numpy()) < (1e-15 if prec == dmwf.DM_FP64 else 1e-12)
