@@ -124,6 +124,11 @@ dm_status dm_set_spectra(dm_plan *plan, const double *cl);
  * Omega and w = alpha / sigma^2 on the device. */
 dm_status dm_set_noise_mask(dm_plan *plan, const double *sigma, const uint8_t *mask);
 
+/* Noise and mask of one RHS b (same layout as dm_set_noise_mask), after the
+ * plan-wide call; alpha, T_h, w and the per-level filters of that RHS follow
+ * it.  DM_EBUSY while a solve is in progress. */
+dm_status dm_set_noise_mask_rhs(dm_plan *plan, int b, const double *sigma, const uint8_t *mask);
+
 /* Schedule (defaults: lambda0 1000, 10 levels, 10 iterations per level). */
 dm_status dm_set_schedule(dm_plan *plan, const dm_schedule *sched);
 
@@ -209,7 +214,7 @@ dm_status dm_legendre_analysis(dm_plan *plan, const double *rc, double *alm, voi
 /* Per-l filter of level lambda (Eq. 8): alm_out = F alm_in with
  * F = V diag(f_e) V^T, f_e = max(S_e, mu)/(max(S_e, mu) + T_h), mu = (lambda-1) T_h. */
 dm_status dm_apply_filter(dm_plan *plan, double lambda, const double *alm_in, double *alm_out, void *stream);
-/* alpha and T_h of the current noise model (host outputs). */
+/* alpha and T_h of the noise model of RHS 0 (host outputs). */
 dm_status dm_noise_info(const dm_plan *plan, double *alpha, double *t_h);
 
 /* --- measurement --------------------------------------------------------- */
@@ -237,6 +242,70 @@ dm_status dm_profile_read(const dm_plan *plan, dm_profile *out);
  * The paper has no counterpart; it is the peak the FP64 Legendre stage is
  * compared against. */
 dm_status dm_measure_alu_peaks(double *fp64_tflops, double *fp32_tflops);
+
+/* --- serving: continuous batching of requests of different geometries ---- */
+
+/* A server keeps one plan ("pool") per (nside, lmax, spectra) whose RHS are
+ * slots.  A worker thread admits queued requests into free slots, or into a new
+ * pool while the device-memory budget allows (idle pools are released to make
+ * room), sets each slot up alone (its noise, mask, tolerance, data and, for a
+ * constrained realisation, its Philox draws), then advances every pool with
+ * busy slots by iters_per_round iterations on the pool's own stream so pools
+ * overlap on the device, and retires converged slots into the caller's buffer.
+ * A request's messenger state stays on the device from admission to
+ * retirement, and its result does not depend on the other requests sharing the
+ * device. */
+typedef struct dm_server dm_server;
+
+typedef enum { DM_REQ_WF = 0, DM_REQ_CR = 1 } dm_request_kind;
+
+typedef struct {
+  size_t hbm_budget_bytes;   /* device memory the pools may reserve */
+  int slots_per_plan;        /* RHS slots per pool (1..1024) */
+  int iters_per_round;       /* iterations between admissions (>= 1) */
+  dm_precision prec;         /* arithmetic of every pool */
+  dm_schedule sched;         /* cooling schedule (eps_final is per request) */
+  int anchor_every;          /* mixed-precision refinement period (0 = 256) */
+  int max_pending;           /* queue bound; dm_serve_submit returns DM_EBUSY beyond it (0 = 100000) */
+} dm_server_config;
+
+typedef struct {
+  int nside, lmax;           /* geometry, 1 <= nside <= 1024, 2 <= lmax <= 4 nside */
+  int kind;                  /* dm_request_kind */
+  double tol;                /* final Cauchy threshold eps_final */
+  uint64_t seed;             /* Philox key of the constrained-realisation draws */
+  const double *cl;          /* host [4][lmax+1], copied at submit */
+  const double *sigma;       /* host [3][npix], copied at submit */
+  const uint8_t *mask;       /* host [npix] or NULL, copied at submit */
+  const double *d;           /* host [3][npix], copied at submit */
+  double *s_out;             /* host [3][npix]: written before the ticket completes; must stay valid until then */
+} dm_request;
+
+typedef struct {
+  dm_status status;          /* DM_OK, DM_ENOTCONV, DM_ENOMEM (never fits), DM_EAGAIN (cancelled), ... */
+  int iters;                 /* dual messenger iterations run */
+  double cauchy_final;
+  double latency_ms;         /* submit to completion (host wall clock) */
+  double queue_ms;           /* submit to admission */
+} dm_result;
+
+typedef struct {
+  int64_t pending, busy_slots, pools, bytes_reserved, rounds, admitted, retired;
+} dm_server_info_t;
+
+dm_status dm_server_create(const dm_server_config *cfg, dm_server **out);
+/* Queue a request; *ticket identifies it.  DM_EINVAL for a bad request,
+ * DM_EBUSY when the queue is full. */
+dm_status dm_serve_submit(dm_server *srv, const dm_request *req, uint64_t *ticket);
+/* DM_OK and *out once the request completed (the ticket is then released),
+ * DM_EAGAIN while it is queued or running, DM_EINVAL for an unknown ticket. */
+dm_status dm_serve_poll(dm_server *srv, uint64_t ticket, dm_result *out);
+/* Remove a request that is still queued (its result reports DM_EAGAIN);
+ * DM_EBUSY once admitted. */
+dm_status dm_serve_cancel(dm_server *srv, uint64_t ticket);
+dm_status dm_server_info(dm_server *srv, dm_server_info_t *out);
+/* Completes every queued and running request, then frees the pools. */
+void dm_server_destroy(dm_server *srv);
 
 #ifdef __cplusplus
 }

@@ -62,39 +62,53 @@ void default_schedule(dm_schedule *s) {
   s->check_every = 8;
 }
 
-// Host copy of the level table; the device copy drives k_control_step.
+}  // namespace
+
+namespace dmwf {
+// Host copy of the level tables (one per RHS); the device copies drive
+// k_control_step.
 dm_status upload_levels(dm_plan *p) {
   const dm_schedule &s = p->sched;
-  LevelDev L{};
-  L.n_levels = s.n_levels;
-  L.max_iter = s.max_iter;
   p->lambdas.assign(s.n_levels, 1.0);
-  for (int k = 0; k < s.n_levels; ++k) {
+  for (int k = 0; k < s.n_levels; ++k)
     p->lambdas[k] = (s.n_levels == 1) ? 1.0 : pow(s.lambda0, 1.0 - (double)k / (double)(s.n_levels - 1));
-    double e;
-    if (s.eta > 0.0)
-      e = std::max(s.eps_final, s.eps0 * pow(s.eta, -(double)k));
-    else
-      e = (s.n_levels == 1) ? s.eps_final
-                            : s.eps0 * pow(s.eps_final / s.eps0, (double)k / (double)(s.n_levels - 1));
-    L.eps[k] = e;
-  }
   p->lambdas[s.n_levels - 1] = 1.0;
-  L.eps[s.n_levels - 1] = s.eps_final;
-  if (!p->forced.empty()) {
-    L.forced = 1;
-    for (int k = 0; k < s.n_levels; ++k) L.fixed_iters[k] = p->forced[k];
-  } else if (s.iters_per_level > 0) {
-    L.forced = 1;
-    for (int k = 0; k < s.n_levels; ++k) L.fixed_iters[k] = s.iters_per_level;
+  if ((int)p->eps_final_rhs.size() != p->batch) p->eps_final_rhs.assign(p->batch, s.eps_final);
+  std::vector<LevelDev> Ls(p->batch);
+  for (int b = 0; b < p->batch; ++b) {
+    LevelDev &L = Ls[b];
+    L = LevelDev{};
+    L.n_levels = s.n_levels;
+    L.max_iter = s.max_iter;
+    const double ef = p->eps_final_rhs[b];
+    for (int k = 0; k < s.n_levels; ++k) {
+      double e;
+      if (s.eta > 0.0)
+        e = std::max(ef, s.eps0 * pow(s.eta, -(double)k));
+      else
+        e = (s.n_levels == 1) ? ef : s.eps0 * pow(ef / s.eps0, (double)k / (double)(s.n_levels - 1));
+      L.eps[k] = e;
+    }
+    L.eps[s.n_levels - 1] = ef;
+    if (!p->forced.empty()) {
+      L.forced = 1;
+      for (int k = 0; k < s.n_levels; ++k) L.fixed_iters[k] = p->forced[k];
+    } else if (s.iters_per_level > 0) {
+      L.forced = 1;
+      for (int k = 0; k < s.n_levels; ++k) L.fixed_iters[k] = s.iters_per_level;
+    }
   }
-  DM_CU(cudaMemcpy(p->lev, &L, sizeof(LevelDev), cudaMemcpyHostToDevice), "upload levels");
+  DM_CU(cudaMemcpy(p->lev, Ls.data(), sizeof(LevelDev) * p->batch, cudaMemcpyHostToDevice), "upload levels");
   return DM_OK;
 }
 
+}  // namespace dmwf
+
+namespace {
+
 dm_status refresh_filters(dm_plan *p) {
   if (!p->have_cl || !p->have_noise) return DM_OK;
-  DM_CU(build_filters(p, 0), "build filters");
+  for (int b = 0; b < p->batch; ++b) DM_CU(build_filters(p, b, 0), "build filters");
   DM_CU(cudaDeviceSynchronize(), "build filters");
   return DM_OK;
 }
@@ -105,6 +119,10 @@ dm_status check_ready(dm_plan *p) {
   if (!p->have_noise) return fail(p, DM_EINVAL, "noise not set (dm_set_noise_mask)");
   return DM_OK;
 }
+
+}  // namespace
+
+namespace dmwf {
 
 // The iteration driver.  Device stages per iteration:
 //   analysis + harmonic step  a <- F_k [a + A (t - s)]      (k_leg_ana + k_ana_reduce)
@@ -288,6 +306,10 @@ dm_status run_dm(dm_plan *p, const double *d, cudaStream_t st) {
   return DM_OK;
 }
 
+}  // namespace dmwf
+
+namespace {
+
 void fill_stats(dm_plan *p, dm_stats *stats, dm_status *rs) {
   std::vector<SolveState> hs(p->batch);
   cudaMemcpy(hs.data(), p->state, sizeof(SolveState) * p->batch, cudaMemcpyDeviceToHost);
@@ -336,16 +358,18 @@ dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out) {
   if (e) return bad(e, "build tables");
   const int64_t B = batch, n3 = 3 * p->npix;
   if ((e = dalloc(p, &p->cl, 4 * (size_t)(lmax + 1)))) return bad(e, "alloc");
-  if ((e = dalloc(p, &p->w, n3))) return bad(e, "alloc");
-  if ((e = dalloc(p, &p->mask, p->npix))) return bad(e, "alloc");
-  if ((e = dalloc(p, &p->sigma, n3))) return bad(e, "alloc");
+  if ((e = dalloc(p, &p->w, (size_t)B * n3))) return bad(e, "alloc");
+  if ((e = dalloc(p, &p->mask, (size_t)B * p->npix))) return bad(e, "alloc");
+  if ((e = dalloc(p, &p->sigma, (size_t)B * n3))) return bad(e, "alloc");
+  p->alpha.assign(B, 0.0);
+  p->t_h.assign(B, 0.0);
   if ((e = dalloc(p, &p->rc, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return bad(e, "alloc rc");
   if ((e = dalloc(p, &p->a, (size_t)B * 3 * p->nalm))) return bad(e, "alloc a");
   if ((e = dalloc(p, &p->apart, (size_t)B * p->nchunk * 3 * p->nalm))) return bad(e, "alloc apart");
   if ((e = dalloc(p, &p->wd, (size_t)B * n3))) return bad(e, "alloc wd");
   if ((e = dalloc(p, &p->norms, (size_t)B * 3 * p->nrings * 2))) return bad(e, "alloc norms");
   if ((e = dalloc(p, &p->state, (size_t)B))) return bad(e, "alloc state");
-  if ((e = dalloc(p, &p->lev, 1))) return bad(e, "alloc lev");
+  if ((e = dalloc(p, &p->lev, (size_t)B))) return bad(e, "alloc lev");
   if ((e = dalloc(p, &p->tmpmap, (size_t)B * n3))) return bad(e, "alloc tmp");
   if ((e = dalloc(p, &p->tmpmap2, (size_t)B * n3))) return bad(e, "alloc tmp");
   if ((e = dalloc(p, &p->tmpalm, (size_t)B * 3 * p->nalm))) return bad(e, "alloc tmp");
@@ -354,7 +378,7 @@ dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out) {
   if ((e = dalloc(p, &p->s64, (size_t)B * n3))) return bad(e, "alloc s");
   if ((e = dalloc(p, &p->rhi, (size_t)B * n3))) return bad(e, "alloc rhi");
   cudaMemset(p->rc, 0, sizeof(double2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
-  cudaMemset(p->mask, 1, p->npix);
+  cudaMemset(p->mask, 1, (size_t)B * p->npix);
   dm_status s = upload_levels(p);
   if (s != DM_OK) {
     free_all(p);
@@ -408,8 +432,8 @@ dm_status dm_set_spectra(dm_plan *p, const double *cl) {
   return refresh_filters(p);
 }
 
-dm_status dm_set_noise_mask(dm_plan *p, const double *sigma, const uint8_t *mask) {
-  if (!p || !sigma) return DM_EINVAL;
+namespace {
+dm_status check_noise(dm_plan *p, const double *sigma, const uint8_t *mask) {
   const int64_t np = p->npix;
   int64_t nobs = 0;
   for (int64_t i = 0; i < np; ++i) {
@@ -423,14 +447,52 @@ dm_status dm_set_noise_mask(dm_plan *p, const double *sigma, const uint8_t *mask
     }
   }
   if (nobs == 0) return fail(p, DM_EINVAL, "mask leaves no observed pixel");
-  DM_CU(cudaMemcpy(p->sigma, sigma, sizeof(double) * 3 * np, cudaMemcpyHostToDevice), "upload sigma");
+  return DM_OK;
+}
+
+dm_status upload_noise(dm_plan *p, int b, const double *sigma, const uint8_t *mask) {
+  const int64_t np = p->npix;
+  DM_CU(cudaMemcpy(p->sigma + (size_t)b * 3 * np, sigma, sizeof(double) * 3 * np, cudaMemcpyHostToDevice), "sigma");
   if (mask)
-    DM_CU(cudaMemcpy(p->mask, mask, np, cudaMemcpyHostToDevice), "upload mask");
+    DM_CU(cudaMemcpy(p->mask + (size_t)b * np, mask, np, cudaMemcpyHostToDevice), "mask");
   else
-    DM_CU(cudaMemset(p->mask, 1, np), "mask");
-  DM_CU(build_noise(p, 0), "noise");
+    DM_CU(cudaMemset(p->mask + (size_t)b * np, 1, np), "mask");
+  DM_CU(build_noise(p, b, 0), "noise");
+  return DM_OK;
+}
+}  // namespace
+
+dm_status dm_set_noise_mask(dm_plan *p, const double *sigma, const uint8_t *mask) {
+  if (!p || !sigma) return DM_EINVAL;
+  dm_status r = check_noise(p, sigma, mask);
+  if (r != DM_OK) return r;
+  r = upload_noise(p, 0, sigma, mask);
+  if (r != DM_OK) return r;
+  const int64_t np = p->npix;
+  for (int b = 1; b < p->batch; ++b) {  // every RHS gets the same noise model
+    DM_CU(cudaMemcpy(p->sigma + (size_t)b * 3 * np, p->sigma, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice), "sigma");
+    DM_CU(cudaMemcpy(p->mask + (size_t)b * np, p->mask, np, cudaMemcpyDeviceToDevice), "mask");
+    DM_CU(cudaMemcpy(p->w + (size_t)b * 3 * np, p->w, sizeof(double) * 3 * np, cudaMemcpyDeviceToDevice), "w");
+    p->alpha[b] = p->alpha[0];
+    p->t_h[b] = p->t_h[0];
+  }
   p->have_noise = true;
   return refresh_filters(p);
+}
+
+dm_status dm_set_noise_mask_rhs(dm_plan *p, int b, const double *sigma, const uint8_t *mask) {
+  if (!p || !sigma || b < 0 || b >= p->batch) return DM_EINVAL;
+  if (!p->have_noise) return fail(p, DM_EINVAL, "set the plan-wide noise first (dm_set_noise_mask)");
+  if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
+  dm_status r = check_noise(p, sigma, mask);
+  if (r != DM_OK) return r;
+  r = upload_noise(p, b, sigma, mask);
+  if (r != DM_OK) return r;
+  if (p->have_cl) {
+    DM_CU(build_filters(p, b, 0), "filters");
+    DM_CU(cudaDeviceSynchronize(), "filters");
+  }
+  return DM_OK;
 }
 
 dm_status dm_set_schedule(dm_plan *p, const dm_schedule *s) {
@@ -591,7 +653,7 @@ dm_status dm_apply_filter(dm_plan *p, double lambda, const double *alm_in, doubl
   if (!p->have_cl || !p->have_noise) return fail(p, DM_EINVAL, "spectra and noise must be set");
   if (!(lambda >= 1.0)) return fail(p, DM_EINVAL, "lambda must be >= 1");
   cudaStream_t st = (cudaStream_t)stream;
-  DM_CU(build_filter_one(p, lambda, p->coef_tmp, st), "filter");
+  DM_CU(build_filter_one(p, lambda, p->t_h[0], p->coef_tmp, st), "filter");
   DM_CU(apply_filter_level(p, p->coef_tmp, (const double2 *)alm_in, (double2 *)alm_out, st), "apply filter");
   return DM_OK;
 }
@@ -643,8 +705,8 @@ dm_status dm_profile_read(const dm_plan *p, dm_profile *out) {
 
 dm_status dm_noise_info(const dm_plan *p, double *alpha, double *t_h) {
   if (!p || !p->have_noise) return DM_EINVAL;
-  if (alpha) *alpha = p->alpha;
-  if (t_h) *t_h = p->t_h;
+  if (alpha) *alpha = p->alpha[0];
+  if (t_h) *t_h = p->t_h[0];
   return DM_OK;
 }
 

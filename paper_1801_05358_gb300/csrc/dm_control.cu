@@ -6,9 +6,10 @@
 namespace dmwf {
 
 // ----------------------------------------------------------------- control
-__global__ void k_control_init(SolveState *st, const LevelDev *lev, int batch) {
+__global__ void k_control_init(SolveState *st, const LevelDev *levs, int batch) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= batch) return;
+  const LevelDev *lev = levs + b;
   SolveState s;
   s.level = 0;
   s.iter_in_level = 0;
@@ -32,10 +33,11 @@ __global__ void k_control_init(SolveState *st, const LevelDev *lev, int batch) {
 // partials in a fixed order, then the stopping rule of Algorithm 1:
 // a level ends when the Cauchy ratio falls below eps_k (or after its fixed
 // count); the next level lowers xi (lambda) and the last level ends the run.
-__global__ void k_control_step(SolveState *st, const LevelDev *__restrict__ lev, const double *__restrict__ norms,
+__global__ void k_control_step(SolveState *st, const LevelDev *__restrict__ levs, const double *__restrict__ norms,
                                int nrings) {
   const int b = blockIdx.x;
   if (st[b].done) return;
+  const LevelDev *lev = levs + b;
   __shared__ double r0[256], r1[256];
   double dd = 0.0, ss = 0.0;
   const int n = 3 * nrings;
@@ -100,7 +102,7 @@ __global__ void k_wd(const double *__restrict__ d, const double *__restrict__ w,
                      int64_t n3, int batch) {
   int64_t total = n3 * batch;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    double ww = w[i % n3];
+    double ww = w[i];
     wd[i] = (ww > 0.0) ? ww * d[i] : 0.0;
   }
 }
@@ -110,9 +112,9 @@ __global__ void k_wd32(const double *__restrict__ d, const double *__restrict__ 
                        float *__restrict__ wd32, int64_t n3, int batch) {
   int64_t total = n3 * batch;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    double ww = w[i % n3];
+    double ww = w[i];
     wd32[i] = (ww > 0.0) ? (float)(ww * d[i]) : 0.0f;
-    if (i < n3) w32[i] = (float)ww;
+    w32[i] = (float)ww;
   }
 }
 
@@ -127,7 +129,7 @@ __global__ void k_anchor_resid(const double *__restrict__ d, const double *__res
                                int64_t n3, int batch) {
   int64_t total = n3 * batch;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const double ww = w[i % n3];
+    const double ww = w[i];
     if (s_hi == nullptr) {  // t_0 - s_0 = d on observed pixels (Algorithm 1 initial guess)
       r[i] = (ww > 0.0) ? d[i] : 0.0;
       shi32[i] = 0.0f;
@@ -151,7 +153,7 @@ __global__ void k_anchor_resid_wd(const double *__restrict__ wd, const double *_
   int64_t total = n3 * batch;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const double sh = s_hi[i];
-    r[i] = wd[i] - w[i % n3] * sh;
+    r[i] = wd[i] - w[i] * sh;
     shi32[i] = (float)sh;
   }
 }
@@ -250,12 +252,12 @@ __global__ void k_draw_noise(const uint64_t *__restrict__ seeds, const double *_
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
     double2 z01 = gauss2(seed, (unsigned)p, 0u, 1u);
     double2 z2 = gauss2(seed, (unsigned)p, 1u, 1u);
-    const bool obs = (mask == nullptr) || mask[p];
+    const bool obs = (mask == nullptr) || mask[(int64_t)b * npix + p];
     const int64_t o = (int64_t)b * 3 * npix + p;
     const double zz[3] = {z01.x, z01.y, z2.x};
     for (int f = 0; f < 3; ++f) {
       const int64_t i = o + f * npix;
-      dhat[i] = obs ? shat[i] + sigma[f * npix + p] * zz[f] : 0.0;
+      dhat[i] = obs ? shat[i] + sigma[i] * zz[f] : 0.0;
     }
   }
 }

@@ -76,7 +76,7 @@ struct dm_plan {
   std::vector<dmwf::RingDev> rings_h;
   std::vector<double> cl_h;     // [4][lmax+1]
   bool have_cl = false, have_noise = false;
-  double alpha = 0.0, t_h = 0.0;
+  std::vector<double> alpha, t_h;   // per RHS: alpha = min N (observed), T_h = alpha Omega
 
   // schedule
   dm_schedule sched{};
@@ -93,11 +93,11 @@ struct dm_plan {
   double *seed = nullptr;       // [mmax+1][npairs][3] : lambda_mm, lp, lm at l0 = max(m, 2)
   int *seed_exp = nullptr;      // [mmax+1][npairs] : scale S (true = v 2^-S), 0 = plain
   double *cl = nullptr;         // [4][lmax+1]
-  double *filt = nullptr;       // [n_levels][lmax+1][4]
+  double *filt = nullptr;       // [B][n_levels][lmax+1][4] per-RHS filters
   int filt_levels = 0;
-  double *w = nullptr;          // [3][npix] alpha / N (0 masked)
-  uint8_t *mask = nullptr;      // [npix]
-  double *sigma = nullptr;      // [3][npix]
+  double *w = nullptr;          // [B][3][npix] alpha / N (0 masked), per RHS
+  uint8_t *mask = nullptr;      // [B][npix]
+  double *sigma = nullptr;      // [B][3][npix]
 
   // workspace (per batch)
   double2 *rc = nullptr;        // [B][3][mmax+1][npairs][2] ring coefficients
@@ -107,7 +107,8 @@ struct dm_plan {
   double *wd = nullptr;         // [B][3][npix] w * d
   double *norms = nullptr;      // [B][3][nrings][2] Cauchy partial sums
   dmwf::SolveState *state = nullptr;   // [B]
-  dmwf::LevelDev *lev = nullptr;
+  dmwf::LevelDev *lev = nullptr;         // [B] per-RHS stopping schedule
+  std::vector<double> eps_final_rhs;     // per RHS (serving sets it per request)
   double *tmpmap = nullptr;     // [B][3][npix] scratch map (CR, host-buffer entry)
   double *tmpmap2 = nullptr;    // [B][3][npix] scratch map
   double2 *tmpalm = nullptr;    // [B][3][nalm] scratch alm (CR)
@@ -120,7 +121,7 @@ struct dm_plan {
   float2 *rc32 = nullptr;       // [B][3][mmax+1][npairs][2]
   float2 *apart32 = nullptr;    // [B][nchunk][3][nalm]
   float *s32 = nullptr;         // [B][3][npix] iteration map
-  float *w32 = nullptr;         // [3][npix]
+  float *w32 = nullptr;         // [B][3][npix]
   float *wd32 = nullptr;        // [B][3][npix]
   float2 *phase32 = nullptr, *bhat32 = nullptr, *twid32 = nullptr;
   // FP64 anchor of the mixed iteration (iterative refinement):
@@ -148,8 +149,8 @@ namespace dmwf {
 
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
 cudaError_t build_tables(dm_plan *p);                        // geometry, phases, chirps, coefficients, seeds
-cudaError_t build_filters(dm_plan *p, cudaStream_t st);      // per-level filter coefficients
-cudaError_t build_noise(dm_plan *p, cudaStream_t st);        // alpha (reduction) and w
+cudaError_t build_filters(dm_plan *p, int b, cudaStream_t st);  // per-level filters of RHS b
+cudaError_t build_noise(dm_plan *p, int b, cudaStream_t st);    // alpha (reduction) and w of RHS b
 
 // ring stage: mode
 enum RingMode { RING_FWD_MAP = 0, RING_INV_MAP = 1, RING_ITER = 2, RING_INIT = 3 };
@@ -164,7 +165,7 @@ cudaError_t legendre_synthesis(dm_plan *p, const double2 *alm, cudaStream_t st);
 enum AnaEpilogue { ANA_PLAIN = 0, ANA_DM_STEP = 1 };
 cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid = nullptr);
 cudaError_t apply_filter_level(dm_plan *p, const double *coef, const double2 *in, double2 *out, cudaStream_t st);
-cudaError_t build_filter_one(dm_plan *p, double lambda, double *coef, cudaStream_t st);
+cudaError_t build_filter_one(dm_plan *p, double lambda, double th, double *coef, cudaStream_t st);
 
 // solver control
 cudaError_t control_init(dm_plan *p, cudaStream_t st);
@@ -176,6 +177,15 @@ cudaError_t copy_s32_to_user(dm_plan *p, double *s_out, cudaStream_t st);
 // written to p->wd; shi32 = s_hi in FP32
 cudaError_t anchor_residual(dm_plan *p, const double *d, const double *s_hi, cudaStream_t st);
 cudaError_t anchor_residual_wd(dm_plan *p, const double *s_hi, cudaStream_t st);  // r = wd - w s_hi
+
+// driver (dm_api.cu), shared with the server (dm_serve.cu)
+dm_status upload_levels(dm_plan *p);
+cudaError_t enqueue_iteration(dm_plan *p, cudaStream_t st, cudaEvent_t *E);
+dm_status anchor(dm_plan *p, cudaStream_t st, bool initial, const double *d, bool need_g);
+dm_status solve_begin(dm_plan *p, const double *d, cudaStream_t st);
+dm_status solve_iterate(dm_plan *p, long max_iters, int *all_done, cudaStream_t st);
+dm_status solve_end(dm_plan *p, double *s_out, double *alm_out, cudaStream_t st, bool to_host);
+dm_status run_dm(dm_plan *p, const double *d, cudaStream_t st);
 
 // constrained realisations
 cudaError_t draw_signal(dm_plan *p, const uint64_t *seeds_dev, double2 *ahat, cudaStream_t st);

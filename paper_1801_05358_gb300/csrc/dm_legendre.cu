@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(ANA_P) k_leg_ana64(const PairDev *__restrict__
 //  ANA_DM_STEP : out = F_level (out + Omega sum)   (a <- F [a + A (t - s)])
 // grid: (l blocks, batch, m)
 __global__ void k_ana_reduce(const double2 *__restrict__ apart, double2 *out, int lmax, int64_t nalm, int nchunk,
-                             double omega, int epilogue, const double *__restrict__ filt,
+                             double omega, int epilogue, const double *__restrict__ filt, int nlev,
                              const SolveState *__restrict__ state) {
   const int b = blockIdx.y, m = blockIdx.z;
   if (state != nullptr && state[b].done) return;
@@ -309,7 +309,7 @@ __global__ void k_ana_reduce(const double2 *__restrict__ apart, double2 *out, in
     o[2 * nalm] = acc[2];
     return;
   }
-  const double *c = filt + ((int64_t)state[b].level * (lmax + 1) + l) * 4;
+  const double *c = filt + (((int64_t)b * nlev + state[b].level) * (lmax + 1) + l) * 4;
   double2 t = cadd(o[0], acc[0]), e = cadd(o[nalm], acc[1]), bb = cadd(o[2 * nalm], acc[2]);
   o[0] = make_double2(c[0] * t.x + c[1] * e.x, c[0] * t.y + c[1] * e.y);
   o[nalm] = make_double2(c[1] * t.x + c[2] * e.x, c[1] * t.y + c[2] * e.y);
@@ -326,6 +326,7 @@ cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream
   double omega = 4.0 * M_PI / (double)p->npix;
   dim3 g2((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
   k_ana_reduce<<<g2, 128, 0, st>>>(p->apart, out, p->lmax, p->nalm, p->nchunk, omega, epilogue, p->filt,
+                                   p->filt_levels,
                                    epilogue == ANA_DM_STEP ? p->state : stp);
   return cudaGetLastError();
 }
@@ -581,7 +582,7 @@ __global__ void __launch_bounds__(ANA_P) k_leg_ana32(const float *__restrict__ p
 
 // chunk sum in FP64, then the FP64 harmonic step and filter
 __global__ void k_ana_reduce32(const float2 *__restrict__ apart, double2 *out, int lmax, int64_t nalm, int nchunk,
-                               double omega, int epilogue, const double *__restrict__ filt,
+                               double omega, int epilogue, const double *__restrict__ filt, int nlev,
                                const SolveState *__restrict__ state, const double2 *__restrict__ g_add) {
   const int b = blockIdx.y, m = blockIdx.z;
   if (state != nullptr && state[b].done) return;
@@ -611,7 +612,7 @@ __global__ void k_ana_reduce32(const float2 *__restrict__ apart, double2 *out, i
     acc[1] = cadd(acc[1], g[nalm]);
     acc[2] = cadd(acc[2], g[2 * nalm]);
   }
-  const double *c = filt + ((int64_t)state[b].level * (lmax + 1) + l) * 4;
+  const double *c = filt + (((int64_t)b * nlev + state[b].level) * (lmax + 1) + l) * 4;
   double2 t = cadd(o[0], acc[0]), e = cadd(o[nalm], acc[1]), bb = cadd(o[2 * nalm], acc[2]);
   o[0] = make_double2(c[0] * t.x + c[1] * e.x, c[0] * t.y + c[1] * e.y);
   o[nalm] = make_double2(c[1] * t.x + c[2] * e.x, c[1] * t.y + c[2] * e.y);
@@ -648,6 +649,7 @@ cudaError_t legendre_analysis32(dm_plan *p, int epilogue, double2 *out, cudaStre
   double omega = 4.0 * M_PI / (double)p->npix;
   dim3 g2((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
   k_ana_reduce32<<<g2, 128, 0, st>>>(p->apart32, out, p->lmax, p->nalm, p->nchunk, omega, epilogue, p->filt,
+                                     p->filt_levels,
                                      epilogue == ANA_DM_STEP ? p->state : stp,
                                      (p->anchor_active && epilogue == ANA_DM_STEP) ? p->g_hi : nullptr);
   return cudaGetLastError();

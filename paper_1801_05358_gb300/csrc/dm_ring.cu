@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) k_ring(const RingDev *__restrict__ rings,
     // With an anchor (mixed precision) the state is Y e, s = s_anchor + Y e, and
     // the data part w (d - s_anchor) is carried in FP64 by the anchor: r = -w Y e.
     double dd = 0.0, ss = 0.0;
-    const int64_t wo = (int64_t)f * npix + Rg.start;
+    const int64_t wo = moff;  // per-RHS weights share the map layout
     for (int j = threadIdx.x; j < h; j += blockDim.x) {
       C z = buf[j];
       R s0 = z.x, s1 = -z.y;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) k_ring(const RingDev *__restrict__ rings,
     }
   } else {
     // forward only: load the real ring (RING_INIT: t_0 - s_0 = d on observed pixels)
-    const int64_t wo = (int64_t)f * npix + Rg.start;
+    const int64_t wo = moff;  // per-RHS weights share the map layout
     for (int j = threadIdx.x; j < h; j += blockDim.x) {
       double x0 = in_map[moff + 2 * j], x1 = in_map[moff + 2 * j + 1];
       if (MODE == RING_INIT) {

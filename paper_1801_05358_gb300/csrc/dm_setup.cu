@@ -382,7 +382,7 @@ cudaError_t setup_fp32(dm_plan *p) {
   if ((e = al(&p->rc32, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return e;
   if ((e = al(&p->apart32, (size_t)B * p->nchunk * 3 * p->nalm))) return e;
   if ((e = al(&p->s32, (size_t)B * n3))) return e;
-  if ((e = al(&p->w32, (size_t)n3))) return e;
+  if ((e = al(&p->w32, (size_t)B * n3))) return e;
   if ((e = al(&p->wd32, (size_t)B * n3))) return e;
   if ((e = al(&p->a_hi, (size_t)B * 3 * p->nalm))) return e;
   if ((e = al(&p->g_hi, (size_t)B * 3 * p->nalm))) return e;
@@ -395,42 +395,55 @@ cudaError_t setup_fp32(dm_plan *p) {
   return cudaDeviceSynchronize();
 }
 
-cudaError_t build_filter_one(dm_plan *p, double lambda, double *coef, cudaStream_t st) {
-  double mu = (lambda - 1.0) * p->t_h;
-  k_filter<<<(p->lmax + 1 + 127) / 128, 128, 0, st>>>(p->cl, p->lmax, mu, p->t_h, coef);
+cudaError_t build_filter_one(dm_plan *p, double lambda, double th, double *coef, cudaStream_t st) {
+  double mu = (lambda - 1.0) * th;
+  k_filter<<<(p->lmax + 1 + 127) / 128, 128, 0, st>>>(p->cl, p->lmax, mu, th, coef);
   return cudaGetLastError();
 }
 
-cudaError_t build_filters(dm_plan *p, cudaStream_t st) {
-  int nl = (int)p->lambdas.size();
+// filters of RHS b for every level: filt[b][k][l][4]
+cudaError_t build_filters(dm_plan *p, int b, cudaStream_t st) {
+  const int nl = (int)p->lambdas.size();
   if (p->filt == nullptr || p->filt_levels < nl) {
     if (p->filt) cudaFree(p->filt);
-    cudaError_t e = cudaMalloc(&p->filt, sizeof(double) * 4 * (p->lmax + 1) * (size_t)(nl > 0 ? nl : 1));
+    p->filt = nullptr;
+    cudaError_t e = cudaMalloc(&p->filt, sizeof(double) * 4 * (p->lmax + 1) * (size_t)nl * p->batch);
     if (e) return e;
     p->filt_levels = nl;
+    // every RHS must be (re)built after a reallocation
+    for (int bb = 0; bb < p->batch; ++bb)
+      for (int k = 0; k < nl; ++k) {
+        e = build_filter_one(p, p->lambdas[k], p->t_h[bb], p->filt + ((size_t)bb * nl + k) * 4 * (p->lmax + 1), st);
+        if (e) return e;
+      }
+    return cudaGetLastError();
   }
   for (int k = 0; k < nl; ++k) {
-    cudaError_t e = build_filter_one(p, p->lambdas[k], p->filt + (size_t)4 * (p->lmax + 1) * k, st);
+    cudaError_t e = build_filter_one(p, p->lambdas[k], p->t_h[b], p->filt + ((size_t)b * p->filt_levels + k) * 4 * (p->lmax + 1), st);
     if (e) return e;
   }
   return cudaGetLastError();
 }
 
-cudaError_t build_noise(dm_plan *p, cudaStream_t st) {
+// alpha of RHS b (min over its observed pixel-components) and its weights w
+cudaError_t build_noise(dm_plan *p, int b, cudaStream_t st) {
   int nb = 256;
   double *partial;
   cudaError_t e = cudaMalloc(&partial, sizeof(double) * nb);
   if (e) return e;
-  k_min_n<<<nb, 256, 0, st>>>(p->sigma, p->mask, p->npix, partial);
+  const int64_t n3 = 3 * p->npix;
+  const double *sg = p->sigma + (size_t)b * n3;
+  const uint8_t *mk = p->mask + (size_t)b * p->npix;
+  k_min_n<<<nb, 256, 0, st>>>(sg, mk, p->npix, partial);
   k_min_final<<<1, 256, 0, st>>>(partial, nb);
-  k_weights<<<1024, 256, 0, st>>>(p->sigma, p->mask, p->npix, partial, p->w);
+  k_weights<<<1024, 256, 0, st>>>(sg, mk, p->npix, partial, p->w + (size_t)b * n3);
   double alpha = 0.0;
   cudaMemcpyAsync(&alpha, partial, sizeof(double), cudaMemcpyDeviceToHost, st);
   e = cudaStreamSynchronize(st);
   cudaFree(partial);
   if (e) return e;
-  p->alpha = alpha;
-  p->t_h = alpha * 4.0 * M_PI / (double)p->npix;
+  p->alpha[b] = alpha;
+  p->t_h[b] = alpha * 4.0 * M_PI / (double)p->npix;
   return cudaGetLastError();
 }
 

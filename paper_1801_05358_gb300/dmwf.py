@@ -25,8 +25,10 @@ EXPORTS = [
     "dm_constrained_realization", "dm_draw_cr_inputs", "dm_alm2map", "dm_map2alm", "dm_ring_fft_forward",
     "dm_ring_fft_inverse", "dm_legendre_synthesis", "dm_legendre_analysis", "dm_apply_filter", "dm_noise_info",
     "dm_profile_enable", "dm_profile_read", "dm_measure_alu_peaks", "dm_solve_begin", "dm_solve_iterate",
-    "dm_solve_end", "dm_set_refinement",
+    "dm_solve_end", "dm_set_refinement", "dm_set_noise_mask_rhs", "dm_server_create", "dm_serve_submit",
+    "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy",
 ]
+DM_REQ_WF, DM_REQ_CR = 0, 1
 
 
 class DmSchedule(ctypes.Structure):
@@ -44,6 +46,28 @@ class DmProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("iterations", ctypes.c_int64), ("ms_analysis", ctypes.c_double),
                 ("ms_reduce", ctypes.c_double), ("ms_synthesis", ctypes.c_double), ("ms_ring", ctypes.c_double),
                 ("ms_control", ctypes.c_double), ("anchors", ctypes.c_int64), ("ms_anchor", ctypes.c_double)]
+
+
+class DmServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("slots_per_plan", ctypes.c_int),
+                ("iters_per_round", ctypes.c_int), ("prec", ctypes.c_int), ("sched", DmSchedule),
+                ("anchor_every", ctypes.c_int), ("max_pending", ctypes.c_int)]
+
+
+class DmRequest(ctypes.Structure):
+    _fields_ = [("nside", ctypes.c_int), ("lmax", ctypes.c_int), ("kind", ctypes.c_int), ("tol", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("cl", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("d", ctypes.c_void_p), ("s_out", ctypes.c_void_p)]
+
+
+class DmResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("cauchy_final", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+
+
+class DmServerInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ["pending", "busy_slots", "pools", "bytes_reserved", "rounds",
+                                               "admitted", "retired"]]
 
 
 class DmError(RuntimeError):
@@ -90,6 +114,14 @@ def lib():
         L.dm_solve_iterate.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
         L.dm_solve_end.argtypes = [vp, vp, vp, vp, vp]
         L.dm_set_refinement.argtypes = [vp, ctypes.c_int]
+        L.dm_set_noise_mask_rhs.argtypes = [vp, ctypes.c_int, vp, vp]
+        L.dm_server_create.argtypes = [ctypes.POINTER(DmServerConfig), ctypes.POINTER(vp)]
+        L.dm_serve_submit.argtypes = [vp, ctypes.POINTER(DmRequest), ctypes.POINTER(ctypes.c_uint64)]
+        L.dm_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(DmResult)]
+        L.dm_serve_cancel.argtypes = [vp, ctypes.c_uint64]
+        L.dm_server_info.argtypes = [vp, ctypes.POINTER(DmServerInfo)]
+        L.dm_server_destroy.argtypes = [vp]
+        L.dm_server_destroy.restype = None
         L.dm_measure_alu_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
@@ -162,6 +194,11 @@ class Plan:
         s = np.ascontiguousarray(sigma, dtype=np.float64)
         m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
         self._check(lib().dm_set_noise_mask(self.h, _np_ptr(s), _np_ptr(m)))
+
+    def set_noise_mask_rhs(self, b, sigma, mask=None):
+        s = np.ascontiguousarray(sigma, dtype=np.float64)
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        self._check(lib().dm_set_noise_mask_rhs(self.h, int(b), _np_ptr(s), _np_ptr(m)))
 
     def set_schedule(self, lambda0=1000.0, n_levels=10, iters_per_level=10, eps0=1e-4, eps_final=1e-6, eta=0.0,
                      max_iter=100000, check_every=8):
@@ -263,3 +300,67 @@ class Plan:
     def apply_filter(self, lam, alm_in, alm_out, stream=None):
         self._check(lib().dm_apply_filter(self.h, ctypes.c_double(lam), _ptr(alm_in), _ptr(alm_out),
                                           _stream(stream)))
+
+
+class Server:
+    """Continuous-batching server (dm_server_*).  Requests carry host arrays;
+    the result map is written into a host array owned by this object until the
+    ticket completes."""
+
+    def __init__(self, hbm_budget_bytes, slots_per_plan=8, iters_per_round=16, prec=DM_FP64, lambda0=1000.0,
+                 n_levels=10, eps0=1e-4, max_iter=1000000, anchor_every=0, max_pending=0):
+        sc = DmSchedule(lambda0, n_levels, 0, eps0, 1e-6, 0.0, max_iter, 8)
+        cfg = DmServerConfig(int(hbm_budget_bytes), slots_per_plan, iters_per_round, prec, sc, anchor_every,
+                             max_pending)
+        h = ctypes.c_void_p()
+        st = lib().dm_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != DM_OK:
+            raise DmError(st, "dm_server_create failed")
+        self.h = h
+        self._live = {}
+
+    def submit(self, nside, lmax, kind, tol, cl, sigma, d, mask=None, seed=0):
+        arrs = dict(cl=np.ascontiguousarray(cl, dtype=np.float64), sigma=np.ascontiguousarray(sigma, dtype=np.float64),
+                    d=np.ascontiguousarray(d, dtype=np.float64),
+                    mask=None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8))
+        out = np.zeros((3, 12 * nside * nside), dtype=np.float64)
+        req = DmRequest(nside, lmax, kind, tol, seed, arrs["cl"].ctypes.data, arrs["sigma"].ctypes.data,
+                        None if arrs["mask"] is None else arrs["mask"].ctypes.data, arrs["d"].ctypes.data,
+                        out.ctypes.data)
+        t = ctypes.c_uint64()
+        st = lib().dm_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if st != DM_OK:
+            raise DmError(st, "dm_serve_submit")
+        self._live[t.value] = out
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (result dict, map)."""
+        r = DmResult()
+        st = lib().dm_serve_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if st == DM_EAGAIN:
+            return None
+        if st != DM_OK:
+            raise DmError(st, "dm_serve_poll")
+        out = self._live.pop(ticket)
+        return dict(status=r.status, iters=r.iters, cauchy_final=r.cauchy_final, latency_ms=r.latency_ms,
+                    queue_ms=r.queue_ms), out
+
+    def cancel(self, ticket):
+        return lib().dm_serve_cancel(self.h, ctypes.c_uint64(ticket))
+
+    def info(self):
+        i = DmServerInfo()
+        lib().dm_server_info(self.h, ctypes.byref(i))
+        return {k: getattr(i, k) for k, _ in DmServerInfo._fields_}
+
+    def close(self):
+        if self.h:
+            lib().dm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
