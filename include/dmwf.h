@@ -171,6 +171,13 @@ dm_status dm_solve_end(dm_plan *plan, double *s_out, double *alm_out, dm_stats *
  * precision iterative refinement; no counterpart in the paper). */
 dm_status dm_set_refinement(dm_plan *plan, int anchor_every);
 
+/* Tensor cores for the mixed-precision Legendre stages (default on): with a
+ * batch of 8, 16, 32 or 64 RHS the contractions over l and over ring pairs
+ * run as tcgen05 GEMMs with BF16 hi/lo split operands and FP32 accumulation
+ * (three products per K step); other batches use the FP32 CUDA-core kernels.
+ * A pipeline wait that gives up reports DM_ETIMEOUT. */
+dm_status dm_set_tensor_cores(dm_plan *plan, int on);
+
 /* Constrained realisations, Section 2.2, Eq. 19:
  * s_CR = W(d - dhat) + shat with shat = Y ahat, ahat ~ S, dhat = shat + nhat,
  * nhat ~ N on observed pixels, drawn from seeds[batch] (host) with the

@@ -46,7 +46,7 @@ void free_all(dm_plan *p) {
                   p->filt, p->w, p->mask, p->sigma, p->rc, p->a, p->apart, p->wd, p->norms, p->state,
                   p->lev, p->tmpmap, p->tmpmap2, p->tmpalm, p->seeds_dev, p->coef_tmp,
                   p->ptab, p->rc32, p->apart32, p->s32, p->w32, p->wd32, p->phase32, p->bhat32, p->twid32,
-                  p->a_hi, p->g_hi, p->shi32, p->s64, p->rhi};
+                  p->a_hi, p->g_hi, p->shi32, p->s64, p->rhi, p->tc_err};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -245,8 +245,11 @@ dm_status solve_iterate(dm_plan *p, long max_iters, int *all_done, cudaStream_t 
     p->iters_launched += window;
     p->since_anchor += (int)window;
     cudaError_t e = cudaMemcpyAsync(hs.data(), p->state, sizeof(SolveState) * p->batch, cudaMemcpyDeviceToHost, st);
+    int tcerr = 0;
+    if (!e && p->tc_err) e = cudaMemcpyAsync(&tcerr, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaStreamSynchronize(st);
     if (e) return cuda_fail(p, e, "poll state");
+    if (tcerr) return fail(p, DM_ETIMEOUT, "a tensor-core pipeline wait gave up");
     if (p->prof_on) {
       for (long k = 0; k < window; ++k) {
         float t[5];
@@ -680,6 +683,12 @@ dm_status dm_solve_end(dm_plan *p, double *s_out, double *alm_out, dm_stats *sta
   DM_CU(cudaStreamSynchronize(st), "sync");
   fill_stats(p, stats, &r);
   return r;
+}
+
+dm_status dm_set_tensor_cores(dm_plan *p, int on) {
+  if (!p) return DM_EINVAL;
+  p->use_tc = on != 0;
+  return DM_OK;
 }
 
 dm_status dm_set_refinement(dm_plan *p, int anchor_every) {

@@ -131,6 +131,8 @@ struct dm_plan {
   float *shi32 = nullptr;       // [B][3][npix] Y a_hi rounded to FP32 (for ||s||)
   bool anchor_active = false;
   int anchor_every = 256;
+  bool use_tc = true;           // tcgen05 Legendre stages when the batch allows
+  int *tc_err = nullptr;        // device flag: a bounded tensor-core wait gave up
   // solve session (dm_solve_begin / iterate / end)
   double *s64 = nullptr;        // [B][3][npix] FP64 iterate s (FP64 mode) / Y a_hi (mixed)
   double *rhi = nullptr;        // [B][3][npix] FP64 anchor residual w (d - Y a_hi)
@@ -177,6 +179,11 @@ cudaError_t copy_s32_to_user(dm_plan *p, double *s_out, cudaStream_t st);
 // written to p->wd; shi32 = s_hi in FP32
 cudaError_t anchor_residual(dm_plan *p, const double *d, const double *s_hi, cudaStream_t st);
 cudaError_t anchor_residual_wd(dm_plan *p, const double *s_hi, cudaStream_t st);  // r = wd - w s_hi
+
+// tensor-core Legendre stages (dm_legendre_tc.cu)
+bool tc_batch_ok(int B);
+cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t st);
+cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st);
 
 // driver (dm_api.cu), shared with the server (dm_serve.cu)
 dm_status upload_levels(dm_plan *p);

@@ -580,7 +580,6 @@ __global__ void __launch_bounds__(ANA_P) k_leg_ana32(const float *__restrict__ p
   }
 }
 
-// chunk sum in FP64, then the FP64 harmonic step and filter
 __global__ void k_ana_reduce32(const float2 *__restrict__ apart, double2 *out, int lmax, int64_t nalm, int nchunk,
                                double omega, int epilogue, const double *__restrict__ filt, int nlev,
                                const SolveState *__restrict__ state, const double2 *__restrict__ g_add) {
@@ -589,15 +588,17 @@ __global__ void k_ana_reduce32(const float2 *__restrict__ apart, double2 *out, i
   const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
   if (l > lmax) return;
   const int64_t i = alm_base(lmax, m) + l;
+  // chunk sum in FP32 (it carries the analysis of the FP32 correction only),
+  // harmonic step and filter in FP64
   double2 acc[3];
   for (int f = 0; f < 3; ++f) {
-    double ax = 0.0, ay = 0.0;
+    float ax = 0.f, ay = 0.f;
     for (int c = 0; c < nchunk; ++c) {
       const float2 v = apart[(((int64_t)b * nchunk + c) * 3 + f) * nalm + i];
       ax += v.x;
       ay += v.y;
     }
-    acc[f] = make_double2(omega * ax, omega * ay);
+    acc[f] = make_double2(omega * (double)ax, omega * (double)ay);
   }
   double2 *o = out + (int64_t)b * 3 * nalm + i;
   if (epilogue == ANA_PLAIN) {
@@ -620,6 +621,7 @@ __global__ void k_ana_reduce32(const float2 *__restrict__ apart, double2 *out, i
 }
 
 cudaError_t legendre_synthesis32(dm_plan *p, const double2 *alm, cudaStream_t st) {
+  if (p->use_tc && tc_batch_ok(p->batch)) return legendre_synthesis_tc(p, alm, st);
   const SolveState *stp = p->state_active ? p->state : nullptr;
   const int pb = (p->npairs + SYN_THREADS - 1) / SYN_THREADS;
   if (p->batch % 4 == 0) {
@@ -636,7 +638,12 @@ cudaError_t legendre_synthesis32(dm_plan *p, const double2 *alm, cudaStream_t st
 
 cudaError_t legendre_analysis32(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid) {
   const SolveState *stp = p->state_active ? p->state : nullptr;
-  if (p->batch % 4 == 0) {
+  int nchunk = p->nchunk;
+  if (p->use_tc && tc_batch_ok(p->batch)) {
+    cudaError_t e = legendre_analysis_tc(p, st);
+    if (e) return e;
+    nchunk = 1;
+  } else if (p->batch % 4 == 0) {
     dim3 g(p->batch / 4, p->nchunk, p->mmax + 1);
     k_leg_ana32<4><<<g, ANA_P, 0, st>>>(p->ptab, p->rc32, p->apart32, p->lmax, p->mmax, p->npairs, p->nalm,
                                         p->nchunk, stp);
@@ -648,7 +655,7 @@ cudaError_t legendre_analysis32(dm_plan *p, int epilogue, double2 *out, cudaStre
   if (mid) cudaEventRecord(mid, st);
   double omega = 4.0 * M_PI / (double)p->npix;
   dim3 g2((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
-  k_ana_reduce32<<<g2, 128, 0, st>>>(p->apart32, out, p->lmax, p->nalm, p->nchunk, omega, epilogue, p->filt,
+  k_ana_reduce32<<<g2, 128, 0, st>>>(p->apart32, out, p->lmax, p->nalm, nchunk, omega, epilogue, p->filt,
                                      p->filt_levels,
                                      epilogue == ANA_DM_STEP ? p->state : stp,
                                      (p->anchor_active && epilogue == ANA_DM_STEP) ? p->g_hi : nullptr);

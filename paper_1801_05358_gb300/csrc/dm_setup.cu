@@ -387,6 +387,8 @@ cudaError_t setup_fp32(dm_plan *p) {
   if ((e = al(&p->a_hi, (size_t)B * 3 * p->nalm))) return e;
   if ((e = al(&p->g_hi, (size_t)B * 3 * p->nalm))) return e;
   if ((e = al(&p->shi32, (size_t)B * n3))) return e;
+  if ((e = al(&p->tc_err, 1))) return e;
+  cudaMemset(p->tc_err, 0, sizeof(int));
   cudaMemset(p->rc32, 0, sizeof(float2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
   k_d2f2<<<512, 256>>>(p->phase, p->phase32, p->ph_total);
   if (p->bh_total > 0) k_d2f2<<<512, 256>>>(p->bhat, p->bhat32, p->bh_total);

@@ -26,7 +26,7 @@ EXPORTS = [
     "dm_ring_fft_inverse", "dm_legendre_synthesis", "dm_legendre_analysis", "dm_apply_filter", "dm_noise_info",
     "dm_profile_enable", "dm_profile_read", "dm_measure_alu_peaks", "dm_solve_begin", "dm_solve_iterate",
     "dm_solve_end", "dm_set_refinement", "dm_set_noise_mask_rhs", "dm_server_create", "dm_serve_submit",
-    "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy",
+    "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores",
 ]
 DM_REQ_WF, DM_REQ_CR = 0, 1
 
@@ -114,6 +114,7 @@ def lib():
         L.dm_solve_iterate.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
         L.dm_solve_end.argtypes = [vp, vp, vp, vp, vp]
         L.dm_set_refinement.argtypes = [vp, ctypes.c_int]
+        L.dm_set_tensor_cores.argtypes = [vp, ctypes.c_int]
         L.dm_set_noise_mask_rhs.argtypes = [vp, ctypes.c_int, vp, vp]
         L.dm_server_create.argtypes = [ctypes.POINTER(DmServerConfig), ctypes.POINTER(vp)]
         L.dm_serve_submit.argtypes = [vp, ctypes.POINTER(DmRequest), ctypes.POINTER(ctypes.c_uint64)]
@@ -255,6 +256,9 @@ class Plan:
         st = lib().dm_solve_end(self.h, _ptr(s_out), _ptr(alm_out), stats, _stream(stream))
         self._check(st, allow=(DM_ENOTCONV,))
         return st, self._stats_out(stats)
+
+    def set_tensor_cores(self, on=True):
+        self._check(lib().dm_set_tensor_cores(self.h, 1 if on else 0))
 
     def set_refinement(self, anchor_every):
         self._check(lib().dm_set_refinement(self.h, int(anchor_every)))

@@ -87,3 +87,53 @@ def test_mixed_first_iterations_nside256(orc):
     s = torch.zeros((1, 3, wl.npix), dtype=torch.float64, device="cuda")
     p.wiener_filter(dev(d), s)
     assert rel(s.cpu().numpy()[0], ref["s"]) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# tcgen05 tensor-core Legendre stages (batches of 8, 16, 32, 64): split-BF16
+# operands, three products, FP32 accumulation.  Single transforms within 2e-5
+# of the oracle; solves within the mixed-mode bound 1e-5 thanks to the FP64
+# anchors.
+@pytest.mark.parametrize("nside,lmax,B", [(8, 16, 8), (16, 47, 16), (64, 128, 8), (32, 64, 32)])
+def test_tc_transforms(orc, nside, lmax, B):
+    alm = W.random_alm(lmax, B, 18)
+    maps = W.random_maps(nside, B, 19)
+    p = dmwf.Plan(nside, lmax, B)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    m_out = torch.zeros((B, 3, 12 * nside * nside), dtype=torch.float64, device="cuda")
+    a_out = torch.zeros((B, 3, (lmax + 1) * (lmax + 2) // 2, 2), dtype=torch.float64, device="cuda")
+    p.alm2map(alm_dev(alm), m_out)
+    p.map2alm(dev(maps), a_out)
+    gm = m_out.cpu().numpy()
+    ga = a_out.cpu().numpy().view(np.complex128)[..., 0]
+    for b in range(0, B, max(1, B // 4)):
+        assert rel(gm[b], orc.alm2map(nside, lmax, alm[b])) < 2e-5
+        assert rel(ga[b], orc.map2alm(nside, lmax, maps[b])) < 2e-5
+
+
+def test_tc_matches_cuda_core_kernels(orc):
+    nside, lmax, B = 32, 64, 16
+    alm = W.random_alm(lmax, B, 28)
+    p = dmwf.Plan(nside, lmax, B)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    out_tc = torch.zeros((B, 3, 12 * nside * nside), dtype=torch.float64, device="cuda")
+    out_simt = torch.zeros_like(out_tc)
+    p.alm2map(alm_dev(alm), out_tc)
+    p.set_tensor_cores(False)
+    p.alm2map(alm_dev(alm), out_simt)
+    assert rel(out_tc.cpu().numpy(), out_simt.cpu().numpy()) < 2e-5
+
+
+def test_tc_fixed_schedule_nside16(orc):
+    wl = W.make_workload("nside16", list(range(8)))
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(1000.0, 10)
+    p = make_plan(wl, 8, lambda0=1000.0, n_levels=10, iters_per_level=10, check_every=16)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    p.set_refinement(16)
+    s = torch.zeros((8, 3, wl.npix), dtype=torch.float64, device="cuda")
+    p.wiener_filter(dev(d), s)
+    got = s.cpu().numpy()
+    for b in [0, 3, 7]:
+        ref = orc.dm_solve(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.mask, d[b], lam, forced_iters=[10] * 10)
+        assert rel(got[b], ref["s"]) < 1e-5
