@@ -221,6 +221,24 @@ dm_status dm_legendre_analysis(dm_plan *plan, const double *rc, double *alm, voi
 /* Per-l filter of level lambda (Eq. 8): alm_out = F alm_in with
  * F = V diag(f_e) V^T, f_e = max(S_e, mu)/(max(S_e, mu) + T_h), mu = (lambda-1) T_h. */
 dm_status dm_apply_filter(dm_plan *plan, double lambda, const double *alm_in, double *alm_out, void *stream);
+/* Allocation-free variant of dm_legendre_analysis (same inputs, same
+ * outputs, FP64), for callers that must not allocate device memory at the
+ * moment they call: work recorded into a CUDA graph by stream capture, a
+ * real-time loop where cudaMalloc/cudaFree could synchronise the device, or
+ * an application that fixes the library's device-memory budget at start-up.
+ * The paper has no counterpart; this is a property of the library.
+ * The per-chunk partial sums go to one file-scope device array of
+ * 64 MiB (held on every GPU that loads the library until exit) instead of
+ * the plan's workspace; plans needing more (batch x ceil(2 nside / 64) x 3 x
+ * nalm x 16 bytes) get DM_EINVAL with a message.  The first call on each
+ * device looks the array's address up (cudaGetSymbolAddress) with that device
+ * current: make it before any stream capture.  Calls share the array, so
+ * calls that overlap on the GPU race and must be serialised by the caller;
+ * every value the call reads from the array it wrote first, so nothing needs
+ * clearing between calls.  No cudaMalloc, cudaFree or allocating library call
+ * is made. */
+dm_status dm_legendre_analysis_noalloc(dm_plan *plan, const double *rc, double *alm, void *stream);
+
 /* alpha and T_h of the noise model of RHS 0 (host outputs). */
 dm_status dm_noise_info(const dm_plan *plan, double *alpha, double *t_h);
 

@@ -27,6 +27,7 @@ EXPORTS = [
     "dm_profile_enable", "dm_profile_read", "dm_measure_alu_peaks", "dm_solve_begin", "dm_solve_iterate",
     "dm_solve_end", "dm_set_refinement", "dm_set_noise_mask_rhs", "dm_server_create", "dm_serve_submit",
     "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores",
+    "dm_legendre_analysis_noalloc",
 ]
 DM_REQ_WF, DM_REQ_CR = 0, 1
 
@@ -104,7 +105,7 @@ def lib():
         L.dm_constrained_realization.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.dm_draw_cr_inputs.argtypes = [vp, vp, vp, vp, vp, vp]
         for name in ["dm_alm2map", "dm_map2alm", "dm_ring_fft_forward", "dm_ring_fft_inverse",
-                     "dm_legendre_synthesis", "dm_legendre_analysis"]:
+                     "dm_legendre_synthesis", "dm_legendre_analysis", "dm_legendre_analysis_noalloc"]:
             getattr(L, name).argtypes = [vp, vp, vp, vp]
         L.dm_apply_filter.argtypes = [vp, ctypes.c_double, vp, vp, vp]
         L.dm_noise_info.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -300,6 +301,11 @@ class Plan:
 
     def legendre_analysis(self, rc, alm, stream=None):
         self._check(lib().dm_legendre_analysis(self.h, _ptr(rc), _ptr(alm), _stream(stream)))
+
+    def legendre_analysis_noalloc(self, rc, alm, stream=None):
+        """dm_legendre_analysis without any device allocation in the call
+        (scratch in a fixed file-scope device array)."""
+        self._check(lib().dm_legendre_analysis_noalloc(self.h, _ptr(rc), _ptr(alm), _stream(stream)))
 
     def apply_filter(self, lam, alm_in, alm_out, stream=None):
         self._check(lib().dm_apply_filter(self.h, ctypes.c_double(lam), _ptr(alm_in), _ptr(alm_out),
