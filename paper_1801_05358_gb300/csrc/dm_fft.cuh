@@ -4,6 +4,18 @@
 // into a complex one of length h = n / 2.  h is a power of two for the
 // equatorial belt when nside is; the other lengths (h = 2i) go through
 // Bluestein's chirp-z convolution (Bluestein 1970) on a power-of-two size M.
+//
+// Twiddles are stage-contiguous: tws[len - 1 + j] = e^{-i pi j / len} for the
+// butterfly half-length len = 1, 2, 4, ... and j < len, so a transform of size
+// M reads the first M - 1 entries and consecutive threads of a stage read
+// consecutive entries.
+//
+// Two radix-2 forms avoid an explicit bit-reversal pass:
+//   fft_dif: natural-order input -> bit-reversed output (Gentleman-Sande)
+//   fft_dit: bit-reversed input  -> natural-order output (Cooley-Tukey)
+// Both compute the forward transform X_k = sum_j x_j e^{-2 pi i jk/M}, and
+// both fuse two radix-2 stages per pass (one closed quadruple per task), so a
+// size-M transform takes ceil(log2 M / 2) barriers.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -42,85 +54,87 @@ __device__ __forceinline__ T2 csub(T2 a, T2 b) {
   a.y -= b.y;
   return a;
 }
-
-template <typename T2, typename TW>
-__device__ __forceinline__ T2 tw_cast(TW w) {
+template <typename T2>
+__device__ __forceinline__ T2 cmul_negi(T2 a) {  // a * (-i)
   T2 r;
-  r.x = w.x;
-  r.y = w.y;
+  r.x = a.y;
+  r.y = -a.x;
   return r;
 }
 
-// In-place forward FFT (kernel e^{-2 pi i jk/M}) of length M = 2^k >= 1 held in
-// shared memory, radix-2 decimation in time after a bit-reversal permutation.
-// twid[k] = e^{-2 pi i k / Mtab}, k < Mtab / 2, Mtab a multiple of M.
-// All threads of the block take part; the caller syncs before and after.
-template <typename T2, typename TW>
-__device__ void fft_pow2(T2 *x, int M, const TW *__restrict__ twid, int Mtab) {
+// index k of a size-2^logM transform in bit-reversed order
+__device__ __forceinline__ int bitrev(int k, int logM) { return (int)(__brev((unsigned)k) >> (32 - logM)); }
+
+// In place, natural order in, bit-reversed order out.  Threads threadIdx.x of
+// blockDim.x take part (every y-slice of the block runs its own transform in
+// lockstep); the caller syncs before, this ends with a block barrier.
+template <typename T2>
+__device__ void fft_dif(T2 *x, int M, const T2 *tws) {
   if (M <= 1) return;
   const int logM = 31 - __clz(M);
-  for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    int j = (int)(__brev((unsigned)i) >> (32 - logM));
-    if (j > i) {
-      T2 t = x[i];
-      x[i] = x[j];
-      x[j] = t;
+  const int tx = threadIdx.x, nt = blockDim.x;
+  int L2 = M >> 1;  // half-length of the first stage of the pass
+  for (; L2 >= 2; L2 >>= 2) {
+    const int L = L2 >> 1;  // stages 2L then L on {B + j + {0, L, 2L, 3L}}, B a multiple of 4L
+    for (int k = tx; k < (M >> 2); k += nt) {
+      const int j = k & (L - 1);
+      const int i0 = ((k - j) << 2) + j;
+      const T2 a0 = x[i0], a1 = x[i0 + L], a2 = x[i0 + 2 * L], a3 = x[i0 + 3 * L];
+      const T2 w2 = tws[2 * L - 1 + j], w1 = tws[L - 1 + j];
+      const T2 b0 = cadd(a0, a2), b2 = cmul(csub(a0, a2), w2);
+      const T2 b1 = cadd(a1, a3), b3 = cmul_negi(cmul(csub(a1, a3), w2));
+      x[i0] = cadd(b0, b1);
+      x[i0 + L] = cmul(csub(b0, b1), w1);
+      x[i0 + 2 * L] = cadd(b2, b3);
+      x[i0 + 3 * L] = cmul(csub(b2, b3), w1);
     }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int len = 1; len < M; len <<= 1) {
-    const int tstride = Mtab / (2 * len);
-    for (int k = threadIdx.x; k < (M >> 1); k += blockDim.x) {
-      const int j = k & (len - 1);
-      const int i0 = ((k - j) << 1) + j;
-      const int i1 = i0 + len;
-      T2 w = tw_cast<T2>(twid[j * tstride]);
-      T2 u = x[i0];
-      T2 v = cmul(x[i1], w);
-      x[i0] = cadd(u, v);
-      x[i1] = csub(u, v);
+  if (logM & 1) {  // last single stage, half-length 1 (twiddle 1)
+    for (int k = tx; k < (M >> 1); k += nt) {
+      const T2 u = x[2 * k], v = x[2 * k + 1];
+      x[2 * k] = cadd(u, v);
+      x[2 * k + 1] = csub(u, v);
     }
     __syncthreads();
   }
 }
 
-// Forward DFT of length h (kernel e^{-2 pi i jk/h}) in place in x[0..h), x having
-// room for M entries.  Power-of-two h: direct.  Otherwise Bluestein:
-//   X_k = c_k sum_j (x_j c_j) conj(c_{k-j}),  c_j = e^{-i pi j^2 / h},
-// the convolution done as IFFT_M(FFT_M(x c) * bhat) with bhat = FFT_M of the
-// zero-padded conj(c) (precomputed).  ph[q] = e^{-i pi q / (2h)}, q < 4h, so
-// c_j = ph[2 j^2 mod 4h].
-template <typename T2, typename TW>
-__device__ void dft_forward(T2 *x, int h, int M, int bluestein, const TW *__restrict__ ph,
-                            const TW *__restrict__ bhat, const TW *__restrict__ twid, int Mtab) {
-  if (!bluestein) {
-    fft_pow2(x, h, twid, Mtab);
-    return;
-  }
-  const int64_t n2 = 4LL * h;
-  for (int j = threadIdx.x; j < M; j += blockDim.x) {
-    if (j < h) {
-      T2 c = tw_cast<T2>(ph[(2LL * j * j) % n2]);
-      x[j] = cmul(x[j], c);
-    } else {
-      x[j].x = 0;
-      x[j].y = 0;
+// In place, bit-reversed order in, natural order out; same conventions.
+template <typename T2>
+__device__ void fft_dit(T2 *x, int M, const T2 *tws) {
+  if (M <= 1) return;
+  const int logM = 31 - __clz(M);
+  const int tx = threadIdx.x, nt = blockDim.x;
+  int L = 1;
+  if (logM & 1) {  // first single stage, half-length 1
+    for (int k = tx; k < (M >> 1); k += nt) {
+      const T2 u = x[2 * k], v = x[2 * k + 1];
+      x[2 * k] = cadd(u, v);
+      x[2 * k + 1] = csub(u, v);
     }
+    __syncthreads();
+    L = 2;
   }
-  __syncthreads();
-  fft_pow2(x, M, twid, Mtab);
-  for (int k = threadIdx.x; k < M; k += blockDim.x) x[k] = cconj(cmul(x[k], tw_cast<T2>(bhat[k])));
-  __syncthreads();
-  fft_pow2(x, M, twid, Mtab);
-  const auto inv = (decltype(x[0].x))1 / (decltype(x[0].x))M;
-  for (int k = threadIdx.x; k < h; k += blockDim.x) {
-    T2 c = tw_cast<T2>(ph[(2LL * k * k) % n2]);
-    T2 v = cconj(x[k]);
-    v.x *= inv;
-    v.y *= inv;
-    x[k] = cmul(v, c);
+  for (; L < M; L <<= 2) {  // stages L then 2L on {B + j + {0, L, 2L, 3L}}
+    for (int k = tx; k < (M >> 2); k += nt) {
+      const int j = k & (L - 1);
+      const int i0 = ((k - j) << 2) + j;
+      const T2 a0 = x[i0], a1 = x[i0 + L], a2 = x[i0 + 2 * L], a3 = x[i0 + 3 * L];
+      const T2 w1 = tws[L - 1 + j], w2 = tws[2 * L - 1 + j];
+      T2 v = cmul(a1, w1);
+      const T2 b0 = cadd(a0, v), b1 = csub(a0, v);
+      v = cmul(a3, w1);
+      const T2 b2 = cadd(a2, v), b3 = csub(a2, v);
+      v = cmul(b2, w2);
+      x[i0] = cadd(b0, v);
+      x[i0 + 2 * L] = csub(b0, v);
+      v = cmul_negi(cmul(b3, w2));
+      x[i0 + L] = cadd(b1, v);
+      x[i0 + 3 * L] = csub(b1, v);
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 }  // namespace dmwf

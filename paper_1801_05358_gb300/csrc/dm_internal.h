@@ -53,6 +53,13 @@ struct SolveState {
   int iters_per_level[DM_MAX_LEVELS];
 };
 
+// Rings of one launch of the ring kernel: ring_order[off .. off + count) with
+// FFT sizes up to M and ring lengths up to n.
+struct RingClass {
+  int off, count;
+  int M, n;
+};
+
 struct LevelDev {
   int n_levels;
   int max_iter;
@@ -88,7 +95,10 @@ struct dm_plan {
   dmwf::PairDev *pairs = nullptr;
   double2 *phase = nullptr;     // e^{-i pi q / n} tables
   double2 *bhat = nullptr;      // Bluestein kernel spectra
-  double2 *twid = nullptr;      // e^{-2 pi i k / fft_M_max}, k < fft_M_max / 2
+  double2 *twid = nullptr;      // stage twiddles: [len - 1 + j] = e^{-i pi j / len}, fft_M_max - 1 entries
+  int *ring_order = nullptr;    // [nrings] ring ids grouped by FFT size class
+  std::vector<int> ring_order_h;
+  std::vector<dmwf::RingClass> ring_classes;
   dmwf::RecCoef *rec = nullptr; // [nalm]
   double *seed = nullptr;       // [mmax+1][npairs][3] : lambda_mm, lp, lm at l0 = max(m, 2)
   int *seed_exp = nullptr;      // [mmax+1][npairs] : scale S (true = v 2^-S), 0 = plain
@@ -157,6 +167,8 @@ cudaError_t build_noise(dm_plan *p, int b, cudaStream_t st);    // alpha (reduct
 // ring stage: mode
 enum RingMode { RING_FWD_MAP = 0, RING_INV_MAP = 1, RING_ITER = 2, RING_INIT = 3 };
 cudaError_t ring_stage(dm_plan *p, int mode, const double *in_map, double *out_map, cudaStream_t st);
+// lanes per block of the ring kernel (1..4) for the given shared-memory words
+int ring_lanes_per_block(size_t word_bytes, int tw_words, int ph_words, int lane_words, int nlanes);
 // public-layout permutations of the ring coefficients
 cudaError_t rc_to_public(dm_plan *p, double2 *pub, cudaStream_t st);
 cudaError_t rc_from_public(dm_plan *p, const double2 *pub, cudaStream_t st);

@@ -1,5 +1,5 @@
 // dm_ring.cu -- the pixel-space half of a dual messenger iteration, one CTA per
-// (ring, Stokes component, RHS):
+// (ring, up to four (Stokes component, RHS) lanes):
 //   inverse ring DFT  F_m -> s           (synthesis F, Algorithm 1)
 //   Cauchy partials   ||s - s_prev||^2, ||s||^2   (stopping rule, Section 3.2)
 //   messenger update  t - s = w (d - s)           (Eq. 9, diagonal N)
@@ -19,16 +19,109 @@ __device__ __forceinline__ int64_t rc_index(int b, int f, int m, int mmax, int p
   return ((((int64_t)b * 3 + f) * (mmax + 1) + m) * npairs + pair) * 2 + side;
 }
 
+// e^{-i pi q / n} for 0 <= q < 2n from the quarter table Tq[r] = e^{-i pi r / n},
+// r <= n/2 (n = 4i is a multiple of 4): e^{-i pi q/n} = (-i)^quad Tq[q - quad n/2].
+template <typename C>
+__device__ __forceinline__ C phase_q(const C *Tq, int q, int n) {
+  const int hq = n >> 1;
+  int quad = 0;
+  if (q >= n) {
+    q -= n;
+    quad = 2;
+  }
+  if (q >= hq) {
+    q -= hq;
+    quad += 1;
+  }
+  const C v = Tq[q];
+  C r;
+  if (quad == 0) {
+    r = v;
+  } else if (quad == 1) {
+    r.x = v.y;
+    r.y = -v.x;
+  } else if (quad == 2) {
+    r.x = -v.x;
+    r.y = -v.y;
+  } else {
+    r.x = -v.y;
+    r.y = v.x;
+  }
+  return r;
+}
+
+// Fold F_m (m = -mmax..mmax, F_{-m} = conj F_m) into C_k = sum_{m = k mod n} F_m e^{i m phi0},
+// phi0 = pi shift / n.
+template <typename C>
+__device__ __forceinline__ C fold_one(const C *__restrict__ rc, const C *Tq, int k, int n, int shift, int mmax,
+                                      int64_t base, int64_t mstride) {
+  C acc;
+  acc.x = 0;
+  acc.y = 0;
+  const int n2 = 2 * n;
+  for (int m = k; m <= mmax; m += n) {
+    const C F = rc[base + (int64_t)m * mstride];
+    acc = cadd(acc, cmulc(F, phase_q(Tq, (m * shift) % n2, n)));
+  }
+  for (int m = n - k; m <= mmax; m += n) {
+    if (m < 1) continue;
+    const C F = rc[base + (int64_t)m * mstride];
+    acc = cadd(acc, cconj(cmulc(F, phase_q(Tq, (m * shift) % n2, n))));
+  }
+  return acc;
+}
+
+// Bluestein chirp c_j = e^{-i pi j^2 / h} = e^{-i pi (2 j^2 mod 2n) / n}, n = 2h
+template <typename C>
+__device__ __forceinline__ C chirp(const C *Tq, int j, int n) {
+  return phase_q(Tq, (int)((2LL * j * j) % (2LL * n)), n);
+}
+
+// Length-h forward DFT of the CTA's lanes in place.  Direct rings (h = M a
+// power of two): bit-reversed input -> natural output.  Bluestein rings:
+// natural input already multiplied by the chirp and zero-padded to M, DIF ->
+// pointwise product with the kernel spectrum (stored in bit-reversed order) ->
+// DIT; the caller applies conj(.) / M and the output chirp when it reads.
+template <typename C>
+__device__ __forceinline__ void ring_dft(C *buf, int M, int bluestein, const C *__restrict__ bhat, const C *tws) {
+  if (!bluestein) {
+    fft_dit(buf, M, tws);
+    return;
+  }
+  fft_dif(buf, M, tws);
+  for (int k = threadIdx.x; k < M; k += blockDim.x) buf[k] = cconj(cmul(buf[k], bhat[k]));
+  __syncthreads();
+  fft_dit(buf, M, tws);
+}
+
+// Output k of ring_dft (k < h)
+template <typename C>
+__device__ __forceinline__ C dft_out(const C *buf, int k, int bluestein, const C *Tq, int n, float invM_f,
+                                     double invM_d) {
+  C v = buf[k];
+  if (bluestein) {
+    v = cconj(v);
+    const auto inv = sizeof(v.x) == 4 ? (decltype(v.x))invM_f : (decltype(v.x))invM_d;
+    v.x *= inv;
+    v.y *= inv;
+    v = cmul(v, chirp(Tq, k, n));
+  }
+  return v;
+}
+
 // R: real type of the FFT and of the iteration maps (double or float); C its
 // complex type.  User maps (in_map, out_user) are always FP64.
-// Block = (blockDim.x threads per lane) x (blockDim.y lanes); the lanes are
-// consecutive (RHS, Stokes) pairs of the same ring, so every lane runs the
-// same FFT plan in lockstep and the block-wide barriers of the FFT stages are
-// shared by blockDim.y transforms.  Lanes of finished RHS compute in shared
-// memory but write nothing.
+// Grid.x walks a list of rings with the same FFT size class; block =
+// (blockDim.x threads per lane) x (blockDim.y lanes).  The lanes of a block are
+// consecutive (RHS, Stokes) pairs of the same ring, so they run the same FFT in
+// lockstep and share the ring's twiddles and quarter phase table in shared
+// memory.  A lane works in place on M + 1 entries: the real-FFT packing and
+// unpacking handle k and h - k in the same thread.  Lanes of finished RHS
+// compute but write nothing.
 template <typename R, typename C, int MODE>
-__global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings, const C *__restrict__ phase,
-                                              const C *__restrict__ bhat, const C *__restrict__ twid, int Mtab,
+__global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings, const int *__restrict__ order,
+                                              const C *__restrict__ phase, const C *__restrict__ bhat,
+                                              const C *__restrict__ twid, int tw_words, int ph_words,
                                               int lane_words, int nlanes, C *__restrict__ rc, int mmax, int npairs,
                                               int64_t npix, int nrings, const double *__restrict__ in_map,
                                               double *__restrict__ out_user, R *s_state, const R *__restrict__ w,
@@ -36,8 +129,8 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
                                               const SolveState *__restrict__ state,
                                               const R *__restrict__ s_anchor) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ double red[8][16][2];
-  const int r = blockIdx.x;
+  __shared__ double red[4][16][2];
+  const int r = order[blockIdx.x];
   const int g = threadIdx.y;
   const int L = blockIdx.y * blockDim.y + g;
   const bool valid = L < nlanes;
@@ -45,56 +138,60 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
   bool live = valid;
   if ((MODE == RING_ITER || MODE == RING_INIT) && state != nullptr && valid && state[b].done) live = false;
   if (!__syncthreads_or(live)) return;
-  C *sm = reinterpret_cast<C *>(sm_raw) + (size_t)g * lane_words;
   const RingDev Rg = rings[r];
-  const int n = Rg.n, h = Rg.h;
-  const int64_t n2 = 2LL * n;
-  const C *ph = phase + Rg.ph_off;  // e^{-i pi q / n}, q < 2n
-  C *buf = sm;                      // FFT work area, M entries
-  C *cb = sm + Rg.M;                // h + 1 spectrum entries
-  const int64_t moff = ((int64_t)b * 3 + f) * npix + Rg.start;
-  const C *bh = bhat + (Rg.bh_off < 0 ? 0 : Rg.bh_off);
+  const int n = Rg.n, h = Rg.h, M = Rg.M, bl = Rg.bluestein;
+  const int logM = 31 - __clz(M);
+  C *tws = reinterpret_cast<C *>(sm_raw);  // stage twiddles (M - 1 used)
+  C *Tq = tws + tw_words;                  // quarter phase table (n/2 + 1 used)
+  C *buf = Tq + ph_words + (size_t)g * lane_words;
   const int tx = threadIdx.x, nt = blockDim.x;
+  {
+    const int tflat = threadIdx.y * nt + tx, nflat = nt * blockDim.y;
+    for (int i = tflat; i < M - 1; i += nflat) tws[i] = twid[i];
+    const C *ph = phase + Rg.ph_off;
+    for (int i = tflat; i <= (n >> 1); i += nflat) Tq[i] = ph[i];
+  }
+  const int64_t moff = ((int64_t)b * 3 + f) * npix + Rg.start;
+  const C *bh = bhat + (bl ? Rg.bh_off : 0);
+  const int64_t rbase = ((((int64_t)b * 3 + f) * (mmax + 1)) * npairs + Rg.pair) * 2 + Rg.side;
+  const int64_t mstride = (int64_t)npairs * 2;
+  const float invM_f = 1.0f / (float)M;
+  const double invM_d = 1.0 / (double)M;
+  __syncthreads();
 
   if (MODE == RING_INV_MAP || MODE == RING_ITER) {
-    // Fold F_m (m = -mmax..mmax, F_{-m} = conj F_m) into C_k = sum_{m = k mod n} F_m e^{i m phi0}, k <= h.
-    for (int k = tx; k <= h; k += nt) {
-      C acc;
-      acc.x = 0;
-      acc.y = 0;
-      for (int m = k; m <= mmax; m += n) {
-        C F = rc[rc_index(b, f, m, mmax, Rg.pair, npairs, Rg.side)];
-        C e = cconj(ph[((int64_t)m * Rg.shift) % n2]);
-        acc = cadd(acc, cmul(F, e));
+    // Z_k = E_k + i O_k, E_k = C_k + conj(C_{h-k}), O_k = (C_k - conj(C_{h-k})) e^{2 pi i k/n},
+    // stored conjugated (forward DFT + conjugation = inverse); one thread per (k, h - k).
+    for (int k = tx; k <= (h >> 1); k += nt) {
+      const int k2 = h - k;
+      const C ck = fold_one(rc, Tq, k, n, Rg.shift, mmax, rbase, mstride);
+      const C ck2 = (k2 == k) ? ck : fold_one(rc, Tq, k2, n, Rg.shift, mmax, rbase, mstride);
+      for (int t = 0; t < 2; ++t) {
+        const int kk = t ? k2 : k;
+        if (t && (k2 >= h || k2 == k)) break;
+        const C a = t ? ck2 : ck, cc = cconj(t ? ck : ck2);
+        const C E = cadd(a, cc), O = cmulc(csub(a, cc), phase_q(Tq, 2 * kk, n));
+        C Z;  // conj(E + i O)
+        Z.x = E.x - O.y;
+        Z.y = -(E.y + O.x);
+        if (bl)
+          buf[kk] = cmul(Z, chirp(Tq, kk, n));
+        else
+          buf[bitrev(kk, logM)] = Z;
       }
-      for (int m = n - k; m <= mmax; m += n) {
-        if (m < 1) continue;
-        C F = rc[rc_index(b, f, m, mmax, Rg.pair, npairs, Rg.side)];
-        C e = cconj(ph[((int64_t)m * Rg.shift) % n2]);
-        acc = cadd(acc, cconj(cmul(F, e)));
+    }
+    if (bl)
+      for (int j = h + tx; j < M; j += nt) {
+        buf[j].x = 0;
+        buf[j].y = 0;
       }
-      cb[k] = acc;
-    }
     __syncthreads();
-    // Pack for the half-length inverse: Z_k = E_k + i O_k with
-    // E_k = C_k + conj(C_{h-k}),  O_k = (C_k - conj(C_{h-k})) e^{2 pi i k/n}; stored conjugated
-    // so that a forward FFT followed by conjugation gives the inverse.
-    for (int k = tx; k < h; k += nt) {
-      C ck = cb[k], cc = cconj(cb[h - k]);
-      C E = cadd(ck, cc);
-      C O = cmul(csub(ck, cc), cconj(ph[2 * k]));
-      C Z;
-      Z.x = E.x - O.y;
-      Z.y = E.y + O.x;
-      buf[k] = cconj(Z);
-    }
-    __syncthreads();
-    dft_forward(buf, h, Rg.M, Rg.bluestein, ph, bh, twid, Mtab);
-    // z_j = conj(buf_j) = s_{2j} + i s_{2j+1}
+    ring_dft(buf, M, bl, bh, tws);
+    // z_j = conj(D_j) = s_{2j} + i s_{2j+1}
     if (MODE == RING_INV_MAP) {
       if (live)
         for (int j = tx; j < h; j += nt) {
-          C z = buf[j];
+          const C z = dft_out(buf, j, bl, Tq, n, invM_f, invM_d);
           out_user[moff + 2 * j] = (double)z.x;
           out_user[moff + 2 * j + 1] = -(double)z.y;
         }
@@ -104,14 +201,14 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
     // With an anchor (mixed precision) the state is Y e, s = s_anchor + Y e, and
     // the data part w (d - s_anchor) is carried in FP64 by the anchor: r = -w Y e.
     double dd = 0.0, ss = 0.0;
-    const int64_t wo = moff;  // per-RHS weights share the map layout
+    // every thread reads and rewrites its own entries j only
     for (int j = tx; j < h; j += nt) {
-      C z = buf[j];
-      R s0 = z.x, s1 = -z.y;
+      const C z = dft_out(buf, j, bl, Tq, n, invM_f, invM_d);
+      const R s0 = z.x, s1 = -z.y;
       C rr;
       if (live) {
-        R o0 = s_state[moff + 2 * j], o1 = s_state[moff + 2 * j + 1];
-        double d0 = (double)s0 - (double)o0, d1 = (double)s1 - (double)o1;
+        const R o0 = s_state[moff + 2 * j], o1 = s_state[moff + 2 * j + 1];
+        const double d0 = (double)s0 - (double)o0, d1 = (double)s1 - (double)o1;
         dd += d0 * d0 + d1 * d1;
         s_state[moff + 2 * j] = s0;
         s_state[moff + 2 * j + 1] = s1;
@@ -119,20 +216,19 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
           const double f0 = (double)s_anchor[moff + 2 * j] + (double)s0;
           const double f1 = (double)s_anchor[moff + 2 * j + 1] + (double)s1;
           ss += f0 * f0 + f1 * f1;
-          rr.x = -w[wo + 2 * j] * s0;
-          rr.y = -w[wo + 2 * j + 1] * s1;
+          rr.x = -w[moff + 2 * j] * s0;
+          rr.y = -w[moff + 2 * j + 1] * s1;
         } else {
           ss += (double)s0 * (double)s0 + (double)s1 * (double)s1;
-          rr.x = wd[moff + 2 * j] - w[wo + 2 * j] * s0;
-          rr.y = wd[moff + 2 * j + 1] - w[wo + 2 * j + 1] * s1;
+          rr.x = wd[moff + 2 * j] - w[moff + 2 * j] * s0;
+          rr.y = wd[moff + 2 * j + 1] - w[moff + 2 * j + 1] * s1;
         }
       } else {
         rr.x = 0;
         rr.y = 0;
       }
-      buf[j] = rr;
+      buf[j] = bl ? cmul(rr, chirp(Tq, j, n)) : rr;
     }
-    // per-lane reduction of (dd, ss): warps never straddle lanes (blockDim.x % 32 == 0)
     for (int o = 16; o > 0; o >>= 1) {
       dd += __shfl_down_sync(0xffffffffu, dd, o);
       ss += __shfl_down_sync(0xffffffffu, ss, o);
@@ -148,75 +244,123 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
         a += red[g][i][0];
         c += red[g][i][1];
       }
-      int64_t no = (((int64_t)b * 3 + f) * nrings + r) * 2;
+      const int64_t no = (((int64_t)b * 3 + f) * nrings + r) * 2;
       norms[no] = a;
       norms[no + 1] = c;
     }
   } else {
     // forward only: load the real ring (RING_INIT: t_0 - s_0 = d on observed pixels)
-    const int64_t wo = moff;
     for (int j = tx; j < h; j += nt) {
       double x0 = 0.0, x1 = 0.0;
       if (valid) {
         x0 = in_map[moff + 2 * j];
         x1 = in_map[moff + 2 * j + 1];
         if (MODE == RING_INIT) {
-          x0 = (w[wo + 2 * j] > (R)0) ? x0 : 0.0;
-          x1 = (w[wo + 2 * j + 1] > (R)0) ? x1 : 0.0;
+          x0 = (w[moff + 2 * j] > (R)0) ? x0 : 0.0;
+          x1 = (w[moff + 2 * j + 1] > (R)0) ? x1 : 0.0;
         }
       }
       C v;
       v.x = (R)x0;
       v.y = (R)x1;
-      buf[j] = v;
+      buf[j] = bl ? cmul(v, chirp(Tq, j, n)) : v;
+    }
+  }
+  if (bl)
+    for (int j = h + tx; j < M; j += nt) {
+      buf[j].x = 0;
+      buf[j].y = 0;
+    }
+  __syncthreads();
+  // forward: Z = DFT_h(z); direct rings take natural input to bit-reversed output
+  if (bl)
+    ring_dft(buf, M, 1, bh, tws);
+  else
+    fft_dif(buf, M, tws);
+  // X_k = E_k + e^{-2 pi i k/n} O_k, E_k = (Z_k + conj Z_{h-k}) / 2, O_k = (Z_k - conj Z_{h-k}) / 2i,
+  // Z_h = Z_0; each thread reads and rewrites the slots of k and h - k; X_h goes to slot M (direct)
+  // or slot h (Bluestein).
+  const R half = (R)0.5;
+  for (int k = tx; k <= (h >> 1); k += nt) {
+    const int k2 = h - k;
+    const int sk = bl ? k : bitrev(k, logM);
+    const int sk2 = (k == 0) ? sk : (bl ? k2 : bitrev(k2, logM));
+    const C zk = dft_out(buf, sk, bl, Tq, n, invM_f, invM_d);
+    const C zk2 = (k == 0) ? zk : dft_out(buf, sk2, bl, Tq, n, invM_f, invM_d);
+    for (int t = 0; t < 2; ++t) {
+      if (t && k2 == k) break;
+      const C a = t ? zk2 : zk, c = cconj(t ? zk : zk2);
+      const int kk = t ? k2 : k;
+      C E, O;
+      E.x = half * (a.x + c.x);
+      E.y = half * (a.y + c.y);
+      const C D = csub(a, c);
+      O.x = half * D.y;
+      O.y = -half * D.x;
+      const C X = cadd(E, cmul(O, phase_q(Tq, 2 * kk, n)));
+      const int slot = t ? ((k == 0) ? (bl ? h : M) : sk2) : sk;
+      buf[slot] = X;
     }
   }
   __syncthreads();
-  // forward: Z = FFT_h(z), X_k = E_k + e^{-2 pi i k/n} O_k, k = 0..h
-  dft_forward(buf, h, Rg.M, Rg.bluestein, ph, bh, twid, Mtab);
-  const R half = (R)0.5;
-  for (int k = tx; k <= h; k += nt) {
-    C zk = buf[k == h ? 0 : k], zc = cconj(buf[k == 0 ? 0 : h - k]);
-    if (k == h) zc = cconj(buf[0]);
-    C E, O;
-    E.x = half * (zk.x + zc.x);
-    E.y = half * (zk.y + zc.y);
-    C D = csub(zk, zc);  // = 2i O_k
-    O.x = half * D.y;
-    O.y = -half * D.x;   // D / (2i)
-    cb[k] = cadd(E, cmul(O, ph[2 * k]));
-  }
-  __syncthreads();
   if (!live) return;
+  const int n2 = 2 * n;
   for (int m = tx; m <= mmax; m += nt) {
-    int q = m % n;
-    C X = (q <= h) ? cb[q] : cconj(cb[n - q]);
-    rc[rc_index(b, f, m, mmax, Rg.pair, npairs, Rg.side)] = cmul(X, ph[((int64_t)m * Rg.shift) % n2]);
+    const int q = m % n;
+    const int qq = (q <= h) ? q : n - q;
+    const int slot = bl ? qq : (qq == h ? M : bitrev(qq, logM));
+    C X = buf[slot];
+    if (q > h) X = cconj(X);
+    rc[rbase + (int64_t)m * mstride] = cmul(X, phase_q(Tq, (m * Rg.shift) % n2, n));
   }
 }
 
+// Rings are launched by size class: one grid per class so that each gets the
+// shared memory (twiddles, quarter phase table, G lanes of M + 1 entries) it needs.
 template <typename R, typename C, int MODE>
 static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const C *twid, C *rc,
                                const double *in_map, double *out_user, R *s_state, const R *w, const R *wd,
                                cudaStream_t st, const R *s_anchor = nullptr) {
-  int hmax = 0;
-  for (const RingDev &Rg : p->rings_h) hmax = Rg.h > hmax ? Rg.h : hmax;
-  int lane_words = 0;
-  for (const RingDev &Rg : p->rings_h) lane_words = std::max(lane_words, Rg.M + Rg.h + 1);
   const int nlanes = 3 * p->batch;
-  const size_t lane_bytes = sizeof(C) * (size_t)lane_words;
-  int G = (int)std::max<size_t>(1, std::min<size_t>(4, (100u << 10) / lane_bytes));
-  G = std::min(G, nlanes);
-  const int T = 128;
-  dim3 grid(p->nrings, (nlanes + G - 1) / G);
-  dim3 block(T, G);
-  size_t smem = lane_bytes * G;
   const SolveState *stp = (MODE == RING_ITER || MODE == RING_INIT) ? p->state : nullptr;
-  cudaFuncSetAttribute(k_ring<R, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_ring<R, C, MODE><<<grid, block, smem, st>>>(p->rings, phase, bhat, twid, p->fft_M_max, lane_words, nlanes, rc,
-                                                p->mmax, p->npairs, p->npix, p->nrings, in_map, out_user, s_state, w,
-                                                wd, p->norms, stp, s_anchor);
-  return cudaGetLastError();
+  const int T = 128;
+  for (const RingClass &rc_cls : p->ring_classes) {
+    const int tw_words = std::max(1, rc_cls.M - 1);
+    const int ph_words = rc_cls.n / 2 + 1;
+    const int lane_words = rc_cls.M + 1;
+    int G = ring_lanes_per_block(sizeof(C), tw_words, ph_words, lane_words, nlanes);
+    const size_t smem = sizeof(C) * ((size_t)tw_words + ph_words + (size_t)G * lane_words);
+    dim3 grid(rc_cls.count, (nlanes + G - 1) / G);
+    dim3 block(T, G);
+    cudaError_t e = cudaFuncSetAttribute(k_ring<R, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_ring<R, C, MODE><<<grid, block, smem, st>>>(p->rings, p->ring_order + rc_cls.off, phase, bhat, twid,
+                                                  tw_words, ph_words, lane_words, nlanes, rc, p->mmax, p->npairs,
+                                                  p->npix, p->nrings, in_map, out_user, s_state, w, wd, p->norms,
+                                                  stp, s_anchor);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Lanes per block: the G in 1..4 that keeps the most lanes resident on an SM
+// (228 KB of shared memory, 1 KB reserved per block, 2048 threads), ties to
+// the larger G.
+int ring_lanes_per_block(size_t word_bytes, int tw_words, int ph_words, int lane_words, int nlanes) {
+  int best = 1;
+  long best_lanes = -1;
+  for (int G = 1; G <= 4; ++G) {
+    const size_t smem = word_bytes * ((size_t)tw_words + ph_words + (size_t)G * lane_words);
+    if (smem > (227u << 10)) break;
+    long blocks = (long)((228u << 10) / (smem + 1024));
+    blocks = std::min<long>(blocks, 2048 / (128 * G));
+    const long lanes = blocks * G;
+    if (lanes >= best_lanes) {
+      best_lanes = lanes;
+      best = G;
+    }
+  }
+  return std::max(1, std::min(best, nlanes));
 }
 
 // FP64 maps for the user-facing modes; the iteration state is s_iter (FP64:

@@ -4,6 +4,8 @@
 // w = alpha / N (Section 2, Appendix B).
 #include <math.h>
 
+#include <algorithm>
+
 #include "dm_fft.cuh"
 #include "dm_internal.h"
 
@@ -41,18 +43,22 @@ __global__ void k_phase(double2 *ph, int nside) {
   }
 }
 
+// Stage twiddles: tw[len - 1 + j] = e^{-i pi j / len}, len = 1, 2, 4, ..., Mtab / 2.
 __global__ void k_twiddle(double2 *tw, int Mtab) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= Mtab / 2) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Mtab - 1) return;
+  const int len = 1 << (31 - __clz(i + 1));
+  const int j = i + 1 - len;
   double s, c;
-  sincospi(-2.0 * (double)k / (double)Mtab, &s, &c);
-  tw[k] = make_double2(c, s);
+  sincospi(-(double)j / (double)len, &s, &c);
+  tw[i] = make_double2(c, s);
 }
 
 // Bluestein kernel spectrum for one ring length: FFT_M of b_j = e^{+i pi j^2/h}
-// placed at j and M - j (|j| < h), zero elsewhere.
+// placed at j and M - j (|j| < h), zero elsewhere, stored in bit-reversed order
+// (the order in which the ring kernel's DIF transform leaves its data).
 __global__ void k_bhat(const RingDev *rings, const int *ring_ids, const double2 *ph, double2 *bhat,
-                       const double2 *twid, int Mtab) {
+                       const double2 *twid) {
   extern __shared__ double2 sm_b[];
   RingDev R = rings[ring_ids[blockIdx.x]];
   const double2 *p = ph + R.ph_off;
@@ -67,7 +73,7 @@ __global__ void k_bhat(const RingDev *rings, const int *ring_ids, const double2 
     if (j > 0) sm_b[M - j] = b;
   }
   __syncthreads();
-  fft_pow2(sm_b, M, twid, Mtab);
+  fft_dif(sm_b, M, twid);
   for (int k = threadIdx.x; k < M; k += blockDim.x) bhat[R.bh_off + k] = sm_b[k];
 }
 
@@ -316,12 +322,35 @@ cudaError_t build_tables(dm_plan *p) {
     }
     R.bh_off = bl_off_by_rad[rad];
   }
+  // Size classes of the ring kernel: rings sorted by FFT size M (largest first),
+  // one class per M, the rings with M <= 256 together.
+  {
+    std::vector<int> ids(p->nrings);
+    for (int r = 0; r < p->nrings; ++r) ids[r] = r;
+    std::stable_sort(ids.begin(), ids.end(),
+                     [&](int a, int b) { return p->rings_h[a].M > p->rings_h[b].M; });
+    p->ring_classes.clear();
+    int last_key = -1;
+    for (int i = 0; i < p->nrings; ++i) {
+      const RingDev &R = p->rings_h[ids[i]];
+      const int key = R.M > 256 ? R.M : 256;
+      if (key != last_key) {
+        p->ring_classes.push_back(RingClass{i, 0, R.M, R.n});
+        last_key = key;
+      }
+      RingClass &c = p->ring_classes.back();
+      ++c.count;
+      c.M = std::max(c.M, R.M);
+      c.n = std::max(c.n, R.n);
+    }
+    p->ring_order_h = ids;
+  }
   cudaError_t e;
   size_t ph_n = 4ull * ns * (ns + 1);
   if ((e = cudaMalloc(&p->rings, sizeof(RingDev) * p->nrings))) return e;
   if ((e = cudaMalloc(&p->pairs, sizeof(PairDev) * p->npairs))) return e;
   if ((e = cudaMalloc(&p->phase, sizeof(double2) * ph_n))) return e;
-  if ((e = cudaMalloc(&p->twid, sizeof(double2) * (p->fft_M_max / 2)))) return e;
+  if ((e = cudaMalloc(&p->twid, sizeof(double2) * (p->fft_M_max - 1)))) return e;
   if ((e = cudaMalloc(&p->bhat, sizeof(double2) * (bh_total > 0 ? bh_total : 1)))) return e;
   p->bh_total = bh_total;
   p->ph_total = (int64_t)ph_n;
@@ -330,21 +359,24 @@ cudaError_t build_tables(dm_plan *p) {
   if ((e = cudaMalloc(&p->seed, sizeof(double) * 3 * nseed))) return e;
   if ((e = cudaMalloc(&p->seed_exp, sizeof(int) * nseed))) return e;
   p->bytes += sizeof(RingDev) * p->nrings + sizeof(PairDev) * p->npairs + sizeof(double2) * ph_n +
-              sizeof(double2) * (p->fft_M_max / 2 + bh_total) + sizeof(RecCoef) * (p->nalm + 1) +
+              sizeof(double2) * (p->fft_M_max - 1 + bh_total) + sizeof(RecCoef) * (p->nalm + 1) +
               (sizeof(double) * 3 + sizeof(int)) * nseed;
   if ((e = cudaMemcpy(p->rings, p->rings_h.data(), sizeof(RingDev) * p->nrings, cudaMemcpyHostToDevice)))
+    return e;
+  if ((e = cudaMalloc(&p->ring_order, sizeof(int) * p->nrings))) return e;
+  if ((e = cudaMemcpy(p->ring_order, p->ring_order_h.data(), sizeof(int) * p->nrings, cudaMemcpyHostToDevice)))
     return e;
   cudaMemset(p->rec, 0, sizeof(RecCoef) * (p->nalm + 1));
   k_pairs<<<(p->npairs + 127) / 128, 128>>>(p->pairs, ns, p->npairs);
   k_phase<<<dim3(8, ns), 256>>>(p->phase, ns);
-  k_twiddle<<<(p->fft_M_max / 2 + 255) / 256, 256>>>(p->twid, p->fft_M_max);
+  k_twiddle<<<(p->fft_M_max - 1 + 255) / 256, 256>>>(p->twid, p->fft_M_max);
   if (!bl_ring.empty()) {
     int *ids;
     if ((e = cudaMalloc(&ids, sizeof(int) * bl_ring.size()))) return e;
     cudaMemcpy(ids, bl_ring.data(), sizeof(int) * bl_ring.size(), cudaMemcpyHostToDevice);
     size_t smem = sizeof(double2) * p->fft_M_max;
     cudaFuncSetAttribute(k_bhat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_bhat<<<(unsigned)bl_ring.size(), 256, smem>>>(p->rings, ids, p->phase, p->bhat, p->twid, p->fft_M_max);
+    k_bhat<<<(unsigned)bl_ring.size(), 256, smem>>>(p->rings, ids, p->phase, p->bhat, p->twid);
     e = cudaDeviceSynchronize();
     cudaFree(ids);
     if (e) return e;
@@ -377,7 +409,7 @@ cudaError_t setup_fp32(dm_plan *p) {
   };
   if ((e = al(&p->phase32, p->ph_total))) return e;
   if ((e = al(&p->bhat32, p->bh_total))) return e;
-  if ((e = al(&p->twid32, p->fft_M_max / 2))) return e;
+  if ((e = al(&p->twid32, p->fft_M_max - 1))) return e;
   if ((e = al(&p->ptab, (size_t)3 * p->nalm * p->npairs))) return e;
   if ((e = al(&p->rc32, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return e;
   if ((e = al(&p->apart32, (size_t)B * p->nchunk * 3 * p->nalm))) return e;
@@ -392,7 +424,7 @@ cudaError_t setup_fp32(dm_plan *p) {
   cudaMemset(p->rc32, 0, sizeof(float2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
   k_d2f2<<<512, 256>>>(p->phase, p->phase32, p->ph_total);
   if (p->bh_total > 0) k_d2f2<<<512, 256>>>(p->bhat, p->bhat32, p->bh_total);
-  k_d2f2<<<64, 256>>>(p->twid, p->twid32, p->fft_M_max / 2);
+  k_d2f2<<<64, 256>>>(p->twid, p->twid32, p->fft_M_max - 1);
   if ((e = gen_tables32(p))) return e;
   return cudaDeviceSynchronize();
 }
