@@ -50,24 +50,16 @@ __device__ __forceinline__ C phase_q(const C *Tq, int q, int n) {
   return r;
 }
 
-// Fold F_m (m = -mmax..mmax, F_{-m} = conj F_m) into C_k = sum_{m = k mod n} F_m e^{i m phi0},
-// phi0 = pi shift / n.
+// Fold the staged S_m = F_m e^{i m phi0} (m = 0..mmax; F_{-m} = conj F_m) into
+// C_k = sum_{m = k mod n, |m| <= mmax} F_m e^{i m phi0}.
 template <typename C>
-__device__ __forceinline__ C fold_one(const C *__restrict__ rc, const C *Tq, int k, int n, int shift, int mmax,
-                                      int64_t base, int64_t mstride) {
+__device__ __forceinline__ C fold_one(const C *S, int k, int n, int mmax) {
   C acc;
   acc.x = 0;
   acc.y = 0;
-  const int n2 = 2 * n;
-  for (int m = k; m <= mmax; m += n) {
-    const C F = rc[base + (int64_t)m * mstride];
-    acc = cadd(acc, cmulc(F, phase_q(Tq, (m * shift) % n2, n)));
-  }
-  for (int m = n - k; m <= mmax; m += n) {
-    if (m < 1) continue;
-    const C F = rc[base + (int64_t)m * mstride];
-    acc = cadd(acc, cconj(cmulc(F, phase_q(Tq, (m * shift) % n2, n))));
-  }
+  for (int m = k; m <= mmax; m += n) acc = cadd(acc, S[m]);
+  for (int m = n - k; m <= mmax; m += n)
+    if (m >= 1) acc = cadd(acc, cconj(S[m]));
   return acc;
 }
 
@@ -122,7 +114,8 @@ template <typename R, typename C, int MODE>
 __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings, const int *__restrict__ order,
                                               const C *__restrict__ phase, const C *__restrict__ bhat,
                                               const C *__restrict__ twid, int tw_words, int ph_words,
-                                              int lane_words, int nlanes, C *__restrict__ rc, int mmax, int npairs,
+                                              int buf_words, int lane_words, int nlanes, C *__restrict__ rc,
+                                              int mmax, int npairs,
                                               int64_t npix, int nrings, const double *__restrict__ in_map,
                                               double *__restrict__ out_user, R *s_state, const R *__restrict__ w,
                                               const R *__restrict__ wd, double *__restrict__ norms,
@@ -143,7 +136,8 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
   const int logM = 31 - __clz(M);
   C *tws = reinterpret_cast<C *>(sm_raw);  // stage twiddles (M - 1 used)
   C *Tq = tws + tw_words;                  // quarter phase table (n/2 + 1 used)
-  C *buf = Tq + ph_words + (size_t)g * lane_words;
+  C *buf = Tq + ph_words + (size_t)g * lane_words;  // M + 1 entries
+  C *S = buf + buf_words;                            // mmax + 1 staged coefficients (inverse modes)
   const int tx = threadIdx.x, nt = blockDim.x;
   {
     const int tflat = threadIdx.y * nt + tx, nflat = nt * blockDim.y;
@@ -162,10 +156,29 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
   if (MODE == RING_INV_MAP || MODE == RING_ITER) {
     // Z_k = E_k + i O_k, E_k = C_k + conj(C_{h-k}), O_k = (C_k - conj(C_{h-k})) e^{2 pi i k/n},
     // stored conjugated (forward DFT + conjugation = inverse); one thread per (k, h - k).
+    // stage S_m = F_m e^{i m phi0}: batches of independent loads per thread
+    {
+      constexpr int U = sizeof(R) == 4 ? 8 : 4;
+      const int n2 = 2 * n;
+      for (int m0 = tx; m0 <= mmax; m0 += U * nt) {
+        C v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int m = m0 + u * nt;
+          if (m <= mmax) v[u] = rc[rbase + (int64_t)m * mstride];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int m = m0 + u * nt;
+          if (m <= mmax) S[m] = cmulc(v[u], phase_q(Tq, (m * Rg.shift) % n2, n));
+        }
+      }
+    }
+    __syncthreads();
     for (int k = tx; k <= (h >> 1); k += nt) {
       const int k2 = h - k;
-      const C ck = fold_one(rc, Tq, k, n, Rg.shift, mmax, rbase, mstride);
-      const C ck2 = (k2 == k) ? ck : fold_one(rc, Tq, k2, n, Rg.shift, mmax, rbase, mstride);
+      const C ck = fold_one(S, k, n, mmax);
+      const C ck2 = (k2 == k) ? ck : fold_one(S, k2, n, mmax);
       for (int t = 0; t < 2; ++t) {
         const int kk = t ? k2 : k;
         if (t && (k2 >= h || k2 == k)) break;
@@ -201,33 +214,55 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
     // With an anchor (mixed precision) the state is Y e, s = s_anchor + Y e, and
     // the data part w (d - s_anchor) is carried in FP64 by the anchor: r = -w Y e.
     double dd = 0.0, ss = 0.0;
-    // every thread reads and rewrites its own entries j only
-    for (int j = tx; j < h; j += nt) {
-      const C z = dft_out(buf, j, bl, Tq, n, invM_f, invM_d);
-      const R s0 = z.x, s1 = -z.y;
-      C rr;
-      if (live) {
-        const R o0 = s_state[moff + 2 * j], o1 = s_state[moff + 2 * j + 1];
-        const double d0 = (double)s0 - (double)o0, d1 = (double)s1 - (double)o1;
-        dd += d0 * d0 + d1 * d1;
-        s_state[moff + 2 * j] = s0;
-        s_state[moff + 2 * j + 1] = s1;
-        if (s_anchor != nullptr) {
-          const double f0 = (double)s_anchor[moff + 2 * j] + (double)s0;
-          const double f1 = (double)s_anchor[moff + 2 * j + 1] + (double)s1;
-          ss += f0 * f0 + f1 * f1;
-          rr.x = -w[moff + 2 * j] * s0;
-          rr.y = -w[moff + 2 * j + 1] * s1;
-        } else {
-          ss += (double)s0 * (double)s0 + (double)s1 * (double)s1;
-          rr.x = wd[moff + 2 * j] - w[moff + 2 * j] * s0;
-          rr.y = wd[moff + 2 * j + 1] - w[moff + 2 * j + 1] * s1;
+    // every thread reads and rewrites its own entries j only; plan-owned maps,
+    // (s_{2j}, s_{2j+1}) read as one aligned pair, two j per batch
+    C *sv = reinterpret_cast<C *>(s_state + moff);
+    const C *wv = reinterpret_cast<const C *>(w + moff);
+    const C *dv = reinterpret_cast<const C *>(wd + moff);
+    const C *av = s_anchor ? reinterpret_cast<const C *>(s_anchor + moff) : nullptr;
+    for (int j0 = tx; j0 < h; j0 += 2 * nt) {
+      C so[2], ww[2], dw[2], sa[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int j = j0 + u * nt;
+        if (live && j < h) {
+          so[u] = sv[j];
+          ww[u] = wv[j];
+          if (av)
+            sa[u] = av[j];
+          else
+            dw[u] = dv[j];
         }
-      } else {
-        rr.x = 0;
-        rr.y = 0;
       }
-      buf[j] = bl ? cmul(rr, chirp(Tq, j, n)) : rr;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int j = j0 + u * nt;
+        if (j >= h) break;
+        const C z = dft_out(buf, j, bl, Tq, n, invM_f, invM_d);
+        C s;
+        s.x = z.x;
+        s.y = -z.y;
+        C rr;
+        if (live) {
+          const double d0 = (double)s.x - (double)so[u].x, d1 = (double)s.y - (double)so[u].y;
+          dd += d0 * d0 + d1 * d1;
+          sv[j] = s;
+          if (av) {
+            const double f0 = (double)sa[u].x + (double)s.x, f1 = (double)sa[u].y + (double)s.y;
+            ss += f0 * f0 + f1 * f1;
+            rr.x = -ww[u].x * s.x;
+            rr.y = -ww[u].y * s.y;
+          } else {
+            ss += (double)s.x * (double)s.x + (double)s.y * (double)s.y;
+            rr.x = dw[u].x - ww[u].x * s.x;
+            rr.y = dw[u].y - ww[u].y * s.y;
+          }
+        } else {
+          rr.x = 0;
+          rr.y = 0;
+        }
+        buf[j] = bl ? cmul(rr, chirp(Tq, j, n)) : rr;
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
       dd += __shfl_down_sync(0xffffffffu, dd, o);
@@ -327,7 +362,9 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
   for (const RingClass &rc_cls : p->ring_classes) {
     const int tw_words = std::max(1, rc_cls.M - 1);
     const int ph_words = rc_cls.n / 2 + 1;
-    const int lane_words = rc_cls.M + 1;
+    const int buf_words = rc_cls.M + 1;
+    const bool staged = (MODE == RING_ITER || MODE == RING_INV_MAP);
+    const int lane_words = buf_words + (staged ? p->mmax + 1 : 0);
     int G = ring_lanes_per_block(sizeof(C), tw_words, ph_words, lane_words, nlanes);
     const size_t smem = sizeof(C) * ((size_t)tw_words + ph_words + (size_t)G * lane_words);
     dim3 grid(rc_cls.count, (nlanes + G - 1) / G);
@@ -335,7 +372,8 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
     cudaError_t e = cudaFuncSetAttribute(k_ring<R, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_ring<R, C, MODE><<<grid, block, smem, st>>>(p->rings, p->ring_order + rc_cls.off, phase, bhat, twid,
-                                                  tw_words, ph_words, lane_words, nlanes, rc, p->mmax, p->npairs,
+                                                  tw_words, ph_words, buf_words, lane_words, nlanes, rc, p->mmax,
+                                                  p->npairs,
                                                   p->npix, p->nrings, in_map, out_user, s_state, w, wd, p->norms,
                                                   stp, s_anchor);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
