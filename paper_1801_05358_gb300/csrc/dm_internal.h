@@ -143,6 +143,10 @@ struct dm_plan {
   int anchor_every = 256;
   bool use_tc = true;           // tcgen05 Legendre stages when the batch allows
   int *tc_err = nullptr;        // device flag: a bounded tensor-core wait gave up
+  // tiled BF16 hi/lo copies of ptab for the tensor-core stages ([0] = lambda, [1] = lam+/lam-)
+  unsigned char *tc_synA[2] = {nullptr, nullptr}, *tc_anaA[2] = {nullptr, nullptr};
+  int64_t *tc_soff = nullptr, *tc_aoff = nullptr;  // block offsets per m / per (m, parity)
+  unsigned char *tc_synB[2] = {nullptr, nullptr};   // per-iteration synthesis B operand tiles
   // solve session (dm_solve_begin / iterate / end)
   double *s64 = nullptr;        // [B][3][npix] FP64 iterate s (FP64 mode) / Y a_hi (mixed)
   double *rhi = nullptr;        // [B][3][npix] FP64 anchor residual w (d - Y a_hi)
@@ -168,7 +172,7 @@ cudaError_t build_noise(dm_plan *p, int b, cudaStream_t st);    // alpha (reduct
 enum RingMode { RING_FWD_MAP = 0, RING_INV_MAP = 1, RING_ITER = 2, RING_INIT = 3 };
 cudaError_t ring_stage(dm_plan *p, int mode, const double *in_map, double *out_map, cudaStream_t st);
 // lanes per block of the ring kernel (1..4) for the given shared-memory words
-int ring_lanes_per_block(size_t word_bytes, int tw_words, int ph_words, int lane_words, int nlanes);
+int ring_lanes_per_block(size_t word_bytes, int tw_words, int ph_words, int lane_words, int nlanes, int regs);
 // public-layout permutations of the ring coefficients
 cudaError_t rc_to_public(dm_plan *p, double2 *pub, cudaStream_t st);
 cudaError_t rc_from_public(dm_plan *p, const double2 *pub, cudaStream_t st);
@@ -194,6 +198,7 @@ cudaError_t anchor_residual_wd(dm_plan *p, const double *s_hi, cudaStream_t st);
 
 // tensor-core Legendre stages (dm_legendre_tc.cu)
 bool tc_batch_ok(int B);
+size_t tc_table_bytes(int lmax, int mmax, int npairs, int B);
 cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t st);
 cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st);
 

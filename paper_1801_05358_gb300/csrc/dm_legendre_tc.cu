@@ -11,11 +11,19 @@
 //             + lam-_l (i G^U, -i G^Q)_p').
 // Both are GEMMs with M = 128 (ring pairs or multipoles), N = 2B or 4B columns
 // (B right-hand sides x re/im x fields), K over multipoles or ring pairs.
-// Operands: the FP32 Legendre tables (generated once by the FP64 recurrence)
-// and the FP32 iterate, each split into BF16 hi + lo in shared memory; three
-// kind::f16 MMAs per K step (hi*hi + hi*lo + lo*hi) accumulate in FP32 in
-// tensor memory.  The FP64 anchors of the mixed mode carry the last digits.
-// Two shared-memory stages: threads stage step c+1 while the MMAs of step c run.
+// Operands: the Legendre tables, split once into BF16 hi + lo and stored in
+// HBM in the K-major core-matrix tile order of each kernel, are streamed into
+// shared memory with bulk asynchronous copies (cp.async.bulk, completion by
+// mbarrier transaction count); the iterate (synthesis) or the ring
+// coefficients (analysis) are split into BF16 hi + lo by the threads, whole
+// 16-byte core-matrix rows per store.  Three kind::f16 MMAs per K step
+// (hi*hi + hi*lo + lo*hi) accumulate in FP32 in tensor memory; the FP64
+// anchors of the mixed mode carry the last digits.  Two shared-memory stages:
+// while the MMAs of step c run, the copy of step c+1's tables and the
+// conversion of its other operand proceed.
+#include <algorithm>
+#include <vector>
+
 #include "dm_internal.h"
 #include "dm_tc.cuh"
 
@@ -30,12 +38,16 @@ constexpr int TILE_A = 4096;  // 128 x 16 BF16
 
 __device__ __forceinline__ int64_t abase(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
 
-__device__ __forceinline__ void put_split(unsigned char *hi, int tile_bytes, int row, int k, float x) {
-  __nv_bfloat16 h, l;
-  split_bf16(x, h, l);
-  const uint32_t off = kmajor_off(row, k);
-  *reinterpret_cast<__nv_bfloat16 *>(hi + off) = h;
-  *reinterpret_cast<__nv_bfloat16 *>(hi + tile_bytes + off) = l;
+// byte offset of the 16-byte core-matrix row (row, k-octet ko) of a [rows x 16] K-major tile
+__device__ __forceinline__ uint32_t crow(int row, int ko) {
+  return (uint32_t)((row >> 3) * 256 + ko * 128 + (row & 7) * 16);
+}
+
+__device__ __forceinline__ void put_row(unsigned char *tile, int tile_bytes, int row, int ko, const float x[8]) {
+  uint4 h, l;
+  split8(x, h, l);
+  *reinterpret_cast<uint4 *>(tile + crow(row, ko)) = h;
+  *reinterpret_cast<uint4 *>(tile + tile_bytes + crow(row, ko)) = l;
 }
 
 __device__ __forceinline__ void mma3(uint32_t d, const unsigned char *a, const unsigned char *b, int tile_b,
@@ -59,8 +71,8 @@ __device__ __forceinline__ float2 e_of(const double2 *a, const double2 *ahi, int
 
 __device__ __forceinline__ void tc_setup(uint64_t *mbar, uint32_t *slot, uint32_t ncols) {
   if (threadIdx.x == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int i = 0; i < 4; ++i) mbar_init(&mbar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if ((threadIdx.x >> 5) == 0) tmem_alloc(slot, ncols);
   fence_before_sync();
@@ -82,75 +94,184 @@ __device__ __forceinline__ void tc_teardown(uint32_t tbase, uint32_t ncols) {
 
 }  // namespace
 
+// ------------------------------------------------------------ table layouts
+// Synthesis: per (m, pair tile pt, K step c) one block of nA tiles, each
+// 128 pairs x 16 multipoles of one parity (l = m + 32 c + par + 2 k), hi then
+// lo.  PART 0 tiles {lambda e, lambda o}; PART 1 {lam+ e, lam+ o, lam- e,
+// lam- o}.  Blocks of one CTA (m, pt) are consecutive in c.
+// Analysis: per (m, parity, l tile lt, K step c) one block of nA tiles, each
+// 128 multipoles (l = m + par + 2 i, i = 128 lt + row) x 16 ring pairs, hi
+// then lo.  PART 0 tile {lambda}; PART 1 {lam+, lam-}.
+__host__ __device__ inline int syn_steps(int lmax, int m) { return (lmax - m + 1 + 31) / 32; }
+__host__ __device__ inline int ana_nl(int lmax, int m, int par) { return (lmax - m + 1 - par + 1) / 2; }
+__host__ __device__ inline int ana_tiles(int lmax, int m, int par) {
+  const int nl = ana_nl(lmax, m, par);
+  return nl > 0 ? (nl + 127) / 128 : 0;
+}
+
+template <int PART>
+__global__ void k_tab_syn(const float *__restrict__ ptab, unsigned char *__restrict__ out,
+                          const int64_t *__restrict__ soff, int lmax, int npairs, int64_t nalm, int npt) {
+  constexpr int nA = PART == 0 ? 2 : 4;
+  const int c = blockIdx.x, pt = blockIdx.y, m = blockIdx.z;
+  const int ns = syn_steps(lmax, m);
+  if (c >= ns) return;
+  const int64_t plane = nalm * (int64_t)npairs, base = abase(lmax, m);
+  unsigned char *blk = out + (soff[m] * npt + (int64_t)pt * ns + c) * (int64_t)(nA * 2 * TILE_A);
+  for (int idx = threadIdx.x; idx < nA * 256; idx += blockDim.x) {
+    const int t = idx >> 8, q = idx & 255, row = q & 127, ko = q >> 7;
+    const int par = t & 1, func = PART == 0 ? 0 : 1 + (t >> 1);
+    const int pair = pt * 128 + row;
+    float x[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const int l = m + 32 * c + par + 2 * (8 * ko + kk);
+      x[kk] = (l <= lmax && pair < npairs) ? ptab[func * plane + (base + l) * npairs + pair] : 0.f;
+    }
+    put_row(blk + t * 2 * TILE_A, TILE_A, row, ko, x);
+  }
+}
+
+template <int PART>
+__global__ void k_tab_ana(const float *__restrict__ ptab, unsigned char *__restrict__ out,
+                          const int64_t *__restrict__ aoff, int lmax, int npairs, int64_t nalm, int nps) {
+  constexpr int nA = PART == 0 ? 1 : 2;
+  const int c = blockIdx.x, lt = blockIdx.y, m = blockIdx.z >> 1, par = blockIdx.z & 1;
+  const int nl = ana_nl(lmax, m, par);
+  if (lt * 128 >= nl) return;
+  const int64_t plane = nalm * (int64_t)npairs, base = abase(lmax, m);
+  unsigned char *blk = out + ((aoff[2 * m + par] + lt) * nps + c) * (int64_t)(nA * 2 * TILE_A);
+  for (int idx = threadIdx.x; idx < nA * 256; idx += blockDim.x) {
+    const int t = idx >> 8, q = idx & 255, row = q >> 1, ko = q & 1;
+    const int func = PART == 0 ? 0 : 1 + t;
+    const int i = lt * 128 + row, l = m + par + 2 * i, pair0 = 16 * c + 8 * ko;
+    float x[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk)
+      x[kk] = (i < nl && pair0 + kk < npairs) ? ptab[func * plane + (base + l) * npairs + pair0 + kk] : 0.f;
+    put_row(blk + t * 2 * TILE_A, TILE_A, row, ko, x);
+  }
+}
+
 // ---------------------------------------------------------------- synthesis
 // PART 0: T (2 A tiles: lambda even / odd; D columns [0, 2B) even, [2B, 4B) odd)
 // PART 1: Q, U (A tiles lam+ e, lam+ o, lam- e, lam- o with B tiles X1 e, X1 o,
 //          X2 e, X2 o; D_e = [0, 4B), D_o = [4B, 8B))
 // grid (pair tiles of 128, m); K steps of 32 consecutive multipoles (16 + 16).
+// The B rows are written so that the 8 threads of a quarter warp fill the 8
+// rows of one core matrix (row order rotated by the k-octet): no bank conflicts.
 template <int PART>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_syn_tc(const float *__restrict__ ptab,
-                                                         const double2 *__restrict__ alm,
-                                                         const double2 *__restrict__ a_hi, float2 *__restrict__ rc,
-                                                         int lmax, int mmax, int npairs, int64_t nalm, int B,
-                                                         uint32_t ncols, int *err) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ uint64_t mbar[2];
-  __shared__ uint32_t tslot;
-  const int NC = (PART == 0) ? 2 * B : 4 * B;  // D columns per parity
-  const int nA = (PART == 0) ? 2 : 4;
-  const int tileB = NC * 32;
-  const int stage = nA * 2 * TILE_A + nA * 2 * tileB;
-  const int m = blockIdx.y, p0 = blockIdx.x * 128;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  tc_setup(mbar, &tslot, ncols);
-  const uint32_t tbase = tslot;
-  const int64_t base = abase(lmax, m);
-  const int64_t plane = nalm * (int64_t)npairs;
-  const int nsteps = (lmax - m + 1 + 31) / 32;
-  const uint32_t idesc = idesc_bf16(128, NC);
-  for (int c = 0; c < nsteps; ++c) {
-    const int s = c & 1;
-    unsigned char *st = sm + s * stage;
-    if (c >= 2) mbar_wait(&mbar[s], ((c - 2) >> 1) & 1, err);
-    unsigned char *Abuf = st, *Bbuf = st + nA * 2 * TILE_A;
-    // A tiles: row = pair (coalesced), k = l step within the parity class
-    for (int idx = tid; idx < nA * 2048; idx += TC_THREADS) {
-      const int t = idx >> 11, r = idx & 2047, k = r >> 7, row = r & 127;
-      const int par = t & 1, func = (PART == 0) ? 0 : 1 + (t >> 1);
-      const int l = m + 32 * c + par + 2 * k, pair = p0 + row;
-      const float x = (l <= lmax && pair < npairs) ? ptab[func * plane + (base + l) * npairs + pair] : 0.f;
-      put_split(Abuf + t * 2 * TILE_A, TILE_A, row, k, x);
-    }
-    // B tiles from the iterate (correction e = a - a_hi in the anchored mixed mode)
-    for (int idx = tid; idx < 2 * B * 16; idx += TC_THREADS) {
-      const int par = idx / (B * 16), rem = idx % (B * 16), b = rem >> 4, k = rem & 15;
-      const int l = m + 32 * c + par + 2 * k;
-      const int64_t ib = (int64_t)b * 3 * nalm + base + l;
-      if (PART == 0) {
-        float2 t = (l <= lmax) ? e_of(alm, a_hi, ib) : make_float2(0.f, 0.f);
-        unsigned char *T = Bbuf + par * 2 * tileB;
-        put_split(T, tileB, 2 * b, k, t.x);
-        put_split(T, tileB, 2 * b + 1, k, t.y);
-      } else {
-        float2 e = make_float2(0.f, 0.f), bb = make_float2(0.f, 0.f);
-        if (l <= lmax) {
-          e = e_of(alm, a_hi, ib + nalm);
-          bb = e_of(alm, a_hi, ib + 2 * nalm);
-        }
-        unsigned char *X1 = Bbuf + par * 2 * tileB, *X2 = Bbuf + (2 + par) * 2 * tileB;
-        put_split(X1, tileB, 4 * b + 0, k, -e.x);   // Q.re <- -aE.re
-        put_split(X1, tileB, 4 * b + 1, k, -e.y);   // Q.im <- -aE.im
-        put_split(X1, tileB, 4 * b + 2, k, -bb.x);  // U.re <- -aB.re
-        put_split(X1, tileB, 4 * b + 3, k, -bb.y);  // U.im <- -aB.im
-        put_split(X2, tileB, 4 * b + 0, k, bb.y);   // Q.re <- (-i aB).re
-        put_split(X2, tileB, 4 * b + 1, k, -bb.x);  // Q.im <- (-i aB).im
-        put_split(X2, tileB, 4 * b + 2, k, -e.y);   // U.re <- (+i aE).re
-        put_split(X2, tileB, 4 * b + 3, k, e.x);    // U.im <- (+i aE).im
+__device__ __forceinline__ void stage_syn_b(unsigned char *Bbuf, int tileB, const double2 *__restrict__ alm,
+                                            const double2 *__restrict__ a_hi, int64_t base, int m, int c, int lmax,
+                                            int64_t nalm, int B) {
+  if (PART == 0) {
+    // task = ((par * B/4 + b/4) * 8) + (b & 3) * 2 + ko: rows 2b, 2b + 1 of parity tile par
+    for (int task = threadIdx.x; task < 4 * B; task += TC_THREADS) {
+      const int ko = task & 1, b = ((task >> 3) % (B >> 2)) * 4 + ((task >> 1) & 3), par = task / (2 * B);
+      float re[8], im[8];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const int l = m + 32 * c + par + 2 * (8 * ko + kk);
+        const float2 v = l <= lmax ? e_of(alm, a_hi, (int64_t)b * 3 * nalm + base + l) : make_float2(0.f, 0.f);
+        re[kk] = v.x;
+        im[kk] = v.y;
       }
+      unsigned char *T = Bbuf + par * 2 * tileB;
+      put_row(T, tileB, 2 * b + ko, ko, ko ? im : re);
+      put_row(T, tileB, 2 * b + (ko ^ 1), ko, ko ? re : im);
     }
-    fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
+  } else {
+    // task = ((par * B/2 + b/2) * 8) + (b & 1) * 4 + f * 2 + ko, f = 0 (E) / 1 (B)
+    for (int task = threadIdx.x; task < 8 * B; task += TC_THREADS) {
+      const int ko = task & 1, f = (task >> 1) & 1, b = ((task >> 3) % (B >> 1)) * 2 + ((task >> 2) & 1);
+      const int par = task / (4 * B);
+      float re[8], im[8], nre[8], nim[8];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const int l = m + 32 * c + par + 2 * (8 * ko + kk);
+        const float2 v =
+            l <= lmax ? e_of(alm, a_hi, ((int64_t)b * 3 + 1 + f) * nalm + base + l) : make_float2(0.f, 0.f);
+        re[kk] = v.x;
+        im[kk] = v.y;
+        nre[kk] = -v.x;
+        nim[kk] = -v.y;
+      }
+      unsigned char *X1 = Bbuf + par * 2 * tileB, *X2 = Bbuf + (2 + par) * 2 * tileB;
+      // X1: E -> rows 4b (-E.re), 4b+1 (-E.im); B -> rows 4b+2 (-B.re), 4b+3 (-B.im)
+      const int r1 = 4 * b + 2 * f;
+      put_row(X1, tileB, r1 + ko, ko, ko ? nim : nre);
+      put_row(X1, tileB, r1 + (ko ^ 1), ko, ko ? nre : nim);
+      // X2: E -> rows 4b+2 (-E.im), 4b+3 (E.re); B -> rows 4b (B.im), 4b+1 (-B.re)
+      const int r2 = 4 * b + 2 * (1 - f);
+      const float *x2a = f == 0 ? nim : im, *x2b = f == 0 ? re : nre;  // rows r2, r2 + 1
+      put_row(X2, tileB, r2 + ko, ko, ko ? x2b : x2a);
+      put_row(X2, tileB, r2 + (ko ^ 1), ko, ko ? x2a : x2b);
+    }
+  }
+}
+
+// The B operand of every (m, K step) once per synthesis, in the tile order of
+// the shared-memory stage: block (m, c) at (soff[m] + c) * nA * 2 * tileB.
+template <int PART>
+__global__ void __launch_bounds__(TC_THREADS) k_syn_b(unsigned char *__restrict__ out, const int64_t *__restrict__ soff,
+                                                      const double2 *__restrict__ alm,
+                                                      const double2 *__restrict__ a_hi, int lmax, int64_t nalm,
+                                                      int B) {
+  const int c = blockIdx.x, m = blockIdx.y;
+  if (c >= syn_steps(lmax, m)) return;
+  constexpr int nA = (PART == 0) ? 2 : 4;
+  const int tileB = ((PART == 0) ? 2 * B : 4 * B) * 32;
+  stage_syn_b<PART>(out + (soff[m] + c) * (int64_t)(nA * 2 * tileB), tileB, alm, a_hi, abase(lmax, m), m, c, lmax,
+                    nalm, B);
+}
+
+constexpr int TC_MAX_STAGES = 8;
+
+// Both operands arrive by bulk copy: thread 0 keeps NS stages in flight and
+// issues the MMAs; the four warps read the accumulators out at the end.
+template <int PART>
+__global__ void __launch_bounds__(128, 1) k_syn_tc(const unsigned char *__restrict__ tab,
+                                                   const unsigned char *__restrict__ bt,
+                                                   const int64_t *__restrict__ soff, float2 *__restrict__ rc,
+                                                   int lmax, int mmax, int npairs, int B, int NS, uint32_t ncols,
+                                                   int *err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint64_t mbar[2 * TC_MAX_STAGES];  // done[NS] (MMAs of the stage finished), full[NS] (operands landed)
+  __shared__ uint32_t tslot;
+  uint64_t *done = mbar, *full = mbar + TC_MAX_STAGES;
+  const int NC = (PART == 0) ? 2 * B : 4 * B;  // D columns per parity
+  constexpr int nA = (PART == 0) ? 2 : 4;
+  const int tileB = NC * 32;
+  const int abytes = nA * 2 * TILE_A, bbytes = nA * 2 * tileB;
+  const int stage = abytes + bbytes;
+  const int m = blockIdx.y, pt = blockIdx.x, npt = gridDim.x, p0 = pt * 128;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < 2 * TC_MAX_STAGES; ++i) mbar_init(&mbar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tslot, ncols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tbase = tslot;
+  const int nsteps = syn_steps(lmax, m);
+  if (tid == 0) {
+    const unsigned char *tabm = tab + (soff[m] * npt + (int64_t)pt * nsteps) * (int64_t)abytes;
+    const unsigned char *btm = bt + soff[m] * (int64_t)bbytes;
+    const uint32_t idesc = idesc_bf16(128, NC);
+    auto issue = [&](int c) {
+      const int s = c % NS;
+      unsigned char *dst = sm + s * stage;
+      mbar_expect_tx(&full[s], (uint32_t)stage);
+      bulk_g2s(dst, tabm + (int64_t)c * abytes, (uint32_t)abytes, &full[s]);
+      bulk_g2s(dst + abytes, btm + (int64_t)c * bbytes, (uint32_t)bbytes, &full[s]);
+    };
+    for (int c = 0; c < NS && c < nsteps; ++c) issue(c);
+    for (int c = 0; c < nsteps; ++c) {
+      const int s = c % NS;
+      unsigned char *Abuf = sm + s * stage, *Bbuf = Abuf + abytes;
+      mbar_wait(&full[s], (c / NS) & 1, err);
       fence_after_sync();
       const uint32_t acc = c > 0 ? 1u : 0u;
       if (PART == 0) {
@@ -163,10 +284,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syn_tc(const float *__restric
         mma3(tbase + NC, Abuf + 1 * 2 * TILE_A, Bbuf + 1 * 2 * tileB, tileB, idesc, acc);
         mma3(tbase + NC, Abuf + 2 * 2 * TILE_A, Bbuf + 2 * 2 * tileB, tileB, idesc, 1u);
       }
-      commit(&mbar[s]);
+      commit(&done[s]);
+      // refill the stage of step c - 1 (its MMAs precede those just issued)
+      if (c >= 1 && c - 1 + NS < nsteps) {
+        mbar_wait(&done[(c - 1) % NS], ((c - 1) / NS) & 1, err);
+        issue(c - 1 + NS);
+      }
     }
+    mbar_wait(&done[(nsteps - 1) % NS], ((nsteps - 1) / NS) & 1, err);
   }
-  tc_drain(mbar, nsteps, err);
+  __syncthreads();
+  fence_after_sync();
   if (warp < 4) {
     const int row = warp * 32 + lane, pair = p0 + row;
     const bool ok = pair < npairs, equator = (pair == npairs - 1);
@@ -208,84 +336,118 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syn_tc(const float *__restric
 //                A = lam- with B2, over 16 pairs per K step)
 // grid (l tiles of 128 multipoles of one parity, parity, m); rows l = m + p + 2 i.
 // Output: out[b][f][alm] (FP32 partial sums with a single chunk).
+// 8 ring pairs (north, south) of one field, as 16 float2; zero past npairs, no
+// south ring at the equator pair.
+__device__ __forceinline__ void load_pairs8(const float2 *__restrict__ g, int pair0, int npairs, float2 v[16]) {
+  if (pair0 + 8 < npairs) {
+    const float4 *g4 = reinterpret_cast<const float4 *>(g + 2 * (int64_t)pair0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float4 q = g4[i];
+      v[2 * i] = make_float2(q.x, q.y);
+      v[2 * i + 1] = make_float2(q.z, q.w);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int pair = pair0 + i;
+      v[2 * i] = pair < npairs ? g[2 * (int64_t)pair] : make_float2(0.f, 0.f);
+      v[2 * i + 1] = pair < npairs - 1 ? g[2 * (int64_t)pair + 1] : make_float2(0.f, 0.f);
+    }
+  }
+}
+
 template <int PART>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_ana_tc(const float *__restrict__ ptab,
+__device__ __forceinline__ void stage_ana_b(unsigned char *Bbuf, int tileB, const float2 *__restrict__ rc, int m,
+                                            int c, int par, int mmax, int npairs, int B) {
+  const float sgn = par == 0 ? 1.f : -1.f;  // G_par = G_N + sgn G_S
+  if (PART == 0) {
+    // task = (b / 4) * 8 + (b & 3) * 2 + ko: rows 2b, 2b + 1
+    for (int task = threadIdx.x; task < 2 * B; task += TC_THREADS) {
+      const int ko = task & 1, b = (task >> 3) * 4 + ((task >> 1) & 3);
+      float2 v[16];
+      load_pairs8(rc + (((int64_t)b * 3 + 0) * (mmax + 1) + m) * npairs * 2, 16 * c + 8 * ko, npairs, v);
+      float re[8], im[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        re[i] = v[2 * i].x + sgn * v[2 * i + 1].x;
+        im[i] = v[2 * i].y + sgn * v[2 * i + 1].y;
+      }
+      put_row(Bbuf, tileB, 2 * b + ko, ko, ko ? im : re);
+      put_row(Bbuf, tileB, 2 * b + (ko ^ 1), ko, ko ? re : im);
+    }
+  } else {
+    // task = (b / 2) * 8 + (b & 1) * 4 + f * 2 + ko, f = 0 (Q) / 1 (U)
+    for (int task = threadIdx.x; task < 4 * B; task += TC_THREADS) {
+      const int ko = task & 1, f = (task >> 1) & 1, b = (task >> 3) * 2 + ((task >> 2) & 1);
+      float2 v[16];
+      load_pairs8(rc + (((int64_t)b * 3 + 1 + f) * (mmax + 1) + m) * npairs * 2, 16 * c + 8 * ko, npairs, v);
+      float pr[8], pi[8], or_[8], oi[8];  // this parity and the opposite one
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        pr[i] = v[2 * i].x + sgn * v[2 * i + 1].x;
+        pi[i] = v[2 * i].y + sgn * v[2 * i + 1].y;
+        or_[i] = v[2 * i].x - sgn * v[2 * i + 1].x;
+        oi[i] = v[2 * i].y - sgn * v[2 * i + 1].y;
+      }
+      float a0[8], a1[8], b0[8], b1[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        // B1: Q -> rows 4b (-Qp.re), 4b+1 (-Qp.im); U -> rows 4b+2 (-Up.re), 4b+3 (-Up.im)
+        a0[i] = -pr[i];
+        a1[i] = -pi[i];
+        // B2: U -> rows 4b (Uo.im), 4b+1 (-Uo.re); Q -> rows 4b+2 (-Qo.im), 4b+3 (Qo.re)
+        b0[i] = f == 1 ? oi[i] : -oi[i];
+        b1[i] = f == 1 ? -or_[i] : or_[i];
+      }
+      unsigned char *B1 = Bbuf, *B2 = Bbuf + 2 * tileB;
+      const int r1 = 4 * b + 2 * f, r2 = 4 * b + 2 * (1 - f);
+      put_row(B1, tileB, r1 + ko, ko, ko ? a1 : a0);
+      put_row(B1, tileB, r1 + (ko ^ 1), ko, ko ? a0 : a1);
+      put_row(B2, tileB, r2 + ko, ko, ko ? b1 : b0);
+      put_row(B2, tileB, r2 + (ko ^ 1), ko, ko ? b0 : b1);
+    }
+  }
+}
+
+template <int PART>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_ana_tc(const unsigned char *__restrict__ tab,
+                                                         const int64_t *__restrict__ aoff,
                                                          const float2 *__restrict__ rc, float2 *__restrict__ out,
                                                          int lmax, int mmax, int npairs, int64_t nalm, int B,
                                                          uint32_t ncols, int *err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ uint64_t mbar[2];
+  __shared__ uint64_t mbar[4];
   __shared__ uint32_t tslot;
+  uint64_t *done = mbar, *full = mbar + 2;
   const int m = blockIdx.z, par = blockIdx.y, lt = blockIdx.x;
-  const int nl = (lmax - m + 1 - par + 1) / 2;  // multipoles of this parity
-  if (nl <= 0 || lt * 128 >= nl) return;        // uniform over the block
+  const int nl = ana_nl(lmax, m, par);
+  if (nl <= 0 || lt * 128 >= nl) return;  // uniform over the block
   const int NC = (PART == 0) ? 2 * B : 4 * B;
-  const int nA = (PART == 0) ? 1 : 2;
+  constexpr int nA = (PART == 0) ? 1 : 2;
   const int tileB = NC * 32;
-  const int stage = nA * 2 * TILE_A + nA * 2 * tileB;
+  const int abytes = nA * 2 * TILE_A;
+  const int stage = abytes + nA * 2 * tileB;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   tc_setup(mbar, &tslot, ncols);
   const uint32_t tbase = tslot;
   const int64_t base = abase(lmax, m);
-  const int64_t plane = nalm * (int64_t)npairs;
   const int nsteps = (npairs + 15) / 16;
+  const unsigned char *tabm = tab + (aoff[2 * m + par] + lt) * nsteps * (int64_t)abytes;
   const uint32_t idesc = idesc_bf16(128, NC);
-  const int opp = par ^ 1;
+  if (tid == 0) {
+    mbar_expect_tx(&full[0], (uint32_t)abytes);
+    bulk_g2s(sm, tabm, (uint32_t)abytes, &full[0]);
+  }
   for (int c = 0; c < nsteps; ++c) {
     const int s = c & 1;
-    unsigned char *st = sm + s * stage;
-    if (c >= 2) mbar_wait(&mbar[s], ((c - 2) >> 1) & 1, err);
-    unsigned char *Abuf = st, *Bbuf = st + nA * 2 * TILE_A;
-    const int pair0 = 16 * c;
-    // A tiles: row = multipole, k = pair (16 consecutive floats per row)
-    for (int idx = tid; idx < nA * 2048; idx += TC_THREADS) {
-      const int t = idx >> 11, r = idx & 2047, row = r >> 4, k = r & 15;
-      const int func = (PART == 0) ? 0 : 1 + t;
-      const int i = lt * 128 + row, l = m + par + 2 * i, pair = pair0 + k;
-      const float x = (i < nl && pair < npairs) ? ptab[func * plane + (base + l) * npairs + pair] : 0.f;
-      put_split(Abuf + t * 2 * TILE_A, TILE_A, row, k, x);
-    }
-    // B tiles from the ring coefficients (parity combinations of the ring pair)
-    for (int idx = tid; idx < B * 16; idx += TC_THREADS) {
-      const int b = idx >> 4, k = idx & 15, pair = pair0 + k;
-      const bool ok = pair < npairs, eq = (pair == npairs - 1);
-      if (PART == 0) {
-        float2 gp = make_float2(0.f, 0.f);
-        if (ok) {
-          const float2 *g = rc + ((((int64_t)b * 3 + 0) * (mmax + 1) + m) * npairs + pair) * 2;
-          const float2 gn = g[0], gs = eq ? make_float2(0.f, 0.f) : g[1];
-          gp = par == 0 ? make_float2(gn.x + gs.x, gn.y + gs.y) : make_float2(gn.x - gs.x, gn.y - gs.y);
-        }
-        put_split(Bbuf, tileB, 2 * b, k, gp.x);
-        put_split(Bbuf, tileB, 2 * b + 1, k, gp.y);
-      } else {
-        float2 qp = make_float2(0.f, 0.f), up = qp, qo = qp, uo = qp;
-        if (ok) {
-          const float2 *gq = rc + ((((int64_t)b * 3 + 1) * (mmax + 1) + m) * npairs + pair) * 2;
-          const float2 *gu = rc + ((((int64_t)b * 3 + 2) * (mmax + 1) + m) * npairs + pair) * 2;
-          const float2 qn = gq[0], qs = eq ? make_float2(0.f, 0.f) : gq[1];
-          const float2 un = gu[0], us = eq ? make_float2(0.f, 0.f) : gu[1];
-          const float2 qe = make_float2(qn.x + qs.x, qn.y + qs.y), qd = make_float2(qn.x - qs.x, qn.y - qs.y);
-          const float2 ue = make_float2(un.x + us.x, un.y + us.y), ud = make_float2(un.x - us.x, un.y - us.y);
-          qp = par == 0 ? qe : qd;
-          up = par == 0 ? ue : ud;
-          qo = opp == 0 ? qe : qd;
-          uo = opp == 0 ? ue : ud;
-        }
-        unsigned char *B1 = Bbuf, *B2 = Bbuf + 2 * tileB;
-        put_split(B1, tileB, 4 * b + 0, k, -qp.x);  // aE.re <- -lam+ GQ.re
-        put_split(B1, tileB, 4 * b + 1, k, -qp.y);  // aE.im
-        put_split(B1, tileB, 4 * b + 2, k, -up.x);  // aB.re <- -lam+ GU.re
-        put_split(B1, tileB, 4 * b + 3, k, -up.y);  // aB.im
-        put_split(B2, tileB, 4 * b + 0, k, uo.y);   // aE.re <- +lam- GU_opp.im
-        put_split(B2, tileB, 4 * b + 1, k, -uo.x);  // aE.im <- -lam- GU_opp.re
-        put_split(B2, tileB, 4 * b + 2, k, -qo.y);  // aB.re <- -lam- GQ_opp.im
-        put_split(B2, tileB, 4 * b + 3, k, qo.x);   // aB.im <- +lam- GQ_opp.re
-      }
-    }
+    unsigned char *Abuf = sm + s * stage, *Bbuf = Abuf + abytes;
+    if (c >= 2) mbar_wait(&done[s], ((c - 2) >> 1) & 1, err);
+    stage_ana_b<PART>(Bbuf, tileB, rc, m, c, par, mmax, npairs, B);
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
+      mbar_wait(&full[s], (c >> 1) & 1, err);
       fence_after_sync();
       const uint32_t acc = c > 0 ? 1u : 0u;
       if (PART == 0) {
@@ -294,10 +456,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ana_tc(const float *__restric
         mma3(tbase, Abuf, Bbuf, tileB, idesc, acc);
         mma3(tbase, Abuf + 2 * TILE_A, Bbuf + 2 * tileB, tileB, idesc, 1u);
       }
-      commit(&mbar[s]);
+      commit(&done[s]);
+      if (c + 1 < nsteps) {
+        if (c >= 1) mbar_wait(&done[s ^ 1], ((c - 1) >> 1) & 1, err);
+        mbar_expect_tx(&full[s ^ 1], (uint32_t)abytes);
+        bulk_g2s(sm + (s ^ 1) * stage, tabm + (int64_t)(c + 1) * abytes, (uint32_t)abytes, &full[s ^ 1]);
+      }
     }
   }
-  tc_drain(mbar, nsteps, err);
+  tc_drain(done, nsteps, err);
   if (warp < 4) {
     const int row = warp * 32 + lane, i = lt * 128 + row;
     const bool ok = i < nl;
@@ -340,46 +507,134 @@ static size_t tc_smem(int stage_bytes, uint32_t ncols) {
   return s > floor_bytes ? s : floor_bytes;
 }
 
+// the same for NS stages
+static size_t tc_smem_n(int stage_bytes, int ns, uint32_t ncols) {
+  size_t s = (size_t)ns * stage_bytes + 1024;
+  const int per_sm = (int)(512 / ncols);
+  const size_t floor_bytes = (232448 / (per_sm + 1)) + 1024;
+  return s > floor_bytes ? s : floor_bytes;
+}
+
 bool tc_batch_ok(int B) { return B == 8 || B == 16 || B == 32 || B == 64; }
 
+// Bytes of the four tiled BF16 table copies of a plan and of the synthesis
+// operand scratch for B right-hand sides (for memory estimates).
+size_t tc_table_bytes(int lmax, int mmax, int npairs, int B) {
+  const int64_t npt = (npairs + 127) / 128, nps = (npairs + 15) / 16;
+  int64_t ssteps = 0, atiles = 0;
+  for (int m = 0; m <= mmax; ++m) {
+    ssteps += syn_steps(lmax, m);
+    atiles += ana_tiles(lmax, m, 0) + ana_tiles(lmax, m, 1);
+  }
+  return (size_t)(ssteps * npt * (2 + 4) * 2 * TILE_A + atiles * nps * (1 + 2) * 2 * TILE_A +
+                  ssteps * (int64_t)B * (2 * 2 * 64 + 4 * 2 * 128));
+}
+
+// The tiled BF16 hi/lo copies of the FP32 Legendre tables, made on first use.
+static cudaError_t tc_tables(dm_plan *p) {
+  if (p->tc_synA[0]) return cudaSuccess;
+  const int npt = (p->npairs + 127) / 128, nps = (p->npairs + 15) / 16;
+  std::vector<int64_t> soff(p->mmax + 2, 0), aoff(2 * (p->mmax + 1) + 1, 0);
+  int max_lt = 0;
+  for (int m = 0; m <= p->mmax; ++m) {
+    soff[m + 1] = soff[m] + syn_steps(p->lmax, m);
+    for (int par = 0; par < 2; ++par) {
+      const int nt = ana_tiles(p->lmax, m, par);
+      aoff[2 * m + par + 1] = aoff[2 * m + par] + nt;
+      max_lt = std::max(max_lt, nt);
+    }
+  }
+  cudaError_t e;
+  const size_t sbytes[2] = {(size_t)soff[p->mmax + 1] * npt * 2 * 2 * TILE_A,
+                            (size_t)soff[p->mmax + 1] * npt * 4 * 2 * TILE_A};
+  const size_t abytes[2] = {(size_t)aoff[2 * (p->mmax + 1)] * nps * 1 * 2 * TILE_A,
+                            (size_t)aoff[2 * (p->mmax + 1)] * nps * 2 * 2 * TILE_A};
+  for (int part = 0; part < 2; ++part) {
+    if ((e = cudaMalloc(&p->tc_synA[part], sbytes[part]))) return e;
+    if ((e = cudaMalloc(&p->tc_anaA[part], abytes[part]))) return e;
+    p->bytes += (int64_t)(sbytes[part] + abytes[part]);
+  }
+  {  // per-iteration B operand of the synthesis (depends on the batch)
+    const size_t b0 = (size_t)soff[p->mmax + 1] * 2 * 2 * (2 * p->batch * 32);
+    const size_t b1 = (size_t)soff[p->mmax + 1] * 4 * 2 * (4 * p->batch * 32);
+    if ((e = cudaMalloc(&p->tc_synB[0], b0))) return e;
+    if ((e = cudaMalloc(&p->tc_synB[1], b1))) return e;
+    p->bytes += (int64_t)(b0 + b1);
+  }
+  if ((e = cudaMalloc(&p->tc_soff, sizeof(int64_t) * soff.size()))) return e;
+  if ((e = cudaMalloc(&p->tc_aoff, sizeof(int64_t) * aoff.size()))) return e;
+  cudaMemcpy(p->tc_soff, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->tc_aoff, aoff.data(), sizeof(int64_t) * aoff.size(), cudaMemcpyHostToDevice);
+  dim3 gs(syn_steps(p->lmax, 0), npt, p->mmax + 1);
+  k_tab_syn<0><<<gs, 256>>>(p->ptab, p->tc_synA[0], p->tc_soff, p->lmax, p->npairs, p->nalm, npt);
+  k_tab_syn<1><<<gs, 256>>>(p->ptab, p->tc_synA[1], p->tc_soff, p->lmax, p->npairs, p->nalm, npt);
+  if (max_lt > 0) {
+    dim3 ga(nps, max_lt, 2 * (p->mmax + 1));
+    k_tab_ana<0><<<ga, 256>>>(p->ptab, p->tc_anaA[0], p->tc_aoff, p->lmax, p->npairs, p->nalm, nps);
+    k_tab_ana<1><<<ga, 256>>>(p->ptab, p->tc_anaA[1], p->tc_aoff, p->lmax, p->npairs, p->nalm, nps);
+  }
+  if ((e = cudaGetLastError())) return e;
+  return cudaDeviceSynchronize();
+}
+
+// stages per CTA: as many as fit in the shared memory of one CTA, or of two
+// when their tensor memory lets two CTAs share an SM (2..TC_MAX_STAGES)
+static int tc_stages(int stage_bytes, uint32_t ncols) {
+  const int per_sm = ncols <= 256 ? 2 : 1;
+  const int ns = (int)(((227u << 10) - 1024u * per_sm) / per_sm) / stage_bytes;
+  return ns < 2 ? 2 : (ns > TC_MAX_STAGES ? TC_MAX_STAGES : ns);
+}
+
 cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t st) {
+  cudaError_t e = tc_tables(p);
+  if (e) return e;
   const int B = p->batch;
   const double2 *ahi = p->anchor_active ? p->a_hi : nullptr;
-  dim3 g((p->npairs + 127) / 128, p->mmax + 1);
+  const int npt = (p->npairs + 127) / 128;
+  dim3 gb(syn_steps(p->lmax, 0), p->mmax + 1);
+  k_syn_b<0><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[0], p->tc_soff, alm, ahi, p->lmax, p->nalm, B);
+  k_syn_b<1><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[1], p->tc_soff, alm, ahi, p->lmax, p->nalm, B);
+  dim3 g(npt, p->mmax + 1);
   {
+    const int stage = 2 * 2 * TILE_A + 2 * 2 * (2 * B * 32);
     const uint32_t nc = pow2_cols(4 * B);
-    const size_t sm = tc_smem(2 * 2 * TILE_A + 2 * 2 * (2 * B * 32), nc);
+    const int ns = tc_stages(stage, nc);
+    const size_t sm = tc_smem_n(stage, ns, nc);
     cudaFuncSetAttribute(k_syn_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_syn_tc<0><<<g, TC_THREADS, sm, st>>>(p->ptab, alm, ahi, p->rc32, p->lmax, p->mmax, p->npairs, p->nalm, B, nc,
-                                           p->tc_err);
+    k_syn_tc<0><<<g, 128, sm, st>>>(p->tc_synA[0], p->tc_synB[0], p->tc_soff, p->rc32, p->lmax, p->mmax,
+                                    p->npairs, B, ns, nc, p->tc_err);
   }
   {
+    const int stage = 4 * 2 * TILE_A + 4 * 2 * (4 * B * 32);
     const uint32_t nc = pow2_cols(8 * B);
-    const size_t sm = tc_smem(4 * 2 * TILE_A + 4 * 2 * (4 * B * 32), nc);
+    const int ns = tc_stages(stage, nc);
+    const size_t sm = tc_smem_n(stage, ns, nc);
     cudaFuncSetAttribute(k_syn_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_syn_tc<1><<<g, TC_THREADS, sm, st>>>(p->ptab, alm, ahi, p->rc32, p->lmax, p->mmax, p->npairs, p->nalm, B, nc,
-                                           p->tc_err);
+    k_syn_tc<1><<<g, 128, sm, st>>>(p->tc_synA[1], p->tc_synB[1], p->tc_soff, p->rc32, p->lmax, p->mmax,
+                                    p->npairs, B, ns, nc, p->tc_err);
   }
   return cudaGetLastError();
 }
 
 cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st) {
+  cudaError_t e = tc_tables(p);
+  if (e) return e;
   const int B = p->batch;
-  const int ltiles = ((p->lmax + 2) / 2 + 127) / 128;
+  const int ltiles = ana_tiles(p->lmax, 0, 0);
   dim3 g(ltiles, 2, p->mmax + 1);
   {
     const uint32_t nc = pow2_cols(2 * B);
     const size_t sm = tc_smem(1 * 2 * TILE_A + 1 * 2 * (2 * B * 32), nc);
     cudaFuncSetAttribute(k_ana_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_ana_tc<0><<<g, TC_THREADS, sm, st>>>(p->ptab, p->rc32, p->apart32, p->lmax, p->mmax, p->npairs, p->nalm, B,
-                                           nc, p->tc_err);
+    k_ana_tc<0><<<g, TC_THREADS, sm, st>>>(p->tc_anaA[0], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
+                                           p->npairs, p->nalm, B, nc, p->tc_err);
   }
   {
     const uint32_t nc = pow2_cols(4 * B);
     const size_t sm = tc_smem(2 * 2 * TILE_A + 2 * 2 * (4 * B * 32), nc);
     cudaFuncSetAttribute(k_ana_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_ana_tc<1><<<g, TC_THREADS, sm, st>>>(p->ptab, p->rc32, p->apart32, p->lmax, p->mmax, p->npairs, p->nalm, B,
-                                           nc, p->tc_err);
+    k_ana_tc<1><<<g, TC_THREADS, sm, st>>>(p->tc_anaA[1], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
+                                           p->npairs, p->nalm, B, nc, p->tc_err);
   }
   return cudaGetLastError();
 }

@@ -365,11 +365,14 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
     const int buf_words = rc_cls.M + 1;
     const bool staged = (MODE == RING_ITER || MODE == RING_INV_MAP);
     const int lane_words = buf_words + (staged ? p->mmax + 1 : 0);
-    int G = ring_lanes_per_block(sizeof(C), tw_words, ph_words, lane_words, nlanes);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_ring<R, C, MODE>);
+    if (e != cudaSuccess) return e;
+    int G = ring_lanes_per_block(sizeof(C), tw_words, ph_words, lane_words, nlanes, fa.numRegs);
     const size_t smem = sizeof(C) * ((size_t)tw_words + ph_words + (size_t)G * lane_words);
     dim3 grid(rc_cls.count, (nlanes + G - 1) / G);
     dim3 block(T, G);
-    cudaError_t e = cudaFuncSetAttribute(k_ring<R, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_ring<R, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_ring<R, C, MODE><<<grid, block, smem, st>>>(p->rings, p->ring_order + rc_cls.off, phase, bhat, twid,
                                                   tw_words, ph_words, buf_words, lane_words, nlanes, rc, p->mmax,
@@ -382,9 +385,9 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
 }
 
 // Lanes per block: the G in 1..4 that keeps the most lanes resident on an SM
-// (228 KB of shared memory, 1 KB reserved per block, 2048 threads), ties to
-// the larger G.
-int ring_lanes_per_block(size_t word_bytes, int tw_words, int ph_words, int lane_words, int nlanes) {
+// (228 KB of shared memory with 1 KB reserved per block, 2048 threads, 64 K
+// registers allocated per warp in units of 256), ties to the larger G.
+int ring_lanes_per_block(size_t word_bytes, int tw_words, int ph_words, int lane_words, int nlanes, int regs) {
   int best = 1;
   long best_lanes = -1;
   for (int G = 1; G <= 4; ++G) {
@@ -392,6 +395,8 @@ int ring_lanes_per_block(size_t word_bytes, int tw_words, int ph_words, int lane
     if (smem > (227u << 10)) break;
     long blocks = (long)((228u << 10) / (smem + 1024));
     blocks = std::min<long>(blocks, 2048 / (128 * G));
+    const long warp_regs = ((long)std::max(regs, 1) * 32 + 255) / 256 * 256;
+    blocks = std::min<long>(blocks, 65536 / (warp_regs * 4 * G));
     const long lanes = blocks * G;
     if (lanes >= best_lanes) {
       best_lanes = lanes;

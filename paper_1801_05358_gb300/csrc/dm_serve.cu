@@ -149,6 +149,7 @@ size_t estimate_bytes(int nside, int lmax, int S, dm_precision prec) {
     b += S * nchunk * 3 * nalm * 8;              // apart32
     b += S * 3 * npix * 4 * 4;                   // s32, w32, wd32, shi32
     b += S * 3 * nalm * 16 * 2;                  // a_hi, g_hi
+    if (dmwf::tc_batch_ok(S)) b += (double)dmwf::tc_table_bytes(lmax, lmax, (int)npairs, S);  // tiled BF16 tables
   }
   return (size_t)(b * 1.05) + (64u << 20);
 }
