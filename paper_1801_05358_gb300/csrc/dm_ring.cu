@@ -50,6 +50,13 @@ __device__ __forceinline__ C phase_q(const C *Tq, int q, int n) {
   return r;
 }
 
+// L2 prefetch of a contiguous byte range by the TMA engine (16-byte aligned
+// start and size): the map segments of a ring are fetched while the inverse
+// transform runs.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Fold the staged S_m = F_m e^{i m phi0} (m = 0..mmax; F_{-m} = conj F_m) into
 // C_k = sum_{m = k mod n, |m| <= mmax} F_m e^{i m phi0}.
 template <typename C>
@@ -149,6 +156,13 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
   const C *bh = bhat + (bl ? Rg.bh_off : 0);
   const int64_t rbase = ((((int64_t)b * 3 + f) * (mmax + 1)) * npairs + Rg.pair) * 2 + Rg.side;
   const int64_t mstride = (int64_t)npairs * 2;
+  if (MODE == RING_ITER && live && tx == 0) {
+    // ring segments start on 16-byte boundaries: n = 4i pixels, starts and npix multiples of 4
+    const uint32_t bytes = (uint32_t)(n * sizeof(R));
+    prefetch_l2(s_state + moff, bytes);
+    prefetch_l2(w + moff, bytes);
+    prefetch_l2(s_anchor ? (const R *)s_anchor + moff : wd + moff, bytes);
+  }
   const float invM_f = 1.0f / (float)M;
   const double invM_d = 1.0 / (double)M;
   __syncthreads();
@@ -210,10 +224,14 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
         }
       return;
     }
-    // RING_ITER: Cauchy partials (FP64), store s, form t - s = w d - w s and pack it.
+    // RING_ITER: Cauchy partials, store s, form t - s = w d - w s and pack it.
     // With an anchor (mixed precision) the state is Y e, s = s_anchor + Y e, and
     // the data part w (d - s_anchor) is carried in FP64 by the anchor: r = -w Y e.
-    double dd = 0.0, ss = 0.0;
+    // Each thread accumulates the Cauchy partials of its few pixels in the map
+    // precision R (FP32 in the mixed mode, whose maps are FP32; FP64 arithmetic
+    // runs at a small fraction of the FP32 rate on this GPU), the sums over
+    // threads run in FP64.
+    R dd_t = 0, ss_t = 0;
     // every thread reads and rewrites its own entries j only; plan-owned maps,
     // (s_{2j}, s_{2j+1}) read as one aligned pair, two j per batch
     C *sv = reinterpret_cast<C *>(s_state + moff);
@@ -244,16 +262,16 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
         s.y = -z.y;
         C rr;
         if (live) {
-          const double d0 = (double)s.x - (double)so[u].x, d1 = (double)s.y - (double)so[u].y;
-          dd += d0 * d0 + d1 * d1;
+          const R d0 = s.x - so[u].x, d1 = s.y - so[u].y;
+          dd_t += d0 * d0 + d1 * d1;
           sv[j] = s;
           if (av) {
-            const double f0 = (double)sa[u].x + (double)s.x, f1 = (double)sa[u].y + (double)s.y;
-            ss += f0 * f0 + f1 * f1;
+            const R f0 = sa[u].x + s.x, f1 = sa[u].y + s.y;
+            ss_t += f0 * f0 + f1 * f1;
             rr.x = -ww[u].x * s.x;
             rr.y = -ww[u].y * s.y;
           } else {
-            ss += (double)s.x * (double)s.x + (double)s.y * (double)s.y;
+            ss_t += s.x * s.x + s.y * s.y;
             rr.x = dw[u].x - ww[u].x * s.x;
             rr.y = dw[u].y - ww[u].y * s.y;
           }
@@ -264,6 +282,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
         buf[j] = bl ? cmul(rr, chirp(Tq, j, n)) : rr;
       }
     }
+    double dd = (double)dd_t, ss = (double)ss_t;
     for (int o = 16; o > 0; o >>= 1) {
       dd += __shfl_down_sync(0xffffffffu, dd, o);
       ss += __shfl_down_sync(0xffffffffu, ss, o);
