@@ -64,8 +64,13 @@ typedef enum {
  * DM_FP64: everything in FP64.
  * DM_MIXED_FP32: FP64 recurrence (Legendre/Wigner values generated in FP64),
  *   FP32 contraction, FP32 ring FFTs and maps on the device; FP64 per-l 3x3
- *   filter, FP64 harmonic state and FP64 convergence norms. */
-typedef enum { DM_FP64 = 0, DM_MIXED_FP32 = 1 } dm_precision;
+ *   filter, FP64 harmonic state and FP64 convergence norms.
+ * DM_FLOAT_FLOAT: the FP64 path with the two Legendre stages computed in
+ *   float-float arithmetic (pairs of FP32 numbers, about 48 significant bits)
+ *   from FP64-generated tables on the FP32 pipe: FP64-class results (relative
+ *   error near 1e-13 per transform) at a fraction of the FP64 cost on GPUs
+ *   whose FP64 rate is low.  Not in the paper (an arithmetic choice). */
+typedef enum { DM_FP64 = 0, DM_MIXED_FP32 = 1, DM_FLOAT_FLOAT = 2 } dm_precision;
 
 /* Cooling and stopping schedule of Algorithm 1 (Section 3.2).
  * Levels: lambda_k = xi_k / T_h = lambda0^(1 - k/(n_levels-1)), k = 0..n_levels-1,
@@ -110,7 +115,7 @@ const char *dm_last_error(const dm_plan *plan);
 /* Sizes of the plan: npix, nalm, nrings, device bytes held. */
 dm_status dm_plan_info(const dm_plan *plan, int64_t *npix, int64_t *nalm, int *nrings, int64_t *workspace_bytes);
 
-/* Arithmetic mode (default DM_FP64). */
+/* Arithmetic mode (default DM_FP64); DM_EBUSY while a solve is in progress. */
 dm_status dm_set_precision(dm_plan *plan, dm_precision prec);
 
 /* Signal covariance, Eq. 10: host array cl[4][lmax+1] (TT, EE, BB, TE).
@@ -170,6 +175,10 @@ dm_status dm_solve_end(dm_plan *plan, double *s_out, double *alm_out, dm_stats *
  * the end, so the iteration keeps the FP64 fixed point (classical mixed
  * precision iterative refinement; no counterpart in the paper). */
 dm_status dm_set_refinement(dm_plan *plan, int anchor_every);
+
+/* Arithmetic of those anchors: DM_FLOAT_FLOAT (default; FP64-class accuracy
+ * on the FP32 pipe) or DM_FP64 (FP64 pipe); DM_EINVAL for other values. */
+dm_status dm_set_anchor_precision(dm_plan *plan, dm_precision prec);
 
 /* Tensor cores for the mixed-precision Legendre stages (default on): with a
  * batch of 8, 16, 32 or 64 RHS the contractions over l and over ring pairs

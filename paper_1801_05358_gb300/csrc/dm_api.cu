@@ -48,7 +48,7 @@ void free_all(dm_plan *p) {
                   p->ptab, p->rc32, p->apart32, p->s32, p->w32, p->wd32, p->phase32, p->bhat32, p->twid32,
                   p->a_hi, p->g_hi, p->shi32, p->s64, p->rhi, p->tc_err, p->ring_order,
                   p->tc_synA[0], p->tc_synA[1], p->tc_anaA[0], p->tc_anaA[1], p->tc_soff, p->tc_aoff,
-                  p->tc_synB[0], p->tc_synB[1]};
+                  p->tc_synB[0], p->tc_synB[1], p->ptab_lo};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -158,6 +158,7 @@ dm_status anchor(dm_plan *p, cudaStream_t st, bool initial, const double *d, boo
   const size_t mn = sizeof(double) * 3 * p->npix * p->batch;
   p->state_active = false;
   p->prec = DM_FP64;
+  p->ff_now = p->anchor_ff;
   cudaError_t e = cudaSuccess;
   cudaEvent_t ta = nullptr, tb = nullptr;
   if (p->prof_on) {
@@ -183,6 +184,7 @@ dm_status anchor(dm_plan *p, cudaStream_t st, bool initial, const double *d, boo
     p->launches += 3;
   }
   p->prec = DM_MIXED_FP32;
+  p->ff_now = false;
   if (!e) e = cudaMemsetAsync(p->s32, 0, sizeof(float) * 3 * p->npix * p->batch, st);
   if (!e)
     e = cudaMemsetAsync(p->rc32, 0, sizeof(float2) * (size_t)p->batch * 3 * (p->mmax + 1) * p->npairs * 2, st);
@@ -415,9 +417,20 @@ dm_status dm_plan_info(const dm_plan *p, int64_t *npix, int64_t *nalm, int *nrin
 
 dm_status dm_set_precision(dm_plan *p, dm_precision prec) {
   if (!p) return DM_EINVAL;
-  if (prec != DM_FP64 && prec != DM_MIXED_FP32) return fail(p, DM_EINVAL, "unknown precision mode");
-  if (prec == DM_MIXED_FP32) DM_CU(setup_fp32(p), "mixed-precision tables");
-  p->prec = prec;
+  if (prec != DM_FP64 && prec != DM_MIXED_FP32 && prec != DM_FLOAT_FLOAT)
+    return fail(p, DM_EINVAL, "unknown precision mode");
+  if (p->session) return fail(p, DM_EBUSY, "a solve is in progress");
+  if (prec != DM_FP64) DM_CU(setup_fp32(p), "float tables");
+  // DM_FLOAT_FLOAT runs the FP64 path with float-float Legendre stages
+  p->prec = prec == DM_MIXED_FP32 ? DM_MIXED_FP32 : DM_FP64;
+  p->ff_legendre = prec == DM_FLOAT_FLOAT;
+  return DM_OK;
+}
+
+dm_status dm_set_anchor_precision(dm_plan *p, dm_precision prec) {
+  if (!p) return DM_EINVAL;
+  if (prec != DM_FP64 && prec != DM_FLOAT_FLOAT) return fail(p, DM_EINVAL, "anchors run in DM_FP64 or DM_FLOAT_FLOAT");
+  p->anchor_ff = prec == DM_FLOAT_FLOAT;
   return DM_OK;
 }
 

@@ -128,6 +128,10 @@ struct dm_plan {
   int64_t bytes = 0;
   // DM_MIXED_FP32 resources (allocated by dm_set_precision)
   float *ptab = nullptr;        // [3][nalm][npairs] lambda, lam+, lam- in FP32 (FP64 recurrence)
+  float *ptab_lo = nullptr;     // [3][nalm][npairs] FP64 value - ptab: float-float tables
+  bool ff_legendre = false;     // DM_FLOAT_FLOAT: Legendre stages in float-float
+  bool anchor_ff = true;        // mixed-mode anchors in float-float (else FP64)
+  bool ff_now = false;          // inside a float-float anchor
   float2 *rc32 = nullptr;       // [B][3][mmax+1][npairs][2]
   float2 *apart32 = nullptr;    // [B][nchunk][3][nalm]
   float *s32 = nullptr;         // [B][3][npix] iteration map
@@ -201,6 +205,8 @@ bool tc_batch_ok(int B);
 size_t tc_table_bytes(int lmax, int mmax, int npairs, int B);
 cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t st);
 cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st);
+cudaError_t legendre_synthesis_ff(dm_plan *p, const double2 *alm, cudaStream_t st);
+cudaError_t legendre_analysis_ff_parts(dm_plan *p, cudaStream_t st);
 
 // driver (dm_api.cu), shared with the server (dm_serve.cu)
 dm_status upload_levels(dm_plan *p);

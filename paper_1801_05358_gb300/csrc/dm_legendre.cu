@@ -180,6 +180,7 @@ cudaError_t legendre_analysis32(dm_plan *p, int epilogue, double2 *out, cudaStre
 
 cudaError_t legendre_synthesis(dm_plan *p, const double2 *alm, cudaStream_t st) {
   if (p->prec != DM_FP64) return legendre_synthesis32(p, alm, st);
+  if (p->ff_legendre || p->ff_now) return legendre_synthesis_ff(p, alm, st);
   dim3 grid((p->npairs + SYN_THREADS - 1) / SYN_THREADS, p->mmax + 1, p->batch);
   k_leg_syn64<<<grid, SYN_THREADS, 0, st>>>(p->pairs, p->rec, p->seed, p->seed_exp, alm, p->rc, p->lmax, p->mmax,
                                            p->npairs, p->nalm, p->state_active ? p->state : nullptr);
@@ -320,8 +321,13 @@ cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream
   if (p->prec != DM_FP64) return legendre_analysis32(p, epilogue, out, st, mid);
   dim3 grid(p->nchunk, p->mmax + 1, p->batch);
   const SolveState *stp = p->state_active ? p->state : nullptr;
-  k_leg_ana64<<<grid, ANA_P, 0, st>>>(p->pairs, p->rec, p->seed, p->seed_exp, p->rc, p->apart, p->lmax, p->mmax,
-                                      p->npairs, p->nalm, p->nchunk, stp);
+  if (p->ff_legendre || p->ff_now) {
+    cudaError_t e = legendre_analysis_ff_parts(p, st);
+    if (e) return e;
+  } else {
+    k_leg_ana64<<<grid, ANA_P, 0, st>>>(p->pairs, p->rec, p->seed, p->seed_exp, p->rc, p->apart, p->lmax, p->mmax,
+                                        p->npairs, p->nalm, p->nchunk, stp);
+  }
   if (mid) cudaEventRecord(mid, st);
   double omega = 4.0 * M_PI / (double)p->npix;
   dim3 g2((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
@@ -361,7 +367,8 @@ cudaError_t apply_filter_level(dm_plan *p, const double *coef, const double2 *in
 
 __global__ void __launch_bounds__(128) k_gen_tables(const PairDev *__restrict__ pairs, const RecCoef *__restrict__ rec,
                                                     const double *__restrict__ seed, const int *__restrict__ seed_exp,
-                                                    float *__restrict__ ptab, int lmax, int npairs, int64_t nalm) {
+                                                    float *__restrict__ ptab, float *__restrict__ ptab_lo, int lmax,
+                                                    int npairs, int64_t nalm) {
   __shared__ RecCoef sc[SYN_CH];
   const int m = blockIdx.y;
   const int p = blockIdx.x * 128 + threadIdx.x;
@@ -382,9 +389,14 @@ __global__ void __launch_bounds__(128) k_gen_tables(const PairDev *__restrict__ 
       if (act) {
         const int64_t o = (base + l) * (int64_t)npairs + p;
         const bool live = (s.S == 0);
-        ptab[o] = live ? (float)s.l0 : 0.0f;
-        ptab[plane + o] = live ? (float)s.p0 : 0.0f;
-        ptab[2 * plane + o] = live ? (float)s.q0 : 0.0f;
+        const double v0 = live ? s.l0 : 0.0, v1 = live ? s.p0 : 0.0, v2 = live ? s.q0 : 0.0;
+        const float h0 = (float)v0, h1 = (float)v1, h2 = (float)v2;
+        ptab[o] = h0;
+        ptab[plane + o] = h1;
+        ptab[2 * plane + o] = h2;
+        ptab_lo[o] = (float)(v0 - (double)h0);
+        ptab_lo[plane + o] = (float)(v1 - (double)h1);
+        ptab_lo[2 * plane + o] = (float)(v2 - (double)h2);
       }
       if (l < lmax) rec_advance(s, sc[j], x, m, l, seed, pp, npairs);
     }
@@ -393,7 +405,8 @@ __global__ void __launch_bounds__(128) k_gen_tables(const PairDev *__restrict__ 
 
 cudaError_t gen_tables32(dm_plan *p) {
   dim3 g((p->npairs + 127) / 128, p->mmax + 1);
-  k_gen_tables<<<g, 128>>>(p->pairs, p->rec, p->seed, p->seed_exp, p->ptab, p->lmax, p->npairs, p->nalm);
+  k_gen_tables<<<g, 128>>>(p->pairs, p->rec, p->seed, p->seed_exp, p->ptab, p->ptab_lo, p->lmax, p->npairs,
+                           p->nalm);
   return cudaGetLastError();
 }
 

@@ -357,56 +357,54 @@ __device__ __forceinline__ void load_pairs8(const float2 *__restrict__ g, int pa
   }
 }
 
+// Analysis B operand, split in two so that the loads of step c + 1 are in
+// flight while step c is converted and multiplied.  One task per thread at
+// most (PART 0: 2B tasks, PART 1: 4B tasks, B <= 64).
+//  PART 0 task = (b / 4) * 8 + (b & 3) * 2 + ko: rows 2b, 2b + 1
+//  PART 1 task = (b / 2) * 8 + (b & 1) * 4 + f * 2 + ko, f = 0 (Q) / 1 (U)
 template <int PART>
-__device__ __forceinline__ void stage_ana_b(unsigned char *Bbuf, int tileB, const float2 *__restrict__ rc, int m,
-                                            int c, int par, int mmax, int npairs, int B) {
+__device__ __forceinline__ void load_ana_b(int task, const float2 *__restrict__ rc, int m, int c, int mmax,
+                                           int npairs, float2 v[16]) {
+  const int ko = task & 1;
+  const int b = PART == 0 ? (task >> 3) * 4 + ((task >> 1) & 3) : (task >> 3) * 2 + ((task >> 2) & 1);
+  const int f = PART == 0 ? 0 : 1 + ((task >> 1) & 1);
+  load_pairs8(rc + (((int64_t)b * 3 + f) * (mmax + 1) + m) * npairs * 2, 16 * c + 8 * ko, npairs, v);
+}
+
+template <int PART>
+__device__ __forceinline__ void convert_ana_b(int task, unsigned char *Bbuf, int tileB, int par, const float2 v[16]) {
   const float sgn = par == 0 ? 1.f : -1.f;  // G_par = G_N + sgn G_S
+  const int ko = task & 1;
   if (PART == 0) {
-    // task = (b / 4) * 8 + (b & 3) * 2 + ko: rows 2b, 2b + 1
-    for (int task = threadIdx.x; task < 2 * B; task += TC_THREADS) {
-      const int ko = task & 1, b = (task >> 3) * 4 + ((task >> 1) & 3);
-      float2 v[16];
-      load_pairs8(rc + (((int64_t)b * 3 + 0) * (mmax + 1) + m) * npairs * 2, 16 * c + 8 * ko, npairs, v);
-      float re[8], im[8];
+    const int b = (task >> 3) * 4 + ((task >> 1) & 3);
+    float re[8], im[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        re[i] = v[2 * i].x + sgn * v[2 * i + 1].x;
-        im[i] = v[2 * i].y + sgn * v[2 * i + 1].y;
-      }
-      put_row(Bbuf, tileB, 2 * b + ko, ko, ko ? im : re);
-      put_row(Bbuf, tileB, 2 * b + (ko ^ 1), ko, ko ? re : im);
+    for (int i = 0; i < 8; ++i) {
+      re[i] = v[2 * i].x + sgn * v[2 * i + 1].x;
+      im[i] = v[2 * i].y + sgn * v[2 * i + 1].y;
     }
+    put_row(Bbuf, tileB, 2 * b + ko, ko, ko ? im : re);
+    put_row(Bbuf, tileB, 2 * b + (ko ^ 1), ko, ko ? re : im);
   } else {
-    // task = (b / 2) * 8 + (b & 1) * 4 + f * 2 + ko, f = 0 (Q) / 1 (U)
-    for (int task = threadIdx.x; task < 4 * B; task += TC_THREADS) {
-      const int ko = task & 1, f = (task >> 1) & 1, b = (task >> 3) * 2 + ((task >> 2) & 1);
-      float2 v[16];
-      load_pairs8(rc + (((int64_t)b * 3 + 1 + f) * (mmax + 1) + m) * npairs * 2, 16 * c + 8 * ko, npairs, v);
-      float pr[8], pi[8], or_[8], oi[8];  // this parity and the opposite one
+    const int f = (task >> 1) & 1, b = (task >> 3) * 2 + ((task >> 2) & 1);
+    float a0[8], a1[8], b0[8], b1[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        pr[i] = v[2 * i].x + sgn * v[2 * i + 1].x;
-        pi[i] = v[2 * i].y + sgn * v[2 * i + 1].y;
-        or_[i] = v[2 * i].x - sgn * v[2 * i + 1].x;
-        oi[i] = v[2 * i].y - sgn * v[2 * i + 1].y;
-      }
-      float a0[8], a1[8], b0[8], b1[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        // B1: Q -> rows 4b (-Qp.re), 4b+1 (-Qp.im); U -> rows 4b+2 (-Up.re), 4b+3 (-Up.im)
-        a0[i] = -pr[i];
-        a1[i] = -pi[i];
-        // B2: U -> rows 4b (Uo.im), 4b+1 (-Uo.re); Q -> rows 4b+2 (-Qo.im), 4b+3 (Qo.re)
-        b0[i] = f == 1 ? oi[i] : -oi[i];
-        b1[i] = f == 1 ? -or_[i] : or_[i];
-      }
-      unsigned char *B1 = Bbuf, *B2 = Bbuf + 2 * tileB;
-      const int r1 = 4 * b + 2 * f, r2 = 4 * b + 2 * (1 - f);
-      put_row(B1, tileB, r1 + ko, ko, ko ? a1 : a0);
-      put_row(B1, tileB, r1 + (ko ^ 1), ko, ko ? a0 : a1);
-      put_row(B2, tileB, r2 + ko, ko, ko ? b1 : b0);
-      put_row(B2, tileB, r2 + (ko ^ 1), ko, ko ? b0 : b1);
+    for (int i = 0; i < 8; ++i) {
+      const float pr = v[2 * i].x + sgn * v[2 * i + 1].x, pi = v[2 * i].y + sgn * v[2 * i + 1].y;  // this parity
+      const float orr = v[2 * i].x - sgn * v[2 * i + 1].x, oi = v[2 * i].y - sgn * v[2 * i + 1].y;  // opposite
+      // B1: Q -> rows 4b (-Qp.re), 4b+1 (-Qp.im); U -> rows 4b+2 (-Up.re), 4b+3 (-Up.im)
+      a0[i] = -pr;
+      a1[i] = -pi;
+      // B2: U -> rows 4b (Uo.im), 4b+1 (-Uo.re); Q -> rows 4b+2 (-Qo.im), 4b+3 (Qo.re)
+      b0[i] = f == 1 ? oi : -oi;
+      b1[i] = f == 1 ? -orr : orr;
     }
+    unsigned char *B1 = Bbuf, *B2 = Bbuf + 2 * tileB;
+    const int r1 = 4 * b + 2 * f, r2 = 4 * b + 2 * (1 - f);
+    put_row(B1, tileB, r1 + ko, ko, ko ? a1 : a0);
+    put_row(B1, tileB, r1 + (ko ^ 1), ko, ko ? a0 : a1);
+    put_row(B2, tileB, r2 + ko, ko, ko ? b1 : b0);
+    put_row(B2, tileB, r2 + (ko ^ 1), ko, ko ? b0 : b1);
   }
 }
 
@@ -439,11 +437,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ana_tc(const unsigned char *_
     mbar_expect_tx(&full[0], (uint32_t)abytes);
     bulk_g2s(sm, tabm, (uint32_t)abytes, &full[0]);
   }
+  const bool has = tid < (PART == 0 ? 2 * B : 4 * B);
+  float2 v[16];
+  if (has) load_ana_b<PART>(tid, rc, m, 0, mmax, npairs, v);
   for (int c = 0; c < nsteps; ++c) {
     const int s = c & 1;
     unsigned char *Abuf = sm + s * stage, *Bbuf = Abuf + abytes;
     if (c >= 2) mbar_wait(&done[s], ((c - 2) >> 1) & 1, err);
-    stage_ana_b<PART>(Bbuf, tileB, rc, m, c, par, mmax, npairs, B);
+    if (has) {
+      convert_ana_b<PART>(tid, Bbuf, tileB, par, v);
+      if (c + 1 < nsteps) load_ana_b<PART>(tid, rc, m, c + 1, mmax, npairs, v);
+    }
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {

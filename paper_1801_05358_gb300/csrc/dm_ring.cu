@@ -71,10 +71,15 @@ __device__ __forceinline__ C fold_one(const C *S, int k, int n, int mmax) {
 }
 
 // Bluestein chirp c_j = e^{-i pi j^2 / h} = e^{-i pi (2 j^2 mod 2n) / n}, n = 2h
+// (32-bit arithmetic: j < h <= 2^15 keeps 2 j^2 below 2^32)
 template <typename C>
 __device__ __forceinline__ C chirp(const C *Tq, int j, int n) {
-  return phase_q(Tq, (int)((2LL * j * j) % (2LL * n)), n);
+  const unsigned jj = (unsigned)j;
+  return phase_q(Tq, (int)((2u * jj * jj) % (2u * (unsigned)n)), n);
 }
+
+// x mod n for 0 <= x, skipping the division in the common case x < n
+__device__ __forceinline__ int mod_small(int x, int n) { return x < n ? x : x % n; }
 
 // Length-h forward DFT of the CTA's lanes in place.  Direct rings (h = M a
 // power of two): bit-reversed input -> natural output.  Bluestein rings:
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int m = m0 + u * nt;
-          if (m <= mmax) S[m] = cmulc(v[u], phase_q(Tq, (m * Rg.shift) % n2, n));
+          if (m <= mmax) S[m] = cmulc(v[u], phase_q(Tq, mod_small(m * Rg.shift, n2), n));
         }
       }
     }
@@ -360,12 +365,12 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
   if (!live) return;
   const int n2 = 2 * n;
   for (int m = tx; m <= mmax; m += nt) {
-    const int q = m % n;
+    const int q = mod_small(m, n);
     const int qq = (q <= h) ? q : n - q;
     const int slot = bl ? qq : (qq == h ? M : bitrev(qq, logM));
     C X = buf[slot];
     if (q > h) X = cconj(X);
-    rc[rbase + (int64_t)m * mstride] = cmul(X, phase_q(Tq, (m * Rg.shift) % n2, n));
+    rc[rbase + (int64_t)m * mstride] = cmul(X, phase_q(Tq, mod_small(m * Rg.shift, n2), n));
   }
 }
 

@@ -411,6 +411,7 @@ cudaError_t setup_fp32(dm_plan *p) {
   if ((e = al(&p->bhat32, p->bh_total))) return e;
   if ((e = al(&p->twid32, p->fft_M_max - 1))) return e;
   if ((e = al(&p->ptab, (size_t)3 * p->nalm * p->npairs))) return e;
+  if ((e = al(&p->ptab_lo, (size_t)3 * p->nalm * p->npairs))) return e;
   if ((e = al(&p->rc32, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return e;
   if ((e = al(&p->apart32, (size_t)B * p->nchunk * 3 * p->nalm))) return e;
   if ((e = al(&p->s32, (size_t)B * n3))) return e;

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libdmwf.so")
 
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ECUDA, DM_ENOTCONV, DM_ETIMEOUT, DM_EAGAIN, DM_EBUSY = range(8)
-DM_FP64, DM_MIXED_FP32 = 0, 1
+DM_FP64, DM_MIXED_FP32, DM_FLOAT_FLOAT = 0, 1, 2
 DM_MAX_LEVELS = 64
 
 EXPORTS = [
@@ -27,6 +27,7 @@ EXPORTS = [
     "dm_profile_enable", "dm_profile_read", "dm_measure_alu_peaks", "dm_solve_begin", "dm_solve_iterate",
     "dm_solve_end", "dm_set_refinement", "dm_set_noise_mask_rhs", "dm_server_create", "dm_serve_submit",
     "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores",
+    "dm_set_anchor_precision",
     "dm_legendre_analysis_noalloc",
 ]
 DM_REQ_WF, DM_REQ_CR = 0, 1
@@ -115,6 +116,7 @@ def lib():
         L.dm_solve_iterate.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
         L.dm_solve_end.argtypes = [vp, vp, vp, vp, vp]
         L.dm_set_refinement.argtypes = [vp, ctypes.c_int]
+        L.dm_set_anchor_precision.argtypes = [vp, ctypes.c_int]
         L.dm_set_tensor_cores.argtypes = [vp, ctypes.c_int]
         L.dm_set_noise_mask_rhs.argtypes = [vp, ctypes.c_int, vp, vp]
         L.dm_server_create.argtypes = [ctypes.POINTER(DmServerConfig), ctypes.POINTER(vp)]
@@ -263,6 +265,9 @@ class Plan:
 
     def set_refinement(self, anchor_every):
         self._check(lib().dm_set_refinement(self.h, int(anchor_every)))
+
+    def set_anchor_precision(self, prec):
+        self._check(lib().dm_set_anchor_precision(self.h, int(prec)))
 
     def wiener_filter_host(self, d_host, s_host, alm_host=None, stream=None):
         stats = (DmStats * self.batch)()
