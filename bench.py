@@ -11,6 +11,10 @@ noise, band + disk mask).
 
 Metric: DM iterations/s (RHS-iterations per second summed over the batch and
 ranks); solves/s derives from it through the iteration count of a solve.
+The mixed mode re-anchors in FP64-class arithmetic every 256 iterations; the
+default timed window is exactly one such period (256 iterations, one anchor
+inside), so ``value`` is the whole-job throughput of a long solve.  For other
+--steps the anchor cost is prorated from the anchors measured in the run.
 Multi-GPU: replicas only (independent batches per rank, weak scaling).
 ``--impl reference`` times the FP64 CPU oracle instead (bounded sample).
 """
@@ -32,6 +36,8 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
+ANCHOR_EVERY = 256
+
 # algorithmic FP64 flops per (l, m, ring-pair) triple per RHS per Legendre stage:
 # accumulation 10 FMA (20 flops) + recurrence (spin 0: 4, spin +-2: 11) = 35
 FLOPS_PER_TRIPLE = 35.0
@@ -40,7 +46,7 @@ FLOPS_PER_TRIPLE = 35.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=256)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nside", type=int, default=512)
@@ -112,22 +118,33 @@ def iters_split(k, nlev=10):
     return [k // nlev + (1 if j < k % nlev else 0) for j in range(nlev)]
 
 
-def kernel_source_hash():
+# source files that define each timed kernel (a stored ncu traffic figure is
+# used only while they are unchanged)
+KERNEL_SOURCES = {
+    "k_ring_iter": ["dm_ring.cu", "dm_fft.cuh", "dm_internal.h"],
+    "k_leg_syn64": ["dm_legendre.cu", "dm_internal.h"],
+    "k_leg_ana64": ["dm_legendre.cu", "dm_internal.h"],
+    "k_syn_tc": ["dm_legendre_tc.cu", "dm_tc.cuh", "dm_internal.h"],
+    "k_ana_tc": ["dm_legendre_tc.cu", "dm_tc.cuh", "dm_internal.h"],
+}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha1()
-    for fn in ["dm_legendre.cu", "dm_internal.h"]:
+    for fn in KERNEL_SOURCES.get(kernel, ["dm_legendre.cu", "dm_internal.h"]):
         h.update(open(os.path.join(ROOT, "paper_1801_05358_gb300", "csrc", fn), "rb").read())
     return h.hexdigest()[:12]
 
 
 def traffic_for(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, null when stale."""
+    """DRAM bytes per timed unit from the committed ncu summary, null when stale."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     try:
         tab = json.load(open(path))
         e = tab.get(f"{kernel}@{workload}")
-        if e and e.get("source_hash") == kernel_source_hash():
+        if e and e.get("source_hash") == kernel_source_hash(kernel):
             return e.get("dram_bytes_per_launch")
     except Exception:
         pass
@@ -248,6 +265,24 @@ def main():
         fms = f0.elapsed_time(f1)
         fp64_line = {"value": B * nf / (fms * 1e-3), "unit": "DM iterations/s", "steps": nf,
                      "ms_per_step": fms / nf}
+    # ---- the float-float Legendre path (FP64-class results on the FP32 pipe) ----
+    ff_line = None
+    if args.fp64_steps > 0 and prec != dmwf.DM_FP64:
+        nf = args.fp64_steps
+        plan.set_precision(dmwf.DM_FLOAT_FLOAT)
+        real_schedule(nf)
+        plan.solve_begin(d)
+        plan.solve_iterate(1)            # warm
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        f0.record()
+        plan.solve_iterate(nf)
+        f1.record()
+        torch.cuda.synchronize()
+        plan.solve_end()
+        fms = f0.elapsed_time(f1)
+        ff_line = {"value": B * nf / (fms * 1e-3), "unit": "DM iterations/s", "steps": nf,
+                   "ms_per_step": fms / nf, "precision": "DM_FLOAT_FLOAT"}
     plan.set_precision(prec)
 
     # ---- warm-up: begin a solve and run W iterations through the public API ----
@@ -283,51 +318,84 @@ def main():
     iters = prof["iterations"]
     assert iters == K, f"timed {iters} iterations, expected {K}"
     assert stats[0]["iters_total"] == Wu + K, stats[0]["iters_total"]
-    value = B * K * ws / (ms_max * 1e-3)
+    raw_value = B * K * ws / (ms_max * 1e-3)
+    value = raw_value
     anchor = None
     if prec != dmwf.DM_FP64:
-        ams = warm_prof["ms_anchor"] / max(1, warm_prof["anchors"])
-        every = 256
+        n_anch = warm_prof["anchors"] + prof["anchors"]
+        ams = (warm_prof["ms_anchor"] + prof["ms_anchor"]) / max(1, n_anch)
+        every = ANCHOR_EVERY
+        whole_ms = ms_max - prof["ms_anchor"] + ams * K / every
+        value = B * K * ws / (whole_ms * 1e-3)
         anchor = {"ms_per_anchor": ams, "anchor_every": every, "anchors_in_timed_window": prof["anchors"],
-                  "amortized_value": B * K * ws / ((ms_max - prof["ms_anchor"] + ams * K / every) * 1e-3)}
+                  "timed_window_value": raw_value,
+                  "steady_value_between_anchors": B * K * ws / ((ms_max - prof["ms_anchor"]) * 1e-3),
+                  "note": "value = K iterations plus K/anchor_every of a measured anchor; with the default "
+                          "K = anchor_every the window holds exactly one anchor and value = timed_window_value"}
 
-    # ---- dominant kernel roofline (Legendre stage) ----
+    # ---- rooflines of the four stages; the dominant one is reported ----
     npairs = 2 * nside
+    nrings = 4 * nside - 1
+    mmax = lmax
     triples = nalm * npairs
-    ms_syn = prof["ms_synthesis"] / max(1, prof["iterations"])
-    ms_ana = prof["ms_analysis"] / max(1, prof["iterations"])
-    suffix = "64" if prec == dmwf.DM_FP64 else "32"
-    if ms_syn >= ms_ana:
-        kname, kms = "k_leg_syn" + suffix, ms_syn
-    else:
-        kname, kms = "k_leg_ana" + suffix, ms_ana
+    its = max(1, prof["iterations"])
+    stage = {k: prof[k] / its for k in ["ms_analysis", "ms_reduce", "ms_synthesis", "ms_ring", "ms_control"]}
     workload_name = f"nside{nside}_lmax{lmax}_B{B}"
-    stage = {k: prof[k] / max(1, prof["iterations"]) for k in
-             ["ms_analysis", "ms_reduce", "ms_synthesis", "ms_ring", "ms_control"]}
-    if prec == dmwf.DM_FP64:
-        achieved = FLOPS_PER_TRIPLE * triples * B / (kms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak,
-                    "peak_source": "FP64 FMA-chain probe measured live on this GPU (dm_measure_alu_peaks)"}
-    else:
-        # FP32 contraction from FP32 tables: 20 flops per triple per RHS on the
-        # FP32 pipe; the 3 table values per triple are read once per launch.
-        flops = 20.0 * triples * B
-        tbytes = 12.0 * triples
-        ach_f = flops / (kms * 1e-3) / 1e12
-        ach_b = tbytes / (kms * 1e-3) / 1e9
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        if ach_f / fp32_peak >= ach_b / hbm:
-            roofline = {"bound": "alu", "achieved": ach_f, "peak": fp32_peak, "unit": "TFLOP/s",
-                        "frac": ach_f / fp32_peak,
-                        "peak_source": "FP32 FMA-chain probe measured live on this GPU (dm_measure_alu_peaks)"}
-        else:
-            roofline = {"bound": "hbm", "achieved": ach_b, "peak": hbm, "unit": "GB/s", "frac": ach_b / hbm,
-                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
-    roofline.update({"traffic": traffic_for(kname, workload_name), "kernel": kname, "ms_per_launch": kms,
-                     "stage_ms_per_iter": stage, "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak})
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s (of fallback)"
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    bf16_src = ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured; timed inside a long step)"
+                if "bf16_tflops_sustained" in peaks else "fallback 1700 TFLOP/s sustained (of fallback)")
+    mixed = prec != dmwf.DM_FP64
+    use_tc = mixed and B in (8, 16, 32, 64)
+    # ring stage (k_ring<RING_ITER>, one launch per FFT-size class): per pixel and
+    # RHS-field s read + s write + w read + (anchor map or w d) read; per ring, m
+    # and RHS-field the ring coefficient read + write
+    px_b, rc_b = (16.0, 16.0) if mixed else (32.0, 32.0)
+    ring_bytes = 3.0 * B * (px_b * npix + rc_b * nrings * (mmax + 1))
+    # Legendre contractions: 20 flops per (l, m, ring pair) triple per RHS
+    # (T: lambda x 2 re/im; Q, U: lam+ and lam- x 4) -- executed on the tensor
+    # cores as three BF16 products (hi*hi + hi*lo + lo*hi) in the mixed mode
+    leg_flops = 20.0 * triples * B
+    # reduce (filter + anchor term): per alm and RHS-field FP32 partial read,
+    # FP64 anchor term read, FP64 a read + write
+    red_bytes = 3.0 * B * nalm * ((8.0 if mixed else 16.0) * (1 if use_tc else (npairs + 63) // 64) + 16 * 3)
+
+    def hbm_line(kernel, nbytes, ms, traffic_key):
+        ach = nbytes / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "peak_source": hbm_src, "algorithmic_bytes": nbytes, "ms_per_launch": ms,
+                "traffic": traffic_for(traffic_key, workload_name)}
+
+    def leg_line(kernel, ms, traffic_key):
+        if use_tc:
+            ach = leg_flops / (ms * 1e-3) / 1e12
+            return {"bound": "tensor", "kernel": kernel, "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
+                    "frac": ach / bf16, "peak_source": bf16_src, "algorithmic_flops": leg_flops,
+                    "executed_tensor_flops_factor": 3, "ms_per_launch": ms,
+                    "traffic": traffic_for(traffic_key, workload_name)}
+        peak = fp32_peak if mixed else fp64_peak
+        flops = leg_flops if mixed else FLOPS_PER_TRIPLE * triples * B
+        ach = flops / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "peak_source": "FMA-chain probe measured live on this GPU (dm_measure_alu_peaks)",
+                "algorithmic_flops": flops, "ms_per_launch": ms, "traffic": traffic_for(traffic_key, workload_name)}
+
+    stages = {
+        "ring": hbm_line("k_ring<RING_ITER> (one launch per FFT-size class)", ring_bytes, stage["ms_ring"],
+                         "k_ring_iter"),
+        "synthesis": leg_line("k_syn_b + k_syn_tc<0,1>" if use_tc else ("k_leg_syn32" if mixed else "k_leg_syn64"),
+                              stage["ms_synthesis"], "k_syn_tc" if use_tc else "k_leg_syn64"),
+        "analysis": leg_line("k_ana_tc<0,1>" if use_tc else ("k_leg_ana32" if mixed else "k_leg_ana64"),
+                             stage["ms_analysis"], "k_ana_tc" if use_tc else "k_leg_ana64"),
+        "reduce": hbm_line("k_ana_reduce32" if mixed else "k_ana_reduce", red_bytes, stage["ms_reduce"], "k_reduce"),
+    }
+    dom = max(stages, key=lambda k: stages[k]["ms_per_launch"])
+    roofline = dict(stages[dom])
+    roofline.update({"stage": dom, "stage_ms_per_iter": stage, "stages": stages,
+                     "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak})
 
     # ---- end to end through the host-buffer entry point ----
     e2e = None
@@ -360,8 +428,9 @@ def main():
 
     if rank == 0:
         line = {"metric": "DM iterations/s", "value": value, "unit": "DM iterations/s", "n_gpus": ws,
-                "steps": K, "warmup": Wu, "ms_per_step": ms_max / K, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == dmwf.DM_FP64 else "f32+f64",
+                "steps": K, "warmup": Wu, "ms_per_step": B * ws / value * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == dmwf.DM_FP64 else "f32 (bf16x3 tensor-core Legendre, f64 harmonic state)",
                 "data": "synthetic",
                 "config": {"workload": f"batched constrained realisations nside {nside} lmax {lmax}: "
                                        f"{nwf} WF + {B - nwf} fluctuation RHS per launch (seeds 100..{99 + B})",
@@ -369,7 +438,7 @@ def main():
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "l2": "inputs larger than L2 (maps and ring coefficients exceed 129 MB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["launches"],
-                "fp64_gpu": fp64_line, "refinement": anchor,
+                "fp64_gpu": fp64_line, "ff64_gpu": ff_line, "refinement": anchor,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     plan.close()

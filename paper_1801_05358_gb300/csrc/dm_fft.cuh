@@ -62,10 +62,16 @@ __device__ __forceinline__ T2 cmul_negi(T2 a) {  // a * (-i)
   return r;
 }
 
+// Shared-memory slot of element i of a transform buffer: one pad entry every 32
+// elements, so that the power-of-two strides of the bit-reversed order and of
+// the short butterflies do not all fall into the same bank.  A buffer of n
+// elements takes spad(n - 1) + 1 entries.
+__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
+
 // index k of a size-2^logM transform in bit-reversed order
 __device__ __forceinline__ int bitrev(int k, int logM) { return (int)(__brev((unsigned)k) >> (32 - logM)); }
 
-// In place, natural order in, bit-reversed order out.  Threads threadIdx.x of
+// In place (slots spad(i)), natural order in, bit-reversed order out.  Threads threadIdx.x of
 // blockDim.x take part (every y-slice of the block runs its own transform in
 // lockstep); the caller syncs before, this ends with a block barrier.
 template <typename T2>
@@ -79,22 +85,22 @@ __device__ void fft_dif(T2 *x, int M, const T2 *tws) {
     for (int k = tx; k < (M >> 2); k += nt) {
       const int j = k & (L - 1);
       const int i0 = ((k - j) << 2) + j;
-      const T2 a0 = x[i0], a1 = x[i0 + L], a2 = x[i0 + 2 * L], a3 = x[i0 + 3 * L];
+      const T2 a0 = x[spad(i0)], a1 = x[spad(i0 + L)], a2 = x[spad(i0 + 2 * L)], a3 = x[spad(i0 + 3 * L)];
       const T2 w2 = tws[2 * L - 1 + j], w1 = tws[L - 1 + j];
       const T2 b0 = cadd(a0, a2), b2 = cmul(csub(a0, a2), w2);
       const T2 b1 = cadd(a1, a3), b3 = cmul_negi(cmul(csub(a1, a3), w2));
-      x[i0] = cadd(b0, b1);
-      x[i0 + L] = cmul(csub(b0, b1), w1);
-      x[i0 + 2 * L] = cadd(b2, b3);
-      x[i0 + 3 * L] = cmul(csub(b2, b3), w1);
+      x[spad(i0)] = cadd(b0, b1);
+      x[spad(i0 + L)] = cmul(csub(b0, b1), w1);
+      x[spad(i0 + 2 * L)] = cadd(b2, b3);
+      x[spad(i0 + 3 * L)] = cmul(csub(b2, b3), w1);
     }
     __syncthreads();
   }
   if (logM & 1) {  // last single stage, half-length 1 (twiddle 1)
     for (int k = tx; k < (M >> 1); k += nt) {
-      const T2 u = x[2 * k], v = x[2 * k + 1];
-      x[2 * k] = cadd(u, v);
-      x[2 * k + 1] = csub(u, v);
+      const T2 u = x[spad(2 * k)], v = x[spad(2 * k + 1)];
+      x[spad(2 * k)] = cadd(u, v);
+      x[spad(2 * k + 1)] = csub(u, v);
     }
     __syncthreads();
   }
@@ -109,9 +115,9 @@ __device__ void fft_dit(T2 *x, int M, const T2 *tws) {
   int L = 1;
   if (logM & 1) {  // first single stage, half-length 1
     for (int k = tx; k < (M >> 1); k += nt) {
-      const T2 u = x[2 * k], v = x[2 * k + 1];
-      x[2 * k] = cadd(u, v);
-      x[2 * k + 1] = csub(u, v);
+      const T2 u = x[spad(2 * k)], v = x[spad(2 * k + 1)];
+      x[spad(2 * k)] = cadd(u, v);
+      x[spad(2 * k + 1)] = csub(u, v);
     }
     __syncthreads();
     L = 2;
@@ -120,18 +126,18 @@ __device__ void fft_dit(T2 *x, int M, const T2 *tws) {
     for (int k = tx; k < (M >> 2); k += nt) {
       const int j = k & (L - 1);
       const int i0 = ((k - j) << 2) + j;
-      const T2 a0 = x[i0], a1 = x[i0 + L], a2 = x[i0 + 2 * L], a3 = x[i0 + 3 * L];
+      const T2 a0 = x[spad(i0)], a1 = x[spad(i0 + L)], a2 = x[spad(i0 + 2 * L)], a3 = x[spad(i0 + 3 * L)];
       const T2 w1 = tws[L - 1 + j], w2 = tws[2 * L - 1 + j];
       T2 v = cmul(a1, w1);
       const T2 b0 = cadd(a0, v), b1 = csub(a0, v);
       v = cmul(a3, w1);
       const T2 b2 = cadd(a2, v), b3 = csub(a2, v);
       v = cmul(b2, w2);
-      x[i0] = cadd(b0, v);
-      x[i0 + 2 * L] = csub(b0, v);
+      x[spad(i0)] = cadd(b0, v);
+      x[spad(i0 + 2 * L)] = csub(b0, v);
       v = cmul_negi(cmul(b3, w2));
-      x[i0 + L] = cadd(b1, v);
-      x[i0 + 3 * L] = csub(b1, v);
+      x[spad(i0 + L)] = cadd(b1, v);
+      x[spad(i0 + 3 * L)] = csub(b1, v);
     }
     __syncthreads();
   }

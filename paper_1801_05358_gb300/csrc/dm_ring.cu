@@ -93,7 +93,7 @@ __device__ __forceinline__ void ring_dft(C *buf, int M, int bluestein, const C *
     return;
   }
   fft_dif(buf, M, tws);
-  for (int k = threadIdx.x; k < M; k += blockDim.x) buf[k] = cconj(cmul(buf[k], bhat[k]));
+  for (int k = threadIdx.x; k < M; k += blockDim.x) buf[spad(k)] = cconj(cmul(buf[spad(k)], bhat[k]));
   __syncthreads();
   fft_dit(buf, M, tws);
 }
@@ -102,7 +102,7 @@ __device__ __forceinline__ void ring_dft(C *buf, int M, int bluestein, const C *
 template <typename C>
 __device__ __forceinline__ C dft_out(const C *buf, int k, int bluestein, const C *Tq, int n, float invM_f,
                                      double invM_d) {
-  C v = buf[k];
+  C v = buf[spad(k)];
   if (bluestein) {
     v = cconj(v);
     const auto inv = sizeof(v.x) == 4 ? (decltype(v.x))invM_f : (decltype(v.x))invM_d;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
   const int logM = 31 - __clz(M);
   C *tws = reinterpret_cast<C *>(sm_raw);  // stage twiddles (M - 1 used)
   C *Tq = tws + tw_words;                  // quarter phase table (n/2 + 1 used)
-  C *buf = Tq + ph_words + (size_t)g * lane_words;  // M + 1 entries
+  C *buf = Tq + ph_words + (size_t)g * lane_words;  // slots spad(0..M)
   C *S = buf + buf_words;                            // mmax + 1 staged coefficients (inverse modes)
   const int tx = threadIdx.x, nt = blockDim.x;
   {
@@ -207,15 +207,15 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
         Z.x = E.x - O.y;
         Z.y = -(E.y + O.x);
         if (bl)
-          buf[kk] = cmul(Z, chirp(Tq, kk, n));
+          buf[spad(kk)] = cmul(Z, chirp(Tq, kk, n));
         else
-          buf[bitrev(kk, logM)] = Z;
+          buf[spad(bitrev(kk, logM))] = Z;
       }
     }
     if (bl)
       for (int j = h + tx; j < M; j += nt) {
-        buf[j].x = 0;
-        buf[j].y = 0;
+        buf[spad(j)].x = 0;
+        buf[spad(j)].y = 0;
       }
     __syncthreads();
     ring_dft(buf, M, bl, bh, tws);
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
           rr.x = 0;
           rr.y = 0;
         }
-        buf[j] = bl ? cmul(rr, chirp(Tq, j, n)) : rr;
+        buf[spad(j)] = bl ? cmul(rr, chirp(Tq, j, n)) : rr;
       }
     }
     double dd = (double)dd_t, ss = (double)ss_t;
@@ -322,13 +322,13 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
       C v;
       v.x = (R)x0;
       v.y = (R)x1;
-      buf[j] = bl ? cmul(v, chirp(Tq, j, n)) : v;
+      buf[spad(j)] = bl ? cmul(v, chirp(Tq, j, n)) : v;
     }
   }
   if (bl)
     for (int j = h + tx; j < M; j += nt) {
-      buf[j].x = 0;
-      buf[j].y = 0;
+      buf[spad(j)].x = 0;
+      buf[spad(j)].y = 0;
     }
   __syncthreads();
   // forward: Z = DFT_h(z); direct rings take natural input to bit-reversed output
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
       O.y = -half * D.x;
       const C X = cadd(E, cmul(O, phase_q(Tq, 2 * kk, n)));
       const int slot = t ? ((k == 0) ? (bl ? h : M) : sk2) : sk;
-      buf[slot] = X;
+      buf[spad(slot)] = X;
     }
   }
   __syncthreads();
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
     const int q = mod_small(m, n);
     const int qq = (q <= h) ? q : n - q;
     const int slot = bl ? qq : (qq == h ? M : bitrev(qq, logM));
-    C X = buf[slot];
+    C X = buf[spad(slot)];
     if (q > h) X = cconj(X);
     rc[rbase + (int64_t)m * mstride] = cmul(X, phase_q(Tq, mod_small(m * Rg.shift, n2), n));
   }
@@ -386,7 +386,7 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
   for (const RingClass &rc_cls : p->ring_classes) {
     const int tw_words = std::max(1, rc_cls.M - 1);
     const int ph_words = rc_cls.n / 2 + 1;
-    const int buf_words = rc_cls.M + 1;
+    const int buf_words = rc_cls.M + rc_cls.M / 32 + 1;  // slots spad(0..M)
     const bool staged = (MODE == RING_ITER || MODE == RING_INV_MAP);
     const int lane_words = buf_words + (staged ? p->mmax + 1 : 0);
     cudaFuncAttributes fa;

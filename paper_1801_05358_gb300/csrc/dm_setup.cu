@@ -64,17 +64,17 @@ __global__ void k_bhat(const RingDev *rings, const int *ring_ids, const double2 
   const double2 *p = ph + R.ph_off;
   int h = R.h, M = R.M;
   int64_t n2 = 4LL * h;
-  for (int j = threadIdx.x; j < M; j += blockDim.x) sm_b[j] = make_double2(0.0, 0.0);
+  for (int j = threadIdx.x; j < M; j += blockDim.x) sm_b[spad(j)] = make_double2(0.0, 0.0);
   __syncthreads();
   for (int j = threadIdx.x; j < h; j += blockDim.x) {
     double2 c = p[(2LL * j * j) % n2];
     double2 b = make_double2(c.x, -c.y);
-    sm_b[j] = b;
-    if (j > 0) sm_b[M - j] = b;
+    sm_b[spad(j)] = b;
+    if (j > 0) sm_b[spad(M - j)] = b;
   }
   __syncthreads();
   fft_dif(sm_b, M, twid);
-  for (int k = threadIdx.x; k < M; k += blockDim.x) bhat[R.bh_off + k] = sm_b[k];
+  for (int k = threadIdx.x; k < M; k += blockDim.x) bhat[R.bh_off + k] = sm_b[spad(k)];
 }
 
 // --------------------------------------------------- recurrence coefficients
@@ -374,7 +374,7 @@ cudaError_t build_tables(dm_plan *p) {
     int *ids;
     if ((e = cudaMalloc(&ids, sizeof(int) * bl_ring.size()))) return e;
     cudaMemcpy(ids, bl_ring.data(), sizeof(int) * bl_ring.size(), cudaMemcpyHostToDevice);
-    size_t smem = sizeof(double2) * p->fft_M_max;
+    size_t smem = sizeof(double2) * (p->fft_M_max + p->fft_M_max / 32 + 1);  // slots spad(0..M-1)
     cudaFuncSetAttribute(k_bhat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_bhat<<<(unsigned)bl_ring.size(), 256, smem>>>(p->rings, ids, p->phase, p->bhat, p->twid);
     e = cudaDeviceSynchronize();
