@@ -143,4 +143,96 @@ __device__ void fft_dit(T2 *x, int M, const T2 *tws) {
   }
 }
 
+// Bluestein convolution core of one ring, in place (slots spad(i)):
+//   x <- FFT_M( conj( FFT_M(x) * bhat ) ),  bhat in bit-reversed order,
+// for an input whose upper half [M/2, M) is zero (h <= M/2 chirped points,
+// zero-filled up to M/2 by the caller; for M < 8 up to M) and of which only
+// the lower half of the output is read.  The first DIF pass skips the zero
+// half, the last DIF stage, the product with bhat and the first DIT stage run
+// as one pass on the same slots (no barrier between them), and the last DIT
+// pass computes only the lower half.  Same threading conventions as above.
+template <typename T2>
+__device__ void bluestein_conv(T2 *x, int M, const T2 *tws, const T2 *__restrict__ bhat) {
+  const int logM = 31 - __clz(M);
+  const int tx = threadIdx.x, nt = blockDim.x;
+  const int lastL2 = (logM & 1) ? 1 : 2;  // half-length of the first stage of the last DIF pass
+  // DIF passes before the last one
+  for (int L2 = M >> 1; L2 > lastL2 && L2 >= 2; L2 >>= 2) {
+    const int L = L2 >> 1;
+    const bool zero_upper = (L2 == (M >> 1));
+    for (int k = tx; k < (M >> 2); k += nt) {
+      const int j = k & (L - 1);
+      const int i0 = ((k - j) << 2) + j;
+      const T2 w2 = tws[2 * L - 1 + j], w1 = tws[L - 1 + j];
+      const T2 a0 = x[spad(i0)], a1 = x[spad(i0 + L)];
+      T2 b0, b1, b2, b3;
+      if (zero_upper) {
+        b0 = a0;
+        b2 = cmul(a0, w2);
+        b1 = a1;
+        b3 = cmul_negi(cmul(a1, w2));
+      } else {
+        const T2 a2 = x[spad(i0 + 2 * L)], a3 = x[spad(i0 + 3 * L)];
+        b0 = cadd(a0, a2);
+        b2 = cmul(csub(a0, a2), w2);
+        b1 = cadd(a1, a3);
+        b3 = cmul_negi(cmul(csub(a1, a3), w2));
+      }
+      x[spad(i0)] = cadd(b0, b1);
+      x[spad(i0 + L)] = cmul(csub(b0, b1), w1);
+      x[spad(i0 + 2 * L)] = cadd(b2, b3);
+      x[spad(i0 + 3 * L)] = cmul(csub(b2, b3), w1);
+    }
+    __syncthreads();
+  }
+  // last DIF pass + pointwise product + first DIT pass on the same slots
+  if (logM & 1) {
+    for (int k = tx; k < (M >> 1); k += nt) {
+      const int s0 = 2 * k, s1 = 2 * k + 1;
+      const T2 u = x[spad(s0)], v = x[spad(s1)];
+      const T2 y0 = cconj(cmul(cadd(u, v), bhat[s0])), y1 = cconj(cmul(csub(u, v), bhat[s1]));
+      x[spad(s0)] = cadd(y0, y1);
+      x[spad(s1)] = csub(y0, y1);
+    }
+  } else {
+    for (int k = tx; k < (M >> 2); k += nt) {
+      const int i0 = 4 * k;
+      const T2 a0 = x[spad(i0)], a1 = x[spad(i0 + 1)], a2 = x[spad(i0 + 2)], a3 = x[spad(i0 + 3)];
+      // DIF radix-4 (unit twiddles): outputs in slots i0 .. i0 + 3
+      const T2 b0 = cadd(a0, a2), b2 = csub(a0, a2), b1 = cadd(a1, a3), b3 = cmul_negi(csub(a1, a3));
+      const T2 y0 = cconj(cmul(cadd(b0, b1), bhat[i0])), y1 = cconj(cmul(csub(b0, b1), bhat[i0 + 1]));
+      const T2 y2 = cconj(cmul(cadd(b2, b3), bhat[i0 + 2])), y3 = cconj(cmul(csub(b2, b3), bhat[i0 + 3]));
+      // DIT radix-4 (unit twiddles) on the same slots
+      const T2 c0 = cadd(y0, y1), c1 = csub(y0, y1), c2 = cadd(y2, y3), c3 = cmul_negi(csub(y2, y3));
+      x[spad(i0)] = cadd(c0, c2);
+      x[spad(i0 + 2)] = csub(c0, c2);
+      x[spad(i0 + 1)] = cadd(c1, c3);
+      x[spad(i0 + 3)] = csub(c1, c3);
+    }
+  }
+  __syncthreads();
+  // remaining DIT passes; the last one (L = M/4) writes only the lower half
+  for (int L = (logM & 1) ? 2 : 4; L < M; L <<= 2) {
+    const bool half_out = (4 * L == M);
+    for (int k = tx; k < (M >> 2); k += nt) {
+      const int j = k & (L - 1);
+      const int i0 = ((k - j) << 2) + j;
+      const T2 a0 = x[spad(i0)], a1 = x[spad(i0 + L)], a2 = x[spad(i0 + 2 * L)], a3 = x[spad(i0 + 3 * L)];
+      const T2 w1 = tws[L - 1 + j], w2 = tws[2 * L - 1 + j];
+      T2 v = cmul(a1, w1);
+      const T2 b0 = cadd(a0, v), b1 = csub(a0, v);
+      v = cmul(a3, w1);
+      const T2 b2 = cadd(a2, v), b3 = csub(a2, v);
+      const T2 v2 = cmul(b2, w2), v3 = cmul_negi(cmul(b3, w2));
+      x[spad(i0)] = cadd(b0, v2);
+      x[spad(i0 + L)] = cadd(b1, v3);
+      if (!half_out) {
+        x[spad(i0 + 2 * L)] = csub(b0, v2);
+        x[spad(i0 + 3 * L)] = csub(b1, v3);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace dmwf

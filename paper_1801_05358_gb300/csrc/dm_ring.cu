@@ -83,20 +83,21 @@ __device__ __forceinline__ int mod_small(int x, int n) { return x < n ? x : x % 
 
 // Length-h forward DFT of the CTA's lanes in place.  Direct rings (h = M a
 // power of two): bit-reversed input -> natural output.  Bluestein rings:
-// natural input already multiplied by the chirp and zero-padded to M, DIF ->
-// pointwise product with the kernel spectrum (stored in bit-reversed order) ->
-// DIT; the caller applies conj(.) / M and the output chirp when it reads.
+// natural input already multiplied by the chirp and zero-padded (to M/2, or to
+// M when M < 8), bluestein_conv (DIF -> product with the kernel spectrum in
+// bit-reversed order -> DIT); the caller applies conj(.) / M and the output
+// chirp when it reads.
 template <typename C>
 __device__ __forceinline__ void ring_dft(C *buf, int M, int bluestein, const C *__restrict__ bhat, const C *tws) {
   if (!bluestein) {
     fft_dit(buf, M, tws);
     return;
   }
-  fft_dif(buf, M, tws);
-  for (int k = threadIdx.x; k < M; k += blockDim.x) buf[spad(k)] = cconj(cmul(buf[spad(k)], bhat[k]));
-  __syncthreads();
-  fft_dit(buf, M, tws);
+  bluestein_conv(buf, M, tws, bhat);
 }
+
+// end of the zero padding a Bluestein input needs (see bluestein_conv)
+__device__ __forceinline__ int bl_zero_end(int M) { return M >= 8 ? (M >> 1) : M; }
 
 // Output k of ring_dft (k < h)
 template <typename C>
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
       }
     }
     if (bl)
-      for (int j = h + tx; j < M; j += nt) {
+      for (int j = h + tx; j < bl_zero_end(M); j += nt) {
         buf[spad(j)].x = 0;
         buf[spad(j)].y = 0;
       }
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
     }
   }
   if (bl)
-    for (int j = h + tx; j < M; j += nt) {
+    for (int j = h + tx; j < bl_zero_end(M); j += nt) {
       buf[spad(j)].x = 0;
       buf[spad(j)].y = 0;
     }
