@@ -48,7 +48,7 @@ void free_all(dm_plan *p) {
                   p->ptab, p->rc32, p->apart32, p->s32, p->w32, p->wd32, p->phase32, p->bhat32, p->twid32,
                   p->a_hi, p->g_hi, p->shi32, p->s64, p->rhi, p->tc_err, p->ring_order,
                   p->tc_synA[0], p->tc_synA[1], p->tc_anaA[0], p->tc_anaA[1], p->tc_soff, p->tc_aoff,
-                  p->tc_synB[0], p->tc_synB[1], p->ptab_lo};
+                  p->tc_synB[0], p->tc_synB[1], p->ptab_lo, p->e32, p->c32, p->clev, p->filt32};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -172,6 +172,7 @@ dm_status anchor(dm_plan *p, cudaStream_t st, bool initial, const double *d, boo
     if (!e) e = anchor_residual(p, d, nullptr, st);
     p->launches += 1;
   } else {
+    if (!e && p->anchor_active) e = materialize_a(p, st);  // the iterate lives in e between anchors
     if (!e) e = cudaMemcpyAsync(p->a_hi, p->a, an, cudaMemcpyDeviceToDevice, st);
     if (!e) e = legendre_synthesis(p, p->a_hi, st);
     if (!e) e = ring_stage(p, RING_INV_MAP, nullptr, p->s64, st);
@@ -181,7 +182,8 @@ dm_status anchor(dm_plan *p, cudaStream_t st, bool initial, const double *d, boo
   if (need_g) {
     if (!e) e = ring_stage(p, RING_FWD_MAP, p->rhi, nullptr, st);
     if (!e) e = legendre_analysis(p, ANA_PLAIN, p->g_hi, st);
-    p->launches += 3;
+    if (!e) e = anchor_c32(p, st);
+    p->launches += 4;
   }
   p->prec = DM_MIXED_FP32;
   p->ff_now = false;

@@ -34,9 +34,11 @@ __global__ void k_control_init(SolveState *st, const LevelDev *levs, int batch) 
 // a level ends when the Cauchy ratio falls below eps_k (or after its fixed
 // count); the next level lowers xi (lambda) and the last level ends the run.
 __global__ void k_control_step(SolveState *st, const LevelDev *__restrict__ levs, const double *__restrict__ norms,
-                               int nrings) {
+                               int nrings, int *clev) {
   const int b = blockIdx.x;
   if (st[b].done) return;
+  // the filtered step of this iteration ran at st[b].level (mixed mode: its c is formed)
+  if (clev != nullptr && threadIdx.x == 0) clev[b] = st[b].level;
   const LevelDev *lev = levs + b;
   __shared__ double r0[256], r1[256];
   double dd = 0.0, ss = 0.0;
@@ -93,7 +95,8 @@ cudaError_t control_init(dm_plan *p, cudaStream_t st) {
 }
 
 cudaError_t control_step(dm_plan *p, cudaStream_t st) {
-  k_control_step<<<p->batch, 256, 0, st>>>(p->state, p->lev, p->norms, p->nrings);
+  k_control_step<<<p->batch, 256, 0, st>>>(p->state, p->lev, p->norms, p->nrings,
+                                           p->anchor_active ? p->clev : nullptr);
   return cudaGetLastError();
 }
 

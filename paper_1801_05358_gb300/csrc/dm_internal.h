@@ -142,6 +142,12 @@ struct dm_plan {
   //   a = a_hi + e;  FP32 stages act on e only; g_hi = A W (d - Y a_hi) in FP64
   double2 *a_hi = nullptr;      // [B][3][nalm]
   double2 *g_hi = nullptr;      // [B][3][nalm]
+  // FP32 iteration state between anchors: e = a - a_hi, updated as
+  //   e <- c + F (e + Omega A r),  c = F (a_hi + g_hi) - a_hi  (FP64-formed per level)
+  float2 *e32 = nullptr;        // [B][3][nalm]
+  float2 *c32 = nullptr;        // [B][3][nalm]
+  int *clev = nullptr;          // [B] level at which c was formed
+  float *filt32 = nullptr;      // FP32 copy of filt
   float *shi32 = nullptr;       // [B][3][npix] Y a_hi rounded to FP32 (for ||s||)
   bool anchor_active = false;
   int anchor_every = 256;
@@ -206,6 +212,8 @@ size_t tc_table_bytes(int lmax, int mmax, int npairs, int B);
 cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t st);
 cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st);
 cudaError_t legendre_synthesis_ff(dm_plan *p, const double2 *alm, cudaStream_t st);
+cudaError_t anchor_c32(dm_plan *p, cudaStream_t st);     // c = F (a_hi + g_hi) - a_hi, e = 0
+cudaError_t materialize_a(dm_plan *p, cudaStream_t st);  // a = a_hi + e
 cudaError_t legendre_analysis_ff_parts(dm_plan *p, cudaStream_t st);
 
 // driver (dm_api.cu), shared with the server (dm_serve.cu)

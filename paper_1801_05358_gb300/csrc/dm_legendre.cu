@@ -416,6 +416,7 @@ template <int NB>
 __global__ void __launch_bounds__(SYN_THREADS) k_leg_syn32(const float *__restrict__ ptab,
                                                            const double2 *__restrict__ alm,
                                                            const double2 *__restrict__ a_sub,
+                                                           const float2 *__restrict__ e32,
                                                            float2 *__restrict__ rc, int lmax, int mmax, int npairs,
                                                            int64_t nalm, const SolveState *__restrict__ state) {
   __shared__ float2 sT[NB][SYN_CH], sE[NB][SYN_CH], sB[NB][SYN_CH];
@@ -440,6 +441,13 @@ __global__ void __launch_bounds__(SYN_THREADS) k_leg_syn32(const float *__restri
     for (int i = threadIdx.x; i < cnt * NB; i += SYN_THREADS) {
       const int k = i / cnt, j = i % cnt;
       const int64_t ob = (int64_t)(b0 + k) * 3 * nalm + base + lc + j;
+      if (e32 != nullptr) {  // FP32 iteration state e = a - a_hi
+        const float2 t = e32[ob], e = e32[ob + nalm], bb = e32[ob + 2 * nalm];
+        sT[k][j] = t;
+        sE[k][j] = make_float2(-e.x, -e.y);
+        sB[k][j] = make_float2(-bb.x, -bb.y);
+        continue;
+      }
       double2 t = alm[ob], e = alm[ob + nalm], bb = alm[ob + 2 * nalm];
       if (a_sub != nullptr) {  // correction e = a - a_hi (FP64 difference, then FP32)
         t = csub(t, a_sub[ob]);
@@ -639,13 +647,127 @@ cudaError_t legendre_synthesis32(dm_plan *p, const double2 *alm, cudaStream_t st
   const int pb = (p->npairs + SYN_THREADS - 1) / SYN_THREADS;
   if (p->batch % 4 == 0) {
     dim3 g(p->batch / 4, pb, p->mmax + 1);
-    k_leg_syn32<4><<<g, SYN_THREADS, 0, st>>>(p->ptab, alm, p->anchor_active ? p->a_hi : nullptr, p->rc32, p->lmax,
-                                              p->mmax, p->npairs, p->nalm, stp);
+    k_leg_syn32<4><<<g, SYN_THREADS, 0, st>>>(p->ptab, alm, p->anchor_active ? p->a_hi : nullptr,
+                                              p->anchor_active ? p->e32 : nullptr, p->rc32, p->lmax, p->mmax,
+                                              p->npairs, p->nalm, stp);
   } else {
     dim3 g(p->batch, pb, p->mmax + 1);
-    k_leg_syn32<1><<<g, SYN_THREADS, 0, st>>>(p->ptab, alm, p->anchor_active ? p->a_hi : nullptr, p->rc32, p->lmax,
-                                              p->mmax, p->npairs, p->nalm, stp);
+    k_leg_syn32<1><<<g, SYN_THREADS, 0, st>>>(p->ptab, alm, p->anchor_active ? p->a_hi : nullptr,
+                                              p->anchor_active ? p->e32 : nullptr, p->rc32, p->lmax, p->mmax,
+                                              p->npairs, p->nalm, stp);
   }
+  return cudaGetLastError();
+}
+
+// Filtered harmonic step of an anchored mixed iteration, on the FP32 state
+// e = a - a_hi (a_hi the FP64 anchor, g_hi = A W (d - Y a_hi) its FP64 term):
+//   a_new = F (a + Omega A r + g_hi)  <=>  e_new = c + F (e + Omega A r),
+//   c = F (a_hi + g_hi) - a_hi.
+// c depends on the level's filter F; it is formed in FP64 (and e_new with it)
+// whenever the level differs from the one c was formed at (clev, advanced by
+// the level control after this kernel), otherwise the step is all FP32.
+__global__ void k_ana_step_e32(const float2 *__restrict__ apart, int nchunk, float omega, int lmax, int64_t nalm,
+                               const double *__restrict__ filt, const float *__restrict__ filt32, int nlev,
+                               const SolveState *__restrict__ state, const int *__restrict__ clev,
+                               const double2 *__restrict__ a_hi, const double2 *__restrict__ g_hi,
+                               float2 *__restrict__ e32, float2 *__restrict__ c32) {
+  const int b = blockIdx.y, m = blockIdx.z;
+  if (state[b].done) return;
+  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
+  if (l > lmax) return;
+  const int64_t i = alm_base(lmax, m) + l, ib = (int64_t)b * 3 * nalm + i;
+  float2 acc[3];
+  for (int f = 0; f < 3; ++f) {
+    float ax = 0.f, ay = 0.f;
+    for (int c = 0; c < nchunk; ++c) {
+      const float2 v = apart[(((int64_t)b * nchunk + c) * 3 + f) * nalm + i];
+      ax += v.x;
+      ay += v.y;
+    }
+    acc[f] = make_float2(omega * ax, omega * ay);
+  }
+  const int lev = state[b].level;
+  const int64_t co = (((int64_t)b * nlev + lev) * (lmax + 1) + l) * 4;
+  if (lev != clev[b]) {
+    const double *cf = filt + co;
+    double2 h[3], x[3], y[3];
+    for (int f = 0; f < 3; ++f) {
+      h[f] = a_hi[ib + f * nalm];
+      const double2 g = g_hi[ib + f * nalm];
+      const float2 e = e32[ib + f * nalm];
+      x[f] = make_double2(h[f].x + g.x, h[f].y + g.y);
+      y[f] = make_double2(x[f].x + (double)e.x + (double)acc[f].x, x[f].y + (double)e.y + (double)acc[f].y);
+    }
+    const double2 cT = make_double2(cf[0] * x[0].x + cf[1] * x[1].x - h[0].x, cf[0] * x[0].y + cf[1] * x[1].y - h[0].y);
+    const double2 cE = make_double2(cf[1] * x[0].x + cf[2] * x[1].x - h[1].x, cf[1] * x[0].y + cf[2] * x[1].y - h[1].y);
+    const double2 cB = make_double2(cf[3] * x[2].x - h[2].x, cf[3] * x[2].y - h[2].y);
+    const double2 eT = make_double2(cf[0] * y[0].x + cf[1] * y[1].x - h[0].x, cf[0] * y[0].y + cf[1] * y[1].y - h[0].y);
+    const double2 eE = make_double2(cf[1] * y[0].x + cf[2] * y[1].x - h[1].x, cf[1] * y[0].y + cf[2] * y[1].y - h[1].y);
+    const double2 eB = make_double2(cf[3] * y[2].x - h[2].x, cf[3] * y[2].y - h[2].y);
+    c32[ib] = make_float2((float)cT.x, (float)cT.y);
+    c32[ib + nalm] = make_float2((float)cE.x, (float)cE.y);
+    c32[ib + 2 * nalm] = make_float2((float)cB.x, (float)cB.y);
+    e32[ib] = make_float2((float)eT.x, (float)eT.y);
+    e32[ib + nalm] = make_float2((float)eE.x, (float)eE.y);
+    e32[ib + 2 * nalm] = make_float2((float)eB.x, (float)eB.y);
+    return;
+  }
+  const float4 cf = *reinterpret_cast<const float4 *>(filt32 + co);
+  float2 y[3], c[3];
+  for (int f = 0; f < 3; ++f) {
+    const float2 e = e32[ib + f * nalm];
+    c[f] = c32[ib + f * nalm];
+    y[f] = make_float2(e.x + acc[f].x, e.y + acc[f].y);
+  }
+  e32[ib] = make_float2(c[0].x + cf.x * y[0].x + cf.y * y[1].x, c[0].y + cf.x * y[0].y + cf.y * y[1].y);
+  e32[ib + nalm] = make_float2(c[1].x + cf.y * y[0].x + cf.z * y[1].x, c[1].y + cf.y * y[0].y + cf.z * y[1].y);
+  e32[ib + 2 * nalm] = make_float2(c[2].x + cf.w * y[2].x, c[2].y + cf.w * y[2].y);
+}
+
+// At an anchor: c = F (a_hi + g_hi) - a_hi at each RHS's current level, e = 0.
+__global__ void k_anchor_c32(const double *__restrict__ filt, int nlev, const SolveState *__restrict__ state,
+                             int *__restrict__ clev, const double2 *__restrict__ a_hi,
+                             const double2 *__restrict__ g_hi, float2 *__restrict__ e32, float2 *__restrict__ c32,
+                             int lmax, int64_t nalm) {
+  const int b = blockIdx.y, m = blockIdx.z;
+  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
+  const int lev = state[b].level;
+  if (blockIdx.x == 0 && m == 0 && threadIdx.x == 0) clev[b] = lev;
+  if (l > lmax) return;
+  const int64_t i = alm_base(lmax, m) + l, ib = (int64_t)b * 3 * nalm + i;
+  const double *cf = filt + (((int64_t)b * nlev + lev) * (lmax + 1) + l) * 4;
+  double2 h[3], x[3];
+  for (int f = 0; f < 3; ++f) {
+    h[f] = a_hi[ib + f * nalm];
+    const double2 g = g_hi[ib + f * nalm];
+    x[f] = make_double2(h[f].x + g.x, h[f].y + g.y);
+    e32[ib + f * nalm] = make_float2(0.f, 0.f);
+  }
+  c32[ib] = make_float2((float)(cf[0] * x[0].x + cf[1] * x[1].x - h[0].x), (float)(cf[0] * x[0].y + cf[1] * x[1].y - h[0].y));
+  c32[ib + nalm] = make_float2((float)(cf[1] * x[0].x + cf[2] * x[1].x - h[1].x),
+                               (float)(cf[1] * x[0].y + cf[2] * x[1].y - h[1].y));
+  c32[ib + 2 * nalm] = make_float2((float)(cf[3] * x[2].x - h[2].x), (float)(cf[3] * x[2].y - h[2].y));
+}
+
+// a = a_hi + e (FP64), before an anchor consumes the iterate
+__global__ void k_materialize(const double2 *__restrict__ a_hi, const float2 *__restrict__ e32,
+                              double2 *__restrict__ a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 h = a_hi[i];
+    const float2 e = e32[i];
+    a[i] = make_double2(h.x + (double)e.x, h.y + (double)e.y);
+  }
+}
+
+cudaError_t anchor_c32(dm_plan *p, cudaStream_t st) {
+  dim3 g((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
+  k_anchor_c32<<<g, 128, 0, st>>>(p->filt, p->filt_levels, p->state, p->clev, p->a_hi, p->g_hi, p->e32, p->c32,
+                                  p->lmax, p->nalm);
+  return cudaGetLastError();
+}
+
+cudaError_t materialize_a(dm_plan *p, cudaStream_t st) {
+  k_materialize<<<1024, 256, 0, st>>>(p->a_hi, p->e32, p->a, (int64_t)p->batch * 3 * p->nalm);
   return cudaGetLastError();
 }
 
@@ -668,6 +790,11 @@ cudaError_t legendre_analysis32(dm_plan *p, int epilogue, double2 *out, cudaStre
   if (mid) cudaEventRecord(mid, st);
   double omega = 4.0 * M_PI / (double)p->npix;
   dim3 g2((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
+  if (epilogue == ANA_DM_STEP && p->anchor_active) {  // FP32 state e between anchors
+    k_ana_step_e32<<<g2, 128, 0, st>>>(p->apart32, nchunk, (float)omega, p->lmax, p->nalm, p->filt, p->filt32,
+                                       p->filt_levels, p->state, p->clev, p->a_hi, p->g_hi, p->e32, p->c32);
+    return cudaGetLastError();
+  }
   k_ana_reduce32<<<g2, 128, 0, st>>>(p->apart32, out, p->lmax, p->nalm, nchunk, omega, epilogue, p->filt,
                                      p->filt_levels,
                                      epilogue == ANA_DM_STEP ? p->state : stp,

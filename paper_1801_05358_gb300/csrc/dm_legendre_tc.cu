@@ -160,10 +160,16 @@ __global__ void k_tab_ana(const float *__restrict__ ptab, unsigned char *__restr
 // grid (pair tiles of 128, m); K steps of 32 consecutive multipoles (16 + 16).
 // The B rows are written so that the 8 threads of a quarter warp fill the 8
 // rows of one core matrix (row order rotated by the k-octet): no bank conflicts.
+// iterate value: the FP32 state e when given, else a - a_hi (a_hi may be null)
+__device__ __forceinline__ float2 iter_of(const float2 *__restrict__ e32, const double2 *__restrict__ alm,
+                                          const double2 *__restrict__ a_hi, int64_t i) {
+  return e32 != nullptr ? e32[i] : e_of(alm, a_hi, i);
+}
+
 template <int PART>
 __device__ __forceinline__ void stage_syn_b(unsigned char *Bbuf, int tileB, const double2 *__restrict__ alm,
-                                            const double2 *__restrict__ a_hi, int64_t base, int m, int c, int lmax,
-                                            int64_t nalm, int B) {
+                                            const double2 *__restrict__ a_hi, const float2 *__restrict__ e32,
+                                            int64_t base, int m, int c, int lmax, int64_t nalm, int B) {
   if (PART == 0) {
     // task = ((par * B/4 + b/4) * 8) + (b & 3) * 2 + ko: rows 2b, 2b + 1 of parity tile par
     for (int task = threadIdx.x; task < 4 * B; task += TC_THREADS) {
@@ -172,7 +178,8 @@ __device__ __forceinline__ void stage_syn_b(unsigned char *Bbuf, int tileB, cons
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) {
         const int l = m + 32 * c + par + 2 * (8 * ko + kk);
-        const float2 v = l <= lmax ? e_of(alm, a_hi, (int64_t)b * 3 * nalm + base + l) : make_float2(0.f, 0.f);
+        const float2 v =
+            l <= lmax ? iter_of(e32, alm, a_hi, (int64_t)b * 3 * nalm + base + l) : make_float2(0.f, 0.f);
         re[kk] = v.x;
         im[kk] = v.y;
       }
@@ -190,7 +197,7 @@ __device__ __forceinline__ void stage_syn_b(unsigned char *Bbuf, int tileB, cons
       for (int kk = 0; kk < 8; ++kk) {
         const int l = m + 32 * c + par + 2 * (8 * ko + kk);
         const float2 v =
-            l <= lmax ? e_of(alm, a_hi, ((int64_t)b * 3 + 1 + f) * nalm + base + l) : make_float2(0.f, 0.f);
+            l <= lmax ? iter_of(e32, alm, a_hi, ((int64_t)b * 3 + 1 + f) * nalm + base + l) : make_float2(0.f, 0.f);
         re[kk] = v.x;
         im[kk] = v.y;
         nre[kk] = -v.x;
@@ -215,14 +222,15 @@ __device__ __forceinline__ void stage_syn_b(unsigned char *Bbuf, int tileB, cons
 template <int PART>
 __global__ void __launch_bounds__(TC_THREADS) k_syn_b(unsigned char *__restrict__ out, const int64_t *__restrict__ soff,
                                                       const double2 *__restrict__ alm,
-                                                      const double2 *__restrict__ a_hi, int lmax, int64_t nalm,
+                                                      const double2 *__restrict__ a_hi,
+                                                      const float2 *__restrict__ e32, int lmax, int64_t nalm,
                                                       int B) {
   const int c = blockIdx.x, m = blockIdx.y;
   if (c >= syn_steps(lmax, m)) return;
   constexpr int nA = (PART == 0) ? 2 : 4;
   const int tileB = ((PART == 0) ? 2 * B : 4 * B) * 32;
-  stage_syn_b<PART>(out + (soff[m] + c) * (int64_t)(nA * 2 * tileB), tileB, alm, a_hi, abase(lmax, m), m, c, lmax,
-                    nalm, B);
+  stage_syn_b<PART>(out + (soff[m] + c) * (int64_t)(nA * 2 * tileB), tileB, alm, a_hi, e32, abase(lmax, m), m, c,
+                    lmax, nalm, B);
 }
 
 constexpr int TC_MAX_STAGES = 8;
@@ -596,8 +604,9 @@ cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t s
   const double2 *ahi = p->anchor_active ? p->a_hi : nullptr;
   const int npt = (p->npairs + 127) / 128;
   dim3 gb(syn_steps(p->lmax, 0), p->mmax + 1);
-  k_syn_b<0><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[0], p->tc_soff, alm, ahi, p->lmax, p->nalm, B);
-  k_syn_b<1><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[1], p->tc_soff, alm, ahi, p->lmax, p->nalm, B);
+  const float2 *e32 = p->anchor_active ? p->e32 : nullptr;  // iteration: the FP32 state e
+  k_syn_b<0><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[0], p->tc_soff, alm, ahi, e32, p->lmax, p->nalm, B);
+  k_syn_b<1><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[1], p->tc_soff, alm, ahi, e32, p->lmax, p->nalm, B);
   dim3 g(npt, p->mmax + 1);
   {
     const int stage = 2 * 2 * TILE_A + 2 * 2 * (2 * B * 32);

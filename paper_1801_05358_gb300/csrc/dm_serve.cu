@@ -116,7 +116,11 @@ dm_plan make_view(const dm_plan *p, int b) {
     v.a_hi += b * na;
     v.g_hi += b * na;
     v.shi32 += b * n3;
+    v.e32 += b * na;
+    v.c32 += b * na;
+    v.clev += b;
   }
+  if (p->filt32) v.filt32 += (size_t)b * p->filt_levels * 4 * (p->lmax + 1);
   v.alpha.assign(1, p->alpha[b]);
   v.t_h.assign(1, p->t_h[b]);
   v.eps_final_rhs.assign(1, p->eps_final_rhs.empty() ? p->sched.eps_final : p->eps_final_rhs[b]);
@@ -261,6 +265,7 @@ dm_status slot_begin(dm_server *S, Pool *pool, int b, Request &r) {
   p->t_h[b] = v.t_h[0];
   v.filt_levels = p->filt_levels;
   v.filt = p->filt + (size_t)b * p->filt_levels * 4 * (p->lmax + 1);
+  if (p->filt32) v.filt32 = p->filt32 + (size_t)b * p->filt_levels * 4 * (p->lmax + 1);
   {
     const int nl = (int)p->lambdas.size();
     for (int k = 0; k < nl; ++k)

@@ -207,10 +207,12 @@ __device__ void filter_one_l(const double *cl, int lmax, int l, double mu, doubl
   out[3] = f3;
 }
 
-__global__ void k_filter(const double *cl, int lmax, double mu, double th, double *coef) {
+__global__ void k_filter(const double *cl, int lmax, double mu, double th, double *coef, float *coef32) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l > lmax) return;
   filter_one_l(cl, lmax, l, mu, th, coef + 4 * l);
+  if (coef32 != nullptr)
+    for (int k = 0; k < 4; ++k) coef32[4 * l + k] = (float)coef[4 * l + k];
 }
 
 // ------------------------------------------------------------------- noise
@@ -420,6 +422,9 @@ cudaError_t setup_fp32(dm_plan *p) {
   if ((e = al(&p->a_hi, (size_t)B * 3 * p->nalm))) return e;
   if ((e = al(&p->g_hi, (size_t)B * 3 * p->nalm))) return e;
   if ((e = al(&p->shi32, (size_t)B * n3))) return e;
+  if ((e = al(&p->e32, (size_t)B * 3 * p->nalm))) return e;
+  if ((e = al(&p->c32, (size_t)B * 3 * p->nalm))) return e;
+  if ((e = al(&p->clev, (size_t)B))) return e;
   if ((e = al(&p->tc_err, 1))) return e;
   cudaMemset(p->tc_err, 0, sizeof(int));
   cudaMemset(p->rc32, 0, sizeof(float2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
@@ -430,9 +435,16 @@ cudaError_t setup_fp32(dm_plan *p) {
   return cudaDeviceSynchronize();
 }
 
+// When coef lies in p->filt, its FP32 copy goes to the same place of p->filt32.
 cudaError_t build_filter_one(dm_plan *p, double lambda, double th, double *coef, cudaStream_t st) {
   double mu = (lambda - 1.0) * th;
-  k_filter<<<(p->lmax + 1 + 127) / 128, 128, 0, st>>>(p->cl, p->lmax, mu, th, coef);
+  float *coef32 = nullptr;
+  if (p->filt32 != nullptr && p->filt != nullptr && coef >= p->filt) {
+    const size_t off = (size_t)(coef - p->filt);
+    const size_t len = (size_t)4 * (p->lmax + 1) * p->filt_levels * p->batch;
+    if (off + (size_t)4 * (p->lmax + 1) <= len) coef32 = p->filt32 + off;
+  }
+  k_filter<<<(p->lmax + 1 + 127) / 128, 128, 0, st>>>(p->cl, p->lmax, mu, th, coef, coef32);
   return cudaGetLastError();
 }
 
@@ -441,8 +453,12 @@ cudaError_t build_filters(dm_plan *p, int b, cudaStream_t st) {
   const int nl = (int)p->lambdas.size();
   if (p->filt == nullptr || p->filt_levels < nl) {
     if (p->filt) cudaFree(p->filt);
+    if (p->filt32) cudaFree(p->filt32);
     p->filt = nullptr;
+    p->filt32 = nullptr;
     cudaError_t e = cudaMalloc(&p->filt, sizeof(double) * 4 * (p->lmax + 1) * (size_t)nl * p->batch);
+    if (e) return e;
+    e = cudaMalloc(&p->filt32, sizeof(float) * 4 * (p->lmax + 1) * (size_t)nl * p->batch);
     if (e) return e;
     p->filt_levels = nl;
     // every RHS must be (re)built after a reallocation
