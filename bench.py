@@ -359,9 +359,11 @@ def main():
     # (T: lambda x 2 re/im; Q, U: lam+ and lam- x 4) -- executed on the tensor
     # cores as three BF16 products (hi*hi + hi*lo + lo*hi) in the mixed mode
     leg_flops = 20.0 * triples * B
-    # reduce (filter + anchor term): per alm and RHS-field FP32 partial read,
-    # FP64 anchor term read, FP64 a read + write
-    red_bytes = 3.0 * B * nalm * ((8.0 if mixed else 16.0) * (1 if use_tc else (npairs + 63) // 64) + 16 * 3)
+    # filtered step: per alm and RHS-field the analysis partial sums, then
+    # mixed: FP32 state e read + write and its FP32 anchor term c read;
+    # FP64: a read + write
+    nparts = 1 if use_tc else (npairs + 63) // 64
+    red_bytes = 3.0 * B * nalm * ((8.0 * nparts + 24.0) if mixed else (16.0 * nparts + 32.0))
 
     def hbm_line(kernel, nbytes, ms, traffic_key):
         ach = nbytes / (ms * 1e-3) / 1e9
@@ -390,7 +392,7 @@ def main():
                               stage["ms_synthesis"], "k_syn_tc" if use_tc else "k_leg_syn64"),
         "analysis": leg_line("k_ana_tc<0,1>" if use_tc else ("k_leg_ana32" if mixed else "k_leg_ana64"),
                              stage["ms_analysis"], "k_ana_tc" if use_tc else "k_leg_ana64"),
-        "reduce": hbm_line("k_ana_reduce32" if mixed else "k_ana_reduce", red_bytes, stage["ms_reduce"], "k_reduce"),
+        "reduce": hbm_line("k_ana_step_e32" if mixed else "k_ana_reduce", red_bytes, stage["ms_reduce"], "k_reduce"),
     }
     dom = max(stages, key=lambda k: stages[k]["ms_per_launch"])
     roofline = dict(stages[dom])

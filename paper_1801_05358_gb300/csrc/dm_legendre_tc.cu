@@ -342,7 +342,9 @@ __global__ void __launch_bounds__(128, 1) k_syn_tc(const unsigned char *__restri
 // PART 0: aT    (A = lambda [128 l x 16 pairs], B rows (b, re/im))
 // PART 1: aE,aB (A = lam+ with B1 rows (b; E.re, E.im, B.re, B.im) and
 //                A = lam- with B2, over 16 pairs per K step)
-// grid (l tiles of 128 multipoles of one parity, parity, m); rows l = m + p + 2 i.
+// grid (groups of LT l tiles of 128 multipoles of one parity, parity, m); rows
+// l = m + p + 2 i.  The LT tiles of a CTA share each converted B tile, one
+// tensor-memory accumulator of NC columns per tile.
 // Output: out[b][f][alm] (FP32 partial sums with a single chunk).
 // 8 ring pairs (north, south) of one field, as 16 float2; zero past npairs, no
 // south ring at the equator pair.
@@ -421,36 +423,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ana_tc(const unsigned char *_
                                                          const int64_t *__restrict__ aoff,
                                                          const float2 *__restrict__ rc, float2 *__restrict__ out,
                                                          int lmax, int mmax, int npairs, int64_t nalm, int B,
-                                                         uint32_t ncols, int *err) {
+                                                         int LT, uint32_t ncols, int *err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t mbar[4];
   __shared__ uint32_t tslot;
   uint64_t *done = mbar, *full = mbar + 2;
-  const int m = blockIdx.z, par = blockIdx.y, lt = blockIdx.x;
+  const int m = blockIdx.z, par = blockIdx.y;
   const int nl = ana_nl(lmax, m, par);
-  if (nl <= 0 || lt * 128 >= nl) return;  // uniform over the block
+  const int lt0 = blockIdx.x * LT;                                   // first l tile of this CTA
+  const int nt = min(LT, (nl > 0 ? (nl + 127) / 128 : 0) - lt0);    // l tiles it takes
+  if (nt <= 0) return;  // uniform over the block
   const int NC = (PART == 0) ? 2 * B : 4 * B;
   constexpr int nA = (PART == 0) ? 1 : 2;
   const int tileB = NC * 32;
   const int abytes = nA * 2 * TILE_A;
-  const int stage = abytes + nA * 2 * tileB;
+  const int stage = LT * abytes + nA * 2 * tileB;  // A tiles of the LT l tiles, then B
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   tc_setup(mbar, &tslot, ncols);
   const uint32_t tbase = tslot;
   const int64_t base = abase(lmax, m);
   const int nsteps = (npairs + 15) / 16;
-  const unsigned char *tabm = tab + (aoff[2 * m + par] + lt) * nsteps * (int64_t)abytes;
+  const unsigned char *tabm = tab + (aoff[2 * m + par] + lt0) * nsteps * (int64_t)abytes;
+  const int64_t tstride = (int64_t)nsteps * abytes;  // next l tile
   const uint32_t idesc = idesc_bf16(128, NC);
-  if (tid == 0) {
-    mbar_expect_tx(&full[0], (uint32_t)abytes);
-    bulk_g2s(sm, tabm, (uint32_t)abytes, &full[0]);
-  }
+  auto issue_a = [&](int c, int s) {
+    mbar_expect_tx(&full[s], (uint32_t)(nt * abytes));
+    for (int j = 0; j < nt; ++j)
+      bulk_g2s(sm + s * stage + j * abytes, tabm + j * tstride + (int64_t)c * abytes, (uint32_t)abytes, &full[s]);
+  };
+  if (tid == 0) issue_a(0, 0);
   const bool has = tid < (PART == 0 ? 2 * B : 4 * B);
   float2 v[16];
   if (has) load_ana_b<PART>(tid, rc, m, 0, mmax, npairs, v);
   for (int c = 0; c < nsteps; ++c) {
     const int s = c & 1;
-    unsigned char *Abuf = sm + s * stage, *Bbuf = Abuf + abytes;
+    unsigned char *Abuf = sm + s * stage, *Bbuf = Abuf + LT * abytes;
     if (c >= 2) mbar_wait(&done[s], ((c - 2) >> 1) & 1, err);
     if (has) {
       convert_ana_b<PART>(tid, Bbuf, tileB, par, v);
@@ -462,40 +469,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ana_tc(const unsigned char *_
       mbar_wait(&full[s], (c >> 1) & 1, err);
       fence_after_sync();
       const uint32_t acc = c > 0 ? 1u : 0u;
-      if (PART == 0) {
-        mma3(tbase, Abuf, Bbuf, tileB, idesc, acc);
-      } else {
-        mma3(tbase, Abuf, Bbuf, tileB, idesc, acc);
-        mma3(tbase, Abuf + 2 * TILE_A, Bbuf + 2 * tileB, tileB, idesc, 1u);
+      for (int j = 0; j < nt; ++j) {  // one accumulator of NC columns per l tile, the same B
+        const unsigned char *Aj = Abuf + j * abytes;
+        const uint32_t dj = tbase + (uint32_t)(j * NC);
+        if (PART == 0) {
+          mma3(dj, Aj, Bbuf, tileB, idesc, acc);
+        } else {
+          mma3(dj, Aj, Bbuf, tileB, idesc, acc);
+          mma3(dj, Aj + 2 * TILE_A, Bbuf + 2 * tileB, tileB, idesc, 1u);
+        }
       }
       commit(&done[s]);
       if (c + 1 < nsteps) {
         if (c >= 1) mbar_wait(&done[s ^ 1], ((c - 1) >> 1) & 1, err);
-        mbar_expect_tx(&full[s ^ 1], (uint32_t)abytes);
-        bulk_g2s(sm + (s ^ 1) * stage, tabm + (int64_t)(c + 1) * abytes, (uint32_t)abytes, &full[s ^ 1]);
+        issue_a(c + 1, s ^ 1);
       }
     }
   }
   tc_drain(done, nsteps, err);
   if (warp < 4) {
-    const int row = warp * 32 + lane, i = lt * 128 + row;
-    const bool ok = i < nl;
-    const int64_t idx = base + m + par + 2 * i;
+    const int row = warp * 32 + lane;
     const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < NC; c0 += 16) {
-      float v[16];
-      tmem_ld16(trow + c0, v);
-      if (!ok) continue;
-      if (PART == 0) {
-        for (int j = 0; j < 8; ++j) {
-          const int b = (c0 >> 1) + j;
-          out[((int64_t)b * 3 + 0) * nalm + idx] = make_float2(v[2 * j], v[2 * j + 1]);
-        }
-      } else {
-        for (int j = 0; j < 4; ++j) {
-          const int b = (c0 >> 2) + j;
-          out[((int64_t)b * 3 + 1) * nalm + idx] = make_float2(v[4 * j], v[4 * j + 1]);
-          out[((int64_t)b * 3 + 2) * nalm + idx] = make_float2(v[4 * j + 2], v[4 * j + 3]);
+    for (int j = 0; j < nt; ++j) {
+      const int i = (lt0 + j) * 128 + row;
+      const bool ok = i < nl;
+      const int64_t idx = base + m + par + 2 * i;
+      for (int c0 = 0; c0 < NC; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)(j * NC) + c0, v);
+        if (!ok) continue;
+        if (PART == 0) {
+          for (int q = 0; q < 8; ++q) {
+            const int b = (c0 >> 1) + q;
+            out[((int64_t)b * 3 + 0) * nalm + idx] = make_float2(v[2 * q], v[2 * q + 1]);
+          }
+        } else {
+          for (int q = 0; q < 4; ++q) {
+            const int b = (c0 >> 2) + q;
+            out[((int64_t)b * 3 + 1) * nalm + idx] = make_float2(v[4 * q], v[4 * q + 1]);
+            out[((int64_t)b * 3 + 2) * nalm + idx] = make_float2(v[4 * q + 2], v[4 * q + 3]);
+          }
         }
       }
     }
@@ -629,25 +642,35 @@ cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t s
   return cudaGetLastError();
 }
 
+// l tiles per CTA: as many accumulators of NC columns as tensor memory holds (at most 4)
+static int ana_tiles_per_cta(int NC) {
+  const int nc = (int)pow2_cols(NC);
+  const int lt = 512 / nc;
+  return lt < 1 ? 1 : (lt > 4 ? 4 : lt);
+}
+
 cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st) {
   cudaError_t e = tc_tables(p);
   if (e) return e;
   const int B = p->batch;
   const int ltiles = ana_tiles(p->lmax, 0, 0);
-  dim3 g(ltiles, 2, p->mmax + 1);
   {
-    const uint32_t nc = pow2_cols(2 * B);
-    const size_t sm = tc_smem(1 * 2 * TILE_A + 1 * 2 * (2 * B * 32), nc);
+    const int NC = 2 * B, LT = ana_tiles_per_cta(NC);
+    const uint32_t nc = pow2_cols(LT * NC);
+    const size_t sm = tc_smem(LT * 1 * 2 * TILE_A + 1 * 2 * (NC * 32), nc);
+    dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
     cudaFuncSetAttribute(k_ana_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_ana_tc<0><<<g, TC_THREADS, sm, st>>>(p->tc_anaA[0], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
-                                           p->npairs, p->nalm, B, nc, p->tc_err);
+                                           p->npairs, p->nalm, B, LT, nc, p->tc_err);
   }
   {
-    const uint32_t nc = pow2_cols(4 * B);
-    const size_t sm = tc_smem(2 * 2 * TILE_A + 2 * 2 * (4 * B * 32), nc);
+    const int NC = 4 * B, LT = ana_tiles_per_cta(NC);
+    const uint32_t nc = pow2_cols(LT * NC);
+    const size_t sm = tc_smem(LT * 2 * 2 * TILE_A + 2 * 2 * (NC * 32), nc);
+    dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
     cudaFuncSetAttribute(k_ana_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_ana_tc<1><<<g, TC_THREADS, sm, st>>>(p->tc_anaA[1], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
-                                           p->npairs, p->nalm, B, nc, p->tc_err);
+                                           p->npairs, p->nalm, B, LT, nc, p->tc_err);
   }
   return cudaGetLastError();
 }
