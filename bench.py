@@ -60,6 +60,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(vals, device, ws):
+    """Element-wise maximum of per-rank timings over all ranks (all_reduce MAX
+    on the rank's device; identity for a single rank)."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_value(batch, steps, ws, ms):
+    """RHS-iterations of every rank divided by the slowest rank's time."""
+    return batch * steps * ws / (ms * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -311,22 +327,19 @@ def main():
     prof = plan.profile_read()
     plan.profile_enable(False)
     st, stats = plan.solve_end(s_out)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     iters = prof["iterations"]
     assert iters == K, f"timed {iters} iterations, expected {K}"
     assert stats[0]["iters_total"] == Wu + K, stats[0]["iters_total"]
-    raw_value = B * K * ws / (ms_max * 1e-3)
-    value = raw_value
-    anchor = None
+    ams, every, local_whole = 0.0, ANCHOR_EVERY, ms
     if prec != dmwf.DM_FP64:
         n_anch = warm_prof["anchors"] + prof["anchors"]
         ams = (warm_prof["ms_anchor"] + prof["ms_anchor"]) / max(1, n_anch)
-        every = ANCHOR_EVERY
-        whole_ms = ms_max - prof["ms_anchor"] + ams * K / every
-        value = B * K * ws / (whole_ms * 1e-3)
+        local_whole = ms - prof["ms_anchor"] + ams * K / every
+    ms_max, whole_ms = max_over_ranks([ms, local_whole], dev, ws)
+    raw_value = whole_job_value(B, K, ws, ms_max)
+    value = whole_job_value(B, K, ws, whole_ms)
+    anchor = None
+    if prec != dmwf.DM_FP64:
         anchor = {"ms_per_anchor": ams, "anchor_every": every, "anchors_in_timed_window": prof["anchors"],
                   "timed_window_value": raw_value,
                   "steady_value_between_anchors": B * K * ws / ((ms_max - prof["ms_anchor"]) * 1e-3),
