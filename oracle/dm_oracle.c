@@ -366,6 +366,99 @@ void orc_legendre_analysis(int nside, int lmax, const double *rc, double *alm) {
   }
 }
 
+/* Sampled transforms, for parity checks at sizes where the full oracle
+ * transforms take too long.  They restrict the sums of orc_legendre_synthesis
+ * + orc_ring_dft_inverse to one ring, and those of orc_ring_dft_forward +
+ * orc_legendre_analysis to one order m; the arithmetic is the same. */
+
+/* G_m = sum_j f_j e^{-i m (phi0 + 2 pi j / n)} for one m (the m-th output of ring_dft_fwd) */
+static void ring_dft_fwd_one(long n, double phi0, const double *f, int m, double *out) {
+  double re = 0.0, im = 0.0;
+  for (long j = 0; j < n; ++j) {
+    long k = ((long)m * j) % n;
+    re += f[j] * cos(2.0 * M_PI * (double)k / (double)n);
+    im -= f[j] * sin(2.0 * M_PI * (double)k / (double)n);
+  }
+  double cp = cos(m * phi0), sp = sin(m * phi0);
+  out[0] = re * cp + im * sp;
+  out[1] = im * cp - re * sp;
+}
+
+/* The three maps of Y a on ring i (1-based): out[3][n_r]. */
+void orc_ring_alm2map(int nside, int lmax, const double *alm, int i, double *out) {
+  long nr, st;
+  double z, omz, opz, p0;
+  orc_ring_info(nside, i, &nr, &st, &z, &omz, &opz, &p0);
+  long nalm = orc_nalm(lmax);
+  long fs = (long)(lmax + 1) * 2;
+  double *F = malloc(sizeof(double) * 3 * fs);
+#pragma omp parallel
+  {
+    double *l0 = malloc(sizeof(double) * (lmax + 1));
+    double *lp = malloc(sizeof(double) * (lmax + 1));
+    double *lm = malloc(sizeof(double) * (lmax + 1));
+#pragma omp for schedule(dynamic)
+    for (int m = 0; m <= lmax; ++m) {
+      orc_lambda(lmax, m, omz, opz, l0, lp, lm);
+      double tr = 0, ti = 0, qr = 0, qi = 0, ur = 0, ui = 0;
+      for (int l = m; l <= lmax; ++l) {
+        long ix = orc_almidx(lmax, l, m);
+        const double *aT = alm + 2 * ix, *aE = alm + 2 * (nalm + ix), *aB = alm + 2 * (2 * nalm + ix);
+        double lpl = 0.5 * (lp[l] + lm[l]), lmi = 0.5 * (lp[l] - lm[l]);
+        tr += aT[0] * l0[l];
+        ti += aT[1] * l0[l];
+        qr += -(aE[0] * lpl - aB[1] * lmi);
+        qi += -(aE[1] * lpl + aB[0] * lmi);
+        ur += -(aB[0] * lpl + aE[1] * lmi);
+        ui += -(aB[1] * lpl - aE[0] * lmi);
+      }
+      F[2 * m] = tr; F[2 * m + 1] = ti;
+      F[fs + 2 * m] = qr; F[fs + 2 * m + 1] = qi;
+      F[2 * fs + 2 * m] = ur; F[2 * fs + 2 * m + 1] = ui;
+    }
+    free(l0); free(lp); free(lm);
+  }
+  for (int f = 0; f < 3; ++f) ring_dft_inv(nr, p0, F + f * fs, lmax, out + f * nr);
+  free(F);
+}
+
+/* Column m of A f = Omega Y^dagger f: out[3][lmax+1] complex (entries l < m zero). */
+void orc_map2alm_m(int nside, int lmax, const double *map, int m, double *out) {
+  int nrg = orc_nrings(nside);
+  long npix = orc_npix(nside);
+  double omega = 4.0 * M_PI / (double)npix;
+  long fs = (long)(lmax + 1) * 2;
+  memset(out, 0, sizeof(double) * 3 * fs);
+#pragma omp parallel
+  {
+    double *l0 = malloc(sizeof(double) * (lmax + 1));
+    double *lp = malloc(sizeof(double) * (lmax + 1));
+    double *lm = malloc(sizeof(double) * (lmax + 1));
+    double *acc = calloc(3 * fs, sizeof(double));
+#pragma omp for schedule(dynamic)
+    for (int i = 1; i <= nrg; ++i) {
+      long nr, st;
+      double z, omz, opz, p0, g[6];
+      orc_ring_info(nside, i, &nr, &st, &z, &omz, &opz, &p0);
+      for (int f = 0; f < 3; ++f) ring_dft_fwd_one(nr, p0, map + f * npix + st, m, g + 2 * f);
+      orc_lambda(lmax, m, omz, opz, l0, lp, lm);
+      for (int l = m; l <= lmax; ++l) {
+        double lpl = 0.5 * (lp[l] + lm[l]), lmi = 0.5 * (lp[l] - lm[l]);
+        double *aT = acc + 2 * l, *aE = acc + fs + 2 * l, *aB = acc + 2 * fs + 2 * l;
+        aT[0] += omega * l0[l] * g[0];
+        aT[1] += omega * l0[l] * g[1];
+        aE[0] += -omega * (lpl * g[2] - lmi * g[5]);
+        aE[1] += -omega * (lpl * g[3] + lmi * g[4]);
+        aB[0] += -omega * (lpl * g[4] + lmi * g[3]);
+        aB[1] += -omega * (lpl * g[5] - lmi * g[2]);
+      }
+    }
+#pragma omp critical
+    for (long k = 0; k < 3 * fs; ++k) out[k] += acc[k];
+    free(l0); free(lp); free(lm); free(acc);
+  }
+}
+
 /* Full transforms: Y (alm -> map) and A = Omega Y^dagger (map -> alm). */
 void orc_alm2map(int nside, int lmax, const double *alm, double *map) {
   int nrg = orc_nrings(nside);

@@ -109,6 +109,23 @@ def lam_ring(lmax, m, omz, opz):
     return out
 
 
+def ring_alm2map(nside, lmax, alm, i):
+    """The three maps of Y a on ring i (1-based), shape (3, n_r): a sampled alm2map."""
+    a = _c2r(alm)
+    nr = ring_info(nside, i)[0]
+    out = np.zeros((3, nr))
+    lib().orc_ring_alm2map(nside, lmax, _d(a), i, _d(out))
+    return out
+
+
+def map2alm_m(nside, lmax, maps, m):
+    """Column m of A f, shape (3, lmax + 1) complex (l < m zero): a sampled map2alm."""
+    f = np.ascontiguousarray(maps, dtype=np.float64)
+    out = np.zeros((3, lmax + 1), dtype=np.complex128)
+    lib().orc_map2alm_m(nside, lmax, _d(f), m, _d(out.view(np.float64)))
+    return out
+
+
 def _c2r(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.complex128)).view(np.float64)
 

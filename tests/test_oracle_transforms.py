@@ -93,3 +93,24 @@ def test_legendre_split_consistent(orc):
     f = W.random_maps(nside, 1, 5)[0]
     rc2 = np.stack([orc.ring_dft_forward(nside, lmax, f[k]) for k in range(3)])
     assert np.allclose(orc.legendre_analysis(nside, lmax, rc2), orc.map2alm(nside, lmax, f), atol=1e-13)
+
+
+@pytest.mark.parametrize("nside,lmax", [(2, 5), (8, 16), (12, 30)])
+def test_sampled_transforms_match_full(orc, nside, lmax):
+    """The one-ring synthesis and the one-order analysis reproduce the
+    corresponding slices of the full transforms (same sums, restricted)."""
+    a = W.random_alm(lmax, 1, 31)[0]
+    f = W.random_maps(nside, 1, 32)[0]
+    full_map = orc.alm2map(nside, lmax, a)
+    full_alm = orc.map2alm(nside, lmax, f)
+    for i in sorted({1, 2, nside, 2 * nside, 3 * nside, 4 * nside - 1}):
+        nr, st = orc.ring_info(nside, i)[:2]
+        got = orc.ring_alm2map(nside, lmax, a, i)
+        ref = full_map[:, st:st + nr]
+        assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    for m in sorted({0, 1, 2, lmax // 2, lmax}):
+        got = orc.map2alm_m(nside, lmax, f, m)
+        idx = [orc.almidx(lmax, l, m) for l in range(m, lmax + 1)]
+        ref = full_alm[:, idx]
+        assert np.all(got[:, :m] == 0)
+        assert np.max(np.abs(got[:, m:] - ref)) <= 1e-13 * np.max(np.abs(full_alm))
