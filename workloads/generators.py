@@ -116,9 +116,15 @@ def mask_band_disks(nside: int, rng: np.random.Generator, band: float, disks) ->
             radii = rng.uniform(rad[0], rad[1], count)
         cs = np.sqrt(1 - cz * cz)
         cx, cy = cs * np.cos(cphi), cs * np.sin(cphi)
+        # a pixel within angle r of the centre has |z - z_c| < r (|d cos / d theta| <= 1);
+        # z does not increase along RING order, so the candidates are one index range
+        negz = -z
         for k in range(count):
-            cosd = vx * cx[k] + vy * cy[k] + vz * cz[k]
-            obs &= cosd < np.cos(radii[k])
+            lo = np.searchsorted(negz, -(cz[k] + radii[k]) - 1e-12, side="left")
+            hi = np.searchsorted(negz, -(cz[k] - radii[k]) + 1e-12, side="right")
+            sl = slice(lo, hi)
+            cosd = vx[sl] * cx[k] + vy[sl] * cy[k] + vz[sl] * cz[k]
+            obs[sl] &= cosd < np.cos(radii[k])
     return obs.astype(np.uint8)
 
 
