@@ -105,8 +105,11 @@ typedef struct {
 /* --- plan ------------------------------------------------------------------ */
 
 /* Create a plan for `batch` right-hand sides of one geometry on the current
- * CUDA device.  1 <= nside <= 1024 (a power of two is not required),
- * 2 <= lmax <= 4 nside, 1 <= batch <= 4096.  Builds the ring geometry, the
+ * CUDA device.  1 <= nside <= 2048 (a power of two is not required),
+ * 2 <= lmax <= 4 nside, 1 <= batch <= 4096, and above nside 1024 at most
+ * 2^31 - 1 pixel-components per plan (batch x 3 x 12 nside^2; nside 2048
+ * allows 14 RHS).  The mixed and float-float modes also need their FP32
+ * hi/lo tables (3 x nalm x 2 nside x 8 bytes) to fit.  Builds the ring geometry, the
  * FFT chirps, the recurrence coefficient and seed tables, and allocates the
  * workspace (DM_ENOMEM if it does not fit). */
 dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out);

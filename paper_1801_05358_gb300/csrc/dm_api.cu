@@ -343,7 +343,9 @@ extern "C" {
 dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out) {
   if (!out) return DM_EINVAL;
   *out = nullptr;
-  if (nside < 1 || nside > 1024 || lmax < 2 || lmax > 4 * nside || batch < 1 || batch > 4096) return DM_EINVAL;
+  if (nside < 1 || nside > 2048 || lmax < 2 || lmax > 4 * nside || batch < 1 || batch > 4096) return DM_EINVAL;
+  // above nside 1024, keep the pixel-components of a plan within 31 bits
+  if (nside > 1024 && (int64_t)batch * 3 * 12 * nside * nside > INT32_MAX) return DM_EINVAL;
   dm_plan *p = new dm_plan();
   cudaGetDevice(&p->device);
   p->nside = nside;

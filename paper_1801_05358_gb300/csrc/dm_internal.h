@@ -36,7 +36,9 @@ struct PairDev {
 //  spin 0 : lam_l = al * x * lam_{l-1} - bl * lam_{l-2}
 //  spin 2 : lp_l = a x lp_{l-1} + ac lm_{l-1} - b lp_{l-2}
 //           lm_l = a x lm_{l-1} + ac lp_{l-1} - b lm_{l-2}
-// with lp/lm = (2lambda +- -2lambda)/2 and a, ac, b taken at the source l-1.
+// with lp/lm = (2lambda +- -2lambda)/2 and a, ac, b taken at the source l-1;
+// the kernels run the equivalent separate recurrences of 2lambda = lp + lm
+// (coefficient a x + ac) and -2lambda = lp - lm (a x - ac).
 struct RecCoef {
   double al, bl, a, ac, b, pad;
 };

@@ -25,19 +25,26 @@ __device__ __forceinline__ int64_t rc_index2(int b, int f, int m, int mmax, int 
 }
 
 // Recurrence state of one ring pair: current and previous values.
+// The two spin-2 functions run as separate recurrences,
+//   2lambda_{l+1} = (a x + ac) 2lambda_l - b 2lambda_{l-1},
+//  -2lambda_{l+1} = (a x - ac) -2lambda_l - b -2lambda_{l-1},
+// and lam+- = (2lambda +- -2lambda)/2 are formed where they are used: near the
+// poles one function is many orders of magnitude below the other, and the
+// coupled lam+- form would inject the large one's rounding into the small one,
+// whose recurrence then amplifies it by about (l/m)^(m+2).
 struct Rec {
   double l0, l1;    // lambda_l, lambda_{l-1}
-  double p0, p1;    // lam+_l, lam+_{l-1}
-  double q0, q1;    // lam-_l, lam-_{l-1}
+  double p0, p1;    // 2lambda_l, 2lambda_{l-1}
+  double q0, q1;    // -2lambda_l, -2lambda_{l-1}
   int S;            // scale: true = value * 2^-S (0 = plain)
 };
 
 // advance from l to l+1 with the coefficients of target l+1
 __device__ __forceinline__ void rec_step(Rec &s, const RecCoef &c, double x) {
   double nl = fma(c.al * x, s.l0, -c.bl * s.l1);
-  double ax = c.a * x;
-  double np = fma(ax, s.p0, fma(c.ac, s.q0, -c.b * s.p1));
-  double nq = fma(ax, s.q0, fma(c.ac, s.p0, -c.b * s.q1));
+  const double cp = fma(c.a, x, c.ac), cm = fma(c.a, x, -c.ac);
+  double np = fma(cp, s.p0, -c.b * s.p1);
+  double nq = fma(cm, s.q0, -c.b * s.q1);
   s.l1 = s.l0;
   s.l0 = nl;
   s.p1 = s.p0;
@@ -142,7 +149,7 @@ __global__ void __launch_bounds__(SYN_THREADS) k_leg_syn64(const PairDev *__rest
       const int l = lc + j;
       if (s.S == 0) {
         const double2 t = sT[j], ne = sE[j], nb = sB[j];
-        const double lam = s.l0, lp = s.p0, lq = s.q0;
+        const double lam = s.l0, lp = 0.5 * (s.p0 + s.q0), lq = 0.5 * (s.p0 - s.q0);
         if (((l - m) & 1) == 0) {
           T0.x = fma(t.x, lam, T0.x); T0.y = fma(t.y, lam, T0.y);
           Q0.x = fma(ne.x, lp, Q0.x); Q0.y = fma(ne.y, lp, Q0.y);   // -aE lam+
@@ -242,8 +249,8 @@ __global__ void __launch_bounds__(ANA_P) k_leg_ana64(const PairDev *__restrict__
       const int l = lc + j;
       const bool live = (s.S == 0) && act;
       P0[t][j] = live ? s.l0 : 0.0;
-      Pp[t][j] = live ? s.p0 : 0.0;
-      Pq[t][j] = live ? s.q0 : 0.0;
+      Pp[t][j] = live ? 0.5 * (s.p0 + s.q0) : 0.0;
+      Pq[t][j] = live ? 0.5 * (s.p0 - s.q0) : 0.0;
       if (l < lmax) rec_advance(s, sc[j], x, m, l, seed, pp, npairs);
     }
     __syncthreads();
@@ -389,7 +396,8 @@ __global__ void __launch_bounds__(128) k_gen_tables(const PairDev *__restrict__ 
       if (act) {
         const int64_t o = (base + l) * (int64_t)npairs + p;
         const bool live = (s.S == 0);
-        const double v0 = live ? s.l0 : 0.0, v1 = live ? s.p0 : 0.0, v2 = live ? s.q0 : 0.0;
+        const double v0 = live ? s.l0 : 0.0, v1 = live ? 0.5 * (s.p0 + s.q0) : 0.0,
+                     v2 = live ? 0.5 * (s.p0 - s.q0) : 0.0;
         const float h0 = (float)v0, h1 = (float)v1, h2 = (float)v2;
         ptab[o] = h0;
         ptab[plane + o] = h1;

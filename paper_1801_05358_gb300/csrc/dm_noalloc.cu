@@ -62,9 +62,10 @@ __device__ __forceinline__ void na_step(NaRec &s, const dmwf::RecCoef &c, double
     s.q0 = seed[3 * o + 2];
   } else {
     const double nl = fma(c.al * x, s.l0, -c.bl * s.l1);
-    const double ax = c.a * x;
-    const double np = fma(ax, s.p0, fma(c.ac, s.q0, -c.b * s.p1));
-    const double nq = fma(ax, s.q0, fma(c.ac, s.p0, -c.b * s.q1));
+    // 2lambda and -2lambda as separate recurrences (p, q)
+    const double cp = fma(c.a, x, c.ac), cm = fma(c.a, x, -c.ac);
+    const double np = fma(cp, s.p0, -c.b * s.p1);
+    const double nq = fma(cm, s.q0, -c.b * s.q1);
     s.l1 = s.l0;
     s.l0 = nl;
     s.p1 = s.p0;
@@ -138,8 +139,8 @@ __global__ void __launch_bounds__(NA_P) k_na_ana(const dmwf::PairDev *__restrict
       const int l = lc + j;
       const bool live = (s.S == 0) && act;
       P0[t][j] = live ? s.l0 : 0.0;
-      Pp[t][j] = live ? s.p0 : 0.0;
-      Pq[t][j] = live ? s.q0 : 0.0;
+      Pp[t][j] = live ? 0.5 * (s.p0 + s.q0) : 0.0;  // lam+
+      Pq[t][j] = live ? 0.5 * (s.p0 - s.q0) : 0.0;  // lam-
       if (l < lmax) na_step(s, sc[j], x, m, l, seed, pp, npairs);
     }
     __syncthreads();

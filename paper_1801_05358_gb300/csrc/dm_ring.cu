@@ -81,6 +81,21 @@ __device__ __forceinline__ C chirp(const C *Tq, int j, int n) {
 // x mod n for 0 <= x, skipping the division in the common case x < n
 __device__ __forceinline__ int mod_small(int x, int n) { return x < n ? x : x % n; }
 
+// The same fold reading F_m from global memory (compact mode).
+template <typename C>
+__device__ __forceinline__ C fold_one_g(const C *__restrict__ rc, const C *Tq, int k, int n, int shift, int mmax,
+                                        int64_t base, int64_t mstride) {
+  C acc;
+  acc.x = 0;
+  acc.y = 0;
+  const int n2 = 2 * n;
+  for (int m = k; m <= mmax; m += n)
+    acc = cadd(acc, cmulc(rc[base + (int64_t)m * mstride], phase_q(Tq, mod_small(m * shift, n2), n)));
+  for (int m = n - k; m <= mmax; m += n)
+    if (m >= 1) acc = cadd(acc, cconj(cmulc(rc[base + (int64_t)m * mstride], phase_q(Tq, mod_small(m * shift, n2), n))));
+  return acc;
+}
+
 // Length-h forward DFT of the CTA's lanes in place.  Direct rings (h = M a
 // power of two): bit-reversed input -> natural output.  Bluestein rings:
 // natural input already multiplied by the chirp and zero-padded (to M/2, or to
@@ -123,7 +138,7 @@ __device__ __forceinline__ C dft_out(const C *buf, int k, int bluestein, const C
 // memory.  A lane works in place on M + 1 entries: the real-FFT packing and
 // unpacking handle k and h - k in the same thread.  Lanes of finished RHS
 // compute but write nothing.
-template <typename R, typename C, int MODE>
+template <typename R, typename C, int MODE, bool COMPACT>
 __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings, const int *__restrict__ order,
                                               const C *__restrict__ phase, const C *__restrict__ bhat,
                                               const C *__restrict__ twid, int tw_words, int ph_words,
@@ -147,16 +162,23 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
   const RingDev Rg = rings[r];
   const int n = Rg.n, h = Rg.h, M = Rg.M, bl = Rg.bluestein;
   const int logM = 31 - __clz(M);
-  C *tws = reinterpret_cast<C *>(sm_raw);  // stage twiddles (M - 1 used)
-  C *Tq = tws + tw_words;                  // quarter phase table (n/2 + 1 used)
-  C *buf = Tq + ph_words + (size_t)g * lane_words;  // slots spad(0..M)
-  C *S = buf + buf_words;                            // mmax + 1 staged coefficients (inverse modes)
+  // Compact mode (COMPACT, rings too long for the full layout): twiddles
+  // and phases are read from global memory (L1-cached) and the ring
+  // coefficients are folded straight from global memory; shared memory holds
+  // only the lane buffers.
+  constexpr bool compact = COMPACT;
+  C *tws_s = reinterpret_cast<C *>(sm_raw);  // stage twiddles (M - 1 used)
+  C *Tq_s = tws_s + tw_words;                // quarter phase table (n/2 + 1 used)
+  C *buf = Tq_s + ph_words + (size_t)g * lane_words;  // slots spad(0..M)
+  C *S = buf + buf_words;                              // mmax + 1 staged coefficients (inverse modes)
+  const C *tws = compact ? twid : tws_s;
+  const C *Tq = compact ? phase + Rg.ph_off : Tq_s;
   const int tx = threadIdx.x, nt = blockDim.x;
-  {
+  if (!compact) {
     const int tflat = threadIdx.y * nt + tx, nflat = nt * blockDim.y;
-    for (int i = tflat; i < M - 1; i += nflat) tws[i] = twid[i];
+    for (int i = tflat; i < M - 1; i += nflat) tws_s[i] = twid[i];
     const C *ph = phase + Rg.ph_off;
-    for (int i = tflat; i <= (n >> 1); i += nflat) Tq[i] = ph[i];
+    for (int i = tflat; i <= (n >> 1); i += nflat) Tq_s[i] = ph[i];
   }
   const int64_t moff = ((int64_t)b * 3 + f) * npix + Rg.start;
   const C *bh = bhat + (bl ? Rg.bh_off : 0);
@@ -177,7 +199,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
     // Z_k = E_k + i O_k, E_k = C_k + conj(C_{h-k}), O_k = (C_k - conj(C_{h-k})) e^{2 pi i k/n},
     // stored conjugated (forward DFT + conjugation = inverse); one thread per (k, h - k).
     // stage S_m = F_m e^{i m phi0}: batches of independent loads per thread
-    {
+    if (!compact) {
       constexpr int U = sizeof(R) == 4 ? 8 : 4;
       const int n2 = 2 * n;
       for (int m0 = tx; m0 <= mmax; m0 += U * nt) {
@@ -197,8 +219,10 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
     __syncthreads();
     for (int k = tx; k <= (h >> 1); k += nt) {
       const int k2 = h - k;
-      const C ck = fold_one(S, k, n, mmax);
-      const C ck2 = (k2 == k) ? ck : fold_one(S, k2, n, mmax);
+      const C ck = compact ? fold_one_g(rc, Tq, k, n, Rg.shift, mmax, rbase, mstride) : fold_one(S, k, n, mmax);
+      const C ck2 = (k2 == k) ? ck
+                              : (compact ? fold_one_g(rc, Tq, k2, n, Rg.shift, mmax, rbase, mstride)
+                                         : fold_one(S, k2, n, mmax));
       for (int t = 0; t < 2; ++t) {
         const int kk = t ? k2 : k;
         if (t && (k2 >= h || k2 == k)) break;
@@ -385,25 +409,30 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
   const SolveState *stp = (MODE == RING_ITER || MODE == RING_INIT) ? p->state : nullptr;
   const int T = 128;
   for (const RingClass &rc_cls : p->ring_classes) {
-    const int tw_words = std::max(1, rc_cls.M - 1);
-    const int ph_words = rc_cls.n / 2 + 1;
+    int tw_words = std::max(1, rc_cls.M - 1);
+    int ph_words = rc_cls.n / 2 + 1;
     const int buf_words = rc_cls.M + rc_cls.M / 32 + 1;  // slots spad(0..M)
     const bool staged = (MODE == RING_ITER || MODE == RING_INV_MAP);
-    const int lane_words = buf_words + (staged ? p->mmax + 1 : 0);
+    int lane_words = buf_words + (staged ? p->mmax + 1 : 0);
+    if (sizeof(C) * ((size_t)tw_words + ph_words + lane_words) > (227u << 10)) {  // compact mode
+      tw_words = ph_words = 0;
+      lane_words = buf_words;
+      if (sizeof(C) * (size_t)lane_words > (227u << 10)) return cudaErrorInvalidValue;
+    }
+    const bool compact = (tw_words == 0);
+    auto kern = compact ? k_ring<R, C, MODE, true> : k_ring<R, C, MODE, false>;
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k_ring<R, C, MODE>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
     int G = ring_lanes_per_block(sizeof(C), tw_words, ph_words, lane_words, nlanes, fa.numRegs);
     const size_t smem = sizeof(C) * ((size_t)tw_words + ph_words + (size_t)G * lane_words);
     dim3 grid(rc_cls.count, (nlanes + G - 1) / G);
     dim3 block(T, G);
-    e = cudaFuncSetAttribute(k_ring<R, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_ring<R, C, MODE><<<grid, block, smem, st>>>(p->rings, p->ring_order + rc_cls.off, phase, bhat, twid,
-                                                  tw_words, ph_words, buf_words, lane_words, nlanes, rc, p->mmax,
-                                                  p->npairs,
-                                                  p->npix, p->nrings, in_map, out_user, s_state, w, wd, p->norms,
-                                                  stp, s_anchor);
+    kern<<<grid, block, smem, st>>>(p->rings, p->ring_order + rc_cls.off, phase, bhat, twid, tw_words, ph_words,
+                                    buf_words, lane_words, nlanes, rc, p->mmax, p->npairs, p->npix, p->nrings, in_map,
+                                    out_user, s_state, w, wd, p->norms, stp, s_anchor);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

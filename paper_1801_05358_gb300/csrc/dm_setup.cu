@@ -114,7 +114,10 @@ __global__ void k_reccoef(RecCoef *rec, int lmax, int mmax) {
 }
 
 // ------------------------------------------------------------------- seeds
-// Per pair and m: lambda_mm and lam+- at l0 = max(m, 2), carried as v * 2^-S.
+// Per pair and m: lambda_mm, 2lambda and -2lambda at l0 = max(m, 2), carried as
+// v * 2^-S.  The two spin-2 functions are kept apart (not as their half sum and
+// difference lam+-): near the poles they differ by many orders of magnitude and
+// the sum would lose the small one.
 //   lambda_mm = prod_{j<=m} (-sqrt((2j+1)/(2j)) sin theta) / sqrt(4 pi)
 //   m >= 2: 2lambda_mm = lambda_mm r tan^2(theta/2), -2lambda_mm = lambda_mm r cot^2(theta/2),
 //           r = sqrt(m(m-1)/((m+1)(m+2)))
@@ -151,21 +154,21 @@ __global__ void k_seeds(const PairDev *pairs, double *seed, int *seed_exp, int m
         mv = n2 * 2.0 * c2 * c * s;             // -2lambda_21 = N2 2 c^3 s
       }
       l0 = ldexp(v, e);
-      lp = 0.5 * (pv + mv);
-      lm = 0.5 * (pv - mv);
+      lp = pv;
+      lm = mv;
       S = 0;
     } else {
       double r = sqrt((double)m * (m - 1) / ((double)(m + 1) * (m + 2)));
       double pv = v * r * t2, mv = v * r / t2;
       if (e >= -600) {
         l0 = ldexp(v, e);
-        lp = ldexp(0.5 * (pv + mv), e);
-        lm = ldexp(0.5 * (pv - mv), e);
+        lp = ldexp(pv, e);
+        lm = ldexp(mv, e);
         S = 0;
       } else {
         l0 = v;
-        lp = 0.5 * (pv + mv);
-        lm = 0.5 * (pv - mv);
+        lp = pv;
+        lm = mv;
         S = -e;
       }
     }
@@ -187,14 +190,21 @@ __device__ void filter_one_l(const double *cl, int lmax, int l, double mu, doubl
     if (tt >= ee) { e1 = tt; e2 = ee; v1x = 1.0; v1y = 0.0; }
     else { e1 = ee; e2 = tt; v1x = 0.0; v1y = 1.0; }
   } else {
-    double hd = 0.5 * (tt - ee);
-    double disc = sqrt(hd * hd + te * te);
-    e1 = 0.5 * (tt + ee) + disc;
-    e2 = (tt * ee - te * te) / e1;
-    double ax = te, ay = e1 - tt, bx = e1 - ee, by = te;
-    double na = sqrt(ax * ax + ay * ay), nb = sqrt(bx * bx + by * by);
+    // decomposed at unit scale: the spectra fall below 1e-150 at high l, where
+    // their squares and products would be subnormal and the eigenvector would
+    // lose its unit length
+    const double sc = fmax(fmax(fabs(tt), fabs(ee)), fabs(te));
+    const double a = tt / sc, c = ee / sc, b = te / sc;
+    const double hd = 0.5 * (a - c);
+    const double disc = hypot(hd, b);
+    const double u1 = 0.5 * (a + c) + disc;
+    const double u2 = (a * c - b * b) / u1;
+    const double ax = b, ay = u1 - a, bx = u1 - c, by = b;
+    const double na = hypot(ax, ay), nb = hypot(bx, by);
     if (na >= nb) { v1x = ax / na; v1y = ay / na; }
     else { v1x = bx / nb; v1y = by / nb; }
+    e1 = u1 * sc;
+    e2 = u2 * sc;
   }
   double v2x = -v1y, v2y = v1x;
   e1 = fmax(e1, 0.0);

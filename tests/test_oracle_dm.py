@@ -256,3 +256,18 @@ def test_cr_inputs_consistent(orc):
     n = orc.draw_noise(nside, wl.sigma, wl.mask, 77)
     assert np.allclose(dhat, (shat + n) * wl.mask, atol=1e-14)
     assert np.all(dhat[:, wl.mask == 0] == 0)
+
+
+def test_filter_is_scalar_where_spectra_underflow(orc):
+    """Where both eigenvalues of the TE block lie far below mu the filter of
+    Eq. 10 is f 1 exactly (any rotation R), even where the analytic spectra
+    (around 1e-160 near l = 750) have subnormal squares and products."""
+    lmax = 4096
+    cl = W.cl_analytic(lmax)
+    th, mu = 1.06e-9, 999.0 * 1.06e-9
+    coef = orc.filter_coefs(lmax, cl, mu, th)
+    f = mu / (mu + th)
+    for l in [700, 740, 750, 753, 756, 760, 800, 1100, 4096]:
+        assert coef[l, 0] == pytest.approx(f, rel=1e-14)
+        assert coef[l, 2] == pytest.approx(f, rel=1e-14)
+        assert abs(coef[l, 1]) <= 1e-14 * f
