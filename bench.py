@@ -57,6 +57,17 @@ def parse():
                     help="iterations of the plain FP64 GPU path timed beside (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve-tol", type=float, default=None,
+                    help="run whole solves to this final Cauchy threshold and report WF solves/s instead")
+    ap.add_argument("--solve-max-iter", type=int, default=200000)
+    ap.add_argument("--serve", action="store_true", help="run a sample of the serving mix instead")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-warm", type=int, default=12)
+    ap.add_argument("--serve-nsides", default="64,128")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-max-iter", type=int, default=30000)
+    ap.add_argument("--serve-budget-gb", type=float, default=200.0)
+    ap.add_argument("--serve-seed", type=int, default=4)
     return ap.parse_args()
 
 
@@ -212,10 +223,199 @@ def run_reference(args):
     return 0
 
 
+def bench_inputs(dmwf, torch, dev, nside, lmax, B):
+    """The batched constrained-realisation workload: one plan with the shared
+    spectra, noise and mask; B // 2 data maps d = Y a + n (Wiener filter) and
+    B - B // 2 fluctuation data maps dhat, seeds 100 .. 99 + B."""
+    npix = 12 * nside * nside
+    nwf = B // 2 if B > 1 else 1
+    seeds = [100 + b for b in range(B)]
+    wl = W.make_workload("nside512", seeds[:nwf], nside=nside, lmax=lmax)
+    plan = dmwf.Plan(nside, lmax, B)
+    plan.set_spectra(wl.cl)
+    plan.set_noise_mask(wl.sigma, wl.mask)
+    nalm = plan.nalm
+    d = torch.zeros((B, 3, npix), dtype=torch.float64, device=dev)
+    alm_in = torch.zeros((B, 3, nalm, 2), dtype=torch.float64, device=dev)
+    for b in range(nwf):
+        alm_in[b] = torch.from_numpy(np.ascontiguousarray(wl.alm_true[b]).view(np.float64).reshape(3, nalm, 2))
+    s_tmp = torch.zeros_like(d)
+    plan.alm2map(alm_in, s_tmp)            # signal maps Y a (product synthesis)
+    for b in range(nwf):
+        d[b] = (s_tmp[b] + torch.from_numpy(wl.noise[b]).to(dev)) * torch.from_numpy(wl.mask).to(dev)
+    if B > nwf:                               # fluctuation data dhat of constrained realisations
+        dh = torch.zeros_like(d)
+        plan.draw_cr_inputs(seeds, dhat=dh)
+        d[nwf:] = dh[nwf:]
+    del s_tmp, alm_in
+    torch.cuda.synchronize()
+    return plan, wl, d
+
+
+def run_solves(args):
+    """Whole solves of the batch, lambda 1000 -> 1 over 10 levels with the
+    Cauchy threshold cooled from 1e-4 to --solve-tol, through dm_wiener_filter
+    (the call a user makes): WF solves/s = B / the device time of the call."""
+    import torch
+
+    from paper_1801_05358_gb300 import dmwf
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nside, B = args.nside, args.batch
+    lmax = args.lmax or 2 * nside
+    plan, wl, d = bench_inputs(dmwf, torch, dev, nside, lmax, B)
+    prec = dmwf.DM_MIXED_FP32 if args.precision == "mixed" else dmwf.DM_FP64
+    plan.set_precision(prec)
+    tol = args.solve_tol
+    s_out = torch.zeros_like(d)
+    # warm-up: tables and first-use allocations, 3 iterations
+    plan.set_schedule(lambda0=1000.0, n_levels=10, iters_per_level=0, eps0=1e-4, eps_final=tol, eta=0.0,
+                      max_iter=args.solve_max_iter, check_every=64)
+    plan.solve_begin(d)
+    plan.solve_iterate(3)
+    plan.solve_end()
+    plan.profile_enable(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        st, stats = plan.wiener_filter(d, s_out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = plan.profile_read()
+    plan.close()
+    its = np.array([x["iters_total"] for x in stats])
+    conv = int(sum(1 for x in stats if x["iters_total"] < args.solve_max_iter))
+    line = {"metric": "WF solves/s", "value": B / (ms * 1e-3), "unit": "solves/s", "n_gpus": 1, "steps": 1,
+            "warmup": 3, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == dmwf.DM_FP64 else "f32 (bf16x3 tensor-core Legendre, f64 harmonic state)",
+            "data": "synthetic",
+            "config": {"workload": f"whole solves of the batched constrained realisations, nside {nside} lmax {lmax}, "
+                                   f"{B} RHS, lambda 1000 -> 1 in 10 levels, Cauchy 1e-4 -> {tol:g}",
+                       "nside": nside, "lmax": lmax, "batch": B, "precision": args.precision, "tol": tol},
+            "iterations_per_rhs": {"mean": float(its.mean()), "min": int(its.min()), "max": int(its.max())},
+            "converged_rhs": conv, "dm_iterations_per_s": float(its.sum()) / (ms * 1e-3),
+            "anchors": prof["anchors"], "gpu_launches": prof["launches"], "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """A sample of the serving mix through dm_serve_submit / dm_serve_poll:
+    requests drawn by workloads.serving_stream (nside from --serve-nsides,
+    lmax = 2 nside, 70 % Wiener filter / 30 % constrained realisation,
+    tolerance 1e-5 or 1e-8, per-request seeds), the 1e-8 ones in float-float
+    pools.  A closed-loop pass over the first --serve-warm requests measures
+    the capacity; the rest then arrive as a Poisson stream at 0.8 x that
+    capacity.  Reports solves/s and the p50 / p99 submit-to-result latency
+    of the Poisson phase."""
+    import torch
+
+    from paper_1801_05358_gb300 import dmwf
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nsides = [int(x) for x in args.serve_nsides.split(",")]
+    reqs = W.serving_stream(args.serve_requests, args.serve_seed, nsides=nsides)
+    # inputs of every request: its own mask, noise, signal and data map
+    synth = {}
+    for r in reqs:
+        wl = W.make_workload("nside16", [r["seed"]], nside=r["nside"], lmax=r["lmax"])
+        if r["nside"] not in synth:
+            synth[r["nside"]] = dmwf.Plan(r["nside"], r["lmax"], 1)
+        nalm = synth[r["nside"]].nalm
+        a = torch.from_numpy(np.ascontiguousarray(wl.alm_true[0]).view(np.float64).reshape(1, 3, nalm, 2)).to(dev)
+        m = torch.zeros((1, 3, 12 * r["nside"] ** 2), dtype=torch.float64, device=dev)
+        synth[r["nside"]].alm2map(a, m)
+        r.update(cl=wl.cl, sigma=wl.sigma, mask=wl.mask, d=wl.data([m[0].cpu().numpy()])[0])
+    for p in synth.values():
+        p.close()
+    torch.cuda.synchronize()
+    srv = dmwf.Server(int(args.serve_budget_gb * (1 << 30)), slots_per_plan=args.serve_slots, iters_per_round=16,
+                      prec=dmwf.DM_MIXED_FP32, max_iter=args.serve_max_iter, strict_tol=1e-6,
+                      strict_prec=dmwf.DM_FLOAT_FLOAT)
+
+    def submit(r):
+        return srv.submit(r["nside"], r["lmax"], r["kind"], r["tol"], r["cl"], r["sigma"], r["d"], r["mask"],
+                          r["seed"])
+
+    def drain(live, results):
+        for t in list(live):
+            got = srv.poll(t)
+            if got is not None:
+                results[t] = (got[0], time.perf_counter())
+                live.discard(t)
+
+    nw = min(args.serve_warm, len(reqs))
+    warm, rest = reqs[:nw], reqs[nw:]
+    # closed loop: all warm requests at once
+    t0 = time.perf_counter()
+    live, res_w = {submit(r) for r in warm}, {}
+    while live:
+        drain(live, res_w)
+        time.sleep(0.002)
+    t_warm = time.perf_counter() - t0
+    capacity = nw / t_warm
+    rate = 0.8 * capacity
+    arr = W.poisson_arrivals(len(rest), rate, args.serve_seed + 1)
+    res, live, tick = {}, set(), {}
+    t0 = time.perf_counter()
+    with ClockSampler(0) as clk:
+        i = 0
+        while i < len(rest) or live:
+            now = time.perf_counter() - t0
+            while i < len(rest) and arr[i] <= now:
+                t = submit(rest[i])
+                tick[t] = rest[i]
+                live.add(t)
+                i += 1
+            drain(live, res)
+            time.sleep(0.001)
+    t_all = time.perf_counter() - t0
+    info = srv.info()
+    srv.close()
+    lat = np.array([r[0]["latency_ms"] for r in res.values()])
+    qms = np.array([r[0]["queue_ms"] for r in res.values()])
+    st = [r[0]["status"] for r in res.values()]
+    its = np.array([r[0]["iters"] for r in res.values()])
+    by = {}
+    for t, (r0, _) in res.items():
+        q = tick[t]
+        k = f"nside{q['nside']}_tol{q['tol']:g}"
+        by.setdefault(k, []).append(r0["latency_ms"])
+    ok = sum(1 for x in st if x == 0)
+    line = {"metric": "WF solves/s (serving)", "value": len(res) / t_all, "unit": "solves/s", "n_gpus": 1,
+            "steps": len(res), "warmup": nw, "ms_per_step": t_all * 1e3 / max(1, len(res)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 mixed pools (tol 1e-5), float-float pools (tol 1e-8)", "data": "synthetic",
+            "config": {"workload": f"serving mix sample: {len(reqs)} requests, nside in {nsides}, lmax = 2 nside, "
+                                   f"70 % WF / 30 % CR, tol 1e-5 or 1e-8, Poisson arrivals at 0.8 x capacity",
+                       "slots_per_pool": args.serve_slots, "max_iter": args.serve_max_iter,
+                       "hbm_budget_gb": args.serve_budget_gb},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "queue_ms": {"p50": float(np.percentile(qms, 50)), "p99": float(np.percentile(qms, 99))},
+            "latency_p50_ms_by_class": {k: float(np.percentile(v, 50)) for k, v in sorted(by.items())},
+            "capacity_closed_loop": capacity, "arrival_rate": rate,
+            "status": {"ok": ok, "not_converged": sum(1 for x in st if x == 4), "other": len(st) - ok -
+                       sum(1 for x in st if x == 4)},
+            "iterations": {"mean": float(its.mean()), "max": int(its.max())},
+            "server": info, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.solve_tol is not None:
+        return run_solves(args)
+    if args.serve:
+        return run_serve(args)
     import torch
     import torch.distributed as dist
 
@@ -232,28 +432,10 @@ def main():
     K, Wu = args.steps, max(3, args.warmup)
     npix = 12 * nside * nside
     nwf = B // 2 if B > 1 else 1
-    seeds = [100 + b for b in range(B)]
 
-    # ---- inputs: shared spectra, noise and mask; data maps per RHS ----
-    wl = W.make_workload("nside512", seeds[:nwf], nside=nside, lmax=lmax)
-    plan = dmwf.Plan(nside, lmax, B)
-    plan.set_spectra(wl.cl)
-    plan.set_noise_mask(wl.sigma, wl.mask)
-    prec = dmwf.DM_MIXED_FP32 if args.precision == "mixed" else dmwf.DM_FP64
+    plan, wl, d = bench_inputs(dmwf, torch, dev, nside, lmax, B)
     nalm = plan.nalm
-    d = torch.zeros((B, 3, npix), dtype=torch.float64, device=dev)
-    alm_in = torch.zeros((B, 3, nalm, 2), dtype=torch.float64, device=dev)
-    for b in range(nwf):
-        alm_in[b] = torch.from_numpy(np.ascontiguousarray(wl.alm_true[b]).view(np.float64).reshape(3, nalm, 2))
-    s_tmp = torch.zeros_like(d)
-    plan.alm2map(alm_in, s_tmp)            # signal maps Y a (product synthesis)
-    for b in range(nwf):
-        d[b] = (s_tmp[b] + torch.from_numpy(wl.noise[b]).to(dev)) * torch.from_numpy(wl.mask).to(dev)
-    if B > nwf:                               # fluctuation data dhat of constrained realisations
-        dh = torch.zeros_like(d)
-        plan.draw_cr_inputs(seeds, dhat=dh)
-        d[nwf:] = dh[nwf:]
-    del s_tmp, alm_in
+    prec = dmwf.DM_MIXED_FP32 if args.precision == "mixed" else dmwf.DM_FP64
     s_out = torch.zeros_like(d)
     torch.cuda.synchronize()
 

@@ -304,6 +304,9 @@ typedef struct {
   dm_schedule sched;         /* cooling schedule (eps_final is per request) */
   int anchor_every;          /* mixed-precision refinement period (0 = 256) */
   int max_pending;           /* queue bound; dm_serve_submit returns DM_EBUSY beyond it (0 = 100000) */
+  double strict_tol;         /* requests with tol < strict_tol run in pools of strict_prec (0 = never) */
+  dm_precision strict_prec;  /* DM_FP64 or DM_FLOAT_FLOAT: a mixed-mode Cauchy ratio cannot resolve
+                                tolerances near the FP32 rounding of the iteration state */
 } dm_server_config;
 
 typedef struct {

@@ -1,7 +1,9 @@
 // dm_serve.cu -- continuous-batching server for Wiener-filter and
 // constrained-realisation requests of different geometries.
 //
-// A pool is one dm_plan per (nside, lmax, spectra) whose RHS are slots.  One
+// A pool is one dm_plan per (nside, lmax, spectra, precision) whose RHS are
+// slots; a request tighter than the strict tolerance goes to an FP64-class
+// pool (DM_FP64 or DM_FLOAT_FLOAT), any other to the default mode.  One
 // worker thread owns the device work:
 //   admission : queued requests go to free slots of their pool, or into a new
 //               pool while the device-memory budget allows; a slot is set up
@@ -62,6 +64,7 @@ struct Slot {
 struct Pool {
   int nside = 0, lmax = 0;
   uint64_t cl_hash = 0;
+  dm_precision prec = DM_FP64;  // mode the plan was set to (DM_FLOAT_FLOAT kept as such)
   dm_plan *plan = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<Slot> slots;
@@ -147,14 +150,16 @@ size_t estimate_bytes(int nside, int lmax, int S, dm_precision prec) {
   b += S * 3 * nalm * 16 * 2;                    // a, tmpalm
   b += S * 3 * npix * 8 * 7;                     // wd, tmpmap(2), s64, rhi, w, sigma
   b += nalm * 48 + (lmax + 1.0) * npairs * 28;   // coefficients, seeds
-  if (prec == DM_MIXED_FP32) {
-    b += 3 * nalm * npairs * 4;                  // FP32 tables
+  if (prec != DM_FP64) {                         // DM_MIXED_FP32 and DM_FLOAT_FLOAT
+    b += 3 * nalm * npairs * 4 * 2;              // FP32 tables, hi and lo
     b += S * 3 * (lmax + 1.0) * npairs * 2 * 8;  // rc32
     b += S * nchunk * 3 * nalm * 8;              // apart32
     b += S * 3 * npix * 4 * 4;                   // s32, w32, wd32, shi32
     b += S * 3 * nalm * 16 * 2;                  // a_hi, g_hi
-    if (dmwf::tc_batch_ok(S)) b += (double)dmwf::tc_table_bytes(lmax, lmax, (int)npairs, S);  // tiled BF16 tables
+    b += S * 3 * nalm * 8 * 2;                   // e32, c32
   }
+  if (prec == DM_MIXED_FP32 && dmwf::tc_batch_ok(S))
+    b += (double)dmwf::tc_table_bytes(lmax, lmax, (int)npairs, S);  // tiled BF16 tables
   return (size_t)(b * 1.05) + (64u << 20);
 }
 
@@ -190,16 +195,23 @@ void finish(dm_server *S, Request &r, dm_status st, int iters, double cauchy) {
   S->done[r.ticket] = res;
 }
 
+// Requests tighter than strict_tol go to pools of strict_prec, the rest to
+// pools of prec.
+dm_precision request_prec(const dm_server *S, const Request &r) {
+  return (S->cfg.strict_tol > 0.0 && r.tol < S->cfg.strict_tol) ? S->cfg.strict_prec : S->cfg.prec;
+}
+
 Pool *make_pool(dm_server *S, const Request &r) {
   const int slots = S->cfg.slots_per_plan;
-  size_t need = estimate_bytes(r.nside, r.lmax, slots, S->cfg.prec);
+  const dm_precision prec = request_prec(S, r);
+  size_t need = estimate_bytes(r.nside, r.lmax, slots, prec);
   if (S->used + need > S->cfg.hbm_budget_bytes) {
     // free idle pools (no busy slot) to make room
     std::lock_guard<std::mutex> lk(S->mu);
     for (size_t i = 0; i < S->pools.size();) {
       Pool *q = S->pools[i].get();
       if (q->busy() == 0) {
-        S->used -= estimate_bytes(q->nside, q->lmax, slots, S->cfg.prec);
+        S->used -= estimate_bytes(q->nside, q->lmax, slots, q->prec);
         cudaStreamDestroy(q->stream);
         dm_plan_destroy(q->plan);
         S->pools.erase(S->pools.begin() + i);
@@ -213,13 +225,14 @@ Pool *make_pool(dm_server *S, const Request &r) {
   pool->nside = r.nside;
   pool->lmax = r.lmax;
   pool->cl_hash = hash_bytes(r.cl.data(), r.cl.size() * sizeof(double));
+  pool->prec = prec;
   if (dm_plan_create(r.nside, r.lmax, slots, &pool->plan) != DM_OK) return nullptr;
   dm_plan *p = pool->plan;
   dm_schedule sc = S->cfg.sched;
   sc.iters_per_level = 0;
   if (dm_set_schedule(p, &sc) != DM_OK || dm_set_spectra(p, r.cl.data()) != DM_OK ||
       dm_set_noise_mask(p, r.sigma.data(), r.has_mask ? r.mask.data() : nullptr) != DM_OK ||
-      dm_set_precision(p, S->cfg.prec) != DM_OK) {
+      dm_set_precision(p, prec) != DM_OK) {
     dm_plan_destroy(p);
     return nullptr;
   }
@@ -229,7 +242,7 @@ Pool *make_pool(dm_server *S, const Request &r) {
   k_mark_done<<<(slots + 127) / 128, 128, 0, pool->stream>>>(p->state, slots);
   p->session = true;
   p->state_active = true;
-  if (S->cfg.prec == DM_MIXED_FP32) p->anchor_active = true;
+  if (prec == DM_MIXED_FP32) p->anchor_active = true;
   cudaStreamSynchronize(pool->stream);
   std::lock_guard<std::mutex> lk(S->mu);
   S->used += need;
@@ -239,9 +252,10 @@ Pool *make_pool(dm_server *S, const Request &r) {
 
 Pool *find_pool(dm_server *S, const Request &r, bool *full) {
   const uint64_t h = hash_bytes(r.cl.data(), r.cl.size() * sizeof(double));
+  const dm_precision prec = request_prec(S, r);
   *full = false;
   for (auto &q : S->pools)
-    if (q->nside == r.nside && q->lmax == r.lmax && q->cl_hash == h) {
+    if (q->nside == r.nside && q->lmax == r.lmax && q->cl_hash == h && q->prec == prec) {
       if (q->busy() < (int)q->slots.size()) return q.get();
       *full = true;
     }
@@ -443,7 +457,8 @@ dm_status dm_server_create(const dm_server_config *cfg, dm_server **out) {
   if (!cfg || !out) return DM_EINVAL;
   *out = nullptr;
   if (cfg->slots_per_plan < 1 || cfg->slots_per_plan > 1024 || cfg->hbm_budget_bytes == 0 ||
-      (cfg->prec != DM_FP64 && cfg->prec != DM_MIXED_FP32))
+      (cfg->prec != DM_FP64 && cfg->prec != DM_MIXED_FP32) || !(cfg->strict_tol >= 0.0) ||
+      (cfg->strict_tol > 0.0 && cfg->strict_prec != DM_FP64 && cfg->strict_prec != DM_FLOAT_FLOAT))
     return DM_EINVAL;
   dm_server *S = new dm_server();
   S->cfg = *cfg;

@@ -53,7 +53,8 @@ class DmProfile(ctypes.Structure):
 class DmServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("slots_per_plan", ctypes.c_int),
                 ("iters_per_round", ctypes.c_int), ("prec", ctypes.c_int), ("sched", DmSchedule),
-                ("anchor_every", ctypes.c_int), ("max_pending", ctypes.c_int)]
+                ("anchor_every", ctypes.c_int), ("max_pending", ctypes.c_int), ("strict_tol", ctypes.c_double),
+                ("strict_prec", ctypes.c_int)]
 
 
 class DmRequest(ctypes.Structure):
@@ -320,13 +321,15 @@ class Plan:
 class Server:
     """Continuous-batching server (dm_server_*).  Requests carry host arrays;
     the result map is written into a host array owned by this object until the
-    ticket completes."""
+    ticket completes.  Requests with tol < strict_tol are served by pools of
+    strict_prec (DM_FP64 or DM_FLOAT_FLOAT), the others by pools of prec."""
 
     def __init__(self, hbm_budget_bytes, slots_per_plan=8, iters_per_round=16, prec=DM_FP64, lambda0=1000.0,
-                 n_levels=10, eps0=1e-4, max_iter=1000000, anchor_every=0, max_pending=0):
+                 n_levels=10, eps0=1e-4, max_iter=1000000, anchor_every=0, max_pending=0, strict_tol=0.0,
+                 strict_prec=DM_FP64):
         sc = DmSchedule(lambda0, n_levels, 0, eps0, 1e-6, 0.0, max_iter, 8)
         cfg = DmServerConfig(int(hbm_budget_bytes), slots_per_plan, iters_per_round, prec, sc, anchor_every,
-                             max_pending)
+                             max_pending, float(strict_tol), strict_prec)
         h = ctypes.c_void_p()
         st = lib().dm_server_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != DM_OK:

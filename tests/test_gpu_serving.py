@@ -4,7 +4,8 @@
 - served Wiener filters and constrained realisations of two geometries match
   the oracle run alone (FP64, relative L2 <= 1e-10, same iteration count);
 - each result is bit-identical alone and in the mix (FP64 and mixed mode);
-- queue bound, cancellation and a budget that can never fit are reported."""
+- queue bound, cancellation and a budget that can never fit are reported;
+- requests tighter than the strict tolerance are routed to FP64-class pools."""
 import time
 
 import numpy as np
@@ -136,3 +137,43 @@ def test_serving_queue_bound_cancel_and_budget(orc):
         time.sleep(0.01)
     assert got is not None and got[0]["status"] == dmwf.DM_ENOMEM
     srv.close()
+
+
+def test_serving_routes_strict_tolerance_to_float_float(orc):
+    """A mixed-mode server with strict_tol 1e-6: the 1e-7 request runs in a
+    float-float pool and meets the FP64 bar against the oracle (same
+    iteration count); the 1e-5 request runs in a mixed pool."""
+    reqs = []
+    for i, tol in enumerate([1e-5, 1e-7]):
+        wl = W.make_workload("nside16", [60 + i], nside=8, lmax=16)
+        reqs.append(dict(nside=8, lmax=16, kind=0, tol=tol, cl=wl.cl, sigma=wl.sigma, mask=wl.mask,
+                         d=_data(orc, wl)[0]))
+    srv = dmwf.Server(8 << 30, slots_per_plan=2, iters_per_round=16, prec=dmwf.DM_MIXED_FP32, strict_tol=1e-6,
+                      strict_prec=dmwf.DM_FLOAT_FLOAT)
+    tickets = [srv.submit(r["nside"], r["lmax"], r["kind"], r["tol"], r["cl"], r["sigma"], r["d"], r["mask"])
+               for r in reqs]
+    out = {}
+    t0 = time.time()
+    while len(out) < 2 and time.time() - t0 < 600:
+        for t in tickets:
+            if t not in out:
+                got = srv.poll(t)
+                if got is not None:
+                    out[t] = got
+        time.sleep(0.01)
+    info = srv.info()
+    srv.close()
+    assert len(out) == 2 and info["pools"] == 2
+    (res_m, _), (res_f, s_f) = out[tickets[0]], out[tickets[1]]
+    assert res_m["status"] == 0 and res_f["status"] == 0
+    r = reqs[1]
+    lam = W.lambda_schedule(1000.0, 10)
+    ref = orc.dm_solve(r["nside"], r["lmax"], r["cl"], r["sigma"], r["mask"], r["d"], lam,
+                       eps=W.eps_schedule(10, 1e-4, r["tol"]))
+    assert res_f["iters"] == ref["iters"]
+    assert rel(s_f, ref["s"]) < 1e-9
+
+
+def test_server_rejects_mixed_strict_precision():
+    with pytest.raises(dmwf.DmError):
+        dmwf.Server(1 << 30, prec=dmwf.DM_MIXED_FP32, strict_tol=1e-6, strict_prec=dmwf.DM_MIXED_FP32)

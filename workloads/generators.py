@@ -238,3 +238,26 @@ def random_alm(lmax: int, nalm_sets: int, seed: int, cl: np.ndarray | None = Non
         cl[3] = 0.0
         cl[1:3, :2] = 0.0
     return np.stack([draw_alm(lmax, cl, rng) for _ in range(nalm_sets)])
+
+
+def serving_stream(n: int, seed: int, nsides=(64, 128, 256, 512, 1024), p_wf: float = 0.7,
+                   tols=(1e-5, 1e-8)) -> list:
+    """The serving mix: n requests with nside drawn uniformly from nsides,
+    lmax = 2 nside, Wiener filter with probability p_wf (else constrained
+    realisation), tolerance drawn uniformly from tols, and a per-request seed
+    (its mask, noise and signal come from make_workload with that seed).
+    Arrival times are drawn separately (poisson_arrivals), so the same mix
+    can be replayed at any rate."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        ns = int(rng.choice(nsides))
+        out.append(dict(nside=ns, lmax=2 * ns, kind=0 if rng.random() < p_wf else 1,
+                        tol=float(rng.choice(tols)), seed=int(seed) * 100000 + i))
+    return out
+
+
+def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate (1/s)."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))
