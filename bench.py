@@ -57,6 +57,8 @@ def parse():
                     help="iterations of the plain FP64 GPU path timed beside (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ring-radix", type=int, default=None, choices=[0, 3, 4],
+                    help="ring transforms of radix 2^k (3 or 4), 0 = generic kernels (default: the plan's)")
     ap.add_argument("--solve-tol", type=float, default=None,
                     help="run whole solves to this final Cauchy threshold and report WF solves/s instead")
     ap.add_argument("--solve-max-iter", type=int, default=200000)
@@ -436,6 +438,8 @@ def main():
     plan, wl, d = bench_inputs(dmwf, torch, dev, nside, lmax, B)
     nalm = plan.nalm
     prec = dmwf.DM_MIXED_FP32 if args.precision == "mixed" else dmwf.DM_FP64
+    if args.ring_radix is not None:
+        plan.set_ring_radix(args.ring_radix)
     s_out = torch.zeros_like(d)
     torch.cuda.synchronize()
 
@@ -632,6 +636,7 @@ def main():
                 "config": {"workload": f"batched constrained realisations nside {nside} lmax {lmax}: "
                                        f"{nwf} WF + {B - nwf} fluctuation RHS per launch (seeds 100..{99 + B})",
                            "nside": nside, "lmax": lmax, "batch": B, "precision": args.precision,
+                           "ring_radix": "plan default" if args.ring_radix is None else args.ring_radix,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "l2": "inputs larger than L2 (maps and ring coefficients exceed 129 MB)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["launches"],

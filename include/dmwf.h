@@ -190,6 +190,13 @@ dm_status dm_set_anchor_precision(dm_plan *plan, dm_precision prec);
  * A pipeline wait that gives up reports DM_ETIMEOUT. */
 dm_status dm_set_tensor_cores(dm_plan *plan, int on);
 
+/* Tuning: the ring transforms of an iteration for rings whose FFT size M is a
+ * power of two in [512, 4096] run as fixed-size kernels of radix 2^lr with
+ * M / 2^lr threads per ring and (RHS, field) lane; lr = 3 (radix 8, the
+ * default) or 4 (radix 16); lr = 0 selects the generic radix-2^2 kernels for
+ * every size.  The results agree to rounding.  DM_EINVAL for other lr. */
+dm_status dm_set_ring_radix(dm_plan *plan, int lr);
+
 /* Constrained realisations, Section 2.2, Eq. 19:
  * s_CR = W(d - dhat) + shat with shat = Y ahat, ahat ~ S, dhat = shat + nhat,
  * nhat ~ N on observed pixels, drawn from seeds[batch] (host) with the

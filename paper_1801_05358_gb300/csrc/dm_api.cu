@@ -48,7 +48,8 @@ void free_all(dm_plan *p) {
                   p->ptab, p->rc32, p->apart32, p->s32, p->w32, p->wd32, p->phase32, p->bhat32, p->twid32,
                   p->a_hi, p->g_hi, p->shi32, p->s64, p->rhi, p->tc_err, p->ring_order,
                   p->tc_synA[0], p->tc_synA[1], p->tc_anaA[0], p->tc_anaA[1], p->tc_soff, p->tc_aoff,
-                  p->tc_synB[0], p->tc_synB[1], p->ptab_lo, p->e32, p->c32, p->clev, p->filt32};
+                  p->tc_synB[0], p->tc_synB[1], p->ptab_lo, p->e32, p->c32, p->clev, p->filt32,
+                  p->twr, p->twr32, p->chirp, p->chirp32};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -707,6 +708,12 @@ dm_status dm_solve_end(dm_plan *p, double *s_out, double *alm_out, dm_stats *sta
 dm_status dm_set_tensor_cores(dm_plan *p, int on) {
   if (!p) return DM_EINVAL;
   p->use_tc = on != 0;
+  return DM_OK;
+}
+
+dm_status dm_set_ring_radix(dm_plan *p, int lr) {
+  if (!p || (lr != 0 && lr != 3 && lr != 4)) return DM_EINVAL;
+  p->ring_lr = lr;
   return DM_OK;
 }
 

@@ -235,4 +235,291 @@ __device__ void bluestein_conv(T2 *x, int M, const T2 *tws, const T2 *__restrict
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Fixed-size transforms, M = 2^LOGM >= 512, radix R = 2^LR (LR = 3 or 4), one
+// lane = M / R threads.
+//
+// Every pass gives each thread one group of R elements {base + r L, r < R} in
+// registers (base = R L (t / L) + t mod L for thread t), so a transform takes
+// ceil(LOGM / LR) shared-memory passes with compile-time strides instead of
+// one pass per two radix-2 stages.  With j = t mod L and W_N = e^{-2 pi i/N}:
+//   DIF pass (natural -> bit-reversed):  y_q = W_{RL}^{jq} sum_r a_r W_R^{rq},
+//                                        stored at base + brev(q) L;
+//   DIT pass (bit-reversed -> natural):  y_q = sum_r a_r W_{RL}^{j brev(r)} W_R^{brev(r) q},
+//                                        stored at base + q L.
+// DIF passes run with L = M/R, M/R^2, ... and a last pass of 2^(LOGM mod LR)
+// points on L = 1 (several groups per thread); DIT passes run in the opposite
+// order.  Both produce exactly the layouts of the radix-2 forms above (the
+// same bit-reversed order), so the families are interchangeable.
+// Twiddles of the pass with stride L > 1: tw[off(L) + (q - 1) L + j] = W_{RL}^{jq}
+// (q = 1..R-1, j < L), tables of the passes in DIF order (fftr_tw_words entries).
+
+__host__ __device__ constexpr int brev_bits(int x, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+  return r;
+}
+
+// offset of the twiddle table of DIF pass P, and the total size
+__host__ __device__ constexpr int fftr_tw_off(int LOGM, int LR, int P) {
+  int o = 0;
+  for (int i = 0; i < P; ++i) {
+    const int L = (1 << LOGM) >> (LR * (i + 1));
+    o += L > 1 ? ((1 << LR) - 1) * L : 0;
+  }
+  return o;
+}
+__host__ __device__ constexpr int fftr_tw_words(int LOGM, int LR) { return fftr_tw_off(LOGM, LR, LOGM / LR); }
+
+template <typename T2>
+__device__ __forceinline__ T2 cmk(decltype(T2::x) x, decltype(T2::x) y) {
+  T2 r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+
+// a * W_16^E for a compile-time E (cos and sin of multiples of pi/8)
+template <int E, typename T2>
+__device__ __forceinline__ T2 w16(T2 a) {
+  using R = decltype(a.x);
+  constexpr int e = E & 15;
+  if constexpr (e == 0) {
+    return a;
+  } else if constexpr (e == 4) {
+    return cmk<T2>(a.y, -a.x);
+  } else if constexpr (e == 8) {
+    return cmk<T2>(-a.x, -a.y);
+  } else if constexpr (e == 12) {
+    return cmk<T2>(-a.y, a.x);
+  } else if constexpr ((e & 3) == 2) {  // |cos| = |sin| = sqrt(1/2)
+    const R h = (R)0.70710678118654752440;
+    constexpr int sc = (e == 2 || e == 14) ? 1 : -1;  // sign of cos(2 pi e / 16)
+    constexpr int ss = (e == 2 || e == 6) ? 1 : -1;   // sign of sin(2 pi e / 16)
+    const R u = sc > 0 ? a.x : -a.x, v = ss > 0 ? a.y : -a.y;      // c a.x, s a.y (over h)
+    const R u2 = sc > 0 ? a.y : -a.y, v2 = ss > 0 ? a.x : -a.x;    // c a.y, s a.x (over h)
+    return cmk<T2>(h * (u + v), h * (u2 - v2));
+  } else {  // odd e: cos and sin are +-cos(pi/8), +-sin(pi/8)
+    const R C8 = (R)0.92387953251128675613, S8 = (R)0.38268343236508977173;
+    constexpr int q = e & 3;  // 1 or 3
+    constexpr int quad = e >> 2;
+    // angle 2 pi e / 16 = quad pi/2 + q pi/8
+    R c = q == 1 ? C8 : S8, s = q == 1 ? S8 : C8;
+    if constexpr (quad == 1) {
+      const R t = c;
+      c = -s;
+      s = t;
+    } else if constexpr (quad == 2) {
+      c = -c;
+      s = -s;
+    } else if constexpr (quad == 3) {
+      const R t = c;
+      c = s;
+      s = -t;
+    }
+    // a * (c - i s)
+    return cmk<T2>(a.x * c + a.y * s, a.y * c - a.x * s);
+  }
+}
+
+template <typename T2>
+__device__ __forceinline__ void dft2r(T2 &x0, T2 &x1) {
+  const T2 t = x0;
+  x0 = cadd(t, x1);
+  x1 = csub(t, x1);
+}
+template <typename T2>
+__device__ __forceinline__ void dft4r(T2 &x0, T2 &x1, T2 &x2, T2 &x3) {
+  const T2 t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = cmul_negi(csub(x1, x3));
+  x0 = cadd(t0, t2);
+  x2 = csub(t0, t2);
+  x1 = cadd(t1, t3);
+  x3 = csub(t1, t3);
+}
+
+// y = DFT_R(a) for R = 2, 4, 8, 16 (natural order in and out; a is clobbered)
+template <int R, typename T2>
+__device__ __forceinline__ void dft_nat(T2 *a, T2 *y) {
+  if constexpr (R == 2) {
+    dft2r(a[0], a[1]);
+    y[0] = a[0];
+    y[1] = a[1];
+  } else if constexpr (R == 4) {
+    dft4r(a[0], a[1], a[2], a[3]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) y[q] = a[q];
+  } else if constexpr (R == 8) {  // n = 2 n1 + n2, k = k1 + 4 k2
+    dft4r(a[0], a[2], a[4], a[6]);
+    dft4r(a[1], a[3], a[5], a[7]);
+    a[3] = w16<2>(a[3]);
+    a[5] = w16<4>(a[5]);
+    a[7] = w16<6>(a[7]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft2r(a[2 * k1], a[2 * k1 + 1]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) y[q] = a[2 * (q & 3) + (q >> 2)];
+  } else {  // R == 16: n = 4 n1 + n2, k = k1 + 4 k2
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4r(a[n2], a[n2 + 4], a[n2 + 8], a[n2 + 12]);
+    a[5] = w16<1>(a[5]);
+    a[9] = w16<2>(a[9]);
+    a[13] = w16<3>(a[13]);
+    a[6] = w16<2>(a[6]);
+    a[10] = w16<4>(a[10]);
+    a[14] = w16<6>(a[14]);
+    a[7] = w16<3>(a[7]);
+    a[11] = w16<6>(a[11]);
+    a[15] = w16<9>(a[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4r(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) y[q] = a[4 * (q & 3) + (q >> 2)];
+  }
+}
+
+// One DIF pass of radix 2^LR and stride L; ZERO_UPPER: the inputs r >= R/2 are zero (not read).
+template <typename T2, int LR, int L, bool ZERO_UPPER>
+__device__ __forceinline__ void difr_pass(T2 *x, const T2 *tw, int t) {
+  constexpr int R = 1 << LR;
+  const int j = t & (L - 1);
+  const int base = ((t - j) << LR) + j;
+  T2 a[R], y[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) a[r] = (ZERO_UPPER && r >= R / 2) ? cmk<T2>(0, 0) : x[spad(base + r * L)];
+  dft_nat<R>(a, y);
+  if constexpr (L > 1) {
+#pragma unroll
+    for (int q = 1; q < R; ++q) y[q] = cmul(y[q], tw[(q - 1) * L + j]);
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) x[spad(base + brev_bits(q, LR) * L)] = y[q];
+}
+
+// One DIT pass of radix 2^LR and stride L; HALF: only the outputs q < R/2 are stored.
+template <typename T2, int LR, int L, bool HALF>
+__device__ __forceinline__ void ditr_pass(T2 *x, const T2 *tw, int t) {
+  constexpr int R = 1 << LR;
+  const int j = t & (L - 1);
+  const int base = ((t - j) << LR) + j;
+  T2 a[R], b[R], y[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) a[r] = x[spad(base + r * L)];
+  if constexpr (L > 1) {
+#pragma unroll
+    for (int r = 1; r < R; ++r) a[r] = cmul(a[r], tw[(brev_bits(r, LR) - 1) * L + j]);
+  }
+#pragma unroll
+  for (int s = 0; s < R; ++s) b[s] = a[brev_bits(s, LR)];
+  dft_nat<R>(b, y);
+#pragma unroll
+  for (int q = 0; q < (HALF ? R / 2 : R); ++q) x[spad(base + q * L)] = y[q];
+}
+
+// The pass of 2^RB points on L = 1 over a thread's E consecutive elements
+template <typename T2, int E, int RB>
+__device__ __forceinline__ void dif_tail(T2 *v) {  // in registers, DIF: out q of group g -> v[gR + brev(q)]
+  constexpr int R = 1 << RB;
+#pragma unroll
+  for (int g = 0; g < E / R; ++g) {
+    T2 a[R], y[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = v[g * R + r];
+    dft_nat<R>(a, y);
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[g * R + brev_bits(q, RB)] = y[q];
+  }
+}
+template <typename T2, int E, int RB>
+__device__ __forceinline__ void dit_tail(T2 *v) {  // in registers, DIT: bit-reversed group -> natural
+  constexpr int R = 1 << RB;
+#pragma unroll
+  for (int g = 0; g < E / R; ++g) {
+    T2 a[R], y[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) a[s] = v[g * R + brev_bits(s, RB)];
+    dft_nat<R>(a, y);
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[g * R + q] = y[q];
+  }
+}
+
+template <typename T2, int LOGM, int LR, int P, bool ZERO_FIRST>
+__device__ __forceinline__ void difr_passes(T2 *x, const T2 *tw, int t, int last) {
+  if constexpr (P < LOGM / LR) {
+    if (P < last) {
+      difr_pass<T2, LR, ((1 << LOGM) >> (LR * (P + 1))), ZERO_FIRST && P == 0>(x, tw + fftr_tw_off(LOGM, LR, P), t);
+      __syncthreads();
+    }
+    difr_passes<T2, LOGM, LR, P + 1, ZERO_FIRST>(x, tw, t, last);
+  }
+}
+template <typename T2, int LOGM, int LR, int P, bool HALF_LAST>
+__device__ __forceinline__ void ditr_passes(T2 *x, const T2 *tw, int t, int first) {
+  // runs P = first, first - 1, ..., 0 (L ascending)
+  if constexpr (P >= 0) {
+    if (P <= first) {
+      ditr_pass<T2, LR, ((1 << LOGM) >> (LR * (P + 1))), HALF_LAST && P == 0>(x, tw + fftr_tw_off(LOGM, LR, P), t);
+      __syncthreads();
+    }
+    ditr_passes<T2, LOGM, LR, P - 1, HALF_LAST>(x, tw, t, first);
+  }
+}
+
+// Natural order in, bit-reversed order out (slots spad(i)); ends with a block barrier.
+template <typename T2, int LOGM, int LR>
+__device__ void fftr_dif(T2 *x, const T2 *tw, int t) {
+  constexpr int NP = LOGM / LR, RB = LOGM % LR, E = 1 << LR;
+  difr_passes<T2, LOGM, LR, 0, false>(x, tw, t, NP);
+  if constexpr (RB > 0) {
+    T2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = x[spad(E * t + i)];
+    dif_tail<T2, E, RB>(v);
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[spad(E * t + i)] = v[i];
+    __syncthreads();
+  }
+}
+
+// Bit-reversed order in, natural order out; ends with a block barrier.
+template <typename T2, int LOGM, int LR>
+__device__ void fftr_dit(T2 *x, const T2 *tw, int t) {
+  constexpr int NP = LOGM / LR, RB = LOGM % LR, E = 1 << LR;
+  if constexpr (RB > 0) {
+    T2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = x[spad(E * t + i)];
+    dit_tail<T2, E, RB>(v);
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[spad(E * t + i)] = v[i];
+    __syncthreads();
+  }
+  ditr_passes<T2, LOGM, LR, NP - 1, false>(x, tw, t, NP - 1);
+}
+
+// Bluestein core with the conventions of bluestein_conv: x <- FFT_M(conj(FFT_M(x) * bhat)),
+// upper input half zero, lower output half computed.  The middle (last DIF
+// pass, product with bhat in bit-reversed order, conjugation, first DIT pass)
+// runs on each thread's E consecutive slots in registers.
+template <typename T2, int LOGM, int LR>
+__device__ void bluesteinr(T2 *x, const T2 *tw, const T2 *__restrict__ bhat, int t) {
+  constexpr int NP = LOGM / LR, RB = LOGM % LR, E = 1 << LR;
+  constexpr int nfull = RB > 0 ? NP : NP - 1;  // full DIF passes outside the middle
+  difr_passes<T2, LOGM, LR, 0, true>(x, tw, t, nfull);
+  {
+    T2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = x[spad(E * t + i)];
+    dif_tail<T2, E, (RB > 0 ? RB : LR)>(v);
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = cconj(cmul(v[i], bhat[E * t + i]));
+    dit_tail<T2, E, (RB > 0 ? RB : LR)>(v);
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[spad(E * t + i)] = v[i];
+  }
+  __syncthreads();
+  ditr_passes<T2, LOGM, LR, NP - 1, true>(x, tw, t, nfull - 1);
+}
+
 }  // namespace dmwf

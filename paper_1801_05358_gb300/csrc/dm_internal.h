@@ -24,6 +24,7 @@ struct RingDev {
   int side;          // 0 = northern (or equatorial) member, 1 = southern member
   int64_t ph_off;    // offset of e^{-i pi q / n}, q in [0, 2n), in the phase table
   int64_t bh_off;    // offset of the Bluestein kernel spectrum (M entries), -1 if none
+  int64_t ch_off;    // offset of the Bluestein chirp e^{-i pi j^2 / h} (h entries), -1 if none
 };
 
 // Per-ring-pair data for the Legendre stages.
@@ -97,7 +98,13 @@ struct dm_plan {
   dmwf::PairDev *pairs = nullptr;
   double2 *phase = nullptr;     // e^{-i pi q / n} tables
   double2 *bhat = nullptr;      // Bluestein kernel spectra
+  double2 *chirp = nullptr;     // Bluestein chirps, one table per ring radius
+  int64_t ch_total = 0;
   double2 *twid = nullptr;      // stage twiddles: [len - 1 + j] = e^{-i pi j / len}, fft_M_max - 1 entries
+  double2 *twr = nullptr;       // pass tables of the fixed-size transforms, M = 2^9 .. 2^12, radix 8 and 16
+  int twr_off[2][16] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};  // [LR - 3][LOGM]: offset in twr (-1: not built)
+  int twr_words = 0;
+  int ring_lr = 3;              // radix 2^ring_lr of the fixed-size ring transforms (0: generic kernels)
   int *ring_order = nullptr;    // [nrings] ring ids grouped by FFT size class
   std::vector<int> ring_order_h;
   std::vector<dmwf::RingClass> ring_classes;
@@ -139,7 +146,7 @@ struct dm_plan {
   float *s32 = nullptr;         // [B][3][npix] iteration map
   float *w32 = nullptr;         // [B][3][npix]
   float *wd32 = nullptr;        // [B][3][npix]
-  float2 *phase32 = nullptr, *bhat32 = nullptr, *twid32 = nullptr;
+  float2 *phase32 = nullptr, *bhat32 = nullptr, *twid32 = nullptr, *twr32 = nullptr, *chirp32 = nullptr;
   // FP64 anchor of the mixed iteration (iterative refinement):
   //   a = a_hi + e;  FP32 stages act on e only; g_hi = A W (d - Y a_hi) in FP64
   double2 *a_hi = nullptr;      // [B][3][nalm]
@@ -184,7 +191,8 @@ cudaError_t build_noise(dm_plan *p, int b, cudaStream_t st);    // alpha (reduct
 enum RingMode { RING_FWD_MAP = 0, RING_INV_MAP = 1, RING_ITER = 2, RING_INIT = 3 };
 cudaError_t ring_stage(dm_plan *p, int mode, const double *in_map, double *out_map, cudaStream_t st);
 // lanes per block of the ring kernel (1..4) for the given shared-memory words
-int ring_lanes_per_block(size_t word_bytes, int tw_words, int ph_words, int lane_words, int nlanes, int regs);
+int ring_lanes_per_block(size_t word_bytes, int tw_words, int ph_words, int lane_words, int nlanes, int regs,
+                         int nt);
 // public-layout permutations of the ring coefficients
 cudaError_t rc_to_public(dm_plan *p, double2 *pub, cudaStream_t st);
 cudaError_t rc_from_public(dm_plan *p, const double2 *pub, cudaStream_t st);

@@ -69,23 +69,6 @@ __device__ __forceinline__ float2 e_of(const double2 *a, const double2 *ahi, int
   return make_float2((float)v.x, (float)v.y);
 }
 
-__device__ __forceinline__ void tc_setup(uint64_t *mbar, uint32_t *slot, uint32_t ncols) {
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(&mbar[i], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if ((threadIdx.x >> 5) == 0) tmem_alloc(slot, ncols);
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
-}
-
-__device__ __forceinline__ void tc_drain(uint64_t *mbar, int n, int *err) {
-  if (n >= 2) mbar_wait(&mbar[(n - 2) & 1], ((n - 2) >> 1) & 1, err);
-  mbar_wait(&mbar[(n - 1) & 1], ((n - 1) >> 1) & 1, err);
-  fence_after_sync();
-}
-
 __device__ __forceinline__ void tc_teardown(uint32_t tbase, uint32_t ncols) {
   fence_before_sync();
   __syncthreads();
@@ -418,16 +401,27 @@ __device__ __forceinline__ void convert_ana_b(int task, unsigned char *Bbuf, int
   }
 }
 
+// Warp roles: warps 0 .. 7 convert the ring-coefficient operand of each K
+// step into its stage, in ngroups groups of nconv warps that take the steps in
+// turn (every thread of the group arrives on full_b), warp 8
+// bulk-copies the table tiles (full_a, transaction bytes), warp 9 issues the
+// MMAs once both halves of a stage are in and commits them to done, which
+// frees the stage; S stages in a ring.  Warps 0-3 read the accumulators after
+// the single-use barrier fin that the MMA thread commits last.
+constexpr int ANA_THREADS = 320;
+constexpr int ANA_MAX_STAGES = 4;
+
 template <int PART>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_ana_tc(const unsigned char *__restrict__ tab,
-                                                         const int64_t *__restrict__ aoff,
-                                                         const float2 *__restrict__ rc, float2 *__restrict__ out,
-                                                         int lmax, int mmax, int npairs, int64_t nalm, int B,
-                                                         int LT, uint32_t ncols, int *err) {
+__global__ void __launch_bounds__(ANA_THREADS, 1) k_ana_tc(const unsigned char *__restrict__ tab,
+                                                          const int64_t *__restrict__ aoff,
+                                                          const float2 *__restrict__ rc, float2 *__restrict__ out,
+                                                          int lmax, int mmax, int npairs, int64_t nalm, int B,
+                                                          int LT, uint32_t ncols, int S, int *err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ uint64_t mbar[4];
+  __shared__ uint64_t bars[3 * ANA_MAX_STAGES + 1];
   __shared__ uint32_t tslot;
-  uint64_t *done = mbar, *full = mbar + 2;
+  uint64_t *full_a = bars, *full_b = bars + ANA_MAX_STAGES, *done = bars + 2 * ANA_MAX_STAGES;
+  uint64_t *fin = bars + 3 * ANA_MAX_STAGES;  // one phase: every MMA of the CTA has completed
   const int m = blockIdx.z, par = blockIdx.y;
   const int nl = ana_nl(lmax, m, par);
   const int lt0 = blockIdx.x * LT;                                   // first l tile of this CTA
@@ -439,55 +433,76 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_ana_tc(const unsigned char *_
   const int abytes = nA * 2 * TILE_A;
   const int stage = LT * abytes + nA * 2 * tileB;  // A tiles of the LT l tiles, then B
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  tc_setup(mbar, &tslot, ncols);
+  const int ntask = (PART == 0) ? 2 * B : 4 * B;  // converter threads with a row pair
+  const int nconv = (ntask + 31) / 32;            // warps of one converter group (<= 8)
+  // groups of converter warps take the K steps in turn, so that the loads of
+  // several steps are in flight when a group alone would wait on each
+  const int ngroups = max(1, min(S, 8 / nconv));
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full_a[i], 1);
+      mbar_init(&full_b[i], 32 * nconv);
+      mbar_init(&done[i], 1);
+    }
+    mbar_init(fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tslot, ncols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
   const uint32_t tbase = tslot;
   const int64_t base = abase(lmax, m);
   const int nsteps = (npairs + 15) / 16;
-  const unsigned char *tabm = tab + (aoff[2 * m + par] + lt0) * nsteps * (int64_t)abytes;
-  const int64_t tstride = (int64_t)nsteps * abytes;  // next l tile
-  const uint32_t idesc = idesc_bf16(128, NC);
-  auto issue_a = [&](int c, int s) {
-    mbar_expect_tx(&full[s], (uint32_t)(nt * abytes));
-    for (int j = 0; j < nt; ++j)
-      bulk_g2s(sm + s * stage + j * abytes, tabm + j * tstride + (int64_t)c * abytes, (uint32_t)abytes, &full[s]);
-  };
-  if (tid == 0) issue_a(0, 0);
-  const bool has = tid < (PART == 0 ? 2 * B : 4 * B);
-  float2 v[16];
-  if (has) load_ana_b<PART>(tid, rc, m, 0, mmax, npairs, v);
-  for (int c = 0; c < nsteps; ++c) {
-    const int s = c & 1;
-    unsigned char *Abuf = sm + s * stage, *Bbuf = Abuf + LT * abytes;
-    if (c >= 2) mbar_wait(&done[s], ((c - 2) >> 1) & 1, err);
-    if (has) {
-      convert_ana_b<PART>(tid, Bbuf, tileB, par, v);
-      if (c + 1 < nsteps) load_ana_b<PART>(tid, rc, m, c + 1, mmax, npairs, v);
+  if (warp < nconv * ngroups) {
+    const int grp = warp / nconv, task = tid - grp * 32 * nconv;
+    const bool has = task < ntask;
+    float2 v[16];
+    if (has && grp < nsteps) load_ana_b<PART>(task, rc, m, grp, mmax, npairs, v);
+    for (int c = grp; c < nsteps; c += ngroups) {
+      const int s = c % S, k = c / S;
+      if (c >= S) mbar_wait(&done[s], (k - 1) & 1, err);
+      if (has) {
+        convert_ana_b<PART>(task, sm + s * stage + LT * abytes, tileB, par, v);
+        if (c + ngroups < nsteps) load_ana_b<PART>(task, rc, m, c + ngroups, mmax, npairs, v);
+      }
+      fence_proxy_async();  // generic-proxy writes -> tensor-core reads
+      mbar_arrive(&full_b[s]);
     }
-    fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      mbar_wait(&full[s], (c >> 1) & 1, err);
+  } else if (warp == 8 && lane == 0) {
+    const unsigned char *tabm = tab + (aoff[2 * m + par] + lt0) * nsteps * (int64_t)abytes;
+    const int64_t tstride = (int64_t)nsteps * abytes;  // next l tile
+    for (int c = 0; c < nsteps; ++c) {
+      const int s = c % S, k = c / S;
+      if (c >= S) mbar_wait(&done[s], (k - 1) & 1, err);
+      mbar_expect_tx(&full_a[s], (uint32_t)(nt * abytes));
+      for (int j = 0; j < nt; ++j)
+        bulk_g2s(sm + s * stage + j * abytes, tabm + j * tstride + (int64_t)c * abytes, (uint32_t)abytes, &full_a[s]);
+    }
+  } else if (warp == 9 && lane == 0) {
+    const uint32_t idesc = idesc_bf16(128, NC);
+    for (int c = 0; c < nsteps; ++c) {
+      const int s = c % S, k = c / S;
+      mbar_wait(&full_a[s], k & 1, err);
+      mbar_wait(&full_b[s], k & 1, err);
       fence_after_sync();
+      const unsigned char *Abuf = sm + s * stage, *Bbuf = Abuf + LT * abytes;
       const uint32_t acc = c > 0 ? 1u : 0u;
       for (int j = 0; j < nt; ++j) {  // one accumulator of NC columns per l tile, the same B
         const unsigned char *Aj = Abuf + j * abytes;
         const uint32_t dj = tbase + (uint32_t)(j * NC);
-        if (PART == 0) {
-          mma3(dj, Aj, Bbuf, tileB, idesc, acc);
-        } else {
-          mma3(dj, Aj, Bbuf, tileB, idesc, acc);
-          mma3(dj, Aj + 2 * TILE_A, Bbuf + 2 * tileB, tileB, idesc, 1u);
-        }
+        mma3(dj, Aj, Bbuf, tileB, idesc, acc);
+        if (PART == 1) mma3(dj, Aj + 2 * TILE_A, Bbuf + 2 * tileB, tileB, idesc, 1u);
       }
       commit(&done[s]);
-      if (c + 1 < nsteps) {
-        if (c >= 1) mbar_wait(&done[s ^ 1], ((c - 1) >> 1) & 1, err);
-        issue_a(c + 1, s ^ 1);
-      }
     }
+    commit(fin);
   }
-  tc_drain(done, nsteps, err);
   if (warp < 4) {
+    // A stage barrier may be several phases behind a warp that did not
+    // convert; fin completes exactly once.
+    mbar_wait(fin, 0, err);
+    fence_after_sync();
     const int row = warp * 32 + lane;
     const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
     for (int j = 0; j < nt; ++j) {
@@ -523,16 +538,8 @@ static uint32_t pow2_cols(int n) {
   return c;
 }
 
-// smem per CTA, raised when needed so that the CTAs sharing an SM never ask
-// for more tensor memory than its 512 columns
-static size_t tc_smem(int stage_bytes, uint32_t ncols) {
-  size_t s = 2 * (size_t)stage_bytes + 1024;
-  const int per_sm = (int)(512 / ncols);
-  const size_t floor_bytes = (232448 / (per_sm + 1)) + 1024;
-  return s > floor_bytes ? s : floor_bytes;
-}
-
-// the same for NS stages
+// smem per CTA for NS stages, raised when needed so that the CTAs sharing an
+// SM never ask for more tensor memory than its 512 columns
 static size_t tc_smem_n(int stage_bytes, int ns, uint32_t ncols) {
   size_t s = (size_t)ns * stage_bytes + 1024;
   const int per_sm = (int)(512 / ncols);
@@ -649,6 +656,13 @@ static int ana_tiles_per_cta(int NC) {
   return lt < 1 ? 1 : (lt > 4 ? 4 : lt);
 }
 
+// Stages of the analysis ring: as many as fit (2 to 4), and at least the
+// shared memory that keeps the CTAs of an SM within its tensor memory.
+static int ana_stages(int stage_bytes) {
+  const int fit = (int)(((227u << 10) - 1024) / (size_t)stage_bytes);
+  return fit < 2 ? 2 : (fit > ANA_MAX_STAGES ? ANA_MAX_STAGES : fit);
+}
+
 cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st) {
   cudaError_t e = tc_tables(p);
   if (e) return e;
@@ -657,20 +671,24 @@ cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st) {
   {
     const int NC = 2 * B, LT = ana_tiles_per_cta(NC);
     const uint32_t nc = pow2_cols(LT * NC);
-    const size_t sm = tc_smem(LT * 1 * 2 * TILE_A + 1 * 2 * (NC * 32), nc);
+    const int stage = LT * 1 * 2 * TILE_A + 1 * 2 * (NC * 32);
+    const int S = ana_stages(stage);
+    const size_t sm = tc_smem_n(stage, S, nc);
     dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
     cudaFuncSetAttribute(k_ana_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_ana_tc<0><<<g, TC_THREADS, sm, st>>>(p->tc_anaA[0], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
-                                           p->npairs, p->nalm, B, LT, nc, p->tc_err);
+    k_ana_tc<0><<<g, ANA_THREADS, sm, st>>>(p->tc_anaA[0], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
+                                            p->npairs, p->nalm, B, LT, nc, S, p->tc_err);
   }
   {
     const int NC = 4 * B, LT = ana_tiles_per_cta(NC);
     const uint32_t nc = pow2_cols(LT * NC);
-    const size_t sm = tc_smem(LT * 2 * 2 * TILE_A + 2 * 2 * (NC * 32), nc);
+    const int stage = LT * 2 * 2 * TILE_A + 2 * 2 * (NC * 32);
+    const int S = ana_stages(stage);
+    const size_t sm = tc_smem_n(stage, S, nc);
     dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
     cudaFuncSetAttribute(k_ana_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_ana_tc<1><<<g, TC_THREADS, sm, st>>>(p->tc_anaA[1], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
-                                           p->npairs, p->nalm, B, LT, nc, p->tc_err);
+    k_ana_tc<1><<<g, ANA_THREADS, sm, st>>>(p->tc_anaA[1], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
+                                            p->npairs, p->nalm, B, LT, nc, S, p->tc_err);
   }
   return cudaGetLastError();
 }

@@ -70,13 +70,6 @@ __device__ __forceinline__ C fold_one(const C *S, int k, int n, int mmax) {
   return acc;
 }
 
-// Bluestein chirp c_j = e^{-i pi j^2 / h} = e^{-i pi (2 j^2 mod 2n) / n}, n = 2h
-// (32-bit arithmetic: j < h <= 2^15 keeps 2 j^2 below 2^32)
-template <typename C>
-__device__ __forceinline__ C chirp(const C *Tq, int j, int n) {
-  const unsigned jj = (unsigned)j;
-  return phase_q(Tq, (int)((2u * jj * jj) % (2u * (unsigned)n)), n);
-}
 
 // x mod n for 0 <= x, skipping the division in the common case x < n
 __device__ __forceinline__ int mod_small(int x, int n) { return x < n ? x : x % n; }
@@ -116,7 +109,7 @@ __device__ __forceinline__ int bl_zero_end(int M) { return M >= 8 ? (M >> 1) : M
 
 // Output k of ring_dft (k < h)
 template <typename C>
-__device__ __forceinline__ C dft_out(const C *buf, int k, int bluestein, const C *Tq, int n, float invM_f,
+__device__ __forceinline__ C dft_out(const C *buf, int k, int bluestein, const C *__restrict__ chp, float invM_f,
                                      double invM_d) {
   C v = buf[spad(k)];
   if (bluestein) {
@@ -124,13 +117,16 @@ __device__ __forceinline__ C dft_out(const C *buf, int k, int bluestein, const C
     const auto inv = sizeof(v.x) == 4 ? (decltype(v.x))invM_f : (decltype(v.x))invM_d;
     v.x *= inv;
     v.y *= inv;
-    v = cmul(v, chirp(Tq, k, n));
+    v = cmul(v, chp[k]);
   }
   return v;
 }
 
 // R: real type of the FFT and of the iteration maps (double or float); C its
-// complex type.  User maps (in_map, out_user) are always FP64.
+// complex type.  User maps (in_map, out_user) are always FP64.  LR > 0: every
+// ring of the launch has FFT size M = 2^LOGM and a lane is M / 2^LR threads
+// running the fixed-size radix-2^LR transforms (twid then holds their pass
+// tables); LR = 0: any size, blockDim.x threads per lane, radix-2^2 passes.
 // Grid.x walks a list of rings with the same FFT size class; block =
 // (blockDim.x threads per lane) x (blockDim.y lanes).  The lanes of a block are
 // consecutive (RHS, Stokes) pairs of the same ring, so they run the same FFT in
@@ -138,8 +134,8 @@ __device__ __forceinline__ C dft_out(const C *buf, int k, int bluestein, const C
 // memory.  A lane works in place on M + 1 entries: the real-FFT packing and
 // unpacking handle k and h - k in the same thread.  Lanes of finished RHS
 // compute but write nothing.
-template <typename R, typename C, int MODE, bool COMPACT>
-__global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings, const int *__restrict__ order,
+template <typename R, typename C, int MODE, bool COMPACT, int LOGM, int LR>
+__global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) ? 2 : 1) k_ring(const RingDev *__restrict__ rings, const int *__restrict__ order,
                                               const C *__restrict__ phase, const C *__restrict__ bhat,
                                               const C *__restrict__ twid, int tw_words, int ph_words,
                                               int buf_words, int lane_words, int nlanes, C *__restrict__ rc,
@@ -148,9 +144,9 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
                                               double *__restrict__ out_user, R *s_state, const R *__restrict__ w,
                                               const R *__restrict__ wd, double *__restrict__ norms,
                                               const SolveState *__restrict__ state,
-                                              const R *__restrict__ s_anchor) {
+                                              const R *__restrict__ s_anchor, const C *__restrict__ chirps) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ double red[4][16][2];
+  __shared__ double red[16][8][2];  // [lane][warp]: up to 16 lanes of up to 8 warps
   const int r = order[blockIdx.x];
   const int g = threadIdx.y;
   const int L = blockIdx.y * blockDim.y + g;
@@ -160,28 +156,34 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
   if ((MODE == RING_ITER || MODE == RING_INIT) && state != nullptr && valid && state[b].done) live = false;
   if (!__syncthreads_or(live)) return;
   const RingDev Rg = rings[r];
-  const int n = Rg.n, h = Rg.h, M = Rg.M, bl = Rg.bluestein;
-  const int logM = 31 - __clz(M);
+  const int n = Rg.n, h = Rg.h, bl = Rg.bluestein;
+  const int M = LR > 0 ? (1 << LOGM) : Rg.M;
+  const int logM = LR > 0 ? LOGM : 31 - __clz(M);
   // Compact mode (COMPACT, rings too long for the full layout): twiddles
   // and phases are read from global memory (L1-cached) and the ring
   // coefficients are folded straight from global memory; shared memory holds
   // only the lane buffers.
   constexpr bool compact = COMPACT;
+  // Fixed-size kernels fold the coefficients straight from global memory too
+  // (each F_m is read once either way); dropping the staged copy halves the
+  // shared memory of a lane, so more lanes stay resident.
+  constexpr bool staged_S = !COMPACT && LR == 0;
   C *tws_s = reinterpret_cast<C *>(sm_raw);  // stage twiddles (M - 1 used)
   C *Tq_s = tws_s + tw_words;                // quarter phase table (n/2 + 1 used)
   C *buf = Tq_s + ph_words + (size_t)g * lane_words;  // slots spad(0..M)
   C *S = buf + buf_words;                              // mmax + 1 staged coefficients (inverse modes)
   const C *tws = compact ? twid : tws_s;
   const C *Tq = compact ? phase + Rg.ph_off : Tq_s;
-  const int tx = threadIdx.x, nt = blockDim.x;
+  const int tx = threadIdx.x, nt = LR > 0 ? ((1 << LOGM) >> LR) : (int)blockDim.x;
   if (!compact) {
     const int tflat = threadIdx.y * nt + tx, nflat = nt * blockDim.y;
-    for (int i = tflat; i < M - 1; i += nflat) tws_s[i] = twid[i];
+    for (int i = tflat; i < tw_words; i += nflat) tws_s[i] = twid[i];
     const C *ph = phase + Rg.ph_off;
     for (int i = tflat; i <= (n >> 1); i += nflat) Tq_s[i] = ph[i];
   }
   const int64_t moff = ((int64_t)b * 3 + f) * npix + Rg.start;
   const C *bh = bhat + (bl ? Rg.bh_off : 0);
+  const C *chp = chirps + (bl ? Rg.ch_off : 0);  // Bluestein chirp e^{-i pi j^2 / h}, j < h
   const int64_t rbase = ((((int64_t)b * 3 + f) * (mmax + 1)) * npairs + Rg.pair) * 2 + Rg.side;
   const int64_t mstride = (int64_t)npairs * 2;
   if (MODE == RING_ITER && live && tx == 0) {
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
     // Z_k = E_k + i O_k, E_k = C_k + conj(C_{h-k}), O_k = (C_k - conj(C_{h-k})) e^{2 pi i k/n},
     // stored conjugated (forward DFT + conjugation = inverse); one thread per (k, h - k).
     // stage S_m = F_m e^{i m phi0}: batches of independent loads per thread
-    if (!compact) {
+    if (staged_S) {
       constexpr int U = sizeof(R) == 4 ? 8 : 4;
       const int n2 = 2 * n;
       for (int m0 = tx; m0 <= mmax; m0 += U * nt) {
@@ -219,9 +221,9 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
     __syncthreads();
     for (int k = tx; k <= (h >> 1); k += nt) {
       const int k2 = h - k;
-      const C ck = compact ? fold_one_g(rc, Tq, k, n, Rg.shift, mmax, rbase, mstride) : fold_one(S, k, n, mmax);
+      const C ck = !staged_S ? fold_one_g(rc, Tq, k, n, Rg.shift, mmax, rbase, mstride) : fold_one(S, k, n, mmax);
       const C ck2 = (k2 == k) ? ck
-                              : (compact ? fold_one_g(rc, Tq, k2, n, Rg.shift, mmax, rbase, mstride)
+                              : (!staged_S ? fold_one_g(rc, Tq, k2, n, Rg.shift, mmax, rbase, mstride)
                                          : fold_one(S, k2, n, mmax));
       for (int t = 0; t < 2; ++t) {
         const int kk = t ? k2 : k;
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
         Z.x = E.x - O.y;
         Z.y = -(E.y + O.x);
         if (bl)
-          buf[spad(kk)] = cmul(Z, chirp(Tq, kk, n));
+          buf[spad(kk)] = cmul(Z, chp[kk]);
         else
           buf[spad(bitrev(kk, logM))] = Z;
       }
@@ -243,12 +245,19 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
         buf[spad(j)].y = 0;
       }
     __syncthreads();
-    ring_dft(buf, M, bl, bh, tws);
+    if constexpr (LR > 0) {
+      if (bl)
+        bluesteinr<C, LOGM, LR>(buf, tws, bh, tx);
+      else
+        fftr_dit<C, LOGM, LR>(buf, tws, tx);
+    } else {
+      ring_dft(buf, M, bl, bh, tws);
+    }
     // z_j = conj(D_j) = s_{2j} + i s_{2j+1}
     if (MODE == RING_INV_MAP) {
       if (live)
         for (int j = tx; j < h; j += nt) {
-          const C z = dft_out(buf, j, bl, Tq, n, invM_f, invM_d);
+          const C z = dft_out(buf, j, bl, chp, invM_f, invM_d);
           out_user[moff + 2 * j] = (double)z.x;
           out_user[moff + 2 * j + 1] = -(double)z.y;
         }
@@ -286,7 +295,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
       for (int u = 0; u < 2; ++u) {
         const int j = j0 + u * nt;
         if (j >= h) break;
-        const C z = dft_out(buf, j, bl, Tq, n, invM_f, invM_d);
+        const C z = dft_out(buf, j, bl, chp, invM_f, invM_d);
         C s;
         s.x = z.x;
         s.y = -z.y;
@@ -309,17 +318,17 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
           rr.x = 0;
           rr.y = 0;
         }
-        buf[spad(j)] = bl ? cmul(rr, chirp(Tq, j, n)) : rr;
+        buf[spad(j)] = bl ? cmul(rr, chp[j]) : rr;
       }
     }
-    double dd = (double)dd_t, ss = (double)ss_t;
+    // warp sums in the map precision, the sums over warps and rings in FP64
     for (int o = 16; o > 0; o >>= 1) {
-      dd += __shfl_down_sync(0xffffffffu, dd, o);
-      ss += __shfl_down_sync(0xffffffffu, ss, o);
+      dd_t += __shfl_down_sync(0xffffffffu, dd_t, o);
+      ss_t += __shfl_down_sync(0xffffffffu, ss_t, o);
     }
     if ((tx & 31) == 0) {
-      red[g][tx >> 5][0] = dd;
-      red[g][tx >> 5][1] = ss;
+      red[g][tx >> 5][0] = (double)dd_t;
+      red[g][tx >> 5][1] = (double)ss_t;
     }
     __syncthreads();
     if (tx == 0 && live) {
@@ -347,7 +356,7 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
       C v;
       v.x = (R)x0;
       v.y = (R)x1;
-      buf[spad(j)] = bl ? cmul(v, chirp(Tq, j, n)) : v;
+      buf[spad(j)] = bl ? cmul(v, chp[j]) : v;
     }
   }
   if (bl)
@@ -357,10 +366,17 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
     }
   __syncthreads();
   // forward: Z = DFT_h(z); direct rings take natural input to bit-reversed output
-  if (bl)
-    ring_dft(buf, M, 1, bh, tws);
-  else
-    fft_dif(buf, M, tws);
+  if constexpr (LR > 0) {
+    if (bl)
+      bluesteinr<C, LOGM, LR>(buf, tws, bh, tx);
+    else
+      fftr_dif<C, LOGM, LR>(buf, tws, tx);
+  } else {
+    if (bl)
+      ring_dft(buf, M, 1, bh, tws);
+    else
+      fft_dif(buf, M, tws);
+  }
   // X_k = E_k + e^{-2 pi i k/n} O_k, E_k = (Z_k + conj Z_{h-k}) / 2, O_k = (Z_k - conj Z_{h-k}) / 2i,
   // Z_h = Z_0; each thread reads and rewrites the slots of k and h - k; X_h goes to slot M (direct)
   // or slot h (Bluestein).
@@ -369,8 +385,8 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
     const int k2 = h - k;
     const int sk = bl ? k : bitrev(k, logM);
     const int sk2 = (k == 0) ? sk : (bl ? k2 : bitrev(k2, logM));
-    const C zk = dft_out(buf, sk, bl, Tq, n, invM_f, invM_d);
-    const C zk2 = (k == 0) ? zk : dft_out(buf, sk2, bl, Tq, n, invM_f, invM_d);
+    const C zk = dft_out(buf, sk, bl, chp, invM_f, invM_d);
+    const C zk2 = (k == 0) ? zk : dft_out(buf, sk2, bl, chp, invM_f, invM_d);
     for (int t = 0; t < 2; ++t) {
       if (t && k2 == k) break;
       const C a = t ? zk2 : zk, c = cconj(t ? zk : zk2);
@@ -401,13 +417,32 @@ __global__ void __launch_bounds__(512) k_ring(const RingDev *__restrict__ rings,
 
 // Rings are launched by size class: one grid per class so that each gets the
 // shared memory (twiddles, quarter phase table, G lanes of M + 1 entries) it needs.
+// Iteration launches of classes with one FFT size M in [512, 4096] take the
+// fixed-size kernel (LOGM = log2 M, radix 2^ring_lr, M / 2^ring_lr threads
+// per lane) unless the plan's ring_lr is 0.
+template <typename R, typename C, int MODE, int LR>
+static void pick_fixed(int logm, void (*&kern)(const RingDev *, const int *, const C *, const C *, const C *, int,
+                                               int, int, int, int, C *, int, int, int64_t, int, const double *,
+                                               double *, R *, const R *, const R *, double *, const SolveState *,
+                                               const R *, const C *)) {
+  switch (logm) {
+    case 9: kern = k_ring<R, C, MODE, false, 9, LR>; break;
+    case 10: kern = k_ring<R, C, MODE, false, 10, LR>; break;
+    case 11: kern = k_ring<R, C, MODE, false, 11, LR>; break;
+    default: kern = k_ring<R, C, MODE, false, 12, LR>; break;
+  }
+}
+
 template <typename R, typename C, int MODE>
-static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const C *twid, C *rc,
+static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const C *chirps, const C *twid, C *rc,
                                const double *in_map, double *out_user, R *s_state, const R *w, const R *wd,
-                               cudaStream_t st, const R *s_anchor = nullptr) {
+                               cudaStream_t st, const R *s_anchor = nullptr, const C *twr = nullptr) {
+  using Kern = void (*)(const RingDev *, const int *, const C *, const C *, const C *, int, int, int, int, int, C *,
+                        int, int, int64_t, int, const double *, double *, R *, const R *, const R *, double *,
+                        const SolveState *, const R *, const C *);
   const int nlanes = 3 * p->batch;
   const SolveState *stp = (MODE == RING_ITER || MODE == RING_INIT) ? p->state : nullptr;
-  const int T = 128;
+  const int lr = p->ring_lr;
   for (const RingClass &rc_cls : p->ring_classes) {
     int tw_words = std::max(1, rc_cls.M - 1);
     int ph_words = rc_cls.n / 2 + 1;
@@ -420,37 +455,58 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
       if (sizeof(C) * (size_t)lane_words > (227u << 10)) return cudaErrorInvalidValue;
     }
     const bool compact = (tw_words == 0);
-    auto kern = compact ? k_ring<R, C, MODE, true> : k_ring<R, C, MODE, false>;
+    const int logm = 31 - __builtin_clz((unsigned)rc_cls.M);
+    const bool fixed = MODE == RING_ITER && !compact && twr != nullptr && (lr == 3 || lr == 4) &&
+                       rc_cls.M == (1 << logm) && logm >= 9 && logm <= 12 && p->twr_off[lr - 3][logm] >= 0;
+    Kern kern = compact ? k_ring<R, C, MODE, true, 0, 0> : k_ring<R, C, MODE, false, 0, 0>;
+    int T = 128;
+    const C *tws = twid;
+    if constexpr (MODE == RING_ITER) {
+      if (fixed) {
+        if (lr == 3)
+          pick_fixed<R, C, MODE, 3>(logm, kern);
+        else
+          pick_fixed<R, C, MODE, 4>(logm, kern);
+        T = rc_cls.M >> lr;
+        tw_words = fftr_tw_words(logm, lr);
+        tws = twr + p->twr_off[lr - 3][logm];
+        lane_words = buf_words;  // no staged coefficients
+      }
+    }
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
-    int G = ring_lanes_per_block(sizeof(C), tw_words, ph_words, lane_words, nlanes, fa.numRegs);
+    int G = ring_lanes_per_block(sizeof(C), tw_words, ph_words, lane_words, nlanes, fa.numRegs, T);
     const size_t smem = sizeof(C) * ((size_t)tw_words + ph_words + (size_t)G * lane_words);
     dim3 grid(rc_cls.count, (nlanes + G - 1) / G);
     dim3 block(T, G);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, block, smem, st>>>(p->rings, p->ring_order + rc_cls.off, phase, bhat, twid, tw_words, ph_words,
+    kern<<<grid, block, smem, st>>>(p->rings, p->ring_order + rc_cls.off, phase, bhat, tws, tw_words, ph_words,
                                     buf_words, lane_words, nlanes, rc, p->mmax, p->npairs, p->npix, p->nrings, in_map,
-                                    out_user, s_state, w, wd, p->norms, stp, s_anchor);
+                                    out_user, s_state, w, wd, p->norms, stp, s_anchor, chirps);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-// Lanes per block: the G in 1..4 that keeps the most lanes resident on an SM
-// (228 KB of shared memory with 1 KB reserved per block, 2048 threads, 64 K
-// registers allocated per warp in units of 256), ties to the larger G.
-int ring_lanes_per_block(size_t word_bytes, int tw_words, int ph_words, int lane_words, int nlanes, int regs) {
+// Lanes per block: the G that keeps the most lanes resident on an SM (228 KB
+// of shared memory with 1 KB reserved per block, 2048 threads, 64 K registers
+// allocated per warp in units of 256), with G x nt <= 512 threads and G <= 16
+// (the kernel's reduction array), ties to the larger G.
+int ring_lanes_per_block(size_t word_bytes, int tw_words, int ph_words, int lane_words, int nlanes, int regs,
+                         int nt) {
   int best = 1;
   long best_lanes = -1;
-  for (int G = 1; G <= 4; ++G) {
+  const int warps = (nt + 31) / 32;
+  for (int G = 1; G <= 16 && G * nt <= 512; ++G) {
     const size_t smem = word_bytes * ((size_t)tw_words + ph_words + (size_t)G * lane_words);
     if (smem > (227u << 10)) break;
     long blocks = (long)((228u << 10) / (smem + 1024));
-    blocks = std::min<long>(blocks, 2048 / (128 * G));
+    blocks = std::min<long>(blocks, 2048 / (nt * G));
+    blocks = std::min<long>(blocks, 32);
     const long warp_regs = ((long)std::max(regs, 1) * 32 + 255) / 256 * 256;
-    blocks = std::min<long>(blocks, 65536 / (warp_regs * 4 * G));
+    blocks = std::min<long>(blocks, 65536 / (warp_regs * warps * G));
     const long lanes = blocks * G;
     if (lanes >= best_lanes) {
       best_lanes = lanes;
@@ -466,32 +522,32 @@ cudaError_t ring_stage(dm_plan *p, int mode, const double *in_map, double *out_m
   if (p->prec == DM_FP64) {
     switch (mode) {
       case RING_FWD_MAP:
-        return launch_ring<double, double2, RING_FWD_MAP>(p, p->phase, p->bhat, p->twid, p->rc, in_map, nullptr,
+        return launch_ring<double, double2, RING_FWD_MAP>(p, p->phase, p->bhat, p->chirp, p->twid, p->rc, in_map, nullptr,
                                                           nullptr, p->w, p->wd, st);
       case RING_INV_MAP:
-        return launch_ring<double, double2, RING_INV_MAP>(p, p->phase, p->bhat, p->twid, p->rc, nullptr, out_map,
+        return launch_ring<double, double2, RING_INV_MAP>(p, p->phase, p->bhat, p->chirp, p->twid, p->rc, nullptr, out_map,
                                                           nullptr, p->w, p->wd, st);
       case RING_ITER:
-        return launch_ring<double, double2, RING_ITER>(p, p->phase, p->bhat, p->twid, p->rc, nullptr, nullptr,
-                                                       out_map, p->w, p->wd, st);
+        return launch_ring<double, double2, RING_ITER>(p, p->phase, p->bhat, p->chirp, p->twid, p->rc, nullptr, nullptr,
+                                                       out_map, p->w, p->wd, st, nullptr, p->twr);
       case RING_INIT:
-        return launch_ring<double, double2, RING_INIT>(p, p->phase, p->bhat, p->twid, p->rc, in_map, nullptr,
+        return launch_ring<double, double2, RING_INIT>(p, p->phase, p->bhat, p->chirp, p->twid, p->rc, in_map, nullptr,
                                                        nullptr, p->w, p->wd, st);
     }
   } else {
     switch (mode) {
       case RING_FWD_MAP:
-        return launch_ring<float, float2, RING_FWD_MAP>(p, p->phase32, p->bhat32, p->twid32, p->rc32, in_map,
+        return launch_ring<float, float2, RING_FWD_MAP>(p, p->phase32, p->bhat32, p->chirp32, p->twid32, p->rc32, in_map,
                                                         nullptr, nullptr, p->w32, p->wd32, st);
       case RING_INV_MAP:
-        return launch_ring<float, float2, RING_INV_MAP>(p, p->phase32, p->bhat32, p->twid32, p->rc32, nullptr,
+        return launch_ring<float, float2, RING_INV_MAP>(p, p->phase32, p->bhat32, p->chirp32, p->twid32, p->rc32, nullptr,
                                                         out_map, nullptr, p->w32, p->wd32, st);
       case RING_ITER:
-        return launch_ring<float, float2, RING_ITER>(p, p->phase32, p->bhat32, p->twid32, p->rc32, nullptr,
+        return launch_ring<float, float2, RING_ITER>(p, p->phase32, p->bhat32, p->chirp32, p->twid32, p->rc32, nullptr,
                                                      nullptr, p->s32, p->w32, p->wd32, st,
-                                                     p->anchor_active ? p->shi32 : nullptr);
+                                                     p->anchor_active ? p->shi32 : nullptr, p->twr32);
       case RING_INIT:
-        return launch_ring<float, float2, RING_INIT>(p, p->phase32, p->bhat32, p->twid32, p->rc32, in_map,
+        return launch_ring<float, float2, RING_INIT>(p, p->phase32, p->bhat32, p->chirp32, p->twid32, p->rc32, in_map,
                                                      nullptr, nullptr, p->w32, p->wd32, st);
     }
   }

@@ -54,6 +54,38 @@ __global__ void k_twiddle(double2 *tw, int Mtab) {
   tw[i] = make_double2(c, s);
 }
 
+// Bluestein chirp of one ring radius: c_j = e^{-i pi j^2 / h}, j < h, with the
+// exponent reduced exactly: j^2 mod 2h (j < h <= 2^15).
+__global__ void k_chirp(const RingDev *rings, const int *ring_ids, double2 *chirp) {
+  const RingDev R = rings[ring_ids[blockIdx.x]];
+  for (int j = threadIdx.x; j < R.h; j += blockDim.x) {
+    const int k = (int)(((int64_t)j * j) % (2 * R.h));
+    double s, c;
+    sincospi(-(double)k / (double)R.h, &s, &c);
+    chirp[R.ch_off + j] = make_double2(c, s);
+  }
+}
+
+// Pass tables of the fixed-size transforms of M = 2^LOGM and radix R = 2^LR
+// (dm_fft.cuh): entry off(P) + (q - 1) L + j = e^{-2 pi i j q / (R L)} for the
+// DIF pass P of stride L = M / R^(P + 1) > 1, q = 1..R-1, j < L.
+__global__ void k_twr(double2 *tw, int LOGM, int LR) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= fftr_tw_words(LOGM, LR)) return;
+  const int R = 1 << LR;
+  for (int P = 0; P < LOGM / LR; ++P) {
+    const int o = fftr_tw_off(LOGM, LR, P), L = (1 << LOGM) >> (LR * (P + 1));
+    if (L > 1 && i < o + (R - 1) * L) {
+      const int q = (i - o) / L + 1, j = (i - o) % L;
+      const int k = (j * q) % (R * L);
+      double s, c;
+      sincospi(-2.0 * (double)k / (double)(R * L), &s, &c);
+      tw[i] = make_double2(c, s);
+      return;
+    }
+  }
+}
+
 // Bluestein kernel spectrum for one ring length: FFT_M of b_j = e^{+i pi j^2/h}
 // placed at j and M - j (|j| < h), zero elsewhere, stored in bit-reversed order
 // (the order in which the ring kernel's DIF transform leaves its data).
@@ -315,14 +347,15 @@ cudaError_t build_tables(dm_plan *p) {
     int rad = R.n / 4;
     R.ph_off = 4LL * rad * (rad - 1);
     R.bh_off = -1;
+    R.ch_off = -1;
     Mmax = R.M > Mmax ? R.M : Mmax;
     p->rings_h[r] = R;
   }
   p->fft_M_max = Mmax < 2 ? 2 : Mmax;
   // Bluestein spectra: one per distinct ring radius (north and south share)
   std::vector<int> bl_ring;  // representative ring per radius needing bluestein
-  std::vector<int64_t> bl_off_by_rad(ns + 1, -1);
-  int64_t bh_total = 0;
+  std::vector<int64_t> bl_off_by_rad(ns + 1, -1), ch_off_by_rad(ns + 1, -1);
+  int64_t bh_total = 0, ch_total = 0;
   for (int r = 0; r < p->nrings; ++r) {
     RingDev &R = p->rings_h[r];
     if (!R.bluestein) continue;
@@ -330,9 +363,12 @@ cudaError_t build_tables(dm_plan *p) {
     if (bl_off_by_rad[rad] < 0) {
       bl_off_by_rad[rad] = bh_total;
       bh_total += R.M;
+      ch_off_by_rad[rad] = ch_total;
+      ch_total += R.h;
       bl_ring.push_back(r);
     }
     R.bh_off = bl_off_by_rad[rad];
+    R.ch_off = ch_off_by_rad[rad];
   }
   // Size classes of the ring kernel: rings sorted by FFT size M (largest first),
   // one class per M, the rings with M <= 256 together.
@@ -365,6 +401,9 @@ cudaError_t build_tables(dm_plan *p) {
   if ((e = cudaMalloc(&p->twid, sizeof(double2) * (p->fft_M_max - 1)))) return e;
   if ((e = cudaMalloc(&p->bhat, sizeof(double2) * (bh_total > 0 ? bh_total : 1)))) return e;
   p->bh_total = bh_total;
+  if ((e = cudaMalloc(&p->chirp, sizeof(double2) * (ch_total > 0 ? ch_total : 1)))) return e;
+  p->ch_total = ch_total;
+  p->bytes += sizeof(double2) * (ch_total > 0 ? ch_total : 1);
   p->ph_total = (int64_t)ph_n;
   if ((e = cudaMalloc(&p->rec, sizeof(RecCoef) * (p->nalm + 1)))) return e;
   size_t nseed = (size_t)(p->mmax + 1) * p->npairs;
@@ -382,6 +421,25 @@ cudaError_t build_tables(dm_plan *p) {
   k_pairs<<<(p->npairs + 127) / 128, 128>>>(p->pairs, ns, p->npairs);
   k_phase<<<dim3(8, ns), 256>>>(p->phase, ns);
   k_twiddle<<<(p->fft_M_max - 1 + 255) / 256, 256>>>(p->twid, p->fft_M_max);
+  {  // pass tables of the fixed-size transforms for the sizes the ring classes use
+    int total = 0;
+    for (int r = 0; r < 2; ++r)
+      for (int k = 0; k < 16; ++k) p->twr_off[r][k] = -1;
+    for (const RingClass &c : p->ring_classes)
+      for (int k = 9; k <= 12; ++k)
+        if (c.M == (1 << k) && p->twr_off[0][k] < 0)
+          for (int lr = 3; lr <= 4; ++lr) {
+            p->twr_off[lr - 3][k] = total;
+            total += fftr_tw_words(k, lr);
+          }
+    if ((e = cudaMalloc(&p->twr, sizeof(double2) * (total > 0 ? total : 1)))) return e;
+    p->twr_words = total;
+    p->bytes += sizeof(double2) * (total > 0 ? total : 1);
+    for (int lr = 3; lr <= 4; ++lr)
+      for (int k = 9; k <= 12; ++k)
+        if (p->twr_off[lr - 3][k] >= 0)
+          k_twr<<<(fftr_tw_words(k, lr) + 255) / 256, 256>>>(p->twr + p->twr_off[lr - 3][k], k, lr);
+  }
   if (!bl_ring.empty()) {
     int *ids;
     if ((e = cudaMalloc(&ids, sizeof(int) * bl_ring.size()))) return e;
@@ -389,6 +447,7 @@ cudaError_t build_tables(dm_plan *p) {
     size_t smem = sizeof(double2) * (p->fft_M_max + p->fft_M_max / 32 + 1);  // slots spad(0..M-1)
     cudaFuncSetAttribute(k_bhat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_bhat<<<(unsigned)bl_ring.size(), 256, smem>>>(p->rings, ids, p->phase, p->bhat, p->twid);
+    k_chirp<<<(unsigned)bl_ring.size(), 256>>>(p->rings, ids, p->chirp);
     e = cudaDeviceSynchronize();
     cudaFree(ids);
     if (e) return e;
@@ -421,7 +480,9 @@ cudaError_t setup_fp32(dm_plan *p) {
   };
   if ((e = al(&p->phase32, p->ph_total))) return e;
   if ((e = al(&p->bhat32, p->bh_total))) return e;
+  if ((e = al(&p->chirp32, p->ch_total))) return e;
   if ((e = al(&p->twid32, p->fft_M_max - 1))) return e;
+  if ((e = al(&p->twr32, p->twr_words))) return e;
   if ((e = al(&p->ptab, (size_t)3 * p->nalm * p->npairs))) return e;
   if ((e = al(&p->ptab_lo, (size_t)3 * p->nalm * p->npairs))) return e;
   if ((e = al(&p->rc32, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return e;
@@ -440,7 +501,9 @@ cudaError_t setup_fp32(dm_plan *p) {
   cudaMemset(p->rc32, 0, sizeof(float2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
   k_d2f2<<<512, 256>>>(p->phase, p->phase32, p->ph_total);
   if (p->bh_total > 0) k_d2f2<<<512, 256>>>(p->bhat, p->bhat32, p->bh_total);
+  if (p->ch_total > 0) k_d2f2<<<512, 256>>>(p->chirp, p->chirp32, p->ch_total);
   k_d2f2<<<64, 256>>>(p->twid, p->twid32, p->fft_M_max - 1);
+  if (p->twr_words > 0) k_d2f2<<<64, 256>>>(p->twr, p->twr32, p->twr_words);
   if ((e = gen_tables32(p))) return e;
   return cudaDeviceSynchronize();
 }

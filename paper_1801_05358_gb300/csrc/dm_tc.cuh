@@ -82,6 +82,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t phase, int *e
   return false;
 }
 
+// Plain arrival of this thread on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
 // Arrive on an mbarrier (count 1) and add bytes to the transaction count of its current phase.
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)

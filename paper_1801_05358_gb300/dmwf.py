@@ -26,7 +26,7 @@ EXPORTS = [
     "dm_ring_fft_inverse", "dm_legendre_synthesis", "dm_legendre_analysis", "dm_apply_filter", "dm_noise_info",
     "dm_profile_enable", "dm_profile_read", "dm_measure_alu_peaks", "dm_solve_begin", "dm_solve_iterate",
     "dm_solve_end", "dm_set_refinement", "dm_set_noise_mask_rhs", "dm_server_create", "dm_serve_submit",
-    "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores",
+    "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores", "dm_set_ring_radix",
     "dm_set_anchor_precision",
     "dm_legendre_analysis_noalloc",
 ]
@@ -263,6 +263,10 @@ class Plan:
 
     def set_tensor_cores(self, on=True):
         self._check(lib().dm_set_tensor_cores(self.h, 1 if on else 0))
+
+    def set_ring_radix(self, lr):
+        """Fixed-size ring transforms of radix 2^lr (3 or 4), or 0 for the generic kernels."""
+        self._check(lib().dm_set_ring_radix(self.h, int(lr)))
 
     def set_refinement(self, anchor_every):
         self._check(lib().dm_set_refinement(self.h, int(anchor_every)))
