@@ -254,6 +254,13 @@ __device__ void bluestein_conv(T2 *x, int M, const T2 *tws, const T2 *__restrict
 // same bit-reversed order), so the families are interchangeable.
 // Twiddles of the pass with stride L > 1: tw[off(L) + (q - 1) L + j] = W_{RL}^{jq}
 // (q = 1..R-1, j < L), tables of the passes in DIF order (fftr_tw_words entries).
+// Element i of a buffer lives at slot sslot(i): the low four bits are XORed
+// with bits 4-7 and 8-11, which spreads every access pattern of these kernels
+// (passes of any stride, a thread's consecutive elements, bit-reversed and
+// natural runs of consecutive indices) evenly over the 16 eight-byte bank
+// pairs; a buffer of M elements takes M slots (M + 16 when slot M is used).
+
+__device__ __forceinline__ int sslot(int i) { return (i & ~15) | ((i ^ (i >> 4) ^ (i >> 8)) & 15); }
 
 __host__ __device__ constexpr int brev_bits(int x, int bits) {
   int r = 0;
@@ -386,14 +393,14 @@ __device__ __forceinline__ void difr_pass(T2 *x, const T2 *tw, int t) {
   const int base = ((t - j) << LR) + j;
   T2 a[R], y[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) a[r] = (ZERO_UPPER && r >= R / 2) ? cmk<T2>(0, 0) : x[spad(base + r * L)];
+  for (int r = 0; r < R; ++r) a[r] = (ZERO_UPPER && r >= R / 2) ? cmk<T2>(0, 0) : x[sslot(base + r * L)];
   dft_nat<R>(a, y);
   if constexpr (L > 1) {
 #pragma unroll
     for (int q = 1; q < R; ++q) y[q] = cmul(y[q], tw[(q - 1) * L + j]);
   }
 #pragma unroll
-  for (int q = 0; q < R; ++q) x[spad(base + brev_bits(q, LR) * L)] = y[q];
+  for (int q = 0; q < R; ++q) x[sslot(base + brev_bits(q, LR) * L)] = y[q];
 }
 
 // One DIT pass of radix 2^LR and stride L; HALF: only the outputs q < R/2 are stored.
@@ -404,7 +411,7 @@ __device__ __forceinline__ void ditr_pass(T2 *x, const T2 *tw, int t) {
   const int base = ((t - j) << LR) + j;
   T2 a[R], b[R], y[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) a[r] = x[spad(base + r * L)];
+  for (int r = 0; r < R; ++r) a[r] = x[sslot(base + r * L)];
   if constexpr (L > 1) {
 #pragma unroll
     for (int r = 1; r < R; ++r) a[r] = cmul(a[r], tw[(brev_bits(r, LR) - 1) * L + j]);
@@ -413,7 +420,7 @@ __device__ __forceinline__ void ditr_pass(T2 *x, const T2 *tw, int t) {
   for (int s = 0; s < R; ++s) b[s] = a[brev_bits(s, LR)];
   dft_nat<R>(b, y);
 #pragma unroll
-  for (int q = 0; q < (HALF ? R / 2 : R); ++q) x[spad(base + q * L)] = y[q];
+  for (int q = 0; q < (HALF ? R / 2 : R); ++q) x[sslot(base + q * L)] = y[q];
 }
 
 // The pass of 2^RB points on L = 1 over a thread's E consecutive elements
@@ -466,7 +473,7 @@ __device__ __forceinline__ void ditr_passes(T2 *x, const T2 *tw, int t, int firs
   }
 }
 
-// Natural order in, bit-reversed order out (slots spad(i)); ends with a block barrier.
+// Natural order in, bit-reversed order out (slots sslot(i)); ends with a block barrier.
 template <typename T2, int LOGM, int LR>
 __device__ void fftr_dif(T2 *x, const T2 *tw, int t) {
   constexpr int NP = LOGM / LR, RB = LOGM % LR, E = 1 << LR;
@@ -474,10 +481,10 @@ __device__ void fftr_dif(T2 *x, const T2 *tw, int t) {
   if constexpr (RB > 0) {
     T2 v[E];
 #pragma unroll
-    for (int i = 0; i < E; ++i) v[i] = x[spad(E * t + i)];
+    for (int i = 0; i < E; ++i) v[i] = x[sslot(E * t + i)];
     dif_tail<T2, E, RB>(v);
 #pragma unroll
-    for (int i = 0; i < E; ++i) x[spad(E * t + i)] = v[i];
+    for (int i = 0; i < E; ++i) x[sslot(E * t + i)] = v[i];
     __syncthreads();
   }
 }
@@ -489,10 +496,10 @@ __device__ void fftr_dit(T2 *x, const T2 *tw, int t) {
   if constexpr (RB > 0) {
     T2 v[E];
 #pragma unroll
-    for (int i = 0; i < E; ++i) v[i] = x[spad(E * t + i)];
+    for (int i = 0; i < E; ++i) v[i] = x[sslot(E * t + i)];
     dit_tail<T2, E, RB>(v);
 #pragma unroll
-    for (int i = 0; i < E; ++i) x[spad(E * t + i)] = v[i];
+    for (int i = 0; i < E; ++i) x[sslot(E * t + i)] = v[i];
     __syncthreads();
   }
   ditr_passes<T2, LOGM, LR, NP - 1, false>(x, tw, t, NP - 1);
@@ -510,13 +517,13 @@ __device__ void bluesteinr(T2 *x, const T2 *tw, const T2 *__restrict__ bhat, int
   {
     T2 v[E];
 #pragma unroll
-    for (int i = 0; i < E; ++i) v[i] = x[spad(E * t + i)];
+    for (int i = 0; i < E; ++i) v[i] = x[sslot(E * t + i)];
     dif_tail<T2, E, (RB > 0 ? RB : LR)>(v);
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = cconj(cmul(v[i], bhat[E * t + i]));
     dit_tail<T2, E, (RB > 0 ? RB : LR)>(v);
 #pragma unroll
-    for (int i = 0; i < E; ++i) x[spad(E * t + i)] = v[i];
+    for (int i = 0; i < E; ++i) x[sslot(E * t + i)] = v[i];
   }
   __syncthreads();
   ditr_passes<T2, LOGM, LR, NP - 1, true>(x, tw, t, nfull - 1);

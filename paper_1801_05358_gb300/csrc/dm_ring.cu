@@ -108,10 +108,15 @@ __device__ __forceinline__ void ring_dft(C *buf, int M, int bluestein, const C *
 __device__ __forceinline__ int bl_zero_end(int M) { return M >= 8 ? (M >> 1) : M; }
 
 // Output k of ring_dft (k < h)
-template <typename C>
+// slot of element i of a lane buffer: padded (generic kernels) or swizzled
+// (fixed-size kernels)
+template <bool SW>
+__device__ __forceinline__ int lslot(int i) { return SW ? sslot(i) : spad(i); }
+
+template <bool SW, typename C>
 __device__ __forceinline__ C dft_out(const C *buf, int k, int bluestein, const C *__restrict__ chp, float invM_f,
                                      double invM_d) {
-  C v = buf[spad(k)];
+  C v = buf[lslot<SW>(k)];
   if (bluestein) {
     v = cconj(v);
     const auto inv = sizeof(v.x) == 4 ? (decltype(v.x))invM_f : (decltype(v.x))invM_d;
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
   constexpr bool staged_S = !COMPACT && LR == 0;
   C *tws_s = reinterpret_cast<C *>(sm_raw);  // stage twiddles (M - 1 used)
   C *Tq_s = tws_s + tw_words;                // quarter phase table (n/2 + 1 used)
-  C *buf = Tq_s + ph_words + (size_t)g * lane_words;  // slots spad(0..M)
+  C *buf = Tq_s + ph_words + (size_t)g * lane_words;  // slots lslot(0..M)
   C *S = buf + buf_words;                              // mmax + 1 staged coefficients (inverse modes)
   const C *tws = compact ? twid : tws_s;
   const C *Tq = compact ? phase + Rg.ph_off : Tq_s;
@@ -234,15 +239,15 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
         Z.x = E.x - O.y;
         Z.y = -(E.y + O.x);
         if (bl)
-          buf[spad(kk)] = cmul(Z, chp[kk]);
+          buf[lslot<(LR > 0)>(kk)] = cmul(Z, chp[kk]);
         else
-          buf[spad(bitrev(kk, logM))] = Z;
+          buf[lslot<(LR > 0)>(bitrev(kk, logM))] = Z;
       }
     }
     if (bl)
       for (int j = h + tx; j < bl_zero_end(M); j += nt) {
-        buf[spad(j)].x = 0;
-        buf[spad(j)].y = 0;
+        buf[lslot<(LR > 0)>(j)].x = 0;
+        buf[lslot<(LR > 0)>(j)].y = 0;
       }
     __syncthreads();
     if constexpr (LR > 0) {
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
     if (MODE == RING_INV_MAP) {
       if (live)
         for (int j = tx; j < h; j += nt) {
-          const C z = dft_out(buf, j, bl, chp, invM_f, invM_d);
+          const C z = dft_out<(LR > 0)>(buf, j, bl, chp, invM_f, invM_d);
           out_user[moff + 2 * j] = (double)z.x;
           out_user[moff + 2 * j + 1] = -(double)z.y;
         }
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
       for (int u = 0; u < 2; ++u) {
         const int j = j0 + u * nt;
         if (j >= h) break;
-        const C z = dft_out(buf, j, bl, chp, invM_f, invM_d);
+        const C z = dft_out<(LR > 0)>(buf, j, bl, chp, invM_f, invM_d);
         C s;
         s.x = z.x;
         s.y = -z.y;
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
           rr.x = 0;
           rr.y = 0;
         }
-        buf[spad(j)] = bl ? cmul(rr, chp[j]) : rr;
+        buf[lslot<(LR > 0)>(j)] = bl ? cmul(rr, chp[j]) : rr;
       }
     }
     // warp sums in the map precision, the sums over warps and rings in FP64
@@ -356,13 +361,13 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
       C v;
       v.x = (R)x0;
       v.y = (R)x1;
-      buf[spad(j)] = bl ? cmul(v, chp[j]) : v;
+      buf[lslot<(LR > 0)>(j)] = bl ? cmul(v, chp[j]) : v;
     }
   }
   if (bl)
     for (int j = h + tx; j < bl_zero_end(M); j += nt) {
-      buf[spad(j)].x = 0;
-      buf[spad(j)].y = 0;
+      buf[lslot<(LR > 0)>(j)].x = 0;
+      buf[lslot<(LR > 0)>(j)].y = 0;
     }
   __syncthreads();
   // forward: Z = DFT_h(z); direct rings take natural input to bit-reversed output
@@ -385,8 +390,8 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
     const int k2 = h - k;
     const int sk = bl ? k : bitrev(k, logM);
     const int sk2 = (k == 0) ? sk : (bl ? k2 : bitrev(k2, logM));
-    const C zk = dft_out(buf, sk, bl, chp, invM_f, invM_d);
-    const C zk2 = (k == 0) ? zk : dft_out(buf, sk2, bl, chp, invM_f, invM_d);
+    const C zk = dft_out<(LR > 0)>(buf, sk, bl, chp, invM_f, invM_d);
+    const C zk2 = (k == 0) ? zk : dft_out<(LR > 0)>(buf, sk2, bl, chp, invM_f, invM_d);
     for (int t = 0; t < 2; ++t) {
       if (t && k2 == k) break;
       const C a = t ? zk2 : zk, c = cconj(t ? zk : zk2);
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
       O.y = -half * D.x;
       const C X = cadd(E, cmul(O, phase_q(Tq, 2 * kk, n)));
       const int slot = t ? ((k == 0) ? (bl ? h : M) : sk2) : sk;
-      buf[spad(slot)] = X;
+      buf[lslot<(LR > 0)>(slot)] = X;
     }
   }
   __syncthreads();
@@ -409,7 +414,7 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
     const int q = mod_small(m, n);
     const int qq = (q <= h) ? q : n - q;
     const int slot = bl ? qq : (qq == h ? M : bitrev(qq, logM));
-    C X = buf[spad(slot)];
+    C X = buf[lslot<(LR > 0)>(slot)];
     if (q > h) X = cconj(X);
     rc[rbase + (int64_t)m * mstride] = cmul(X, phase_q(Tq, mod_small(m * Rg.shift, n2), n));
   }
@@ -446,7 +451,7 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
   for (const RingClass &rc_cls : p->ring_classes) {
     int tw_words = std::max(1, rc_cls.M - 1);
     int ph_words = rc_cls.n / 2 + 1;
-    const int buf_words = rc_cls.M + rc_cls.M / 32 + 1;  // slots spad(0..M)
+    int buf_words = rc_cls.M + rc_cls.M / 32 + 1;  // slots spad(0..M)
     const bool staged = (MODE == RING_ITER || MODE == RING_INV_MAP);
     int lane_words = buf_words + (staged ? p->mmax + 1 : 0);
     if (sizeof(C) * ((size_t)tw_words + ph_words + lane_words) > (227u << 10)) {  // compact mode
@@ -470,7 +475,7 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
         T = rc_cls.M >> lr;
         tw_words = fftr_tw_words(logm, lr);
         tws = twr + p->twr_off[lr - 3][logm];
-        lane_words = buf_words;  // no staged coefficients
+        lane_words = buf_words = rc_cls.M + 16;  // swizzled slots 0..M, no staged coefficients
       }
     }
     cudaFuncAttributes fa;
