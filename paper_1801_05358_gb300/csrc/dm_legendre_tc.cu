@@ -219,7 +219,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_syn_b(unsigned char *__restrict_
 constexpr int TC_MAX_STAGES = 8;
 
 // Both operands arrive by bulk copy: thread 0 keeps NS stages in flight and
-// issues the MMAs; the four warps read the accumulators out at the end.
+// issues the MMAs; the four warps read the accumulators out at the end.  A
+// stage holds one unit of work: a whole K step for spin 0, and for spin 2 the
+// half of a K step that feeds one parity accumulator (lam+_e X1_e + lam-_o X2_o
+// into D_e, lam+_o X1_o + lam-_e X2_e into D_o), so that twice as many stages
+// fit in shared memory.
 template <int PART>
 __global__ void __launch_bounds__(128, 1) k_syn_tc(const unsigned char *__restrict__ tab,
                                                    const unsigned char *__restrict__ bt,
@@ -232,9 +236,12 @@ __global__ void __launch_bounds__(128, 1) k_syn_tc(const unsigned char *__restri
   uint64_t *done = mbar, *full = mbar + TC_MAX_STAGES;
   const int NC = (PART == 0) ? 2 * B : 4 * B;  // D columns per parity
   constexpr int nA = (PART == 0) ? 2 : 4;
+  constexpr int UPS = (PART == 0) ? 1 : 2;     // stage units per K step
+  constexpr int nU = nA / UPS;                 // tiles per unit
   const int tileB = NC * 32;
-  const int abytes = nA * 2 * TILE_A, bbytes = nA * 2 * tileB;
-  const int stage = abytes + bbytes;
+  const int abytes = nA * 2 * TILE_A, bbytes = nA * 2 * tileB;   // per K step in global memory
+  const int uabytes = nU * 2 * TILE_A, ubbytes = nU * 2 * tileB;  // per unit in shared memory
+  const int stage = uabytes + ubbytes;
   const int m = blockIdx.y, pt = blockIdx.x, npt = gridDim.x, p0 = pt * 128;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -247,42 +254,46 @@ __global__ void __launch_bounds__(128, 1) k_syn_tc(const unsigned char *__restri
   fence_after_sync();
   const uint32_t tbase = tslot;
   const int nsteps = syn_steps(lmax, m);
+  const int nunits = nsteps * UPS;
   if (tid == 0) {
     const unsigned char *tabm = tab + (soff[m] * npt + (int64_t)pt * nsteps) * (int64_t)abytes;
     const unsigned char *btm = bt + soff[m] * (int64_t)bbytes;
     const uint32_t idesc = idesc_bf16(128, NC);
-    auto issue = [&](int c) {
-      const int s = c % NS;
+    // tile j of unit u: spin 0 tiles {0, 1}; spin 2 parity e tiles {0, 3}, parity o tiles {1, 2}
+    auto tile = [&](int u, int j) { return PART == 0 ? j : ((u & 1) == 0 ? 3 * j : 1 + j); };
+    auto issue = [&](int u) {
+      const int s = u % NS, c = u / UPS;
       unsigned char *dst = sm + s * stage;
       mbar_expect_tx(&full[s], (uint32_t)stage);
-      bulk_g2s(dst, tabm + (int64_t)c * abytes, (uint32_t)abytes, &full[s]);
-      bulk_g2s(dst + abytes, btm + (int64_t)c * bbytes, (uint32_t)bbytes, &full[s]);
+      for (int j = 0; j < nU; ++j)
+        bulk_g2s(dst + j * 2 * TILE_A, tabm + (int64_t)c * abytes + tile(u, j) * 2 * TILE_A, 2u * TILE_A, &full[s]);
+      for (int j = 0; j < nU; ++j)
+        bulk_g2s(dst + uabytes + j * 2 * tileB, btm + (int64_t)c * bbytes + tile(u, j) * 2 * tileB,
+                 (uint32_t)(2 * tileB), &full[s]);
     };
-    for (int c = 0; c < NS && c < nsteps; ++c) issue(c);
-    for (int c = 0; c < nsteps; ++c) {
-      const int s = c % NS;
-      unsigned char *Abuf = sm + s * stage, *Bbuf = Abuf + abytes;
-      mbar_wait(&full[s], (c / NS) & 1, err);
+    for (int u = 0; u < NS && u < nunits; ++u) issue(u);
+    for (int u = 0; u < nunits; ++u) {
+      const int s = u % NS, c = u / UPS;
+      unsigned char *Abuf = sm + s * stage, *Bbuf = Abuf + uabytes;
+      mbar_wait(&full[s], (u / NS) & 1, err);
       fence_after_sync();
       const uint32_t acc = c > 0 ? 1u : 0u;
       if (PART == 0) {
         mma3(tbase, Abuf, Bbuf, tileB, idesc, acc);
         mma3(tbase + NC, Abuf + 2 * TILE_A, Bbuf + 2 * tileB, tileB, idesc, acc);
       } else {
-        // D_e += lam+_e X1_e + lam-_o X2_o ;  D_o += lam+_o X1_o + lam-_e X2_e
-        mma3(tbase, Abuf + 0 * 2 * TILE_A, Bbuf + 0 * 2 * tileB, tileB, idesc, acc);
-        mma3(tbase, Abuf + 3 * 2 * TILE_A, Bbuf + 3 * 2 * tileB, tileB, idesc, 1u);
-        mma3(tbase + NC, Abuf + 1 * 2 * TILE_A, Bbuf + 1 * 2 * tileB, tileB, idesc, acc);
-        mma3(tbase + NC, Abuf + 2 * 2 * TILE_A, Bbuf + 2 * 2 * tileB, tileB, idesc, 1u);
+        const uint32_t d = (u & 1) ? tbase + NC : tbase;
+        mma3(d, Abuf, Bbuf, tileB, idesc, acc);
+        mma3(d, Abuf + 2 * TILE_A, Bbuf + 2 * tileB, tileB, idesc, 1u);
       }
       commit(&done[s]);
-      // refill the stage of step c - 1 (its MMAs precede those just issued)
-      if (c >= 1 && c - 1 + NS < nsteps) {
-        mbar_wait(&done[(c - 1) % NS], ((c - 1) / NS) & 1, err);
-        issue(c - 1 + NS);
+      // refill the stage of unit u - 1 (its MMAs precede those just issued)
+      if (u >= 1 && u - 1 + NS < nunits) {
+        mbar_wait(&done[(u - 1) % NS], ((u - 1) / NS) & 1, err);
+        issue(u - 1 + NS);
       }
     }
-    mbar_wait(&done[(nsteps - 1) % NS], ((nsteps - 1) / NS) & 1, err);
+    mbar_wait(&done[(nunits - 1) % NS], ((nunits - 1) / NS) & 1, err);
   }
   __syncthreads();
   fence_after_sync();
@@ -638,7 +649,7 @@ cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t s
                                     p->npairs, B, ns, nc, p->tc_err);
   }
   {
-    const int stage = 4 * 2 * TILE_A + 4 * 2 * (4 * B * 32);
+    const int stage = 2 * 2 * TILE_A + 2 * 2 * (4 * B * 32);  // half a K step (one parity)
     const uint32_t nc = pow2_cols(8 * B);
     const int ns = tc_stages(stage, nc);
     const size_t sm = tc_smem_n(stage, ns, nc);
