@@ -155,6 +155,7 @@ KERNEL_SOURCES = {
     "k_leg_ana64": ["dm_legendre.cu", "dm_internal.h"],
     "k_syn_tc": ["dm_legendre_tc.cu", "dm_tc.cuh", "dm_internal.h"],
     "k_ana_tc": ["dm_legendre_tc.cu", "dm_tc.cuh", "dm_internal.h"],
+    "k_reduce": ["dm_legendre.cu", "dm_internal.h"],
 }
 
 
