@@ -46,7 +46,7 @@ void free_all(dm_plan *p) {
                   p->filt, p->w, p->mask, p->sigma, p->rc, p->a, p->apart, p->wd, p->norms, p->state,
                   p->lev, p->tmpmap, p->tmpmap2, p->tmpalm, p->seeds_dev, p->coef_tmp,
                   p->ptab, p->rc32, p->apart32, p->s32, p->w32, p->wd32, p->phase32, p->bhat32, p->twid32,
-                  p->a_hi, p->g_hi, p->shi32, p->s64, p->rhi, p->tc_err, p->ring_order,
+                  p->a_hi, p->g_hi, p->shi32, p->s64, p->rhi, p->tc_err, p->ring_order, p->pair_order,
                   p->tc_synA[0], p->tc_synA[1], p->tc_anaA[0], p->tc_anaA[1], p->tc_soff, p->tc_aoff,
                   p->tc_synB[0], p->tc_synB[1], p->ptab_lo, p->e32, p->c32, p->clev, p->filt32,
                   p->twr, p->twr32, p->chirp, p->chirp32};

@@ -61,6 +61,7 @@ struct SolveState {
 struct RingClass {
   int off, count;
   int M, n;
+  int poff, pcount;  // pair_order[poff .. poff + pcount): the northern (or equatorial) rings of the class
 };
 
 struct LevelDev {
@@ -106,6 +107,8 @@ struct dm_plan {
   int twr_words = 0;
   int ring_lr = 3;              // radix 2^ring_lr of the fixed-size ring transforms (0: generic kernels)
   int *ring_order = nullptr;    // [nrings] ring ids grouped by FFT size class
+  int *pair_order = nullptr;    // [npairs] the side-0 ring of each pair, grouped by class
+  std::vector<int> pair_order_h;
   std::vector<int> ring_order_h;
   std::vector<dmwf::RingClass> ring_classes;
   dmwf::RecCoef *rec = nullptr; // [nalm]

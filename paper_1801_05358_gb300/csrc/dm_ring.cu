@@ -89,6 +89,57 @@ __device__ __forceinline__ C fold_one_g(const C *__restrict__ rc, const C *Tq, i
   return acc;
 }
 
+// The coefficients of the northern and southern rings of a pair for one
+// (RHS, field, m) are adjacent (side 0, side 1): one 16-byte access for FP32,
+// two adjacent ones (one sector) for FP64.
+template <typename C>
+__device__ __forceinline__ void ld2(const C *__restrict__ p, C &a, C &b) {
+  if constexpr (sizeof(C) == 8) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    a.x = v.x;
+    a.y = v.y;
+    b.x = v.z;
+    b.y = v.w;
+  } else {
+    a = p[0];
+    b = p[1];
+  }
+}
+template <typename C>
+__device__ __forceinline__ void st2(C *p, C a, C b) {
+  if constexpr (sizeof(C) == 8) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    p[0] = a;
+    p[1] = b;
+  }
+}
+
+// fold_one_g for both rings of a pair at once (base: side-0 index of m = 0);
+// the two rings share n, the phase offset and hence every phase.
+template <typename C>
+__device__ __forceinline__ void fold_pair_g(const C *__restrict__ rc, const C *Tq, int k, int n, int shift, int mmax,
+                                            int64_t base, int64_t mstride, C &an, C &as) {
+  an.x = an.y = 0;
+  as.x = as.y = 0;
+  const int n2 = 2 * n;
+  for (int m = k; m <= mmax; m += n) {
+    C vn, vs;
+    ld2(rc + base + (int64_t)m * mstride, vn, vs);
+    const C ph = phase_q(Tq, mod_small(m * shift, n2), n);
+    an = cadd(an, cmulc(vn, ph));
+    as = cadd(as, cmulc(vs, ph));
+  }
+  for (int m = n - k; m <= mmax; m += n)
+    if (m >= 1) {
+      C vn, vs;
+      ld2(rc + base + (int64_t)m * mstride, vn, vs);
+      const C ph = phase_q(Tq, mod_small(m * shift, n2), n);
+      an = cadd(an, cconj(cmulc(vn, ph)));
+      as = cadd(as, cconj(cmulc(vs, ph)));
+    }
+}
+
 // Length-h forward DFT of the CTA's lanes in place.  Direct rings (h = M a
 // power of two): bit-reversed input -> natural output.  Bluestein rings:
 // natural input already multiplied by the chirp and zero-padded (to M/2, or to
@@ -152,13 +203,26 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
                                               const R *__restrict__ s_anchor, const C *__restrict__ chirps) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ double red[16][8][2];  // [lane][warp]: up to 16 lanes of up to 8 warps
-  const int r = order[blockIdx.x];
   const int g = threadIdx.y;
-  const int L = blockIdx.y * blockDim.y + g;
-  const bool valid = L < nlanes;
-  const int b = valid ? L / 3 : 0, f = valid ? L % 3 : 0;
-  bool live = valid;
-  if ((MODE == RING_ITER || MODE == RING_INIT) && state != nullptr && valid && state[b].done) live = false;
+  // Paired kernels (fixed-size kernels whose lane is at most 256 threads, so
+  // that two lanes fit a block): grid.x walks the northern (or the equatorial)
+  // ring of each ring pair, and lanes 2q, 2q + 1 of a block are the northern
+  // and southern rings for the same (RHS, field).  The fold of the
+  // coefficients, the unpacking and the coefficient store then run once per
+  // pair over the threads of both lanes, with one 16-byte access per m.
+  constexpr bool pr = LR > 0 && ((1 << LOGM) >> LR) <= 256;
+  const int Lv = blockIdx.y * blockDim.y + g;
+  const int side = pr ? (Lv & 1) : 0;
+  const int L = pr ? (Lv >> 1) : Lv;
+  const int r0 = order[blockIdx.x];
+  const bool has_pair = pr && (nrings - 1 - r0) != r0;  // the equator ring has no partner
+  const int r = (pr && side) ? nrings - 1 - r0 : r0;
+  const bool valid_pair = L < nlanes;
+  const bool valid = valid_pair && (side == 0 || has_pair);
+  const int b = valid_pair ? L / 3 : 0, f = valid_pair ? L % 3 : 0;
+  bool plive = valid_pair;  // the pair's (RHS, field) is still iterating
+  if ((MODE == RING_ITER || MODE == RING_INIT) && state != nullptr && valid_pair && state[b].done) plive = false;
+  const bool live = plive && valid;
   if (!__syncthreads_or(live)) return;
   const RingDev Rg = rings[r];
   const int n = Rg.n, h = Rg.h, bl = Rg.bluestein;
@@ -176,10 +240,13 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
   C *tws_s = reinterpret_cast<C *>(sm_raw);  // stage twiddles (M - 1 used)
   C *Tq_s = tws_s + tw_words;                // quarter phase table (n/2 + 1 used)
   C *buf = Tq_s + ph_words + (size_t)g * lane_words;  // slots lslot(0..M)
+  C *bufN = Tq_s + ph_words + (size_t)(g & ~1) * lane_words, *bufS = bufN + lane_words;  // paired lanes
   C *S = buf + buf_words;                              // mmax + 1 staged coefficients (inverse modes)
   const C *tws = compact ? twid : tws_s;
   const C *Tq = compact ? phase + Rg.ph_off : Tq_s;
   const int tx = threadIdx.x, nt = LR > 0 ? ((1 << LOGM) >> LR) : (int)blockDim.x;
+  const int tp = side * nt + tx, ntp = pr ? 2 * nt : nt;  // thread and thread count of a pair loop
+  const int t0 = pr ? tp : tx;
   if (!compact) {
     const int tflat = threadIdx.y * nt + tx, nflat = nt * blockDim.y;
     for (int i = tflat; i < tw_words; i += nflat) tws_s[i] = twid[i];
@@ -190,6 +257,7 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
   const C *bh = bhat + (bl ? Rg.bh_off : 0);
   const C *chp = chirps + (bl ? Rg.ch_off : 0);  // Bluestein chirp e^{-i pi j^2 / h}, j < h
   const int64_t rbase = ((((int64_t)b * 3 + f) * (mmax + 1)) * npairs + Rg.pair) * 2 + Rg.side;
+  const int64_t rbaseP = ((((int64_t)b * 3 + f) * (mmax + 1)) * npairs + Rg.pair) * 2;  // side 0
   const int64_t mstride = (int64_t)npairs * 2;
   if (MODE == RING_ITER && live && tx == 0) {
     // ring segments start on 16-byte boundaries: n = 4i pixels, starts and npix multiples of 4
@@ -224,24 +292,43 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
       }
     }
     __syncthreads();
-    for (int k = tx; k <= (h >> 1); k += nt) {
+    // packed value of kk (t = 0: k, t = 1: h - k) into buffer x
+    auto pack = [&](C *x, C ck, C ck2, int t, int kk) {
+      const C a = t ? ck2 : ck, cc = cconj(t ? ck : ck2);
+      const C E = cadd(a, cc), O = cmulc(csub(a, cc), phase_q(Tq, 2 * kk, n));
+      C Z;  // conj(E + i O)
+      Z.x = E.x - O.y;
+      Z.y = -(E.y + O.x);
+      if (bl)
+        x[lslot<(LR > 0)>(kk)] = cmul(Z, chp[kk]);
+      else
+        x[lslot<(LR > 0)>(bitrev(kk, logM))] = Z;
+    };
+    for (int k = t0; k <= (h >> 1); k += ntp) {
       const int k2 = h - k;
+      if (pr) {
+        C ckN, ckS, ck2N, ck2S;
+        fold_pair_g(rc, Tq, k, n, Rg.shift, mmax, rbaseP, mstride, ckN, ckS);
+        if (k2 == k) {
+          ck2N = ckN;
+          ck2S = ckS;
+        } else {
+          fold_pair_g(rc, Tq, k2, n, Rg.shift, mmax, rbaseP, mstride, ck2N, ck2S);
+        }
+        for (int t = 0; t < 2; ++t) {
+          if (t && (k2 >= h || k2 == k)) break;
+          pack(bufN, ckN, ck2N, t, t ? k2 : k);
+          pack(bufS, ckS, ck2S, t, t ? k2 : k);
+        }
+        continue;
+      }
       const C ck = !staged_S ? fold_one_g(rc, Tq, k, n, Rg.shift, mmax, rbase, mstride) : fold_one(S, k, n, mmax);
       const C ck2 = (k2 == k) ? ck
                               : (!staged_S ? fold_one_g(rc, Tq, k2, n, Rg.shift, mmax, rbase, mstride)
                                          : fold_one(S, k2, n, mmax));
       for (int t = 0; t < 2; ++t) {
-        const int kk = t ? k2 : k;
         if (t && (k2 >= h || k2 == k)) break;
-        const C a = t ? ck2 : ck, cc = cconj(t ? ck : ck2);
-        const C E = cadd(a, cc), O = cmulc(csub(a, cc), phase_q(Tq, 2 * kk, n));
-        C Z;  // conj(E + i O)
-        Z.x = E.x - O.y;
-        Z.y = -(E.y + O.x);
-        if (bl)
-          buf[lslot<(LR > 0)>(kk)] = cmul(Z, chp[kk]);
-        else
-          buf[lslot<(LR > 0)>(bitrev(kk, logM))] = Z;
+        pack(buf, ck, ck2, t, t ? k2 : k);
       }
     }
     if (bl)
@@ -386,12 +473,12 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
   // Z_h = Z_0; each thread reads and rewrites the slots of k and h - k; X_h goes to slot M (direct)
   // or slot h (Bluestein).
   const R half = (R)0.5;
-  for (int k = tx; k <= (h >> 1); k += nt) {
+  auto unpack = [&](C *x, int k) {
     const int k2 = h - k;
     const int sk = bl ? k : bitrev(k, logM);
     const int sk2 = (k == 0) ? sk : (bl ? k2 : bitrev(k2, logM));
-    const C zk = dft_out<(LR > 0)>(buf, sk, bl, chp, invM_f, invM_d);
-    const C zk2 = (k == 0) ? zk : dft_out<(LR > 0)>(buf, sk2, bl, chp, invM_f, invM_d);
+    const C zk = dft_out<(LR > 0)>(x, sk, bl, chp, invM_f, invM_d);
+    const C zk2 = (k == 0) ? zk : dft_out<(LR > 0)>(x, sk2, bl, chp, invM_f, invM_d);
     for (int t = 0; t < 2; ++t) {
       if (t && k2 == k) break;
       const C a = t ? zk2 : zk, c = cconj(t ? zk : zk2);
@@ -404,19 +491,41 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
       O.y = -half * D.x;
       const C X = cadd(E, cmul(O, phase_q(Tq, 2 * kk, n)));
       const int slot = t ? ((k == 0) ? (bl ? h : M) : sk2) : sk;
-      buf[lslot<(LR > 0)>(slot)] = X;
+      x[lslot<(LR > 0)>(slot)] = X;
+    }
+  };
+  for (int k = t0; k <= (h >> 1); k += ntp) {
+    if (pr) {
+      unpack(bufN, k);
+      unpack(bufS, k);
+    } else {
+      unpack(buf, k);
     }
   }
   __syncthreads();
-  if (!live) return;
+  if (!(pr ? plive : live)) return;
   const int n2 = 2 * n;
-  for (int m = tx; m <= mmax; m += nt) {
+  for (int m = t0; m <= mmax; m += ntp) {
     const int q = mod_small(m, n);
     const int qq = (q <= h) ? q : n - q;
     const int slot = bl ? qq : (qq == h ? M : bitrev(qq, logM));
-    C X = buf[lslot<(LR > 0)>(slot)];
-    if (q > h) X = cconj(X);
-    rc[rbase + (int64_t)m * mstride] = cmul(X, phase_q(Tq, mod_small(m * Rg.shift, n2), n));
+    const C ph = phase_q(Tq, mod_small(m * Rg.shift, n2), n);
+    if (pr) {
+      C XN = bufN[lslot<(LR > 0)>(slot)], XS = bufS[lslot<(LR > 0)>(slot)];
+      if (q > h) {
+        XN = cconj(XN);
+        XS = cconj(XS);
+      }
+      C *dst = rc + rbaseP + (int64_t)m * mstride;
+      if (has_pair)
+        st2(dst, cmul(XN, ph), cmul(XS, ph));
+      else
+        dst[0] = cmul(XN, ph);
+    } else {
+      C X = buf[lslot<(LR > 0)>(slot)];
+      if (q > h) X = cconj(X);
+      rc[rbase + (int64_t)m * mstride] = cmul(X, ph);
+    }
   }
 }
 
@@ -481,15 +590,21 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
-    int G = ring_lanes_per_block(sizeof(C), tw_words, ph_words, lane_words, nlanes, fa.numRegs, T);
+    // fixed-size kernels take both rings of a pair per block when two lanes
+    // fit (the kernel's compile-time pr)
+    const bool paired = fixed && T <= 256;
+    const int vlanes = paired ? 2 * nlanes : nlanes;
+    int G = ring_lanes_per_block(sizeof(C), tw_words, ph_words, lane_words, vlanes, fa.numRegs, T);
+    if (paired) G = std::max(2, G & ~1);
     const size_t smem = sizeof(C) * ((size_t)tw_words + ph_words + (size_t)G * lane_words);
-    dim3 grid(rc_cls.count, (nlanes + G - 1) / G);
+    dim3 grid(paired ? rc_cls.pcount : rc_cls.count, (vlanes + G - 1) / G);
     dim3 block(T, G);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, block, smem, st>>>(p->rings, p->ring_order + rc_cls.off, phase, bhat, tws, tw_words, ph_words,
-                                    buf_words, lane_words, nlanes, rc, p->mmax, p->npairs, p->npix, p->nrings, in_map,
-                                    out_user, s_state, w, wd, p->norms, stp, s_anchor, chirps);
+    const int *order = paired ? p->pair_order + rc_cls.poff : p->ring_order + rc_cls.off;
+    kern<<<grid, block, smem, st>>>(p->rings, order, phase, bhat, tws, tw_words, ph_words, buf_words, lane_words,
+                                    nlanes, rc, p->mmax, p->npairs, p->npix, p->nrings, in_map, out_user, s_state, w,
+                                    wd, p->norms, stp, s_anchor, chirps);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -392,6 +392,15 @@ cudaError_t build_tables(dm_plan *p) {
       c.n = std::max(c.n, R.n);
     }
     p->ring_order_h = ids;
+    // the northern (or equatorial) member of each pair, class by class: the
+    // paired ring kernels take a pair per block (both members have one size)
+    p->pair_order_h.clear();
+    for (RingClass &c : p->ring_classes) {
+      c.poff = (int)p->pair_order_h.size();
+      for (int i = c.off; i < c.off + c.count; ++i)
+        if (p->rings_h[ids[i]].side == 0) p->pair_order_h.push_back(ids[i]);
+      c.pcount = (int)p->pair_order_h.size() - c.poff;
+    }
   }
   cudaError_t e;
   size_t ph_n = 4ull * ns * (ns + 1);
@@ -416,6 +425,11 @@ cudaError_t build_tables(dm_plan *p) {
     return e;
   if ((e = cudaMalloc(&p->ring_order, sizeof(int) * p->nrings))) return e;
   if ((e = cudaMemcpy(p->ring_order, p->ring_order_h.data(), sizeof(int) * p->nrings, cudaMemcpyHostToDevice)))
+    return e;
+  const size_t npo = p->pair_order_h.size();
+  if ((e = cudaMalloc(&p->pair_order, sizeof(int) * (npo > 0 ? npo : 1)))) return e;
+  if (npo > 0 &&
+      (e = cudaMemcpy(p->pair_order, p->pair_order_h.data(), sizeof(int) * npo, cudaMemcpyHostToDevice)))
     return e;
   cudaMemset(p->rec, 0, sizeof(RecCoef) * (p->nalm + 1));
   k_pairs<<<(p->npairs + 127) / 128, 128>>>(p->pairs, ns, p->npairs);
