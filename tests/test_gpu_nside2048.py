@@ -6,8 +6,8 @@ computes whole rings of alm2map and whole orders m of map2alm one at a time
 (oracle.ring_alm2map / map2alm_m, pinned to the full transforms at small
 sizes).  The GPU runs the full transforms and one dual messenger iteration in
 the FP64 mode; the mixed mode's tables do not fit this size (3 x nalm x npairs
-FP32 values, about 412 GB).  The data map of the iteration is the config-3
-noise realisation on the observed pixels of the config-3 mask (no GPU result
+FP32 values, about 412 GB).  The data map of the iteration is the nside 2048
+recipe's noise realisation on the observed pixels of its mask (no GPU result
 enters an expected value).  Bar: the FP64 one, 1e-10 relative L2 per sample,
 except on the two rings nearest each pole (theta < 1e-3): there the oracle's
 own FP64 spin-2 recurrences are accurate to 2e-9 relative at l = 4096 (pinned
