@@ -685,6 +685,164 @@ double orc_chi2(int nside, int lmax, const double *cl, const double *sigma, cons
 }
 
 /* ------------------------------------------------------------------------ */
+/* Correlated noise with distinct temperature and polarisation masks           */
+/* (the 3x3 per-pixel noise covariance of Section 2.1 and Appendix B).         */
+/*                                                                              */
+/* Per pixel N = Sigma C Sigma, Sigma = diag(sigma_I, sigma_Q, sigma_U) and C  */
+/* the unit-diagonal correlation matrix of (rho_IQ, rho_IU, rho_QU).  Masked    */
+/* components carry Sigma^{-1} = 0 (Appendix B): maskT for I, maskP for Q, U,  */
+/* so N^{-1} = Sigma^{-1} C^{-1} Sigma^{-1} has zero rows and columns there.    */
+/* T = alpha 1, alpha the smallest eigenvalue of N (Algorithm 1), taken over   */
+/* the observed components of each pixel: alpha = min_i 1 / lambda_max(N_i^{-1}).*/
+/* The messenger equation of Appendix B,                                        */
+/*   t = (Nbar^{-1} + T^{-1})^{-1} (T^{-1} s + Nbar^{-1} d),  Nbar = N - T,     */
+/* written with Nbar^{-1} = Sigma^{-1} P^T (Delta - alpha P Sigma^{-2} P^T)^{-1} */
+/* P Sigma^{-1} (C = P^T Delta P), equals t = s + W (d - s) with               */
+/* W = alpha N^{-1}: with G = Sigma^{-1} P^T and M = Delta - alpha G^T G,       */
+/* (G M^{-1} G^T + 1/alpha)^{-1} G M^{-1} G^T = alpha G (M + alpha G^T G)^{-1} G^T */
+/* = alpha G Delta^{-1} G^T.  The last form needs no M^{-1}, so it also holds  */
+/* in the corner case Nbar = 0 of Section 2.1, where W has eigenvalue 1 and    */
+/* t = d along that direction.                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Largest eigenvalue of a symmetric 3x3 matrix (cyclic Jacobi rotations). */
+static double eigmax3(const double A_in[9]) {
+  double A[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) A[i][j] = A_in[3 * i + j];
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+    double scale = fabs(A[0][0]) + fabs(A[1][1]) + fabs(A[2][2]);
+    if (off <= 1e-300 || off <= 1e-17 * scale) break;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        if (A[p][q] == 0.0) continue;
+        double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < 3; ++k) {  /* A <- A J */
+          double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - sn * akq;
+          A[k][q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < 3; ++k) {  /* A <- J^T A */
+          double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - sn * aqk;
+          A[q][k] = sn * apk + c * aqk;
+        }
+      }
+  }
+  double e = A[0][0];
+  if (A[1][1] > e) e = A[1][1];
+  if (A[2][2] > e) e = A[2][2];
+  return e;
+}
+
+/* ninv[p][9] = N_p^{-1} (row-major 3x3, components I, Q, U). */
+void orc_cov_ninv(long npix, const double *sigma, const double *rho, const uint8_t *maskT, const uint8_t *maskP,
+                  double *ninv) {
+  for (long p = 0; p < npix; ++p) {
+    const double r01 = rho[p], r02 = rho[npix + p], r12 = rho[2 * npix + p];
+    /* C^{-1} by cofactors (C symmetric, unit diagonal) */
+    const double c00 = 1.0 - r12 * r12, c11 = 1.0 - r02 * r02, c22 = 1.0 - r01 * r01;
+    const double c01 = r02 * r12 - r01, c02 = r01 * r12 - r02, c12 = r01 * r02 - r12;
+    const double det = 1.0 + 2.0 * r01 * r02 * r12 - r01 * r01 - r02 * r02 - r12 * r12;
+    const double ci[9] = {c00 / det, c01 / det, c02 / det, c01 / det, c11 / det, c12 / det,
+                          c02 / det, c12 / det, c22 / det};
+    double si[3];
+    si[0] = (!maskT || maskT[p]) ? 1.0 / sigma[p] : 0.0;
+    si[1] = (!maskP || maskP[p]) ? 1.0 / sigma[npix + p] : 0.0;
+    si[2] = (!maskP || maskP[p]) ? 1.0 / sigma[2 * npix + p] : 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) ninv[9 * p + 3 * i + j] = si[i] * ci[3 * i + j] * si[j];
+  }
+}
+
+double orc_cov_alpha(long npix, const double *ninv) {
+  double a = INFINITY;
+  for (long p = 0; p < npix; ++p) {
+    const double e = eigmax3(ninv + 9 * p);
+    if (e > 0.0 && 1.0 / e < a) a = 1.0 / e;
+  }
+  return a;
+}
+
+/* t = s + alpha N^{-1} (d - s), per pixel over its three components. */
+void orc_messenger_update_cov(long npix, double alpha, const double *ninv, const double *d, const double *s,
+                              double *t) {
+  for (long p = 0; p < npix; ++p) {
+    double r[3];
+    for (int i = 0; i < 3; ++i) r[i] = d[i * npix + p] - s[i * npix + p];
+    for (int i = 0; i < 3; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < 3; ++j) acc += ninv[9 * p + 3 * i + j] * r[j];
+      t[i * npix + p] = s[i * npix + p] + alpha * acc;
+    }
+  }
+}
+
+/* The dual messenger loop of orc_dm_solve with the noise model above: the
+ * same harmonic step, synthesis, Cauchy test and level control; the
+ * messenger update is orc_messenger_update_cov, and t_0 is d on the observed
+ * components (0 on masked ones). */
+int orc_dm_solve_cov(int nside, int lmax, const double *cl, const double *sigma, const double *rho,
+                     const uint8_t *maskT, const uint8_t *maskP, const double *d, int nlev, const double *lambdas,
+                     const double *eps, const int *forced_iters, int max_iter, double *s_out, double *alm_out,
+                     int *iters_out, double *cauchy_out) {
+  long npix = orc_npix(nside), nalm = orc_nalm(lmax);
+  long n3 = 3 * npix;
+  double *ninv = malloc(sizeof(double) * 9 * npix);
+  orc_cov_ninv(npix, sigma, rho, maskT, maskP, ninv);
+  double alpha = orc_cov_alpha(npix, ninv);
+  double omega = 4.0 * M_PI / (double)npix;
+  double th = alpha * omega;
+  double *t = malloc(sizeof(double) * n3), *s = malloc(sizeof(double) * n3), *sn = malloc(sizeof(double) * n3);
+  double *r = malloc(sizeof(double) * n3);
+  double *a = malloc(sizeof(double) * 6 * nalm), *ar = malloc(sizeof(double) * 6 * nalm);
+  double *coef = malloc(sizeof(double) * 4 * (lmax + 1));
+  for (long p = 0; p < npix; ++p) {
+    const int obs[3] = {!maskT || maskT[p], !maskP || maskP[p], !maskP || maskP[p]};
+    for (int f = 0; f < 3; ++f) {
+      s[f * npix + p] = 0.0;
+      t[f * npix + p] = obs[f] ? d[f * npix + p] : 0.0;
+    }
+  }
+  memset(a, 0, sizeof(double) * 6 * nalm);
+  int it = 0;
+  for (int k = 0; k < nlev; ++k) {
+    double mu = (lambdas[k] - 1.0) * th;
+    orc_filter_coefs(lmax, cl, mu, th, coef);
+    int nk = 0;
+    for (;;) {
+      if (!forced_iters && it >= max_iter) break;
+      if (forced_iters && nk >= forced_iters[k]) break;
+      for (long i = 0; i < n3; ++i) r[i] = t[i] - s[i];
+      orc_map2alm(nside, lmax, r, ar);
+      for (long i = 0; i < 6 * nalm; ++i) a[i] += ar[i];
+      orc_apply_filter(lmax, coef, a);
+      orc_alm2map(nside, lmax, a, sn);
+      double dd = 0.0, ss = 0.0;
+      for (long i = 0; i < n3; ++i) {
+        dd += (sn[i] - s[i]) * (sn[i] - s[i]);
+        ss += sn[i] * sn[i];
+      }
+      double cauchy = (ss > 0.0) ? sqrt(dd / ss) : 0.0;
+      memcpy(s, sn, sizeof(double) * n3);
+      orc_messenger_update_cov(npix, alpha, ninv, d, s, t);
+      if (cauchy_out && it < max_iter) cauchy_out[it] = cauchy;
+      ++it;
+      ++nk;
+      if (!forced_iters && cauchy < eps[k]) break;
+    }
+    if (iters_out) iters_out[k] = nk;
+  }
+  memcpy(s_out, s, sizeof(double) * n3);
+  if (alm_out) memcpy(alm_out, a, sizeof(double) * 6 * nalm);
+  free(ninv); free(t); free(s); free(sn); free(r); free(a); free(ar); free(coef);
+  return it;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Constrained realisations (Section 2.2, Eq. 19):                             */
 /*   s_CR = W(d - dhat) + shat,  shat = Y ahat with ahat ~ S,                  */
 /*   dhat = shat + nhat with nhat ~ N on observed pixels.                      */

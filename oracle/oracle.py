@@ -56,6 +56,8 @@ def lib():
         L.orc_alpha.restype = ctypes.c_double
         L.orc_chi2.restype = ctypes.c_double
         L.orc_dm_solve.restype = ctypes.c_int
+        L.orc_cov_alpha.restype = ctypes.c_double
+        L.orc_dm_solve_cov.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -217,6 +219,62 @@ def messenger_update(w, d, s):
     t = np.zeros_like(s)
     lib().orc_messenger_update(w.size, _d(w), _d(d), _d(s), _d(t))
     return t
+
+
+def cov_ninv(sigma, rho, maskT, maskP):
+    """Per-pixel N^{-1} [npix, 3, 3] of the correlated noise model (Appendix B)."""
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    rh = np.ascontiguousarray(rho, dtype=np.float64)
+    mt, mtp = _mask_ptr(maskT)
+    mp_, mpp = _mask_ptr(maskP)
+    npix = sg.shape[1]
+    out = np.zeros((npix, 3, 3))
+    lib().orc_cov_ninv(npix, _d(sg), _d(rh), mtp, mpp, _d(out))
+    return out
+
+
+def cov_alpha(ninv):
+    n = np.ascontiguousarray(ninv, dtype=np.float64)
+    return lib().orc_cov_alpha(n.shape[0], _d(n))
+
+
+def messenger_update_cov(alpha_, ninv, d, s):
+    n = np.ascontiguousarray(ninv, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    t = np.zeros_like(s)
+    lib().orc_messenger_update_cov(n.shape[0], ctypes.c_double(alpha_), _d(n), _d(d), _d(s), _d(t))
+    return t
+
+
+def dm_solve_cov(nside, lmax, cl, sigma, rho, maskT, maskP, d, lambdas, eps=None, forced_iters=None,
+                 max_iter=100000):
+    """Algorithm 1 with the correlated noise model and distinct T/P masks.
+    Returns dict(s, alm, iters_per_level, cauchy, iters)."""
+    lambdas = np.ascontiguousarray(lambdas, dtype=np.float64)
+    nlev = lambdas.size
+    eps = np.ascontiguousarray(np.zeros(nlev) if eps is None else eps, dtype=np.float64)
+    c = np.ascontiguousarray(cl, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    rh = np.ascontiguousarray(rho, dtype=np.float64)
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    mt, mtp = _mask_ptr(maskT)
+    mp_, mpp = _mask_ptr(maskP)
+    s = np.zeros((3, npix(nside)))
+    alm = np.zeros((3, nalm(lmax)), dtype=np.complex128)
+    iters = np.zeros(nlev, dtype=np.int32)
+    if forced_iters is not None:
+        fi = np.ascontiguousarray(forced_iters, dtype=np.int32)
+        fptr = fi.ctypes.data_as(_ip)
+        max_iter = int(fi.sum())
+    else:
+        fi = None
+        fptr = ctypes.cast(None, _ip)
+    cauchy = np.zeros(max(max_iter, 1))
+    n = lib().orc_dm_solve_cov(nside, lmax, _d(c), _d(sg), _d(rh), mtp, mpp, _d(dd), nlev, _d(lambdas), _d(eps),
+                               fptr, max_iter, _d(s), _d(alm.view(np.float64)), iters.ctypes.data_as(_ip),
+                               _d(cauchy))
+    return dict(s=s, alm=alm, iters_per_level=iters, cauchy=cauchy[:n], iters=n)
 
 
 def dm_solve(nside, lmax, cl, sigma, mask, d, lambdas, eps=None, forced_iters=None, max_iter=100000):

@@ -1,0 +1,209 @@
+"""Pins of the oracle's correlated-noise model (3x3 noise covariance per
+pixel, distinct temperature and polarisation masks; Section 2.1 and
+Appendix B).
+
+- N^{-1} against numpy's inverse of Sigma C Sigma, with masked components
+  (Sigma^{-1} = 0) zeroed;
+- alpha against numpy's eigenvalues of N;
+- the update t = s + alpha N^{-1} (d - s) against the literal messenger
+  equation of Appendix B, t = (Nbar^{-1} + T^{-1})^{-1}(T^{-1} s + Nbar^{-1} d)
+  with Nbar^{-1} = Sigma^{-1} P^T (Delta - alpha P Sigma^{-2} P^T)^{-1} P Sigma^{-1};
+- the corner case Nbar = 0 of Section 2.1 (t = d along that direction);
+- masked components: t = s there, and their data never enter;
+- uncorrelated noise with one mask: the same solve as the diagonal oracle;
+- the converged loop against a dense Wiener-filter solve with the
+  block-diagonal N^{-1} at nside 4."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.harmonics_ref import alm_to_params, dense_synthesis
+from tests.test_oracle_dm import _dense_problem, _prior_precision
+
+
+def _corr(rho):
+    """[npix, 3, 3] correlation matrices from [3, npix] (rho_IQ, rho_IU, rho_QU)."""
+    npix = rho.shape[1]
+    C = np.empty((npix, 3, 3))
+    C[:, 0, 0] = C[:, 1, 1] = C[:, 2, 2] = 1.0
+    C[:, 0, 1] = C[:, 1, 0] = rho[0]
+    C[:, 0, 2] = C[:, 2, 0] = rho[1]
+    C[:, 1, 2] = C[:, 2, 1] = rho[2]
+    return C
+
+
+def _random_model(npix, seed, masked=True):
+    rng = np.random.default_rng(seed)
+    sigma = rng.uniform(0.5, 2.0, (3, npix))
+    rho = rng.uniform(-0.3, 0.3, (3, npix))
+    mt = (rng.random(npix) > 0.3).astype(np.uint8) if masked else np.ones(npix, np.uint8)
+    mp = (rng.random(npix) > 0.3).astype(np.uint8) if masked else np.ones(npix, np.uint8)
+    return sigma, rho, mt, mp
+
+
+def test_ninv_is_masked_inverse_of_sigma_c_sigma(orc):
+    sigma, rho, mt, mp = _random_model(200, 1)
+    ninv = orc.cov_ninv(sigma, rho, mt, mp)
+    C = _corr(rho)
+    for p in range(200):
+        si = np.array([mt[p] / sigma[0, p], mp[p] / sigma[1, p], mp[p] / sigma[2, p]])
+        ref = si[:, None] * np.linalg.inv(C[p]) * si[None, :]
+        assert np.allclose(ninv[p], ref, rtol=1e-13, atol=1e-15)
+        if mt[p] and mp[p]:
+            N = np.diag(sigma[:, p]) @ C[p] @ np.diag(sigma[:, p])
+            assert np.allclose(ninv[p], np.linalg.inv(N), rtol=1e-12)
+
+
+def test_alpha_is_smallest_eigenvalue_of_n(orc):
+    sigma, rho, mt, mp = _random_model(300, 2, masked=False)
+    ninv = orc.cov_ninv(sigma, rho, mt, mp)
+    C = _corr(rho)
+    lam = min(np.linalg.eigvalsh(np.diag(sigma[:, p]) @ C[p] @ np.diag(sigma[:, p])).min() for p in range(300))
+    assert orc.cov_alpha(ninv) == pytest.approx(lam, rel=1e-13)
+    # with masks: the smallest eigenvalue over the observed components
+    sigma, rho, mt, mp = _random_model(300, 3)
+    ninv = orc.cov_ninv(sigma, rho, mt, mp)
+    ref = min(1.0 / np.linalg.eigvalsh(ninv[p]).max() for p in range(300) if np.abs(ninv[p]).max() > 0)
+    assert orc.cov_alpha(ninv) == pytest.approx(ref, rel=1e-13)
+
+
+@pytest.mark.parametrize("masked", [False, True])
+def test_update_equals_appendix_b_messenger_equation(orc, masked):
+    """The literal Appendix B formula with C = P^T Delta P (numpy eigh) and
+    T = alpha 1, at pixels where Nbar is invertible."""
+    npix = 120
+    sigma, rho, mt, mp = _random_model(npix, 4, masked)
+    ninv = orc.cov_ninv(sigma, rho, mt, mp)
+    alpha = orc.cov_alpha(ninv)
+    rng = np.random.default_rng(5)
+    d, s = rng.standard_normal((3, npix)), rng.standard_normal((3, npix))
+    t = orc.messenger_update_cov(alpha, ninv, d, s)
+    C = _corr(rho)
+    checked = 0
+    for p in range(npix):
+        si = np.diag([mt[p] / sigma[0, p], mp[p] / sigma[1, p], mp[p] / sigma[2, p]])
+        ev, V = np.linalg.eigh(C[p])
+        P, Delta = V.T, np.diag(ev)
+        M = Delta - alpha * P @ si @ si @ P.T
+        if np.linalg.eigvalsh(M).min() < 1e-6:
+            continue  # the corner case, checked below
+        nbinv = si @ P.T @ np.linalg.inv(M) @ P @ si
+        lhs = nbinv + np.eye(3) / alpha
+        ref = np.linalg.solve(lhs, s[:, p] / alpha + nbinv @ d[:, p])
+        assert np.allclose(t[:, p], ref, rtol=1e-11, atol=1e-12)
+        checked += 1
+    assert checked >= npix - 2
+
+
+def test_corner_case_keeps_the_data(orc):
+    """At the pixel where alpha is attained (Nbar = 0 along one direction v of
+    Section 2.1) the update keeps the data there: v . t = v . d."""
+    npix = 80
+    sigma, rho, mt, mp = _random_model(npix, 6, masked=False)
+    ninv = orc.cov_ninv(sigma, rho, mt, mp)
+    alpha = orc.cov_alpha(ninv)
+    C = _corr(rho)
+    N = [np.diag(sigma[:, p]) @ C[p] @ np.diag(sigma[:, p]) for p in range(npix)]
+    p0 = int(np.argmin([np.linalg.eigvalsh(n).min() for n in N]))
+    ev, V = np.linalg.eigh(N[p0])
+    v = V[:, 0]
+    assert ev[0] == pytest.approx(alpha, rel=1e-13)
+    rng = np.random.default_rng(7)
+    d, s = rng.standard_normal((3, npix)), rng.standard_normal((3, npix))
+    t = orc.messenger_update_cov(alpha, ninv, d, s)
+    assert v @ t[:, p0] == pytest.approx(v @ d[:, p0], abs=1e-13)
+
+
+def test_masked_components_keep_s_and_ignore_d(orc):
+    npix = 150
+    sigma, rho, mt, mp = _random_model(npix, 8)
+    ninv = orc.cov_ninv(sigma, rho, mt, mp)
+    alpha = orc.cov_alpha(ninv)
+    rng = np.random.default_rng(9)
+    d, s = rng.standard_normal((3, npix)), rng.standard_normal((3, npix))
+    t = orc.messenger_update_cov(alpha, ninv, d, s)
+    obs = np.stack([mt, mp, mp]).astype(bool)
+    assert np.array_equal(t[~obs], s[~obs])
+    d2 = d.copy()
+    d2[~obs] = 1e6 * rng.standard_normal((~obs).sum())
+    assert np.array_equal(orc.messenger_update_cov(alpha, ninv, d2, s), t)
+
+
+def test_uncorrelated_common_mask_is_the_diagonal_solve(orc):
+    """rho = 0 and one mask for I, Q and U: the correlated-noise solve is the
+    diagonal one (alpha = min sigma^2, W = alpha / sigma^2) up to rounding."""
+    wl = W.make_workload("nside16", [11], nside=8, lmax=16)
+    d = wl.data([orc.alm2map(8, 16, wl.alm_true[0])])[0]
+    rho = np.zeros_like(wl.sigma)
+    lam = W.lambda_schedule(1000.0, 4)
+    ref = orc.dm_solve(8, 16, wl.cl, wl.sigma, wl.mask, d, lam, forced_iters=[3, 3, 3, 3])
+    got = orc.dm_solve_cov(8, 16, wl.cl, wl.sigma, rho, wl.mask, wl.mask, d, lam, forced_iters=[3, 3, 3, 3])
+    assert got["iters"] == 12
+    assert np.linalg.norm(got["s"] - ref["s"]) / np.linalg.norm(ref["s"]) < 1e-13
+    assert np.linalg.norm(got["alm"] - ref["alm"]) / np.linalg.norm(ref["alm"]) < 1e-13
+
+
+@pytest.mark.parametrize("level_lambda", [1.0, 40.0])
+def test_cov_fixed_point_is_dense_wiener_filter(orc, level_lambda):
+    """At a fixed level the loop converges to (S'^{-1} + Y^T N^{-1} Y) x =
+    Y^T N^{-1} d with the block-diagonal N^{-1} (I, Q, U of a pixel coupled)
+    and distinct temperature and polarisation masks, solved densely at
+    nside 4."""
+    nside, lmax = 4, 8
+    cl, params_all, sigma, mask, z, phi = _dense_problem(nside, lmax, 3)
+    npix = z.size
+    rng = np.random.default_rng(12)
+    rho = rng.uniform(-0.3, 0.3, (3, npix))
+    mask_t = (np.abs(z) > 0.25).astype(np.uint8)
+    mask_p = (np.abs(z - 0.1) > 0.2).astype(np.uint8)
+    ninv = orc.cov_ninv(sigma, rho, mask_t, mask_p)
+    alpha = orc.cov_alpha(ninv)
+    th = alpha * 4 * np.pi / npix
+    mu = (level_lambda - 1.0) * th
+    params = [p for p in params_all if not (p[0] == 0 and p[1] == 0 and mu == 0.0)]
+    Y = dense_synthesis(nside, lmax, z, phi, params)
+    Nd = np.zeros((3 * npix, 3 * npix))
+    for p in range(npix):
+        for i in range(3):
+            for j in range(3):
+                Nd[i * npix + p, j * npix + p] = ninv[p, i, j]
+    obs = np.stack([mask_t, mask_p, mask_p])
+    d = W.random_maps(nside, 1, 8)[0] * 0.05 * obs
+    P = _prior_precision(cl, params, mu)
+    x = np.linalg.solve(P + Y.T @ Nd @ Y, Y.T @ Nd @ d.reshape(-1))
+    r = orc.dm_solve_cov(nside, lmax, cl, sigma, rho, mask_t, mask_p, d, [level_lambda], eps=[1e-15],
+                         max_iter=60000)
+    xo = alm_to_params(r["alm"], params, lmax)
+    assert np.linalg.norm(xo - x) / np.linalg.norm(x) < 1e-9
+    s_ref = (Y @ x).reshape(3, -1)
+    assert np.linalg.norm(r["s"] - s_ref) / np.linalg.norm(s_ref) < 1e-9
+
+
+def test_correlated_noise_draws_have_the_model_covariance():
+    """draw_noise_cov: the sample covariance of many draws of one pixel model
+    is Sigma C Sigma (to the sampling error), and masked components are 0."""
+    n = 200000
+    sigma = np.tile(np.array([[1.0], [1.5], [0.7]]), (1, n))
+    rho = np.tile(np.array([[0.25], [-0.2], [0.1]]), (1, n))
+    ones = np.ones(n, np.uint8)
+    x = W.draw_noise_cov(sigma, rho, ones, ones, np.random.default_rng(13))
+    C = _corr(rho[:, :1])[0]
+    ref = np.diag(sigma[:, 0]) @ C @ np.diag(sigma[:, 0])
+    assert np.allclose(np.cov(x), ref, atol=0.02)
+    mt = np.zeros(n, np.uint8)
+    y = W.draw_noise_cov(sigma, rho, mt, ones, np.random.default_rng(14))
+    assert not y[0].any() and y[1].any()
+
+
+def test_masked_data_never_enter_the_solve(orc):
+    """Arbitrary values on masked components of d change nothing, from the
+    first iteration on (t_0 is d on observed components only)."""
+    wl = W.make_cov_workload([15], 8, 16)
+    d = wl.data([orc.alm2map(8, 16, wl.alm_true[0])])[0]
+    obs = np.stack([wl.mask, wl.mask_p, wl.mask_p]).astype(bool)
+    d2 = d.copy()
+    d2[~obs] = np.random.default_rng(16).standard_normal((~obs).sum())
+    lam = W.lambda_schedule(1000.0, 2)
+    a = orc.dm_solve_cov(8, 16, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d, lam, forced_iters=[2, 2])
+    b = orc.dm_solve_cov(8, 16, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d2, lam, forced_iters=[2, 2])
+    assert np.array_equal(a["s"], b["s"]) and np.array_equal(a["alm"], b["alm"])
