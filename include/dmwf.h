@@ -137,6 +137,25 @@ dm_status dm_set_noise_mask(dm_plan *plan, const double *sigma, const uint8_t *m
  * it.  DM_EBUSY while a solve is in progress. */
 dm_status dm_set_noise_mask_rhs(dm_plan *plan, int b, const double *sigma, const uint8_t *mask);
 
+/* Correlated noise with distinct temperature and polarisation masks, for every
+ * RHS of the plan (the 3x3 per-pixel noise covariance of Section 2.1 and
+ * Appendix B).  sigma: host [3][npix] (I, Q, U) amplitudes; rho: host [3][npix]
+ * correlations (rho_IQ, rho_IU, rho_QU), N = Sigma C Sigma with C the
+ * unit-diagonal correlation matrix; mask_t: host [npix], 1 = temperature
+ * observed (NULL = all); mask_p: the same for Q and U.  Masked components
+ * carry Sigma^{-1} = 0 (Appendix B).  alpha is the smallest eigenvalue of N
+ * over the observed components, and the messenger update is Appendix B's
+ * t = (Nbar^{-1} + T^{-1})^{-1} (T^{-1} s + Nbar^{-1} d), applied as
+ * s + alpha N^{-1} (d - s).  Copied at the call.  Solves then run in DM_FP64
+ * or DM_FLOAT_FLOAT (DM_EINVAL in DM_MIXED_FP32 at dm_solve_begin);
+ * constrained realisations and per-RHS noise return DM_EINVAL.
+ * dm_set_noise_mask returns the plan to diagonal noise.  DM_EINVAL for a
+ * correlation matrix that is not positive definite, sigma <= 0 or non-finite
+ * on an observed component, or no observed component; DM_EBUSY during a
+ * solve. */
+dm_status dm_set_noise_cov(dm_plan *plan, const double *sigma, const double *rho, const uint8_t *mask_t,
+                           const uint8_t *mask_p);
+
 /* Schedule (defaults: lambda0 1000, 10 levels, 10 iterations per level). */
 dm_status dm_set_schedule(dm_plan *plan, const dm_schedule *sched);
 

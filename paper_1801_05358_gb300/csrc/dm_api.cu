@@ -49,7 +49,7 @@ void free_all(dm_plan *p) {
                   p->a_hi, p->g_hi, p->shi32, p->s64, p->rhi, p->tc_err, p->ring_order, p->pair_order,
                   p->tc_synA[0], p->tc_synA[1], p->tc_anaA[0], p->tc_anaA[1], p->tc_soff, p->tc_aoff,
                   p->tc_synB[0], p->tc_synB[1], p->ptab_lo, p->e32, p->c32, p->clev, p->filt32,
-                  p->twr, p->twr32, p->chirp, p->chirp32};
+                  p->twr, p->twr32, p->chirp, p->chirp32, p->wcov};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -142,7 +142,7 @@ cudaError_t enqueue_iteration(dm_plan *p, cudaStream_t st, cudaEvent_t *E) {
   if (E) cudaEventRecord(E[2], st);
   if ((e = legendre_synthesis(p, p->a, st))) return e;
   if (E) cudaEventRecord(E[3], st);
-  if ((e = ring_stage(p, RING_ITER, nullptr, p->s64, st))) return e;
+  if ((e = p->cov ? cov_ring_stage(p, st) : ring_stage(p, RING_ITER, nullptr, p->s64, st))) return e;
   if (E) cudaEventRecord(E[4], st);
   if ((e = control_step(p, st))) return e;
   if (E) cudaEventRecord(E[5], st);
@@ -208,8 +208,10 @@ dm_status anchor(dm_plan *p, cudaStream_t st, bool initial, const double *d, boo
 }
 
 dm_status solve_begin(dm_plan *p, const double *d, cudaStream_t st) {
+  if (p->cov && p->prec != DM_FP64)
+    return fail(p, DM_EINVAL, "correlated noise (dm_set_noise_cov) runs in DM_FP64 or DM_FLOAT_FLOAT");
   DM_CU(cudaMemsetAsync(p->a, 0, sizeof(double2) * 3 * p->nalm * p->batch, st), "zero a");
-  DM_CU(prepare_wd(p, d, st), "w d");
+  DM_CU(p->cov ? cov_prepare_wd(p, d, st) : prepare_wd(p, d, st), "w d");
   DM_CU(control_init(p, st), "control init");
   p->launches += 2;
   if (p->prec == DM_FP64) {
@@ -487,6 +489,7 @@ dm_status upload_noise(dm_plan *p, int b, const double *sigma, const uint8_t *ma
 
 dm_status dm_set_noise_mask(dm_plan *p, const double *sigma, const uint8_t *mask) {
   if (!p || !sigma) return DM_EINVAL;
+  if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
   dm_status r = check_noise(p, sigma, mask);
   if (r != DM_OK) return r;
   r = upload_noise(p, 0, sigma, mask);
@@ -500,12 +503,14 @@ dm_status dm_set_noise_mask(dm_plan *p, const double *sigma, const uint8_t *mask
     p->t_h[b] = p->t_h[0];
   }
   p->have_noise = true;
+  p->cov = false;
   return refresh_filters(p);
 }
 
 dm_status dm_set_noise_mask_rhs(dm_plan *p, int b, const double *sigma, const uint8_t *mask) {
   if (!p || !sigma || b < 0 || b >= p->batch) return DM_EINVAL;
   if (!p->have_noise) return fail(p, DM_EINVAL, "set the plan-wide noise first (dm_set_noise_mask)");
+  if (p->cov) return fail(p, DM_EINVAL, "per-RHS diagonal noise cannot be mixed with dm_set_noise_cov");
   if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
   dm_status r = check_noise(p, sigma, mask);
   if (r != DM_OK) return r;
@@ -527,6 +532,9 @@ dm_status dm_set_schedule(dm_plan *p, const dm_schedule *s) {
     return fail(p, DM_EINVAL, "bad Cauchy thresholds");
   p->sched = *s;
   if (p->sched.check_every < 1) p->sched.check_every = 1;
+  // every RHS takes the schedule's final tolerance (the server then sets its
+  // slots' own tolerances through their views)
+  p->eps_final_rhs.assign(p->batch, s->eps_final);
   if (!p->forced.empty() && (int)p->forced.size() != s->n_levels) p->forced.clear();
   dm_status r = upload_levels(p);
   if (r != DM_OK) return r;
@@ -582,6 +590,7 @@ dm_status dm_draw_cr_inputs(dm_plan *p, const uint64_t *seeds, double *ahat, dou
                             void *stream) {
   if (!p || !seeds) return DM_EINVAL;
   if (!p->have_cl || !p->have_noise) return fail(p, DM_EINVAL, "spectra and noise must be set");
+  if (p->cov) return fail(p, DM_EINVAL, "constrained-realisation draws take the diagonal noise model");
   cudaStream_t st = (cudaStream_t)stream;
   DM_CU(cudaMemcpyAsync(p->seeds_dev, seeds, sizeof(uint64_t) * p->batch, cudaMemcpyHostToDevice, st), "seeds");
   DM_CU(draw_signal(p, p->seeds_dev, p->tmpalm, st), "draw signal");
@@ -602,6 +611,7 @@ dm_status dm_constrained_realization(dm_plan *p, const double *d, const uint64_t
   dm_status r = check_ready(p);
   if (r != DM_OK) return r;
   if (!d || !seeds || !s_cr_out) return fail(p, DM_EINVAL, "null buffer");
+  if (p->cov) return fail(p, DM_EINVAL, "constrained realisations take the diagonal noise model");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = 3 * p->npix * p->batch;
   // shat -> tmpmap, ahat -> tmpalm, dhat -> tmpmap2, then tmpmap2 = d - dhat

@@ -87,6 +87,8 @@ struct dm_plan {
   std::vector<dmwf::RingDev> rings_h;
   std::vector<double> cl_h;     // [4][lmax+1]
   bool have_cl = false, have_noise = false;
+  bool cov = false;             // correlated 3x3 noise (dm_set_noise_cov), plan-wide
+  double *wcov = nullptr;       // [npix][6] W = alpha N^{-1} (xx, yy, zz, xy, xz, yz)
   std::vector<double> alpha, t_h;   // per RHS: alpha = min N (observed), T_h = alpha Omega
 
   // schedule
@@ -212,6 +214,8 @@ cudaError_t build_filter_one(dm_plan *p, double lambda, double th, double *coef,
 cudaError_t control_init(dm_plan *p, cudaStream_t st);
 cudaError_t control_step(dm_plan *p, cudaStream_t st);
 cudaError_t prepare_wd(dm_plan *p, const double *d, cudaStream_t st);
+cudaError_t cov_prepare_wd(dm_plan *p, const double *d, cudaStream_t st);  // dm_cov.cu
+cudaError_t cov_ring_stage(dm_plan *p, cudaStream_t st);
 cudaError_t setup_fp32(dm_plan *p);                          // tables and buffers of DM_MIXED_FP32
 cudaError_t copy_s32_to_user(dm_plan *p, double *s_out, cudaStream_t st);
 // anchor residual: r = w (d - s_hi) (or d on observed pixels when s_hi == nullptr),

@@ -27,7 +27,7 @@ EXPORTS = [
     "dm_profile_enable", "dm_profile_read", "dm_measure_alu_peaks", "dm_solve_begin", "dm_solve_iterate",
     "dm_solve_end", "dm_set_refinement", "dm_set_noise_mask_rhs", "dm_server_create", "dm_serve_submit",
     "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores", "dm_set_ring_radix",
-    "dm_set_anchor_precision",
+    "dm_set_anchor_precision", "dm_set_noise_cov",
     "dm_legendre_analysis_noalloc",
 ]
 DM_REQ_WF, DM_REQ_CR = 0, 1
@@ -100,6 +100,7 @@ def lib():
         L.dm_set_precision.argtypes = [vp, ctypes.c_int]
         L.dm_set_spectra.argtypes = [vp, vp]
         L.dm_set_noise_mask.argtypes = [vp, vp, vp]
+        L.dm_set_noise_cov.argtypes = [vp, vp, vp, vp, vp]
         L.dm_set_schedule.argtypes = [vp, ctypes.POINTER(DmSchedule)]
         L.dm_set_forced_iters.argtypes = [vp, vp]
         L.dm_wiener_filter.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -267,6 +268,16 @@ class Plan:
     def set_ring_radix(self, lr):
         """Fixed-size ring transforms of radix 2^lr (3 or 4), or 0 for the generic kernels."""
         self._check(lib().dm_set_ring_radix(self.h, int(lr)))
+
+    def set_noise_cov(self, sigma, rho, mask_t=None, mask_p=None):
+        """Correlated 3x3 noise per pixel with distinct T / P masks (dm_set_noise_cov)."""
+        sg = np.ascontiguousarray(sigma, dtype=np.float64)
+        rh = np.ascontiguousarray(rho, dtype=np.float64)
+        mt = None if mask_t is None else np.ascontiguousarray(mask_t, dtype=np.uint8)
+        mp = None if mask_p is None else np.ascontiguousarray(mask_p, dtype=np.uint8)
+        self._check(lib().dm_set_noise_cov(self.h, sg.ctypes.data, rh.ctypes.data,
+                                           None if mt is None else mt.ctypes.data,
+                                           None if mp is None else mp.ctypes.data))
 
     def set_refinement(self, anchor_every):
         self._check(lib().dm_set_refinement(self.h, int(anchor_every)))

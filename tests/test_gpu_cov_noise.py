@@ -1,0 +1,87 @@
+"""Correlated 3x3 per-pixel noise with distinct temperature and polarisation
+masks (dm_set_noise_cov; Section 2.1 and Appendix B) against the oracle's
+orc_dm_solve_cov, through the C ABI: FP64 and float-float solves at the FP64
+bar (relative L2 <= 1e-10), batches, the free-running Cauchy schedule, and the
+calls the mode rejects."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_helpers import alm_host, dev, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1801_05358_gb300 import dmwf  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _plan(wl, B, **sched):
+    p = dmwf.Plan(wl.nside, wl.lmax, B)
+    p.set_spectra(wl.cl)
+    p.set_noise_cov(wl.sigma, wl.rho, wl.mask, wl.mask_p)
+    p.set_schedule(**sched)
+    return p
+
+
+def _data(orc, wl):
+    return np.stack([wl.data([orc.alm2map(wl.nside, wl.lmax, a)])[0] for a in wl.alm_true])
+
+
+@pytest.mark.parametrize("nside,B,prec", [(8, 1, dmwf.DM_FP64), (16, 3, dmwf.DM_FP64),
+                                          (16, 2, dmwf.DM_FLOAT_FLOAT)])
+def test_cov_fixed_schedule_matches_oracle(orc, nside, B, prec):
+    wl = W.make_cov_workload(list(range(20, 20 + B)), nside, 2 * nside)
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(1000.0, 4)
+    p = _plan(wl, B, lambda0=1000.0, n_levels=4, iters_per_level=4)
+    p.set_precision(prec)
+    s = torch.zeros((B, 3, wl.npix), dtype=torch.float64, device="cuda")
+    a = torch.zeros((B, 3, (wl.lmax + 1) * (wl.lmax + 2) // 2, 2), dtype=torch.float64, device="cuda")
+    st, stats = p.wiener_filter(dev(d), s, a)
+    p.close()
+    assert all(x["iters_total"] == 16 for x in stats)
+    gs, ga = s.cpu().numpy(), alm_host(a, (B, 3, -1))
+    for b in range(B):
+        ref = orc.dm_solve_cov(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d[b], lam,
+                               forced_iters=[4, 4, 4, 4])
+        assert rel(gs[b], ref["s"]) < 1e-10
+        assert rel(ga[b], ref["alm"]) < 1e-10
+
+
+def test_cov_cauchy_schedule_matches_oracle(orc):
+    """Free-running levels (Cauchy 1e-3 -> 1e-5): the same per-level counts."""
+    wl = W.make_cov_workload([30], 8, 16)
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(1000.0, 3)
+    eps = W.eps_schedule(3, 1e-3, 1e-5)
+    ref = orc.dm_solve_cov(8, 16, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d[0], lam, eps=eps)
+    p = _plan(wl, 1, lambda0=1000.0, n_levels=3, iters_per_level=0, eps0=1e-3, eps_final=1e-5, eta=0.0,
+              check_every=1)
+    s = torch.zeros((1, 3, wl.npix), dtype=torch.float64, device="cuda")
+    st, stats = p.wiener_filter(dev(d), s)
+    p.close()
+    assert list(stats[0]["iters_per_level"][:3]) == list(ref["iters_per_level"])
+    assert rel(s.cpu().numpy()[0], ref["s"]) < 1e-10
+
+
+def test_cov_rejections():
+    wl = W.make_cov_workload([31], 4, 8)
+    p = dmwf.Plan(4, 8, 1)
+    p.set_spectra(wl.cl)
+    bad = wl.rho.copy()
+    bad[:, 0] = [0.9, 0.9, -0.9]  # not positive definite
+    with pytest.raises(RuntimeError):
+        p.set_noise_cov(wl.sigma, bad, wl.mask, wl.mask_p)
+    p.set_noise_cov(wl.sigma, wl.rho, wl.mask, wl.mask_p)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    d = torch.zeros((1, 3, wl.npix), dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError):
+        p.wiener_filter(d, torch.zeros_like(d))
+    p.close()
