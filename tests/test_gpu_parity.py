@@ -166,6 +166,24 @@ def test_dm_cauchy_schedule_matches_oracle(orc):
     assert rel(s.cpu().numpy()[0], ref["s"]) < 1e-10
 
 
+def test_dm_cauchy_schedule_nondefault_final_tolerance(orc):
+    """dm_set_schedule's final tolerance reaches every RHS (a plan created with
+    the default 1e-6, then scheduled 1e-3 -> 1e-5): the per-level counts agree
+    with the oracle's."""
+    wl = W.make_workload("nside16", [2, 3], nside=8, lmax=16)
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(1000.0, 3)
+    eps = W.eps_schedule(3, 1e-3, 1e-5)
+    p = make_plan(wl, 2, lambda0=1000.0, n_levels=3, iters_per_level=0, eps0=1e-3, eps_final=1e-5, eta=0.0,
+                  check_every=8)
+    s = torch.zeros((2, 3, wl.npix), dtype=torch.float64, device="cuda")
+    st, stats = p.wiener_filter(dev(d), s)
+    for b in range(2):
+        ref = orc.dm_solve(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.mask, d[b], lam, eps=eps)
+        assert stats[b]["iters_per_level"][:3] == list(ref["iters_per_level"])
+        assert rel(s.cpu().numpy()[b], ref["s"]) < 1e-10
+
+
 def test_cr_inputs_match_oracle(orc):
     """Philox draws, ahat ~ S, shat = Y ahat, dhat = shat + nhat (Section 2.2)."""
     wl = W.make_workload("nside16", [0], nside=8, lmax=16)
