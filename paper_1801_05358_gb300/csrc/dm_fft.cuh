@@ -15,7 +15,10 @@
 //   fft_dit: bit-reversed input  -> natural-order output (Cooley-Tukey)
 // Both compute the forward transform X_k = sum_j x_j e^{-2 pi i jk/M}, and
 // both fuse two radix-2 stages per pass (one closed quadruple per task), so a
-// size-M transform takes ceil(log2 M / 2) barriers.
+// size-M transform takes ceil(log2 M / 2) barriers.  These generic forms take
+// any M; the fixed-size family at the end of this file (fftr_*, radix 8 or
+// 16 per pass in registers, XOR-swizzled slots) produces the same layouts for
+// one compile-time M and serves the iteration's rings of 512 to 4096 points.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -1,13 +1,15 @@
 // dm_ring.cu -- the pixel-space half of a dual messenger iteration, one CTA per
-// (ring, up to four (Stokes component, RHS) lanes):
+// ring (or, in the paired fixed-size kernels, per northern/southern ring pair)
+// and up to sixteen (Stokes component, RHS) lanes:
 //   inverse ring DFT  F_m -> s           (synthesis F, Algorithm 1)
 //   Cauchy partials   ||s - s_prev||^2, ||s||^2   (stopping rule, Section 3.2)
 //   messenger update  t - s = w (d - s)           (Eq. 9, diagonal N)
 //   forward ring DFT  (t - s) -> G_m     (analysis F^dagger, Algorithm 1)
 // A real ring of n pixels is packed as a complex sequence of h = n/2 points.
 //
-// Ring coefficients live in rc[b][f][m][pair][side] (double2): the Legendre
-// kernels read a ring pair (north, south) as one 32-byte item.
+// Ring coefficients live in rc[b][f][m][pair][side] (double2 in the FP64
+// modes, float2 in the mixed mode): the Legendre kernels read a ring pair
+// (north, south) as one item, and so does the paired ring kernel.
 #include <algorithm>
 
 #include "dm_fft.cuh"
