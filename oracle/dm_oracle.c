@@ -30,7 +30,9 @@
  *
  * Functions whose results are pinned by the -m "not gpu" tests: geometry,
  * harmonics, ring DFTs, synthesis/analysis, per-l filter, the messenger
- * update, the level loop, chi^2, Philox and the constrained-realisation draws.
+ * update, the level loop, chi^2, Philox and the constrained-realisation draws,
+ * and the correlated-noise model (Appendix B) with its update, solve and CR
+ * noise draws.
  */
 #include <math.h>
 #include <stdint.h>
@@ -939,5 +941,61 @@ void orc_cr_inputs(int nside, int lmax, const double *cl, const double *sigma, c
     for (long p = 0; p < npix; ++p) {
       long i = f * npix + p;
       dhat[i] = (!mask || mask[p]) ? shat[i] + dhat[i] : 0.0;
+    }
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* Constrained-realisation inputs with the correlated noise model above.       */
+/* Eq. 18 needs nhat drawn with the covariance the solve's precision implies.  */
+/* On a fully observed pixel that is N = Sigma C Sigma: nhat = Sigma x with    */
+/* x = L z, C = L L^T (Cholesky) and z the three normals of orc_draw_noise     */
+/* (the same Philox counters). Where Sigma^{-1} = 0 on some components the     */
+/* precision of the observed block o is (Sigma^{-1} C^{-1} Sigma^{-1})_oo,     */
+/* whose inverse is Sigma_o (C_oo - C_om C_mm^{-1} C_mo) Sigma_o: the          */
+/* covariance of x_o given x_m = 0, drawn as x_o - C_om C_mm^{-1} x_m. Masked  */
+/* components are 0; dhat = shat + nhat on observed components.               */
+/* ------------------------------------------------------------------------ */
+void orc_draw_noise_cov(int nside, const double *sigma, const double *rho, const uint8_t *maskT,
+                        const uint8_t *maskP, uint64_t seed, double *n) {
+  long npix = orc_npix(nside);
+  for (long p = 0; p < npix; ++p) {
+    double z[4];
+    orc_gauss_pair(seed, (uint32_t)p, 0u, 1u, &z[0], &z[1]);
+    orc_gauss_pair(seed, (uint32_t)p, 1u, 1u, &z[2], &z[3]);
+    const double r01 = rho[p], r02 = rho[npix + p], r12 = rho[2 * npix + p];
+    /* Cholesky factor of the correlation matrix, row by row */
+    const double l10 = r01, l20 = r02;
+    const double l11 = sqrt(1.0 - l10 * l10);
+    const double l21 = (r12 - l20 * l10) / l11;
+    const double l22 = sqrt(1.0 - l20 * l20 - l21 * l21);
+    double x[3] = {z[0], l10 * z[0] + l11 * z[1], l20 * z[0] + l21 * z[1] + l22 * z[2]};
+    const int ot = !maskT || maskT[p], op = !maskP || maskP[p];
+    if (!ot && op) { /* m = {I}: C_mm = 1, C_om = (r01, r02) */
+      x[1] -= r01 * x[0];
+      x[2] -= r02 * x[0];
+    } else if (ot && !op) { /* m = {Q, U}: C_mm^{-1} = [[1, -r12], [-r12, 1]] / (1 - r12^2) */
+      const double y1 = (x[1] - r12 * x[2]) / (1.0 - r12 * r12);
+      const double y2 = (x[2] - r12 * x[1]) / (1.0 - r12 * r12);
+      x[0] -= r01 * y1 + r02 * y2;
+    }
+    n[p] = ot ? sigma[p] * x[0] : 0.0;
+    n[npix + p] = op ? sigma[npix + p] * x[1] : 0.0;
+    n[2 * npix + p] = op ? sigma[2 * npix + p] * x[2] : 0.0;
+  }
+}
+
+void orc_cr_inputs_cov(int nside, int lmax, const double *cl, const double *sigma, const double *rho,
+                       const uint8_t *maskT, const uint8_t *maskP, uint64_t seed, double *ahat, double *shat,
+                       double *dhat) {
+  long npix = orc_npix(nside);
+  orc_draw_signal_alm(lmax, cl, seed, ahat);
+  orc_alm2map(nside, lmax, ahat, shat);
+  orc_draw_noise_cov(nside, sigma, rho, maskT, maskP, seed, dhat);
+  for (int f = 0; f < 3; ++f)
+    for (long p = 0; p < npix; ++p) {
+      const int obs = f == 0 ? (!maskT || maskT[p]) : (!maskP || maskP[p]);
+      long i = f * npix + p;
+      dhat[i] = obs ? shat[i] + dhat[i] : 0.0;
     }
 }

@@ -367,6 +367,44 @@ def constrained_realization(nside, lmax, cl, sigma, mask, d, seed, lambdas, eps=
     return r
 
 
+def draw_noise_cov(nside, sigma, rho, maskT, maskP, seed):
+    """nhat ~ N of the correlated noise model (Sigma L z with the Philox normals)."""
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    rh = np.ascontiguousarray(rho, dtype=np.float64)
+    mt, mtp = _mask_ptr(maskT)
+    mp_, mpp = _mask_ptr(maskP)
+    n = np.zeros((3, npix(nside)))
+    lib().orc_draw_noise_cov(nside, _d(sg), _d(rh), mtp, mpp, ctypes.c_uint64(seed), _d(n))
+    return n
+
+
+def cr_inputs_cov(nside, lmax, cl, sigma, rho, maskT, maskP, seed):
+    """(ahat, shat, dhat) of a constrained realisation under the correlated noise model."""
+    c = np.ascontiguousarray(cl, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    rh = np.ascontiguousarray(rho, dtype=np.float64)
+    mt, mtp = _mask_ptr(maskT)
+    mp_, mpp = _mask_ptr(maskP)
+    ahat = np.zeros((3, nalm(lmax)), dtype=np.complex128)
+    shat = np.zeros((3, npix(nside)))
+    dhat = np.zeros((3, npix(nside)))
+    lib().orc_cr_inputs_cov(nside, lmax, _d(c), _d(sg), _d(rh), mtp, mpp, ctypes.c_uint64(seed),
+                            _d(ahat.view(np.float64)), _d(shat), _d(dhat))
+    return ahat, shat, dhat
+
+
+def constrained_realization_cov(nside, lmax, cl, sigma, rho, maskT, maskP, d, seed, lambdas, eps=None,
+                                forced_iters=None, max_iter=100000):
+    """s_CR = W(d - dhat) + shat (Eq. 19) under the correlated noise model."""
+    ahat, shat, dhat = cr_inputs_cov(nside, lmax, cl, sigma, rho, maskT, maskP, seed)
+    r = dm_solve_cov(nside, lmax, cl, sigma, rho, maskT, maskP, np.asarray(d) - dhat, lambdas, eps, forced_iters,
+                     max_iter)
+    r["s_cr"] = r["s"] + shat
+    r["alm_cr"] = r["alm"] + ahat
+    r["shat"], r["dhat"], r["ahat"] = shat, dhat, ahat
+    return r
+
+
 def level_lambdas(lambda0, nlev):
     """Geometric cooling lambda_k = lambda0^(1 - k/(nlev-1)), last level exactly 1."""
     if nlev == 1:

@@ -12,7 +12,13 @@ Appendix B).
 - masked components: t = s there, and their data never enter;
 - uncorrelated noise with one mask: the same solve as the diagonal oracle;
 - the converged loop against a dense Wiener-filter solve with the
-  block-diagonal N^{-1} at nside 4."""
+  block-diagonal N^{-1} at nside 4;
+- constrained-realisation noise draws (Eq. 18): uncorrelated with one mask
+  they are the diagonal draws; their sample covariance is the inverse of the
+  observed block of N^{-1} (Sigma C Sigma on fully observed pixels, the
+  conditional covariance on partially masked ones); the CR inputs are the
+  signal draw plus that noise on observed components; the fluctuation
+  shat - W dhat has the posterior covariance at nside 4."""
 import numpy as np
 import pytest
 
@@ -207,3 +213,88 @@ def test_masked_data_never_enter_the_solve(orc):
     a = orc.dm_solve_cov(8, 16, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d, lam, forced_iters=[2, 2])
     b = orc.dm_solve_cov(8, 16, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d2, lam, forced_iters=[2, 2])
     assert np.array_equal(a["s"], b["s"]) and np.array_equal(a["alm"], b["alm"])
+
+
+def test_cov_cr_draw_reduces_to_the_diagonal_draw(orc):
+    """rho = 0 and one mask: the correlated CR noise draw is the diagonal one,
+    value for value (same Philox normals, L = 1)."""
+    wl = W.make_workload("nside16", [0], nside=16, lmax=32)
+    rho = np.zeros_like(wl.sigma)
+    a = orc.draw_noise_cov(16, wl.sigma, rho, wl.mask, wl.mask, 91)
+    b = orc.draw_noise(16, wl.sigma, wl.mask, 91)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("case", ["observed", "t_masked", "p_masked"])
+def test_cov_cr_draw_covariance_is_inverse_observed_precision(orc, case):
+    """Over 786432 pixels of one noise model the sample covariance of the
+    observed components is ((Sigma^{-1} C^{-1} Sigma^{-1})_oo)^{-1}, from
+    numpy's inverses; it differs from the marginal Sigma_o C_oo Sigma_o on
+    partially masked pixels by far more than the sampling error."""
+    nside = 256
+    n = 12 * nside * nside
+    sd = np.array([1.0, 1.5, 0.7])
+    r = np.array([0.5, -0.4, 0.3])
+    sigma = np.tile(sd[:, None], (1, n))
+    rho = np.tile(r[:, None], (1, n))
+    mt = np.full(n, case != "t_masked", np.uint8)
+    mp = np.full(n, case != "p_masked", np.uint8)
+    x = orc.draw_noise_cov(nside, sigma, rho, mt, mp, 17)
+    o = {"observed": [0, 1, 2], "t_masked": [1, 2], "p_masked": [0]}[case]
+    m = [i for i in range(3) if i not in o]
+    assert not x[m].any()
+    C = _corr(rho[:, :1])[0]
+    N = np.diag(sd) @ C @ np.diag(sd)
+    ref = np.linalg.inv(np.linalg.inv(N)[np.ix_(o, o)])
+    emp = np.atleast_2d(np.cov(x[o]))
+    tol = 6 * np.sqrt((np.outer(np.diag(ref), np.diag(ref)) + ref ** 2) / n)
+    assert np.all(np.abs(emp - ref) < tol)
+    assert np.all(np.abs(x[o].mean(axis=1)) < 6 * np.sqrt(np.diag(ref) / n))
+    if m:
+        marginal = N[np.ix_(o, o)]
+        assert np.max(np.abs(marginal - ref) - tol) > 0
+
+
+def test_cov_cr_inputs_consistent(orc):
+    """ahat and shat are the signal draw of the diagonal CR inputs (the same
+    seed); dhat = shat + nhat on observed components and 0 on masked ones."""
+    wl = W.make_cov_workload([5], 4, 8)
+    ahat, shat, dhat = orc.cr_inputs_cov(4, 8, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, 77)
+    a0, s0, _ = orc.cr_inputs(4, 8, wl.cl, wl.sigma[0:1].repeat(3, 0), wl.mask, 77)
+    assert np.array_equal(ahat, a0) and np.array_equal(shat, s0)
+    assert np.allclose(shat, orc.alm2map(4, 8, ahat), atol=1e-14)
+    nh = orc.draw_noise_cov(4, wl.sigma, wl.rho, wl.mask, wl.mask_p, 77)
+    obs = np.stack([wl.mask, wl.mask_p, wl.mask_p]).astype(bool)
+    assert np.allclose(dhat, np.where(obs, shat + nh, 0.0), atol=1e-14)
+    assert np.all(dhat[~obs] == 0)
+
+
+@pytest.mark.slow
+def test_cov_fluctuation_covariance_is_posterior(orc):
+    """f = ahat - W dhat has <f f^T> = (S^{-1} + Y^T N^{-1} Y)^{-1} (Eq. 18)
+    with the block-diagonal N^{-1} and distinct masks: the mean Mahalanobis
+    norm of f under that covariance equals the dimension."""
+    nside, lmax = 4, 8
+    cl, params_all, sigma, _, z, phi = _dense_problem(nside, lmax, 3)
+    npix = z.size
+    rng = np.random.default_rng(21)
+    rho = rng.uniform(-0.3, 0.3, (3, npix))
+    mask_t = (np.abs(z) > 0.25).astype(np.uint8)
+    mask_p = (np.abs(z - 0.1) > 0.2).astype(np.uint8)
+    ninv = orc.cov_ninv(sigma, rho, mask_t, mask_p)
+    params = [p for p in params_all if not (p[0] == 0 and p[1] == 0)]
+    Y = dense_synthesis(nside, lmax, z, phi, params)
+    Nd = np.zeros((3 * npix, 3 * npix))
+    for i in range(3):
+        for j in range(3):
+            Nd[i * npix + np.arange(npix), j * npix + np.arange(npix)] = ninv[:, i, j]
+    H = _prior_precision(cl, params, 0.0) + Y.T @ Nd @ Y
+    Wmat = np.linalg.solve(H, Y.T @ Nd)
+    K = 400
+    q = []
+    for seed in range(K):
+        ahat, _, dhat = orc.cr_inputs_cov(nside, lmax, cl, sigma, rho, mask_t, mask_p, 2000 + seed)
+        f = alm_to_params(ahat, params, lmax) - Wmat @ dhat.reshape(-1)
+        q.append(f @ H @ f)
+    n = len(params)
+    assert abs(np.mean(q) - n) < 5 * np.sqrt(2.0 * n / K)
