@@ -272,10 +272,17 @@ __global__ void __launch_bounds__(128, 1) k_syn_tc(const unsigned char *__restri
                  (uint32_t)(2 * tileB), &full[s]);
     };
     for (int u = 0; u < NS && u < nunits; ++u) issue(u);
+    // units whose copies were issued, whose operands were waited for, whose MMAs were committed
+    int issued = min(NS, nunits), landed = 0, committed = 0;
+    bool bad = false;
     for (int u = 0; u < nunits; ++u) {
       const int s = u % NS, c = u / UPS;
       unsigned char *Abuf = sm + s * stage, *Bbuf = Abuf + uabytes;
-      mbar_wait(&full[s], (u / NS) & 1, err);
+      if (!mbar_wait(&full[s], (u / NS) & 1, err)) {
+        bad = true;
+        break;
+      }
+      landed = u + 1;
       fence_after_sync();
       const uint32_t acc = c > 0 ? 1u : 0u;
       if (PART == 0) {
@@ -287,13 +294,23 @@ __global__ void __launch_bounds__(128, 1) k_syn_tc(const unsigned char *__restri
         mma3(d, Abuf + 2 * TILE_A, Bbuf + 2 * tileB, tileB, idesc, 1u);
       }
       commit(&done[s]);
+      committed = u + 1;
       // refill the stage of unit u - 1 (its MMAs precede those just issued)
       if (u >= 1 && u - 1 + NS < nunits) {
-        mbar_wait(&done[(u - 1) % NS], ((u - 1) / NS) & 1, err);
+        if (!mbar_wait(&done[(u - 1) % NS], ((u - 1) / NS) & 1, err)) {
+          bad = true;
+          break;
+        }
         issue(u - 1 + NS);
+        issued = u + NS;
       }
     }
-    mbar_wait(&done[(nunits - 1) % NS], ((nunits - 1) / NS) & 1, err);
+    // after a failed wait no more work is issued; copies still in flight (one
+    // phase per stage at most) land before the CTA's shared memory goes away
+    if (bad)
+      for (int v = landed; v < issued; ++v) mbar_wait(&full[v % NS], (v / NS) & 1, err);
+    // the last commit covers every MMA issued before it
+    if (committed > 0) mbar_wait(&done[(committed - 1) % NS], ((committed - 1) / NS) & 1, err);
   }
   __syncthreads();
   fence_after_sync();
@@ -431,6 +448,7 @@ __global__ void __launch_bounds__(ANA_THREADS, 1) k_ana_tc(const unsigned char *
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t bars[3 * ANA_MAX_STAGES + 1];
   __shared__ uint32_t tslot;
+  __shared__ int cta_bad;  // some wait of this CTA gave up
   uint64_t *full_a = bars, *full_b = bars + ANA_MAX_STAGES, *done = bars + 2 * ANA_MAX_STAGES;
   uint64_t *fin = bars + 3 * ANA_MAX_STAGES;  // one phase: every MMA of the CTA has completed
   const int m = blockIdx.z, par = blockIdx.y;
@@ -456,6 +474,7 @@ __global__ void __launch_bounds__(ANA_THREADS, 1) k_ana_tc(const unsigned char *
       mbar_init(&done[i], 1);
     }
     mbar_init(fin, 1);
+    cta_bad = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(&tslot, ncols);
@@ -465,6 +484,7 @@ __global__ void __launch_bounds__(ANA_THREADS, 1) k_ana_tc(const unsigned char *
   const uint32_t tbase = tslot;
   const int64_t base = abase(lmax, m);
   const int nsteps = (npairs + 15) / 16;
+  int issued = 0;  // K steps whose A copies the producer issued
   if (warp < nconv * ngroups) {
     const int grp = warp / nconv, task = tid - grp * 32 * nconv;
     const bool has = task < ntask;
@@ -472,7 +492,10 @@ __global__ void __launch_bounds__(ANA_THREADS, 1) k_ana_tc(const unsigned char *
     if (has && grp < nsteps) load_ana_b<PART>(task, rc, m, grp, mmax, npairs, v);
     for (int c = grp; c < nsteps; c += ngroups) {
       const int s = c % S, k = c / S;
-      if (c >= S) mbar_wait(&done[s], (k - 1) & 1, err);
+      if (c >= S && !mbar_wait(&done[s], (k - 1) & 1, err)) {
+        cta_bad = 1;
+        break;
+      }
       if (has) {
         convert_ana_b<PART>(task, sm + s * stage + LT * abytes, tileB, par, v);
         if (c + ngroups < nsteps) load_ana_b<PART>(task, rc, m, c + ngroups, mmax, npairs, v);
@@ -485,17 +508,23 @@ __global__ void __launch_bounds__(ANA_THREADS, 1) k_ana_tc(const unsigned char *
     const int64_t tstride = (int64_t)nsteps * abytes;  // next l tile
     for (int c = 0; c < nsteps; ++c) {
       const int s = c % S, k = c / S;
-      if (c >= S) mbar_wait(&done[s], (k - 1) & 1, err);
+      if (c >= S && !mbar_wait(&done[s], (k - 1) & 1, err)) {
+        cta_bad = 1;
+        break;
+      }
       mbar_expect_tx(&full_a[s], (uint32_t)(nt * abytes));
       for (int j = 0; j < nt; ++j)
         bulk_g2s(sm + s * stage + j * abytes, tabm + j * tstride + (int64_t)c * abytes, (uint32_t)abytes, &full_a[s]);
+      issued = c + 1;
     }
   } else if (warp == 9 && lane == 0) {
     const uint32_t idesc = idesc_bf16(128, NC);
     for (int c = 0; c < nsteps; ++c) {
       const int s = c % S, k = c / S;
-      mbar_wait(&full_a[s], k & 1, err);
-      mbar_wait(&full_b[s], k & 1, err);
+      if (!mbar_wait(&full_a[s], k & 1, err) || !mbar_wait(&full_b[s], k & 1, err)) {
+        cta_bad = 1;
+        break;
+      }
       fence_after_sync();
       const unsigned char *Abuf = sm + s * stage, *Bbuf = Abuf + LT * abytes;
       const uint32_t acc = c > 0 ? 1u : 0u;
@@ -513,6 +542,7 @@ __global__ void __launch_bounds__(ANA_THREADS, 1) k_ana_tc(const unsigned char *
     // A stage barrier may be several phases behind a warp that did not
     // convert; fin completes exactly once.
     mbar_wait(fin, 0, err);
+    __syncwarp();  // converged for the warp-wide tcgen05.ld
     fence_after_sync();
     const int row = warp * 32 + lane;
     const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
@@ -539,6 +569,13 @@ __global__ void __launch_bounds__(ANA_THREADS, 1) k_ana_tc(const unsigned char *
       }
     }
   }
+  // Step c was issued only after the MMAs of step c - S, which waited for its
+  // copies, so each stage has at most its last issued phase outstanding.  When
+  // any wait of the CTA gave up, those copies land before its shared memory
+  // goes away.
+  __syncthreads();
+  if (cta_bad && warp == 8 && lane == 0)
+    for (int c = max(0, issued - S); c < issued; ++c) mbar_wait(&full_a[c % S], (c / S) & 1, err);
   tc_teardown(tbase, ncols);
 }
 

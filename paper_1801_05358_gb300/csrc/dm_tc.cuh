@@ -64,10 +64,24 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
 }
 
-// Bounded wait on an mbarrier phase; returns false (and sets *err) when it gives up.
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// A wait gives up after this much wall time; a normal one lasts microseconds.
+constexpr uint64_t MBAR_TIMEOUT_NS = 1000000000ull;
+
+// Bounded wait on an mbarrier phase. It gives up after MBAR_TIMEOUT_NS of wall
+// time (%globaltimer, read every 16 tries), or after 1 ms once *err shows that
+// another wait has already given up, so that a failure ends every CTA quickly;
+// 2^30 tries bound it should the timer not advance. Returns false (and sets
+// *err, when given) when it gives up.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t phase, int *err) {
   const uint32_t a = smem_u32(mbar);
-  for (long it = 0; it < (1L << 26); ++it) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0; it < (1u << 30); ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -77,6 +91,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t phase, int *e
         : "r"(a), "r"(phase)
         : "memory");
     if (ok) return true;
+    if ((it & 15u) == 15u) {
+      const uint64_t now = globaltimer_ns();
+      if (t0 == 0) t0 = now;
+      const uint64_t dt = now - t0;
+      if (dt > MBAR_TIMEOUT_NS) break;
+      if (err && dt > 1000000ull && *(volatile int *)err) break;
+    }
   }
   if (err) atomicExch(err, 1);
   return false;
