@@ -360,8 +360,11 @@ typedef struct {
 } dm_server_info_t;
 
 dm_status dm_server_create(const dm_server_config *cfg, dm_server **out);
-/* Queue a request; *ticket identifies it.  DM_EINVAL for a bad request,
- * DM_EBUSY when the queue is full. */
+/* Queue a request; *ticket identifies it.  DM_EINVAL for a bad request (sizes,
+ * kind, tolerance, sigma not finite and > 0 on an observed pixel, or a mask
+ * with no observed pixel), DM_EBUSY when the queue is full.  A request the
+ * plan setup rejects later completes with that status; one that can never fit
+ * the memory budget completes with DM_ENOMEM. */
 dm_status dm_serve_submit(dm_server *srv, const dm_request *req, uint64_t *ticket);
 /* DM_OK and *out once the request completed (the ticket is then released),
  * DM_EAGAIN while it is queued or running, DM_EINVAL for an unknown ticket. */

@@ -21,6 +21,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -179,7 +180,7 @@ struct dm_server {
   bool stop = false;
   std::thread worker;
   std::string err;
-  int64_t rounds = 0, admitted = 0, retired = 0;
+  std::atomic<int64_t> rounds{0}, admitted{0}, retired{0};  // written by the worker, read by dm_server_info
 };
 
 namespace {
@@ -201,7 +202,10 @@ dm_precision request_prec(const dm_server *S, const Request &r) {
   return (S->cfg.strict_tol > 0.0 && r.tol < S->cfg.strict_tol) ? S->cfg.strict_prec : S->cfg.prec;
 }
 
-Pool *make_pool(dm_server *S, const Request &r) {
+// A new pool for r, or nullptr with *why = DM_ENOMEM when the budget (or the
+// device) has no room for it, else the status of the call that rejected r.
+Pool *make_pool(dm_server *S, const Request &r, dm_status *why) {
+  *why = DM_ENOMEM;
   const int slots = S->cfg.slots_per_plan;
   const dm_precision prec = request_prec(S, r);
   size_t need = estimate_bytes(r.nside, r.lmax, slots, prec);
@@ -226,18 +230,27 @@ Pool *make_pool(dm_server *S, const Request &r) {
   pool->lmax = r.lmax;
   pool->cl_hash = hash_bytes(r.cl.data(), r.cl.size() * sizeof(double));
   pool->prec = prec;
-  if (dm_plan_create(r.nside, r.lmax, slots, &pool->plan) != DM_OK) return nullptr;
+  dm_status rs = dm_plan_create(r.nside, r.lmax, slots, &pool->plan);
+  if (rs != DM_OK) {
+    *why = rs == DM_EINVAL ? DM_EINVAL : DM_ENOMEM;
+    return nullptr;
+  }
   dm_plan *p = pool->plan;
   dm_schedule sc = S->cfg.sched;
   sc.iters_per_level = 0;
-  if (dm_set_schedule(p, &sc) != DM_OK || dm_set_spectra(p, r.cl.data()) != DM_OK ||
-      dm_set_noise_mask(p, r.sigma.data(), r.has_mask ? r.mask.data() : nullptr) != DM_OK ||
-      dm_set_precision(p, prec) != DM_OK) {
+  if ((rs = dm_set_schedule(p, &sc)) != DM_OK || (rs = dm_set_spectra(p, r.cl.data())) != DM_OK ||
+      (rs = dm_set_noise_mask(p, r.sigma.data(), r.has_mask ? r.mask.data() : nullptr)) != DM_OK ||
+      (rs = dm_set_precision(p, prec)) != DM_OK) {
     dm_plan_destroy(p);
+    *why = rs;
     return nullptr;
   }
   p->anchor_every = S->cfg.anchor_every > 0 ? S->cfg.anchor_every : 256;
-  cudaStreamCreateWithFlags(&pool->stream, cudaStreamNonBlocking);
+  if (cudaStreamCreateWithFlags(&pool->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    dm_plan_destroy(p);
+    *why = DM_ECUDA;
+    return nullptr;
+  }
   pool->slots.resize(slots);
   k_mark_done<<<(slots + 127) / 128, 128, 0, pool->stream>>>(p->state, slots);
   p->session = true;
@@ -357,14 +370,15 @@ void worker_main(dm_server *S) {
           std::unique_ptr<Request> req = std::move(S->pending[idx]);
           S->pending.erase(S->pending.begin() + idx);
           lk.unlock();
-          pool = make_pool(S, *req);
+          dm_status why = DM_OK;
+          pool = make_pool(S, *req, &why);
           lk.lock();
           if (!pool) {
             bool busy_elsewhere = false;
             for (auto &q : S->pools) busy_elsewhere = busy_elsewhere || q->busy() > 0;
-            if (!busy_elsewhere) {  // can never fit: fail the request
+            if (why != DM_ENOMEM || !busy_elsewhere) {  // rejected, or can never fit: fail the request
               dm_result res{};
-              res.status = DM_ENOMEM;
+              res.status = why;
               res.latency_ms = ms_since(req->t_submit);
               S->done[req->ticket] = res;
             } else {                // retry once memory frees up
@@ -475,13 +489,16 @@ dm_status dm_serve_submit(dm_server *S, const dm_request *q, uint64_t *ticket) {
       !q->s_out || (q->kind != DM_REQ_WF && q->kind != DM_REQ_CR) || !(q->tol > 0.0))
     return DM_EINVAL;
   const int64_t npix = 12LL * q->nside * q->nside;
+  int64_t observed = 0;
   for (int64_t i = 0; i < npix; ++i) {
     if (q->mask && !q->mask[i]) continue;
+    ++observed;
     for (int f = 0; f < 3; ++f) {
       const double s = q->sigma[f * npix + i];
       if (!(s > 0.0) || !std::isfinite(s)) return DM_EINVAL;
     }
   }
+  if (observed == 0) return DM_EINVAL;  // the mask leaves nothing to filter
   auto r = std::make_unique<Request>();
   r->nside = q->nside;
   r->lmax = q->lmax;
@@ -542,9 +559,9 @@ dm_status dm_server_info(dm_server *S, dm_server_info_t *out) {
   out->busy_slots = busy;
   out->pools = (int64_t)S->pools.size();
   out->bytes_reserved = (int64_t)S->used;
-  out->rounds = S->rounds;
-  out->admitted = S->admitted;
-  out->retired = S->retired;
+  out->rounds = S->rounds.load();
+  out->admitted = S->admitted.load();
+  out->retired = S->retired.load();
   return DM_OK;
 }
 
