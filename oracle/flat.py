@@ -1,0 +1,138 @@
+"""Flat-sky dual messenger oracle: the paper's own setting (Section 2.1,
+Eqs. 12-16, Algorithm 1) on a square patch of side L with N x N pixels.
+
+TEST INFRASTRUCTURE ONLY: tests/ call it, and the CUDA product path never
+imports it.  Plain numpy in float64; numpy's FFT is the only library step.
+
+Conventions:
+
+* pixel (row i, column j) sits at x = j L / N, y = i L / N (axis 0 is y,
+  axis 1 is x) and has area Omega_p = (L / N)^2;
+* a mode of integer wavenumber (k_x, k_y) in numpy FFT order has
+  l = 2 pi k / L; phi_l is the angle between l and the l_x axis;
+* F^dagger (analysis): a_l = Omega_p sum_x m(x) e^{-i l.x}; F (synthesis):
+  m(x) = L^-2 sum_l a_l e^{i l.x}.  F^dagger F is the identity on the harmonic
+  space, the exact inverse that Algorithm 1 writes as sigma^-1 F^dagger;
+* temperature a^T = F^dagger I; polarisation by the rotation of Eqs. 13-16,
+  Q = E cos 2phi - B sin 2phi and U = E sin 2phi + B cos 2phi per mode, and its
+  inverse E = Q cos 2phi + U sin 2phi, B = -Q sin 2phi + U cos 2phi;
+* the Nyquist row and column of an even N (k_x or k_y = -N/2) are not part of
+  the harmonic space: a mode there is its own conjugate partner, so the
+  rotation by the angle of l could not keep real fields real.  Analysis
+  drops them;
+* <|a_l|^2> = L^2 C_|l| for a patch of area L^2, and the noise of a pixel
+  with variance alpha has Fourier power L^2 Omega_p alpha.  So the per-mode
+  filter takes C_l and T_h = alpha Omega_p, as on the sphere.
+
+Because F^dagger F = 1 here, the iteration is Algorithm 1 as printed:
+a = (S-bar + U)(S-bar + xi)^-1 F^dagger t, s = F a, t = (1 - w) s + w d with
+w = alpha / N per pixel-component (0 where masked).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def geometry(N: int, L: float):
+    """(l_x, l_y, phi, keep) per mode of an N x N grid of side L; keep is False
+    on the Nyquist row and column of an even N."""
+    k = np.fft.fftfreq(N, d=1.0 / N)
+    ky, kx = np.meshgrid(k, k, indexing="ij")
+    lx, ly = 2.0 * np.pi * kx / L, 2.0 * np.pi * ky / L
+    phi = np.arctan2(ly, lx)
+    keep = np.ones((N, N), bool)
+    if N % 2 == 0:
+        keep &= (kx != -(N // 2)) & (ky != -(N // 2))
+    return lx, ly, phi, keep
+
+
+def analysis(maps: np.ndarray, L: float) -> np.ndarray:
+    """(I, Q, U) maps [3, N, N] -> (T, E, B) Fourier coefficients [3, N, N]."""
+    N = maps.shape[-1]
+    _, _, phi, keep = geometry(N, L)
+    h = (L / N) ** 2 * np.fft.fft2(maps, axes=(-2, -1))
+    c, s = np.cos(2.0 * phi), np.sin(2.0 * phi)
+    t = h[0]
+    e = h[1] * c + h[2] * s
+    b = -h[1] * s + h[2] * c
+    return np.stack([t, e, b]) * keep
+
+
+def synthesis(alm: np.ndarray, L: float) -> np.ndarray:
+    """(T, E, B) Fourier coefficients [3, N, N] -> real (I, Q, U) maps.  The
+    coefficients of real fields are Hermitian; the imaginary part the inverse
+    FFT leaves is rounding and is dropped."""
+    N = alm.shape[-1]
+    _, _, phi, keep = geometry(N, L)
+    a = alm * keep
+    c, s = np.cos(2.0 * phi), np.sin(2.0 * phi)
+    h = np.stack([a[0], a[1] * c - a[2] * s, a[1] * s + a[2] * c])
+    return (np.fft.ifft2(h, axes=(-2, -1)) * (N * N / L ** 2)).real
+
+
+def filter_coefs(S: np.ndarray, mu: float, th: float) -> np.ndarray:
+    """Per-mode filter (S-bar + U)(S-bar + xi)^-1 of Algorithm 1 with
+    S-bar = max(S_e - mu, 0) on the eigenvalues S_e of the mode's 3x3 block
+    (Eq. 10), so that S-bar + U = max(S_e, mu) and S-bar + xi = that + T_h.
+    Returns [4, N, N]: the symmetric TE block (f_TT, f_TE, f_EE) and f_BB."""
+    tt, ee, bb, te = S
+    blk = np.stack([np.stack([tt, te], -1), np.stack([te, ee], -1)], -2)  # [N, N, 2, 2]
+    e, v = np.linalg.eigh(blk)
+    sp = np.maximum(np.maximum(e, 0.0), mu)
+    f = sp / (sp + th)
+    F = np.einsum("...ik,...k,...jk->...ij", v, f, v)
+    sb = np.maximum(np.maximum(bb, 0.0), mu)
+    return np.stack([F[..., 0, 0], F[..., 0, 1], F[..., 1, 1], sb / (sb + th)])
+
+
+def apply_filter(coef: np.ndarray, a: np.ndarray) -> np.ndarray:
+    return np.stack([coef[0] * a[0] + coef[1] * a[1], coef[1] * a[0] + coef[2] * a[1], coef[3] * a[2]])
+
+
+def weights(sigma: np.ndarray, mask_t: np.ndarray, mask_p: np.ndarray):
+    """(alpha, w): alpha = min N over observed pixel-components (T = alpha 1,
+    Section 2), w = alpha / N there and 0 where masked (N^-1 = 0)."""
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    var = sigma ** 2
+    alpha = var[obs].min()
+    return alpha, np.where(obs, alpha / np.where(obs, var, 1.0), 0.0)
+
+
+def dm_solve(d, sigma, mask_t, mask_p, S, L, lambdas, eps=None, forced_iters=None, max_iter=100000):
+    """Algorithm 1 on the flat patch.  d, sigma [3, N, N]; masks [N, N] (1 =
+    observed); S [4, N, N] spectra per mode; lambdas the cooling levels
+    (lambda = xi / T_h, mu = (lambda - 1) T_h); per level either a Cauchy
+    threshold eps[k] on ||s_i - s_{i-1}|| / ||s_i|| or a fixed count
+    forced_iters[k].  Returns s, alm and the iteration record."""
+    d = np.asarray(d, dtype=np.float64)
+    N = d.shape[-1]
+    alpha, w = weights(sigma, mask_t, mask_p)
+    th = alpha * (L / N) ** 2
+    obs = w > 0
+    s = np.zeros_like(d)
+    t = np.where(obs, d, 0.0)
+    a = np.zeros((3, N, N), np.complex128)
+    iters_per_level, cauchy = [], []
+    it = 0
+    for k, lam in enumerate(lambdas):
+        coef = filter_coefs(S, (lam - 1.0) * th, th)
+        nk = 0
+        while True:
+            if forced_iters is not None and nk >= forced_iters[k]:
+                break
+            if forced_iters is None and it >= max_iter:
+                break
+            a = apply_filter(coef, analysis(t, L))
+            sn = synthesis(a, L)
+            ss = np.sum(sn * sn)
+            c = np.sqrt(np.sum((sn - s) ** 2) / ss) if ss > 0 else 0.0
+            s = sn
+            t = (1.0 - w) * s + w * d
+            cauchy.append(c)
+            it += 1
+            nk += 1
+            if forced_iters is None and c < eps[k]:
+                break
+        iters_per_level.append(nk)
+    return {"s": s, "alm": a, "iters": it, "iters_per_level": np.array(iters_per_level),
+            "cauchy": np.array(cauchy), "alpha": alpha}

@@ -1,0 +1,185 @@
+"""Pins of the flat-sky oracle (oracle/flat.py; Section 2.1, Eqs. 12-16,
+Algorithm 1), the paper's own setting on a square patch.
+
+- analysis against the direct sums a_l = Omega_p sum_x m(x) e^{-i l.x} at
+  N = 6 (brute force), its polarisation part in the spin-2 form
+  E + iB = e^{-2i phi}(Q + iU) of the rotation of Eqs. 15-16, and the Nyquist
+  row and column dropped;
+- synthesis is the exact inverse of analysis on the harmonic space, and
+  synthesis after analysis is a projection;
+- E and B as gradient and curl modes: Q = (dx^2 - dy^2) psi, U = 2 dx dy psi
+  is pure E with E = F^dagger[laplacian psi], and Q = -2 dx dy chi,
+  U = (dx^2 - dy^2) chi is pure B with B = F^dagger[laplacian chi]
+  (derivatives taken spectrally, x along axis 1);
+- parity: under the mirror x -> -x, (Q, U) -> (Q, -U), E is even and B odd;
+- the first iteration is the per-mode filter of F^dagger d, and with
+  homogeneous unmasked noise (w = 1) it is already the fixed point;
+- the converged loop against the textbook pixel-space Wiener filter
+  S (S + N)^-1 d on the observed components, with S built densely from plane
+  waves, at N = 8 with distinct T and P masks, at lambda = 1 and 40."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import flat as F
+
+L = 10.0 * W.DEG
+
+
+def _random_maps(N, seed):
+    return np.random.default_rng(seed).standard_normal((3, N, N))
+
+
+def test_analysis_is_the_direct_sum():
+    N = 6
+    m = _random_maps(N, 1)
+    got = F.analysis(m, L)
+    om = (L / N) ** 2
+    k = np.fft.fftfreq(N, d=1.0 / N)
+    iy, ix = np.mgrid[0:N, 0:N]
+    x, y = ix * L / N, iy * L / N
+    for a in range(N):
+        for b in range(N):
+            ly, lx = 2 * np.pi * k[a] / L, 2 * np.pi * k[b] / L
+            if k[a] == -N // 2 or k[b] == -N // 2:
+                assert np.all(got[:, a, b] == 0)
+                continue
+            ph = np.exp(-1j * (lx * x + ly * y))
+            h = om * np.array([np.sum(m[f] * ph) for f in range(3)])
+            assert abs(got[0, a, b] - h[0]) < 1e-13
+            phi = np.arctan2(ly, lx)
+            eb = np.exp(-2j * phi) * (h[1] + 1j * h[2])  # E + iB for real coefficients E, B
+            # E and B are complex here; split E + iB = e^{-2i phi}(Q + iU) into its
+            # two linear parts with the conjugate relation E - iB = e^{2i phi}(Q - iU)
+            ebc = np.exp(2j * phi) * (h[1] - 1j * h[2])
+            e, bb = (eb + ebc) / 2, (eb - ebc) / 2j
+            assert abs(got[1, a, b] - e) < 1e-13 and abs(got[2, a, b] - bb) < 1e-13
+
+
+def test_synthesis_inverts_analysis():
+    N = 32
+    a = F.analysis(_random_maps(N, 2), L)
+    m = F.synthesis(a, L)
+    assert np.max(np.abs(F.analysis(m, L) - a)) < 1e-13 * np.max(np.abs(a))
+    m2 = F.synthesis(F.analysis(m, L), L)
+    assert np.max(np.abs(m2 - m)) < 1e-13 * np.max(np.abs(m))
+    # a map with Nyquist content is changed by the projection, but only there
+    r = _random_maps(N, 3)
+    pr = F.synthesis(F.analysis(r, L), L)
+    resid = F.analysis(r - pr, L)
+    assert np.max(np.abs(resid)) < 1e-13 * np.max(np.abs(F.analysis(r, L)))
+
+
+def _spectral_derivs(psi, N):
+    k = 2 * np.pi * np.fft.fftfreq(N, d=1.0 / N) / L
+    ky, kx = np.meshgrid(k, k, indexing="ij")
+    h = np.fft.fft2(psi)
+    d = lambda f: np.fft.ifft2(f * h).real
+    return d(-kx * kx), d(-ky * ky), d(-kx * ky)  # dxx, dyy, dxy
+
+
+def _smooth_field(N, seed):
+    """A real field without Nyquist content."""
+    r = np.random.default_rng(seed).standard_normal((N, N))
+    h = np.fft.fft2(r) * ~W.flat_nyquist(N)
+    return np.fft.ifft2(h).real
+
+
+@pytest.mark.parametrize("N", [16, 33])
+def test_gradient_and_curl_fields_are_pure_e_and_b(N):
+    psi, chi = _smooth_field(N, 4), _smooth_field(N, 5)
+    pxx, pyy, pxy = _spectral_derivs(psi, N)
+    cxx, cyy, cxy = _spectral_derivs(chi, N)
+    lap = lambda f: F.analysis(np.stack([f, 0 * f, 0 * f]), L)[0]
+    zero = np.zeros((N, N))
+    ae = F.analysis(np.stack([zero, pxx - pyy, 2 * pxy]), L)
+    ab = F.analysis(np.stack([zero, -2 * cxy, cxx - cyy]), L)
+    ref_e, ref_b = lap(pxx + pyy), lap(cxx + cyy)
+    scale = np.max(np.abs(ref_e))
+    assert np.max(np.abs(ae[1] - ref_e)) < 1e-12 * scale
+    assert np.max(np.abs(ae[2])) < 1e-12 * scale
+    assert np.max(np.abs(ab[2] - ref_b)) < 1e-12 * np.max(np.abs(ref_b))
+    assert np.max(np.abs(ab[1])) < 1e-12 * np.max(np.abs(ref_b))
+
+
+def test_mirror_parity_of_e_and_b():
+    N = 24
+    m = _random_maps(N, 6)
+    flip = lambda f: np.roll(f[..., ::-1], 1, axis=-1)  # x_j -> -x_j (mod L), also k_x -> -k_x
+    mm = np.stack([flip(m[0]), flip(m[1]), -flip(m[2])])
+    a, am = F.analysis(m, L), F.analysis(mm, L)
+    assert np.max(np.abs(am[0] - flip(a[0]))) < 1e-13
+    assert np.max(np.abs(am[1] - flip(a[1]))) < 1e-13
+    assert np.max(np.abs(am[2] + flip(a[2]))) < 1e-13
+
+
+def test_first_iteration_and_homogeneous_fixed_point():
+    N = 32
+    S = W.flat_spectra(N, L, lscale=300.0)
+    sigma = np.full((3, N, N), 2e-3)
+    ones = np.ones((N, N), np.uint8)
+    d = _random_maps(N, 7) * 1e-3
+    r = F.dm_solve(d, sigma, ones, ones, S, L, [1.0], forced_iters=[2])
+    th = 4e-6 * (L / N) ** 2
+    ad = F.analysis(d, L)
+    ref = np.zeros_like(ad)
+    for i in range(N):
+        for j in range(N):
+            tt, ee, bb, te = S[:, i, j]
+            blk = np.array([[tt, te, 0], [te, ee, 0], [0, 0, bb]])
+            ref[:, i, j] = blk @ np.linalg.solve(blk + th * np.eye(3), ad[:, i, j])
+    assert np.max(np.abs(r["alm"] - ref)) < 1e-12 * np.max(np.abs(ref))
+    assert r["cauchy"][1] < 1e-13  # w = 1: t = d after every step, so step 2 repeats step 1
+
+
+def _dense_signal(S, N, mu):
+    """Pixel covariance [3 N^2, 3 N^2] of the signal S' = V max(S_e, mu) V^T per
+    mode, summed over the harmonic space as plane waves:
+    Cov[X(x), Y(x')] = L^-2 sum_l (R S' R^T)_XY cos(l.(x - x'))."""
+    k = np.fft.fftfreq(N, d=1.0 / N)
+    iy, ix = np.mgrid[0:N, 0:N]
+    x, y = (ix * L / N).ravel(), (iy * L / N).ravel()
+    dx, dy = x[:, None] - x[None, :], y[:, None] - y[None, :]
+    C = np.zeros((3, 3, N * N, N * N))
+    for a in range(N):
+        for b in range(N):
+            if k[a] == -N // 2 or k[b] == -N // 2:
+                continue
+            ly, lx = 2 * np.pi * k[a] / L, 2 * np.pi * k[b] / L
+            tt, ee, bb, te = S[:, a, b]
+            e, v = np.linalg.eigh(np.array([[tt, te], [te, ee]]))
+            te_blk = (v * np.maximum(np.maximum(e, 0.0), mu)) @ v.T
+            sp = np.zeros((3, 3))
+            sp[:2, :2] = te_blk
+            sp[2, 2] = max(bb, mu)
+            phi = np.arctan2(ly, lx)
+            c, s = np.cos(2 * phi), np.sin(2 * phi)
+            R = np.array([[1, 0, 0], [0, c, -s], [0, s, c]])
+            M = R @ sp @ R.T
+            cw = np.cos(lx * dx + ly * dy)
+            C += M[:, :, None, None] * cw[None, None]
+    C /= L ** 2
+    return C.transpose(0, 2, 1, 3).reshape(3 * N * N, 3 * N * N)
+
+
+@pytest.mark.parametrize("lam", [1.0, 40.0])
+def test_fixed_point_is_the_pixel_space_wiener_filter(lam):
+    N = 8
+    S = W.flat_spectra(N, L, lscale=300.0)
+    rng = np.random.default_rng(8)
+    st = 0.1 * (0.75 + 0.5 * rng.random((N, N)))  # S / T_h up to about 100: the level converges fast
+    sigma = np.stack([st, np.sqrt(2) * st, np.sqrt(2) * st])
+    mask_t = (rng.random((N, N)) > 0.25).astype(np.uint8)
+    mask_p = (rng.random((N, N)) > 0.2).astype(np.uint8)
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    d = _random_maps(N, 9) * 0.1 * obs
+    r = F.dm_solve(d, sigma, mask_t, mask_p, S, L, [lam], eps=[1e-15], max_iter=20000)
+    assert r["iters"] < 20000
+    alpha = (sigma ** 2)[obs].min()
+    mu = (lam - 1.0) * alpha * (L / N) ** 2
+    Sp = _dense_signal(S, N, mu)
+    o = obs.ravel()
+    nv = (sigma ** 2).ravel()[o]
+    x = np.linalg.solve(Sp[np.ix_(o, o)] + np.diag(nv), d.ravel()[o])
+    s_ref = (Sp[:, o] @ x).reshape(3, N, N)
+    assert np.linalg.norm(r["s"] - s_ref) / np.linalg.norm(s_ref) < 1e-9

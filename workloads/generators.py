@@ -21,6 +21,10 @@ Recipe (all seeded through numpy's PCG64 via SeedSequence):
   sqrt(2) sigma_T; an optional (1 + cos^2 theta) scan-depth factor;
 * mask: |z| < band removed, plus disks (centres uniform on the sphere), a pixel
   is masked when its centre lies inside a disk.
+
+The flat-sky section at the end keeps the paper's own geometry (a 10 degree
+patch on a 1024^2 grid, T and P masks of f_sky 0.78 and 0.82) with the same
+stand-in spectra evaluated at each Fourier mode's |l|.
 """
 from __future__ import annotations
 
@@ -325,4 +329,131 @@ def make_cov_workload(seeds, nside: int, lmax: int | None = None, band_t: float 
         r_sig, r_noise = _streams(sd, 2)
         wl.alm_true.append(draw_alm(lm, cl, r_sig))
         wl.noise.append(draw_noise_cov(sigma, rho, mask_t, mask_p, r_noise))
+    return wl
+
+
+# ----------------------------------------------------------------- flat sky
+# The paper's own setting (Section 3.1): a square patch of side L = 10 degrees
+# on an N x N grid (N = 1024), T and P masks covering f_sky = 0.78 and 0.82,
+# noise of a few uK.  Stand-ins, as on the sphere: the analytic spectra
+# evaluated at the real |l| of each Fourier mode, with a damping scale that
+# reaches the patch's multipoles (l from 2 pi / L = 36 to the Nyquist l =
+# pi N / L); inhomogeneous diagonal noise; masks made of a strip and disks.
+#
+# Fourier convention shared with the consumers of these arrays: a mode of
+# integer wavenumber (k_x, k_y), numpy FFT order, axis 0 = y and axis 1 = x,
+# has l = 2 pi k / L and <|a_l|^2> = L^2 C_|l|.  Modes on the Nyquist row or
+# column (k = -N/2) carry no signal.
+
+FLAT_L = 10.0 * DEG
+FLAT_N = 1024
+FLAT_LSCALE = 1500.0
+
+
+def flat_ell(N: int, L: float) -> np.ndarray:
+    """|l| of every mode of an N x N grid of side L (numpy FFT order)."""
+    k = np.fft.fftfreq(N, d=1.0 / N)
+    return 2.0 * np.pi / L * np.hypot(k[:, None], k[None, :])
+
+
+def flat_nyquist(N: int) -> np.ndarray:
+    """True on the Nyquist row and column of an even N (no such modes for odd N)."""
+    k = np.fft.fftfreq(N, d=1.0 / N)
+    ny = (k == -(N // 2)) if N % 2 == 0 else np.zeros(N, bool)
+    return ny[:, None] | ny[None, :]
+
+
+def cl_flat(ell: np.ndarray, lscale: float = FLAT_LSCALE) -> np.ndarray:
+    """[4, ...] = TT, EE, BB, TE at real multipoles ell: the sphere recipe's
+    formulas with damping scale lscale; 0 at l = 0 and polarisation only
+    from l = 2."""
+    ell = np.asarray(ell, dtype=np.float64)
+    pos = ell > 0
+    safe = np.where(pos, ell, 1.0)
+    tt = np.where(pos, np.exp(-(safe / lscale) ** 2) / (safe * (safe + 1.0)), 0.0)
+    pol = ell >= 2
+    ee = np.where(pol, 0.05 * tt, 0.0)
+    bb = 0.01 * ee
+    te = np.where(pol, 0.3 * np.sqrt(tt * ee), 0.0)
+    return np.stack([tt, ee, bb, te])
+
+
+def flat_spectra(N: int, L: float, lscale: float = FLAT_LSCALE) -> np.ndarray:
+    """[4, N, N] spectra per Fourier mode, 0 on the Nyquist row and column."""
+    return cl_flat(flat_ell(N, L), lscale) * ~flat_nyquist(N)
+
+
+def draw_flat_alm(S: np.ndarray, L: float, rng: np.random.Generator) -> np.ndarray:
+    """Gaussian (T, E, B) Fourier coefficients [3, N, N] complex128 with
+    <|a_l|^2> = L^2 C_l and the Hermitian symmetry of real fields, from the
+    per-mode 2x2 TE Cholesky factor (B independent): unit white-noise maps,
+    Fourier transformed and scaled by L / N per mode."""
+    tt, ee, bb, te = S
+    N = S.shape[-1]
+    z = np.fft.fft2(rng.standard_normal((3, N, N)), axes=(-2, -1)) * (L / N)
+    l11 = np.sqrt(np.maximum(tt, 0.0))
+    l21 = np.where(l11 > 0, te / np.where(l11 > 0, l11, 1.0), 0.0)
+    l22 = np.sqrt(np.maximum(ee - l21 ** 2, 0.0))
+    lbb = np.sqrt(np.maximum(bb, 0.0))
+    return np.stack([l11 * z[0], l21 * z[0] + l22 * z[1], lbb * z[2]])
+
+
+def flat_noise_sigma(N: int, L: float, S: np.ndarray, rng: np.random.Generator, level: float = 0.04):
+    """sigma_T = s0 (0.75 + 0.5 U(0,1)) per pixel with s0 = level x the analytic
+    T rms of the patch, sqrt(sum_l C_l^TT) / L; sigma_Q = sigma_U = sqrt(2) sigma_T."""
+    s0 = level * np.sqrt(S[0].sum()) / L
+    st = s0 * (0.75 + 0.5 * rng.random((N, N)))
+    return np.stack([st, np.sqrt(2.0) * st, np.sqrt(2.0) * st])
+
+
+def flat_mask(N: int, rng: np.random.Generator, fsky: float, strip: float = 0.1) -> np.ndarray:
+    """uint8 [N, N], 1 = observed: a horizontal strip of height strip x N through
+    the middle, then disks of radius 1 to 4 % of N at uniform centres until
+    the observed fraction drops to fsky."""
+    y, x = np.mgrid[0:N, 0:N]
+    m = np.ones((N, N), np.uint8)
+    h = int(round(strip * N))
+    m[(N - h) // 2:(N - h) // 2 + h, :] = 0
+    while m.mean() > fsky:
+        cy, cx = rng.random(2) * N
+        r = N * (0.01 + 0.03 * rng.random())
+        m[(y - cy) ** 2 + (x - cx) ** 2 < r * r] = 0
+    return m
+
+
+@dataclass
+class FlatWorkload:
+    """One flat-sky problem: spectra per mode, noise, T and P masks, the true
+    (T, E, B) Fourier coefficients per RHS and their noise realisations."""
+    N: int
+    L: float
+    S: np.ndarray                 # [4, N, N] TT, EE, BB, TE per mode
+    sigma: np.ndarray             # [3, N, N]
+    mask_t: np.ndarray            # [N, N]
+    mask_p: np.ndarray            # [N, N]
+    alm_true: list = field(default_factory=list)
+    noise: list = field(default_factory=list)
+    seeds: list = field(default_factory=list)
+
+    def data(self, signal_maps):
+        """d = s + n on observed components, 0 on masked ones."""
+        obs = np.stack([self.mask_t, self.mask_p, self.mask_p])
+        return [(s + n) * obs for s, n in zip(signal_maps, self.noise)]
+
+
+def make_flat_workload(seeds, N: int = FLAT_N, L: float = FLAT_L, lscale: float = FLAT_LSCALE,
+                       fsky_t: float = 0.78, fsky_p: float = 0.82, level: float = 0.04) -> FlatWorkload:
+    """Spectra, noise sigma and masks from the first seed; per-RHS signal and
+    noise draws from each seed."""
+    seeds = list(seeds)
+    S = flat_spectra(N, L, lscale)
+    r_sigma, r_mt, r_mp = _streams(seeds[0] * 7919 + 3, 3)
+    sigma = flat_noise_sigma(N, L, S, r_sigma, level)
+    mask_t = flat_mask(N, r_mt, fsky_t)
+    mask_p = flat_mask(N, r_mp, fsky_p)
+    wl = FlatWorkload(N=N, L=L, S=S, sigma=sigma, mask_t=mask_t, mask_p=mask_p, seeds=seeds)
+    for sd in seeds:
+        r_sig, r_noise = _streams(sd + 104729, 2)
+        wl.alm_true.append(draw_flat_alm(S, L, r_sig))
+        wl.noise.append(sigma * r_noise.standard_normal(sigma.shape))
     return wl
