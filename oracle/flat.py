@@ -136,3 +136,48 @@ def dm_solve(d, sigma, mask_t, mask_p, S, L, lambdas, eps=None, forced_iters=Non
         iters_per_level.append(nk)
     return {"s": s, "alm": a, "iters": it, "iters_per_level": np.array(iters_per_level),
             "cauchy": np.array(cauchy), "alpha": alpha}
+
+
+def _block_pow(S: np.ndarray, p: float):
+    """Per-mode powers of the signal covariance block for the parameters it
+    constrains: [4, N, N] (TE block entries and BB) of V diag(S_e^p) V^T over
+    the eigenvalues S_e > 0, 0 on the null directions (a pseudo-inverse)."""
+    tt, ee, bb, te = S
+    blk = np.stack([np.stack([tt, te], -1), np.stack([te, ee], -1)], -2)
+    e, v = np.linalg.eigh(blk)
+    tiny = 1e-300
+    ep = np.where(e > tiny, np.where(e > tiny, e, 1.0) ** p, 0.0)
+    M = np.einsum("...ik,...k,...jk->...ij", v, ep, v)
+    bp = np.where(bb > tiny, np.where(bb > tiny, bb, 1.0) ** p, 0.0)
+    return np.stack([M[..., 0, 0], M[..., 0, 1], M[..., 1, 1], bp])
+
+
+def wf_residual(alm, d, sigma, mask_t, mask_p, S, L):
+    """||A x - y|| / ||y|| of the Wiener filter in the form A x = y with
+    A = 1 + S^1/2 F^H N^-1 F S^1/2, x = S^-1/2 a and y = S^1/2 F^H N^-1 d,
+    where F is the synthesis and F^H its adjoint (the diagnostic the paper
+    reports beside its solutions, Section 3.2 and Appendix C).  Here <a a^H> = L^2 C per mode,
+    the adjoint of F (synthesis) is analysis / (Omega_p L^2), and N^-1 = 0 on
+    masked pixel-components."""
+    N = d.shape[-1]
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    ninv = np.where(obs, 1.0 / np.where(obs, sigma ** 2, 1.0), 0.0)
+    adj = lambda m: analysis(m, L) / ((L / N) ** 2 * L ** 2)
+    Sa = S * L ** 2
+    half, mhalf = _block_pow(Sa, 0.5), _block_pow(Sa, -0.5)
+    y = apply_filter(half, adj(ninv * d))
+    r = apply_filter(mhalf, alm) - apply_filter(half, adj(ninv * (d - synthesis(alm, L))))
+    return float(np.sqrt(np.sum(np.abs(r) ** 2) / np.sum(np.abs(y) ** 2)))
+
+
+def chi2(alm, d, sigma, mask_t, mask_p, S, L):
+    """(d - s)^T N^-1 (d - s) over observed pixel-components plus
+    sum over modes a^H S^-1 a with <a a^H> = L^2 C (Eq. 3), S^-1 taken on the
+    non-zero eigenvalues of each mode's block."""
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    s = synthesis(alm, L)
+    r = (d - s)[obs]
+    noise = np.sum(r * r / (sigma[obs] ** 2))
+    inv = _block_pow(S * L ** 2, -1.0)
+    prior = np.sum(np.real(np.conj(alm) * apply_filter(inv, alm)))
+    return float(noise + prior)

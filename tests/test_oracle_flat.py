@@ -183,3 +183,30 @@ def test_fixed_point_is_the_pixel_space_wiener_filter(lam):
     x = np.linalg.solve(Sp[np.ix_(o, o)] + np.diag(nv), d.ravel()[o])
     s_ref = (Sp[:, o] @ x).reshape(3, N, N)
     assert np.linalg.norm(r["s"] - s_ref) / np.linalg.norm(s_ref) < 1e-9
+
+
+def test_residual_and_chi2_at_the_wiener_filter():
+    """At the dense Wiener filter of the N = 8 problem the residual
+    ||A x - y|| / ||y|| vanishes and chi^2 takes its minimum
+    d_o^T (S_oo + N_oo)^-1 d_o (observed components o); a perturbed solution
+    has a finite residual and a larger chi^2."""
+    N = 8
+    S = W.flat_spectra(N, L, lscale=300.0)
+    rng = np.random.default_rng(10)
+    st = 0.1 * (0.75 + 0.5 * rng.random((N, N)))
+    sigma = np.stack([st, np.sqrt(2) * st, np.sqrt(2) * st])
+    mask_t = (rng.random((N, N)) > 0.25).astype(np.uint8)
+    mask_p = (rng.random((N, N)) > 0.2).astype(np.uint8)
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    d = _random_maps(N, 11) * 0.1 * obs
+    Sp = _dense_signal(S, N, 0.0)
+    o = obs.ravel()
+    x = np.linalg.solve(Sp[np.ix_(o, o)] + np.diag((sigma ** 2).ravel()[o]), d.ravel()[o])
+    s_wf = (Sp[:, o] @ x).reshape(3, N, N)
+    a_wf = F.analysis(s_wf, L)
+    assert F.wf_residual(a_wf, d, sigma, mask_t, mask_p, S, L) < 1e-10
+    c2 = F.chi2(a_wf, d, sigma, mask_t, mask_p, S, L)
+    assert c2 == pytest.approx(float(d.ravel()[o] @ x), rel=1e-9)
+    pert = a_wf + 0.01 * F.analysis(_random_maps(N, 12) * 0.1, L) * (S[[0, 1, 2]] > 0)
+    assert F.wf_residual(pert, d, sigma, mask_t, mask_p, S, L) > 1e-4
+    assert F.chi2(pert, d, sigma, mask_t, mask_p, S, L) > c2
