@@ -181,3 +181,78 @@ def chi2(alm, d, sigma, mask_t, mask_p, S, L):
     inv = _block_pow(S * L ** 2, -1.0)
     prior = np.sum(np.real(np.conj(alm) * apply_filter(inv, alm)))
     return float(noise + prior)
+
+
+# ---------------------------------------------------------------- Appendix A
+# Jacobi refinement s^{n+1} = s^n + W~(d - W^+ s^n).  W~ is the dual messenger
+# operator run with the per-level iteration counts of the usual solve, kept
+# fixed so that W~ is one linear operator.  Data enter the messenger update
+# t = (Nbar^-1 + T^-1)^-1 (T^-1 s + Nbar^-1 d) only through its data term,
+# h = w d on observed components.  For the correction the data are
+# W^+ s = N (S^-1 + N^-1) s, whose data term is T Z = alpha (S^+ + N^-1) s with
+# S^+ the pixel-space pseudo-inverse of the signal covariance: w s on observed
+# components plus alpha S^+ s on every pixel, masked ones included (the limit
+# N -> infinity of w W^+ s there).  This is Appendix A's rewriting of the
+# messenger equation in terms of Z, free of N on masked pixels.  Every run of
+# W~ starts from t_0 = h, the update applied to s = 0, so that W~ sees h only
+# through F^dagger h.  The Wiener-filter equation holds on the directions
+# S spans; along its null directions (the T monopole and E, B at l = 0 on the
+# patch) the data carry no equation, yet W~ at levels with mu > 0 would pass
+# them.  So the correction's data term is projected onto the range of S in
+# harmonic space before W~ runs; the exact Wiener filter is then a fixed point
+# of the refinement whatever the counts.
+
+
+def dm_frozen(h, w, S, L, lambdas, counts, th):
+    """W~ applied to a messenger data term h [3, N, N]: t_0 = h, then for each
+    level k, counts[k] times a = filter_k(F^dagger t), s = F a,
+    t = (1 - w) s + h.  Returns (s, a)."""
+    t = np.array(h, dtype=np.float64)
+    s = np.zeros_like(t)
+    a = np.zeros(t.shape, np.complex128)
+    for lam, n in zip(lambdas, counts):
+        coef = filter_coefs(S, (lam - 1.0) * th, th)
+        for _ in range(int(n)):
+            a = apply_filter(coef, analysis(t, L))
+            s = synthesis(a, L)
+            t = (1.0 - w) * s + h
+    return s, a
+
+
+def jacobi_data_term(s, w, alpha, S, L):
+    """T Z of Appendix A for the signal map s: w s + alpha S^+ s, where
+    S^+ s = Omega_p L^2 F S_a^+ F^dagger s and S_a = L^2 C per mode."""
+    N = s.shape[-1]
+    sinv = _block_pow(S * L ** 2, -1.0)
+    return w * s + alpha * (L / N) ** 2 * L ** 2 * synthesis(apply_filter(sinv, analysis(s, L)), L)
+
+
+def range_projected(x, S, L):
+    """x minus the synthesis of the part of F^dagger x along the null
+    directions of each mode's signal block, so that F^dagger of the result is
+    the projection of F^dagger x onto the range of S."""
+    g = analysis(x, L)
+    keep = apply_filter(_block_pow(S, 0.0), g)
+    return x - synthesis(g - keep, L)
+
+
+def jacobi_refine(d, sigma, mask_t, mask_p, S, L, lambdas, eps=None, forced_iters=None, n_refine=1,
+                  max_iter=100000):
+    """The usual solve (recording its per-level counts), then n_refine steps
+    s <- s + W~(P(w d - T Z(s))) with W~ run at those counts (Appendix A) and
+    P the projection onto the range of S.
+    Returns the final s, alm, the counts and the map after each step."""
+    r = dm_solve(d, sigma, mask_t, mask_p, S, L, lambdas, eps=eps, forced_iters=forced_iters, max_iter=max_iter)
+    N = d.shape[-1]
+    alpha, w = weights(sigma, mask_t, mask_p)
+    th = alpha * (L / N) ** 2
+    counts = r["iters_per_level"]
+    hd = w * np.asarray(d, dtype=np.float64)
+    s = r["s"]
+    steps = [s]
+    for _ in range(n_refine):
+        x = range_projected(hd - jacobi_data_term(s, w, alpha, S, L), S, L)
+        c, _ = dm_frozen(x, w, S, L, lambdas, counts, th)
+        s = s + c
+        steps.append(s)
+    return {"s": s, "alm": analysis(s, L), "counts": counts, "steps": steps, "solve": r}

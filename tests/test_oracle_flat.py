@@ -210,3 +210,51 @@ def test_residual_and_chi2_at_the_wiener_filter():
     pert = a_wf + 0.01 * F.analysis(_random_maps(N, 12) * 0.1, L) * (S[[0, 1, 2]] > 0)
     assert F.wf_residual(pert, d, sigma, mask_t, mask_p, S, L) > 1e-4
     assert F.chi2(pert, d, sigma, mask_t, mask_p, S, L) > c2
+
+
+def _n8_problem(seed):
+    N = 8
+    S = W.flat_spectra(N, L, lscale=300.0)
+    rng = np.random.default_rng(seed)
+    st = 0.1 * (0.75 + 0.5 * rng.random((N, N)))
+    sigma = np.stack([st, np.sqrt(2) * st, np.sqrt(2) * st])
+    mask_t = (rng.random((N, N)) > 0.25).astype(np.uint8)
+    mask_p = (rng.random((N, N)) > 0.2).astype(np.uint8)
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    d = _random_maps(N, seed + 1) * 0.1 * obs
+    Sp = _dense_signal(S, N, 0.0)
+    o = obs.ravel()
+    x = np.linalg.solve(Sp[np.ix_(o, o)] + np.diag((sigma ** 2).ravel()[o]), d.ravel()[o])
+    return N, S, sigma, mask_t, mask_p, d, (Sp[:, o] @ x).reshape(3, N, N)
+
+
+def test_jacobi_data_term_vanishes_against_the_data_at_the_wiener_filter():
+    """On the range of S, F^dagger (w d - T Z(s_WF)) = 0: the Wiener-filter
+    equation itself, so the Wiener filter is a fixed point of the refinement
+    whatever the counts of W~ (Appendix A).  Along the null directions of S
+    (l = 0 here) the data term is not zero, which is why the correction is
+    projected; away from the Wiener filter the projected term is not zero."""
+    N, S, sigma, mask_t, mask_p, d, s_wf = _n8_problem(20)
+    alpha, w = F.weights(sigma, mask_t, mask_p)
+    x = w * d - F.jacobi_data_term(s_wf, w, alpha, S, L)
+    ref = np.max(np.abs(F.analysis(w * d, L)))
+    g = F.analysis(F.range_projected(x, S, L), L)
+    assert np.max(np.abs(g)) < 1e-10 * ref
+    assert np.max(np.abs(F.analysis(x, L)[:, 0, 0])) > 1e-3 * ref  # the l = 0 mode
+    s_off = s_wf + 0.01 * F.synthesis(F.analysis(_random_maps(N, 21), L), L)
+    g2 = F.analysis(F.range_projected(w * d - F.jacobi_data_term(s_off, w, alpha, S, L), S, L), L)
+    assert np.max(np.abs(g2)) > 1e-4 * ref
+
+
+def test_jacobi_refinement_converges_to_the_wiener_filter():
+    """A deliberately short usual solve (3 levels of 15 iterations, relative
+    error 7e-2), then refinement steps with W~ at those counts: the distance
+    to the dense Wiener filter falls at every step until rounding, and is
+    below 1e-12 after 20 steps."""
+    N, S, sigma, mask_t, mask_p, d, s_wf = _n8_problem(22)
+    r = F.jacobi_refine(d, sigma, mask_t, mask_p, S, L, [20.0, 4.0, 1.0], forced_iters=[15, 15, 15],
+                        n_refine=20)
+    err = [np.linalg.norm(s - s_wf) / np.linalg.norm(s_wf) for s in r["steps"]]
+    assert err[0] > 1e-2
+    assert all(b < a for a, b in zip(err[:12], err[1:13]))
+    assert err[-1] < 1e-12
