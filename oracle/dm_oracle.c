@@ -31,8 +31,8 @@
  * Functions whose results are pinned by the -m "not gpu" tests: geometry,
  * harmonics, ring DFTs, synthesis/analysis, per-l filter, the messenger
  * update, the level loop, chi^2, Philox and the constrained-realisation draws,
- * and the correlated-noise model (Appendix B) with its update, solve and CR
- * noise draws.
+ * the correlated-noise model (Appendix B) with its update, solve and CR
+ * noise draws, and the modified Jacobi refinement (Appendix A).
  */
 #include <math.h>
 #include <stdint.h>
@@ -998,4 +998,86 @@ void orc_cr_inputs_cov(int nside, int lmax, const double *cl, const double *sigm
       long i = f * npix + p;
       dhat[i] = obs ? shat[i] + dhat[i] : 0.0;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The modified Jacobi refinement of Appendix A, in the harmonic form the     */
+/* sphere allows: a <- a + W~(P g(a)).                                         */
+/* - W~ is the dual messenger operator at the per-level iteration counts of   */
+/*   the usual solve, driven by a harmonic source g instead of data: from     */
+/*   a = 0, counts[k] times a <- F_k [a + g - A(w Y a)].  With g = A(w d) this */
+/*   is the iteration of orc_dm_solve after its first step.                    */
+/* - g(a) = A(w (d - Y a)) - alpha Omega C^+ a is the harmonic image of the    */
+/*   correction's data term w d - T Z, where T Z = alpha (S^+ + N^-1) s is     */
+/*   Appendix A's rewriting of the data term of W^+ s = N (S^-1 + N^-1) s; on  */
+/*   the sphere A S^+ (Y a) = Omega C^+ a, so no pixel-space inverse is needed. */
+/*   At the fixed point of the usual iteration at lambda = 1, g = 0 on the    */
+/*   range of C (there F^-1 a = a + A(w(d - Y a)) with F = C (C + T_h)^-1).     */
+/* - P projects onto the range of each l's block: along its null directions   */
+/*   (C_0^TT = 0, E and B below l = 2) no equation holds, yet W~ at mu > 0     */
+/*   would pass them.                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Per-l pseudo-inverse C^+ and range projector of the (TT, TE, EE; BB) block,
+ * in the [4(lmax+1)] layout orc_apply_filter takes. */
+void orc_cl_pinv(int lmax, const double *cl, double *pinv, double *proj) {
+  const double *tt = cl, *ee = cl + (lmax + 1), *bb = cl + 2 * (lmax + 1), *te = cl + 3 * (lmax + 1);
+  for (int l = 0; l <= lmax; ++l) {
+    double e1, e2, v1[2], v2[2];
+    eig2(tt[l], te[l], ee[l], &e1, &e2, v1, v2);
+    const double i1 = e1 > 0.0 ? 1.0 / e1 : 0.0, i2 = e2 > 0.0 ? 1.0 / e2 : 0.0;
+    const double p1 = e1 > 0.0 ? 1.0 : 0.0, p2 = e2 > 0.0 ? 1.0 : 0.0;
+    pinv[4 * l + 0] = i1 * v1[0] * v1[0] + i2 * v2[0] * v2[0];
+    pinv[4 * l + 1] = i1 * v1[0] * v1[1] + i2 * v2[0] * v2[1];
+    pinv[4 * l + 2] = i1 * v1[1] * v1[1] + i2 * v2[1] * v2[1];
+    pinv[4 * l + 3] = bb[l] > 0.0 ? 1.0 / bb[l] : 0.0;
+    proj[4 * l + 0] = p1 * v1[0] * v1[0] + p2 * v2[0] * v2[0];
+    proj[4 * l + 1] = p1 * v1[0] * v1[1] + p2 * v2[0] * v2[1];
+    proj[4 * l + 2] = p1 * v1[1] * v1[1] + p2 * v2[1] * v2[1];
+    proj[4 * l + 3] = bb[l] > 0.0 ? 1.0 : 0.0;
+  }
+}
+
+/* g = P [A(w (d - Y a)) - alpha Omega C^+ a] */
+void orc_jacobi_source(int nside, int lmax, const double *cl, const double *sigma, const uint8_t *mask,
+                       const double *d, const double *alm, double *g) {
+  long npix = orc_npix(nside), nalm = orc_nalm(lmax), n3 = 3 * npix;
+  double alpha = orc_alpha(npix, sigma, mask);
+  double omega = 4.0 * M_PI / (double)npix;
+  double *w = malloc(sizeof(double) * n3), *s = malloc(sizeof(double) * n3);
+  double *ca = malloc(sizeof(double) * 6 * nalm);
+  double *pinv = malloc(sizeof(double) * 4 * (lmax + 1)), *proj = malloc(sizeof(double) * 4 * (lmax + 1));
+  orc_weights(npix, sigma, mask, alpha, w);
+  orc_cl_pinv(lmax, cl, pinv, proj);
+  orc_alm2map(nside, lmax, alm, s);
+  for (long i = 0; i < n3; ++i) s[i] = w[i] * (d[i] - s[i]);
+  orc_map2alm(nside, lmax, s, g);
+  memcpy(ca, alm, sizeof(double) * 6 * nalm);
+  orc_apply_filter(lmax, pinv, ca);
+  for (long i = 0; i < 6 * nalm; ++i) g[i] -= alpha * omega * ca[i];
+  orc_apply_filter(lmax, proj, g);
+  free(w); free(s); free(ca); free(pinv); free(proj);
+}
+
+/* a = W~(g): from a = 0, counts[k] times a <- F_k [a + g - A(w Y a)]. */
+void orc_dm_frozen(int nside, int lmax, const double *cl, const double *sigma, const uint8_t *mask,
+                   const double *g, int nlev, const double *lambdas, const int *counts, double *alm) {
+  long npix = orc_npix(nside), nalm = orc_nalm(lmax), n3 = 3 * npix;
+  double alpha = orc_alpha(npix, sigma, mask);
+  double th = alpha * 4.0 * M_PI / (double)npix;
+  double *w = malloc(sizeof(double) * n3), *s = malloc(sizeof(double) * n3);
+  double *ar = malloc(sizeof(double) * 6 * nalm), *coef = malloc(sizeof(double) * 4 * (lmax + 1));
+  orc_weights(npix, sigma, mask, alpha, w);
+  memset(alm, 0, sizeof(double) * 6 * nalm);
+  for (int k = 0; k < nlev; ++k) {
+    orc_filter_coefs(lmax, cl, (lambdas[k] - 1.0) * th, th, coef);
+    for (int it = 0; it < counts[k]; ++it) {
+      orc_alm2map(nside, lmax, alm, s);
+      for (long i = 0; i < n3; ++i) s[i] *= w[i];
+      orc_map2alm(nside, lmax, s, ar);
+      for (long i = 0; i < 6 * nalm; ++i) alm[i] += g[i] - ar[i];
+      orc_apply_filter(lmax, coef, alm);
+    }
+  }
+  free(w); free(s); free(ar); free(coef);
 }

@@ -405,6 +405,57 @@ def constrained_realization_cov(nside, lmax, cl, sigma, rho, maskT, maskP, d, se
     return r
 
 
+def cl_pinv(lmax, cl):
+    """(C^+, range projector) per l in the filter-coefficient layout [lmax+1, 4]."""
+    c = np.ascontiguousarray(cl, dtype=np.float64)
+    pinv = np.zeros((lmax + 1, 4))
+    proj = np.zeros((lmax + 1, 4))
+    lib().orc_cl_pinv(lmax, _d(c), _d(pinv), _d(proj))
+    return pinv, proj
+
+
+def jacobi_source(nside, lmax, cl, sigma, mask, d, alm):
+    """P [A(w (d - Y a)) - alpha Omega C^+ a] (Appendix A, harmonic form)."""
+    c = np.ascontiguousarray(cl, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    a = np.ascontiguousarray(alm, dtype=np.complex128)
+    m, mp = _mask_ptr(mask)
+    g = np.zeros((3, nalm(lmax)), dtype=np.complex128)
+    lib().orc_jacobi_source(nside, lmax, _d(c), _d(sg), mp, _d(dd), _d(a.view(np.float64)), _d(g.view(np.float64)))
+    return g
+
+
+def dm_frozen(nside, lmax, cl, sigma, mask, g, lambdas, counts):
+    """W~(g): the dual messenger iteration at fixed per-level counts, driven by
+    the harmonic source g, from a = 0."""
+    c = np.ascontiguousarray(cl, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    gg = np.ascontiguousarray(g, dtype=np.complex128)
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    cnt = np.ascontiguousarray(counts, dtype=np.int32)
+    m, mp = _mask_ptr(mask)
+    a = np.zeros((3, nalm(lmax)), dtype=np.complex128)
+    lib().orc_dm_frozen(nside, lmax, _d(c), _d(sg), mp, _d(gg.view(np.float64)), len(lam), _d(lam),
+                        cnt.ctypes.data_as(_ip), _d(a.view(np.float64)))
+    return a
+
+
+def jacobi_refine(nside, lmax, cl, sigma, mask, d, lambdas, eps=None, forced_iters=None, n_refine=1,
+                  max_iter=100000):
+    """Appendix A: the usual solve (recording its per-level counts), then
+    n_refine steps a <- a + W~(P g(a)) at those counts."""
+    r = dm_solve(nside, lmax, cl, sigma, mask, d, lambdas, eps, forced_iters, max_iter)
+    counts = np.asarray(r["iters_per_level"], dtype=np.int32)
+    a = r["alm"]
+    steps = [a]
+    for _ in range(n_refine):
+        a = a + dm_frozen(nside, lmax, cl, sigma, mask, jacobi_source(nside, lmax, cl, sigma, mask, d, a),
+                          lambdas, counts)
+        steps.append(a)
+    return {"alm": a, "s": alm2map(nside, lmax, a), "counts": counts, "steps": steps, "solve": r}
+
+
 def level_lambdas(lambda0, nlev):
     """Geometric cooling lambda_k = lambda0^(1 - k/(nlev-1)), last level exactly 1."""
     if nlev == 1:
