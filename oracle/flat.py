@@ -183,6 +183,70 @@ def chi2(alm, d, sigma, mask_t, mask_p, S, L):
     return float(noise + prior)
 
 
+# ------------------------------------------------- correlated noise (App. B)
+# The paper's own noise model: per pixel N = Sigma C Sigma with C the
+# unit-diagonal correlation matrix of (rho_IQ, rho_IU, rho_QU).  Masks enter
+# as Sigma^-1 = 0 on masked components (I on the temperature mask, Q and U on
+# the polarisation mask), so N^-1 = Sigma^-1 C^-1 Sigma^-1 with zero rows and
+# columns there.  T = alpha 1 with alpha the smallest eigenvalue of N over the
+# observed components, alpha = min over pixels of 1 / lambda_max(N^-1).  The
+# messenger equation of Appendix B then reads t = s + alpha N^-1 (d - s).
+
+
+def cov_ninv(sigma, rho, mask_t, mask_p):
+    """[3, 3, N, N] per-pixel N^-1 with masked components' rows and columns 0."""
+    r01, r02, r12 = rho
+    one = np.ones_like(r01)
+    C = np.stack([np.stack([one, r01, r02]), np.stack([r01, one, r12]), np.stack([r02, r12, one])])
+    Ci = np.moveaxis(np.linalg.inv(np.moveaxis(C, (0, 1), (-2, -1))), (-2, -1), (0, 1))
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    si = np.where(obs, 1.0 / np.where(obs, sigma, 1.0), 0.0)
+    return si[:, None] * Ci * si[None, :]
+
+
+def cov_alpha(ninv):
+    lam = np.linalg.eigvalsh(np.moveaxis(ninv, (0, 1), (-2, -1)))[..., -1]
+    return float(1.0 / lam[lam > 0].max())
+
+
+def dm_solve_cov(d, sigma, rho, mask_t, mask_p, S, L, lambdas, eps=None, forced_iters=None, max_iter=100000):
+    """Algorithm 1 on the flat patch with the correlated noise model: as
+    dm_solve, with the messenger update t = s + alpha N^-1 (d - s)."""
+    d = np.asarray(d, dtype=np.float64)
+    N = d.shape[-1]
+    ninv = cov_ninv(sigma, rho, mask_t, mask_p)
+    alpha = cov_alpha(ninv)
+    th = alpha * (L / N) ** 2
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    s = np.zeros_like(d)
+    t = np.where(obs, d, 0.0)
+    a = np.zeros((3, N, N), np.complex128)
+    iters_per_level, cauchy = [], []
+    it = 0
+    for k, lam in enumerate(lambdas):
+        coef = filter_coefs(S, (lam - 1.0) * th, th)
+        nk = 0
+        while True:
+            if forced_iters is not None and nk >= forced_iters[k]:
+                break
+            if forced_iters is None and it >= max_iter:
+                break
+            a = apply_filter(coef, analysis(t, L))
+            sn = synthesis(a, L)
+            ss = np.sum(sn * sn)
+            c = np.sqrt(np.sum((sn - s) ** 2) / ss) if ss > 0 else 0.0
+            s = sn
+            t = s + alpha * np.einsum("ij...,j...->i...", ninv, np.where(obs, d, 0.0) - s)
+            cauchy.append(c)
+            it += 1
+            nk += 1
+            if forced_iters is None and c < eps[k]:
+                break
+        iters_per_level.append(nk)
+    return {"s": s, "alm": a, "iters": it, "iters_per_level": np.array(iters_per_level),
+            "cauchy": np.array(cauchy), "alpha": alpha}
+
+
 # ---------------------------------------------------------------- Appendix A
 # Jacobi refinement s^{n+1} = s^n + W~(d - W^+ s^n).  W~ is the dual messenger
 # operator run with the per-level iteration counts of the usual solve, kept

@@ -45,3 +45,18 @@ def test_draws_are_hermitian_with_the_stated_variance():
         assert np.mean(ratio) == pytest.approx(1.0, abs=0.02)
     sel = S[3] > 0
     assert np.mean(cross[sel] / K / L ** 2 / S[3][sel]) == pytest.approx(1.0, abs=0.03)
+
+
+def test_correlated_noise_option():
+    N = 128
+    wl = W.make_flat_workload([6, 7], N=N, rho_max=0.3)
+    assert wl.rho is not None and np.abs(wl.rho).max() <= 0.3
+    n = wl.noise[0]
+    obs = np.stack([wl.mask_t, wl.mask_p, wl.mask_p]).astype(bool)
+    assert not n[~obs].any()
+    both = obs[0] & obs[1]
+    # E[x y | rho] = rho_IQ for the normalised noise, so E[x y rho] = E[rho^2]
+    # (about 0.03), where noise that ignored rho would give 0
+    x, y, r = n[0][both] / wl.sigma[0][both], n[1][both] / wl.sigma[1][both], wl.rho[0][both]
+    assert np.mean(x * y * r) == pytest.approx(np.mean(r * r), abs=5 * np.std(x * y * r) / np.sqrt(both.sum()))
+    assert W.make_flat_workload([6], N=N).rho is None

@@ -258,3 +258,69 @@ def test_jacobi_refinement_converges_to_the_wiener_filter():
     assert err[0] > 1e-2
     assert all(b < a for a, b in zip(err[:12], err[1:13]))
     assert err[-1] < 1e-12
+
+
+def _cov_model(N, seed, rho_max=0.3):
+    rng = np.random.default_rng(seed)
+    st = 0.1 * (0.75 + 0.5 * rng.random((N, N)))
+    sigma = np.stack([st, np.sqrt(2) * st, np.sqrt(2) * st])
+    rho = rng.uniform(-rho_max, rho_max, (3, N, N))
+    mask_t = (rng.random((N, N)) > 0.25).astype(np.uint8)
+    mask_p = (rng.random((N, N)) > 0.2).astype(np.uint8)
+    return sigma, rho, mask_t, mask_p
+
+
+def test_cov_ninv_and_alpha_against_numpy():
+    N = 6
+    sigma, rho, mask_t, mask_p = _cov_model(N, 30)
+    ninv = F.cov_ninv(sigma, rho, mask_t, mask_p)
+    lam_max = 0.0
+    for i in range(N):
+        for j in range(N):
+            C = np.array([[1, rho[0, i, j], rho[1, i, j]], [rho[0, i, j], 1, rho[2, i, j]],
+                          [rho[1, i, j], rho[2, i, j], 1]])
+            Sg = np.diag(sigma[:, i, j])
+            ref = np.linalg.inv(Sg @ C @ Sg)
+            o = np.array([mask_t[i, j], mask_p[i, j], mask_p[i, j]], bool)
+            # Sigma^-1 = 0 on masked components: rows and columns of C^-1 scaled away
+            ref = ref * np.outer(o, o)
+            assert np.max(np.abs(ninv[:, :, i, j] - ref)) < 1e-12 * np.max(np.abs(ref) + 1e-300)
+            if o.any():
+                lam_max = max(lam_max, np.linalg.eigvalsh(ninv[:, :, i, j]).max())
+    assert F.cov_alpha(ninv) == pytest.approx(1.0 / lam_max, rel=1e-13)
+
+
+def test_cov_solve_at_zero_correlation_is_the_diagonal_solve():
+    N = 16
+    S = W.flat_spectra(N, L, lscale=300.0)
+    sigma, _, mask_t, mask_p = _cov_model(N, 31)
+    d = _random_maps(N, 32) * 0.1
+    lam = [40.0, 4.0, 1.0]
+    a = F.dm_solve(d, sigma, mask_t, mask_p, S, L, lam, forced_iters=[5, 5, 5])
+    b = F.dm_solve_cov(d, sigma, np.zeros_like(sigma), mask_t, mask_p, S, L, lam, forced_iters=[5, 5, 5])
+    assert np.linalg.norm(b["s"] - a["s"]) / np.linalg.norm(a["s"]) < 1e-13
+
+
+@pytest.mark.parametrize("lam", [1.0, 40.0])
+def test_cov_fixed_point_is_the_wiener_filter(lam):
+    """(S'^-1 + N^-1)^-1 N^-1 d = S' (1 + N^-1 S')^-1 N^-1 d with the block
+    per-pixel N^-1 (singular where masked), S' the dense plane-wave signal
+    covariance of the level, at N = 8."""
+    N = 8
+    S = W.flat_spectra(N, L, lscale=300.0)
+    sigma, rho, mask_t, mask_p = _cov_model(N, 33)
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    d = _random_maps(N, 34) * 0.1 * obs
+    r = F.dm_solve_cov(d, sigma, rho, mask_t, mask_p, S, L, [lam], eps=[1e-15], max_iter=20000)
+    assert r["iters"] < 20000
+    ninv = F.cov_ninv(sigma, rho, mask_t, mask_p)
+    n = 3 * N * N
+    Nd = np.zeros((n, n))
+    pix = np.arange(N * N)
+    for i in range(3):
+        for j in range(3):
+            Nd[i * N * N + pix, j * N * N + pix] = ninv[i, j].ravel()
+    mu = (lam - 1.0) * r["alpha"] * (L / N) ** 2
+    Sp = _dense_signal(S, N, mu)
+    s_ref = Sp @ np.linalg.solve(np.eye(n) + Nd @ Sp, Nd @ d.ravel())
+    assert np.linalg.norm(r["s"].ravel() - s_ref) / np.linalg.norm(s_ref) < 1e-9

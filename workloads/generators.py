@@ -434,6 +434,7 @@ class FlatWorkload:
     alm_true: list = field(default_factory=list)
     noise: list = field(default_factory=list)
     seeds: list = field(default_factory=list)
+    rho: np.ndarray | None = None  # [3, N, N] (rho_IQ, rho_IU, rho_QU) when the noise is correlated
 
     def data(self, signal_maps):
         """d = s + n on observed components, 0 on masked ones."""
@@ -442,9 +443,12 @@ class FlatWorkload:
 
 
 def make_flat_workload(seeds, N: int = FLAT_N, L: float = FLAT_L, lscale: float = FLAT_LSCALE,
-                       fsky_t: float = 0.78, fsky_p: float = 0.82, level: float = 0.04) -> FlatWorkload:
+                       fsky_t: float = 0.78, fsky_p: float = 0.82, level: float = 0.04,
+                       rho_max: float = 0.0) -> FlatWorkload:
     """Spectra, noise sigma and masks from the first seed; per-RHS signal and
-    noise draws from each seed."""
+    noise draws from each seed.  With rho_max > 0 the noise is correlated
+    across I, Q and U as in the paper's run: per-pixel correlations uniform in
+    [-rho_max, rho_max] and n = Sigma L z (draw_noise_cov)."""
     seeds = list(seeds)
     S = flat_spectra(N, L, lscale)
     r_sigma, r_mt, r_mp = _streams(seeds[0] * 7919 + 3, 3)
@@ -452,8 +456,14 @@ def make_flat_workload(seeds, N: int = FLAT_N, L: float = FLAT_L, lscale: float 
     mask_t = flat_mask(N, r_mt, fsky_t)
     mask_p = flat_mask(N, r_mp, fsky_p)
     wl = FlatWorkload(N=N, L=L, S=S, sigma=sigma, mask_t=mask_t, mask_p=mask_p, seeds=seeds)
+    if rho_max > 0:
+        wl.rho = _streams(seeds[0] * 7919 + 5, 1)[0].uniform(-rho_max, rho_max, (3, N, N))
     for sd in seeds:
         r_sig, r_noise = _streams(sd + 104729, 2)
         wl.alm_true.append(draw_flat_alm(S, L, r_sig))
-        wl.noise.append(sigma * r_noise.standard_normal(sigma.shape))
+        if wl.rho is None:
+            wl.noise.append(sigma * r_noise.standard_normal(sigma.shape))
+        else:
+            n = draw_noise_cov(sigma.reshape(3, -1), wl.rho.reshape(3, -1), mask_t.ravel(), mask_p.ravel(), r_noise)
+            wl.noise.append(n.reshape(3, N, N))
     return wl
