@@ -247,6 +247,71 @@ def dm_solve_cov(d, sigma, rho, mask_t, mask_p, S, L, lambdas, eps=None, forced_
             "cauchy": np.array(cauchy), "alpha": alpha}
 
 
+# ------------------------------------------ constrained realisations (Eq. 19)
+# s_CR = W(d - dhat) + shat with shat a signal draw from the prior and
+# dhat = shat + nhat, nhat a noise draw whose covariance is the inverse of the
+# precision the solve uses (Eq. 18).  The random numbers are inputs: unit
+# white-noise maps z_s (signal) and z_n (noise), [3, N, N] each.
+
+
+def draw_signal(z_s, S, L):
+    """Fourier coefficients [3, N, N] with <a a^H> = L^2 C per mode and the
+    Hermitian symmetry of real fields: the per-mode Cholesky factor of the
+    TE block (and sqrt C^BB) applied to (L / N) FFT(z_s)."""
+    N = z_s.shape[-1]
+    tt, ee, bb, te = S
+    h = (L / N) * np.fft.fft2(z_s, axes=(-2, -1))
+    l11 = np.sqrt(np.maximum(tt, 0.0))
+    l21 = np.where(l11 > 0, te / np.where(l11 > 0, l11, 1.0), 0.0)
+    l22 = np.sqrt(np.maximum(ee - l21 ** 2, 0.0))
+    _, _, _, keep = geometry(N, L)
+    return np.stack([l11 * h[0], l21 * h[0] + l22 * h[1], np.sqrt(np.maximum(bb, 0.0)) * h[2]]) * keep
+
+
+def draw_noise(z_n, sigma, mask_t, mask_p, rho=None):
+    """Noise draw on observed components, 0 on masked ones.  Diagonal model:
+    sigma z.  Correlated model: Sigma x with x = L z (C = L L^T) on a fully
+    observed pixel; where some components are masked (Sigma^-1 = 0 there) the
+    observed block of the precision inverts to the covariance of x_o given
+    x_m = 0, drawn as x_o - C_om C_mm^-1 x_m."""
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    if rho is None:
+        return np.where(obs, sigma * z_n, 0.0)
+    r01, r02, r12 = rho
+    l11 = np.sqrt(1.0 - r01 ** 2)
+    l21 = (r12 - r02 * r01) / l11
+    l22 = np.sqrt(1.0 - r02 ** 2 - l21 ** 2)
+    x0 = z_n[0]
+    x1 = r01 * z_n[0] + l11 * z_n[1]
+    x2 = r02 * z_n[0] + l21 * z_n[1] + l22 * z_n[2]
+    ot, op = obs[0], obs[1]
+    t_only = ot & ~op  # Q, U masked: condition I on x_Q = x_U = 0
+    p_only = op & ~ot  # I masked: condition Q, U on x_I = 0
+    y1 = (x1 - r12 * x2) / (1.0 - r12 ** 2)
+    y2 = (x2 - r12 * x1) / (1.0 - r12 ** 2)
+    x0 = np.where(t_only, x0 - (r01 * y1 + r02 * y2), x0)
+    x1 = np.where(p_only, x1 - r01 * z_n[0], x1)
+    x2 = np.where(p_only, x2 - r02 * z_n[0], x2)
+    return np.where(obs, sigma * np.stack([x0, x1, x2]), 0.0)
+
+
+def constrained_realization(d, z_s, z_n, sigma, mask_t, mask_p, S, L, lambdas, rho=None, **solve_args):
+    """s_CR = W(d - dhat) + shat (Eq. 19) with W the dual messenger solve
+    (dm_solve, or dm_solve_cov when rho is given)."""
+    a_hat = draw_signal(z_s, S, L)
+    s_hat = synthesis(a_hat, L)
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    d_hat = np.where(obs, s_hat + draw_noise(z_n, sigma, mask_t, mask_p, rho), 0.0)
+    if rho is None:
+        r = dm_solve(np.asarray(d) - d_hat, sigma, mask_t, mask_p, S, L, lambdas, **solve_args)
+    else:
+        r = dm_solve_cov(np.asarray(d) - d_hat, sigma, rho, mask_t, mask_p, S, L, lambdas, **solve_args)
+    r["s_cr"] = r["s"] + s_hat
+    r["alm_cr"] = r["alm"] + a_hat
+    r["s_hat"], r["d_hat"], r["a_hat"] = s_hat, d_hat, a_hat
+    return r
+
+
 # ---------------------------------------------------------------- Appendix A
 # Jacobi refinement s^{n+1} = s^n + W~(d - W^+ s^n).  W~ is the dual messenger
 # operator run with the per-level iteration counts of the usual solve, kept

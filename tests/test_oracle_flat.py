@@ -324,3 +324,73 @@ def test_cov_fixed_point_is_the_wiener_filter(lam):
     Sp = _dense_signal(S, N, mu)
     s_ref = Sp @ np.linalg.solve(np.eye(n) + Nd @ Sp, Nd @ d.ravel())
     assert np.linalg.norm(r["s"].ravel() - s_ref) / np.linalg.norm(s_ref) < 1e-9
+
+
+def test_cr_draws_reduce_and_condition():
+    """The signal draw has the stated per-mode covariance; the correlated
+    noise draw at rho = 0 is the diagonal one, and on a fully observed pixel
+    its covariance is Sigma C Sigma while a pixel with Q, U masked has the
+    conditional variance sigma_I^2 / (C^-1)_II."""
+    N = 64
+    S = W.flat_spectra(N, L)
+    rng = np.random.default_rng(40)
+    acc = np.zeros((3, N, N))
+    K = 300
+    for _ in range(K):
+        a = F.draw_signal(rng.standard_normal((3, N, N)), S, L)
+        acc += np.abs(a) ** 2
+    sel = S[0] > 0
+    assert np.mean(acc[0][sel] / K / L ** 2 / S[0][sel]) == pytest.approx(1.0, abs=0.02)
+    sigma = np.full((3, N, N), 2.0)
+    ones = np.ones((N, N), np.uint8)
+    z = rng.standard_normal((3, N, N))
+    assert np.array_equal(F.draw_noise(z, sigma, ones, ones, np.zeros((3, N, N))), F.draw_noise(z, sigma, ones, ones))
+    r = np.array([0.5, -0.4, 0.3])
+    rho = np.broadcast_to(r[:, None, None], (3, N, N)).copy()
+    C = np.array([[1, r[0], r[1]], [r[0], 1, r[2]], [r[1], r[2], 1]])
+    zeros = np.zeros((N, N), np.uint8)
+    full, t_only = [], []
+    for _ in range(40):
+        z = rng.standard_normal((3, N, N))
+        full.append(F.draw_noise(z, sigma, ones, ones, rho).reshape(3, -1))
+        t_only.append(F.draw_noise(z, sigma, ones, zeros, rho).reshape(3, -1))
+    full, t_only = np.concatenate(full, 1), np.concatenate(t_only, 1)
+    n = full.shape[1]
+    assert np.allclose(np.cov(full), 4.0 * C, atol=6 * 4.0 * np.sqrt(2.0 / n))
+    assert not t_only[1:].any()
+    assert np.var(t_only[0]) == pytest.approx(4.0 / np.linalg.inv(C)[0, 0], rel=6 * np.sqrt(2.0 / n))
+
+
+@pytest.mark.parametrize("correlated", [False, True])
+def test_cr_fluctuation_has_the_posterior_covariance(correlated):
+    """f = shat - W dhat (Eq. 18) with the dense Wiener filter W at N = 8:
+    f^T P^+ f averages the rank of P, the posterior covariance
+    P = S (1 + N^-1 S)^-1, over 400 draws."""
+    N = 8
+    S = W.flat_spectra(N, L, lscale=300.0)
+    sigma, rho, mask_t, mask_p = _cov_model(N, 41)
+    if not correlated:
+        rho = None
+    ninv = F.cov_ninv(sigma, np.zeros_like(sigma) if rho is None else rho, mask_t, mask_p)
+    n = 3 * N * N
+    Nd = np.zeros((n, n))
+    pix = np.arange(N * N)
+    for i in range(3):
+        for j in range(3):
+            Nd[i * N * N + pix, j * N * N + pix] = ninv[i, j].ravel()
+    Sp = _dense_signal(S, N, 0.0)
+    Wd = Sp @ np.linalg.solve(np.eye(n) + Nd @ Sp, Nd)
+    P = Sp @ np.linalg.inv(np.eye(n) + Nd @ Sp)
+    P = 0.5 * (P + P.T)
+    Pp = np.linalg.pinv(P, rcond=1e-10, hermitian=True)
+    rank = np.linalg.matrix_rank(P, tol=1e-10 * np.abs(P).max(), hermitian=True)
+    rng = np.random.default_rng(42)
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    q = []
+    K = 400
+    for _ in range(K):
+        s_hat = F.synthesis(F.draw_signal(rng.standard_normal((3, N, N)), S, L), L)
+        d_hat = np.where(obs, s_hat + F.draw_noise(rng.standard_normal((3, N, N)), sigma, mask_t, mask_p, rho), 0.0)
+        f = s_hat.ravel() - Wd @ d_hat.ravel()
+        q.append(f @ Pp @ f)
+    assert abs(np.mean(q) - rank) < 5 * np.sqrt(2.0 * rank / K)
