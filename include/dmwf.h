@@ -122,7 +122,8 @@ dm_status dm_plan_info(const dm_plan *plan, int64_t *npix, int64_t *nalm, int *n
 dm_status dm_set_precision(dm_plan *plan, dm_precision prec);
 
 /* Signal covariance, Eq. 10: host array cl[4][lmax+1] (TT, EE, BB, TE).
- * Each per-l TE block must be positive semi-definite (DM_EINVAL otherwise). */
+ * Each per-l TE block must be positive semi-definite (DM_EINVAL otherwise).
+ * DM_EBUSY while a solve is in progress. */
 dm_status dm_set_spectra(dm_plan *plan, const double *cl);
 
 /* Noise and mask (shared by every RHS of the plan), host arrays:
@@ -156,12 +157,13 @@ dm_status dm_set_noise_mask_rhs(dm_plan *plan, int b, const double *sigma, const
 dm_status dm_set_noise_cov(dm_plan *plan, const double *sigma, const double *rho, const uint8_t *mask_t,
                            const uint8_t *mask_p);
 
-/* Schedule (defaults: lambda0 1000, 10 levels, 10 iterations per level). */
+/* Schedule (defaults: lambda0 1000, 10 levels, 10 iterations per level).
+ * DM_EBUSY while a solve is in progress. */
 dm_status dm_set_schedule(dm_plan *plan, const dm_schedule *sched);
 
 /* Force the per-level iteration counts (length n_levels of the schedule),
  * overriding iters_per_level and the Cauchy test; NULL clears it.  Used to
- * replay a recorded run. */
+ * replay a recorded run.  DM_EBUSY while a solve is in progress. */
 dm_status dm_set_forced_iters(dm_plan *plan, const int *iters);
 
 /* --- the hot path -------------------------------------------------------- */
@@ -186,7 +188,9 @@ dm_status dm_wiener_filter_host(dm_plan *plan, const double *d_host, double *s_h
  *  dm_solve_iterate runs up to max_iters iterations, stops early once every
  *                   RHS met its stopping rule (*all_done = 1); synchronises;
  *  dm_solve_end     writes s_out / alm_out (device, may be NULL) and stats.
- * DM_EBUSY when a solve is already in progress on the plan. */
+ * DM_EBUSY when a solve is already in progress on the plan.  A solve that
+ * fails (a CUDA error, DM_ETIMEOUT) ends its session, in these calls and in
+ * dm_wiener_filter / dm_constrained_realization, so the plan stays usable. */
 dm_status dm_solve_begin(dm_plan *plan, const double *d, void *stream);
 dm_status dm_solve_iterate(dm_plan *plan, int max_iters, int *all_done, void *stream);
 dm_status dm_solve_end(dm_plan *plan, double *s_out, double *alm_out, dm_stats *stats, void *stream);

@@ -116,6 +116,13 @@ dm_status refresh_filters(dm_plan *p) {
   return DM_OK;
 }
 
+// A failed solve leaves the plan usable: no session, no stage state.
+void end_session(dm_plan *p) {
+  p->state_active = false;
+  p->anchor_active = false;
+  p->session = false;
+}
+
 dm_status check_ready(dm_plan *p) {
   if (!p) return DM_EINVAL;
   if (!p->have_cl) return fail(p, DM_EINVAL, "spectra not set (dm_set_spectra)");
@@ -290,11 +297,12 @@ dm_status solve_end(dm_plan *p, double *s_out, double *alm_out, cudaStream_t st,
   if (!p->session) return fail(p, DM_EINVAL, "no solve in progress (dm_solve_begin)");
   if (p->prec != DM_FP64) {
     dm_status r = anchor(p, st, false, nullptr, false);
-    if (r != DM_OK) return r;
-    p->anchor_active = false;
+    if (r != DM_OK) {
+      end_session(p);
+      return r;
+    }
   }
-  p->state_active = false;
-  p->session = false;
+  end_session(p);
   const cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   if (s_out) DM_CU(cudaMemcpyAsync(s_out, p->s64, sizeof(double) * 3 * p->npix * p->batch, kind, st), "copy s");
   if (alm_out) DM_CU(cudaMemcpyAsync(alm_out, p->a, sizeof(double2) * 3 * p->nalm * p->batch, kind, st), "copy alm");
@@ -303,7 +311,10 @@ dm_status solve_end(dm_plan *p, double *s_out, double *alm_out, cudaStream_t st,
 
 dm_status run_dm(dm_plan *p, const double *d, cudaStream_t st) {
   dm_status r = solve_begin(p, d, st);
-  if (r != DM_OK) return r;
+  if (r != DM_OK) {
+    end_session(p);
+    return r;
+  }
   const dm_schedule &S = p->sched;
   long cap = (long)S.max_iter + 4;
   if (S.iters_per_level > 0 || !p->forced.empty()) {
@@ -313,7 +324,10 @@ dm_status run_dm(dm_plan *p, const double *d, cudaStream_t st) {
   }
   int all = 0;
   r = solve_iterate(p, cap, &all, st);
-  if (r != DM_OK) return r;
+  if (r != DM_OK) {
+    end_session(p);
+    return r;
+  }
   if (!all) return fail(p, DM_ENOTCONV, "iteration cap reached");
   return DM_OK;
 }
@@ -443,6 +457,7 @@ dm_status dm_set_anchor_precision(dm_plan *p, dm_precision prec) {
 
 dm_status dm_set_spectra(dm_plan *p, const double *cl) {
   if (!p || !cl) return DM_EINVAL;
+  if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
   const int L = p->lmax + 1;
   for (int l = 0; l < L; ++l) {
     double tt = cl[l], ee = cl[L + l], bb = cl[2 * L + l], te = cl[3 * L + l];
@@ -525,6 +540,7 @@ dm_status dm_set_noise_mask_rhs(dm_plan *p, int b, const double *sigma, const ui
 
 dm_status dm_set_schedule(dm_plan *p, const dm_schedule *s) {
   if (!p || !s) return DM_EINVAL;
+  if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
   if (s->n_levels < 1 || s->n_levels > DM_MAX_LEVELS || !(s->lambda0 >= 1.0) || s->max_iter < 1 ||
       s->iters_per_level < 0)
     return fail(p, DM_EINVAL, "bad schedule");
@@ -543,6 +559,7 @@ dm_status dm_set_schedule(dm_plan *p, const dm_schedule *s) {
 
 dm_status dm_set_forced_iters(dm_plan *p, const int *iters) {
   if (!p) return DM_EINVAL;
+  if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
   if (!iters) {
     p->forced.clear();
   } else {
@@ -696,7 +713,9 @@ dm_status dm_solve_begin(dm_plan *p, const double *d, void *stream) {
   if (r != DM_OK) return r;
   if (!d) return fail(p, DM_EINVAL, "null buffer");
   if (p->session) return fail(p, DM_EBUSY, "a solve is already in progress on this plan");
-  return solve_begin(p, d, (cudaStream_t)stream);
+  r = solve_begin(p, d, (cudaStream_t)stream);
+  if (r != DM_OK) end_session(p);
+  return r;
 }
 
 dm_status dm_solve_iterate(dm_plan *p, int max_iters, int *all_done, void *stream) {
