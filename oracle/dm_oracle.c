@@ -1081,3 +1081,64 @@ void orc_dm_frozen(int nside, int lmax, const double *cl, const double *sigma, c
   }
   free(w); free(s); free(ar); free(coef);
 }
+
+/* ------------------------------------------------------------------------ */
+/* True residual of the Wiener-filter equation, the diagnostic the paper      */
+/* reports beside its solutions (Section 3.2, Appendix C): ||A x - y|| / ||y|| */
+/* with A = 1 + S^1/2 Y^T N^-1 Y S^1/2, x = S^-1/2 a, y = S^1/2 Y^T N^-1 d.    */
+/* In the iteration's own terms Y^T N^-1 (d - Y a) - S^-1 a is proportional   */
+/* to g(a) = A(w (d - Y a)) - alpha Omega C^+ a and Y^T N^-1 d to A(w d), so   */
+/* the ratio is ||C^1/2 g|| / ||C^1/2 A(w d)|| with each (l, m > 0) counted    */
+/* twice (its -m partner) and C^1/2 per l from the (TT, TE, EE; BB) block.     */
+/* ------------------------------------------------------------------------ */
+static double weighted_half_norm2(int lmax, const double *half, const double *alm) {
+  long nalm = orc_nalm(lmax);
+  double acc = 0.0;
+  for (int m = 0; m <= lmax; ++m)
+    for (int l = m; l <= lmax; ++l) {
+      long ix = orc_almidx(lmax, l, m);
+      const double *c = half + 4 * l;
+      const double fac = m == 0 ? 1.0 : 2.0;
+      for (int p = 0; p < 2; ++p) {
+        double t = alm[2 * ix + p], e = alm[2 * (nalm + ix) + p], b = alm[2 * (2 * nalm + ix) + p];
+        double ht = c[0] * t + c[1] * e, he = c[1] * t + c[2] * e, hb = c[3] * b;
+        acc += fac * (ht * ht + he * he + hb * hb);
+      }
+    }
+  return acc;
+}
+
+double orc_wf_residual(int nside, int lmax, const double *cl, const double *sigma, const uint8_t *mask,
+                       const double *d, const double *alm) {
+  long npix = orc_npix(nside), nalm = orc_nalm(lmax), n3 = 3 * npix;
+  const double *tt = cl, *ee = cl + (lmax + 1), *bb = cl + 2 * (lmax + 1), *te = cl + 3 * (lmax + 1);
+  double alpha = orc_alpha(npix, sigma, mask);
+  double omega = 4.0 * M_PI / (double)npix;
+  double *w = malloc(sizeof(double) * n3), *s = malloc(sizeof(double) * n3);
+  double *g = malloc(sizeof(double) * 6 * nalm), *y = malloc(sizeof(double) * 6 * nalm);
+  double *ca = malloc(sizeof(double) * 6 * nalm);
+  double *pinv = malloc(sizeof(double) * 4 * (lmax + 1)), *proj = malloc(sizeof(double) * 4 * (lmax + 1));
+  double *half = malloc(sizeof(double) * 4 * (lmax + 1));
+  orc_weights(npix, sigma, mask, alpha, w);
+  orc_cl_pinv(lmax, cl, pinv, proj);
+  for (int l = 0; l <= lmax; ++l) {
+    double e1, e2, v1[2], v2[2];
+    eig2(tt[l], te[l], ee[l], &e1, &e2, v1, v2);
+    const double r1 = e1 > 0.0 ? sqrt(e1) : 0.0, r2 = e2 > 0.0 ? sqrt(e2) : 0.0;
+    half[4 * l + 0] = r1 * v1[0] * v1[0] + r2 * v2[0] * v2[0];
+    half[4 * l + 1] = r1 * v1[0] * v1[1] + r2 * v2[0] * v2[1];
+    half[4 * l + 2] = r1 * v1[1] * v1[1] + r2 * v2[1] * v2[1];
+    half[4 * l + 3] = bb[l] > 0.0 ? sqrt(bb[l]) : 0.0;
+  }
+  for (long i = 0; i < n3; ++i) s[i] = w[i] * d[i];
+  orc_map2alm(nside, lmax, s, y);
+  orc_alm2map(nside, lmax, alm, s);
+  for (long i = 0; i < n3; ++i) s[i] = w[i] * (d[i] - s[i]);
+  orc_map2alm(nside, lmax, s, g);
+  memcpy(ca, alm, sizeof(double) * 6 * nalm);
+  orc_apply_filter(lmax, pinv, ca);
+  for (long i = 0; i < 6 * nalm; ++i) g[i] -= alpha * omega * ca[i];
+  const double num = weighted_half_norm2(lmax, half, g), den = weighted_half_norm2(lmax, half, y);
+  free(w); free(s); free(g); free(y); free(ca); free(pinv); free(proj); free(half);
+  return den > 0.0 ? sqrt(num / den) : 0.0;
+}

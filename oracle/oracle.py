@@ -58,6 +58,7 @@ def lib():
         L.orc_dm_solve.restype = ctypes.c_int
         L.orc_cov_alpha.restype = ctypes.c_double
         L.orc_dm_solve_cov.restype = ctypes.c_int
+        L.orc_wf_residual.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -412,6 +413,16 @@ def cl_pinv(lmax, cl):
     proj = np.zeros((lmax + 1, 4))
     lib().orc_cl_pinv(lmax, _d(c), _d(pinv), _d(proj))
     return pinv, proj
+
+
+def wf_residual(nside, lmax, cl, sigma, mask, d, alm):
+    """||A x - y|| / ||y|| of the Wiener-filter equation at the iterate alm."""
+    c = np.ascontiguousarray(cl, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    a = np.ascontiguousarray(alm, dtype=np.complex128)
+    m, mp = _mask_ptr(mask)
+    return lib().orc_wf_residual(nside, lmax, _d(c), _d(sg), mp, _d(dd), _d(a.view(np.float64)))
 
 
 def jacobi_source(nside, lmax, cl, sigma, mask, d, alm):

@@ -9,8 +9,11 @@ W~ the dual messenger operator at fixed per-level counts driven by g.
   solve's iteration from another start (t_0 = d there, w d here): their
   difference shrinks by more than 1e3 from 20 to 200 iterations a level;
 - refinement from a deliberately short solve converges to the dense Wiener
-  filter."""
+  filter;
+- the true residual ||A x - y|| / ||y|| of the Wiener-filter equation (the
+  paper's diagnostic) against the dense normal equations."""
 import numpy as np
+import pytest
 
 import workloads as W
 from tests.harmonics_ref import alm_to_params, dense_synthesis, params_to_alm
@@ -75,3 +78,29 @@ def test_refinement_converges_to_the_wiener_filter(orc):
     assert err[0] > 1e-3
     assert all(b < a for a, b in zip(err[:8], err[1:9]))
     assert err[-1] < 1e-10
+
+
+def test_true_residual_against_the_dense_normal_equations(orc):
+    """||A x - y|| / ||y|| with A = 1 + P^-1/2 Y^T N^-1 Y P^-1/2 on the real
+    parameters of the nside-4 problem (P the prior precision, Y from scipy
+    and Goldberg): the oracle's residual equals it at random iterates and
+    vanishes at the dense Wiener filter."""
+    nside, lmax = 4, 8
+    cl, params_all, sigma, mask, z, phi = _dense_problem(nside, lmax, 3)
+    params = [p for p in params_all if not (p[0] == 0 and p[1] == 0)]
+    Y = dense_synthesis(nside, lmax, z, phi, params)
+    Ninv = (mask[None, :] / sigma ** 2).reshape(-1)
+    d = W.random_maps(nside, 1, 35)[0] * 0.05 * mask[None, :]
+    P = _prior_precision(cl, params, 0.0)
+    e, v = np.linalg.eigh(P)
+    Pmh = (v / np.sqrt(e)) @ v.T
+    H = P + Y.T @ (Ninv[:, None] * Y)
+    rhs = Y.T @ (Ninv * d.reshape(-1))
+    dense = lambda x: np.linalg.norm(Pmh @ (H @ x - rhs)) / np.linalg.norm(Pmh @ rhs)
+    x_wf = np.linalg.solve(H, rhs)
+    assert orc.wf_residual(nside, lmax, cl, sigma, mask, d, params_to_alm(x_wf, params, lmax)) < 1e-10
+    rng = np.random.default_rng(36)
+    for scale in [1e-3, 1e-1, 1.0]:
+        x = x_wf + scale * np.linalg.norm(x_wf) / np.sqrt(len(x_wf)) * rng.standard_normal(len(x_wf))
+        got = orc.wf_residual(nside, lmax, cl, sigma, mask, d, params_to_alm(x, params, lmax))
+        assert got == pytest.approx(dense(x), rel=1e-9)
