@@ -271,3 +271,43 @@ def test_filter_is_scalar_where_spectra_underflow(orc):
         assert coef[l, 0] == pytest.approx(f, rel=1e-14)
         assert coef[l, 2] == pytest.approx(f, rel=1e-14)
         assert abs(coef[l, 1]) <= 1e-14 * f
+
+
+@pytest.mark.slow
+def test_cr_power_spectrum_is_unbiased(orc):
+    """Constrained realisations through the oracle's own converged solve
+    (Eq. 19), over true signals drawn from the prior and their data: the mean
+    power of a_CR per field pair, pooled over l, equals the input spectrum
+    (Section 3.2: CRs restore the power the Wiener filter suppresses)."""
+    nside, lmax = 4, 8
+    cl, _, sigma, mask, _, _ = _dense_problem(nside, lmax, 3)
+    rng = np.random.default_rng(50)
+    K = 150
+    pw = np.zeros((4, lmax + 1))  # TT, EE, BB, TE
+    for k in range(K):
+        a = W.draw_alm(lmax, cl, rng)
+        d = (orc.alm2map(nside, lmax, a) + sigma * rng.standard_normal(sigma.shape)) * mask[None, :]
+        r = orc.constrained_realization(nside, lmax, cl, sigma, mask, d, 7000 + k, [1.0], eps=[1e-10],
+                                        max_iter=20000)
+        acr = r["alm_cr"]
+        for m in range(lmax + 1):
+            fac = 1.0 if m == 0 else 2.0
+            for l in range(m, lmax + 1):
+                ix = orc.almidx(lmax, l, m)
+                t, e, b = acr[:, ix]
+                pw[0, l] += fac * abs(t) ** 2
+                pw[1, l] += fac * abs(e) ** 2
+                pw[2, l] += fac * abs(b) ** 2
+                pw[3, l] += fac * (t * np.conj(e)).real
+    ells = np.arange(lmax + 1)
+    pw /= K * (2 * ells + 1)[None, :]
+    for row, lmin in [(0, 1), (1, 2), (2, 2)]:
+        sel = slice(lmin, lmax + 1)
+        ratio = pw[row, sel] / cl[row, sel]
+        se = np.sqrt(np.sum(2.0 / (K * (2 * ells[sel] + 1)))) / len(ratio)  # standard error of the mean ratio
+        assert abs(np.mean(ratio) - 1.0) < 5 * se
+    # TE: the cross power against C^TE, as z-scores pooled over l
+    sel = slice(2, lmax + 1)
+    ref = cl[3, sel]
+    sd = np.sqrt((cl[0, sel] * cl[1, sel] + ref ** 2) / (K * (2 * ells[sel] + 1)))
+    assert abs(np.mean((pw[3, sel] - ref) / sd)) < 5.0 / np.sqrt(len(ref))
