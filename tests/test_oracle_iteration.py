@@ -125,3 +125,25 @@ def test_quadrature_error_is_second_order_in_ring_spacing(orc):
         for a, b in zip(e[:-1], e[1:]):
             assert 3.6 < a / b < 4.4
     assert err[-1] < 3e-3 and leak[-1] < 6e-4
+
+
+@pytest.mark.parametrize("lam", [1.0, 40.0])
+def test_spectral_radius_below_one_at_lmax_11(lam):
+    """At nside 4 / lmax 11 (= 3 nside - 1) A Y spans 0.53 to 1.48, yet the
+    level still contracts: rho(M) = 0.996 (against 0.978 at lmax 8)."""
+    nside, lmax = 4, 11
+    cl, params, sigma, mask, z, phi = _dense_problem(nside, lmax, 3)
+    npix = z.size
+    Y = dense_synthesis(nside, lmax, z, phi, params)
+    D = np.array([1.0 if p[2] == 0 else 2.0 for p in params])
+    A = 4 * np.pi / npix * (Y.T / D[:, None])
+    ay = np.linalg.eigvals(A @ Y).real
+    assert ay.max() > 1.4 and ay.min() < 0.6
+    obs = np.tile(mask, 3).astype(bool)
+    N = (sigma ** 2).reshape(-1)
+    alpha = N[obs].min()
+    w = np.where(obs, alpha / N, 0.0)
+    th = alpha * 4 * np.pi / npix
+    F = _filter_matrix(cl, params, (lam - 1.0) * th, th)
+    rho = np.abs(np.linalg.eigvals(F @ (np.eye(len(params)) - A @ (w[:, None] * Y)))).max()
+    assert 0.99 < rho < 1.0
