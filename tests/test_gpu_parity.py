@@ -233,3 +233,30 @@ def test_session_api_equals_one_call(orc, prec):
     st, stats = p.solve_end(s2)
     assert stats[0]["iters_total"] == 18
     assert rel(s2.cpu().numpy(), s1.cpu().numpy()) < (1e-15 if prec == dmwf.DM_FP64 else 1e-12)
+
+
+
+def test_setters_refuse_changes_during_a_session(orc):
+    """dm_set_schedule, dm_set_forced_iters and dm_set_spectra return DM_EBUSY
+    between dm_solve_begin and dm_solve_end (they rewrite device-side level
+    tables or filters); the session then ends normally and the plan accepts
+    them again."""
+    wl = W.make_workload("nside16", [2], nside=8, lmax=16)
+    d = _data(orc, wl)
+    p = make_plan(wl, 1, lambda0=100.0, n_levels=3, iters_per_level=6, check_every=4)
+    s = torch.zeros((1, 3, wl.npix), dtype=torch.float64, device="cuda")
+    p.solve_begin(dev(d))
+    for call in (lambda: p.set_schedule(lambda0=10.0, n_levels=2, iters_per_level=3),
+                 lambda: p.set_forced_iters([1, 1, 1]),
+                 lambda: p.set_spectra(wl.cl)):
+        with pytest.raises(dmwf.DmError) as e:
+            call()
+        assert e.value.status == dmwf.DM_EBUSY
+    assert p.solve_iterate(100)
+    st, stats = p.solve_end(s)
+    assert stats[0]["iters_total"] == 18
+    p.set_schedule(lambda0=10.0, n_levels=2, iters_per_level=3)
+    p.set_spectra(wl.cl)
+    st, stats = p.wiener_filter(dev(d), s)
+    assert stats[0]["iters_total"] == 6
+    p.close()
