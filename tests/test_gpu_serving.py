@@ -119,6 +119,11 @@ def test_serving_queue_bound_cancel_and_budget(orc):
             assert e.status == dmwf.DM_EBUSY
             busy += 1
     assert busy >= 1
+    # a mask with no observed pixel is refused at submission
+    with pytest.raises(dmwf.DmError) as e:
+        srv.submit(r["nside"], r["lmax"], r["kind"], r["tol"], r["cl"], r["sigma"], r["d"],
+                   np.zeros_like(np.asarray(r["mask"], dtype=np.uint8)))
+    assert e.value.status == dmwf.DM_EINVAL
     cancelled = [t for t in tickets if srv.cancel(t) == dmwf.DM_OK]
     assert cancelled
     for t in cancelled:
