@@ -394,3 +394,30 @@ def test_cr_fluctuation_has_the_posterior_covariance(correlated):
         f = s_hat.ravel() - Wd @ d_hat.ravel()
         q.append(f @ Pp @ f)
     assert abs(np.mean(q) - rank) < 5 * np.sqrt(2.0 * rank / K)
+
+
+@pytest.mark.parametrize("correlated", [False, True])
+def test_level_accounting_and_linearity(correlated):
+    """Per-level counts add up to the total; each level ends at the first
+    iteration whose Cauchy ratio is below its threshold; with fixed counts the
+    solve is linear in the data."""
+    N = 16
+    S = W.flat_spectra(N, L, lscale=300.0)
+    sigma, rho, mask_t, mask_p = _cov_model(N, 60)
+    solve = (lambda *a, **k: F.dm_solve_cov(a[0], sigma, rho, mask_t, mask_p, *a[1:], **k)) if correlated else \
+        (lambda *a, **k: F.dm_solve(a[0], sigma, mask_t, mask_p, *a[1:], **k))
+    obs = np.stack([mask_t, mask_p, mask_p]).astype(bool)
+    d1 = _random_maps(N, 61) * 0.1 * obs
+    d2 = _random_maps(N, 62) * 0.1 * obs
+    lam = [100.0, 10.0, 1.0]
+    eps = [1e-3, 1e-4, 1e-5]
+    r = solve(d1, S, L, lam, eps=eps)
+    ipl = r["iters_per_level"]
+    assert ipl.sum() == r["iters"] and np.all(ipl >= 1)
+    ends = np.cumsum(ipl) - 1
+    starts = np.concatenate([[0], ends[:-1] + 1])
+    for st, en, e in zip(starts, ends, eps):
+        assert r["cauchy"][en] < e and np.all(r["cauchy"][st:en] >= e)
+    f = lambda d: solve(d, S, L, lam, forced_iters=[3, 3, 3])["s"]
+    a, b, c = f(d1), f(d2), f(d1 + 2 * d2)
+    assert np.linalg.norm(c - a - 2 * b) / np.linalg.norm(c) < 1e-12
