@@ -276,7 +276,7 @@ Pool *find_pool(dm_server *S, const Request &r, bool *full) {
 }
 
 // Set slot b up alone and run its first iteration (t_0 = d), then anchor.
-dm_status slot_begin(dm_server *S, Pool *pool, int b, Request &r) {
+dm_status slot_begin(Pool *pool, int b, Request &r) {
   dm_plan *p = pool->plan;
   cudaStream_t st = pool->stream;
   const int64_t n3 = 3 * p->npix;
@@ -418,7 +418,7 @@ void worker_main(dm_server *S) {
     for (auto &pb : fresh) {
       Pool *pool = pb.first;
       const int b = pb.second;
-      dm_status rs = slot_begin(S, pool, b, *pool->slots[b].req);
+      dm_status rs = slot_begin(pool, b, *pool->slots[b].req);
       S->admitted++;
       if (rs != DM_OK) {
         finish(S, *pool->slots[b].req, rs, 0, 0.0);
