@@ -383,7 +383,7 @@ cudaError_t build_tables(dm_plan *p) {
       const RingDev &R = p->rings_h[ids[i]];
       const int key = R.M > 256 ? R.M : 256;
       if (key != last_key) {
-        p->ring_classes.push_back(RingClass{i, 0, R.M, R.n});
+        p->ring_classes.push_back(RingClass{i, 0, R.M, R.n, 0, 0});  // poff, pcount set below
         last_key = key;
       }
       RingClass &c = p->ring_classes.back();
