@@ -40,7 +40,7 @@ def _rank_main(rank, ws, port, out):
 
 def test_two_rank_max_and_value():
     ws = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of this multi-threaded process
     out = mgr.dict()
     mp.spawn(_rank_main, args=(ws, _free_port(), out), nprocs=ws, join=True)
     for r in range(ws):
