@@ -421,3 +421,19 @@ def test_level_accounting_and_linearity(correlated):
     f = lambda d: solve(d, S, L, lam, forced_iters=[3, 3, 3])["s"]
     a, b, c = f(d1), f(d2), f(d1 + 2 * d2)
     assert np.linalg.norm(c - a - 2 * b) / np.linalg.norm(c) < 1e-12
+
+
+@pytest.mark.slow
+def test_chi2_at_the_wiener_filter_matches_degrees_of_freedom():
+    """Section 3.2: at the converged Wiener filter chi^2 (Eq. 3) has the
+    expectation n_dof, the number of observed pixel-components, with
+    standard deviation sqrt(2 n_dof).  Signal and noise drawn from the
+    model at N = 64 (the paper's patch, 4 % noise), one level at lambda = 1
+    to a Cauchy ratio of 1e-5 (the distance to the exact Wiener filter then
+    adds far less than one standard deviation to chi^2)."""
+    wl = W.make_flat_workload([8], N=64)
+    d = wl.data([F.synthesis(wl.alm_true[0], wl.L)])[0]
+    r = F.dm_solve(d, wl.sigma, wl.mask_t, wl.mask_p, wl.S, wl.L, [1.0], eps=[1e-5], max_iter=100000)
+    ndof = int(wl.mask_t.sum() + 2 * wl.mask_p.sum())
+    c2 = F.chi2(r["alm"], d, wl.sigma, wl.mask_t, wl.mask_p, wl.S, wl.L)
+    assert abs(c2 - ndof) < 5 * np.sqrt(2.0 * ndof)
