@@ -217,6 +217,8 @@ dm_status anchor(dm_plan *p, cudaStream_t st, bool initial, const double *d, boo
 dm_status solve_begin(dm_plan *p, const double *d, cudaStream_t st) {
   if (p->cov && p->prec != DM_FP64)
     return fail(p, DM_EINVAL, "correlated noise (dm_set_noise_cov) runs in DM_FP64 or DM_FLOAT_FLOAT");
+  // a tensor-core wait that gave up in an earlier solve does not count against this one
+  if (p->tc_err) DM_CU(cudaMemsetAsync(p->tc_err, 0, sizeof(int), st), "clear wait flag");
   DM_CU(cudaMemsetAsync(p->a, 0, sizeof(double2) * 3 * p->nalm * p->batch, st), "zero a");
   DM_CU(p->cov ? cov_prepare_wd(p, d, st) : prepare_wd(p, d, st), "w d");
   DM_CU(control_init(p, st), "control init");
