@@ -210,7 +210,10 @@ dm_status dm_set_anchor_precision(dm_plan *plan, dm_precision prec);
  * batch of 8, 16, 32 or 64 RHS the contractions over l and over ring pairs
  * run as tcgen05 GEMMs with BF16 hi/lo split operands and FP32 accumulation
  * (three products per K step); other batches use the FP32 CUDA-core kernels.
- * A pipeline wait that gives up reports DM_ETIMEOUT. */
+ * A pipeline wait that gives up (after 1 s) makes the solve calls return
+ * DM_ETIMEOUT; the single-stage calls (dm_alm2map, dm_legendre_synthesis, ...)
+ * return without synchronising and do not check it.  Each solve starts with
+ * the flag cleared. */
 dm_status dm_set_tensor_cores(dm_plan *plan, int on);
 
 /* Tuning: the ring transforms of an iteration for rings whose FFT size M is a
