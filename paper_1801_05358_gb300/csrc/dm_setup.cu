@@ -483,8 +483,22 @@ cudaError_t gen_tables32(dm_plan *p);  // dm_legendre.cu
 // Tables and buffers of DM_MIXED_FP32: FP32 copies of the FFT tables, the FP32
 // Legendre tables (FP64 recurrence), FP32 ring coefficients and maps.
 cudaError_t setup_fp32(dm_plan *p) {
-  if (p->ptab) return cudaSuccess;
+  if (p->ptab) return cudaSuccess;  // set only after everything below succeeded
   cudaError_t e;
+  // all or nothing: on any error every buffer allocated here is freed again,
+  // so that a later call starts over instead of finding a half-built state
+  void **owned[] = {(void **)&p->phase32, (void **)&p->bhat32, (void **)&p->chirp32, (void **)&p->twid32,
+                    (void **)&p->twr32,   (void **)&p->ptab,   (void **)&p->ptab_lo, (void **)&p->rc32,
+                    (void **)&p->apart32, (void **)&p->s32,    (void **)&p->w32,     (void **)&p->wd32,
+                    (void **)&p->a_hi,    (void **)&p->g_hi,   (void **)&p->shi32,   (void **)&p->e32,
+                    (void **)&p->c32,     (void **)&p->clev,   (void **)&p->tc_err};
+  auto undo = [&](cudaError_t err) {
+    for (void **q : owned) {
+      if (*q) cudaFree(*q);
+      *q = nullptr;
+    }
+    return err;
+  };
   const int64_t B = p->batch, n3 = 3 * p->npix;
   auto al = [&](auto **ptr, size_t cnt) {
     size_t bytes = sizeof(**ptr) * (cnt > 0 ? cnt : 1);
@@ -492,25 +506,25 @@ cudaError_t setup_fp32(dm_plan *p) {
     if (!r) p->bytes += (int64_t)bytes;
     return r;
   };
-  if ((e = al(&p->phase32, p->ph_total))) return e;
-  if ((e = al(&p->bhat32, p->bh_total))) return e;
-  if ((e = al(&p->chirp32, p->ch_total))) return e;
-  if ((e = al(&p->twid32, p->fft_M_max - 1))) return e;
-  if ((e = al(&p->twr32, p->twr_words))) return e;
-  if ((e = al(&p->ptab, (size_t)3 * p->nalm * p->npairs))) return e;
-  if ((e = al(&p->ptab_lo, (size_t)3 * p->nalm * p->npairs))) return e;
-  if ((e = al(&p->rc32, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return e;
-  if ((e = al(&p->apart32, (size_t)B * p->nchunk * 3 * p->nalm))) return e;
-  if ((e = al(&p->s32, (size_t)B * n3))) return e;
-  if ((e = al(&p->w32, (size_t)B * n3))) return e;
-  if ((e = al(&p->wd32, (size_t)B * n3))) return e;
-  if ((e = al(&p->a_hi, (size_t)B * 3 * p->nalm))) return e;
-  if ((e = al(&p->g_hi, (size_t)B * 3 * p->nalm))) return e;
-  if ((e = al(&p->shi32, (size_t)B * n3))) return e;
-  if ((e = al(&p->e32, (size_t)B * 3 * p->nalm))) return e;
-  if ((e = al(&p->c32, (size_t)B * 3 * p->nalm))) return e;
-  if ((e = al(&p->clev, (size_t)B))) return e;
-  if ((e = al(&p->tc_err, 1))) return e;
+  if ((e = al(&p->phase32, p->ph_total))) return undo(e);
+  if ((e = al(&p->bhat32, p->bh_total))) return undo(e);
+  if ((e = al(&p->chirp32, p->ch_total))) return undo(e);
+  if ((e = al(&p->twid32, p->fft_M_max - 1))) return undo(e);
+  if ((e = al(&p->twr32, p->twr_words))) return undo(e);
+  if ((e = al(&p->ptab, (size_t)3 * p->nalm * p->npairs))) return undo(e);
+  if ((e = al(&p->ptab_lo, (size_t)3 * p->nalm * p->npairs))) return undo(e);
+  if ((e = al(&p->rc32, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return undo(e);
+  if ((e = al(&p->apart32, (size_t)B * p->nchunk * 3 * p->nalm))) return undo(e);
+  if ((e = al(&p->s32, (size_t)B * n3))) return undo(e);
+  if ((e = al(&p->w32, (size_t)B * n3))) return undo(e);
+  if ((e = al(&p->wd32, (size_t)B * n3))) return undo(e);
+  if ((e = al(&p->a_hi, (size_t)B * 3 * p->nalm))) return undo(e);
+  if ((e = al(&p->g_hi, (size_t)B * 3 * p->nalm))) return undo(e);
+  if ((e = al(&p->shi32, (size_t)B * n3))) return undo(e);
+  if ((e = al(&p->e32, (size_t)B * 3 * p->nalm))) return undo(e);
+  if ((e = al(&p->c32, (size_t)B * 3 * p->nalm))) return undo(e);
+  if ((e = al(&p->clev, (size_t)B))) return undo(e);
+  if ((e = al(&p->tc_err, 1))) return undo(e);
   cudaMemset(p->tc_err, 0, sizeof(int));
   cudaMemset(p->rc32, 0, sizeof(float2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
   k_d2f2<<<512, 256>>>(p->phase, p->phase32, p->ph_total);
@@ -518,8 +532,9 @@ cudaError_t setup_fp32(dm_plan *p) {
   if (p->ch_total > 0) k_d2f2<<<512, 256>>>(p->chirp, p->chirp32, p->ch_total);
   k_d2f2<<<64, 256>>>(p->twid, p->twid32, p->fft_M_max - 1);
   if (p->twr_words > 0) k_d2f2<<<64, 256>>>(p->twr, p->twr32, p->twr_words);
-  if ((e = gen_tables32(p))) return e;
-  return cudaDeviceSynchronize();
+  if ((e = gen_tables32(p))) return undo(e);
+  if ((e = cudaDeviceSynchronize())) return undo(e);
+  return cudaSuccess;
 }
 
 // When coef lies in p->filt, its FP32 copy goes to the same place of p->filt32.
