@@ -197,7 +197,9 @@ extern "C" dm_status dm_set_noise_cov(dm_plan *p, const double *sigma, const dou
     p->alpha[b] = alpha;
     p->t_h[b] = alpha * 4.0 * M_PI / (double)np;
   }
-  if (e) {
+  if (e) {  // the weights are partly overwritten: the plan needs its noise set again
+    p->have_noise = false;
+    p->cov = false;
     p->err = "upload correlated-noise weights";
     return DM_ECUDA;
   }
