@@ -509,6 +509,7 @@ dm_status dm_set_noise_mask(dm_plan *p, const double *sigma, const uint8_t *mask
   if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
   dm_status r = check_noise(p, sigma, mask);
   if (r != DM_OK) return r;
+  p->have_noise = false;  // until every RHS has the new model (a failed upload leaves none)
   r = upload_noise(p, 0, sigma, mask);
   if (r != DM_OK) return r;
   const int64_t np = p->npix;
@@ -531,12 +532,14 @@ dm_status dm_set_noise_mask_rhs(dm_plan *p, int b, const double *sigma, const ui
   if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
   dm_status r = check_noise(p, sigma, mask);
   if (r != DM_OK) return r;
+  p->have_noise = false;  // a failed upload leaves RHS b half-set: the plan then needs its noise again
   r = upload_noise(p, b, sigma, mask);
   if (r != DM_OK) return r;
   if (p->have_cl) {
     DM_CU(build_filters(p, b, 0), "filters");
     DM_CU(cudaDeviceSynchronize(), "filters");
   }
+  p->have_noise = true;
   return DM_OK;
 }
 
