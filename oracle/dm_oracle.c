@@ -1108,18 +1108,17 @@ static double weighted_half_norm2(int lmax, const double *half, const double *al
   return acc;
 }
 
-double orc_wf_residual(int nside, int lmax, const double *cl, const double *sigma, const uint8_t *mask,
-                       const double *d, const double *alm) {
-  long npix = orc_npix(nside), nalm = orc_nalm(lmax), n3 = 3 * npix;
+/* ||C^1/2 (A r - alpha Omega C^+ a)|| / ||C^1/2 A y|| for the weighted pixel
+ * maps r = W (d - Y a) and y = W d (each (l, m > 0) counted twice). */
+static double residual_ratio(int nside, int lmax, const double *cl, double alpha, const double *r, const double *y,
+                             const double *alm) {
+  long nalm = orc_nalm(lmax);
   const double *tt = cl, *ee = cl + (lmax + 1), *bb = cl + 2 * (lmax + 1), *te = cl + 3 * (lmax + 1);
-  double alpha = orc_alpha(npix, sigma, mask);
-  double omega = 4.0 * M_PI / (double)npix;
-  double *w = malloc(sizeof(double) * n3), *s = malloc(sizeof(double) * n3);
-  double *g = malloc(sizeof(double) * 6 * nalm), *y = malloc(sizeof(double) * 6 * nalm);
+  double omega = 4.0 * M_PI / (double)orc_npix(nside);
+  double *g = malloc(sizeof(double) * 6 * nalm), *ya = malloc(sizeof(double) * 6 * nalm);
   double *ca = malloc(sizeof(double) * 6 * nalm);
   double *pinv = malloc(sizeof(double) * 4 * (lmax + 1)), *proj = malloc(sizeof(double) * 4 * (lmax + 1));
   double *half = malloc(sizeof(double) * 4 * (lmax + 1));
-  orc_weights(npix, sigma, mask, alpha, w);
   orc_cl_pinv(lmax, cl, pinv, proj);
   for (int l = 0; l <= lmax; ++l) {
     double e1, e2, v1[2], v2[2];
@@ -1130,15 +1129,46 @@ double orc_wf_residual(int nside, int lmax, const double *cl, const double *sigm
     half[4 * l + 2] = r1 * v1[1] * v1[1] + r2 * v2[1] * v2[1];
     half[4 * l + 3] = bb[l] > 0.0 ? sqrt(bb[l]) : 0.0;
   }
-  for (long i = 0; i < n3; ++i) s[i] = w[i] * d[i];
-  orc_map2alm(nside, lmax, s, y);
-  orc_alm2map(nside, lmax, alm, s);
-  for (long i = 0; i < n3; ++i) s[i] = w[i] * (d[i] - s[i]);
-  orc_map2alm(nside, lmax, s, g);
+  orc_map2alm(nside, lmax, y, ya);
+  orc_map2alm(nside, lmax, r, g);
   memcpy(ca, alm, sizeof(double) * 6 * nalm);
   orc_apply_filter(lmax, pinv, ca);
   for (long i = 0; i < 6 * nalm; ++i) g[i] -= alpha * omega * ca[i];
-  const double num = weighted_half_norm2(lmax, half, g), den = weighted_half_norm2(lmax, half, y);
-  free(w); free(s); free(g); free(y); free(ca); free(pinv); free(proj); free(half);
+  const double num = weighted_half_norm2(lmax, half, g), den = weighted_half_norm2(lmax, half, ya);
+  free(g); free(ya); free(ca); free(pinv); free(proj); free(half);
   return den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+double orc_wf_residual(int nside, int lmax, const double *cl, const double *sigma, const uint8_t *mask,
+                       const double *d, const double *alm) {
+  long npix = orc_npix(nside), n3 = 3 * npix;
+  double alpha = orc_alpha(npix, sigma, mask);
+  double *w = malloc(sizeof(double) * n3), *r = malloc(sizeof(double) * n3), *y = malloc(sizeof(double) * n3);
+  orc_weights(npix, sigma, mask, alpha, w);
+  orc_alm2map(nside, lmax, alm, r);
+  for (long i = 0; i < n3; ++i) {
+    y[i] = w[i] * d[i];
+    r[i] = w[i] * (d[i] - r[i]);
+  }
+  const double out = residual_ratio(nside, lmax, cl, alpha, r, y, alm);
+  free(w); free(r); free(y);
+  return out;
+}
+
+/* The same with the correlated noise model: W = alpha N^-1 per pixel (3 x 3). */
+double orc_wf_residual_cov(int nside, int lmax, const double *cl, const double *sigma, const double *rho,
+                           const uint8_t *maskT, const uint8_t *maskP, const double *d, const double *alm) {
+  long npix = orc_npix(nside), n3 = 3 * npix;
+  double *ninv = malloc(sizeof(double) * 9 * npix), *s = malloc(sizeof(double) * n3);
+  double *r = malloc(sizeof(double) * n3), *y = malloc(sizeof(double) * n3), *z = malloc(sizeof(double) * n3);
+  orc_cov_ninv(npix, sigma, rho, maskT, maskP, ninv);
+  double alpha = orc_cov_alpha(npix, ninv);
+  orc_alm2map(nside, lmax, alm, s);
+  memset(z, 0, sizeof(double) * n3);
+  orc_messenger_update_cov(npix, alpha, ninv, d, z, y);  /* y = 0 + alpha N^-1 (d - 0) */
+  orc_messenger_update_cov(npix, alpha, ninv, d, s, r);  /* r = s + alpha N^-1 (d - s) */
+  for (long i = 0; i < n3; ++i) r[i] -= s[i];
+  const double out = residual_ratio(nside, lmax, cl, alpha, r, y, alm);
+  free(ninv); free(s); free(r); free(y); free(z);
+  return out;
 }

@@ -23,7 +23,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from tests.harmonics_ref import alm_to_params, dense_synthesis
+from tests.harmonics_ref import alm_to_params, dense_synthesis, params_to_alm
 from tests.test_oracle_dm import _dense_problem, _prior_precision
 
 
@@ -298,3 +298,39 @@ def test_cov_fluctuation_covariance_is_posterior(orc):
         q.append(f @ H @ f)
     n = len(params)
     assert abs(np.mean(q) - n) < 5 * np.sqrt(2.0 * n / K)
+
+
+def test_cov_true_residual_against_the_dense_normal_equations(orc):
+    """||A x - y|| / ||y|| with the block-diagonal N^-1 and distinct masks at
+    nside 4 (P the prior precision, Y from scipy and Goldberg): the oracle's
+    value equals the dense one at random iterates and vanishes at the dense
+    Wiener filter."""
+    nside, lmax = 4, 8
+    cl, params_all, sigma, mask, z, phi = _dense_problem(nside, lmax, 3)
+    npix = z.size
+    rng = np.random.default_rng(70)
+    rho = rng.uniform(-0.3, 0.3, (3, npix))
+    mask_t = (np.abs(z) > 0.25).astype(np.uint8)
+    mask_p = (np.abs(z - 0.1) > 0.2).astype(np.uint8)
+    ninv = orc.cov_ninv(sigma, rho, mask_t, mask_p)
+    params = [p for p in params_all if not (p[0] == 0 and p[1] == 0)]
+    Y = dense_synthesis(nside, lmax, z, phi, params)
+    Nd = np.zeros((3 * npix, 3 * npix))
+    for i in range(3):
+        for j in range(3):
+            Nd[i * npix + np.arange(npix), j * npix + np.arange(npix)] = ninv[:, i, j]
+    obs = np.stack([mask_t, mask_p, mask_p])
+    d = W.random_maps(nside, 1, 71)[0] * 0.05 * obs
+    P = _prior_precision(cl, params, 0.0)
+    e, v = np.linalg.eigh(P)
+    Pmh = (v / np.sqrt(e)) @ v.T
+    H = P + Y.T @ Nd @ Y
+    rhs = Y.T @ Nd @ d.reshape(-1)
+    dense = lambda x: np.linalg.norm(Pmh @ (H @ x - rhs)) / np.linalg.norm(Pmh @ rhs)
+    res = lambda x: orc.wf_residual_cov(nside, lmax, cl, sigma, rho, mask_t, mask_p, d,
+                                        params_to_alm(x, params, lmax))
+    x_wf = np.linalg.solve(H, rhs)
+    assert res(x_wf) < 1e-10
+    for scale in [1e-3, 1e-1, 1.0]:
+        x = x_wf + scale * np.linalg.norm(x_wf) / np.sqrt(len(x_wf)) * rng.standard_normal(len(x_wf))
+        assert res(x) == pytest.approx(dense(x), rel=1e-9)
