@@ -656,17 +656,11 @@ int orc_dm_solve(int nside, int lmax, const double *cl, const double *sigma, con
  * observed pixel-components plus a^dagger S^{-1} a over the harmonic modes of
  * a real field (m = 0 once, m > 0 twice), S^{-1} taken on the non-zero
  * eigenvalues of the per-l block of Eq. 10. */
-double orc_chi2(int nside, int lmax, const double *cl, const double *sigma, const uint8_t *mask,
-                const double *d, const double *s, const double *alm) {
-  long npix = orc_npix(nside), nalm = orc_nalm(lmax);
+/* a^dagger S^-1 a over the harmonic modes of a real field (m = 0 once,
+ * m > 0 twice), S^-1 on the non-zero eigenvalues of each l's block */
+static double chi2_prior(int lmax, const double *cl, const double *alm) {
+  long nalm = orc_nalm(lmax);
   double chi = 0.0;
-  for (int f = 0; f < 3; ++f)
-    for (long p = 0; p < npix; ++p)
-      if (!mask || mask[p]) {
-        double r = d[f * npix + p] - s[f * npix + p];
-        double n = sigma[f * npix + p] * sigma[f * npix + p];
-        chi += r * r / n;
-      }
   const double *tt = cl, *ee = cl + (lmax + 1), *bb = cl + 2 * (lmax + 1), *te = cl + 3 * (lmax + 1);
   for (int l = 0; l <= lmax; ++l) {
     double e1, e2, v1[2], v2[2];
@@ -684,6 +678,20 @@ double orc_chi2(int nside, int lmax, const double *cl, const double *sigma, cons
     }
   }
   return chi;
+}
+
+double orc_chi2(int nside, int lmax, const double *cl, const double *sigma, const uint8_t *mask,
+                const double *d, const double *s, const double *alm) {
+  long npix = orc_npix(nside);
+  double chi = 0.0;
+  for (int f = 0; f < 3; ++f)
+    for (long p = 0; p < npix; ++p)
+      if (!mask || mask[p]) {
+        double r = d[f * npix + p] - s[f * npix + p];
+        double n = sigma[f * npix + p] * sigma[f * npix + p];
+        chi += r * r / n;
+      }
+  return chi + chi2_prior(lmax, cl, alm);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1153,6 +1161,26 @@ double orc_wf_residual(int nside, int lmax, const double *cl, const double *sigm
   const double out = residual_ratio(nside, lmax, cl, alpha, r, y, alm);
   free(w); free(r); free(y);
   return out;
+}
+
+/* chi^2 of Eq. 3 with the correlated noise model: (d - s)^T N^-1 (d - s) with
+ * the per-pixel block N^-1 (zero rows and columns on masked components), plus
+ * the prior term of orc_chi2. */
+double orc_chi2_cov(int nside, int lmax, const double *cl, const double *sigma, const double *rho,
+                    const uint8_t *maskT, const uint8_t *maskP, const double *d, const double *s,
+                    const double *alm) {
+  long npix = orc_npix(nside);
+  double *ninv = malloc(sizeof(double) * 9 * npix);
+  orc_cov_ninv(npix, sigma, rho, maskT, maskP, ninv);
+  double chi = 0.0;
+  for (long p = 0; p < npix; ++p) {
+    double r[3];
+    for (int f = 0; f < 3; ++f) r[f] = d[f * npix + p] - s[f * npix + p];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) chi += r[a] * ninv[9 * p + 3 * a + b] * r[b];
+  }
+  free(ninv);
+  return chi + chi2_prior(lmax, cl, alm);
 }
 
 /* The same with the correlated noise model: W = alpha N^-1 per pixel (3 x 3). */

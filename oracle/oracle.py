@@ -60,6 +60,7 @@ def lib():
         L.orc_dm_solve_cov.restype = ctypes.c_int
         L.orc_wf_residual.restype = ctypes.c_double
         L.orc_wf_residual_cov.restype = ctypes.c_double
+        L.orc_chi2_cov.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -424,6 +425,19 @@ def wf_residual(nside, lmax, cl, sigma, mask, d, alm):
     a = np.ascontiguousarray(alm, dtype=np.complex128)
     m, mp = _mask_ptr(mask)
     return lib().orc_wf_residual(nside, lmax, _d(c), _d(sg), mp, _d(dd), _d(a.view(np.float64)))
+
+
+def chi2_cov(nside, lmax, cl, sigma, rho, maskT, maskP, d, s, alm):
+    """chi^2 of Eq. 3 with the correlated noise model (block N^-1)."""
+    c = np.ascontiguousarray(cl, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    rh = np.ascontiguousarray(rho, dtype=np.float64)
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    ss = np.ascontiguousarray(s, dtype=np.float64)
+    a = np.ascontiguousarray(alm, dtype=np.complex128)
+    mt, mtp = _mask_ptr(maskT)
+    mp_, mpp = _mask_ptr(maskP)
+    return lib().orc_chi2_cov(nside, lmax, _d(c), _d(sg), _d(rh), mtp, mpp, _d(dd), _d(ss), _d(a.view(np.float64)))
 
 
 def wf_residual_cov(nside, lmax, cl, sigma, rho, maskT, maskP, d, alm):

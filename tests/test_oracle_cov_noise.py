@@ -334,3 +334,34 @@ def test_cov_true_residual_against_the_dense_normal_equations(orc):
     for scale in [1e-3, 1e-1, 1.0]:
         x = x_wf + scale * np.linalg.norm(x_wf) / np.sqrt(len(x_wf)) * rng.standard_normal(len(x_wf))
         assert res(x) == pytest.approx(dense(x), rel=1e-9)
+
+
+def test_cov_chi2_minimum_is_the_dense_identity(orc):
+    """chi^2 with the block N^-1 at the dense Wiener filter equals
+    d^T N^-1 d - b^T H^-1 b (b = Y^T N^-1 d, H = P + Y^T N^-1 Y) at nside 4,
+    with distinct masks; at rho = 0 and one mask it is the diagonal chi^2."""
+    nside, lmax = 4, 8
+    cl, params_all, sigma, mask, z, phi = _dense_problem(nside, lmax, 3)
+    npix = z.size
+    rng = np.random.default_rng(74)
+    rho = rng.uniform(-0.3, 0.3, (3, npix))
+    mask_t = (np.abs(z) > 0.25).astype(np.uint8)
+    mask_p = (np.abs(z - 0.1) > 0.2).astype(np.uint8)
+    ninv = orc.cov_ninv(sigma, rho, mask_t, mask_p)
+    params = [p for p in params_all if not (p[0] == 0 and p[1] == 0)]
+    Y = dense_synthesis(nside, lmax, z, phi, params)
+    Nd = np.zeros((3 * npix, 3 * npix))
+    for i in range(3):
+        for j in range(3):
+            Nd[i * npix + np.arange(npix), j * npix + np.arange(npix)] = ninv[:, i, j]
+    d = W.random_maps(nside, 1, 75)[0] * 0.05 * np.stack([mask_t, mask_p, mask_p])
+    H = _prior_precision(cl, params, 0.0) + Y.T @ Nd @ Y
+    b = Y.T @ Nd @ d.reshape(-1)
+    x = np.linalg.solve(H, b)
+    a = params_to_alm(x, params, lmax)
+    s = orc.alm2map(nside, lmax, a)
+    got = orc.chi2_cov(nside, lmax, cl, sigma, rho, mask_t, mask_p, d, s, a)
+    assert got == pytest.approx(d.reshape(-1) @ Nd @ d.reshape(-1) - b @ x, rel=1e-10)
+    zero = np.zeros_like(rho)
+    assert orc.chi2_cov(nside, lmax, cl, sigma, zero, mask, mask, d, s, a) == pytest.approx(
+        orc.chi2(nside, lmax, cl, sigma, mask, d, s, a), rel=1e-13)

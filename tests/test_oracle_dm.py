@@ -313,3 +313,24 @@ def test_cr_power_spectrum_is_unbiased(orc):
     ref = cl[3, sel]
     sd = np.sqrt((cl[0, sel] * cl[1, sel] + ref ** 2) / (K * (2 * ells[sel] + 1)))
     assert abs(np.mean((pw[3, sel] - ref) / sd)) < 5.0 / np.sqrt(len(ref))
+
+
+def test_chi2_minimum_is_the_dense_identity(orc):
+    """At the Wiener filter x* = H^-1 b (H = P + Y^T N^-1 Y, b = Y^T N^-1 d),
+    chi^2 of Eq. 3 takes its minimum d^T N^-1 d - b^T H^-1 b: an exact check of
+    both terms of orc_chi2 at nside 4; away from x* it is larger."""
+    nside, lmax = 4, 8
+    cl, params_all, sigma, mask, z, phi = _dense_problem(nside, lmax, 3)
+    params = [p for p in params_all if not (p[0] == 0 and p[1] == 0)]
+    Y = dense_synthesis(nside, lmax, z, phi, params)
+    Ninv = (mask[None, :] / sigma ** 2).reshape(-1)
+    d = W.random_maps(nside, 1, 72)[0] * 0.05 * mask[None, :]
+    H = _prior_precision(cl, params, 0.0) + Y.T @ (Ninv[:, None] * Y)
+    b = Y.T @ (Ninv * d.reshape(-1))
+    x = np.linalg.solve(H, b)
+    ref = d.reshape(-1) @ (Ninv * d.reshape(-1)) - b @ x
+    a = params_to_alm(x, params, lmax)
+    got = orc.chi2(nside, lmax, cl, sigma, mask, d, orc.alm2map(nside, lmax, a), a)
+    assert got == pytest.approx(ref, rel=1e-10)
+    a2 = params_to_alm(x + 1e-2 * np.abs(x).max() * np.random.default_rng(73).standard_normal(len(x)), params, lmax)
+    assert orc.chi2(nside, lmax, cl, sigma, mask, d, orc.alm2map(nside, lmax, a2), a2) > got
