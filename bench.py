@@ -181,16 +181,55 @@ def traffic_for(kernel, workload):
     return None
 
 
+ORACLE_ITERS = 3
+
+
+def oracle_data(O, nside, lmax, wl):
+    """Data map of RHS 0 made on the host: the oracle's synthesis of the drawn
+    signal plus the drawn noise, masked (no value from the CUDA path)."""
+    return wl.data([O.alm2map(nside, lmax, wl.alm_true[0])])[0]
+
+
 def cpu_baseline(nside, lmax, wl, d0):
-    """The oracle as it stands, one dual messenger iteration of one RHS."""
+    """The oracle as it stands: ORACLE_ITERS dual messenger iterations of one
+    RHS at lambda = 1 (a bounded sample of the workload).  Its map is also the
+    reference of the bench line's error_vs_oracle."""
     from oracle import oracle as O
     cores = os.cpu_count()
     t0 = time.perf_counter()
-    O.dm_solve(nside, lmax, wl.cl, wl.sigma, wl.mask, d0, [1.0], forced_iters=[1])
+    ref = O.dm_solve(nside, lmax, wl.cl, wl.sigma, wl.mask, d0, [1.0], forced_iters=[ORACLE_ITERS])
     dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": "DM iterations/s", "cores": cores, "kind": "oracle",
-            "sample": f"1 dual messenger iteration of 1 RHS at nside {nside}, lmax {lmax} (FP64, {cores} OpenMP threads)",
-            "seconds": dt}
+    return {"value": ORACLE_ITERS / dt, "unit": "DM iterations/s", "cores": cores, "kind": "oracle",
+            "sample": f"{ORACLE_ITERS} dual messenger iterations of 1 RHS at nside {nside}, lmax {lmax}, lambda 1 "
+                      f"(FP64, {cores} OpenMP threads)",
+            "seconds": dt}, ref
+
+
+def error_vs_oracle(plan, d, d0, ref, prec, torch):
+    """The same ORACLE_ITERS iterations on the GPU in the bench's own launch
+    configuration (the whole batch, its precision and kernels), with RHS 0
+    holding the host-made data d0: relative L2 error of RHS 0's map and
+    coefficients against the oracle, plus the device diagnostics."""
+    from paper_1801_05358_gb300 import dmwf
+    dd = d.clone()
+    dd[0] = torch.from_numpy(d0).to(d.device)
+    plan.set_forced_iters(None)
+    plan.set_schedule(lambda0=1.0, n_levels=1, iters_per_level=ORACLE_ITERS, check_every=ORACLE_ITERS)
+    s = torch.zeros_like(dd)
+    a = torch.zeros((d.shape[0], 3, plan.nalm, 2), dtype=torch.float64, device=d.device)
+    st, stats = plan.wiener_filter(dd, s, a)
+    torch.cuda.synchronize()
+    s0 = s[0].cpu().numpy()
+    a0 = a[0].cpu().numpy().view(np.complex128)[..., 0]
+    e_s = float(np.linalg.norm(s0 - ref["s"]) / np.linalg.norm(ref["s"]))
+    e_a = float(np.linalg.norm(a0 - ref["alm"]) / np.linalg.norm(ref["alm"]))
+    out = {"rel_l2_map": e_s, "rel_l2_alm": e_a, "rhs": 0, "iterations": ORACLE_ITERS, "lambda": 1.0,
+           "bar": 1e-5 if prec != dmwf.DM_FP64 else 1e-10,
+           "note": "the bench's plan, batch and precision; RHS 0's data made on the host by the oracle's synthesis"}
+    for k in ("true_resid", "chi2"):
+        if k in stats[0]:
+            out["gpu_" + k] = stats[0][k]
+    return out
 
 
 def run_reference(args):
@@ -202,14 +241,13 @@ def run_reference(args):
     from oracle import oracle as O
     O.build()
     wl = W.make_workload("nside512", [100], nside=nside, lmax=lmax)
-    d0 = wl.data([O.alm2map(nside, lmax, wl.alm_true[0])])[0]
+    d0 = oracle_data(O, nside, lmax, wl)
     steps = max(1, min(args.steps, 4))
     warm = min(args.warmup, 1)
     for _ in range(warm):
         O.dm_solve(nside, lmax, wl.cl, wl.sigma, wl.mask, d0, [1.0], forced_iters=[1])
     t0 = time.perf_counter()
-    for _ in range(steps):
-        O.dm_solve(nside, lmax, wl.cl, wl.sigma, wl.mask, d0, [1.0], forced_iters=[1])
+    O.dm_solve(nside, lmax, wl.cl, wl.sigma, wl.mask, d0, [1.0], forced_iters=[steps])
     dt = time.perf_counter() - t0
     v = steps / dt
     cores = os.cpu_count()
@@ -503,14 +541,23 @@ def main():
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    # the K steps run as up to 16 equal chunks with an event pair each, for
+    # the median over chunks beside the total
+    nch = max(1, min(16, K))
+    sizes = [K // nch + (1 if j < K % nch else 0) for j in range(nch)]
+    cev = [torch.cuda.Event(enable_timing=True) for _ in range(nch + 1)]
     with ClockSampler(local) as clk:
         e0.record(stream)
-        plan.solve_iterate(K)
+        cev[0].record(stream)
+        for j, n in enumerate(sizes):
+            plan.solve_iterate(n)
+            cev[j + 1].record(stream)
         e1.record(stream)
         torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
+    chunk_ms = [cev[j].elapsed_time(cev[j + 1]) / sizes[j] for j in range(nch)]
     prof = plan.profile_read()
     plan.profile_enable(False)
     st, stats = plan.solve_end(s_out)
@@ -550,11 +597,16 @@ def main():
                 if "bf16_tflops_sustained" in peaks else "fallback 1700 TFLOP/s sustained (of fallback)")
     mixed = prec != dmwf.DM_FP64
     use_tc = mixed and B in (8, 16, 32, 64)
-    # ring stage (k_ring<RING_ITER>, one launch per FFT-size class): per pixel and
-    # RHS-field s read + s write + w read + (anchor map or w d) read; per ring, m
-    # and RHS-field the ring coefficient read + write
+    # ring stage (k_ring<RING_ITER>, one launch per FFT-size class).
+    # Algorithmic bytes (the map bytes of the hot-path scope): per pixel and
+    # RHS-field w d (the anchor map in the mixed mode), s_prev and s, in the
+    # map precision, with w shared by the batch.  What the kernel must also
+    # move, the ring coefficients (read + write per ring, m and RHS-field)
+    # and w per RHS, is implementation traffic, reported beside it.
+    px_alg = 12.0 if mixed else 24.0
+    ring_bytes = 3.0 * B * px_alg * npix
     px_b, rc_b = (16.0, 16.0) if mixed else (32.0, 32.0)
-    ring_bytes = 3.0 * B * (px_b * npix + rc_b * nrings * (mmax + 1))
+    ring_impl_bytes = 3.0 * B * (px_b * npix + rc_b * nrings * (mmax + 1))
     # Legendre contractions: 20 flops per (l, m, ring pair) triple per RHS
     # (T: lambda x 2 re/im; Q, U: lam+ and lam- x 4) -- executed on the tensor
     # cores as three BF16 products (hi*hi + hi*lo + lo*hi) in the mixed mode
@@ -565,11 +617,16 @@ def main():
     nparts = 1 if use_tc else (npairs + 63) // 64
     red_bytes = 3.0 * B * nalm * ((8.0 * nparts + 24.0) if mixed else (16.0 * nparts + 32.0))
 
-    def hbm_line(kernel, nbytes, ms, traffic_key):
+    def hbm_line(kernel, nbytes, ms, traffic_key, impl_bytes=None):
         ach = nbytes / (ms * 1e-3) / 1e9
-        return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "peak_source": hbm_src, "algorithmic_bytes": nbytes, "ms_per_launch": ms,
-                "traffic": traffic_for(traffic_key, workload_name)}
+        tr = traffic_for(traffic_key, workload_name)
+        out = {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+               "peak_source": hbm_src, "algorithmic_bytes": nbytes, "ms_per_launch": ms, "traffic": tr,
+               "traffic_over_algorithmic": (tr / nbytes) if tr else None}
+        if impl_bytes is not None:
+            out["implementation_bytes"] = impl_bytes
+            out["implementation_frac"] = impl_bytes / (ms * 1e-3) / 1e9 / hbm
+        return out
 
     def leg_line(kernel, ms, traffic_key):
         if use_tc:
@@ -587,7 +644,7 @@ def main():
 
     stages = {
         "ring": hbm_line("k_ring<RING_ITER> (one launch per FFT-size class)", ring_bytes, stage["ms_ring"],
-                         "k_ring_iter"),
+                         "k_ring_iter", ring_impl_bytes),
         "synthesis": leg_line("k_syn_b + k_syn_tc<0,1>" if use_tc else ("k_leg_syn32" if mixed else "k_leg_syn64"),
                               stage["ms_synthesis"], "k_syn_tc" if use_tc else "k_leg_syn64"),
         "analysis": leg_line("k_ana_tc<0,1>" if use_tc else ("k_leg_ana32" if mixed else "k_leg_ana64"),
@@ -622,11 +679,13 @@ def main():
                        f"iterations, end); d in and s out once per call"}
 
     # ---- CPU baseline (oracle), rank 0 at N = 1 only ----
-    cpu = None
+    cpu, err = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
         O.build()
-        cpu = cpu_baseline(nside, lmax, wl, d[0].cpu().numpy())
+        d0 = oracle_data(O, nside, lmax, wl)
+        cpu, ref0 = cpu_baseline(nside, lmax, wl, d0)
+        err = error_vs_oracle(plan, d, d0, ref0, prec, torch)
 
     if rank == 0:
         line = {"metric": "DM iterations/s", "value": value, "unit": "DM iterations/s", "n_gpus": ws,
@@ -640,6 +699,10 @@ def main():
                            "ring_radix": "plan default" if args.ring_radix is None else args.ring_radix,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "l2": "inputs larger than L2 (maps and ring coefficients exceed 129 MB)"},
+                "ms_per_step_median": float(np.median(chunk_ms)),
+                "timing": {"chunks": nch, "chunk_ms_per_step": chunk_ms,
+                           "median_ms_per_step": float(np.median(chunk_ms))},
+                "error_vs_oracle": err,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["launches"],
                 "fp64_gpu": fp64_line, "ff64_gpu": ff_line, "refinement": anchor,
                 "clocks": clk.summary()}

@@ -94,12 +94,28 @@ typedef struct {
 
 #define DM_MAX_LEVELS 64
 
-/* Per-RHS statistics, valid after the call returns. */
+/* Per-RHS statistics, valid after the call returns.
+ * true_resid and chi2 are the paper's quality measures of the final iterate
+ * (Section 3.2, Table 1; Appendix C), evaluated on the device in FP64-class
+ * arithmetic (FP64, or float-float Legendre stages in DM_FLOAT_FLOAT and for
+ * the mixed mode's float-float anchors):
+ *  true_resid = ||A x - y|| / ||y||, A = 1 + S^1/2 Y^T N^-1 Y S^1/2,
+ *               x = S^-1/2 a, y = S^1/2 Y^T N^-1 d  (with the analysis
+ *               A = Omega Y^T standing in for Y^T, as in the iteration);
+ *  chi2       = (d - s)^T N^-1 (d - s) + a^T S^+ a  (Eq. 3; observed
+ *               pixel-components only, S^+ the per-l pseudo-inverse).
+ * Both are NaN when dm_set_diagnostics turned them off or under correlated
+ * noise (dm_set_noise_cov).  For a constrained realisation they describe its
+ * Wiener-filter solve W(d - dhat).  ms_total is the device time of the call
+ * (or from dm_solve_begin to dm_solve_end), diagnostics excluded. */
 typedef struct {
   int iters_total;
   int levels_done;
   int iters_per_level[DM_MAX_LEVELS];
   double cauchy_final;
+  double true_resid;
+  double chi2;
+  float ms_total;
 } dm_stats;
 
 /* --- plan ------------------------------------------------------------------ */
@@ -195,6 +211,12 @@ dm_status dm_solve_begin(dm_plan *plan, const double *d, void *stream);
 dm_status dm_solve_iterate(dm_plan *plan, int max_iters, int *all_done, void *stream);
 dm_status dm_solve_end(dm_plan *plan, double *s_out, double *alm_out, dm_stats *stats, void *stream);
 
+/* End-of-solve diagnostics (default on): with a non-NULL stats argument the
+ * solve calls evaluate true_resid and chi2 of dm_stats, at the cost of two
+ * FP64-class analyses and map reductions per call (Section 3.2, Appendix C).
+ * 0 turns them off (the fields are then NaN). */
+dm_status dm_set_diagnostics(dm_plan *plan, int on);
+
 /* Mixed precision refinement: the FP32 stages act on the correction
  * e = a - a_hi around an FP64 anchor a_hi, and A W (d - Y a_hi) is recomputed
  * with the FP64 transforms every anchor_every iterations (default 256) and at
@@ -277,7 +299,9 @@ dm_status dm_apply_filter(dm_plan *plan, double lambda, const double *alm_in, do
  * the plan's workspace; plans needing more (batch x ceil(2 nside / 64) x 3 x
  * nalm x 16 bytes) get DM_EINVAL with a message.  The first call on each
  * device looks the array's address up (cudaGetSymbolAddress) with that device
- * current: make it before any stream capture.  Calls share the array, so
+ * current: make it before any stream capture.  The address is cached for the
+ * life of the process: after cudaDeviceReset on a device, do not call this
+ * entry point on that device again.  Calls share the array, so
  * calls that overlap on the GPU race and must be serialised by the caller;
  * every value the call reads from the array it wrote first, so nothing needs
  * clearing between calls.  No cudaMalloc, cudaFree or allocating library call

@@ -49,9 +49,12 @@ void free_all(dm_plan *p) {
                   p->a_hi, p->g_hi, p->shi32, p->s64, p->rhi, p->tc_err, p->ring_order, p->pair_order,
                   p->tc_synA[0], p->tc_synA[1], p->tc_anaA[0], p->tc_anaA[1], p->tc_soff, p->tc_aoff,
                   p->tc_synB[0], p->tc_synB[1], p->ptab_lo, p->e32, p->c32, p->clev, p->filt32,
-                  p->twr, p->twr32, p->chirp, p->chirp32, p->wcov};
+                  p->twr, p->twr32, p->chirp, p->chirp32, p->wcov, p->diag_tab, p->diag_alm, p->diag_part,
+                  p->diag_ao};
   for (void *q : ptrs)
     if (q) cudaFree(q);
+  if (p->ev_begin) cudaEventDestroy(p->ev_begin);
+  if (p->ev_end) cudaEventDestroy(p->ev_end);
 }
 
 void default_schedule(dm_schedule *s) {
@@ -338,9 +341,21 @@ dm_status run_dm(dm_plan *p, const double *d, cudaStream_t st) {
 
 namespace {
 
-void fill_stats(dm_plan *p, dm_stats *stats, dm_status *rs) {
+// Stats of every RHS after a solve (the stream is synchronised): counts,
+// Cauchy value, the FP64 diagnostics when enabled and ms_total from the
+// solve's begin and end events.
+void fill_stats(dm_plan *p, dm_stats *stats, dm_status *rs, cudaStream_t st) {
   std::vector<SolveState> hs(p->batch);
   cudaMemcpy(hs.data(), p->state, sizeof(SolveState) * p->batch, cudaMemcpyDeviceToHost);
+  std::vector<double> resid(p->batch, NAN), chi2(p->batch, NAN);
+  float ms = NAN;
+  if (stats) {
+    if (cudaEventSynchronize(p->ev_end) == cudaSuccess) cudaEventElapsedTime(&ms, p->ev_begin, p->ev_end);
+    if (p->diag_on) {
+      cudaError_t e = diagnostics(p, st, resid, chi2);
+      if (e != cudaSuccess && *rs == DM_OK) *rs = cuda_fail(p, e, "diagnostics");
+    }
+  }
   bool notconv = false;
   for (int b = 0; b < p->batch; ++b) {
     notconv = notconv || hs[b].notconv;
@@ -351,6 +366,9 @@ void fill_stats(dm_plan *p, dm_stats *stats, dm_status *rs) {
     o.levels_done = hs[b].done ? p->sched.n_levels : hs[b].level;
     for (int k = 0; k < DM_MAX_LEVELS; ++k) o.iters_per_level[k] = hs[b].iters_per_level[k];
     o.cauchy_final = hs[b].cauchy;
+    o.true_resid = resid[b];
+    o.chi2 = chi2[b];
+    o.ms_total = ms;
   }
   if (notconv && *rs == DM_OK) *rs = fail(p, DM_ENOTCONV, "max_iter reached before the last level converged");
 }
@@ -407,6 +425,7 @@ dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out) {
   if ((e = dalloc(p, &p->coef_tmp, 4 * (size_t)(lmax + 1)))) return bad(e, "alloc coef");
   if ((e = dalloc(p, &p->s64, (size_t)B * n3))) return bad(e, "alloc s");
   if ((e = dalloc(p, &p->rhi, (size_t)B * n3))) return bad(e, "alloc rhi");
+  if ((e = cudaEventCreate(&p->ev_begin)) || (e = cudaEventCreate(&p->ev_end))) return bad(e, "events");
   cudaMemset(p->rc, 0, sizeof(double2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
   cudaMemset(p->mask, 1, (size_t)B * p->npix);
   dm_status s = upload_levels(p);
@@ -470,6 +489,7 @@ dm_status dm_set_spectra(dm_plan *p, const double *cl) {
   }
   p->cl_h.assign(cl, cl + 4 * L);
   DM_CU(cudaMemcpy(p->cl, cl, sizeof(double) * 4 * L, cudaMemcpyHostToDevice), "upload cl");
+  DM_CU(diag_tables(p), "diagnostic tables");
   p->have_cl = true;
   return refresh_filters(p);
 }
@@ -581,12 +601,14 @@ dm_status dm_wiener_filter(dm_plan *p, const double *d, double *s_out, double *a
   if (r != DM_OK) return r;
   if (!d || !s_out) return fail(p, DM_EINVAL, "null buffer");
   cudaStream_t st = (cudaStream_t)stream;
+  DM_CU(cudaEventRecord(p->ev_begin, st), "event");
   r = run_dm(p, d, st);
   if (r != DM_OK && r != DM_ENOTCONV) return r;
   dm_status r2 = solve_end(p, s_out, alm_out, st, false);
   if (r2 != DM_OK) return r2;
+  DM_CU(cudaEventRecord(p->ev_end, st), "event");
   DM_CU(cudaStreamSynchronize(st), "sync");
-  fill_stats(p, stats, &r);
+  fill_stats(p, stats, &r, st);
   return r;
 }
 
@@ -597,14 +619,16 @@ dm_status dm_wiener_filter_host(dm_plan *p, const double *d_host, double *s_host
   if (!d_host || !s_host) return fail(p, DM_EINVAL, "null buffer");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t mb = sizeof(double) * 3 * p->npix * p->batch;
+  DM_CU(cudaEventRecord(p->ev_begin, st), "event");
   // tmpmap2 holds d
   DM_CU(cudaMemcpyAsync(p->tmpmap2, d_host, mb, cudaMemcpyHostToDevice, st), "h2d");
   r = run_dm(p, p->tmpmap2, st);
   if (r != DM_OK && r != DM_ENOTCONV) return r;
   dm_status r2 = solve_end(p, s_host, alm_host, st, true);
   if (r2 != DM_OK) return r2;
+  DM_CU(cudaEventRecord(p->ev_end, st), "event");
   DM_CU(cudaStreamSynchronize(st), "sync");
-  fill_stats(p, stats, &r);
+  fill_stats(p, stats, &r, st);
   return r;
 }
 
@@ -637,6 +661,7 @@ dm_status dm_constrained_realization(dm_plan *p, const double *d, const uint64_t
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = 3 * p->npix * p->batch;
   // shat -> tmpmap, ahat -> tmpalm, dhat -> tmpmap2, then tmpmap2 = d - dhat
+  DM_CU(cudaEventRecord(p->ev_begin, st), "event");
   DM_CU(cudaMemcpyAsync(p->seeds_dev, seeds, sizeof(uint64_t) * p->batch, cudaMemcpyHostToDevice, st), "seeds");
   DM_CU(draw_signal(p, p->seeds_dev, p->tmpalm, st), "draw signal");
   DM_CU(legendre_synthesis(p, p->tmpalm, st), "synthesis");
@@ -650,8 +675,9 @@ dm_status dm_constrained_realization(dm_plan *p, const double *d, const uint64_t
   if (r2 != DM_OK) return r2;
   DM_CU(axpy_maps(n, p->tmpmap, 1.0, s_cr_out, st), "+ shat");
   if (alm_cr_out) DM_CU(axpy_maps(6 * p->nalm * p->batch, (const double *)p->tmpalm, 1.0, alm_cr_out, st), "+ ahat");
+  DM_CU(cudaEventRecord(p->ev_end, st), "event");
   DM_CU(cudaStreamSynchronize(st), "sync");
-  fill_stats(p, stats, &r);
+  fill_stats(p, stats, &r, st);
   return r;
 }
 
@@ -718,6 +744,7 @@ dm_status dm_solve_begin(dm_plan *p, const double *d, void *stream) {
   if (r != DM_OK) return r;
   if (!d) return fail(p, DM_EINVAL, "null buffer");
   if (p->session) return fail(p, DM_EBUSY, "a solve is already in progress on this plan");
+  DM_CU(cudaEventRecord(p->ev_begin, (cudaStream_t)stream), "event");
   r = solve_begin(p, d, (cudaStream_t)stream);
   if (r != DM_OK) end_session(p);
   return r;
@@ -734,9 +761,16 @@ dm_status dm_solve_end(dm_plan *p, double *s_out, double *alm_out, dm_stats *sta
   cudaStream_t st = (cudaStream_t)stream;
   dm_status r = solve_end(p, s_out, alm_out, st, false);
   if (r != DM_OK) return r;
+  DM_CU(cudaEventRecord(p->ev_end, st), "event");
   DM_CU(cudaStreamSynchronize(st), "sync");
-  fill_stats(p, stats, &r);
+  fill_stats(p, stats, &r, st);
   return r;
+}
+
+dm_status dm_set_diagnostics(dm_plan *p, int on) {
+  if (!p) return DM_EINVAL;
+  p->diag_on = on != 0;
+  return DM_OK;
 }
 
 dm_status dm_set_tensor_cores(dm_plan *p, int on) {

@@ -178,6 +178,13 @@ struct dm_plan {
   int since_anchor = 0;
   int64_t iters_launched = 0;
   int64_t bh_total = 0, ph_total = 0;
+  // end-of-solve diagnostics (dm_diag.cu): true residual and chi^2 in FP64
+  bool diag_on = true;
+  double *diag_tab = nullptr;   // [lmax+1][8]: C^1/2 and C^+ per l (tt, te, ee, bb)
+  double2 *diag_alm = nullptr;  // [B][3][nalm] analysis of w d, then of w (d - Y a)
+  double *diag_part = nullptr;  // per-block partial sums
+  double *diag_ao = nullptr;    // [B] alpha Omega
+  cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // ms_total of a solve
   // measurement
   bool prof_on = false;
   dm_profile prof{};
@@ -247,5 +254,9 @@ cudaError_t draw_signal(dm_plan *p, const uint64_t *seeds_dev, double2 *ahat, cu
 cudaError_t draw_noise_add(dm_plan *p, const uint64_t *seeds_dev, const double *shat, double *dhat,
                            cudaStream_t st);
 cudaError_t axpy_maps(int64_t n, const double *x, double alpha, double *y, cudaStream_t st);
+
+// end-of-solve diagnostics (dm_diag.cu)
+cudaError_t diag_tables(dm_plan *p);
+cudaError_t diagnostics(dm_plan *p, cudaStream_t st, std::vector<double> &resid, std::vector<double> &chi2);
 
 }  // namespace dmwf

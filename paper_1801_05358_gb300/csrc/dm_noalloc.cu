@@ -19,6 +19,9 @@
 // exits (DM_NOALLOC_SCRATCH_BYTES bytes).  Its device address is looked up
 // once per device with cudaGetSymbolAddress on the first call made with that
 // device current; make that first call before any stream capture starts.
+// The cached address belongs to the device's current context: a caller that
+// ends that context (cudaDeviceReset) must not call this entry point on that
+// device again in the same process, since the cache is not looked up anew.
 // All calls share the array: calls that overlap on the GPU (different streams
 // or threads) race on it and must be serialised by the caller.  Every partial
 // sum the reduction reads is written by the same call first, so nothing in the
@@ -28,6 +31,7 @@
 #include <mutex>
 
 #include "dm_internal.h"
+#include "dm_rec.cuh"
 
 #define DM_NOALLOC_SCRATCH_BYTES (64u << 20)
 
@@ -43,50 +47,6 @@ std::mutex g_mu;
 double2 *g_ptr[64] = {nullptr};
 
 __device__ __forceinline__ int64_t na_base(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
-
-struct NaRec {
-  double l0, l1, p0, p1, q0, q1;
-  int S;
-};
-
-__device__ __forceinline__ void na_step(NaRec &s, const dmwf::RecCoef &c, double x, int m, int l, const double *seed,
-                                        int p, int npairs) {
-  if (m < 2 && l + 1 == 2) {
-    const int64_t o = (int64_t)m * npairs + p;
-    const double nl = fma(c.al * x, s.l0, -c.bl * s.l1);
-    s.l1 = s.l0;
-    s.l0 = nl;
-    s.p1 = 0.0;
-    s.q1 = 0.0;
-    s.p0 = seed[3 * o + 1];
-    s.q0 = seed[3 * o + 2];
-  } else {
-    const double nl = fma(c.al * x, s.l0, -c.bl * s.l1);
-    // 2lambda and -2lambda as separate recurrences (p, q)
-    const double cp = fma(c.a, x, c.ac), cm = fma(c.a, x, -c.ac);
-    const double np = fma(cp, s.p0, -c.b * s.p1);
-    const double nq = fma(cm, s.q0, -c.b * s.q1);
-    s.l1 = s.l0;
-    s.l0 = nl;
-    s.p1 = s.p0;
-    s.p0 = np;
-    s.q1 = s.q0;
-    s.q0 = nq;
-  }
-  if (s.S) {
-    const double big = 0x1p300;
-    if (fabs(s.l0) > big || fabs(s.p0) > big || fabs(s.q0) > big) {
-      s.l0 *= 0x1p-300; s.l1 *= 0x1p-300; s.p0 *= 0x1p-300;
-      s.p1 *= 0x1p-300; s.q0 *= 0x1p-300; s.q1 *= 0x1p-300;
-      s.S -= 300;
-      if (s.S < 600) {
-        const double f = ldexp(1.0, -s.S);
-        s.l0 *= f; s.l1 *= f; s.p0 *= f; s.p1 *= f; s.q0 *= f; s.q1 *= f;
-        s.S = 0;
-      }
-    }
-  }
-}
 
 // Legendre analysis partial sums over one chunk of 64 ring pairs, reading the
 // ring coefficients in the public layout rc[b][f][ring][m].
@@ -117,17 +77,8 @@ __global__ void __launch_bounds__(NA_P) k_na_ana(const dmwf::PairDev *__restrict
       G[t][2 * f + 1] = make_double2(gn.x - gs.x, gn.y - gs.y);
     }
   }
-  NaRec s;
-  {
-    const int64_t o = (int64_t)m * npairs + pp;
-    s.l0 = seed[3 * o];
-    s.l1 = 0.0;
-    s.S = seed_exp[o];
-    s.p0 = (m >= 2) ? seed[3 * o + 1] : 0.0;
-    s.q0 = (m >= 2) ? seed[3 * o + 2] : 0.0;
-    s.p1 = 0.0;
-    s.q1 = 0.0;
-  }
+  dmwf::Rec s;
+  dmwf::rec_init(s, seed, seed_exp, m, pp, npairs);
   const int64_t base = na_base(lmax, m);
   const int lj = t % NA_L, part_id = t / NA_L;
   for (int lc = m; lc <= lmax; lc += NA_L) {
@@ -141,7 +92,7 @@ __global__ void __launch_bounds__(NA_P) k_na_ana(const dmwf::PairDev *__restrict
       P0[t][j] = live ? s.l0 : 0.0;
       Pp[t][j] = live ? 0.5 * (s.p0 + s.q0) : 0.0;  // lam+
       Pq[t][j] = live ? 0.5 * (s.p0 - s.q0) : 0.0;  // lam-
-      if (l < lmax) na_step(s, sc[j], x, m, l, seed, pp, npairs);
+      if (l < lmax) dmwf::rec_advance(s, sc[j], x, m, l, seed, pp, npairs);
     }
     __syncthreads();
     double aTr = 0, aTi = 0, aEr = 0, aEi = 0, aBr = 0, aBi = 0;
@@ -209,7 +160,15 @@ extern "C" dm_status dm_legendre_analysis_noalloc(dm_plan *p, const double *rc, 
     return DM_EINVAL;
   }
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DM_ECUDA;
+  const cudaError_t eg = cudaGetDevice(&dev);
+  if (eg != cudaSuccess) {
+    p->err = std::string("dm_legendre_analysis_noalloc: cudaGetDevice failed: ") + cudaGetErrorString(eg);
+    return DM_ECUDA;
+  }
+  if (dev < 0 || dev >= 64) {
+    p->err = "dm_legendre_analysis_noalloc: device ordinal " + std::to_string(dev) + " beyond the 64 this call tracks";
+    return DM_ECUDA;
+  }
   double2 *scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -492,11 +492,15 @@ cudaError_t setup_fp32(dm_plan *p) {
                     (void **)&p->apart32, (void **)&p->s32,    (void **)&p->w32,     (void **)&p->wd32,
                     (void **)&p->a_hi,    (void **)&p->g_hi,   (void **)&p->shi32,   (void **)&p->e32,
                     (void **)&p->c32,     (void **)&p->clev,   (void **)&p->tc_err};
+  // the workspace figure goes back to what it was on entry, so a failed
+  // set-up (and its retries) does not inflate dm_plan_info's byte count
+  const int64_t bytes_on_entry = p->bytes;
   auto undo = [&](cudaError_t err) {
     for (void **q : owned) {
       if (*q) cudaFree(*q);
       *q = nullptr;
     }
+    p->bytes = bytes_on_entry;
     return err;
   };
   const int64_t B = p->batch, n3 = 3 * p->npix;

@@ -28,7 +28,7 @@ EXPORTS = [
     "dm_solve_end", "dm_set_refinement", "dm_set_noise_mask_rhs", "dm_server_create", "dm_serve_submit",
     "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores", "dm_set_ring_radix",
     "dm_set_anchor_precision", "dm_set_noise_cov",
-    "dm_legendre_analysis_noalloc",
+    "dm_legendre_analysis_noalloc", "dm_set_diagnostics",
 ]
 DM_REQ_WF, DM_REQ_CR = 0, 1
 
@@ -41,7 +41,8 @@ class DmSchedule(ctypes.Structure):
 
 class DmStats(ctypes.Structure):
     _fields_ = [("iters_total", ctypes.c_int), ("levels_done", ctypes.c_int),
-                ("iters_per_level", ctypes.c_int * DM_MAX_LEVELS), ("cauchy_final", ctypes.c_double)]
+                ("iters_per_level", ctypes.c_int * DM_MAX_LEVELS), ("cauchy_final", ctypes.c_double),
+                ("true_resid", ctypes.c_double), ("chi2", ctypes.c_double), ("ms_total", ctypes.c_float)]
 
 
 class DmProfile(ctypes.Structure):
@@ -120,6 +121,7 @@ def lib():
         L.dm_set_refinement.argtypes = [vp, ctypes.c_int]
         L.dm_set_anchor_precision.argtypes = [vp, ctypes.c_int]
         L.dm_set_tensor_cores.argtypes = [vp, ctypes.c_int]
+        L.dm_set_diagnostics.argtypes = [vp, ctypes.c_int]
         L.dm_set_noise_mask_rhs.argtypes = [vp, ctypes.c_int, vp, vp]
         L.dm_server_create.argtypes = [ctypes.POINTER(DmServerConfig), ctypes.POINTER(vp)]
         L.dm_serve_submit.argtypes = [vp, ctypes.POINTER(DmRequest), ctypes.POINTER(ctypes.c_uint64)]
@@ -246,7 +248,8 @@ class Plan:
     @staticmethod
     def _stats_out(stats_arr):
         return [dict(iters_total=s.iters_total, levels_done=s.levels_done,
-                     iters_per_level=list(s.iters_per_level), cauchy_final=s.cauchy_final) for s in stats_arr]
+                     iters_per_level=list(s.iters_per_level), cauchy_final=s.cauchy_final,
+                     true_resid=s.true_resid, chi2=s.chi2, ms_total=s.ms_total) for s in stats_arr]
 
     def wiener_filter(self, d, s_out, alm_out=None, stream=None):
         stats = (DmStats * self.batch)()
@@ -267,6 +270,10 @@ class Plan:
         st = lib().dm_solve_end(self.h, _ptr(s_out), _ptr(alm_out), stats, _stream(stream))
         self._check(st, allow=(DM_ENOTCONV,))
         return st, self._stats_out(stats)
+
+    def set_diagnostics(self, on=True):
+        """End-of-solve true residual and chi^2 in the stats (default on)."""
+        self._check(lib().dm_set_diagnostics(self.h, 1 if on else 0))
 
     def set_tensor_cores(self, on=True):
         self._check(lib().dm_set_tensor_cores(self.h, 1 if on else 0))

@@ -48,3 +48,34 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(dmwf, "LIB_PATH", "/nonexistent/libdmwf.so")
     with pytest.raises(ImportError):
         dmwf.lib()
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets the C
+    compiler gives it from include/dmwf.h (gcc, host ABI)."""
+    import shutil
+    import subprocess
+
+    from paper_1801_05358_gb300 import dmwf
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no host C compiler")
+    pairs = {"dm_schedule": dmwf.DmSchedule, "dm_stats": dmwf.DmStats, "dm_profile": dmwf.DmProfile,
+             "dm_server_config": dmwf.DmServerConfig, "dm_request": dmwf.DmRequest, "dm_result": dmwf.DmResult,
+             "dm_server_info_t": dmwf.DmServerInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dmwf.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

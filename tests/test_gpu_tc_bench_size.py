@@ -13,9 +13,7 @@ edges and the equator; the orders cover m = 0, small m, the middle and
 m = lmax.  Bar: 2e-5 relative L2 over the samples, the single-transform
 bound of the smaller tensor-core tests.  A CPU model of the arithmetic (BF16
 hi/lo operands, the three products, FP32 sums per K step of 16) gives
-2e-6 to 5e-6 on spin-0 synthesis rings at this size.  This file is
-collected last: it is the newest GPU test, so a run stopping at the first
-failure has already run every other test."""
+2e-6 to 5e-6 on spin-0 synthesis rings at this size."""
 import numpy as np
 import pytest
 
