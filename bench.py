@@ -58,7 +58,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ring-radix", type=int, default=None, choices=[0, 3, 4],
-                    help="ring transforms of radix 2^k (3 or 4), 0 = generic kernels (default: the plan's)")
+                    help="ring transforms of radix 2^k (3 or 4), 0 = generic kernels (default: autotuned)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in launch heuristics instead of dm_autotune's picks")
     ap.add_argument("--solve-tol", type=float, default=None,
                     help="run whole solves to this final Cauchy threshold and report WF solves/s instead")
     ap.add_argument("--solve-max-iter", type=int, default=200000)
@@ -525,6 +527,11 @@ def main():
         ff_line = {"value": B * nf / (fms * 1e-3), "unit": "DM iterations/s", "steps": nf,
                    "ms_per_step": fms / nf, "precision": "DM_FLOAT_FLOAT"}
     plan.set_precision(prec)
+    tuning = None
+    if args.ring_radix is None and not args.no_autotune:
+        t0 = time.perf_counter()
+        tuning = plan.autotune()
+        tuning["seconds"] = time.perf_counter() - t0
 
     # ---- warm-up: begin a solve and run W iterations through the public API ----
     real_schedule(max(1, K))
@@ -696,7 +703,8 @@ def main():
                 "config": {"workload": f"batched constrained realisations nside {nside} lmax {lmax}: "
                                        f"{nwf} WF + {B - nwf} fluctuation RHS per launch (seeds 100..{99 + B})",
                            "nside": nside, "lmax": lmax, "batch": B, "precision": args.precision,
-                           "ring_radix": "plan default" if args.ring_radix is None else args.ring_radix,
+                           "ring_radix": ("autotuned" if tuning else "plan default") if args.ring_radix is None
+                           else args.ring_radix,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "l2": "inputs larger than L2 (maps and ring coefficients exceed 129 MB)"},
                 "ms_per_step_median": float(np.median(chunk_ms)),
@@ -704,7 +712,7 @@ def main():
                            "median_ms_per_step": float(np.median(chunk_ms))},
                 "error_vs_oracle": err,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["launches"],
-                "fp64_gpu": fp64_line, "ff64_gpu": ff_line, "refinement": anchor,
+                "fp64_gpu": fp64_line, "ff64_gpu": ff_line, "refinement": anchor, "autotune": tuning,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     plan.close()

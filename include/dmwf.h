@@ -308,6 +308,51 @@ dm_status dm_apply_filter(dm_plan *plan, double lambda, const double *alm_in, do
  * is made. */
 dm_status dm_legendre_analysis_noalloc(dm_plan *plan, const double *rc, double *alm, void *stream);
 
+/* --- launch tuning ----------------------------------------------------- */
+
+#define DM_TUNE_MAX_CLASSES 12
+
+/* Launch configuration of the iteration's kernels (no counterpart in the
+ * paper; a property of this library).  Ring stage: one launch per FFT-size
+ * class of rings (classes ordered by decreasing FFT size); per class the
+ * radix of the fixed-size transforms (3: radix 8, 4: radix 16, 0: the generic
+ * radix-4 kernels; classes whose size is not a power of two in [512, 4096]
+ * always run the generic ones) and the (RHS, field) lanes per block.
+ * Tensor-core stages (DM_MIXED_FP32 with 8, 16, 32 or 64 RHS): pipeline
+ * stages of the spin-0 and spin-2 synthesis kernels, l tiles per CTA and
+ * pipeline stages of the two analysis kernels.  A value of 0 (-1 for a
+ * radix) means the built-in heuristic.  The ms_ fields report the stage time
+ * per iteration of the pick and of the heuristic, as measured by
+ * dm_autotune (0 when not measured). */
+typedef struct {
+  int n_ring_classes;
+  int ring_radix_lr[DM_TUNE_MAX_CLASSES];
+  int ring_lanes[DM_TUNE_MAX_CLASSES];
+  int syn_stages[2];
+  int ana_ltiles[2];
+  int ana_stages[2];
+  float ms_ring, ms_ring_default;
+  float ms_synthesis, ms_synthesis_default;
+  float ms_analysis, ms_analysis_default;
+  int from_cache;  /* 1: taken from the process-wide cache without measuring */
+} dm_tuning;
+
+/* Time the candidate launch configurations of the plan's current precision
+ * on its own buffers with CUDA events on `stream` and keep the fastest per
+ * launch.  Results are cached per process for (device, nside, lmax, batch,
+ * precision, tensor cores); a later plan of the same kind takes them without
+ * measuring unless force != 0.  Outside a solve only (DM_EBUSY during one);
+ * it overwrites the plan's iteration buffers, so call it before
+ * dm_solve_begin.  Results of a solve do not depend on the configuration
+ * beyond rounding.  Synchronises. */
+dm_status dm_autotune(dm_plan *plan, int force, void *stream);
+/* The configuration in use (after dm_autotune or dm_set_tuning; zeros and
+ * -1 radixes when neither ran). */
+dm_status dm_get_tuning(const dm_plan *plan, dm_tuning *out);
+/* Apply a configuration (e.g. one stored from an earlier dm_get_tuning);
+ * out-of-range values fall back to the heuristic; DM_EBUSY during a solve. */
+dm_status dm_set_tuning(dm_plan *plan, const dm_tuning *t);
+
 /* alpha and T_h of the noise model of RHS 0 (host outputs). */
 dm_status dm_noise_info(const dm_plan *plan, double *alpha, double *t_h);
 

@@ -394,6 +394,7 @@ dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out) {
   p->nrings = 4 * nside - 1;
   p->npairs = 2 * nside;
   p->nchunk = (p->npairs + 63) / 64;
+  for (int i = 0; i < DM_TUNE_MAX_CLASSES; ++i) p->tune_ring_lr[i] = -1;
   default_schedule(&p->sched);
   cudaError_t e = build_tables(p);
   auto bad = [&](cudaError_t err, const char *w) {
@@ -782,6 +783,7 @@ dm_status dm_set_tensor_cores(dm_plan *p, int on) {
 dm_status dm_set_ring_radix(dm_plan *p, int lr) {
   if (!p || (lr != 0 && lr != 3 && lr != 4)) return DM_EINVAL;
   p->ring_lr = lr;
+  for (int i = 0; i < DM_TUNE_MAX_CLASSES; ++i) p->tune_ring_lr[i] = -1;  // an explicit radix overrides a tuned one
   return DM_OK;
 }
 

@@ -178,7 +178,25 @@ struct dm_plan {
   int since_anchor = 0;
   int64_t iters_launched = 0;
   int64_t bh_total = 0, ph_total = 0;
-  // end-of-solve diagnostics (dm_diag.cu): true residual and chi^2 in FP64
+  // launch tuning (dm_tune.cu): per ring-size class the radix and lanes per
+  // block, per tensor-core kernel its pipeline depth and tiles; 0 or -1 = the
+  // built-in heuristic.  tune_only_* restrict a stage call to one launch while
+  // the tuner times it.
+  int tune_ring_lr[DM_TUNE_MAX_CLASSES];   // -1: the plan's ring_lr
+  int tune_ring_G[DM_TUNE_MAX_CLASSES];    // 0: heuristic lanes per block
+  int ring_G_used[DM_TUNE_MAX_CLASSES];    // what the last iteration launch used
+  int ring_lr_used[DM_TUNE_MAX_CLASSES];
+  int tune_syn_ns[2] = {0, 0};             // k_syn_tc<PART> stages
+  int tune_ana_lt[2] = {0, 0};             // k_ana_tc<PART> l tiles per CTA
+  int tune_ana_S[2] = {0, 0};              // k_ana_tc<PART> stages
+  int syn_ns_used[2] = {0, 0}, ana_lt_used[2] = {0, 0}, ana_S_used[2] = {0, 0};
+  int tune_only_class = -1, tune_only_part = -1;
+  bool tuned = false;
+  dm_tuning tuning{};
+  // launch autotuner (dm_tune.cu)
+dm_status autotune(dm_plan *p, cudaStream_t st, std::string &err);
+
+// end-of-solve diagnostics (dm_diag.cu): true residual and chi^2 in FP64
   bool diag_on = true;
   double *diag_tab = nullptr;   // [lmax+1][8]: C^1/2 and C^+ per l (tt, te, ee, bb)
   double2 *diag_alm = nullptr;  // [B][3][nalm] analysis of w d, then of w (d - Y a)
@@ -254,6 +272,9 @@ cudaError_t draw_signal(dm_plan *p, const uint64_t *seeds_dev, double2 *ahat, cu
 cudaError_t draw_noise_add(dm_plan *p, const uint64_t *seeds_dev, const double *shat, double *dhat,
                            cudaStream_t st);
 cudaError_t axpy_maps(int64_t n, const double *x, double alpha, double *y, cudaStream_t st);
+
+// launch autotuner (dm_tune.cu)
+dm_status autotune(dm_plan *p, cudaStream_t st, std::string &err);
 
 // end-of-solve diagnostics (dm_diag.cu)
 cudaError_t diag_tables(dm_plan *p);

@@ -665,6 +665,13 @@ static int tc_stages(int stage_bytes, uint32_t ncols) {
   return ns < 2 ? 2 : (ns > TC_MAX_STAGES ? TC_MAX_STAGES : ns);
 }
 
+// a requested stage count within what one CTA's shared memory holds, else the heuristic
+static int syn_stages_pick(int want, int stage_bytes, uint32_t ncols) {
+  if (want <= 0) return tc_stages(stage_bytes, ncols);
+  const int fit = (int)(((227u << 10) - 1024u) / (unsigned)stage_bytes);
+  return std::max(2, std::min(want, std::min(fit, TC_MAX_STAGES)));
+}
+
 cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t st) {
   cudaError_t e = tc_tables(p);
   if (e) return e;
@@ -673,22 +680,25 @@ cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t s
   const int npt = (p->npairs + 127) / 128;
   dim3 gb(syn_steps(p->lmax, 0), p->mmax + 1);
   const float2 *e32 = p->anchor_active ? p->e32 : nullptr;  // iteration: the FP32 state e
-  k_syn_b<0><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[0], p->tc_soff, alm, ahi, e32, p->lmax, p->nalm, B);
-  k_syn_b<1><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[1], p->tc_soff, alm, ahi, e32, p->lmax, p->nalm, B);
+  const bool run0 = p->tune_only_part != 1, run1 = p->tune_only_part != 0;
+  if (run0) k_syn_b<0><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[0], p->tc_soff, alm, ahi, e32, p->lmax, p->nalm, B);
+  if (run1) k_syn_b<1><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[1], p->tc_soff, alm, ahi, e32, p->lmax, p->nalm, B);
   dim3 g(npt, p->mmax + 1);
-  {
+  if (run0) {
     const int stage = 2 * 2 * TILE_A + 2 * 2 * (2 * B * 32);
     const uint32_t nc = pow2_cols(4 * B);
-    const int ns = tc_stages(stage, nc);
+    const int ns = syn_stages_pick(p->tune_syn_ns[0], stage, nc);
+    p->syn_ns_used[0] = ns;
     const size_t sm = tc_smem_n(stage, ns, nc);
     cudaFuncSetAttribute(k_syn_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_syn_tc<0><<<g, 128, sm, st>>>(p->tc_synA[0], p->tc_synB[0], p->tc_soff, p->rc32, p->lmax, p->mmax,
                                     p->npairs, B, ns, nc, p->tc_err);
   }
-  {
+  if (run1) {
     const int stage = 2 * 2 * TILE_A + 2 * 2 * (4 * B * 32);  // half a K step (one parity)
     const uint32_t nc = pow2_cols(8 * B);
-    const int ns = tc_stages(stage, nc);
+    const int ns = syn_stages_pick(p->tune_syn_ns[1], stage, nc);
+    p->syn_ns_used[1] = ns;
     const size_t sm = tc_smem_n(stage, ns, nc);
     cudaFuncSetAttribute(k_syn_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_syn_tc<1><<<g, 128, sm, st>>>(p->tc_synA[1], p->tc_synB[1], p->tc_soff, p->rc32, p->lmax, p->mmax,
@@ -711,27 +721,43 @@ static int ana_stages(int stage_bytes) {
   return fit < 2 ? 2 : (fit > ANA_MAX_STAGES ? ANA_MAX_STAGES : fit);
 }
 
+// requested l tiles per CTA within tensor memory (LT x NC columns <= 512), else the heuristic
+static int ana_lt_pick(int want, int NC) {
+  const int mx = ana_tiles_per_cta(NC);
+  return want <= 0 ? mx : std::max(1, std::min(want, mx));
+}
+// requested stages within one CTA's shared memory (2 .. ANA_MAX_STAGES), else the heuristic
+static int ana_S_pick(int want, int stage_bytes) {
+  if (want <= 0) return ana_stages(stage_bytes);
+  const int fit = (int)(((227u << 10) - 1024) / (size_t)stage_bytes);
+  return std::max(2, std::min(want, std::min(fit, ANA_MAX_STAGES)));
+}
+
 cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st) {
   cudaError_t e = tc_tables(p);
   if (e) return e;
   const int B = p->batch;
   const int ltiles = ana_tiles(p->lmax, 0, 0);
-  {
-    const int NC = 2 * B, LT = ana_tiles_per_cta(NC);
+  if (p->tune_only_part != 1) {
+    const int NC = 2 * B, LT = ana_lt_pick(p->tune_ana_lt[0], NC);
     const uint32_t nc = pow2_cols(LT * NC);
     const int stage = LT * 1 * 2 * TILE_A + 1 * 2 * (NC * 32);
-    const int S = ana_stages(stage);
+    const int S = ana_S_pick(p->tune_ana_S[0], stage);
+    p->ana_lt_used[0] = LT;
+    p->ana_S_used[0] = S;
     const size_t sm = tc_smem_n(stage, S, nc);
     dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
     cudaFuncSetAttribute(k_ana_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_ana_tc<0><<<g, ANA_THREADS, sm, st>>>(p->tc_anaA[0], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
                                             p->npairs, p->nalm, B, LT, nc, S, p->tc_err);
   }
-  {
-    const int NC = 4 * B, LT = ana_tiles_per_cta(NC);
+  if (p->tune_only_part != 0) {
+    const int NC = 4 * B, LT = ana_lt_pick(p->tune_ana_lt[1], NC);
     const uint32_t nc = pow2_cols(LT * NC);
     const int stage = LT * 2 * 2 * TILE_A + 2 * 2 * (NC * 32);
-    const int S = ana_stages(stage);
+    const int S = ana_S_pick(p->tune_ana_S[1], stage);
+    p->ana_lt_used[1] = LT;
+    p->ana_S_used[1] = S;
     const size_t sm = tc_smem_n(stage, S, nc);
     dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
     cudaFuncSetAttribute(k_ana_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -558,8 +558,11 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
                         const SolveState *, const R *, const C *);
   const int nlanes = 3 * p->batch;
   const SolveState *stp = (MODE == RING_ITER || MODE == RING_INIT) ? p->state : nullptr;
-  const int lr = p->ring_lr;
-  for (const RingClass &rc_cls : p->ring_classes) {
+  for (int ci = 0; ci < (int)p->ring_classes.size(); ++ci) {
+    const RingClass &rc_cls = p->ring_classes[ci];
+    if (p->tune_only_class >= 0 && ci != p->tune_only_class) continue;
+    const bool tcls = ci < DM_TUNE_MAX_CLASSES;
+    const int lr = (tcls && p->tune_ring_lr[ci] >= 0) ? p->tune_ring_lr[ci] : p->ring_lr;
     int tw_words = std::max(1, rc_cls.M - 1);
     int ph_words = rc_cls.n / 2 + 1;
     int buf_words = rc_cls.M + rc_cls.M / 32 + 1;  // slots spad(0..M)
@@ -597,7 +600,18 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
     const bool paired = fixed && T <= 256;
     const int vlanes = paired ? 2 * nlanes : nlanes;
     int G = ring_lanes_per_block(sizeof(C), tw_words, ph_words, lane_words, vlanes, fa.numRegs, T);
+    if (tcls && p->tune_ring_G[ci] > 0) {  // tuned: clamp to what the launch allows
+      int gmax = 1;
+      while (gmax < 16 && (gmax + 1) * T <= 512 && (gmax + 1) * T <= fa.maxThreadsPerBlock &&
+             sizeof(C) * ((size_t)tw_words + ph_words + (size_t)(gmax + 1) * lane_words) <= (227u << 10))
+        ++gmax;
+      G = std::min(std::min(p->tune_ring_G[ci], gmax), vlanes);
+    }
     if (paired) G = std::max(2, G & ~1);
+    if (MODE == RING_ITER && tcls) {
+      p->ring_G_used[ci] = G;
+      p->ring_lr_used[ci] = fixed ? lr : 0;
+    }
     const size_t smem = sizeof(C) * ((size_t)tw_words + ph_words + (size_t)G * lane_words);
     dim3 grid(paired ? rc_cls.pcount : rc_cls.count, (vlanes + G - 1) / G);
     dim3 block(T, G);

@@ -28,7 +28,7 @@ EXPORTS = [
     "dm_solve_end", "dm_set_refinement", "dm_set_noise_mask_rhs", "dm_server_create", "dm_serve_submit",
     "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores", "dm_set_ring_radix",
     "dm_set_anchor_precision", "dm_set_noise_cov",
-    "dm_legendre_analysis_noalloc", "dm_set_diagnostics",
+    "dm_legendre_analysis_noalloc", "dm_set_diagnostics", "dm_autotune", "dm_get_tuning", "dm_set_tuning",
 ]
 DM_REQ_WF, DM_REQ_CR = 0, 1
 
@@ -49,6 +49,19 @@ class DmProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("iterations", ctypes.c_int64), ("ms_analysis", ctypes.c_double),
                 ("ms_reduce", ctypes.c_double), ("ms_synthesis", ctypes.c_double), ("ms_ring", ctypes.c_double),
                 ("ms_control", ctypes.c_double), ("anchors", ctypes.c_int64), ("ms_anchor", ctypes.c_double)]
+
+
+DM_TUNE_MAX_CLASSES = 12
+
+
+class DmTuning(ctypes.Structure):
+    _fields_ = [("n_ring_classes", ctypes.c_int), ("ring_radix_lr", ctypes.c_int * DM_TUNE_MAX_CLASSES),
+                ("ring_lanes", ctypes.c_int * DM_TUNE_MAX_CLASSES), ("syn_stages", ctypes.c_int * 2),
+                ("ana_ltiles", ctypes.c_int * 2), ("ana_stages", ctypes.c_int * 2),
+                ("ms_ring", ctypes.c_float), ("ms_ring_default", ctypes.c_float),
+                ("ms_synthesis", ctypes.c_float), ("ms_synthesis_default", ctypes.c_float),
+                ("ms_analysis", ctypes.c_float), ("ms_analysis_default", ctypes.c_float),
+                ("from_cache", ctypes.c_int)]
 
 
 class DmServerConfig(ctypes.Structure):
@@ -122,6 +135,9 @@ def lib():
         L.dm_set_anchor_precision.argtypes = [vp, ctypes.c_int]
         L.dm_set_tensor_cores.argtypes = [vp, ctypes.c_int]
         L.dm_set_diagnostics.argtypes = [vp, ctypes.c_int]
+        L.dm_autotune.argtypes = [vp, ctypes.c_int, vp]
+        L.dm_get_tuning.argtypes = [vp, ctypes.POINTER(DmTuning)]
+        L.dm_set_tuning.argtypes = [vp, ctypes.POINTER(DmTuning)]
         L.dm_set_noise_mask_rhs.argtypes = [vp, ctypes.c_int, vp, vp]
         L.dm_server_create.argtypes = [ctypes.POINTER(DmServerConfig), ctypes.POINTER(vp)]
         L.dm_serve_submit.argtypes = [vp, ctypes.POINTER(DmRequest), ctypes.POINTER(ctypes.c_uint64)]
@@ -274,6 +290,32 @@ class Plan:
     def set_diagnostics(self, on=True):
         """End-of-solve true residual and chi^2 in the stats (default on)."""
         self._check(lib().dm_set_diagnostics(self.h, 1 if on else 0))
+
+    def autotune(self, force=False, stream=None):
+        """Time the launch candidates on this plan (dm_autotune); returns the picks."""
+        self._check(lib().dm_autotune(self.h, 1 if force else 0, _stream(stream)))
+        return self.tuning()
+
+    def tuning(self):
+        t = DmTuning()
+        self._check(lib().dm_get_tuning(self.h, ctypes.byref(t)))
+        n = t.n_ring_classes
+        out = {k: getattr(t, k) for k, _ in DmTuning._fields_ if not k.startswith(("ring_", "syn_", "ana_"))}
+        out.update(ring_radix_lr=list(t.ring_radix_lr)[:n], ring_lanes=list(t.ring_lanes)[:n],
+                   syn_stages=list(t.syn_stages), ana_ltiles=list(t.ana_ltiles), ana_stages=list(t.ana_stages))
+        return out
+
+    def set_tuning(self, d):
+        t = DmTuning()
+        t.n_ring_classes = len(d.get("ring_lanes", []))
+        for i, v in enumerate(d.get("ring_radix_lr", [])):
+            t.ring_radix_lr[i] = v
+        for i, v in enumerate(d.get("ring_lanes", [])):
+            t.ring_lanes[i] = v
+        for k in ("syn_stages", "ana_ltiles", "ana_stages"):
+            for i, v in enumerate(d.get(k, [0, 0])):
+                getattr(t, k)[i] = v
+        self._check(lib().dm_set_tuning(self.h, ctypes.byref(t)))
 
     def set_tensor_cores(self, on=True):
         self._check(lib().dm_set_tensor_cores(self.h, 1 if on else 0))

@@ -62,7 +62,7 @@ def test_binding_structs_match_the_c_layout(tmp_path):
         pytest.skip("no host C compiler")
     pairs = {"dm_schedule": dmwf.DmSchedule, "dm_stats": dmwf.DmStats, "dm_profile": dmwf.DmProfile,
              "dm_server_config": dmwf.DmServerConfig, "dm_request": dmwf.DmRequest, "dm_result": dmwf.DmResult,
-             "dm_server_info_t": dmwf.DmServerInfo}
+             "dm_server_info_t": dmwf.DmServerInfo, "dm_tuning": dmwf.DmTuning}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dmwf.h"', "int main(void) {"]
     for cname, py in pairs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
