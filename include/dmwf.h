@@ -164,8 +164,12 @@ dm_status dm_set_noise_mask_rhs(dm_plan *plan, int b, const double *sigma, const
  * over the observed components, and the messenger update is Appendix B's
  * t = (Nbar^{-1} + T^{-1})^{-1} (T^{-1} s + Nbar^{-1} d), applied as
  * s + alpha N^{-1} (d - s).  Copied at the call.  Solves then run in DM_FP64
- * or DM_FLOAT_FLOAT (DM_EINVAL in DM_MIXED_FP32 at dm_solve_begin);
- * constrained realisations and per-RHS noise return DM_EINVAL.
+ * or DM_FLOAT_FLOAT (DM_EINVAL in DM_MIXED_FP32 at dm_solve_begin); per-RHS
+ * noise returns DM_EINVAL.  Constrained realisations draw the noise whose
+ * covariance the solve's precision inverts (Eq. 18): Sigma L z with C = L L^T
+ * on fully observed pixels, and on partly masked ones the draw conditioned
+ * on zero noise on the masked components (x_o - C_om C_mm^{-1} x_m), from the
+ * unit normals described at dm_draw_cr_inputs.
  * dm_set_noise_mask returns the plan to diagonal noise.  DM_EINVAL for a
  * correlation matrix that is not positive definite, sigma <= 0 or non-finite
  * on an observed component, or no observed component; DM_EBUSY during a
@@ -262,11 +266,28 @@ dm_status dm_constrained_realization(dm_plan *plan, const double *d, const uint6
  *   with L the Cholesky factor of [[TT, TE], [TE, EE]] and sqrt(BB); m = 0 real
  *   (full variance), m > 0 re and im each at half variance.
  *  nhat: for pixel p, counters (p, 0, 1, 0) -> (I, Q), (p, 1, 1, 0) -> (U, -),
- *   times sigma, zero on masked pixels.
+ *   times sigma, zero on masked pixels (under dm_set_noise_cov these three
+ *   normals z give the correlated draw described there, zero on masked
+ *   components).
  * Outputs (device, any may be NULL): ahat [batch][3][nalm] complex128,
  * shat = Y ahat and dhat = (shat + nhat) on observed pixels, [batch][3][npix]. */
 dm_status dm_draw_cr_inputs(dm_plan *plan, const uint64_t *seeds, double *ahat, double *shat, double *dhat,
                             void *stream);
+
+/* The modified Jacobi refinement of Appendix A after a Wiener-filter solve:
+ * the usual solve of d (as dm_wiener_filter), then n_refine steps
+ *   a <- a + W~(P g(a)),  g(a) = A(w (d - Y a)) - alpha Omega C^+ a,
+ * where W~ is the dual messenger iteration at the per-level counts the solve
+ * took (per RHS), driven by the harmonic source g instead of data (from
+ * a = 0: a <- F_k [a + g - A(w Y a)]), C^+ the per-l pseudo-inverse of the
+ * signal covariance and P the projector onto its range.  g vanishes at the
+ * Wiener filter, so the refined solution converges to it for any counts.
+ * Buffers as in dm_wiener_filter (d must stay valid until the call returns);
+ * stats report iters_total = (1 + n_refine) x the solve's count and the
+ * diagnostics of the refined a.  Diagonal noise only (DM_EINVAL under
+ * dm_set_noise_cov).  Synchronises. */
+dm_status dm_jacobi_refine(dm_plan *plan, const double *d, int n_refine, double *s_out, double *alm_out,
+                           dm_stats *stats, void *stream);
 
 /* --- transform stages (the steps of the iteration, exposed for testing) ---- */
 

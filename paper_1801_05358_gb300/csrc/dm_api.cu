@@ -50,7 +50,7 @@ void free_all(dm_plan *p) {
                   p->tc_synA[0], p->tc_synA[1], p->tc_anaA[0], p->tc_anaA[1], p->tc_soff, p->tc_aoff,
                   p->tc_synB[0], p->tc_synB[1], p->ptab_lo, p->e32, p->c32, p->clev, p->filt32,
                   p->twr, p->twr32, p->chirp, p->chirp32, p->wcov, p->diag_tab, p->diag_alm, p->diag_part,
-                  p->diag_ao};
+                  p->diag_ao, p->covdraw, p->jsrc, p->jacc};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (p->ev_begin) cudaEventDestroy(p->ev_begin);
@@ -103,6 +103,21 @@ dm_status upload_levels(dm_plan *p) {
       L.forced = 1;
       for (int k = 0; k < s.n_levels; ++k) L.fixed_iters[k] = s.iters_per_level;
     }
+  }
+  DM_CU(cudaMemcpy(p->lev, Ls.data(), sizeof(LevelDev) * p->batch, cudaMemcpyHostToDevice), "upload levels");
+  return DM_OK;
+}
+
+// The schedule's levels with a forced count per RHS and level (counts[B][n_levels]).
+dm_status upload_levels_counts(dm_plan *p, const std::vector<int> &counts) {
+  dm_status r = upload_levels(p);
+  if (r != DM_OK) return r;
+  const int nl = p->sched.n_levels;
+  std::vector<LevelDev> Ls(p->batch);
+  DM_CU(cudaMemcpy(Ls.data(), p->lev, sizeof(LevelDev) * p->batch, cudaMemcpyDeviceToHost), "levels");
+  for (int b = 0; b < p->batch; ++b) {
+    Ls[b].forced = 1;
+    for (int k = 0; k < nl; ++k) Ls[b].fixed_iters[k] = counts[(size_t)b * nl + k];
   }
   DM_CU(cudaMemcpy(p->lev, Ls.data(), sizeof(LevelDev) * p->batch, cudaMemcpyHostToDevice), "upload levels");
   return DM_OK;
@@ -193,6 +208,8 @@ dm_status anchor(dm_plan *p, cudaStream_t st, bool initial, const double *d, boo
   if (need_g) {
     if (!e) e = ring_stage(p, RING_FWD_MAP, p->rhi, nullptr, st);
     if (!e) e = legendre_analysis(p, ANA_PLAIN, p->g_hi, st);
+    if (!e && p->src_active)  // harmonic source of a W~ run: g_hi = g + A W (d - Y a_hi)
+      e = axpy_maps(6 * p->nalm * p->batch, (const double *)p->jsrc, 1.0, (double *)p->g_hi, st);
     if (!e) e = anchor_c32(p, st);
     p->launches += 4;
   }
@@ -637,7 +654,6 @@ dm_status dm_draw_cr_inputs(dm_plan *p, const uint64_t *seeds, double *ahat, dou
                             void *stream) {
   if (!p || !seeds) return DM_EINVAL;
   if (!p->have_cl || !p->have_noise) return fail(p, DM_EINVAL, "spectra and noise must be set");
-  if (p->cov) return fail(p, DM_EINVAL, "constrained-realisation draws take the diagonal noise model");
   cudaStream_t st = (cudaStream_t)stream;
   DM_CU(cudaMemcpyAsync(p->seeds_dev, seeds, sizeof(uint64_t) * p->batch, cudaMemcpyHostToDevice, st), "seeds");
   DM_CU(draw_signal(p, p->seeds_dev, p->tmpalm, st), "draw signal");
@@ -658,7 +674,6 @@ dm_status dm_constrained_realization(dm_plan *p, const double *d, const uint64_t
   dm_status r = check_ready(p);
   if (r != DM_OK) return r;
   if (!d || !seeds || !s_cr_out) return fail(p, DM_EINVAL, "null buffer");
-  if (p->cov) return fail(p, DM_EINVAL, "constrained realisations take the diagonal noise model");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = 3 * p->npix * p->batch;
   // shat -> tmpmap, ahat -> tmpalm, dhat -> tmpmap2, then tmpmap2 = d - dhat
@@ -765,6 +780,70 @@ dm_status dm_solve_end(dm_plan *p, double *s_out, double *alm_out, dm_stats *sta
   DM_CU(cudaEventRecord(p->ev_end, st), "event");
   DM_CU(cudaStreamSynchronize(st), "sync");
   fill_stats(p, stats, &r, st);
+  return r;
+}
+
+dm_status dm_jacobi_refine(dm_plan *p, const double *d, int n_refine, double *s_out, double *alm_out,
+                           dm_stats *stats, void *stream) {
+  dm_status r = check_ready(p);
+  if (r != DM_OK) return r;
+  if (!d || !s_out || n_refine < 0) return fail(p, DM_EINVAL, "null buffer or negative refinement count");
+  if (p->cov) return fail(p, DM_EINVAL, "the Jacobi refinement takes the diagonal noise model");
+  if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
+  cudaStream_t st = (cudaStream_t)stream;
+  DM_CU(cudaEventRecord(p->ev_begin, st), "event");
+  // the usual solve, whose per-level counts W~ then repeats
+  r = run_dm(p, d, st);
+  if (r != DM_OK && r != DM_ENOTCONV) return r;
+  const dm_status r_solve = r;
+  dm_status r2 = solve_end(p, nullptr, nullptr, st, false);
+  if (r2 != DM_OK) return r2;
+  const int nl = p->sched.n_levels, B = p->batch;
+  std::vector<SolveState> hs(B);
+  DM_CU(cudaMemcpyAsync(hs.data(), p->state, sizeof(SolveState) * B, cudaMemcpyDeviceToHost, st), "state");
+  DM_CU(cudaStreamSynchronize(st), "sync");
+  std::vector<int> counts((size_t)B * nl);
+  long cap = 4;
+  for (int b = 0; b < B; ++b) {
+    long tot = 0;
+    for (int k = 0; k < nl; ++k) tot += counts[(size_t)b * nl + k] = hs[b].iters_per_level[k];
+    cap = std::max(cap, tot + 4);
+  }
+  DM_CU(jacobi_alloc(p), "refinement buffers");
+  const size_t an = sizeof(double2) * 3 * (size_t)p->nalm * B;
+  DM_CU(cudaMemcpyAsync(p->jacc, p->a, an, cudaMemcpyDeviceToDevice, st), "copy a");
+  const size_t mb = sizeof(double) * 3 * (size_t)p->npix * B;
+  for (int it = 0; it < n_refine; ++it) {
+    DM_CU(jacobi_source(p, d, st), "refinement source");
+    r = upload_levels_counts(p, counts);
+    if (r != DM_OK) return r;
+    // W~(g): the iteration from a = 0 with w d = 0 and g added before the filter
+    DM_CU(cudaMemsetAsync(p->tmpmap2, 0, mb, st), "zero data");
+    p->src_active = true;
+    r = solve_begin(p, p->tmpmap2, st);
+    int all = 0;
+    if (r == DM_OK) r = solve_iterate(p, cap, &all, st);
+    if (r == DM_OK) r = solve_end(p, nullptr, nullptr, st, false);
+    p->src_active = false;
+    if (r != DM_OK) {
+      end_session(p);
+      upload_levels(p);
+      return r;
+    }
+    DM_CU(axpy_maps(6 * p->nalm * B, (const double *)p->a, 1.0, (double *)p->jacc, st), "a += W~ g");
+  }
+  r = upload_levels(p);
+  if (r != DM_OK) return r;
+  DM_CU(cudaMemcpyAsync(p->a, p->jacc, an, cudaMemcpyDeviceToDevice, st), "copy a");
+  DM_CU(jacobi_final(p, d, st), "final map");
+  DM_CU(cudaMemcpyAsync(s_out, p->s64, mb, cudaMemcpyDeviceToDevice, st), "copy s");
+  if (alm_out) DM_CU(cudaMemcpyAsync(alm_out, p->a, an, cudaMemcpyDeviceToDevice, st), "copy alm");
+  DM_CU(cudaEventRecord(p->ev_end, st), "event");
+  DM_CU(cudaStreamSynchronize(st), "sync");
+  r = r_solve;
+  fill_stats(p, stats, &r, st);
+  if (stats)
+    for (int b = 0; b < B; ++b) stats[b].iters_total = hs[b].iters_total * (1 + n_refine);
   return r;
 }
 

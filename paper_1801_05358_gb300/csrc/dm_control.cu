@@ -265,10 +265,34 @@ __global__ void k_draw_noise(const uint64_t *__restrict__ seeds, const double *_
   }
 }
 
+// Correlated noise (dm_set_noise_cov): n = D z per pixel with the same unit
+// normals as the diagonal draw and the per-pixel draw matrix D; a component
+// is observed where its weight diag(W) is positive.
+__global__ void k_draw_noise_cov(const uint64_t *__restrict__ seeds, const double *__restrict__ D,
+                                 const double *__restrict__ w, const double *__restrict__ shat, double *dhat,
+                                 int64_t npix) {
+  const int b = blockIdx.y;
+  const uint64_t seed = seeds[b];
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+    const double2 z01 = gauss2(seed, (unsigned)p, 0u, 1u);
+    const double2 z2 = gauss2(seed, (unsigned)p, 1u, 1u);
+    const double *Dp = D + 9 * p;
+    const int64_t o = (int64_t)b * 3 * npix + p;
+    for (int f = 0; f < 3; ++f) {
+      const double n = Dp[3 * f] * z01.x + Dp[3 * f + 1] * z01.y + Dp[3 * f + 2] * z2.x;
+      const int64_t i = o + f * npix;
+      dhat[i] = (w[i] > 0.0) ? shat[i] + n : 0.0;
+    }
+  }
+}
+
 cudaError_t draw_noise_add(dm_plan *p, const uint64_t *seeds_dev, const double *shat, double *dhat,
                            cudaStream_t st) {
   dim3 g(1024, p->batch);
-  k_draw_noise<<<g, 256, 0, st>>>(seeds_dev, p->sigma, p->mask, shat, dhat, p->npix);
+  if (p->cov)
+    k_draw_noise_cov<<<g, 256, 0, st>>>(seeds_dev, p->covdraw, p->w, shat, dhat, p->npix);
+  else
+    k_draw_noise<<<g, 256, 0, st>>>(seeds_dev, p->sigma, p->mask, shat, dhat, p->npix);
   return cudaGetLastError();
 }
 

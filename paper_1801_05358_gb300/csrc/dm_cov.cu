@@ -122,6 +122,37 @@ static double sym3_max_eig(double a00, double a11, double a22, double a01, doubl
   return q + 2.0 * pp * cos(phi);
 }
 
+// The noise draw of a constrained realisation under this noise model,
+// n = D z for unit normals z (Eq. 18 needs the covariance that the solve's
+// precision inverts): C = L L^T row by row, x = L z; on a pixel with masked
+// components the observed block of N^{-1} inverts to
+// Sigma_o (C_oo - C_om C_mm^{-1} C_mo) Sigma_o, drawn by subtracting
+// C_om C_mm^{-1} x_m from x_o (the draw conditioned on zero noise on the
+// masked components); masked components get n = 0.  D[9] row-major,
+// D = diag(sigma on observed components) K L with K that conditioning.
+static void noise_draw_matrix(double s0, double s1, double s2, double r01, double r02, double r12, bool ot,
+                              bool op, double *D) {
+  const double l10 = r01, l20 = r02, l11 = sqrt(1.0 - l10 * l10);
+  const double l21 = (r12 - l20 * l10) / l11, l22 = sqrt(1.0 - l20 * l20 - l21 * l21);
+  const double L[3][3] = {{1.0, 0.0, 0.0}, {l10, l11, 0.0}, {l20, l21, l22}};
+  double K[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  if (!ot && op) {  // I masked: x_Q -= r01 x_I, x_U -= r02 x_I
+    K[1][0] = -r01;
+    K[2][0] = -r02;
+  } else if (ot && !op) {  // Q, U masked: x_I -= (r01, r02) C_mm^{-1} (x_Q, x_U)
+    const double q = 1.0 - r12 * r12;
+    K[0][1] = -(r01 - r02 * r12) / q;
+    K[0][2] = -(r02 - r01 * r12) / q;
+  }
+  const double sg[3] = {ot ? s0 : 0.0, op ? s1 : 0.0, op ? s2 : 0.0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += K[i][k] * L[k][j];
+      D[3 * i + j] = sg[i] * acc;
+    }
+}
+
 }  // namespace dmwf
 
 using namespace dmwf;
@@ -134,7 +165,7 @@ extern "C" dm_status dm_set_noise_cov(dm_plan *p, const double *sigma, const dou
     return DM_EBUSY;
   }
   const int64_t np = p->npix;
-  std::vector<double> ninv(6 * (size_t)np), wdiag(3 * (size_t)np);
+  std::vector<double> ninv(6 * (size_t)np), wdiag(3 * (size_t)np), dmat(9 * (size_t)np);
   double alpha = INFINITY;
   int64_t nobs = 0;
   for (int64_t i = 0; i < np; ++i) {
@@ -156,6 +187,7 @@ extern "C" dm_status dm_set_noise_cov(dm_plan *p, const double *sigma, const dou
       si[f] = obs ? 1.0 / sg : 0.0;
     }
     if (ot || op) ++nobs;
+    noise_draw_matrix(sigma[i], sigma[np + i], sigma[2 * np + i], r01, r02, r12, ot, op, dmat.data() + 9 * i);
     // C^{-1} (adjugate over the determinant), then Sigma^{-1} C^{-1} Sigma^{-1}
     const double i00 = (1.0 - r12 * r12) / det, i11 = (1.0 - r02 * r02) / det, i22 = (1.0 - r01 * r01) / det;
     const double i01 = (r02 * r12 - r01) / det, i02 = (r01 * r12 - r02) / det, i12 = (r01 * r02 - r12) / det;
@@ -186,7 +218,16 @@ extern "C" dm_status dm_set_noise_cov(dm_plan *p, const double *sigma, const dou
     }
     p->bytes += (int64_t)(sizeof(double) * 6 * (size_t)np);
   }
+  if (!p->covdraw) {
+    cudaError_t e = cudaMalloc(&p->covdraw, sizeof(double) * 9 * (size_t)np);
+    if (e) {
+      p->err = "alloc correlated-noise draw matrices";
+      return DM_ENOMEM;
+    }
+    p->bytes += (int64_t)(sizeof(double) * 9 * (size_t)np);
+  }
   cudaError_t e = cudaMemcpy(p->wcov, ninv.data(), sizeof(double) * 6 * (size_t)np, cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemcpy(p->covdraw, dmat.data(), sizeof(double) * 9 * (size_t)np, cudaMemcpyHostToDevice);
   std::vector<uint8_t> any(np);
   for (int64_t i = 0; i < np; ++i) any[i] = ((!mask_t || mask_t[i]) || (!mask_p || mask_p[i])) ? 1 : 0;
   for (int b = 0; b < p->batch && !e; ++b) {

@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(DG_THREADS) k_diag_resid_map(const double *__r
 
 // Per (m, RHS) block, over l: mode 0 sums fac |C^1/2 g|^2 (den); mode 1 sums
 // fac |C^1/2 (g - alpha Omega C^+ a)|^2 (num) and fac a^T C^+ a (prior).
-// tab[l][8] = C^1/2 (tt, te, ee, bb), C^+ (tt, te, ee, bb).  grid (mmax+1, batch).
+// tab[l][DIAG_TAB_W] = C^1/2, C^+ and the range projector P, each (tt, te, ee,
+// bb).  grid (mmax+1, batch).
 __global__ void __launch_bounds__(DG_THREADS) k_diag_alm(const double2 *__restrict__ g,
                                                          const double2 *__restrict__ a,
                                                          const double *__restrict__ tab,
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(DG_THREADS) k_diag_alm(const double2 *__restri
   const double2 *ab = a + (int64_t)b * 3 * nalm + base;
   double acc = 0.0, pri = 0.0;
   for (int l = m + threadIdx.x; l <= lmax; l += DG_THREADS) {
-    const double *h = tab + 8 * (int64_t)l, *q = h + 4;
+    const double *h = tab + DIAG_TAB_W * (int64_t)l, *q = h + 4;
     double2 gt = gb[l], ge = gb[nalm + l], gbb = gb[2 * nalm + l];
     if (mode) {
       const double2 at = ab[l], ae = ab[nalm + l], abb = ab[2 * nalm + l];
@@ -135,10 +136,11 @@ void eig_sym2(double tt, double te, double ee, double &e1, double &e2, double &c
 
 }  // namespace
 
-// C^1/2 and C^+ per l on the host (FP64), uploaded beside the spectra.
+// C^1/2, C^+ and the range projector per l on the host (FP64), uploaded
+// beside the spectra.
 cudaError_t diag_tables(dm_plan *p) {
   const int L = p->lmax + 1;
-  std::vector<double> t(8 * (size_t)L, 0.0);
+  std::vector<double> t(DIAG_TAB_W * (size_t)L, 0.0);
   for (int l = 0; l < L; ++l) {
     const double tt = p->cl_h[l], ee = p->cl_h[L + l], bb = p->cl_h[2 * L + l], te = p->cl_h[3 * L + l];
     double e1, e2, c, s;
@@ -146,7 +148,7 @@ cudaError_t diag_tables(dm_plan *p) {
     const double r1 = e1 > 0.0 ? sqrt(e1) : 0.0, r2 = e2 > 0.0 ? sqrt(e2) : 0.0;
     const double i1 = e1 > 0.0 ? 1.0 / e1 : 0.0, i2 = e2 > 0.0 ? 1.0 / e2 : 0.0;
     // f(C) = f(e1) v1 v1^T + f(e2) v2 v2^T, v1 = (c, s), v2 = (-s, c)
-    double *h = &t[8 * (size_t)l], *q = h + 4;
+    double *h = &t[DIAG_TAB_W * (size_t)l], *q = h + 4, *pr = h + 8;
     h[0] = r1 * c * c + r2 * s * s;
     h[1] = (r1 - r2) * c * s;
     h[2] = r1 * s * s + r2 * c * c;
@@ -155,14 +157,19 @@ cudaError_t diag_tables(dm_plan *p) {
     q[1] = (i1 - i2) * c * s;
     q[2] = i1 * s * s + i2 * c * c;
     q[3] = bb > 0.0 ? 1.0 / bb : 0.0;
+    const double p1 = e1 > 0.0 ? 1.0 : 0.0, p2 = e2 > 0.0 ? 1.0 : 0.0;
+    pr[0] = p1 * c * c + p2 * s * s;
+    pr[1] = (p1 - p2) * c * s;
+    pr[2] = p1 * s * s + p2 * c * c;
+    pr[3] = bb > 0.0 ? 1.0 : 0.0;
   }
   cudaError_t e = cudaSuccess;
   if (!p->diag_tab) {
-    e = cudaMalloc((void **)&p->diag_tab, sizeof(double) * 8 * (size_t)L);
+    e = cudaMalloc((void **)&p->diag_tab, sizeof(double) * DIAG_TAB_W * (size_t)L);
     if (e) return e;
-    p->bytes += (int64_t)(sizeof(double) * 8 * (size_t)L);
+    p->bytes += (int64_t)(sizeof(double) * DIAG_TAB_W * (size_t)L);
   }
-  return cudaMemcpy(p->diag_tab, t.data(), sizeof(double) * 8 * (size_t)L, cudaMemcpyHostToDevice);
+  return cudaMemcpy(p->diag_tab, t.data(), sizeof(double) * DIAG_TAB_W * (size_t)L, cudaMemcpyHostToDevice);
 }
 
 // The diagnostics of every RHS of the plan's final iterate (p->a, with

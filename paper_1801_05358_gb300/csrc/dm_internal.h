@@ -12,6 +12,8 @@
 
 namespace dmwf {
 
+constexpr int DIAG_TAB_W = 12;  // doubles per l of the diagnostic tables
+
 // Per-ring geometry and FFT plan (device array, one entry per ring).
 struct RingDev {
   int64_t start;     // first pixel of the ring (RING order)
@@ -89,6 +91,7 @@ struct dm_plan {
   bool have_cl = false, have_noise = false;
   bool cov = false;             // correlated 3x3 noise (dm_set_noise_cov), plan-wide
   double *wcov = nullptr;       // [npix][6] W = alpha N^{-1} (xx, yy, zz, xy, xz, yz)
+  double *covdraw = nullptr;    // [npix][9] noise draw matrix of constrained realisations (correlated noise)
   std::vector<double> alpha, t_h;   // per RHS: alpha = min N (observed), T_h = alpha Omega
 
   // schedule
@@ -193,12 +196,13 @@ struct dm_plan {
   int tune_only_class = -1, tune_only_part = -1;
   bool tuned = false;
   dm_tuning tuning{};
-  // launch autotuner (dm_tune.cu)
-dm_status autotune(dm_plan *p, cudaStream_t st, std::string &err);
-
-// end-of-solve diagnostics (dm_diag.cu): true residual and chi^2 in FP64
+  // modified Jacobi refinement (dm_jacobi.cu)
+  double2 *jsrc = nullptr;      // [B][3][nalm] harmonic source g of a W~ run
+  double2 *jacc = nullptr;      // [B][3][nalm] the refined iterate
+  bool src_active = false;      // the iteration adds jsrc before the filter
+  // end-of-solve diagnostics (dm_diag.cu): true residual and chi^2 in FP64
   bool diag_on = true;
-  double *diag_tab = nullptr;   // [lmax+1][8]: C^1/2 and C^+ per l (tt, te, ee, bb)
+  double *diag_tab = nullptr;   // [lmax+1][DIAG_TAB_W]: C^1/2, C^+ and range projector per l (tt, te, ee, bb)
   double2 *diag_alm = nullptr;  // [B][3][nalm] analysis of w d, then of w (d - Y a)
   double *diag_part = nullptr;  // per-block partial sums
   double *diag_ao = nullptr;    // [B] alpha Omega
@@ -272,6 +276,21 @@ cudaError_t draw_signal(dm_plan *p, const uint64_t *seeds_dev, double2 *ahat, cu
 cudaError_t draw_noise_add(dm_plan *p, const uint64_t *seeds_dev, const double *shat, double *dhat,
                            cudaStream_t st);
 cudaError_t axpy_maps(int64_t n, const double *x, double alpha, double *y, cudaStream_t st);
+
+// modified Jacobi refinement (dm_jacobi.cu)
+cudaError_t jacobi_alloc(dm_plan *p);
+cudaError_t jacobi_source(dm_plan *p, const double *d, cudaStream_t st);  // jsrc = P g(jacc)
+cudaError_t jacobi_final(dm_plan *p, const double *d, cudaStream_t st);   // s64 = Y a, wd = w d
+
+// launch autotuner (dm_tune.cu)
+dm_status autotune(dm_plan *p, cudaStream_t st, std::string &err);
+
+dm_status upload_levels_counts(dm_plan *p, const std::vector<int> &counts);  // per-RHS forced counts [B][n_levels]
+
+// modified Jacobi refinement (dm_jacobi.cu)
+cudaError_t jacobi_alloc(dm_plan *p);
+cudaError_t jacobi_source(dm_plan *p, const double *d, cudaStream_t st);  // jsrc = P g(jacc)
+cudaError_t jacobi_final(dm_plan *p, const double *d, cudaStream_t st);   // s64 = Y a, wd = w d
 
 // launch autotuner (dm_tune.cu)
 dm_status autotune(dm_plan *p, cudaStream_t st, std::string &err);

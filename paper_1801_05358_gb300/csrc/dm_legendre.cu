@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(ANA_P) k_leg_ana64(const PairDev *__restrict__
 // grid: (l blocks, batch, m)
 __global__ void k_ana_reduce(const double2 *__restrict__ apart, double2 *out, int lmax, int64_t nalm, int nchunk,
                              double omega, int epilogue, const double *__restrict__ filt, int nlev,
-                             const SolveState *__restrict__ state) {
+                             const SolveState *__restrict__ state, const double2 *__restrict__ src) {
   const int b = blockIdx.y, m = blockIdx.z;
   if (state != nullptr && state[b].done) return;
   const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
@@ -237,6 +237,12 @@ __global__ void k_ana_reduce(const double2 *__restrict__ apart, double2 *out, in
     return;
   }
   const double *c = filt + (((int64_t)b * nlev + state[b].level) * (lmax + 1) + l) * 4;
+  if (src != nullptr) {  // a harmonic source (the Jacobi refinement's W~ runs): a <- F [a + g + A (t - s)]
+    const double2 *g = src + (int64_t)b * 3 * nalm + i;
+    acc[0] = cadd(acc[0], g[0]);
+    acc[1] = cadd(acc[1], g[nalm]);
+    acc[2] = cadd(acc[2], g[2 * nalm]);
+  }
   double2 t = cadd(o[0], acc[0]), e = cadd(o[nalm], acc[1]), bb = cadd(o[2 * nalm], acc[2]);
   o[0] = make_double2(c[0] * t.x + c[1] * e.x, c[0] * t.y + c[1] * e.y);
   o[nalm] = make_double2(c[1] * t.x + c[2] * e.x, c[1] * t.y + c[2] * e.y);
@@ -259,7 +265,8 @@ cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream
   dim3 g2((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
   k_ana_reduce<<<g2, 128, 0, st>>>(p->apart, out, p->lmax, p->nalm, p->nchunk, omega, epilogue, p->filt,
                                    p->filt_levels,
-                                   epilogue == ANA_DM_STEP ? p->state : stp);
+                                   epilogue == ANA_DM_STEP ? p->state : stp,
+                                   (epilogue == ANA_DM_STEP && p->src_active) ? p->jsrc : nullptr);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ EXPORTS = [
     "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores", "dm_set_ring_radix",
     "dm_set_anchor_precision", "dm_set_noise_cov",
     "dm_legendre_analysis_noalloc", "dm_set_diagnostics", "dm_autotune", "dm_get_tuning", "dm_set_tuning",
+    "dm_jacobi_refine",
 ]
 DM_REQ_WF, DM_REQ_CR = 0, 1
 
@@ -136,6 +137,7 @@ def lib():
         L.dm_set_tensor_cores.argtypes = [vp, ctypes.c_int]
         L.dm_set_diagnostics.argtypes = [vp, ctypes.c_int]
         L.dm_autotune.argtypes = [vp, ctypes.c_int, vp]
+        L.dm_jacobi_refine.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
         L.dm_get_tuning.argtypes = [vp, ctypes.POINTER(DmTuning)]
         L.dm_set_tuning.argtypes = [vp, ctypes.POINTER(DmTuning)]
         L.dm_set_noise_mask_rhs.argtypes = [vp, ctypes.c_int, vp, vp]
@@ -339,6 +341,14 @@ class Plan:
 
     def set_anchor_precision(self, prec):
         self._check(lib().dm_set_anchor_precision(self.h, int(prec)))
+
+    def jacobi_refine(self, d, n_refine, s_out, alm_out=None, stream=None):
+        """Wiener filter plus n_refine modified Jacobi steps (Appendix A)."""
+        stats = (DmStats * self.batch)()
+        st = lib().dm_jacobi_refine(self.h, _ptr(d), int(n_refine), _ptr(s_out), _ptr(alm_out), stats,
+                                    _stream(stream))
+        self._check(st, allow=(DM_ENOTCONV,))
+        return st, self._stats_out(stats)
 
     def wiener_filter_host(self, d_host, s_host, alm_host=None, stream=None):
         stats = (DmStats * self.batch)()

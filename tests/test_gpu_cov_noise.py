@@ -1,8 +1,9 @@
 """Correlated 3x3 per-pixel noise with distinct temperature and polarisation
 masks (dm_set_noise_cov; Section 2.1 and Appendix B) against the oracle's
 orc_dm_solve_cov, through the C ABI: FP64 and float-float solves at the FP64
-bar (relative L2 <= 1e-10), batches, the free-running Cauchy schedule, and the
-calls the mode rejects."""
+bar (relative L2 <= 1e-10), batches, the free-running Cauchy schedule,
+constrained realisations (their conditional noise draws, Eq. 18 and 19) and
+the calls the mode rejects."""
 import numpy as np
 import pytest
 
@@ -85,3 +86,46 @@ def test_cov_rejections():
     with pytest.raises(RuntimeError):
         p.wiener_filter(d, torch.zeros_like(d))
     p.close()
+
+
+def test_cov_cr_inputs_match_oracle(orc):
+    """The constrained-realisation draws under correlated noise: the signal
+    draw, its synthesis and the conditional noise draw of Eq. 18 (zero on
+    masked components), against orc_cr_inputs_cov, seed by seed."""
+    wl = W.make_cov_workload([40], 16, 32)
+    seeds = [901, 12345678901]
+    p = _plan(wl, 2, lambda0=10.0, n_levels=2, iters_per_level=2)
+    ah = torch.zeros((2, 3, (wl.lmax + 1) * (wl.lmax + 2) // 2, 2), dtype=torch.float64, device="cuda")
+    sh = torch.zeros((2, 3, wl.npix), dtype=torch.float64, device="cuda")
+    dh = torch.zeros_like(sh)
+    p.draw_cr_inputs(seeds, ahat=ah, shat=sh, dhat=dh)
+    ga, gs, gd = alm_host(ah, (2, 3, -1)), sh.cpu().numpy(), dh.cpu().numpy()
+    p.close()
+    for b, sd in enumerate(seeds):
+        a_ref, s_ref, d_ref = orc.cr_inputs_cov(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, sd)
+        assert rel(ga[b], a_ref) < 1e-13
+        assert rel(gs[b], s_ref) < 1e-13
+        assert rel(gd[b], d_ref) < 1e-13
+        assert np.all(gd[b][0][wl.mask == 0] == 0.0) and np.all(gd[b][1:][:, wl.mask_p == 0] == 0.0)
+
+
+@pytest.mark.parametrize("prec", [dmwf.DM_FP64, dmwf.DM_FLOAT_FLOAT])
+def test_cov_constrained_realization_matches_oracle(orc, prec):
+    """s_CR = W(d - dhat) + shat (Eq. 19) under correlated noise, one dual
+    messenger run per realisation, against the oracle at the FP64 bar."""
+    wl = W.make_cov_workload([41, 42], 16, 32)
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(100.0, 3)
+    seeds = [5, 6]
+    p = _plan(wl, 2, lambda0=100.0, n_levels=3, iters_per_level=4)
+    p.set_precision(prec)
+    s = torch.zeros((2, 3, wl.npix), dtype=torch.float64, device="cuda")
+    a = torch.zeros((2, 3, (wl.lmax + 1) * (wl.lmax + 2) // 2, 2), dtype=torch.float64, device="cuda")
+    st, stats = p.constrained_realization(dev(d), seeds, s, a)
+    gs, ga = s.cpu().numpy(), alm_host(a, (2, 3, -1))
+    p.close()
+    for b, sd in enumerate(seeds):
+        ref = orc.constrained_realization_cov(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d[b],
+                                              sd, lam, forced_iters=[4, 4, 4])
+        assert rel(gs[b], ref["s_cr"]) < 1e-10
+        assert rel(ga[b], ref["alm_cr"]) < 1e-10
