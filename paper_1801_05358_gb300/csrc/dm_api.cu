@@ -50,7 +50,8 @@ void free_all(dm_plan *p) {
                   p->tc_synA[0], p->tc_synA[1], p->tc_anaA[0], p->tc_anaA[1], p->tc_soff, p->tc_aoff,
                   p->tc_synB[0], p->tc_synB[1], p->ptab_lo, p->e32, p->c32, p->clev, p->filt32,
                   p->twr, p->twr32, p->chirp, p->chirp32, p->wcov, p->diag_tab, p->diag_alm, p->diag_part,
-                  p->diag_ao, p->covdraw, p->jsrc, p->jacc};
+                  p->diag_ao, p->covdraw, p->jsrc, p->jacc, p->bhatT[0], p->bhatT[1], p->bhatT32[0],
+                  p->bhatT32[1]};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (p->ev_begin) cudaEventDestroy(p->ev_begin);

@@ -388,6 +388,30 @@ __device__ __forceinline__ void dft_nat(T2 *a, T2 *y) {
   }
 }
 
+// The twiddles w[q] = W_{RL}^{jq}, q = 1 .. R-1, of a pass: the rows q = 1, 2,
+// 4 (and 8) are read from the pass table, the others are products of at most
+// three of them, which trades shared-memory loads (the transforms' bound)
+// for a few multiplications.
+template <typename T2, int R, int L>
+__device__ __forceinline__ void pass_twiddles(const T2 *tw, int j, T2 *w) {
+  w[1] = tw[j];
+  if constexpr (R >= 4) {
+    w[2] = tw[L + j];
+    w[3] = cmul(w[1], w[2]);
+  }
+  if constexpr (R >= 8) {
+    w[4] = tw[3 * L + j];
+    w[5] = cmul(w[1], w[4]);
+    w[6] = cmul(w[2], w[4]);
+    w[7] = cmul(w[3], w[4]);
+  }
+  if constexpr (R >= 16) {
+    w[8] = tw[7 * L + j];
+#pragma unroll
+    for (int q = 9; q < 16; ++q) w[q] = cmul(w[q - 8], w[8]);
+  }
+}
+
 // One DIF pass of radix 2^LR and stride L; ZERO_UPPER: the inputs r >= R/2 are zero (not read).
 template <typename T2, int LR, int L, bool ZERO_UPPER>
 __device__ __forceinline__ void difr_pass(T2 *x, const T2 *tw, int t) {
@@ -399,8 +423,10 @@ __device__ __forceinline__ void difr_pass(T2 *x, const T2 *tw, int t) {
   for (int r = 0; r < R; ++r) a[r] = (ZERO_UPPER && r >= R / 2) ? cmk<T2>(0, 0) : x[sslot(base + r * L)];
   dft_nat<R>(a, y);
   if constexpr (L > 1) {
+    T2 w[R];
+    pass_twiddles<T2, R, L>(tw, j, w);
 #pragma unroll
-    for (int q = 1; q < R; ++q) y[q] = cmul(y[q], tw[(q - 1) * L + j]);
+    for (int q = 1; q < R; ++q) y[q] = cmul(y[q], w[q]);
   }
 #pragma unroll
   for (int q = 0; q < R; ++q) x[sslot(base + brev_bits(q, LR) * L)] = y[q];
@@ -416,8 +442,10 @@ __device__ __forceinline__ void ditr_pass(T2 *x, const T2 *tw, int t) {
 #pragma unroll
   for (int r = 0; r < R; ++r) a[r] = x[sslot(base + r * L)];
   if constexpr (L > 1) {
+    T2 w[R];
+    pass_twiddles<T2, R, L>(tw, j, w);
 #pragma unroll
-    for (int r = 1; r < R; ++r) a[r] = cmul(a[r], tw[(brev_bits(r, LR) - 1) * L + j]);
+    for (int r = 1; r < R; ++r) a[r] = cmul(a[r], w[brev_bits(r, LR)]);
   }
 #pragma unroll
   for (int s = 0; s < R; ++s) b[s] = a[brev_bits(s, LR)];
@@ -464,15 +492,15 @@ __device__ __forceinline__ void difr_passes(T2 *x, const T2 *tw, int t, int last
     difr_passes<T2, LOGM, LR, P + 1, ZERO_FIRST>(x, tw, t, last);
   }
 }
-template <typename T2, int LOGM, int LR, int P, bool HALF_LAST>
+template <typename T2, int LOGM, int LR, int P, bool HALF_LAST, int PLO = 0>
 __device__ __forceinline__ void ditr_passes(T2 *x, const T2 *tw, int t, int first) {
-  // runs P = first, first - 1, ..., 0 (L ascending)
-  if constexpr (P >= 0) {
+  // runs P = first, first - 1, ..., PLO (L ascending)
+  if constexpr (P >= PLO) {
     if (P <= first) {
       ditr_pass<T2, LR, ((1 << LOGM) >> (LR * (P + 1))), HALF_LAST && P == 0>(x, tw + fftr_tw_off(LOGM, LR, P), t);
       __syncthreads();
     }
-    ditr_passes<T2, LOGM, LR, P - 1, HALF_LAST>(x, tw, t, first);
+    ditr_passes<T2, LOGM, LR, P - 1, HALF_LAST, PLO>(x, tw, t, first);
   }
 }
 
@@ -511,7 +539,9 @@ __device__ void fftr_dit(T2 *x, const T2 *tw, int t) {
 // Bluestein core with the conventions of bluestein_conv: x <- FFT_M(conj(FFT_M(x) * bhat)),
 // upper input half zero, lower output half computed.  The middle (last DIF
 // pass, product with bhat in bit-reversed order, conjugation, first DIT pass)
-// runs on each thread's E consecutive slots in registers.
+// runs on each thread's E consecutive slots in registers.  bhat is stored
+// transposed for these kernels, entry E t + i at i (M / E) + t, so that the
+// threads of a warp read consecutive entries.
 template <typename T2, int LOGM, int LR>
 __device__ void bluesteinr(T2 *x, const T2 *tw, const T2 *__restrict__ bhat, int t) {
   constexpr int NP = LOGM / LR, RB = LOGM % LR, E = 1 << LR;
@@ -523,13 +553,124 @@ __device__ void bluesteinr(T2 *x, const T2 *tw, const T2 *__restrict__ bhat, int
     for (int i = 0; i < E; ++i) v[i] = x[sslot(E * t + i)];
     dif_tail<T2, E, (RB > 0 ? RB : LR)>(v);
 #pragma unroll
-    for (int i = 0; i < E; ++i) v[i] = cconj(cmul(v[i], bhat[E * t + i]));
+    for (int i = 0; i < E; ++i) v[i] = cconj(cmul(v[i], bhat[i * ((1 << LOGM) >> LR) + t]));
     dit_tail<T2, E, (RB > 0 ? RB : LR)>(v);
 #pragma unroll
     for (int i = 0; i < E; ++i) x[sslot(E * t + i)] = v[i];
   }
   __syncthreads();
   ditr_passes<T2, LOGM, LR, NP - 1, true>(x, tw, t, nfull - 1);
+}
+
+// ---------------------------------------------------------------------------
+// An inverse transform, a pointwise map of its output and the next forward
+// transform, with the last pass of the first and the first pass of the second
+// fused in registers.  The last DIT pass (P = 0, stride L = M / R) leaves
+// elements t + q L (q < R, natural order) in thread t, and the first DIF pass
+// (P = 0) reads exactly those elements, with the same twiddle row, so the map
+// runs between them without going through shared memory: one read and one
+// write of the buffer instead of three of each.
+
+// The DIT transform without its last pass: the register tail and the passes
+// P = NP - 1 .. 1; ends with a block barrier.
+template <typename T2, int LOGM, int LR>
+__device__ void fftr_dit_head(T2 *x, const T2 *tw, int t) {
+  constexpr int NP = LOGM / LR, RB = LOGM % LR, E = 1 << LR;
+  if constexpr (RB > 0) {
+    T2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = x[sslot(E * t + i)];
+    dit_tail<T2, E, RB>(v);
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[sslot(E * t + i)] = v[i];
+    __syncthreads();
+  }
+  ditr_passes<T2, LOGM, LR, NP - 1, false, 1>(x, tw, t, NP - 1);
+}
+
+// The DIF transform without its first pass: P = 1 .. NP - 1 and the register
+// tail; ends with a block barrier.
+template <typename T2, int LOGM, int LR>
+__device__ void fftr_dif_tail(T2 *x, const T2 *tw, int t) {
+  constexpr int NP = LOGM / LR, RB = LOGM % LR, E = 1 << LR;
+  difr_passes<T2, LOGM, LR, 1, false>(x, tw, t, NP);
+  if constexpr (RB > 0) {
+    T2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = x[sslot(E * t + i)];
+    dif_tail<T2, E, RB>(v);
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[sslot(E * t + i)] = v[i];
+    __syncthreads();
+  }
+}
+
+// bluesteinr without its last DIT pass (P = 0).
+template <typename T2, int LOGM, int LR>
+__device__ void bluesteinr_head(T2 *x, const T2 *tw, const T2 *__restrict__ bhat, int t) {
+  constexpr int NP = LOGM / LR, RB = LOGM % LR, E = 1 << LR;
+  constexpr int nfull = RB > 0 ? NP : NP - 1;
+  difr_passes<T2, LOGM, LR, 0, true>(x, tw, t, nfull);
+  {
+    T2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = x[sslot(E * t + i)];
+    dif_tail<T2, E, (RB > 0 ? RB : LR)>(v);
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = cconj(cmul(v[i], bhat[i * ((1 << LOGM) >> LR) + t]));
+    dit_tail<T2, E, (RB > 0 ? RB : LR)>(v);
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[sslot(E * t + i)] = v[i];
+  }
+  __syncthreads();
+  ditr_passes<T2, LOGM, LR, NP - 1, true, 1>(x, tw, t, nfull - 1);
+}
+
+// bluesteinr without its first DIF pass (P = 0).
+template <typename T2, int LOGM, int LR>
+__device__ void bluesteinr_tail(T2 *x, const T2 *tw, const T2 *__restrict__ bhat, int t) {
+  constexpr int NP = LOGM / LR, RB = LOGM % LR, E = 1 << LR;
+  constexpr int nfull = RB > 0 ? NP : NP - 1;
+  difr_passes<T2, LOGM, LR, 1, false>(x, tw, t, nfull);
+  {
+    T2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = x[sslot(E * t + i)];
+    dif_tail<T2, E, (RB > 0 ? RB : LR)>(v);
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = cconj(cmul(v[i], bhat[i * ((1 << LOGM) >> LR) + t]));
+    dit_tail<T2, E, (RB > 0 ? RB : LR)>(v);
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[sslot(E * t + i)] = v[i];
+  }
+  __syncthreads();
+  ditr_passes<T2, LOGM, LR, NP - 1, true>(x, tw, t, nfull - 1);
+}
+
+// The fused pass: DIT pass P = 0, y_q <- f(q, y_q) for the output element
+// t + q L, DIF pass P = 0 on the mapped values.  HALF (Bluestein): only the
+// outputs q < R/2 are mapped, and the forward input is zero for q >= R/2.
+// Each thread writes back only the slots it read, so no barrier is needed
+// inside; the caller syncs after it.
+template <typename T2, int LOGM, int LR, bool HALF, typename F>
+__device__ __forceinline__ void fused_dit_dif(T2 *x, const T2 *tw, int t, F f) {
+  constexpr int R = 1 << LR, L = (1 << LOGM) >> LR;
+  T2 a[R], b[R], w[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) a[r] = x[sslot(t + r * L)];
+  pass_twiddles<T2, R, L>(tw, t, w);
+#pragma unroll
+  for (int r = 1; r < R; ++r) a[r] = cmul(a[r], w[brev_bits(r, LR)]);
+#pragma unroll
+  for (int s = 0; s < R; ++s) b[s] = a[brev_bits(s, LR)];
+  dft_nat<R>(b, a);  // a[q]: output element t + q L
+#pragma unroll
+  for (int q = 0; q < R; ++q) a[q] = (HALF && q >= R / 2) ? cmk<T2>(0, 0) : f(q, a[q]);
+  dft_nat<R>(a, b);
+#pragma unroll
+  for (int q = 1; q < R; ++q) b[q] = cmul(b[q], w[q]);
+#pragma unroll
+  for (int q = 0; q < R; ++q) x[sslot(t + brev_bits(q, LR) * L)] = b[q];
 }
 
 }  // namespace dmwf

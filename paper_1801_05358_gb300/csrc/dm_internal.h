@@ -104,6 +104,7 @@ struct dm_plan {
   dmwf::PairDev *pairs = nullptr;
   double2 *phase = nullptr;     // e^{-i pi q / n} tables
   double2 *bhat = nullptr;      // Bluestein kernel spectra
+  double2 *bhatT[2] = {nullptr, nullptr};  // the same transposed for the fixed-size kernels of radix 8, 16
   double2 *chirp = nullptr;     // Bluestein chirps, one table per ring radius
   int64_t ch_total = 0;
   double2 *twid = nullptr;      // stage twiddles: [len - 1 + j] = e^{-i pi j / len}, fft_M_max - 1 entries
@@ -155,6 +156,7 @@ struct dm_plan {
   float *w32 = nullptr;         // [B][3][npix]
   float *wd32 = nullptr;        // [B][3][npix]
   float2 *phase32 = nullptr, *bhat32 = nullptr, *twid32 = nullptr, *twr32 = nullptr, *chirp32 = nullptr;
+  float2 *bhatT32[2] = {nullptr, nullptr};
   // FP64 anchor of the mixed iteration (iterative refinement):
   //   a = a_hi + e;  FP32 stages act on e only; g_hi = A W (d - Y a_hi) in FP64
   double2 *a_hi = nullptr;      // [B][3][nalm]

@@ -339,11 +339,11 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
         buf[lslot<(LR > 0)>(j)].y = 0;
       }
     __syncthreads();
-    if constexpr (LR > 0) {
+    if constexpr (LR > 0) {  // all but the last pass: that one is fused with the update below
       if (bl)
-        bluesteinr<C, LOGM, LR>(buf, tws, bh, tx);
+        bluesteinr_head<C, LOGM, LR>(buf, tws, bh, tx);
       else
-        fftr_dit<C, LOGM, LR>(buf, tws, tx);
+        fftr_dit_head<C, LOGM, LR>(buf, tws, tx);
     } else {
       ring_dft(buf, M, bl, bh, tws);
     }
@@ -371,6 +371,51 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
     const C *wv = reinterpret_cast<const C *>(w + moff);
     const C *dv = reinterpret_cast<const C *>(wd + moff);
     const C *av = s_anchor ? reinterpret_cast<const C *>(s_anchor + moff) : nullptr;
+    if constexpr (LR > 0) {
+      // the fixed-size kernels: last inverse pass, this update and the first
+      // forward pass in registers (fused_dit_dif); element j = tx + q M/2^LR
+      const R invM = sizeof(R) == 4 ? (R)invM_f : (R)invM_d;
+      auto upd = [&](int q, C y) -> C {
+        const int j = tx + q * ((1 << LOGM) >> LR);
+        C rr;
+        rr.x = 0;
+        rr.y = 0;
+        if (j >= h) return rr;  // the Bluestein zero padding (direct rings: h = M)
+        C z = y;
+        if (bl) {
+          z = cconj(z);
+          z.x *= invM;
+          z.y *= invM;
+          z = cmul(z, chp[j]);
+        }
+        C sn;
+        sn.x = z.x;
+        sn.y = -z.y;
+        if (live) {
+          const C so = sv[j], ww = wv[j];
+          const R d0 = sn.x - so.x, d1 = sn.y - so.y;
+          dd_t += d0 * d0 + d1 * d1;
+          sv[j] = sn;
+          if (av) {
+            const C sa = av[j];
+            const R f0 = sa.x + sn.x, f1 = sa.y + sn.y;
+            ss_t += f0 * f0 + f1 * f1;
+            rr.x = -ww.x * sn.x;
+            rr.y = -ww.y * sn.y;
+          } else {
+            const C dw = dv[j];
+            ss_t += sn.x * sn.x + sn.y * sn.y;
+            rr.x = dw.x - ww.x * sn.x;
+            rr.y = dw.y - ww.y * sn.y;
+          }
+        }
+        return bl ? cmul(rr, chp[j]) : rr;
+      };
+      if (bl)
+        fused_dit_dif<C, LOGM, LR, true>(buf, tws, tx, upd);
+      else
+        fused_dit_dif<C, LOGM, LR, false>(buf, tws, tx, upd);
+    } else
     for (int j0 = tx; j0 < h; j0 += 2 * nt) {
       C so[2], ww[2], dw[2], sa[2];
 #pragma unroll
@@ -453,18 +498,18 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
       buf[lslot<(LR > 0)>(j)] = bl ? cmul(v, chp[j]) : v;
     }
   }
-  if (bl)
+  if (LR == 0 && bl)  // (the fused pass of the fixed-size kernels wrote the padding)
     for (int j = h + tx; j < bl_zero_end(M); j += nt) {
       buf[lslot<(LR > 0)>(j)].x = 0;
       buf[lslot<(LR > 0)>(j)].y = 0;
     }
   __syncthreads();
   // forward: Z = DFT_h(z); direct rings take natural input to bit-reversed output
-  if constexpr (LR > 0) {
+  if constexpr (LR > 0) {  // its first pass ran fused with the update
     if (bl)
-      bluesteinr<C, LOGM, LR>(buf, tws, bh, tx);
+      bluesteinr_tail<C, LOGM, LR>(buf, tws, bh, tx);
     else
-      fftr_dif<C, LOGM, LR>(buf, tws, tx);
+      fftr_dif_tail<C, LOGM, LR>(buf, tws, tx);
   } else {
     if (bl)
       ring_dft(buf, M, 1, bh, tws);
@@ -552,7 +597,8 @@ static void pick_fixed(int logm, void (*&kern)(const RingDev *, const int *, con
 template <typename R, typename C, int MODE>
 static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const C *chirps, const C *twid, C *rc,
                                const double *in_map, double *out_user, R *s_state, const R *w, const R *wd,
-                               cudaStream_t st, const R *s_anchor = nullptr, const C *twr = nullptr) {
+                               cudaStream_t st, const R *s_anchor = nullptr, const C *twr = nullptr,
+                               const C *const *bhatT = nullptr) {
   using Kern = void (*)(const RingDev *, const int *, const C *, const C *, const C *, int, int, int, int, int, C *,
                         int, int, int64_t, int, const double *, double *, R *, const R *, const R *, double *,
                         const SolveState *, const R *, const C *);
@@ -576,7 +622,8 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
     const bool compact = (tw_words == 0);
     const int logm = 31 - __builtin_clz((unsigned)rc_cls.M);
     const bool fixed = MODE == RING_ITER && !compact && twr != nullptr && (lr == 3 || lr == 4) &&
-                       rc_cls.M == (1 << logm) && logm >= 9 && logm <= 12 && p->twr_off[lr - 3][logm] >= 0;
+                       rc_cls.M == (1 << logm) && logm >= 9 && logm <= 12 && p->twr_off[lr - 3][logm] >= 0 &&
+                       (bhatT == nullptr || bhatT[lr - 3] != nullptr || p->bh_total == 0);
     Kern kern = compact ? k_ring<R, C, MODE, true, 0, 0> : k_ring<R, C, MODE, false, 0, 0>;
     int T = 128;
     const C *tws = twid;
@@ -618,7 +665,9 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int *order = paired ? p->pair_order + rc_cls.poff : p->ring_order + rc_cls.off;
-    kern<<<grid, block, smem, st>>>(p->rings, order, phase, bhat, tws, tw_words, ph_words, buf_words, lane_words,
+    // the fixed-size kernels read the Bluestein spectra transposed
+    const C *bh_k = (fixed && bhatT != nullptr && bhatT[lr - 3] != nullptr) ? bhatT[lr - 3] : bhat;
+    kern<<<grid, block, smem, st>>>(p->rings, order, phase, bh_k, tws, tw_words, ph_words, buf_words, lane_words,
                                     nlanes, rc, p->mmax, p->npairs, p->npix, p->nrings, in_map, out_user, s_state, w,
                                     wd, p->norms, stp, s_anchor, chirps);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -665,7 +714,7 @@ cudaError_t ring_stage(dm_plan *p, int mode, const double *in_map, double *out_m
                                                           nullptr, p->w, p->wd, st);
       case RING_ITER:
         return launch_ring<double, double2, RING_ITER>(p, p->phase, p->bhat, p->chirp, p->twid, p->rc, nullptr, nullptr,
-                                                       out_map, p->w, p->wd, st, nullptr, p->twr);
+                                                       out_map, p->w, p->wd, st, nullptr, p->twr, p->bhatT);
       case RING_INIT:
         return launch_ring<double, double2, RING_INIT>(p, p->phase, p->bhat, p->chirp, p->twid, p->rc, in_map, nullptr,
                                                        nullptr, p->w, p->wd, st);
@@ -681,7 +730,7 @@ cudaError_t ring_stage(dm_plan *p, int mode, const double *in_map, double *out_m
       case RING_ITER:
         return launch_ring<float, float2, RING_ITER>(p, p->phase32, p->bhat32, p->chirp32, p->twid32, p->rc32, nullptr,
                                                      nullptr, p->s32, p->w32, p->wd32, st,
-                                                     p->anchor_active ? p->shi32 : nullptr, p->twr32);
+                                                     p->anchor_active ? p->shi32 : nullptr, p->twr32, p->bhatT32);
       case RING_INIT:
         return launch_ring<float, float2, RING_INIT>(p, p->phase32, p->bhat32, p->chirp32, p->twid32, p->rc32, in_map,
                                                      nullptr, nullptr, p->w32, p->wd32, st);

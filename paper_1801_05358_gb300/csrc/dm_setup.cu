@@ -89,6 +89,17 @@ __global__ void k_twr(double2 *tw, int LOGM, int LR) {
 // Bluestein kernel spectrum for one ring length: FFT_M of b_j = e^{+i pi j^2/h}
 // placed at j and M - j (|j| < h), zero elsewhere, stored in bit-reversed order
 // (the order in which the ring kernel's DIF transform leaves its data).
+// The Bluestein spectrum of a ring transposed for the fixed-size kernels whose
+// threads hold E consecutive entries: entry E t + i moves to i (M / E) + t.
+__global__ void k_bhat_t(const RingDev *rings, const int *ring_ids, const double2 *bhat, double2 *out, int E) {
+  const RingDev R = rings[ring_ids[blockIdx.x]];
+  const int M = R.M;
+  if (M % E != 0) return;
+  const int nt = M / E;
+  for (int k = threadIdx.x; k < M; k += blockDim.x)
+    out[R.bh_off + (int64_t)(k % E) * nt + k / E] = bhat[R.bh_off + k];
+}
+
 __global__ void k_bhat(const RingDev *rings, const int *ring_ids, const double2 *ph, double2 *bhat,
                        const double2 *twid) {
   extern __shared__ double2 sm_b[];
@@ -462,6 +473,15 @@ cudaError_t build_tables(dm_plan *p) {
     cudaFuncSetAttribute(k_bhat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_bhat<<<(unsigned)bl_ring.size(), 256, smem>>>(p->rings, ids, p->phase, p->bhat, p->twid);
     k_chirp<<<(unsigned)bl_ring.size(), 256>>>(p->rings, ids, p->chirp);
+    for (int lr = 3; lr <= 4 && !e; ++lr) {  // transposed copies for the fixed-size kernels of radix 2^lr
+      if ((e = cudaMalloc(&p->bhatT[lr - 3], sizeof(double2) * bh_total))) break;
+      p->bytes += (int64_t)(sizeof(double2) * bh_total);
+      k_bhat_t<<<(unsigned)bl_ring.size(), 256>>>(p->rings, ids, p->bhat, p->bhatT[lr - 3], 1 << lr);
+    }
+    if (e) {
+      cudaFree(ids);
+      return e;
+    }
     e = cudaDeviceSynchronize();
     cudaFree(ids);
     if (e) return e;
@@ -487,7 +507,8 @@ cudaError_t setup_fp32(dm_plan *p) {
   cudaError_t e;
   // all or nothing: on any error every buffer allocated here is freed again,
   // so that a later call starts over instead of finding a half-built state
-  void **owned[] = {(void **)&p->phase32, (void **)&p->bhat32, (void **)&p->chirp32, (void **)&p->twid32,
+  void **owned[] = {(void **)&p->phase32, (void **)&p->bhat32, (void **)&p->bhatT32[0], (void **)&p->bhatT32[1],
+                    (void **)&p->chirp32, (void **)&p->twid32,
                     (void **)&p->twr32,   (void **)&p->ptab,   (void **)&p->ptab_lo, (void **)&p->rc32,
                     (void **)&p->apart32, (void **)&p->s32,    (void **)&p->w32,     (void **)&p->wd32,
                     (void **)&p->a_hi,    (void **)&p->g_hi,   (void **)&p->shi32,   (void **)&p->e32,
@@ -512,6 +533,8 @@ cudaError_t setup_fp32(dm_plan *p) {
   };
   if ((e = al(&p->phase32, p->ph_total))) return undo(e);
   if ((e = al(&p->bhat32, p->bh_total))) return undo(e);
+  if (p->bhatT[0] && (e = al(&p->bhatT32[0], p->bh_total))) return undo(e);
+  if (p->bhatT[1] && (e = al(&p->bhatT32[1], p->bh_total))) return undo(e);
   if ((e = al(&p->chirp32, p->ch_total))) return undo(e);
   if ((e = al(&p->twid32, p->fft_M_max - 1))) return undo(e);
   if ((e = al(&p->twr32, p->twr_words))) return undo(e);
@@ -533,6 +556,8 @@ cudaError_t setup_fp32(dm_plan *p) {
   cudaMemset(p->rc32, 0, sizeof(float2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
   k_d2f2<<<512, 256>>>(p->phase, p->phase32, p->ph_total);
   if (p->bh_total > 0) k_d2f2<<<512, 256>>>(p->bhat, p->bhat32, p->bh_total);
+  for (int k = 0; k < 2; ++k)
+    if (p->bhatT32[k]) k_d2f2<<<512, 256>>>(p->bhatT[k], p->bhatT32[k], p->bh_total);
   if (p->ch_total > 0) k_d2f2<<<512, 256>>>(p->chirp, p->chirp32, p->ch_total);
   k_d2f2<<<64, 256>>>(p->twid, p->twid32, p->fft_M_max - 1);
   if (p->twr_words > 0) k_d2f2<<<64, 256>>>(p->twr, p->twr32, p->twr_words);
