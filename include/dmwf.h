@@ -349,6 +349,9 @@ typedef struct {
   int n_ring_classes;
   int ring_radix_lr[DM_TUNE_MAX_CLASSES];
   int ring_lanes[DM_TUNE_MAX_CLASSES];
+  int ring_fused[DM_TUNE_MAX_CLASSES];  /* fixed-size kernels: 1 = last inverse pass, messenger update and
+                                           first forward pass fused in registers, 0 = separate passes,
+                                           -1 = default (fused) */
   int syn_stages[2];
   int ana_ltiles[2];
   int ana_stages[2];
@@ -402,6 +405,18 @@ dm_status dm_profile_read(const dm_plan *plan, dm_profile *out);
  * The paper has no counterpart; it is the peak the FP64 Legendre stage is
  * compared against. */
 dm_status dm_measure_alu_peaks(double *fp64_tflops, double *fp32_tflops);
+
+/* --- testing hook --------------------------------------------------------- */
+
+/* Failure test of the tensor-core pipeline's bounded waits (no counterpart in
+ * the paper): while on, the spin-0 tensor-core analysis of the mixed mode
+ * withholds one plain mbarrier arrival (the first converter thread of its
+ * first CTA, first K step), so the MMA warp's wait gives up after 1 s with no
+ * copy or MMA in flight on that barrier; the CTA then drains its copies,
+ * frees its tensor memory and exits, and the solve calls return
+ * DM_ETIMEOUT.  The plan and the CUDA context stay usable: turn it off and
+ * the next solve is normal.  Not for production use. */
+dm_status dm_test_tc_withhold(dm_plan *plan, int on);
 
 /* --- serving: continuous batching of requests of different geometries ---- */
 

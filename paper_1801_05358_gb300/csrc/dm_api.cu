@@ -412,7 +412,7 @@ dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out) {
   p->nrings = 4 * nside - 1;
   p->npairs = 2 * nside;
   p->nchunk = (p->npairs + 63) / 64;
-  for (int i = 0; i < DM_TUNE_MAX_CLASSES; ++i) p->tune_ring_lr[i] = -1;
+  for (int i = 0; i < DM_TUNE_MAX_CLASSES; ++i) p->tune_ring_lr[i] = p->tune_ring_fuse[i] = -1;
   default_schedule(&p->sched);
   cudaError_t e = build_tables(p);
   auto bad = [&](cudaError_t err, const char *w) {
@@ -846,6 +846,12 @@ dm_status dm_jacobi_refine(dm_plan *p, const double *d, int n_refine, double *s_
   if (stats)
     for (int b = 0; b < B; ++b) stats[b].iters_total = hs[b].iters_total * (1 + n_refine);
   return r;
+}
+
+dm_status dm_test_tc_withhold(dm_plan *p, int on) {
+  if (!p) return DM_EINVAL;
+  p->tc_withhold = on != 0;
+  return DM_OK;
 }
 
 dm_status dm_set_diagnostics(dm_plan *p, int on) {

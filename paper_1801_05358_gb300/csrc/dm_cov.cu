@@ -94,14 +94,16 @@ cudaError_t cov_prepare_wd(dm_plan *p, const double *d, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// the pixel part of an iteration with correlated noise (FP64 state p->s64)
+// the pixel part of an iteration with correlated noise (FP64 state p->s64);
+// its scratch map is rhi, which only the mixed mode's anchors use otherwise
+// (tmpmap keeps shat of a constrained realisation across the solve)
 cudaError_t cov_ring_stage(dm_plan *p, cudaStream_t st) {
-  cudaError_t e = ring_stage(p, RING_INV_MAP, nullptr, p->tmpmap, st);
+  cudaError_t e = ring_stage(p, RING_INV_MAP, nullptr, p->rhi, st);
   if (e) return e;
-  k_cov_update<<<dim3(p->nrings, p->batch), 256, 0, st>>>(p->rings, p->s64, p->tmpmap, p->wd, p->wcov, p->norms,
+  k_cov_update<<<dim3(p->nrings, p->batch), 256, 0, st>>>(p->rings, p->s64, p->rhi, p->wd, p->wcov, p->norms,
                                                           p->state, p->npix, p->nrings);
   if ((e = cudaGetLastError())) return e;
-  return ring_stage(p, RING_FWD_MAP, p->tmpmap, nullptr, st);
+  return ring_stage(p, RING_FWD_MAP, p->rhi, nullptr, st);
 }
 
 // Largest eigenvalue of a symmetric 3x3 matrix from the roots of its

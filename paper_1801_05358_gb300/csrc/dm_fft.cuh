@@ -655,20 +655,33 @@ __device__ void bluesteinr_tail(T2 *x, const T2 *tw, const T2 *__restrict__ bhat
 template <typename T2, int LOGM, int LR, bool HALF, typename F>
 __device__ __forceinline__ void fused_dit_dif(T2 *x, const T2 *tw, int t, F f) {
   constexpr int R = 1 << LR, L = (1 << LOGM) >> LR;
-  T2 a[R], b[R], w[R];
+  T2 a[R], b[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) a[r] = x[sslot(t + r * L)];
-  pass_twiddles<T2, R, L>(tw, t, w);
+  {
+    T2 w[R];
+    pass_twiddles<T2, R, L>(tw, t, w);
 #pragma unroll
-  for (int r = 1; r < R; ++r) a[r] = cmul(a[r], w[brev_bits(r, LR)]);
+    for (int r = 1; r < R; ++r) a[r] = cmul(a[r], w[brev_bits(r, LR)]);
+  }
 #pragma unroll
   for (int s = 0; s < R; ++s) b[s] = a[brev_bits(s, LR)];
   dft_nat<R>(b, a);  // a[q]: output element t + q L
+  // two elements at a time: the compiler barrier keeps the loads of the map
+  // from being hoisted all at once (they would not fit the register budget)
 #pragma unroll
-  for (int q = 0; q < R; ++q) a[q] = (HALF && q >= R / 2) ? cmk<T2>(0, 0) : f(q, a[q]);
+  for (int q = 0; q < R; q += 2) {
+    a[q] = (HALF && q >= R / 2) ? cmk<T2>(0, 0) : f(q, a[q]);
+    a[q + 1] = (HALF && q + 1 >= R / 2) ? cmk<T2>(0, 0) : f(q + 1, a[q + 1]);
+    asm volatile("" ::: "memory");
+  }
   dft_nat<R>(a, b);
+  {  // the same twiddle row, read again rather than held across the map
+    T2 w[R];
+    pass_twiddles<T2, R, L>(tw, t, w);
 #pragma unroll
-  for (int q = 1; q < R; ++q) b[q] = cmul(b[q], w[q]);
+    for (int q = 1; q < R; ++q) b[q] = cmul(b[q], w[q]);
+  }
 #pragma unroll
   for (int q = 0; q < R; ++q) x[sslot(t + brev_bits(q, LR) * L)] = b[q];
 }

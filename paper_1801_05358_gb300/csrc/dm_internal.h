@@ -172,6 +172,7 @@ struct dm_plan {
   int anchor_every = 256;
   bool use_tc = true;           // tcgen05 Legendre stages when the batch allows
   int *tc_err = nullptr;        // device flag: a bounded tensor-core wait gave up
+  int tc_withhold = 0;          // test hook: one withheld arrival in the spin-0 analysis (dm_test_tc_withhold)
   // tiled BF16 hi/lo copies of ptab for the tensor-core stages ([0] = lambda, [1] = lam+/lam-)
   unsigned char *tc_synA[2] = {nullptr, nullptr}, *tc_anaA[2] = {nullptr, nullptr};
   int64_t *tc_soff = nullptr, *tc_aoff = nullptr;  // block offsets per m / per (m, parity)
@@ -191,6 +192,8 @@ struct dm_plan {
   int tune_ring_G[DM_TUNE_MAX_CLASSES];    // 0: heuristic lanes per block
   int ring_G_used[DM_TUNE_MAX_CLASSES];    // what the last iteration launch used
   int ring_lr_used[DM_TUNE_MAX_CLASSES];
+  int tune_ring_fuse[DM_TUNE_MAX_CLASSES];  // fixed-size kernels: 1 fused update pass (default), 0 separate
+  int ring_fuse_used[DM_TUNE_MAX_CLASSES];
   int tune_syn_ns[2] = {0, 0};             // k_syn_tc<PART> stages
   int tune_ana_lt[2] = {0, 0};             // k_ana_tc<PART> l tiles per CTA
   int tune_ana_S[2] = {0, 0};              // k_ana_tc<PART> stages

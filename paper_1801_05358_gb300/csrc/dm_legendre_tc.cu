@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(ANA_THREADS, 1) k_ana_tc(const unsigned char *
                                                           const int64_t *__restrict__ aoff,
                                                           const float2 *__restrict__ rc, float2 *__restrict__ out,
                                                           int lmax, int mmax, int npairs, int64_t nalm, int B,
-                                                          int LT, uint32_t ncols, int S, int *err) {
+                                                          int LT, uint32_t ncols, int S, int *err, int withhold) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t bars[3 * ANA_MAX_STAGES + 1];
   __shared__ uint32_t tslot;
@@ -501,7 +501,12 @@ __global__ void __launch_bounds__(ANA_THREADS, 1) k_ana_tc(const unsigned char *
         if (c + ngroups < nsteps) load_ana_b<PART>(task, rc, m, c + ngroups, mmax, npairs, v);
       }
       fence_proxy_async();  // generic-proxy writes -> tensor-core reads
-      mbar_arrive(&full_b[s]);
+      // test hook (dm_test_tc_withhold): the first converter thread of the
+      // first CTA withholds its plain arrival for the first K step, so that the
+      // MMA warp's bounded wait gives up with nothing asynchronous in flight
+      // that targets the withheld barrier
+      if (!(withhold && c == 0 && task == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0))
+        mbar_arrive(&full_b[s]);
     }
   } else if (warp == 8 && lane == 0) {
     const unsigned char *tabm = tab + (aoff[2 * m + par] + lt0) * nsteps * (int64_t)abytes;
@@ -749,7 +754,7 @@ cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st) {
     dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
     cudaFuncSetAttribute(k_ana_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_ana_tc<0><<<g, ANA_THREADS, sm, st>>>(p->tc_anaA[0], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
-                                            p->npairs, p->nalm, B, LT, nc, S, p->tc_err);
+                                            p->npairs, p->nalm, B, LT, nc, S, p->tc_err, p->tc_withhold);
   }
   if (p->tune_only_part != 0) {
     const int NC = 4 * B, LT = ana_lt_pick(p->tune_ana_lt[1], NC);
@@ -762,7 +767,7 @@ cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st) {
     dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
     cudaFuncSetAttribute(k_ana_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_ana_tc<1><<<g, ANA_THREADS, sm, st>>>(p->tc_anaA[1], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
-                                            p->npairs, p->nalm, B, LT, nc, S, p->tc_err);
+                                            p->npairs, p->nalm, B, LT, nc, S, p->tc_err, 0);
   }
   return cudaGetLastError();
 }

@@ -192,7 +192,7 @@ __device__ __forceinline__ C dft_out(const C *buf, int k, int bluestein, const C
 // memory.  A lane works in place on M + 1 entries: the real-FFT packing and
 // unpacking handle k and h - k in the same thread.  Lanes of finished RHS
 // compute but write nothing.
-template <typename R, typename C, int MODE, bool COMPACT, int LOGM, int LR>
+template <typename R, typename C, int MODE, bool COMPACT, int LOGM, int LR, bool FUSE = false>
 __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) ? 2 : 1) k_ring(const RingDev *__restrict__ rings, const int *__restrict__ order,
                                               const C *__restrict__ phase, const C *__restrict__ bhat,
                                               const C *__restrict__ twid, int tw_words, int ph_words,
@@ -339,11 +339,16 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
         buf[lslot<(LR > 0)>(j)].y = 0;
       }
     __syncthreads();
-    if constexpr (LR > 0) {  // all but the last pass: that one is fused with the update below
+    if constexpr (LR > 0 && FUSE) {  // all but the last pass: that one is fused with the update below
       if (bl)
         bluesteinr_head<C, LOGM, LR>(buf, tws, bh, tx);
       else
         fftr_dit_head<C, LOGM, LR>(buf, tws, tx);
+    } else if constexpr (LR > 0) {
+      if (bl)
+        bluesteinr<C, LOGM, LR>(buf, tws, bh, tx);
+      else
+        fftr_dit<C, LOGM, LR>(buf, tws, tx);
     } else {
       ring_dft(buf, M, bl, bh, tws);
     }
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
     const C *wv = reinterpret_cast<const C *>(w + moff);
     const C *dv = reinterpret_cast<const C *>(wd + moff);
     const C *av = s_anchor ? reinterpret_cast<const C *>(s_anchor + moff) : nullptr;
-    if constexpr (LR > 0) {
+    if constexpr (LR > 0 && FUSE) {
       // the fixed-size kernels: last inverse pass, this update and the first
       // forward pass in registers (fused_dit_dif); element j = tx + q M/2^LR
       const R invM = sizeof(R) == 4 ? (R)invM_f : (R)invM_d;
@@ -498,18 +503,23 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
       buf[lslot<(LR > 0)>(j)] = bl ? cmul(v, chp[j]) : v;
     }
   }
-  if (LR == 0 && bl)  // (the fused pass of the fixed-size kernels wrote the padding)
+  if (!FUSE && bl)  // (a fused pass wrote the padding itself)
     for (int j = h + tx; j < bl_zero_end(M); j += nt) {
       buf[lslot<(LR > 0)>(j)].x = 0;
       buf[lslot<(LR > 0)>(j)].y = 0;
     }
   __syncthreads();
   // forward: Z = DFT_h(z); direct rings take natural input to bit-reversed output
-  if constexpr (LR > 0) {  // its first pass ran fused with the update
+  if constexpr (LR > 0 && FUSE) {  // its first pass ran fused with the update
     if (bl)
       bluesteinr_tail<C, LOGM, LR>(buf, tws, bh, tx);
     else
       fftr_dif_tail<C, LOGM, LR>(buf, tws, tx);
+  } else if constexpr (LR > 0) {
+    if (bl)
+      bluesteinr<C, LOGM, LR>(buf, tws, bh, tx);
+    else
+      fftr_dif<C, LOGM, LR>(buf, tws, tx);
   } else {
     if (bl)
       ring_dft(buf, M, 1, bh, tws);
@@ -581,16 +591,16 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
 // Iteration launches of classes with one FFT size M in [512, 4096] take the
 // fixed-size kernel (LOGM = log2 M, radix 2^ring_lr, M / 2^ring_lr threads
 // per lane) unless the plan's ring_lr is 0.
-template <typename R, typename C, int MODE, int LR>
+template <typename R, typename C, int MODE, int LR, bool FUSE>
 static void pick_fixed(int logm, void (*&kern)(const RingDev *, const int *, const C *, const C *, const C *, int,
                                                int, int, int, int, C *, int, int, int64_t, int, const double *,
                                                double *, R *, const R *, const R *, double *, const SolveState *,
                                                const R *, const C *)) {
   switch (logm) {
-    case 9: kern = k_ring<R, C, MODE, false, 9, LR>; break;
-    case 10: kern = k_ring<R, C, MODE, false, 10, LR>; break;
-    case 11: kern = k_ring<R, C, MODE, false, 11, LR>; break;
-    default: kern = k_ring<R, C, MODE, false, 12, LR>; break;
+    case 9: kern = k_ring<R, C, MODE, false, 9, LR, FUSE>; break;
+    case 10: kern = k_ring<R, C, MODE, false, 10, LR, FUSE>; break;
+    case 11: kern = k_ring<R, C, MODE, false, 11, LR, FUSE>; break;
+    default: kern = k_ring<R, C, MODE, false, 12, LR, FUSE>; break;
   }
 }
 
@@ -629,10 +639,12 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
     const C *tws = twid;
     if constexpr (MODE == RING_ITER) {
       if (fixed) {
+        const bool fuse = !(tcls && p->tune_ring_fuse[ci] == 0);  // fused unless tuned otherwise
         if (lr == 3)
-          pick_fixed<R, C, MODE, 3>(logm, kern);
+          fuse ? pick_fixed<R, C, MODE, 3, true>(logm, kern) : pick_fixed<R, C, MODE, 3, false>(logm, kern);
         else
-          pick_fixed<R, C, MODE, 4>(logm, kern);
+          fuse ? pick_fixed<R, C, MODE, 4, true>(logm, kern) : pick_fixed<R, C, MODE, 4, false>(logm, kern);
+        if (tcls) p->ring_fuse_used[ci] = fuse ? 1 : 0;
         T = rc_cls.M >> lr;
         tw_words = fftr_tw_words(logm, lr);
         tws = twr + p->twr_off[lr - 3][logm];

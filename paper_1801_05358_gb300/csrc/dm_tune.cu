@@ -9,6 +9,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <array>
 #include <map>
 #include <mutex>
 #include <string>
@@ -40,6 +41,8 @@ void apply(dm_plan *p, const dm_tuning &t) {
     p->tune_ring_lr[i] = (lr == 0 || lr == 3 || lr == 4) ? lr : -1;
     const int g = in ? t.ring_lanes[i] : 0;
     p->tune_ring_G[i] = (g >= 1 && g <= 16) ? g : 0;
+    const int fu = in ? t.ring_fused[i] : -1;
+    p->tune_ring_fuse[i] = (fu == 0 || fu == 1) ? fu : -1;
   }
   for (int k = 0; k < 2; ++k) {
     p->tune_syn_ns[k] = (t.syn_stages[k] >= 2 && t.syn_stages[k] <= 8) ? t.syn_stages[k] : 0;
@@ -95,38 +98,49 @@ dm_status autotune(dm_plan *p, cudaStream_t st, std::string &err) {
     auto run = [&]() { return ring_stage(p, RING_ITER, nullptr, p->s64, st); };
     p->tune_ring_lr[ci] = -1;
     p->tune_ring_G[ci] = 0;
+    p->tune_ring_fuse[ci] = -1;
     const float t_def = time_it(p, st, run, reps, e0, e1);
     if (t_def < 0.f) {
       err = "ring stage failed with the default configuration";
       rs = DM_ECUDA;
       break;
     }
+    // a candidate is (radix, lanes per block, fused update pass); the
+    // generic kernels have no fused variant
+    auto used_now = [&]() {
+      const int lr = p->ring_lr_used[ci];
+      return std::array<int, 3>{lr, p->ring_G_used[ci], lr > 0 ? p->ring_fuse_used[ci] : 0};
+    };
     float best = t_def;
-    int best_lr = p->ring_lr_used[ci], best_g = p->ring_G_used[ci];
-    std::vector<std::pair<int, int>> seen{{best_lr, best_g}};
+    std::array<int, 3> bestc = used_now();
+    std::vector<std::array<int, 3>> seen{bestc};
     const int lrs[3] = {3, 4, 0};
-    for (int li = 0; li < 3; ++li) {
-      for (int g = 1; g <= 16; ++g) {
-        p->tune_ring_lr[ci] = lrs[li];
-        p->tune_ring_G[ci] = g;
-        if (run() != cudaSuccess) break;  // the untimed probe call sets the *_used fields
-        const std::pair<int, int> used{p->ring_lr_used[ci], p->ring_G_used[ci]};
-        bool dup = false;
-        for (auto &s : seen) dup = dup || s == used;
-        if (dup) continue;
-        seen.push_back(used);
-        const float ms = time_it(p, st, run, reps, e0, e1);
-        if (ms > 0.f && ms < best) {
-          best = ms;
-          best_lr = used.first;
-          best_g = used.second;
+    for (int li = 0; li < 3; ++li)
+      for (int fu = 1; fu >= 0; --fu) {
+        if (lrs[li] == 0 && fu == 0) continue;
+        for (int g = 1; g <= 16; ++g) {
+          p->tune_ring_lr[ci] = lrs[li];
+          p->tune_ring_G[ci] = g;
+          p->tune_ring_fuse[ci] = fu;
+          if (run() != cudaSuccess) break;  // the untimed probe call sets the *_used fields
+          const std::array<int, 3> used = used_now();
+          bool dup = false;
+          for (auto &s : seen) dup = dup || s == used;
+          if (dup) continue;
+          seen.push_back(used);
+          const float ms = time_it(p, st, run, reps, e0, e1);
+          if (ms > 0.f && ms < best) {
+            best = ms;
+            bestc = used;
+          }
         }
       }
-    }
-    t.ring_radix_lr[ci] = best_lr;
-    t.ring_lanes[ci] = best_g;
-    p->tune_ring_lr[ci] = best_lr;
-    p->tune_ring_G[ci] = best_g;
+    t.ring_radix_lr[ci] = bestc[0];
+    t.ring_lanes[ci] = bestc[1];
+    t.ring_fused[ci] = bestc[0] > 0 ? bestc[2] : -1;
+    p->tune_ring_lr[ci] = bestc[0];
+    p->tune_ring_G[ci] = bestc[1];
+    p->tune_ring_fuse[ci] = t.ring_fused[ci];
     t.ms_ring += best;
     t.ms_ring_default += t_def;
   }
@@ -267,6 +281,7 @@ dm_status dm_get_tuning(const dm_plan *p, dm_tuning *out) {
   for (int i = 0; i < DM_TUNE_MAX_CLASSES; ++i) {
     out->ring_radix_lr[i] = p->tune_ring_lr[i];
     out->ring_lanes[i] = p->tune_ring_G[i];
+    out->ring_fused[i] = p->tune_ring_fuse[i];
   }
   for (int k = 0; k < 2; ++k) {
     out->syn_stages[k] = p->tune_syn_ns[k];

@@ -29,7 +29,7 @@ EXPORTS = [
     "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores", "dm_set_ring_radix",
     "dm_set_anchor_precision", "dm_set_noise_cov",
     "dm_legendre_analysis_noalloc", "dm_set_diagnostics", "dm_autotune", "dm_get_tuning", "dm_set_tuning",
-    "dm_jacobi_refine",
+    "dm_jacobi_refine", "dm_test_tc_withhold",
 ]
 DM_REQ_WF, DM_REQ_CR = 0, 1
 
@@ -57,7 +57,8 @@ DM_TUNE_MAX_CLASSES = 12
 
 class DmTuning(ctypes.Structure):
     _fields_ = [("n_ring_classes", ctypes.c_int), ("ring_radix_lr", ctypes.c_int * DM_TUNE_MAX_CLASSES),
-                ("ring_lanes", ctypes.c_int * DM_TUNE_MAX_CLASSES), ("syn_stages", ctypes.c_int * 2),
+                ("ring_lanes", ctypes.c_int * DM_TUNE_MAX_CLASSES),
+                ("ring_fused", ctypes.c_int * DM_TUNE_MAX_CLASSES), ("syn_stages", ctypes.c_int * 2),
                 ("ana_ltiles", ctypes.c_int * 2), ("ana_stages", ctypes.c_int * 2),
                 ("ms_ring", ctypes.c_float), ("ms_ring_default", ctypes.c_float),
                 ("ms_synthesis", ctypes.c_float), ("ms_synthesis_default", ctypes.c_float),
@@ -138,6 +139,7 @@ def lib():
         L.dm_set_diagnostics.argtypes = [vp, ctypes.c_int]
         L.dm_autotune.argtypes = [vp, ctypes.c_int, vp]
         L.dm_jacobi_refine.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
+        L.dm_test_tc_withhold.argtypes = [vp, ctypes.c_int]
         L.dm_get_tuning.argtypes = [vp, ctypes.POINTER(DmTuning)]
         L.dm_set_tuning.argtypes = [vp, ctypes.POINTER(DmTuning)]
         L.dm_set_noise_mask_rhs.argtypes = [vp, ctypes.c_int, vp, vp]
@@ -289,6 +291,10 @@ class Plan:
         self._check(st, allow=(DM_ENOTCONV,))
         return st, self._stats_out(stats)
 
+    def test_tc_withhold(self, on=True):
+        """Failure-test hook: one withheld mbarrier arrival in the tensor-core analysis."""
+        self._check(lib().dm_test_tc_withhold(self.h, 1 if on else 0))
+
     def set_diagnostics(self, on=True):
         """End-of-solve true residual and chi^2 in the stats (default on)."""
         self._check(lib().dm_set_diagnostics(self.h, 1 if on else 0))
@@ -304,6 +310,7 @@ class Plan:
         n = t.n_ring_classes
         out = {k: getattr(t, k) for k, _ in DmTuning._fields_ if not k.startswith(("ring_", "syn_", "ana_"))}
         out.update(ring_radix_lr=list(t.ring_radix_lr)[:n], ring_lanes=list(t.ring_lanes)[:n],
+                   ring_fused=list(t.ring_fused)[:n],
                    syn_stages=list(t.syn_stages), ana_ltiles=list(t.ana_ltiles), ana_stages=list(t.ana_stages))
         return out
 
@@ -314,6 +321,10 @@ class Plan:
             t.ring_radix_lr[i] = v
         for i, v in enumerate(d.get("ring_lanes", [])):
             t.ring_lanes[i] = v
+        for i in range(DM_TUNE_MAX_CLASSES):
+            t.ring_fused[i] = -1
+        for i, v in enumerate(d.get("ring_fused", [])):
+            t.ring_fused[i] = v
         for k in ("syn_stages", "ana_ltiles", "ana_stages"):
             for i, v in enumerate(d.get(k, [0, 0])):
                 getattr(t, k)[i] = v
