@@ -406,6 +406,37 @@ dm_status dm_profile_read(const dm_plan *plan, dm_profile *out);
  * compared against. */
 dm_status dm_measure_alu_peaks(double *fp64_tflops, double *fp32_tflops);
 
+/* --- the flat-sky setting (Section 2.1, Section 3.1) ----------------------- */
+
+/* A plan for the paper's own flat-sky problem: an N x N grid (N a power of two,
+ * 16 <= N <= 2048) of a square patch of side L radians, batch RHS.  Maps are
+ * [batch][3][N * N] float64 row-major (pixel (y, x) at (y L/N, x L/N)).
+ * Transforms: a_l = Omega_p sum_x m(x) e^{-i l.x} with Omega_p = (L/N)^2 and
+ * l = 2 pi k / L, m(x) = L^-2 sum_l a_l e^{i l.x}; polarisation by the E/B
+ * rotation of Eqs. 13-16, E = Q cos 2phi + U sin 2phi,
+ * B = -Q sin 2phi + U cos 2phi, phi the angle of l from the l_x axis.  The
+ * Nyquist row and column are outside the harmonic space.  Harmonic layout
+ * (alm_out of the solve calls): [batch][3][N/2][N] complex128, kx = 0 .. N/2-1
+ * major, ky in FFT order (0 .. N/2-1, then -N/2 .. -1); the modes kx < 0 are
+ * the complex conjugates of (-kx, -ky).  The pair is exact (F^dagger F = 1),
+ * so the iteration is Algorithm 1 as printed.  Solves (dm_wiener_filter,
+ * dm_wiener_filter_host, dm_solve_*), the transform stages (dm_alm2map,
+ * dm_map2alm, the ring and column stages), the schedule calls and
+ * dm_autotune work on it, in DM_FP64; the sphere-only calls (spectra per l,
+ * HEALPix noise setters, constrained realisations, the Jacobi refinement,
+ * dm_apply_filter, the diagnostics, which are NaN) return DM_EINVAL. */
+dm_status dm_plan_create_flat(int N, double L, int batch, dm_plan **out);
+/* Spectra per Fourier mode, host S[4][N][N] (TT, EE, BB, TE) in numpy FFT
+ * order (axis 0 = ky, axis 1 = kx), <|a_l|^2> = L^2 C per mode; each 2x2 TE
+ * block positive semi-definite. */
+dm_status dm_set_spectra_flat(dm_plan *plan, const double *S);
+/* Diagonal noise with distinct temperature and polarisation masks, host
+ * sigma[3][N * N], mask_t / mask_p [N * N] (1 = observed, NULL = all):
+ * alpha = min sigma^2 over observed components, w = alpha / sigma^2 there and
+ * 0 on masked components (N^{-1} = 0), T_h = alpha Omega_p.  Shared by every
+ * RHS. */
+dm_status dm_set_noise_flat(dm_plan *plan, const double *sigma, const uint8_t *mask_t, const uint8_t *mask_p);
+
 /* --- testing hook --------------------------------------------------------- */
 
 /* Failure test of the tensor-core pipeline's bounded waits (no counterpart in

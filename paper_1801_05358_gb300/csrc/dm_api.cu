@@ -393,6 +393,60 @@ void fill_stats(dm_plan *p, dm_stats *stats, dm_status *rs, cudaStream_t st) {
 
 }  // namespace
 
+namespace dmwf {
+
+// The workspace of a plan whose geometry tables are built (sizes from
+// npix, nalm, nrings, npairs, mmax and batch): allocates, initialises the
+// schedule and hands the plan out; frees it on failure.
+dm_status plan_workspace(dm_plan *p, dm_plan **out) {
+  for (int i = 0; i < DM_TUNE_MAX_CLASSES; ++i) p->tune_ring_lr[i] = p->tune_ring_fuse[i] = -1;
+  default_schedule(&p->sched);
+  cudaError_t e = cudaSuccess;
+  auto bad = [&](cudaError_t err, const char *w) {
+    dm_status s = cuda_fail(p, err, w);
+    fprintf(stderr, "dm_plan_create: %s\n", p->err.c_str());
+    free_all(p);
+    delete p;
+    return s;
+  };
+  const int64_t B = p->batch, n3 = 3 * p->npix;
+  const int L = p->flat ? (int)p->nmodes : p->lmax + 1;  // spectra entries per field
+  if ((e = dalloc(p, &p->cl, 4 * (size_t)L))) return bad(e, "alloc");
+  if ((e = dalloc(p, &p->w, (size_t)B * n3))) return bad(e, "alloc");
+  if ((e = dalloc(p, &p->mask, (size_t)B * p->npix))) return bad(e, "alloc");
+  if ((e = dalloc(p, &p->sigma, (size_t)B * n3))) return bad(e, "alloc");
+  p->alpha.assign(B, 0.0);
+  p->t_h.assign(B, 0.0);
+  if ((e = dalloc(p, &p->rc, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return bad(e, "alloc rc");
+  if ((e = dalloc(p, &p->a, (size_t)B * 3 * p->nalm))) return bad(e, "alloc a");
+  if (!p->flat && (e = dalloc(p, &p->apart, (size_t)B * p->nchunk * 3 * p->nalm))) return bad(e, "alloc apart");
+  if ((e = dalloc(p, &p->wd, (size_t)B * n3))) return bad(e, "alloc wd");
+  if ((e = dalloc(p, &p->norms, (size_t)B * 3 * p->nrings * 2))) return bad(e, "alloc norms");
+  if ((e = dalloc(p, &p->state, (size_t)B))) return bad(e, "alloc state");
+  if ((e = dalloc(p, &p->lev, (size_t)B))) return bad(e, "alloc lev");
+  if ((e = dalloc(p, &p->tmpmap, (size_t)B * n3))) return bad(e, "alloc tmp");
+  if ((e = dalloc(p, &p->tmpmap2, (size_t)B * n3))) return bad(e, "alloc tmp");
+  if ((e = dalloc(p, &p->tmpalm, (size_t)B * 3 * p->nalm))) return bad(e, "alloc tmp");
+  if ((e = dalloc(p, &p->seeds_dev, (size_t)B))) return bad(e, "alloc seeds");
+  if ((e = dalloc(p, &p->coef_tmp, 4 * (size_t)L))) return bad(e, "alloc coef");
+  if ((e = dalloc(p, &p->s64, (size_t)B * n3))) return bad(e, "alloc s");
+  if ((e = dalloc(p, &p->rhi, (size_t)B * n3))) return bad(e, "alloc rhi");
+  if ((e = cudaEventCreate(&p->ev_begin)) || (e = cudaEventCreate(&p->ev_end))) return bad(e, "events");
+  cudaMemset(p->rc, 0, sizeof(double2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
+  cudaMemset(p->mask, 1, (size_t)B * p->npix);
+  dm_status s = upload_levels(p);
+  if (s != DM_OK) {
+    free_all(p);
+    delete p;
+    return s;
+  }
+  if ((e = cudaDeviceSynchronize())) return bad(e, "create");
+  *out = p;
+  return DM_OK;
+}
+
+}  // namespace dmwf
+
 extern "C" {
 
 dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out) {
@@ -412,50 +466,15 @@ dm_status dm_plan_create(int nside, int lmax, int batch, dm_plan **out) {
   p->nrings = 4 * nside - 1;
   p->npairs = 2 * nside;
   p->nchunk = (p->npairs + 63) / 64;
-  for (int i = 0; i < DM_TUNE_MAX_CLASSES; ++i) p->tune_ring_lr[i] = p->tune_ring_fuse[i] = -1;
-  default_schedule(&p->sched);
   cudaError_t e = build_tables(p);
-  auto bad = [&](cudaError_t err, const char *w) {
-    dm_status s = cuda_fail(p, err, w);
+  if (e) {
+    dm_status s = cuda_fail(p, e, "build tables");
     fprintf(stderr, "dm_plan_create: %s\n", p->err.c_str());
     free_all(p);
     delete p;
     return s;
-  };
-  if (e) return bad(e, "build tables");
-  const int64_t B = batch, n3 = 3 * p->npix;
-  if ((e = dalloc(p, &p->cl, 4 * (size_t)(lmax + 1)))) return bad(e, "alloc");
-  if ((e = dalloc(p, &p->w, (size_t)B * n3))) return bad(e, "alloc");
-  if ((e = dalloc(p, &p->mask, (size_t)B * p->npix))) return bad(e, "alloc");
-  if ((e = dalloc(p, &p->sigma, (size_t)B * n3))) return bad(e, "alloc");
-  p->alpha.assign(B, 0.0);
-  p->t_h.assign(B, 0.0);
-  if ((e = dalloc(p, &p->rc, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return bad(e, "alloc rc");
-  if ((e = dalloc(p, &p->a, (size_t)B * 3 * p->nalm))) return bad(e, "alloc a");
-  if ((e = dalloc(p, &p->apart, (size_t)B * p->nchunk * 3 * p->nalm))) return bad(e, "alloc apart");
-  if ((e = dalloc(p, &p->wd, (size_t)B * n3))) return bad(e, "alloc wd");
-  if ((e = dalloc(p, &p->norms, (size_t)B * 3 * p->nrings * 2))) return bad(e, "alloc norms");
-  if ((e = dalloc(p, &p->state, (size_t)B))) return bad(e, "alloc state");
-  if ((e = dalloc(p, &p->lev, (size_t)B))) return bad(e, "alloc lev");
-  if ((e = dalloc(p, &p->tmpmap, (size_t)B * n3))) return bad(e, "alloc tmp");
-  if ((e = dalloc(p, &p->tmpmap2, (size_t)B * n3))) return bad(e, "alloc tmp");
-  if ((e = dalloc(p, &p->tmpalm, (size_t)B * 3 * p->nalm))) return bad(e, "alloc tmp");
-  if ((e = dalloc(p, &p->seeds_dev, (size_t)B))) return bad(e, "alloc seeds");
-  if ((e = dalloc(p, &p->coef_tmp, 4 * (size_t)(lmax + 1)))) return bad(e, "alloc coef");
-  if ((e = dalloc(p, &p->s64, (size_t)B * n3))) return bad(e, "alloc s");
-  if ((e = dalloc(p, &p->rhi, (size_t)B * n3))) return bad(e, "alloc rhi");
-  if ((e = cudaEventCreate(&p->ev_begin)) || (e = cudaEventCreate(&p->ev_end))) return bad(e, "events");
-  cudaMemset(p->rc, 0, sizeof(double2) * (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2);
-  cudaMemset(p->mask, 1, (size_t)B * p->npix);
-  dm_status s = upload_levels(p);
-  if (s != DM_OK) {
-    free_all(p);
-    delete p;
-    return s;
   }
-  if ((e = cudaDeviceSynchronize())) return bad(e, "create");
-  *out = p;
-  return DM_OK;
+  return plan_workspace(p, out);
 }
 
 void dm_plan_destroy(dm_plan *p) {
@@ -480,6 +499,7 @@ dm_status dm_set_precision(dm_plan *p, dm_precision prec) {
   if (!p) return DM_EINVAL;
   if (prec != DM_FP64 && prec != DM_MIXED_FP32 && prec != DM_FLOAT_FLOAT)
     return fail(p, DM_EINVAL, "unknown precision mode");
+  if (p->flat && prec != DM_FP64) return fail(p, DM_EINVAL, "flat-sky plans run in DM_FP64");
   if (p->session) return fail(p, DM_EBUSY, "a solve is in progress");
   if (prec != DM_FP64) DM_CU(setup_fp32(p), "float tables");
   // DM_FLOAT_FLOAT runs the FP64 path with float-float Legendre stages
@@ -496,6 +516,7 @@ dm_status dm_set_anchor_precision(dm_plan *p, dm_precision prec) {
 }
 
 dm_status dm_set_spectra(dm_plan *p, const double *cl) {
+  if (p && p->flat) return fail(p, DM_EINVAL, "flat-sky plans take dm_set_spectra_flat");
   if (!p || !cl) return DM_EINVAL;
   if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
   const int L = p->lmax + 1;
@@ -544,6 +565,7 @@ dm_status upload_noise(dm_plan *p, int b, const double *sigma, const uint8_t *ma
 }  // namespace
 
 dm_status dm_set_noise_mask(dm_plan *p, const double *sigma, const uint8_t *mask) {
+  if (p && p->flat) return fail(p, DM_EINVAL, "flat-sky plans take dm_set_noise_flat");
   if (!p || !sigma) return DM_EINVAL;
   if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
   dm_status r = check_noise(p, sigma, mask);
@@ -565,6 +587,7 @@ dm_status dm_set_noise_mask(dm_plan *p, const double *sigma, const uint8_t *mask
 }
 
 dm_status dm_set_noise_mask_rhs(dm_plan *p, int b, const double *sigma, const uint8_t *mask) {
+  if (p && p->flat) return fail(p, DM_EINVAL, "flat-sky plans share one noise model (dm_set_noise_flat)");
   if (!p || !sigma || b < 0 || b >= p->batch) return DM_EINVAL;
   if (!p->have_noise) return fail(p, DM_EINVAL, "set the plan-wide noise first (dm_set_noise_mask)");
   if (p->cov) return fail(p, DM_EINVAL, "per-RHS diagonal noise cannot be mixed with dm_set_noise_cov");
@@ -653,6 +676,7 @@ dm_status dm_wiener_filter_host(dm_plan *p, const double *d_host, double *s_host
 
 dm_status dm_draw_cr_inputs(dm_plan *p, const uint64_t *seeds, double *ahat, double *shat, double *dhat,
                             void *stream) {
+  if (p && p->flat) return fail(p, DM_EINVAL, "constrained realisations are built for sphere plans");
   if (!p || !seeds) return DM_EINVAL;
   if (!p->have_cl || !p->have_noise) return fail(p, DM_EINVAL, "spectra and noise must be set");
   cudaStream_t st = (cudaStream_t)stream;
@@ -672,6 +696,7 @@ dm_status dm_draw_cr_inputs(dm_plan *p, const uint64_t *seeds, double *ahat, dou
 
 dm_status dm_constrained_realization(dm_plan *p, const double *d, const uint64_t *seeds, double *s_cr_out,
                                      double *alm_cr_out, dm_stats *stats, void *stream) {
+  if (p && p->flat) return fail(p, DM_EINVAL, "constrained realisations are built for sphere plans");
   dm_status r = check_ready(p);
   if (r != DM_OK) return r;
   if (!d || !seeds || !s_cr_out) return fail(p, DM_EINVAL, "null buffer");
@@ -747,6 +772,7 @@ dm_status dm_legendre_analysis(dm_plan *p, const double *rc, double *alm, void *
 }
 
 dm_status dm_apply_filter(dm_plan *p, double lambda, const double *alm_in, double *alm_out, void *stream) {
+  if (p && p->flat) return fail(p, DM_EINVAL, "dm_apply_filter takes per-l spectra (sphere plans)");
   if (!p || !alm_in || !alm_out) return DM_EINVAL;
   if (!p->have_cl || !p->have_noise) return fail(p, DM_EINVAL, "spectra and noise must be set");
   if (!(lambda >= 1.0)) return fail(p, DM_EINVAL, "lambda must be >= 1");
@@ -786,6 +812,7 @@ dm_status dm_solve_end(dm_plan *p, double *s_out, double *alm_out, dm_stats *sta
 
 dm_status dm_jacobi_refine(dm_plan *p, const double *d, int n_refine, double *s_out, double *alm_out,
                            dm_stats *stats, void *stream) {
+  if (p && p->flat) return fail(p, DM_EINVAL, "the Jacobi refinement is built for sphere plans");
   dm_status r = check_ready(p);
   if (r != DM_OK) return r;
   if (!d || !s_out || n_refine < 0) return fail(p, DM_EINVAL, "null buffer or negative refinement count");

@@ -161,6 +161,10 @@ using namespace dmwf;
 
 extern "C" dm_status dm_set_noise_cov(dm_plan *p, const double *sigma, const double *rho, const uint8_t *mask_t,
                                       const uint8_t *mask_p) {
+  if (p && p->flat) {
+    p->err = "sphere plans only";
+    return DM_EINVAL;
+  }
   if (!p || !sigma || !rho) return DM_EINVAL;
   if (p->session) {
     p->err = "a solve is in progress on this plan";

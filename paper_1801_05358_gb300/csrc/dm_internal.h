@@ -82,6 +82,12 @@ struct dm_plan {
   int64_t npix = 0, nalm = 0;
   int nrings = 0, npairs = 0;
   int fft_M_max = 1;            // largest FFT size over rings
+  // flat-sky plans (dm_plan_create_flat, the paper's own setting): rows of an
+  // N x N grid are the rings; harmonic modes (kx < N/2, all ky) replace (l, m)
+  bool flat = false;
+  int flatN = 0;
+  double flatL = 0.0;           // side of the patch in radians
+  int64_t nmodes = 0;           // N / 2 x N stored modes
   dm_precision prec = DM_FP64;
   std::string err;
 
@@ -223,6 +229,13 @@ namespace dmwf {
 
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
 cudaError_t build_tables(dm_plan *p);                        // geometry, phases, chirps, coefficients, seeds
+cudaError_t build_tables_flat(dm_plan *p);                   // rows of a flat N x N grid as rings
+cudaError_t build_filter_table(const double *cl4, int64_t n, double mu, double th, double *coef,
+                               cudaStream_t st);             // per-index filters of spectra cl4[4][n]
+dm_status plan_workspace(dm_plan *p, dm_plan **out);         // dm_api.cu: workspace of a built plan
+// flat-sky harmonic stages (dm_flat.cu)
+cudaError_t flat_synthesis(dm_plan *p, const double2 *alm, cudaStream_t st);
+cudaError_t flat_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid);
 cudaError_t build_filters(dm_plan *p, int b, cudaStream_t st);  // per-level filters of RHS b
 cudaError_t build_noise(dm_plan *p, int b, cudaStream_t st);    // alpha (reduction) and w of RHS b
 

@@ -105,6 +105,7 @@ cudaError_t legendre_synthesis32(dm_plan *p, const double2 *alm, cudaStream_t st
 cudaError_t legendre_analysis32(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid);
 
 cudaError_t legendre_synthesis(dm_plan *p, const double2 *alm, cudaStream_t st) {
+  if (p->flat) return flat_synthesis(p, alm, st);  // flat sky: column transforms (dm_flat.cu)
   if (p->prec != DM_FP64) return legendre_synthesis32(p, alm, st);
   if (p->ff_legendre || p->ff_now) return legendre_synthesis_ff(p, alm, st);
   dim3 grid((p->npairs + SYN_THREADS - 1) / SYN_THREADS, p->mmax + 1, p->batch);
@@ -250,6 +251,7 @@ __global__ void k_ana_reduce(const double2 *__restrict__ apart, double2 *out, in
 }
 
 cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid) {
+  if (p->flat) return flat_analysis(p, epilogue, out, st, mid);
   if (p->prec != DM_FP64) return legendre_analysis32(p, epilogue, out, st, mid);
   dim3 grid(p->nchunk, p->mmax + 1, p->batch);
   const SolveState *stp = p->state_active ? p->state : nullptr;

@@ -150,6 +150,10 @@ __global__ void k_na_reduce(const double2 *__restrict__ part, double2 *__restric
 }  // namespace
 
 extern "C" dm_status dm_legendre_analysis_noalloc(dm_plan *p, const double *rc, double *alm, void *stream) {
+  if (p && p->flat) {
+    p->err = "sphere plans only";
+    return DM_EINVAL;
+  }
   if (!p || !rc || !alm) return DM_EINVAL;
   const int nchunk = (p->npairs + NA_P - 1) / NA_P;
   const size_t need = sizeof(double2) * (size_t)p->batch * nchunk * 3 * (size_t)p->nalm;

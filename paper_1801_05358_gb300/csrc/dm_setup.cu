@@ -318,6 +318,89 @@ static int next_pow2(int v) {
   return r;
 }
 
+// e^{-i pi q / n}, q in [0, 2n), for one ring length n (flat-sky rows)
+__global__ void k_phase_n(double2 *ph, int n) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 2 * n; q += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(-(double)q / (double)n, &s, &c);
+    ph[q] = make_double2(c, s);
+  }
+}
+
+// Flat-sky geometry: the N rows of an N x N grid (row-major maps) are N
+// rings of n = N pixels at phi_j = 2 pi j / N (no half-pixel shift), FFT
+// size M = N / 2 (a power of two, no Bluestein), paired as (y, N - 1 - y) so
+// that the paired ring kernels apply; one size class.
+cudaError_t build_tables_flat(dm_plan *p) {
+  const int N = p->flatN;
+  p->rings_h.resize(N);
+  for (int y = 0; y < N; ++y) {
+    RingDev R{};
+    R.start = (int64_t)y * N;
+    R.n = N;
+    R.h = N / 2;
+    R.M = N / 2;
+    R.bluestein = 0;
+    R.shift = 0;
+    R.pair = y < N / 2 ? y : N - 1 - y;
+    R.side = y < N / 2 ? 0 : 1;
+    R.ph_off = 0;
+    R.bh_off = -1;
+    R.ch_off = -1;
+    p->rings_h[y] = R;
+  }
+  p->fft_M_max = N;  // the column transforms are N points (the row transforms N / 2)
+  p->bh_total = 0;
+  p->ch_total = 0;
+  p->ring_classes.clear();
+  p->ring_classes.push_back(RingClass{0, N, N / 2, N, 0, N / 2});
+  p->ring_order_h.resize(N);
+  for (int y = 0; y < N; ++y) p->ring_order_h[y] = y;
+  p->pair_order_h.resize(N / 2);
+  for (int y = 0; y < N / 2; ++y) p->pair_order_h[y] = y;
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->rings, sizeof(RingDev) * N))) return e;
+  if ((e = cudaMalloc(&p->phase, sizeof(double2) * 2 * N))) return e;
+  if ((e = cudaMalloc(&p->twid, sizeof(double2) * (p->fft_M_max - 1)))) return e;
+  if ((e = cudaMalloc(&p->bhat, sizeof(double2)))) return e;
+  if ((e = cudaMalloc(&p->chirp, sizeof(double2)))) return e;
+  if ((e = cudaMalloc(&p->ring_order, sizeof(int) * N))) return e;
+  if ((e = cudaMalloc(&p->pair_order, sizeof(int) * (N / 2)))) return e;
+  p->ph_total = 2 * N;
+  p->bytes += sizeof(RingDev) * N + sizeof(double2) * (2 * N + p->fft_M_max + 1) + sizeof(int) * (N + N / 2);
+  cudaMemcpy(p->rings, p->rings_h.data(), sizeof(RingDev) * N, cudaMemcpyHostToDevice);
+  cudaMemcpy(p->ring_order, p->ring_order_h.data(), sizeof(int) * N, cudaMemcpyHostToDevice);
+  cudaMemcpy(p->pair_order, p->pair_order_h.data(), sizeof(int) * (N / 2), cudaMemcpyHostToDevice);
+  k_phase_n<<<(2 * N + 255) / 256, 256>>>(p->phase, N);
+  k_twiddle<<<(p->fft_M_max + 255) / 256, 256>>>(p->twid, p->fft_M_max);
+  {  // pass tables of the fixed-size transforms when N / 2 is 2^9 .. 2^12
+    int total = 0;
+    for (int r = 0; r < 2; ++r)
+      for (int k = 0; k < 16; ++k) p->twr_off[r][k] = -1;
+    const int logm = 31 - __builtin_clz((unsigned)(N / 2));
+    if ((N / 2) == (1 << logm) && logm >= 9 && logm <= 12)
+      for (int lr = 3; lr <= 4; ++lr) {
+        p->twr_off[lr - 3][logm] = total;
+        total += fftr_tw_words(logm, lr);
+      }
+    if ((e = cudaMalloc(&p->twr, sizeof(double2) * (total > 0 ? total : 1)))) return e;
+    p->twr_words = total;
+    p->bytes += sizeof(double2) * (total > 0 ? total : 1);
+    for (int lr = 3; lr <= 4; ++lr)
+      if (p->twr_off[lr - 3][logm] >= 0 && logm <= 12 && logm >= 9)
+        k_twr<<<(fftr_tw_words(logm, lr) + 255) / 256, 256>>>(p->twr + p->twr_off[lr - 3][logm], logm, lr);
+  }
+  if ((e = cudaGetLastError())) return e;
+  return cudaDeviceSynchronize();
+}
+
+// Filters of every index of spectra cl4[4][n] for one level (mu, T_h):
+// coef[n][4], the per-l filter math applied to per-mode spectra.
+cudaError_t build_filter_table(const double *cl4, int64_t n, double mu, double th, double *coef, cudaStream_t st) {
+  k_filter<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(cl4, (int)(n - 1), mu, th, coef, nullptr);
+  return cudaGetLastError();
+}
+
 cudaError_t build_tables(dm_plan *p) {
   const int ns = p->nside;
   // host-side ring metadata (integer geometry of the RING scheme)
@@ -579,9 +662,27 @@ cudaError_t build_filter_one(dm_plan *p, double lambda, double th, double *coef,
   return cudaGetLastError();
 }
 
-// filters of RHS b for every level: filt[b][k][l][4]
+// filters of RHS b for every level: filt[b][k][l][4]; a flat-sky plan keeps
+// one table per level for every RHS, filt[k][mode][4] (its noise is shared)
 cudaError_t build_filters(dm_plan *p, int b, cudaStream_t st) {
   const int nl = (int)p->lambdas.size();
+  if (p->flat) {
+    if (b != 0) return cudaSuccess;
+    if (p->filt == nullptr || p->filt_levels < nl) {
+      if (p->filt) cudaFree(p->filt);
+      p->filt = nullptr;
+      cudaError_t e = cudaMalloc(&p->filt, sizeof(double) * 4 * (size_t)p->nmodes * nl);
+      if (e) return e;
+      p->filt_levels = nl;
+    }
+    for (int k = 0; k < nl; ++k) {
+      const double th = p->t_h[0];
+      cudaError_t e = build_filter_table(p->cl, p->nmodes, (p->lambdas[k] - 1.0) * th, th,
+                                         p->filt + (size_t)k * 4 * p->nmodes, st);
+      if (e) return e;
+    }
+    return cudaGetLastError();
+  }
   if (p->filt == nullptr || p->filt_levels < nl) {
     if (p->filt) cudaFree(p->filt);
     if (p->filt32) cudaFree(p->filt32);

@@ -29,7 +29,7 @@ EXPORTS = [
     "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores", "dm_set_ring_radix",
     "dm_set_anchor_precision", "dm_set_noise_cov",
     "dm_legendre_analysis_noalloc", "dm_set_diagnostics", "dm_autotune", "dm_get_tuning", "dm_set_tuning",
-    "dm_jacobi_refine", "dm_test_tc_withhold",
+    "dm_jacobi_refine", "dm_test_tc_withhold", "dm_plan_create_flat", "dm_set_spectra_flat", "dm_set_noise_flat",
 ]
 DM_REQ_WF, DM_REQ_CR = 0, 1
 
@@ -140,6 +140,9 @@ def lib():
         L.dm_autotune.argtypes = [vp, ctypes.c_int, vp]
         L.dm_jacobi_refine.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
         L.dm_test_tc_withhold.argtypes = [vp, ctypes.c_int]
+        L.dm_plan_create_flat.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(vp)]
+        L.dm_set_spectra_flat.argtypes = [vp, vp]
+        L.dm_set_noise_flat.argtypes = [vp, vp, vp, vp]
         L.dm_get_tuning.argtypes = [vp, ctypes.POINTER(DmTuning)]
         L.dm_set_tuning.argtypes = [vp, ctypes.POINTER(DmTuning)]
         L.dm_set_noise_mask_rhs.argtypes = [vp, ctypes.c_int, vp, vp]
@@ -479,3 +482,33 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class FlatPlan(Plan):
+    """A flat-sky plan (dm_plan_create_flat): an N x N grid of side L radians.
+    Maps [batch, 3, N * N] row-major; harmonic modes [batch, 3, N/2, N]
+    complex (kx major, ky in FFT order)."""
+
+    def __init__(self, N: int, L: float, batch: int = 1):
+        h = ctypes.c_void_p()
+        st = lib().dm_plan_create_flat(int(N), ctypes.c_double(L), int(batch), ctypes.byref(h))
+        if st != DM_OK:
+            raise DmError(st, "dm_plan_create_flat failed (N a power of two in [16, 2048], L > 0, batch)")
+        self.h = h
+        self.N, self.L, self.batch = N, L, batch
+        self.nside, self.lmax = None, N // 2 - 1
+        self.npix = N * N
+        self.nalm = (N // 2) * N
+        self.nrings = N
+        self._keep = []
+
+    def set_spectra(self, S):
+        """Spectra per mode [4, N, N] (TT, EE, BB, TE) in numpy FFT order."""
+        c = np.ascontiguousarray(S, dtype=np.float64)
+        self._check(lib().dm_set_spectra_flat(self.h, _np_ptr(c)))
+
+    def set_noise(self, sigma, mask_t=None, mask_p=None):
+        s = np.ascontiguousarray(sigma, dtype=np.float64)
+        mt = None if mask_t is None else np.ascontiguousarray(mask_t, dtype=np.uint8)
+        mp = None if mask_p is None else np.ascontiguousarray(mask_p, dtype=np.uint8)
+        self._check(lib().dm_set_noise_flat(self.h, _np_ptr(s), _np_ptr(mt), _np_ptr(mp)))

@@ -1,0 +1,119 @@
+"""The flat-sky path on the GPU (the paper's own setting, Section 2.1 and 3.1:
+2-D FFT transforms with the E/B rotation of Eqs. 13-16) against the flat-sky
+oracle (oracle/flat.py), element by element through the C ABI:
+
+- the analysis and synthesis alone (random maps, random Hermitian modes);
+- the dual messenger solve at the oracle's per-level counts, batches of RHS,
+  distinct temperature and polarisation masks, on grids of 64, 256 and
+  1024 pixels (the paper's 1024^2, where the row transforms take the
+  fixed-size ring kernels);
+- the free-running Cauchy schedule: the same per-level counts.
+
+Layouts: the oracle's modes are [3, N, N] in numpy order (axis 0 = ky); the
+library keeps kx = 0 .. N/2 - 1 with every ky, [3, N/2, N].  Bar: the FP64
+bar, 1e-10 for solves and 1e-12 for single transforms."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import flat as F
+from tests.gpu_helpers import dev, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1801_05358_gb300 import dmwf  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _ours(a):
+    """oracle modes [..., 3, N, N] (ky, kx) -> the library's [..., 3, N/2, N] (kx < N/2, ky)"""
+    N = a.shape[-1]
+    return np.swapaxes(a[..., :, :N // 2], -1, -2)
+
+
+def _alm_of(t, B, N):
+    return t.cpu().numpy().view(np.complex128)[..., 0].reshape(B, 3, N // 2, N)
+
+
+def _plan(wl, B, **sched):
+    p = dmwf.FlatPlan(wl.N, wl.L, B)
+    p.set_spectra(wl.S)
+    p.set_noise(wl.sigma.reshape(3, -1), wl.mask_t.ravel(), wl.mask_p.ravel())
+    if sched:
+        p.set_schedule(**sched)
+    return p
+
+
+@pytest.mark.parametrize("N", [64, 1024])
+def test_flat_transforms(N):
+    L = W.FLAT_L
+    rng = np.random.default_rng(N)
+    B = 2
+    maps = rng.standard_normal((B, 3, N, N))
+    ref_a = np.stack([F.analysis(m, L) for m in maps])
+    alm_in = np.stack([F.analysis(m, L) for m in rng.standard_normal((B, 3, N, N))])  # Hermitian modes
+    ref_m = np.stack([F.synthesis(a, L) for a in alm_in])
+    p = dmwf.FlatPlan(N, L, B)
+    a_out = torch.zeros((B, 3, N * N // 2, 2), dtype=torch.float64, device="cuda")
+    m_out = torch.zeros((B, 3, N * N), dtype=torch.float64, device="cuda")
+    p.map2alm(dev(maps.reshape(B, 3, -1)), a_out)
+    p.alm2map(dev(np.ascontiguousarray(_ours(alm_in)).view(np.float64)), m_out)
+    torch.cuda.synchronize()
+    got_a = _alm_of(a_out, B, N)
+    got_m = m_out.cpu().numpy().reshape(B, 3, N, N)
+    p.close()
+    for b in range(B):
+        assert rel(got_a[b], _ours(ref_a[b])) < 1e-12
+        assert rel(got_m[b], ref_m[b]) < 1e-12
+
+
+@pytest.mark.parametrize("N,B", [(64, 2), (256, 1), (1024, 1)])
+def test_flat_solve_matches_oracle(N, B):
+    wl = W.make_flat_workload(list(range(3, 3 + B)), N=N)
+    d = np.stack(wl.data([F.synthesis(a, wl.L) for a in wl.alm_true]))
+    lam = W.lambda_schedule(1000.0, 3)
+    counts = [3, 3, 3]
+    p = _plan(wl, B, lambda0=1000.0, n_levels=3, iters_per_level=3, check_every=4)
+    s = torch.zeros((B, 3, N * N), dtype=torch.float64, device="cuda")
+    a = torch.zeros((B, 3, N * N // 2, 2), dtype=torch.float64, device="cuda")
+    st, stats = p.wiener_filter(dev(d.reshape(B, 3, -1)), s, a)
+    gs = s.cpu().numpy().reshape(B, 3, N, N)
+    ga = _alm_of(a, B, N)
+    p.close()
+    for b in range(B):
+        assert stats[b]["iters_per_level"][:3] == counts
+        ref = F.dm_solve(d[b], wl.sigma, wl.mask_t, wl.mask_p, wl.S, wl.L, lam, forced_iters=counts)
+        assert rel(gs[b], ref["s"]) < 1e-10
+        assert rel(ga[b], _ours(ref["alm"])) < 1e-10
+
+
+def test_flat_cauchy_schedule_matches_oracle():
+    N = 64
+    wl = W.make_flat_workload([9], N=N)
+    d = wl.data([F.synthesis(wl.alm_true[0], wl.L)])[0]
+    lam = W.lambda_schedule(100.0, 3)
+    eps = W.eps_schedule(3, 1e-2, 1e-4)
+    ref = F.dm_solve(d, wl.sigma, wl.mask_t, wl.mask_p, wl.S, wl.L, lam, eps=eps)
+    p = _plan(wl, 1, lambda0=100.0, n_levels=3, iters_per_level=0, eps0=1e-2, eps_final=1e-4, eta=0.0,
+              check_every=1)
+    s = torch.zeros((1, 3, N * N), dtype=torch.float64, device="cuda")
+    st, stats = p.wiener_filter(dev(d.reshape(1, 3, -1)), s)
+    p.close()
+    assert list(stats[0]["iters_per_level"][:3]) == list(ref["iters_per_level"])
+    assert rel(s.cpu().numpy().reshape(3, N, N), ref["s"]) < 1e-10
+
+
+def test_flat_plan_refuses_sphere_calls():
+    p = dmwf.FlatPlan(32, W.FLAT_L, 1)
+    with pytest.raises(dmwf.DmError):
+        p.set_precision(dmwf.DM_MIXED_FP32)
+    with pytest.raises(dmwf.DmError):
+        dmwf.Plan.set_spectra(p, np.zeros((4, 3)))
+    p.close()
