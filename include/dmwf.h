@@ -274,6 +274,28 @@ dm_status dm_constrained_realization(dm_plan *plan, const double *d, const uint6
 dm_status dm_draw_cr_inputs(dm_plan *plan, const uint64_t *seeds, double *ahat, double *shat, double *dhat,
                             void *stream);
 
+/* Progressive working resolution (the speed-up proposed in Section 4, with
+ * l_iter of Section 2): with margin > 0 the solve calls (dm_wiener_filter,
+ * dm_wiener_filter_host, dm_constrained_realization) run each cooling level
+ * k at the smallest resolution whose band limit stays a margin above that
+ * level's l_iter: L_k = min(lmax, max(lmin, ceil((1 + margin) l_iter(mu_k)))),
+ * l_iter(mu) the largest l whose TE block or BB has an eigenvalue above
+ * mu_k = (lambda_k - 1) T_h, and nside_k the smallest power of two with
+ * 2 nside_k >= L_k; the last level runs at full resolution.  A coarse level
+ * sees per Stokes component the inverse-noise weighted mean of the observed
+ * children of each coarse pixel (noise variance 1 / sum N^-1), its own alpha,
+ * w and T_h, and the filter of threshold mu_k; the harmonic iterate carries
+ * over between levels (modes above L_k dropped or zero) and the usual step
+ * continues from it.  Each resolution gets a plan of the same batch and
+ * precision, made on first use and kept until the spectra, noise or
+ * arithmetic change.  Needs a power-of-two nside and plan-wide diagonal
+ * noise (dm_set_noise_mask); stats report the count of every level.
+ * margin = 0 (default) turns it off.  No counterpart in the paper's runs. */
+dm_status dm_set_progressive(dm_plan *plan, double margin, int lmin);
+/* (nside_k, L_k) of every level of the last progressive solve (host arrays of
+ * the schedule's n_levels); DM_EINVAL before one ran. */
+dm_status dm_get_progressive_levels(const dm_plan *plan, int *nside_k, int *lmax_k);
+
 /* The modified Jacobi refinement of Appendix A after a Wiener-filter solve:
  * the usual solve of d (as dm_wiener_filter), then n_refine steps
  *   a <- a + W~(P g(a)),  g(a) = A(w (d - Y a)) - alpha Omega C^+ a,
@@ -351,7 +373,7 @@ typedef struct {
   int ring_lanes[DM_TUNE_MAX_CLASSES];
   int ring_fused[DM_TUNE_MAX_CLASSES];  /* fixed-size kernels: 1 = last inverse pass, messenger update and
                                            first forward pass fused in registers, 0 = separate passes,
-                                           -1 = default (fused) */
+                                           -1 = default (separate) */
   int syn_stages[2];
   int ana_ltiles[2];
   int ana_stages[2];

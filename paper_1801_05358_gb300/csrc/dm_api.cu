@@ -40,6 +40,7 @@ cudaError_t dalloc(dm_plan *p, T **ptr, size_t count) {
 }
 
 void free_all(dm_plan *p) {
+  prog_release(p);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   p->ev.clear();
   void *ptrs[] = {p->rings, p->pairs, p->phase, p->bhat, p->twid, p->rec, p->seed, p->seed_exp, p->cl,
@@ -80,6 +81,7 @@ dm_status upload_levels(dm_plan *p) {
   for (int k = 0; k < s.n_levels; ++k)
     p->lambdas[k] = (s.n_levels == 1) ? 1.0 : pow(s.lambda0, 1.0 - (double)k / (double)(s.n_levels - 1));
   p->lambdas[s.n_levels - 1] = 1.0;
+  if (s.n_levels == 1 && p->lambda_single > 0.0) p->lambdas[0] = p->lambda_single;
   if ((int)p->eps_final_rhs.size() != p->batch) p->eps_final_rhs.assign(p->batch, s.eps_final);
   std::vector<LevelDev> Ls(p->batch);
   for (int b = 0; b < p->batch; ++b) {
@@ -315,8 +317,16 @@ dm_status solve_iterate(dm_plan *p, long max_iters, int *all_done, cudaStream_t 
   return DM_OK;
 }
 
-// Final iterate into s_out (mixed: one last FP64 synthesis of a).
+// Final iterate into s_out (mixed: one last FP64 synthesis of a).  After a
+// progressive solve (which ended its sessions itself) only the copies remain.
 dm_status solve_end(dm_plan *p, double *s_out, double *alm_out, cudaStream_t st, bool to_host) {
+  if (!p->session && p->prog_margin > 0.0 && !p->prog_res.empty()) {
+    const cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (s_out) DM_CU(cudaMemcpyAsync(s_out, p->s64, sizeof(double) * 3 * p->npix * p->batch, kind, st), "copy s");
+    if (alm_out)
+      DM_CU(cudaMemcpyAsync(alm_out, p->a, sizeof(double2) * 3 * p->nalm * p->batch, kind, st), "copy alm");
+    return DM_OK;
+  }
   if (!p->session) return fail(p, DM_EINVAL, "no solve in progress (dm_solve_begin)");
   if (p->prec != DM_FP64) {
     dm_status r = anchor(p, st, false, nullptr, false);
@@ -333,6 +343,15 @@ dm_status solve_end(dm_plan *p, double *s_out, double *alm_out, cudaStream_t st,
 }
 
 dm_status run_dm(dm_plan *p, const double *d, cudaStream_t st) {
+  if (p->prog_margin > 0.0) {
+    if (!p->noise_shared || p->cov || p->flat || (p->nside & (p->nside - 1)) != 0)
+      return fail(p, DM_EINVAL,
+                  "progressive resolution needs a sphere plan of power-of-two nside with plan-wide diagonal noise");
+    p->prog_notconv = false;
+    dm_status r = run_progressive(p, d, st);
+    if (r != DM_OK) return r;
+    return p->prog_notconv ? fail(p, DM_ENOTCONV, "iteration cap reached") : DM_OK;
+  }
   dm_status r = solve_begin(p, d, st);
   if (r != DM_OK) {
     end_session(p);
@@ -387,6 +406,15 @@ void fill_stats(dm_plan *p, dm_stats *stats, dm_status *rs, cudaStream_t st) {
     o.true_resid = resid[b];
     o.chi2 = chi2[b];
     o.ms_total = ms;
+    if (p->prog_margin > 0.0 && !p->prog_res.empty()) {  // a progressive solve: counts of every level's plan
+      const int nl = (int)p->prog_res.size() / 2;
+      o.iters_total = 0;
+      for (int k = 0; k < nl && k < DM_MAX_LEVELS; ++k) {
+        o.iters_per_level[k] = p->prog_counts[(size_t)b * nl + k];
+        o.iters_total += o.iters_per_level[k];
+      }
+      o.levels_done = nl;
+    }
   }
   if (notconv && *rs == DM_OK) *rs = fail(p, DM_ENOTCONV, "max_iter reached before the last level converged");
 }
@@ -501,6 +529,7 @@ dm_status dm_set_precision(dm_plan *p, dm_precision prec) {
     return fail(p, DM_EINVAL, "unknown precision mode");
   if (p->flat && prec != DM_FP64) return fail(p, DM_EINVAL, "flat-sky plans run in DM_FP64");
   if (p->session) return fail(p, DM_EBUSY, "a solve is in progress");
+  prog_release(p);
   if (prec != DM_FP64) DM_CU(setup_fp32(p), "float tables");
   // DM_FLOAT_FLOAT runs the FP64 path with float-float Legendre stages
   p->prec = prec == DM_MIXED_FP32 ? DM_MIXED_FP32 : DM_FP64;
@@ -528,6 +557,7 @@ dm_status dm_set_spectra(dm_plan *p, const double *cl) {
       return fail(p, DM_EINVAL, "spectrum block not positive semi-definite at l = " + std::to_string(l));
   }
   p->cl_h.assign(cl, cl + 4 * L);
+  prog_release(p);
   DM_CU(cudaMemcpy(p->cl, cl, sizeof(double) * 4 * L, cudaMemcpyHostToDevice), "upload cl");
   DM_CU(diag_tables(p), "diagnostic tables");
   p->have_cl = true;
@@ -583,6 +613,13 @@ dm_status dm_set_noise_mask(dm_plan *p, const double *sigma, const uint8_t *mask
   }
   p->have_noise = true;
   p->cov = false;
+  p->noise_shared = true;
+  p->sigma_h.assign(sigma, sigma + 3 * np);
+  if (mask)
+    p->mask_h.assign(mask, mask + np);
+  else
+    p->mask_h.assign(np, 1);
+  prog_release(p);
   return refresh_filters(p);
 }
 
@@ -595,6 +632,7 @@ dm_status dm_set_noise_mask_rhs(dm_plan *p, int b, const double *sigma, const ui
   dm_status r = check_noise(p, sigma, mask);
   if (r != DM_OK) return r;
   p->have_noise = false;  // a failed upload leaves RHS b half-set: the plan then needs its noise again
+  p->noise_shared = false;
   r = upload_noise(p, b, sigma, mask);
   if (r != DM_OK) return r;
   if (p->have_cl) {
@@ -881,6 +919,27 @@ dm_status dm_test_tc_withhold(dm_plan *p, int on) {
   return DM_OK;
 }
 
+dm_status dm_set_progressive(dm_plan *p, double margin, int lmin) {
+  if (!p || !(margin >= 0.0) || !std::isfinite(margin) || lmin < 2) return DM_EINVAL;
+  if (p->session) return fail(p, DM_EBUSY, "a solve is in progress on this plan");
+  if (margin > 0.0 && (p->flat || (p->nside & (p->nside - 1)) != 0))
+    return fail(p, DM_EINVAL, "progressive resolution needs a sphere plan of power-of-two nside");
+  p->prog_margin = margin;
+  p->prog_lmin = lmin;
+  p->prog_res.clear();
+  return DM_OK;
+}
+
+dm_status dm_get_progressive_levels(const dm_plan *p, int *nside_k, int *lmax_k) {
+  if (!p || p->prog_res.empty()) return DM_EINVAL;
+  const int nl = (int)p->prog_res.size() / 2;
+  for (int k = 0; k < nl; ++k) {
+    if (nside_k) nside_k[k] = p->prog_res[2 * k];
+    if (lmax_k) lmax_k[k] = p->prog_res[2 * k + 1];
+  }
+  return DM_OK;
+}
+
 dm_status dm_set_diagnostics(dm_plan *p, int on) {
   if (!p) return DM_EINVAL;
   p->diag_on = on != 0;
@@ -889,6 +948,7 @@ dm_status dm_set_diagnostics(dm_plan *p, int on) {
 
 dm_status dm_set_tensor_cores(dm_plan *p, int on) {
   if (!p) return DM_EINVAL;
+  prog_release(p);
   p->use_tc = on != 0;
   return DM_OK;
 }
@@ -902,6 +962,7 @@ dm_status dm_set_ring_radix(dm_plan *p, int lr) {
 
 dm_status dm_set_refinement(dm_plan *p, int anchor_every) {
   if (!p || anchor_every < 1) return DM_EINVAL;
+  prog_release(p);
   p->anchor_every = anchor_every;
   return DM_OK;
 }

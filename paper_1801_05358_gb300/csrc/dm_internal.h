@@ -207,6 +207,17 @@ struct dm_plan {
   int tune_only_class = -1, tune_only_part = -1;
   bool tuned = false;
   dm_tuning tuning{};
+  // progressive working resolution (dm_prog.cu)
+  double prog_margin = 0.0;     // > 0: each level at the resolution its l_iter needs
+  int prog_lmin = 8;
+  std::vector<void *> prog_levels;   // plans of the coarse resolutions (made on first use)
+  std::vector<int> prog_counts;      // [B][n_levels] counts of the last progressive solve
+  std::vector<int> prog_res;         // [n_levels][2] (nside_k, L_k) of the last progressive solve
+  bool prog_notconv = false;
+  double lambda_single = 0.0;   // > 0: the lambda of a one-level schedule (a level plan's mu)
+  std::vector<double> sigma_h;  // host copy of the plan-wide noise (dm_set_noise_mask)
+  std::vector<uint8_t> mask_h;
+  bool noise_shared = false;    // every RHS has the plan-wide diagonal noise
   // modified Jacobi refinement (dm_jacobi.cu)
   double2 *jsrc = nullptr;      // [B][3][nalm] harmonic source g of a W~ run
   double2 *jacc = nullptr;      // [B][3][nalm] the refined iterate
@@ -295,6 +306,11 @@ cudaError_t draw_noise_add(dm_plan *p, const uint64_t *seeds_dev, const double *
                            cudaStream_t st);
 cudaError_t axpy_maps(int64_t n, const double *x, double alpha, double *y, cudaStream_t st);
 
+// progressive working resolution (dm_prog.cu)
+dm_status solve_begin_warm(dm_plan *p, const double *d, cudaStream_t st);
+dm_status run_progressive(dm_plan *p, const double *d, cudaStream_t st);
+void prog_release(dm_plan *p);
+
 // modified Jacobi refinement (dm_jacobi.cu)
 cudaError_t jacobi_alloc(dm_plan *p);
 cudaError_t jacobi_source(dm_plan *p, const double *d, cudaStream_t st);  // jsrc = P g(jacc)
@@ -304,6 +320,11 @@ cudaError_t jacobi_final(dm_plan *p, const double *d, cudaStream_t st);   // s64
 dm_status autotune(dm_plan *p, cudaStream_t st, std::string &err);
 
 dm_status upload_levels_counts(dm_plan *p, const std::vector<int> &counts);  // per-RHS forced counts [B][n_levels]
+
+// progressive working resolution (dm_prog.cu)
+dm_status solve_begin_warm(dm_plan *p, const double *d, cudaStream_t st);
+dm_status run_progressive(dm_plan *p, const double *d, cudaStream_t st);
+void prog_release(dm_plan *p);
 
 // modified Jacobi refinement (dm_jacobi.cu)
 cudaError_t jacobi_alloc(dm_plan *p);

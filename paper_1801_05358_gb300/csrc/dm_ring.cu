@@ -639,7 +639,9 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
     const C *tws = twid;
     if constexpr (MODE == RING_ITER) {
       if (fixed) {
-        const bool fuse = !(tcls && p->tune_ring_fuse[ci] == 0);  // fused unless tuned otherwise
+        // separate passes unless tuned otherwise (measured faster on the
+        // bench workload: the fused pass spills at the 64-register cap)
+        const bool fuse = tcls && p->tune_ring_fuse[ci] == 1;
         if (lr == 3)
           fuse ? pick_fixed<R, C, MODE, 3, true>(logm, kern) : pick_fixed<R, C, MODE, 3, false>(logm, kern);
         else

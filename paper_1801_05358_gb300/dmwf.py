@@ -30,6 +30,7 @@ EXPORTS = [
     "dm_set_anchor_precision", "dm_set_noise_cov",
     "dm_legendre_analysis_noalloc", "dm_set_diagnostics", "dm_autotune", "dm_get_tuning", "dm_set_tuning",
     "dm_jacobi_refine", "dm_test_tc_withhold", "dm_plan_create_flat", "dm_set_spectra_flat", "dm_set_noise_flat",
+    "dm_set_progressive", "dm_get_progressive_levels",
 ]
 DM_REQ_WF, DM_REQ_CR = 0, 1
 
@@ -140,6 +141,8 @@ def lib():
         L.dm_autotune.argtypes = [vp, ctypes.c_int, vp]
         L.dm_jacobi_refine.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
         L.dm_test_tc_withhold.argtypes = [vp, ctypes.c_int]
+        L.dm_set_progressive.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+        L.dm_get_progressive_levels.argtypes = [vp, vp, vp]
         L.dm_plan_create_flat.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(vp)]
         L.dm_set_spectra_flat.argtypes = [vp, vp]
         L.dm_set_noise_flat.argtypes = [vp, vp, vp, vp]
@@ -297,6 +300,16 @@ class Plan:
     def test_tc_withhold(self, on=True):
         """Failure-test hook: one withheld mbarrier arrival in the tensor-core analysis."""
         self._check(lib().dm_test_tc_withhold(self.h, 1 if on else 0))
+
+    def set_progressive(self, margin=0.25, lmin=8):
+        """Progressive working resolution per cooling level (0 turns it off)."""
+        self._check(lib().dm_set_progressive(self.h, ctypes.c_double(margin), int(lmin)))
+
+    def progressive_levels(self, n_levels):
+        nk = np.zeros(n_levels, dtype=np.int32)
+        lk = np.zeros(n_levels, dtype=np.int32)
+        self._check(lib().dm_get_progressive_levels(self.h, _np_ptr(nk), _np_ptr(lk)))
+        return list(zip(nk.tolist(), lk.tolist()))
 
     def set_diagnostics(self, on=True):
         """End-of-solve true residual and chi^2 in the stats (default on)."""
