@@ -61,6 +61,8 @@ def parse():
                     help="ring transforms of radix 2^k (3 or 4), 0 = generic kernels (default: autotuned)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch heuristics instead of dm_autotune's picks")
+    ap.add_argument("--tuning", default=None,
+                    help="JSON of launch picks (a bench line's autotune object) applied instead of tuning")
     ap.add_argument("--solve-tol", type=float, default=None,
                     help="run whole solves to this final Cauchy threshold and report WF solves/s instead")
     ap.add_argument("--solve-max-iter", type=int, default=200000)
@@ -156,18 +158,18 @@ def iters_split(k, nlev=10):
 # source files that define each timed kernel (a stored ncu traffic figure is
 # used only while they are unchanged)
 KERNEL_SOURCES = {
-    "k_ring_iter": ["dm_ring.cu", "dm_fft.cuh", "dm_internal.h"],
-    "k_leg_syn64": ["dm_legendre.cu", "dm_internal.h"],
-    "k_leg_ana64": ["dm_legendre.cu", "dm_internal.h"],
-    "k_syn_tc": ["dm_legendre_tc.cu", "dm_tc.cuh", "dm_internal.h"],
-    "k_ana_tc": ["dm_legendre_tc.cu", "dm_tc.cuh", "dm_internal.h"],
-    "k_reduce": ["dm_legendre.cu", "dm_internal.h"],
+    "k_ring_iter": ["dm_ring.cu", "dm_fft.cuh"],
+    "k_leg_syn64": ["dm_legendre.cu", "dm_rec.cuh"],
+    "k_leg_ana64": ["dm_legendre.cu", "dm_rec.cuh"],
+    "k_syn_tc": ["dm_legendre_tc.cu", "dm_tc.cuh"],
+    "k_ana_tc": ["dm_legendre_tc.cu", "dm_tc.cuh"],
+    "k_reduce": ["dm_legendre.cu"],
 }
 
 
 def kernel_source_hash(kernel):
     h = hashlib.sha1()
-    for fn in KERNEL_SOURCES.get(kernel, ["dm_legendre.cu", "dm_internal.h"]):
+    for fn in KERNEL_SOURCES.get(kernel, ["dm_legendre.cu"]):
         h.update(open(os.path.join(ROOT, "paper_1801_05358_gb300", "csrc", fn), "rb").read())
     return h.hexdigest()[:12]
 
@@ -603,7 +605,11 @@ def main():
                    "ms_per_step": fms / nf, "precision": "DM_FLOAT_FLOAT"}
     plan.set_precision(prec)
     tuning = None
-    if args.ring_radix is None and not args.no_autotune:
+    if args.tuning:
+        plan.set_tuning(json.loads(open(args.tuning).read() if os.path.exists(args.tuning) else args.tuning))
+        tuning = plan.tuning()
+        tuning["source"] = "applied (--tuning)"
+    elif args.ring_radix is None and not args.no_autotune:
         t0 = time.perf_counter()
         tuning = plan.autotune()
         tuning["seconds"] = time.perf_counter() - t0
@@ -745,6 +751,7 @@ def main():
         plan.set_forced_iters(iters_split(K))
         d_host = d.cpu().pin_memory()
         s_host = torch.empty_like(d_host).pin_memory()
+        plan.set_diagnostics(False)  # a throughput call: no end-of-solve residual and chi^2
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -752,13 +759,14 @@ def main():
         plan.wiener_filter_host(d_host, s_host)
         h1.record(stream)
         torch.cuda.synchronize()
+        plan.set_diagnostics(True)
         wall = time.perf_counter() - t0
         ems = max(h0.elapsed_time(h1), wall * 1e3)
         nbytes = d_host.numel() * 8
         e2e = {"value": B * K / (ems * 1e-3), "unit": "DM iterations/s",
                "h2d_bytes_per_step": nbytes / K, "d2h_bytes_per_step": nbytes / K,
                "note": f"one dm_wiener_filter_host call of {K} iterations (a whole solve: begin, {K} "
-                       f"iterations, end); d in and s out once per call"}
+                       f"iterations, end); d in and s out once per call; end-of-solve diagnostics off"}
 
     # ---- CPU baseline (oracle), rank 0 at N = 1 only ----
     cpu, err = None, None
