@@ -242,6 +242,19 @@ dm_status dm_set_anchor_precision(dm_plan *plan, dm_precision prec);
  * the flag cleared. */
 dm_status dm_set_tensor_cores(dm_plan *plan, int on);
 
+/* Source of the tensor cores' Legendre operand (default 1).
+ * 1: the kernels generate each tile from checkpoints of the FP64 recurrence
+ *    (the state at every 64th multipole of each (m, ring pair), stored in
+ *    FP32 with a power-of-two scale: 32 bytes per checkpoint, about 150 MB at
+ *    nside 512 / lmax 1024) and advance it in FP32 with a float-float
+ *    product by cos(theta), the Legendre functions' recurrence in l of
+ *    Section 2.3 run inside the contraction;
+ * 0: they stream tiles of stored BF16 hi/lo tables (16 GB at nside 512 /
+ *    lmax 1024), built on first use.
+ * Both give the same products to within the BF16 hi/lo rounding.  DM_EINVAL
+ * for a null plan, DM_EBUSY during a solve session. */
+dm_status dm_set_tc_tiles(dm_plan *plan, int generate);
+
 /* Tuning: the ring transforms of an iteration for rings whose FFT size M is a
  * power of two in [512, 4096] run as fixed-size kernels of radix 2^lr with
  * M / 2^lr threads per ring and (RHS, field) lane; lr = 3 (radix 8, the

@@ -183,6 +183,16 @@ struct dm_plan {
   unsigned char *tc_synA[2] = {nullptr, nullptr}, *tc_anaA[2] = {nullptr, nullptr};
   int64_t *tc_soff = nullptr, *tc_aoff = nullptr;  // block offsets per m / per (m, parity)
   unsigned char *tc_synB[2] = {nullptr, nullptr};   // per-iteration synthesis B operand tiles
+  // tensor-core Legendre tiles generated in the kernels (dm_legendre_otf.cu):
+  // FP32 recurrence from FP32 checkpoints of the FP64 recurrence, one per
+  // (m, block of 64 multipoles, ring pair), instead of the stored tables
+  int tc_gen = 1;               // 1: generate the tiles in the kernels; 0: stream the stored tables
+  float4 *ck0 = nullptr;        // [nck][npairs] (lambda_l, lambda_l-1 or D_l, S0, S2): S as int bits, value x 2^-S
+  float4 *ck2 = nullptr;        // [nck][npairs] (2lam_l, 2lam_l-1 or D, -2lam_l, -2lam_l-1 or D) / 2, x 2^-S2
+  int64_t *cko = nullptr;       // [mmax + 2] first checkpoint block of each m
+  float4 *rq0 = nullptr;        // [nalm] FP32 spin-0 coefficients of target l (al, bl, al - 1 - bl, 0)
+  float4 *rq2 = nullptr;        // [nalm] FP32 spin-2 coefficients (a, ac, b, 0)
+  float2 *rq2d = nullptr;       // [nalm] (a + ac - 1 - b, a - ac - 1 - b) for the difference form of target l
   // solve session (dm_solve_begin / iterate / end)
   double *s64 = nullptr;        // [B][3][npix] FP64 iterate s (FP64 mode) / Y a_hi (mixed)
   double *rhi = nullptr;        // [B][3][npix] FP64 anchor residual w (d - Y a_hi)
@@ -286,6 +296,11 @@ bool tc_batch_ok(int B);
 size_t tc_table_bytes(int lmax, int mmax, int npairs, int B);
 cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t st);
 cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st);
+// tensor-core stages with the Legendre tiles generated in the kernels (dm_legendre_otf.cu)
+cudaError_t gen_setup(dm_plan *p);
+size_t gen_bytes(int lmax, int mmax, int npairs);
+cudaError_t syn_gen_launch(dm_plan *p, bool run0, bool run1, cudaStream_t st);
+cudaError_t ana_gen_launch(dm_plan *p, cudaStream_t st);
 cudaError_t legendre_synthesis_ff(dm_plan *p, const double2 *alm, cudaStream_t st);
 cudaError_t anchor_c32(dm_plan *p, cudaStream_t st);     // c = F (a_hi + g_hi) - a_hi, e = 0
 cudaError_t materialize_a(dm_plan *p, cudaStream_t st);  // a = a_hi + e

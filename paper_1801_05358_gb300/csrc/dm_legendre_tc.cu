@@ -26,6 +26,7 @@
 
 #include "dm_internal.h"
 #include "dm_tc.cuh"
+#include "dm_tc_tiles.cuh"
 
 namespace dmwf {
 
@@ -34,30 +35,6 @@ using namespace tc;
 namespace {
 
 constexpr int TC_THREADS = 256;
-constexpr int TILE_A = 4096;  // 128 x 16 BF16
-
-__device__ __forceinline__ int64_t abase(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
-
-// byte offset of the 16-byte core-matrix row (row, k-octet ko) of a [rows x 16] K-major tile
-__device__ __forceinline__ uint32_t crow(int row, int ko) {
-  return (uint32_t)((row >> 3) * 256 + ko * 128 + (row & 7) * 16);
-}
-
-__device__ __forceinline__ void put_row(unsigned char *tile, int tile_bytes, int row, int ko, const float x[8]) {
-  uint4 h, l;
-  split8(x, h, l);
-  *reinterpret_cast<uint4 *>(tile + crow(row, ko)) = h;
-  *reinterpret_cast<uint4 *>(tile + tile_bytes + crow(row, ko)) = l;
-}
-
-__device__ __forceinline__ void mma3(uint32_t d, const unsigned char *a, const unsigned char *b, int tile_b,
-                                     uint32_t idesc, uint32_t acc) {
-  const uint64_t ah = smem_desc(smem_u32(a)), al = smem_desc(smem_u32(a + TILE_A));
-  const uint64_t bh = smem_desc(smem_u32(b)), bl = smem_desc(smem_u32(b + tile_b));
-  mma_bf16(d, ah, bh, idesc, acc);
-  mma_bf16(d, ah, bl, idesc, 1u);
-  mma_bf16(d, al, bh, idesc, 1u);
-}
 
 __device__ __forceinline__ float2 e_of(const double2 *a, const double2 *ahi, int64_t i) {
   double2 v = a[i];
@@ -67,12 +44,6 @@ __device__ __forceinline__ float2 e_of(const double2 *a, const double2 *ahi, int
     v.y -= h.y;
   }
   return make_float2((float)v.x, (float)v.y);
-}
-
-__device__ __forceinline__ void tc_teardown(uint32_t tbase, uint32_t ncols) {
-  fence_before_sync();
-  __syncthreads();
-  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tbase, ncols);
 }
 
 }  // namespace
@@ -85,12 +56,6 @@ __device__ __forceinline__ void tc_teardown(uint32_t tbase, uint32_t ncols) {
 // Analysis: per (m, parity, l tile lt, K step c) one block of nA tiles, each
 // 128 multipoles (l = m + par + 2 i, i = 128 lt + row) x 16 ring pairs, hi
 // then lo.  PART 0 tile {lambda}; PART 1 {lam+, lam-}.
-__host__ __device__ inline int syn_steps(int lmax, int m) { return (lmax - m + 1 + 31) / 32; }
-__host__ __device__ inline int ana_nl(int lmax, int m, int par) { return (lmax - m + 1 - par + 1) / 2; }
-__host__ __device__ inline int ana_tiles(int lmax, int m, int par) {
-  const int nl = ana_nl(lmax, m, par);
-  return nl > 0 ? (nl + 127) / 128 : 0;
-}
 
 template <int PART>
 __global__ void k_tab_syn(const float *__restrict__ ptab, unsigned char *__restrict__ out,
@@ -357,77 +322,6 @@ __global__ void __launch_bounds__(128, 1) k_syn_tc(const unsigned char *__restri
 // l = m + p + 2 i.  The LT tiles of a CTA share each converted B tile, one
 // tensor-memory accumulator of NC columns per tile.
 // Output: out[b][f][alm] (FP32 partial sums with a single chunk).
-// 8 ring pairs (north, south) of one field, as 16 float2; zero past npairs, no
-// south ring at the equator pair.
-__device__ __forceinline__ void load_pairs8(const float2 *__restrict__ g, int pair0, int npairs, float2 v[16]) {
-  if (pair0 + 8 < npairs) {
-    const float4 *g4 = reinterpret_cast<const float4 *>(g + 2 * (int64_t)pair0);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float4 q = g4[i];
-      v[2 * i] = make_float2(q.x, q.y);
-      v[2 * i + 1] = make_float2(q.z, q.w);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int pair = pair0 + i;
-      v[2 * i] = pair < npairs ? g[2 * (int64_t)pair] : make_float2(0.f, 0.f);
-      v[2 * i + 1] = pair < npairs - 1 ? g[2 * (int64_t)pair + 1] : make_float2(0.f, 0.f);
-    }
-  }
-}
-
-// Analysis B operand, split in two so that the loads of step c + 1 are in
-// flight while step c is converted and multiplied.  One task per thread at
-// most (PART 0: 2B tasks, PART 1: 4B tasks, B <= 64).
-//  PART 0 task = (b / 4) * 8 + (b & 3) * 2 + ko: rows 2b, 2b + 1
-//  PART 1 task = (b / 2) * 8 + (b & 1) * 4 + f * 2 + ko, f = 0 (Q) / 1 (U)
-template <int PART>
-__device__ __forceinline__ void load_ana_b(int task, const float2 *__restrict__ rc, int m, int c, int mmax,
-                                           int npairs, float2 v[16]) {
-  const int ko = task & 1;
-  const int b = PART == 0 ? (task >> 3) * 4 + ((task >> 1) & 3) : (task >> 3) * 2 + ((task >> 2) & 1);
-  const int f = PART == 0 ? 0 : 1 + ((task >> 1) & 1);
-  load_pairs8(rc + (((int64_t)b * 3 + f) * (mmax + 1) + m) * npairs * 2, 16 * c + 8 * ko, npairs, v);
-}
-
-template <int PART>
-__device__ __forceinline__ void convert_ana_b(int task, unsigned char *Bbuf, int tileB, int par, const float2 v[16]) {
-  const float sgn = par == 0 ? 1.f : -1.f;  // G_par = G_N + sgn G_S
-  const int ko = task & 1;
-  if (PART == 0) {
-    const int b = (task >> 3) * 4 + ((task >> 1) & 3);
-    float re[8], im[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      re[i] = v[2 * i].x + sgn * v[2 * i + 1].x;
-      im[i] = v[2 * i].y + sgn * v[2 * i + 1].y;
-    }
-    put_row(Bbuf, tileB, 2 * b + ko, ko, ko ? im : re);
-    put_row(Bbuf, tileB, 2 * b + (ko ^ 1), ko, ko ? re : im);
-  } else {
-    const int f = (task >> 1) & 1, b = (task >> 3) * 2 + ((task >> 2) & 1);
-    float a0[8], a1[8], b0[8], b1[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float pr = v[2 * i].x + sgn * v[2 * i + 1].x, pi = v[2 * i].y + sgn * v[2 * i + 1].y;  // this parity
-      const float orr = v[2 * i].x - sgn * v[2 * i + 1].x, oi = v[2 * i].y - sgn * v[2 * i + 1].y;  // opposite
-      // B1: Q -> rows 4b (-Qp.re), 4b+1 (-Qp.im); U -> rows 4b+2 (-Up.re), 4b+3 (-Up.im)
-      a0[i] = -pr;
-      a1[i] = -pi;
-      // B2: U -> rows 4b (Uo.im), 4b+1 (-Uo.re); Q -> rows 4b+2 (-Qo.im), 4b+3 (Qo.re)
-      b0[i] = f == 1 ? oi : -oi;
-      b1[i] = f == 1 ? -orr : orr;
-    }
-    unsigned char *B1 = Bbuf, *B2 = Bbuf + 2 * tileB;
-    const int r1 = 4 * b + 2 * f, r2 = 4 * b + 2 * (1 - f);
-    put_row(B1, tileB, r1 + ko, ko, ko ? a1 : a0);
-    put_row(B1, tileB, r1 + (ko ^ 1), ko, ko ? a0 : a1);
-    put_row(B2, tileB, r2 + ko, ko, ko ? b1 : b0);
-    put_row(B2, tileB, r2 + (ko ^ 1), ko, ko ? b0 : b1);
-  }
-}
 
 // Warp roles: warps 0 .. 7 convert the ring-coefficient operand of each K
 // step into its stage, in ngroups groups of nconv warps that take the steps in
@@ -585,20 +479,6 @@ __global__ void __launch_bounds__(ANA_THREADS, 1) k_ana_tc(const unsigned char *
 }
 
 // ------------------------------------------------------------------ launch
-static uint32_t pow2_cols(int n) {
-  uint32_t c = 32;
-  while ((int)c < n) c <<= 1;
-  return c;
-}
-
-// smem per CTA for NS stages, raised when needed so that the CTAs sharing an
-// SM never ask for more tensor memory than its 512 columns
-static size_t tc_smem_n(int stage_bytes, int ns, uint32_t ncols) {
-  size_t s = (size_t)ns * stage_bytes + 1024;
-  const int per_sm = (int)(512 / ncols);
-  const size_t floor_bytes = (232448 / (per_sm + 1)) + 1024;
-  return s > floor_bytes ? s : floor_bytes;
-}
 
 bool tc_batch_ok(int B) { return B == 8 || B == 16 || B == 32 || B == 64; }
 
@@ -615,41 +495,63 @@ size_t tc_table_bytes(int lmax, int mmax, int npairs, int B) {
                   ssteps * (int64_t)B * (2 * 2 * 64 + 4 * 2 * 128));
 }
 
-// The tiled BF16 hi/lo copies of the FP32 Legendre tables, made on first use.
-static cudaError_t tc_tables(dm_plan *p) {
-  if (p->tc_synA[0]) return cudaSuccess;
-  const int npt = (p->npairs + 127) / 128, nps = (p->npairs + 15) / 16;
+// Block offsets per m (synthesis) and per (m, parity) (analysis), and the
+// per-iteration B operand of the synthesis: needed by both the stored-table
+// and the generated-tile kernels.
+static cudaError_t tc_scratch(dm_plan *p) {
+  if (p->tc_synB[1]) return cudaSuccess;
   std::vector<int64_t> soff(p->mmax + 2, 0), aoff(2 * (p->mmax + 1) + 1, 0);
-  int max_lt = 0;
   for (int m = 0; m <= p->mmax; ++m) {
     soff[m + 1] = soff[m] + syn_steps(p->lmax, m);
-    for (int par = 0; par < 2; ++par) {
-      const int nt = ana_tiles(p->lmax, m, par);
-      aoff[2 * m + par + 1] = aoff[2 * m + par] + nt;
-      max_lt = std::max(max_lt, nt);
-    }
+    for (int par = 0; par < 2; ++par) aoff[2 * m + par + 1] = aoff[2 * m + par] + ana_tiles(p->lmax, m, par);
   }
   cudaError_t e;
-  const size_t sbytes[2] = {(size_t)soff[p->mmax + 1] * npt * 2 * 2 * TILE_A,
-                            (size_t)soff[p->mmax + 1] * npt * 4 * 2 * TILE_A};
-  const size_t abytes[2] = {(size_t)aoff[2 * (p->mmax + 1)] * nps * 1 * 2 * TILE_A,
-                            (size_t)aoff[2 * (p->mmax + 1)] * nps * 2 * 2 * TILE_A};
-  for (int part = 0; part < 2; ++part) {
-    if ((e = cudaMalloc(&p->tc_synA[part], sbytes[part]))) return e;
-    if ((e = cudaMalloc(&p->tc_anaA[part], abytes[part]))) return e;
-    p->bytes += (int64_t)(sbytes[part] + abytes[part]);
+  if (!p->tc_soff) {
+    if ((e = cudaMalloc(&p->tc_soff, sizeof(int64_t) * soff.size()))) return e;
+    cudaMemcpy(p->tc_soff, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice);
   }
-  {  // per-iteration B operand of the synthesis (depends on the batch)
-    const size_t b0 = (size_t)soff[p->mmax + 1] * 2 * 2 * (2 * p->batch * 32);
-    const size_t b1 = (size_t)soff[p->mmax + 1] * 4 * 2 * (4 * p->batch * 32);
+  if (!p->tc_aoff) {
+    if ((e = cudaMalloc(&p->tc_aoff, sizeof(int64_t) * aoff.size()))) return e;
+    cudaMemcpy(p->tc_aoff, aoff.data(), sizeof(int64_t) * aoff.size(), cudaMemcpyHostToDevice);
+  }
+  const size_t b0 = (size_t)soff[p->mmax + 1] * 2 * 2 * (2 * p->batch * 32);
+  const size_t b1 = (size_t)soff[p->mmax + 1] * 4 * 2 * (4 * p->batch * 32);
+  if (!p->tc_synB[0]) {
     if ((e = cudaMalloc(&p->tc_synB[0], b0))) return e;
-    if ((e = cudaMalloc(&p->tc_synB[1], b1))) return e;
-    p->bytes += (int64_t)(b0 + b1);
+    p->bytes += (int64_t)b0;
   }
-  if ((e = cudaMalloc(&p->tc_soff, sizeof(int64_t) * soff.size()))) return e;
-  if ((e = cudaMalloc(&p->tc_aoff, sizeof(int64_t) * aoff.size()))) return e;
-  cudaMemcpy(p->tc_soff, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(p->tc_aoff, aoff.data(), sizeof(int64_t) * aoff.size(), cudaMemcpyHostToDevice);
+  if ((e = cudaMalloc(&p->tc_synB[1], b1))) return e;
+  p->bytes += (int64_t)b1;
+  return cudaSuccess;
+}
+
+// The tiled BF16 hi/lo copies of the FP32 Legendre tables, made on first use.
+static cudaError_t tc_tables(dm_plan *p) {
+  if (p->tc_synA[1] && p->tc_anaA[1]) return cudaSuccess;
+  cudaError_t e = tc_scratch(p);
+  if (e) return e;
+  const int npt = (p->npairs + 127) / 128, nps = (p->npairs + 15) / 16;
+  int64_t ssteps = 0, atiles = 0;
+  int max_lt = 0;
+  for (int m = 0; m <= p->mmax; ++m) {
+    ssteps += syn_steps(p->lmax, m);
+    for (int par = 0; par < 2; ++par) {
+      atiles += ana_tiles(p->lmax, m, par);
+      max_lt = std::max(max_lt, ana_tiles(p->lmax, m, par));
+    }
+  }
+  const size_t sbytes[2] = {(size_t)ssteps * npt * 2 * 2 * TILE_A, (size_t)ssteps * npt * 4 * 2 * TILE_A};
+  const size_t abytes[2] = {(size_t)atiles * nps * 1 * 2 * TILE_A, (size_t)atiles * nps * 2 * 2 * TILE_A};
+  for (int part = 0; part < 2; ++part) {
+    if (!p->tc_synA[part]) {
+      if ((e = cudaMalloc(&p->tc_synA[part], sbytes[part]))) return e;
+      p->bytes += (int64_t)sbytes[part];
+    }
+    if (!p->tc_anaA[part]) {
+      if ((e = cudaMalloc(&p->tc_anaA[part], abytes[part]))) return e;
+      p->bytes += (int64_t)abytes[part];
+    }
+  }
   dim3 gs(syn_steps(p->lmax, 0), npt, p->mmax + 1);
   k_tab_syn<0><<<gs, 256>>>(p->ptab, p->tc_synA[0], p->tc_soff, p->lmax, p->npairs, p->nalm, npt);
   k_tab_syn<1><<<gs, 256>>>(p->ptab, p->tc_synA[1], p->tc_soff, p->lmax, p->npairs, p->nalm, npt);
@@ -678,7 +580,7 @@ static int syn_stages_pick(int want, int stage_bytes, uint32_t ncols) {
 }
 
 cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t st) {
-  cudaError_t e = tc_tables(p);
+  cudaError_t e = p->tc_gen ? tc_scratch(p) : tc_tables(p);
   if (e) return e;
   const int B = p->batch;
   const double2 *ahi = p->anchor_active ? p->a_hi : nullptr;
@@ -688,6 +590,7 @@ cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t s
   const bool run0 = p->tune_only_part != 1, run1 = p->tune_only_part != 0;
   if (run0) k_syn_b<0><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[0], p->tc_soff, alm, ahi, e32, p->lmax, p->nalm, B);
   if (run1) k_syn_b<1><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[1], p->tc_soff, alm, ahi, e32, p->lmax, p->nalm, B);
+  if (p->tc_gen) return syn_gen_launch(p, run0, run1, st);
   dim3 g(npt, p->mmax + 1);
   if (run0) {
     const int stage = 2 * 2 * TILE_A + 2 * 2 * (2 * B * 32);
@@ -739,6 +642,7 @@ static int ana_S_pick(int want, int stage_bytes) {
 }
 
 cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st) {
+  if (p->tc_gen) return ana_gen_launch(p, st);
   cudaError_t e = tc_tables(p);
   if (e) return e;
   const int B = p->batch;

@@ -31,7 +31,7 @@ std::string tune_key(const dm_plan *p) {
     dev = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount);
   return dev + "|" + std::to_string(p->nside) + "|" + std::to_string(p->lmax) + "|" + std::to_string(p->batch) +
          "|" + std::to_string((int)p->prec) + "|" + std::to_string((int)p->ff_legendre) + "|" +
-         std::to_string((int)(p->use_tc && tc_batch_ok(p->batch)));
+         std::to_string((int)(p->use_tc && tc_batch_ok(p->batch))) + "|" + std::to_string(p->tc_gen);
 }
 
 void apply(dm_plan *p, const dm_tuning &t) {
@@ -47,7 +47,7 @@ void apply(dm_plan *p, const dm_tuning &t) {
   for (int k = 0; k < 2; ++k) {
     p->tune_syn_ns[k] = (t.syn_stages[k] >= 2 && t.syn_stages[k] <= 8) ? t.syn_stages[k] : 0;
     p->tune_ana_lt[k] = (t.ana_ltiles[k] >= 1 && t.ana_ltiles[k] <= 4) ? t.ana_ltiles[k] : 0;
-    p->tune_ana_S[k] = (t.ana_stages[k] >= 2 && t.ana_stages[k] <= 4) ? t.ana_stages[k] : 0;
+    p->tune_ana_S[k] = (t.ana_stages[k] >= 1 && t.ana_stages[k] <= 5) ? t.ana_stages[k] : 0;
   }
 }
 
@@ -192,7 +192,7 @@ dm_status autotune(dm_plan *p, cudaStream_t st, std::string &err) {
       int best_lt = p->ana_lt_used[part], best_S = p->ana_S_used[part];
       std::vector<std::pair<int, int>> aseen{{best_lt, best_S}};
       for (int lt = 1; lt <= 4; ++lt)
-        for (int S = 2; S <= 4; ++S) {
+        for (int S = 2; S <= (p->tc_gen ? 5 : 4); ++S) {
           p->tune_ana_lt[part] = lt;
           p->tune_ana_S[part] = S;
           if (ana() != cudaSuccess) break;

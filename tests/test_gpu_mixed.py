@@ -137,3 +137,33 @@ def test_tc_fixed_schedule_nside16(orc):
     for b in [0, 3, 7]:
         ref = orc.dm_solve(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.mask, d[b], lam, forced_iters=[10] * 10)
         assert rel(got[b], ref["s"]) < 1e-5
+
+
+# The tensor-core operand generated in the kernels (dm_set_tc_tiles, the
+# default) from checkpoints of the FP64 recurrence every 64 multipoles,
+# against the oracle and against the stored-table tiles: several checkpoint
+# blocks, polar rings (difference form of the recurrence), high orders whose
+# values start far below FP32 range (scaled checkpoints).
+@pytest.mark.parametrize("nside,lmax,B", [(64, 128, 8), (128, 383, 8), (256, 512, 16)])
+def test_tc_generated_tiles(orc, nside, lmax, B):
+    alm = W.random_alm(lmax, B, 38)
+    maps = W.random_maps(nside, B, 39)
+    p = dmwf.Plan(nside, lmax, B)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    npix, nalm = 12 * nside * nside, (lmax + 1) * (lmax + 2) // 2
+    res = {}
+    for gen in (True, False):
+        p.set_tc_tiles(gen)
+        m_out = torch.zeros((B, 3, npix), dtype=torch.float64, device="cuda")
+        a_out = torch.zeros((B, 3, nalm, 2), dtype=torch.float64, device="cuda")
+        p.alm2map(alm_dev(alm), m_out)
+        p.map2alm(dev(maps), a_out)
+        torch.cuda.synchronize()
+        res[gen] = (m_out.cpu().numpy(), a_out.cpu().numpy().view(np.complex128)[..., 0])
+    p.close()
+    gm, ga = res[True]
+    tm, ta = res[False]
+    assert rel(gm, tm) < 2e-5 and rel(ga, ta) < 2e-5
+    for b in (0, B - 1):
+        assert rel(gm[b], orc.alm2map(nside, lmax, alm[b])) < 2e-5
+        assert rel(ga[b], orc.map2alm(nside, lmax, maps[b])) < 2e-5
