@@ -242,7 +242,9 @@ dm_status dm_set_anchor_precision(dm_plan *plan, dm_precision prec);
  * the flag cleared. */
 dm_status dm_set_tensor_cores(dm_plan *plan, int on);
 
-/* Source of the tensor cores' Legendre operand (default 1).
+/* Source of the tensor cores' Legendre operand (default -1: stored tiles when
+ * they and the FP32 tables they are cut from take at most 40 GiB, as at
+ * nside 512 / lmax 1024 (26 GB), else generated tiles).
  * 1: the kernels generate each tile from checkpoints of the FP64 recurrence
  *    (the state at every 64th multipole of each (m, ring pair), stored in
  *    FP32 with a power-of-two scale: 32 bytes per checkpoint, about 150 MB at
@@ -251,9 +253,20 @@ dm_status dm_set_tensor_cores(dm_plan *plan, int on);
  *    Section 2.3 run inside the contraction;
  * 0: they stream tiles of stored BF16 hi/lo tables (16 GB at nside 512 /
  *    lmax 1024), built on first use.
- * Both give the same products to within the BF16 hi/lo rounding.  DM_EINVAL
- * for a null plan, DM_EBUSY during a solve session. */
+ * Both give the same products to within the BF16 hi/lo rounding.  Without
+ * stored tiles the plan keeps no full FP32 tables either: the float-float
+ * anchors generate theirs per slab of orders (1 GiB).  DM_EINVAL for a null
+ * plan, DM_EBUSY during a solve session. */
 dm_status dm_set_tc_tiles(dm_plan *plan, int generate);
+
+/* Memory for the float-float stages' per-slab Legendre tables, used when the
+ * plan has no full FP32 tables (DM_FLOAT_FLOAT, and DM_MIXED_FP32's anchors
+ * with generated tiles): each stage call generates the tables of one slab of
+ * orders m (FP64 recurrence, hi and lo in FP32) and contracts it before the
+ * next.  bytes: the largest slab (default 1 GiB; at least one order m is
+ * always taken).  Takes effect at the next stage call; DM_EINVAL for a null
+ * plan or bytes < 1, DM_EBUSY during a solve session. */
+dm_status dm_set_ff_slab_bytes(dm_plan *plan, int64_t bytes);
 
 /* Tuning: the ring transforms of an iteration for rings whose FFT size M is a
  * power of two in [512, 4096] run as fixed-size kernels of radix 2^lr with
@@ -476,9 +489,10 @@ dm_status dm_set_noise_flat(dm_plan *plan, const double *sigma, const uint8_t *m
 
 /* Failure test of the tensor-core pipeline's bounded waits (no counterpart in
  * the paper): while on, the spin-0 tensor-core analysis of the mixed mode
- * withholds one plain mbarrier arrival (the first converter thread of its
- * first CTA, first K step), so the MMA warp's wait gives up after 1 s with no
- * copy or MMA in flight on that barrier; the CTA then drains its copies,
+ * withholds one plain mbarrier arrival (with stored tiles the first converter
+ * thread of its first CTA, with generated tiles the first lane of its first
+ * worker warp; first K step), so the MMA warp's wait gives up after 1 s with
+ * no copy or MMA in flight on that barrier; the CTA then drains its copies,
  * frees its tensor memory and exits, and the solve calls return
  * DM_ETIMEOUT.  The plan and the CUDA context stay usable: turn it off and
  * the next solve is normal.  Not for production use. */

@@ -52,7 +52,7 @@ void free_all(dm_plan *p) {
                   p->tc_synB[0], p->tc_synB[1], p->ptab_lo, p->e32, p->c32, p->clev, p->filt32,
                   p->twr, p->twr32, p->chirp, p->chirp32, p->wcov, p->diag_tab, p->diag_alm, p->diag_part,
                   p->diag_ao, p->covdraw, p->jsrc, p->jacc, p->bhatT[0], p->bhatT[1], p->bhatT32[0],
-                  p->bhatT32[1], p->ck0, p->ck2, p->cko, p->rq0, p->rq2, p->rq2d};
+                  p->bhatT32[1], p->ck0, p->ck2, p->cko, p->rq0, p->rq2, p->rq2d, p->ffs, p->ffs_lo};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (p->ev_begin) cudaEventDestroy(p->ev_begin);
@@ -913,6 +913,17 @@ dm_status dm_jacobi_refine(dm_plan *p, const double *d, int n_refine, double *s_
   return r;
 }
 
+dm_status dm_set_ff_slab_bytes(dm_plan *p, int64_t bytes) {
+  if (!p || bytes < 1) return DM_EINVAL;
+  if (p->session) return DM_EBUSY;
+  p->ffs_cap = bytes;
+  if (p->ffs) cudaFree(p->ffs);
+  if (p->ffs_lo) cudaFree(p->ffs_lo);
+  p->ffs = p->ffs_lo = nullptr;
+  p->ffs_m.clear();
+  return DM_OK;
+}
+
 dm_status dm_test_tc_withhold(dm_plan *p, int on) {
   if (!p) return DM_EINVAL;
   p->tc_withhold = on != 0;
@@ -957,7 +968,8 @@ dm_status dm_set_tc_tiles(dm_plan *p, int generate) {
   if (!p) return DM_EINVAL;
   if (p->session) return DM_EBUSY;
   prog_release(p);
-  p->tc_gen = generate != 0 ? 1 : 0;
+  p->tc_gen = generate < 0 ? -1 : (generate != 0 ? 1 : 0);
+  p->tc_gen_used = -1;
   return DM_OK;
 }
 

@@ -151,8 +151,16 @@ struct dm_plan {
   bool state_active = false;    // kernels consult state[] (skip finished RHS)
   int64_t bytes = 0;
   // DM_MIXED_FP32 resources (allocated by dm_set_precision)
+  bool fp32_ready = false;      // the buffers of the FP32 modes exist (setup_fp32 succeeded)
+  // Full FP32 tables: built on first use by the kernels that read them (the
+  // CUDA-core FP32 Legendre stages and the stored-table tensor-core tiles).
+  // The float-float stages read them when present and otherwise generate
+  // them per slab of orders m into ffs / ffs_lo.
   float *ptab = nullptr;        // [3][nalm][npairs] lambda, lam+, lam- in FP32 (FP64 recurrence)
   float *ptab_lo = nullptr;     // [3][nalm][npairs] FP64 value - ptab: float-float tables
+  float *ffs = nullptr, *ffs_lo = nullptr;  // slab tables of the float-float stages
+  std::vector<int> ffs_m;       // slab boundaries in m (first orders, then mmax + 1)
+  int64_t ffs_cap = (int64_t)1 << 30;  // bytes of the largest slab (hi and lo)
   bool ff_legendre = false;     // DM_FLOAT_FLOAT: Legendre stages in float-float
   bool anchor_ff = true;        // mixed-mode anchors in float-float (else FP64)
   bool ff_now = false;          // inside a float-float anchor
@@ -186,7 +194,8 @@ struct dm_plan {
   // tensor-core Legendre tiles generated in the kernels (dm_legendre_otf.cu):
   // FP32 recurrence from FP32 checkpoints of the FP64 recurrence, one per
   // (m, block of 64 multipoles, ring pair), instead of the stored tables
-  int tc_gen = 1;               // 1: generate the tiles in the kernels; 0: stream the stored tables
+  int tc_gen = -1;              // 1: generate the tiles in the kernels; 0: stream the stored tables; -1: auto
+  int tc_gen_used = -1;         // the resolved choice (tc_generate)
   float4 *ck0 = nullptr;        // [nck][npairs] (lambda_l, lambda_l-1 or D_l, S0, S2): S as int bits, value x 2^-S
   float4 *ck2 = nullptr;        // [nck][npairs] (2lam_l, 2lam_l-1 or D, -2lam_l, -2lam_l-1 or D) / 2, x 2^-S2
   int64_t *cko = nullptr;       // [mmax + 2] first checkpoint block of each m
@@ -284,7 +293,11 @@ cudaError_t control_step(dm_plan *p, cudaStream_t st);
 cudaError_t prepare_wd(dm_plan *p, const double *d, cudaStream_t st);
 cudaError_t cov_prepare_wd(dm_plan *p, const double *d, cudaStream_t st);  // dm_cov.cu
 cudaError_t cov_ring_stage(dm_plan *p, cudaStream_t st);
-cudaError_t setup_fp32(dm_plan *p);                          // tables and buffers of DM_MIXED_FP32
+cudaError_t setup_fp32(dm_plan *p);
+cudaError_t ensure_ptab(dm_plan *p);  // the full FP32 tables, built on first use
+// first alm index of order m (m = mmax + 1 = lmax + 1 gives nalm): idx(l, m) = start(m) + l - m
+inline int64_t alm_start_h(int lmax, int m) { return (int64_t)m * (2 * lmax + 3 - m) / 2; }
+cudaError_t gen_tables32_slab(dm_plan *p, float *hi, float *lo, int m0, int m1, cudaStream_t st);                          // tables and buffers of DM_MIXED_FP32
 cudaError_t copy_s32_to_user(dm_plan *p, double *s_out, cudaStream_t st);
 // anchor residual: r = w (d - s_hi) (or d on observed pixels when s_hi == nullptr),
 // written to p->wd; shi32 = s_hi in FP32
@@ -298,6 +311,8 @@ cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t s
 cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st);
 // tensor-core stages with the Legendre tiles generated in the kernels (dm_legendre_otf.cu)
 cudaError_t gen_setup(dm_plan *p);
+bool tc_tables_fit(int lmax, int mmax, int npairs, int B);  // auto rule: stored tiles when they fit
+bool tc_generate(dm_plan *p);                               // the plan's resolved choice
 size_t gen_bytes(int lmax, int mmax, int npairs);
 cudaError_t syn_gen_launch(dm_plan *p, bool run0, bool run1, cudaStream_t st);
 cudaError_t ana_gen_launch(dm_plan *p, cudaStream_t st);

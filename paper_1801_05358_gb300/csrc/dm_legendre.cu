@@ -300,12 +300,14 @@ cudaError_t apply_filter_level(dm_plan *p, const double *coef, const double2 *in
 // contraction; FP32 ring coefficients; FP64 harmonic state and filter.
 // ======================================================================
 
+// Tables of the orders m0 + blockIdx.y: entry (idx(l, m) - base0) * npairs +
+// pair of each function plane (plane entries apart), base0 = idx(m0, m0).
 __global__ void __launch_bounds__(128) k_gen_tables(const PairDev *__restrict__ pairs, const RecCoef *__restrict__ rec,
                                                     const double *__restrict__ seed, const int *__restrict__ seed_exp,
                                                     float *__restrict__ ptab, float *__restrict__ ptab_lo, int lmax,
-                                                    int npairs, int64_t nalm) {
+                                                    int npairs, int m0, int64_t base0, int64_t plane) {
   __shared__ RecCoef sc[SYN_CH];
-  const int m = blockIdx.y;
+  const int m = m0 + blockIdx.y;
   const int p = blockIdx.x * 128 + threadIdx.x;
   const bool act = p < npairs;
   const int pp = act ? p : npairs - 1;
@@ -313,7 +315,6 @@ __global__ void __launch_bounds__(128) k_gen_tables(const PairDev *__restrict__ 
   Rec s;
   rec_init(s, seed, seed_exp, m, pp, npairs);
   const int64_t base = alm_base(lmax, m);
-  const int64_t plane = nalm * (int64_t)npairs;
   for (int lc = m; lc <= lmax; lc += SYN_CH) {
     const int cnt = min(SYN_CH, lmax + 1 - lc);
     __syncthreads();
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(128) k_gen_tables(const PairDev *__restrict__ 
     for (int j = 0; j < cnt; ++j) {
       const int l = lc + j;
       if (act) {
-        const int64_t o = (base + l) * (int64_t)npairs + p;
+        const int64_t o = (base + l - base0) * (int64_t)npairs + p;
         const bool live = (s.S == 0);
         const double v0 = live ? s.l0 : 0.0, v1 = live ? 0.5 * (s.p0 + s.q0) : 0.0,
                      v2 = live ? 0.5 * (s.p0 - s.q0) : 0.0;
@@ -339,10 +340,14 @@ __global__ void __launch_bounds__(128) k_gen_tables(const PairDev *__restrict__ 
   }
 }
 
-cudaError_t gen_tables32(dm_plan *p) {
-  dim3 g((p->npairs + 127) / 128, p->mmax + 1);
-  k_gen_tables<<<g, 128>>>(p->pairs, p->rec, p->seed, p->seed_exp, p->ptab, p->ptab_lo, p->lmax, p->npairs,
-                           p->nalm);
+// Tables of the orders [m0, m1) into hi / lo, laid out as the full tables
+// restricted to those orders (planes of (idx(m1, m1) - idx(m0, m0)) x npairs).
+cudaError_t gen_tables32_slab(dm_plan *p, float *hi, float *lo, int m0, int m1, cudaStream_t st) {
+  if (m1 <= m0) return cudaSuccess;
+  const int64_t b0 = alm_start_h(p->lmax, m0), b1 = alm_start_h(p->lmax, m1);
+  dim3 g((p->npairs + 127) / 128, m1 - m0);
+  k_gen_tables<<<g, 128, 0, st>>>(p->pairs, p->rec, p->seed, p->seed_exp, hi, lo, p->lmax, p->npairs, m0, b0,
+                                  (b1 - b0) * (int64_t)p->npairs);
   return cudaGetLastError();
 }
 
@@ -579,6 +584,7 @@ __global__ void k_ana_reduce32(const float2 *__restrict__ apart, double2 *out, i
 
 cudaError_t legendre_synthesis32(dm_plan *p, const double2 *alm, cudaStream_t st) {
   if (p->use_tc && tc_batch_ok(p->batch)) return legendre_synthesis_tc(p, alm, st);
+  if (cudaError_t e = ensure_ptab(p)) return e;
   const SolveState *stp = p->state_active ? p->state : nullptr;
   const int pb = (p->npairs + SYN_THREADS - 1) / SYN_THREADS;
   if (p->batch % 4 == 0) {
@@ -714,6 +720,8 @@ cudaError_t legendre_analysis32(dm_plan *p, int epilogue, double2 *out, cudaStre
     cudaError_t e = legendre_analysis_tc(p, st);
     if (e) return e;
     nchunk = 1;
+  } else if (cudaError_t e = ensure_ptab(p)) {
+    return e;
   } else if (p->batch % 4 == 0) {
     dim3 g(p->batch / 4, p->nchunk, p->mmax + 1);
     k_leg_ana32<4><<<g, ANA_P, 0, st>>>(p->ptab, p->rc32, p->apart32, p->lmax, p->mmax, p->npairs, p->nalm,

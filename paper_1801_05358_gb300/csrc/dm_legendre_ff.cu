@@ -16,6 +16,8 @@
 // the FP64 cost.  Products and sums are written with __fmul_rn / __fadd_rn so
 // that the compiler does not contract them into FMAs, which would break the
 // error-free transformations.
+#include <algorithm>
+
 #include "dm_internal.h"
 
 namespace dmwf {
@@ -89,16 +91,19 @@ __device__ __forceinline__ void syn_ff_step(ff (&acc)[2][6], ff lam, ff lp, ff l
 // Synthesis: one thread per ring pair, NB right-hand sides; the a_lm of a chunk
 // of FF_SYN_CH multipoles are staged in shared memory as float-float.
 // Output: ring coefficients rc[b][f][m][pair][side] in FP64.
+// Tables: entry (idx(l, m) - base0) * npairs + pair of each function plane
+// (plane entries apart), for the orders m0 + blockIdx.z.
 template <int NB>
 __global__ void __launch_bounds__(FF_SYN_THREADS) k_leg_syn_ff(const float *__restrict__ ptab,
                                                               const float *__restrict__ ptab_lo,
                                                               const double2 *__restrict__ alm,
                                                               double2 *__restrict__ rc, int lmax, int mmax,
                                                               int npairs, int64_t nalm, int batch,
-                                                              const SolveState *__restrict__ state) {
+                                                              const SolveState *__restrict__ state, int m0,
+                                                              int64_t base0, int64_t plane) {
   // per RHS and l: T (re, im), -E (re, im), -B (re, im), each float-float
   __shared__ ff sA[NB][FF_SYN_CH][6];
-  const int b0 = blockIdx.x * NB, m = blockIdx.z;
+  const int b0 = blockIdx.x * NB, m = m0 + blockIdx.z;
   bool any = false;
   for (int k = 0; k < NB; ++k) any = any || (b0 + k < batch && (state == nullptr || !state[b0 + k].done));
   if (!any) return;
@@ -113,8 +118,7 @@ __global__ void __launch_bounds__(FF_SYN_THREADS) k_leg_syn_ff(const float *__re
     for (int q = 0; q < 2; ++q)
 #pragma unroll
       for (int i = 0; i < 6; ++i) acc[k][q][i] = ff{0.f, 0.f};
-  const int64_t base = ff_alm_base(lmax, m);
-  const int64_t plane = nalm * (int64_t)npairs;
+  const int64_t base = ff_alm_base(lmax, m), tbase = base - base0;
   for (int lc = m; lc <= lmax; lc += FF_SYN_CH) {
     const int cnt = min(FF_SYN_CH, lmax + 1 - lc);
     __syncthreads();
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(FF_SYN_THREADS) k_leg_syn_ff(const float *__re
     __syncthreads();
     for (int j = 0; j < cnt; ++j) {
       const int l = lc + j;
-      const int64_t o = (base + l) * (int64_t)npairs + pp;
+      const int64_t o = (tbase + l) * (int64_t)npairs + pp;
       const ff lam{ptab[o], ptab_lo[o]}, lp{ptab[plane + o], ptab_lo[plane + o]},
           lq{ptab[2 * plane + o], ptab_lo[2 * plane + o]};
       if (((l - m) & 1) == 0) {
@@ -170,12 +174,13 @@ __global__ void __launch_bounds__(FF_ANA_P) k_leg_ana_ff(const float *__restrict
                                                         const float *__restrict__ ptab_lo,
                                                         const double2 *__restrict__ rc, double2 *__restrict__ apart,
                                                         int lmax, int mmax, int npairs, int64_t nalm, int nchunk,
-                                                        int batch, const SolveState *__restrict__ state) {
+                                                        int batch, const SolveState *__restrict__ state, int m0,
+                                                        int64_t base0, int64_t plane) {
   __shared__ ff P[3][FF_ANA_P][FF_ANA_L + 1];
   // per pair and RHS: (T, Q, U) x (even, odd) x (re, im)
   __shared__ ff G[FF_ANA_P][NB][12];
   __shared__ ff red[FF_ANA_PARTS][FF_ANA_L][NB][6];
-  const int b0 = blockIdx.x * NB, chunk = blockIdx.y, m = blockIdx.z;
+  const int b0 = blockIdx.x * NB, chunk = blockIdx.y, m = m0 + blockIdx.z;
   bool any = false;
   for (int k = 0; k < NB; ++k) any = any || (b0 + k < batch && (state == nullptr || !state[b0 + k].done));
   if (!any) return;
@@ -196,14 +201,13 @@ __global__ void __launch_bounds__(FF_ANA_P) k_leg_ana_ff(const float *__restrict
       G[t][k][4 * f + 3] = ff_split(gn.y - gs.y);
     }
   }
-  const int64_t base = ff_alm_base(lmax, m);
-  const int64_t plane = nalm * (int64_t)npairs;
+  const int64_t base = ff_alm_base(lmax, m), tbase = base - base0;
   const int lj = t % FF_ANA_L, part = t / FF_ANA_L;
   for (int lc = m; lc <= lmax; lc += FF_ANA_L) {
     const int cnt = min(FF_ANA_L, lmax + 1 - lc);
     __syncthreads();
     for (int j = 0; j < cnt; ++j) {
-      const int64_t o = (base + lc + j) * (int64_t)npairs + pp;
+      const int64_t o = (tbase + lc + j) * (int64_t)npairs + pp;
 #pragma unroll
       for (int fn = 0; fn < 3; ++fn)
         P[fn][t][j] = act ? ff{ptab[fn * plane + o], ptab_lo[fn * plane + o]} : ff{0.f, 0.f};
@@ -267,19 +271,81 @@ __global__ void __launch_bounds__(FF_ANA_P) k_leg_ana_ff(const float *__restrict
 
 constexpr int FF_NB = 2;
 
+// Slabs of orders whose tables (3 functions, hi and lo) take at most
+// p->ffs_cap bytes (one order at least):
+// the float-float stages of a plan without the full FP32 tables generate each
+// slab's tables (FP64 recurrence) and then contract it.
+static cudaError_t ff_slabs(dm_plan *p) {
+  if (!p->ffs_m.empty()) return cudaSuccess;
+  const size_t cap = (size_t)p->ffs_cap, per_entry = 3 * 2 * sizeof(float) * (size_t)p->npairs;
+  std::vector<int> mb{0};
+  size_t cur = 0, most = 0;
+  for (int m = 0; m <= p->mmax; ++m) {
+    const size_t e = (size_t)(p->lmax - m + 1) * per_entry;
+    if (cur > 0 && cur + e > cap) {
+      mb.push_back(m);
+      most = std::max(most, cur);
+      cur = 0;
+    }
+    cur += e;
+  }
+  mb.push_back(p->mmax + 1);
+  most = std::max(most, cur);
+  const size_t n = most / (2 * sizeof(float));
+  cudaError_t e = cudaMalloc(&p->ffs, sizeof(float) * n);
+  if (!e) e = cudaMalloc(&p->ffs_lo, sizeof(float) * n);
+  if (e) {
+    cudaFree(p->ffs);
+    cudaFree(p->ffs_lo);
+    p->ffs = p->ffs_lo = nullptr;
+    return e;
+  }
+  p->bytes += (int64_t)(2 * sizeof(float) * n);
+  p->ffs_m = mb;
+  return cudaSuccess;
+}
+
 cudaError_t legendre_synthesis_ff(dm_plan *p, const double2 *alm, cudaStream_t st) {
-  dim3 g((p->batch + FF_NB - 1) / FF_NB, (p->npairs + FF_SYN_THREADS - 1) / FF_SYN_THREADS, p->mmax + 1);
-  k_leg_syn_ff<FF_NB><<<g, FF_SYN_THREADS, 0, st>>>(p->ptab, p->ptab_lo, alm, p->rc, p->lmax, p->mmax, p->npairs,
-                                                    p->nalm, p->batch, p->state_active ? p->state : nullptr);
+  const SolveState *stp = p->state_active ? p->state : nullptr;
+  if (p->ptab) {
+    dim3 g((p->batch + FF_NB - 1) / FF_NB, (p->npairs + FF_SYN_THREADS - 1) / FF_SYN_THREADS, p->mmax + 1);
+    k_leg_syn_ff<FF_NB><<<g, FF_SYN_THREADS, 0, st>>>(p->ptab, p->ptab_lo, alm, p->rc, p->lmax, p->mmax, p->npairs,
+                                                      p->nalm, p->batch, stp, 0, 0, p->nalm * (int64_t)p->npairs);
+    return cudaGetLastError();
+  }
+  if (cudaError_t e = ff_slabs(p)) return e;
+  for (size_t k = 0; k + 1 < p->ffs_m.size(); ++k) {
+    const int m0 = p->ffs_m[k], m1 = p->ffs_m[k + 1];
+    if (cudaError_t e = gen_tables32_slab(p, p->ffs, p->ffs_lo, m0, m1, st)) return e;
+    const int64_t b0 = alm_start_h(p->lmax, m0), b1 = alm_start_h(p->lmax, m1);
+    dim3 g((p->batch + FF_NB - 1) / FF_NB, (p->npairs + FF_SYN_THREADS - 1) / FF_SYN_THREADS, m1 - m0);
+    k_leg_syn_ff<FF_NB><<<g, FF_SYN_THREADS, 0, st>>>(p->ffs, p->ffs_lo, alm, p->rc, p->lmax, p->mmax, p->npairs,
+                                                      p->nalm, p->batch, stp, m0, b0,
+                                                      (b1 - b0) * (int64_t)p->npairs);
+  }
   return cudaGetLastError();
 }
 
 // partial sums per chunk of 64 ring pairs into p->apart (the FP64 reduction follows)
 cudaError_t legendre_analysis_ff_parts(dm_plan *p, cudaStream_t st) {
-  dim3 g((p->batch + FF_NB - 1) / FF_NB, p->nchunk, p->mmax + 1);
-  k_leg_ana_ff<FF_NB><<<g, FF_ANA_P, 0, st>>>(p->ptab, p->ptab_lo, p->rc, p->apart, p->lmax, p->mmax, p->npairs,
-                                              p->nalm, p->nchunk, p->batch,
-                                              p->state_active ? p->state : nullptr);
+  const SolveState *stp = p->state_active ? p->state : nullptr;
+  if (p->ptab) {
+    dim3 g((p->batch + FF_NB - 1) / FF_NB, p->nchunk, p->mmax + 1);
+    k_leg_ana_ff<FF_NB><<<g, FF_ANA_P, 0, st>>>(p->ptab, p->ptab_lo, p->rc, p->apart, p->lmax, p->mmax, p->npairs,
+                                                p->nalm, p->nchunk, p->batch, stp, 0, 0,
+                                                p->nalm * (int64_t)p->npairs);
+    return cudaGetLastError();
+  }
+  if (cudaError_t e = ff_slabs(p)) return e;
+  for (size_t k = 0; k + 1 < p->ffs_m.size(); ++k) {
+    const int m0 = p->ffs_m[k], m1 = p->ffs_m[k + 1];
+    if (cudaError_t e = gen_tables32_slab(p, p->ffs, p->ffs_lo, m0, m1, st)) return e;
+    const int64_t b0 = alm_start_h(p->lmax, m0), b1 = alm_start_h(p->lmax, m1);
+    dim3 g((p->batch + FF_NB - 1) / FF_NB, p->nchunk, m1 - m0);
+    k_leg_ana_ff<FF_NB><<<g, FF_ANA_P, 0, st>>>(p->ffs, p->ffs_lo, p->rc, p->apart, p->lmax, p->mmax, p->npairs,
+                                                p->nalm, p->nchunk, p->batch, stp, m0, b0,
+                                                (b1 - b0) * (int64_t)p->npairs);
+  }
   return cudaGetLastError();
 }
 

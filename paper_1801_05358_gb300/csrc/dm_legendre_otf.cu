@@ -771,6 +771,21 @@ cudaError_t gen_setup(dm_plan *p) {
   return cudaSuccess;
 }
 
+// Stored tiles when they and the FP32 tables they are cut from take at most
+// 40 GiB (nside 512 / lmax 1024: 26 GB); generated tiles beyond, where the
+// tables would crowd out the batch (nside 1024 / lmax 2048: about 210 GB).
+bool tc_tables_fit(int lmax, int mmax, int npairs, int B) {
+  const int64_t nalm = (int64_t)(mmax + 1) * (2 * lmax + 2 - mmax) / 2;
+  const double bytes = (double)tc_table_bytes(lmax, mmax, npairs, B) + 24.0 * (double)nalm * npairs;
+  return bytes <= 40.0 * (1u << 30);
+}
+
+bool tc_generate(dm_plan *p) {
+  if (p->tc_gen >= 0) return p->tc_gen != 0;
+  if (p->tc_gen_used < 0) p->tc_gen_used = tc_tables_fit(p->lmax, p->mmax, p->npairs, p->batch) ? 0 : 1;
+  return p->tc_gen_used != 0;
+}
+
 size_t gen_bytes(int lmax, int mmax, int npairs) {
   int64_t nck = 0;
   for (int m = 0; m <= mmax; ++m) nck += (lmax - m + 1 + CKL - 1) / CKL;

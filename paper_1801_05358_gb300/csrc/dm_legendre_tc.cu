@@ -529,6 +529,7 @@ static cudaError_t tc_scratch(dm_plan *p) {
 static cudaError_t tc_tables(dm_plan *p) {
   if (p->tc_synA[1] && p->tc_anaA[1]) return cudaSuccess;
   cudaError_t e = tc_scratch(p);
+  if (!e) e = ensure_ptab(p);  // the tiles are cut from the FP32 tables
   if (e) return e;
   const int npt = (p->npairs + 127) / 128, nps = (p->npairs + 15) / 16;
   int64_t ssteps = 0, atiles = 0;
@@ -580,7 +581,7 @@ static int syn_stages_pick(int want, int stage_bytes, uint32_t ncols) {
 }
 
 cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t st) {
-  cudaError_t e = p->tc_gen ? tc_scratch(p) : tc_tables(p);
+  cudaError_t e = tc_generate(p) ? tc_scratch(p) : tc_tables(p);
   if (e) return e;
   const int B = p->batch;
   const double2 *ahi = p->anchor_active ? p->a_hi : nullptr;
@@ -590,7 +591,7 @@ cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t s
   const bool run0 = p->tune_only_part != 1, run1 = p->tune_only_part != 0;
   if (run0) k_syn_b<0><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[0], p->tc_soff, alm, ahi, e32, p->lmax, p->nalm, B);
   if (run1) k_syn_b<1><<<gb, TC_THREADS, 0, st>>>(p->tc_synB[1], p->tc_soff, alm, ahi, e32, p->lmax, p->nalm, B);
-  if (p->tc_gen) return syn_gen_launch(p, run0, run1, st);
+  if (tc_generate(p)) return syn_gen_launch(p, run0, run1, st);
   dim3 g(npt, p->mmax + 1);
   if (run0) {
     const int stage = 2 * 2 * TILE_A + 2 * 2 * (2 * B * 32);
@@ -642,7 +643,7 @@ static int ana_S_pick(int want, int stage_bytes) {
 }
 
 cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st) {
-  if (p->tc_gen) return ana_gen_launch(p, st);
+  if (tc_generate(p)) return ana_gen_launch(p, st);
   cudaError_t e = tc_tables(p);
   if (e) return e;
   const int B = p->batch;

@@ -111,7 +111,7 @@ dm_plan make_view(const dm_plan *p, int b) {
   v.sigma += b * n3;
   v.mask += (size_t)b * p->npix;
   v.filt += (size_t)b * p->filt_levels * 4 * (p->lmax + 1);
-  if (p->ptab) {
+  if (p->fp32_ready) {
     v.rc32 += b * nrc;
     v.apart32 += (size_t)b * p->nchunk * na;
     v.s32 += b * n3;
@@ -151,16 +151,23 @@ size_t estimate_bytes(int nside, int lmax, int S, dm_precision prec) {
   b += S * 3 * nalm * 16 * 2;                    // a, tmpalm
   b += S * 3 * npix * 8 * 7;                     // wd, tmpmap(2), s64, rhi, w, sigma
   b += nalm * 48 + (lmax + 1.0) * npairs * 28;   // coefficients, seeds
+  const bool tc = prec == DM_MIXED_FP32 && dmwf::tc_batch_ok(S);
+  const bool stored = tc && dmwf::tc_tables_fit(lmax, lmax, (int)npairs, S);
   if (prec != DM_FP64) {                         // DM_MIXED_FP32 and DM_FLOAT_FLOAT
-    b += 3 * nalm * npairs * 4 * 2;              // FP32 tables, hi and lo
+    if (stored || (prec == DM_MIXED_FP32 && !tc))
+      b += 3 * nalm * npairs * 4 * 2;            // FP32 tables, hi and lo
+    else
+      b += (double)(1u << 30);                   // per-slab tables of the float-float stages
     b += S * 3 * (lmax + 1.0) * npairs * 2 * 8;  // rc32
     b += S * nchunk * 3 * nalm * 8;              // apart32
     b += S * 3 * npix * 4 * 4;                   // s32, w32, wd32, shi32
     b += S * 3 * nalm * 16 * 2;                  // a_hi, g_hi
     b += S * 3 * nalm * 8 * 2;                   // e32, c32
   }
-  if (prec == DM_MIXED_FP32 && dmwf::tc_batch_ok(S))
+  if (stored)
     b += (double)dmwf::tc_table_bytes(lmax, lmax, (int)npairs, S);  // tiled BF16 tables
+  else if (tc)
+    b += (double)dmwf::gen_bytes(lmax, lmax, (int)npairs) + S * (lmax + 1.0) * (lmax + 2.0) * 12 * 32;  // checkpoints, B scratch
   return (size_t)(b * 1.05) + (64u << 20);
 }
 

@@ -583,16 +583,17 @@ __global__ void k_d2f2(const double2 *in, float2 *out, int64_t n) {
 
 cudaError_t gen_tables32(dm_plan *p);  // dm_legendre.cu
 
-// Tables and buffers of DM_MIXED_FP32: FP32 copies of the FFT tables, the FP32
-// Legendre tables (FP64 recurrence), FP32 ring coefficients and maps.
+// Buffers of DM_MIXED_FP32 and DM_FLOAT_FLOAT: FP32 copies of the FFT tables,
+// FP32 ring coefficients and maps.  The FP32 Legendre tables are not made
+// here: the kernels that read them build them on first use (ensure_ptab).
 cudaError_t setup_fp32(dm_plan *p) {
-  if (p->ptab) return cudaSuccess;  // set only after everything below succeeded
+  if (p->fp32_ready) return cudaSuccess;  // set only after everything below succeeded
   cudaError_t e;
   // all or nothing: on any error every buffer allocated here is freed again,
   // so that a later call starts over instead of finding a half-built state
   void **owned[] = {(void **)&p->phase32, (void **)&p->bhat32, (void **)&p->bhatT32[0], (void **)&p->bhatT32[1],
                     (void **)&p->chirp32, (void **)&p->twid32,
-                    (void **)&p->twr32,   (void **)&p->ptab,   (void **)&p->ptab_lo, (void **)&p->rc32,
+                    (void **)&p->twr32,   (void **)&p->rc32,
                     (void **)&p->apart32, (void **)&p->s32,    (void **)&p->w32,     (void **)&p->wd32,
                     (void **)&p->a_hi,    (void **)&p->g_hi,   (void **)&p->shi32,   (void **)&p->e32,
                     (void **)&p->c32,     (void **)&p->clev,   (void **)&p->tc_err};
@@ -621,8 +622,6 @@ cudaError_t setup_fp32(dm_plan *p) {
   if ((e = al(&p->chirp32, p->ch_total))) return undo(e);
   if ((e = al(&p->twid32, p->fft_M_max - 1))) return undo(e);
   if ((e = al(&p->twr32, p->twr_words))) return undo(e);
-  if ((e = al(&p->ptab, (size_t)3 * p->nalm * p->npairs))) return undo(e);
-  if ((e = al(&p->ptab_lo, (size_t)3 * p->nalm * p->npairs))) return undo(e);
   if ((e = al(&p->rc32, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return undo(e);
   if ((e = al(&p->apart32, (size_t)B * p->nchunk * 3 * p->nalm))) return undo(e);
   if ((e = al(&p->s32, (size_t)B * n3))) return undo(e);
@@ -644,8 +643,28 @@ cudaError_t setup_fp32(dm_plan *p) {
   if (p->ch_total > 0) k_d2f2<<<512, 256>>>(p->chirp, p->chirp32, p->ch_total);
   k_d2f2<<<64, 256>>>(p->twid, p->twid32, p->fft_M_max - 1);
   if (p->twr_words > 0) k_d2f2<<<64, 256>>>(p->twr, p->twr32, p->twr_words);
-  if ((e = gen_tables32(p))) return undo(e);
   if ((e = cudaDeviceSynchronize())) return undo(e);
+  p->fp32_ready = true;
+  return cudaSuccess;
+}
+
+// The full FP32 Legendre tables (3 x nalm x npairs, hi and lo), made once.
+cudaError_t ensure_ptab(dm_plan *p) {
+  if (p->ptab) return cudaSuccess;
+  const size_t n = (size_t)3 * p->nalm * p->npairs;
+  float *hi = nullptr, *lo = nullptr;
+  cudaError_t e = cudaMalloc(&hi, sizeof(float) * n);
+  if (!e) e = cudaMalloc(&lo, sizeof(float) * n);
+  if (!e) e = gen_tables32_slab(p, hi, lo, 0, p->mmax + 1, 0);
+  if (!e) e = cudaDeviceSynchronize();
+  if (e) {
+    cudaFree(hi);
+    cudaFree(lo);
+    return e;
+  }
+  p->ptab = hi;
+  p->ptab_lo = lo;
+  p->bytes += (int64_t)(2 * sizeof(float) * n);
   return cudaSuccess;
 }
 

@@ -113,3 +113,42 @@ def test_anchor_precision_rejects_mixed():
     p = dmwf.Plan(4, 8, 1)
     with pytest.raises(RuntimeError):
         p.set_anchor_precision(dmwf.DM_MIXED_FP32)
+
+
+# Without full FP32 tables (DM_FLOAT_FLOAT never builds them) the float-float
+# stages generate their tables per slab of orders m and contract each slab
+# before the next; slabs of a few kilobytes force many slabs of uneven length.
+@pytest.mark.parametrize("slab", [1, 40_000, 300_000])
+def test_ff_slabs_match_oracle(orc, slab):
+    nside, lmax, B = 16, 47, 3
+    alm = W.random_alm(lmax, B, 61)
+    maps = W.random_maps(nside, B, 62)
+    p = dmwf.Plan(nside, lmax, B)
+    p.set_precision(dmwf.DM_FLOAT_FLOAT)
+    p.set_ff_slab_bytes(slab)
+    m_out = torch.zeros((B, 3, 12 * nside * nside), dtype=torch.float64, device="cuda")
+    a_out = torch.zeros((B, 3, (lmax + 1) * (lmax + 2) // 2, 2), dtype=torch.float64, device="cuda")
+    p.alm2map(alm_dev(alm), m_out)
+    p.map2alm(dev(maps), a_out)
+    gm = m_out.cpu().numpy()
+    ga = a_out.cpu().numpy().view(np.complex128)[..., 0]
+    p.close()
+    for b in range(B):
+        assert rel(gm[b], orc.alm2map(nside, lmax, alm[b])) < 1e-12
+        assert rel(ga[b], orc.map2alm(nside, lmax, maps[b])) < 1e-12
+
+
+def test_ff_slab_solve_matches_oracle(orc):
+    wl = W.make_workload("nside16", [4, 5])
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(1000.0, 4)
+    p = make_plan(wl, 2, lambda0=1000.0, n_levels=4, iters_per_level=5)
+    p.set_precision(dmwf.DM_FLOAT_FLOAT)
+    p.set_ff_slab_bytes(100_000)
+    s = torch.zeros((2, 3, wl.npix), dtype=torch.float64, device="cuda")
+    p.wiener_filter(dev(d), s)
+    got = s.cpu().numpy()
+    p.close()
+    for b in range(2):
+        ref = orc.dm_solve(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.mask, d[b], lam, forced_iters=[5] * 4)
+        assert rel(got[b], ref["s"]) < 1e-10

@@ -167,3 +167,24 @@ def test_tc_generated_tiles(orc, nside, lmax, B):
     for b in (0, B - 1):
         assert rel(gm[b], orc.alm2map(nside, lmax, alm[b])) < 2e-5
         assert rel(ga[b], orc.map2alm(nside, lmax, maps[b])) < 2e-5
+
+
+def test_tc_generated_tiles_solve(orc):
+    """The mixed solve with generated tiles and slab-generated float-float
+    anchors (no full tables at all), at the oracle's forced counts."""
+    wl = W.make_workload("nside16", list(range(8)))
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(1000.0, 10)
+    p = make_plan(wl, 8, lambda0=1000.0, n_levels=10, iters_per_level=10, check_every=16)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    p.set_tc_tiles(True)
+    p.set_ff_slab_bytes(200_000)
+    p.set_anchor_precision(dmwf.DM_FLOAT_FLOAT)
+    p.set_refinement(16)
+    s = torch.zeros((8, 3, wl.npix), dtype=torch.float64, device="cuda")
+    p.wiener_filter(dev(d), s)
+    got = s.cpu().numpy()
+    p.close()
+    for b in [0, 5]:
+        ref = orc.dm_solve(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.mask, d[b], lam, forced_iters=[10] * 10)
+        assert rel(got[b], ref["s"]) < 1e-5
