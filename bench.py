@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ring-radix", type=int, default=None, choices=[0, 3, 4],
                     help="ring transforms of radix 2^k (3 or 4), 0 = generic kernels (default: autotuned)")
+    ap.add_argument("--tc-tiles", default="auto", choices=["auto", "stored", "generated"],
+                    help="tensor-core Legendre operand: stored tiles, generated in the kernels, or by size")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch heuristics instead of dm_autotune's picks")
     ap.add_argument("--tuning", default=None,
@@ -315,6 +317,7 @@ def run_solves(args):
     lmax = args.lmax or 2 * nside
     plan, wl, d = bench_inputs(dmwf, torch, dev, nside, lmax, B)
     prec = dmwf.DM_MIXED_FP32 if args.precision == "mixed" else dmwf.DM_FP64
+    plan.set_tc_tiles({"auto": None, "stored": False, "generated": True}[args.tc_tiles])
     plan.set_precision(prec)
     if args.progressive > 0:
         plan.set_progressive(args.progressive, 8)
@@ -603,6 +606,7 @@ def main():
         fms = f0.elapsed_time(f1)
         ff_line = {"value": B * nf / (fms * 1e-3), "unit": "DM iterations/s", "steps": nf,
                    "ms_per_step": fms / nf, "precision": "DM_FLOAT_FLOAT"}
+    plan.set_tc_tiles({"auto": None, "stored": False, "generated": True}[args.tc_tiles])
     plan.set_precision(prec)
     tuning = None
     if args.tuning:
@@ -789,6 +793,7 @@ def main():
                            "ring_radix": ("autotuned" if tuning else "plan default") if args.ring_radix is None
                            else args.ring_radix,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                           "tc_tiles": args.tc_tiles,
                            "l2": "inputs larger than L2 (maps and ring coefficients exceed 129 MB)"},
                 "ms_per_step_median": float(np.median(chunk_ms)),
                 "timing": {"chunks": nch, "chunk_ms_per_step": chunk_ms,

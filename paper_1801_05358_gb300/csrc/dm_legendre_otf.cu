@@ -492,9 +492,7 @@ constexpr int SGEN_MAX_NS = 8;
 template <int PART, bool DF>
 __device__ __forceinline__ void syn_step(unsigned char *Ae, unsigned char *Ao, int r, int lb, int lmax, int ls,
                                          bool act, float &a0, float &a1, float &b0, float &b1, int &S, float &sc,
-                                         const Xs &xs, const float4 *__restrict__ rq0,
-                                         const float4 *__restrict__ rq2, const float2 *__restrict__ rq2d,
-                                         int64_t base) {
+                                         const Xs &xs, float4 cA, float2 cD) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     float ve[8], vo[8], we[8], wo[8];  // spin 0: lambda; spin 2: v = lam+, w = lam-
@@ -516,19 +514,22 @@ __device__ __forceinline__ void syn_step(unsigned char *Ae, unsigned char *Ao, i
         ve[t >> 1] = v;
         we[t >> 1] = w;
       }
+      // the coefficients of target l + 1, held by lane 16 h + t of the warp
+      const int src = 16 * h + t;
+      const float c0 = __shfl_sync(0xffffffffu, cA.x, src), c1 = __shfl_sync(0xffffffffu, cA.y, src);
+      const float c2 = __shfl_sync(0xffffffffu, cA.z, src);
+      float dp = 0.f, dq = 0.f;
+      if (PART == 0 && DF) dp = c2;
+      if (PART == 1 && DF) {
+        dp = __shfl_sync(0xffffffffu, cD.x, src);
+        dq = __shfl_sync(0xffffffffu, cD.y, src);
+      }
       if (l < lmax && l >= ls) {
         if (PART == 0) {
-          const float4 cf = rq0[base + l + 1];
-          step<DF>(a0, a1, cf.x, 0.f, cf.y, cf.z, xs);
+          step<DF>(a0, a1, c0, 0.f, c1, dp, xs);
           if (S > 0 && fabsf(a0) > 0x1p32f) rescale(a0, a1, b0, b1, S, sc);
         } else {
-          const float4 cf = rq2[base + l + 1];
-          float dp = 0.f, dq = 0.f;
-          if (DF) {
-            const float2 dd = rq2d[base + l + 1];
-            dp = dd.x;
-            dq = dd.y;
-          }
+          const float4 cf = make_float4(c0, c1, c2, 0.f);
           step<DF>(a0, a1, cf.x, cf.y, cf.z, dp, xs);
           step<DF>(b0, b1, cf.x, -cf.y, cf.z, dq, xs);
           if (S > 0 && fabsf(a0) + fabsf(b0) > 0x1p32f) rescale(a0, a1, b0, b1, S, sc);
@@ -600,7 +601,23 @@ __global__ void __launch_bounds__(160, 1) k_syn_gen(
     const int ls = (PART == 1 && m < 2) ? 2 : 0;  // spin 2 starts at l = 2
     float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, sc = 1.f;
     int S = 0;
+    // lane t holds the coefficients of target l = m + 32 c + t + 1 for the
+    // current K step c (cA, cD) and the next one (nA, nD), loaded a step ahead;
+    // the checkpoint of the next block is loaded a block ahead (k0, k2)
+    auto coef = [&](int c, float4 &ca, float2 &cd) {
+      const int l1 = m + 32 * c + lane + 1;
+      ca = make_float4(0.f, 0.f, 0.f, 0.f);
+      cd = make_float2(0.f, 0.f);
+      if (l1 <= lmax) {
+        ca = PART == 0 ? rq0[base + l1] : rq2[base + l1];
+        if (PART == 1) cd = rq2d[base + l1];
+      }
+    };
+    float4 cA, nA, k0 = ck0[ckb], k2 = PART == 1 ? ck2[ckb] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 cD, nD;
+    coef(0, cA, cD);
     for (int c = 0; c < nsteps; ++c) {
+      if (c + 1 < nsteps) coef(c + 1, nA, nD);
       bool ok = true;
       for (int h = 0; h < UPS; ++h) {
         const int u = c * UPS + h;
@@ -608,28 +625,32 @@ __global__ void __launch_bounds__(160, 1) k_syn_gen(
       }
       if (!ok) break;
       if ((c & 1) == 0) {  // restart at the checkpoint of block c / 2
-        const int64_t o = ckb + (int64_t)(c >> 1) * npairs;
-        const float4 q0 = ck0[o];
         if (PART == 0) {
-          a0 = q0.x;
-          a1 = q0.y;
-          S = __float_as_int(q0.z);
+          a0 = k0.x;
+          a1 = k0.y;
+          S = __float_as_int(k0.z);
         } else {
-          const float4 q2 = ck2[o];
-          a0 = q2.x;
-          a1 = q2.y;
-          b0 = q2.z;
-          b1 = q2.w;
-          S = __float_as_int(q0.w);
+          a0 = k2.x;
+          a1 = k2.y;
+          b0 = k2.z;
+          b1 = k2.w;
+          S = __float_as_int(k0.w);
         }
         sc = scale_of(S);
+        if (c + 2 < nsteps) {
+          const int64_t o = ckb + (int64_t)((c >> 1) + 1) * npairs;
+          k0 = ck0[o];
+          if (PART == 1) k2 = ck2[o];
+        }
       }
       unsigned char *Ae = sm + ((c * UPS) % NS) * stage;
       unsigned char *Ao = PART == 0 ? Ae : sm + ((c * UPS + 1) % NS) * stage;
       if (df)
-        syn_step<PART, true>(Ae, Ao, r, m + 32 * c, lmax, ls, act, a0, a1, b0, b1, S, sc, xs, rq0, rq2, rq2d, base);
+        syn_step<PART, true>(Ae, Ao, r, m + 32 * c, lmax, ls, act, a0, a1, b0, b1, S, sc, xs, cA, cD);
       else
-        syn_step<PART, false>(Ae, Ao, r, m + 32 * c, lmax, ls, act, a0, a1, b0, b1, S, sc, xs, rq0, rq2, rq2d, base);
+        syn_step<PART, false>(Ae, Ao, r, m + 32 * c, lmax, ls, act, a0, a1, b0, b1, S, sc, xs, cA, cD);
+      cA = nA;
+      cD = nD;
       fence_proxy_async();
       for (int h = 0; h < UPS; ++h) mbar_arrive(&full_a[(c * UPS + h) % NS]);
     }

@@ -75,20 +75,24 @@ constexpr uint64_t MBAR_TIMEOUT_NS = 1000000000ull;
 
 // Bounded wait on an mbarrier phase. It gives up after MBAR_TIMEOUT_NS of wall
 // time (%globaltimer, read every 16 tries), or after 1 ms once *err shows that
-// another wait has already given up, so that a failure ends every CTA quickly;
-// 2^30 tries bound it should the timer not advance. Returns false (and sets
-// *err, when given) when it gives up.
+// another wait has already given up, so that a failure ends every CTA quickly.
+// Each try suspends the thread until the phase completes or MBAR_SUSPEND_NS
+// pass (the try_wait time hint), so that a waiting warp does not take issue
+// slots from the warps it waits for.  2^22 tries bound it should the timer not
+// advance (at least tens of milliseconds, at most about 17 s).  Returns false
+// (and sets *err, when given) when it gives up.
+constexpr uint32_t MBAR_SUSPEND_NS = 4000;
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t phase, int *err) {
   const uint32_t a = smem_u32(mbar);
   uint64_t t0 = 0;
-  for (uint32_t it = 0; it < (1u << 30); ++it) {
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(a), "r"(phase)
+        : "r"(a), "r"(phase), "r"(MBAR_SUSPEND_NS)
         : "memory");
     if (ok) return true;
     if ((it & 15u) == 15u) {
