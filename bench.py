@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="iterations of the plain FP64 GPU path timed beside (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-solve", action="store_true",
+                    help="skip the whole-solve leg of the default run (WF solves/s to --solve-leg-tol)")
+    ap.add_argument("--solve-leg-tol", type=float, default=1e-5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ring-radix", type=int, default=None, choices=[0, 3, 4],
                     help="ring transforms of radix 2^k (3 or 4), 0 = generic kernels (default: autotuned)")
@@ -772,6 +775,44 @@ def main():
                "note": f"one dm_wiener_filter_host call of {K} iterations (a whole solve: begin, {K} "
                        f"iterations, end); d in and s out once per call; end-of-solve diagnostics off"}
 
+    # ---- whole solves of the same batch (the metric's WF solves/s) ----
+    solves = None
+    if not args.no_solve and prec == dmwf.DM_MIXED_FP32:
+        tol = args.solve_leg_tol
+        plan.set_forced_iters(None)
+        plan.set_schedule(lambda0=1000.0, n_levels=10, iters_per_level=0, eps0=1e-4, eps_final=tol, eta=0.0,
+                          max_iter=100000, check_every=64)
+        plan.set_progressive(0.25, 8)
+        s_sol = torch.zeros_like(d)
+        torch.cuda.synchronize()
+        with ClockSampler(0) as sclk:
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            _, sstats = plan.wiener_filter(d, s_sol)
+            g1.record(stream)
+            torch.cuda.synchronize()
+        sms = g0.elapsed_time(g1)
+        slev = plan.progressive_levels(10)
+        plan.set_progressive(0.0, 8)
+        its = np.array([x["iters_total"] for x in sstats])
+        solves = {"value": B / (sms * 1e-3), "unit": "WF solves/s", "seconds": sms * 1e-3,
+                  "rhs": B, "tol": tol, "converged_rhs": int(sum(1 for x in sstats if x["iters_total"] < 100000)),
+                  "iterations_per_rhs": {"mean": float(its.mean()), "min": int(its.min()), "max": int(its.max())},
+                  "true_resid": {"mean": float(np.mean([x["true_resid"] for x in sstats])),
+                                 "max": float(np.max([x["true_resid"] for x in sstats]))},
+                  "schedule": f"lambda 1000 -> 1 in 10 levels, Cauchy 1e-4 -> {tol:g}, progressive working "
+                              f"resolution (margin 0.25): {slev}",
+                  "fp64_gpu_derived": None, "clocks": sclk.summary(),
+                  "note": "one dm_wiener_filter call on the bench's batch (every RHS is a Wiener-filter solve; "
+                          "the constrained realisations' fluctuation RHS included)"}
+        if fp64_line is not None and (nside, lmax, B, tol) == (512, 1024, 64, 1e-5):
+            # plain FP64: its measured iterations/s over the full-resolution iteration count of the same
+            # schedule (FP64 solves take the oracle's counts; measured at nside 512 / 1e-5: 7378 per RHS)
+            solves["fp64_gpu_derived"] = {"value": fp64_line["value"] / 7378.0, "unit": "WF solves/s",
+                                          "iterations_per_rhs": 7378,
+                                          "note": "derived: plain FP64 DM iterations/s / 7378, the mean count of "
+                                                  "the full-resolution mixed solve of this batch to 1e-5"}
+
     # ---- CPU baseline (oracle), rank 0 at N = 1 only ----
     cpu, err = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -800,7 +841,8 @@ def main():
                            "median_ms_per_step": float(np.median(chunk_ms))},
                 "error_vs_oracle": err,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["launches"],
-                "fp64_gpu": fp64_line, "ff64_gpu": ff_line, "refinement": anchor, "autotune": tuning,
+                "fp64_gpu": fp64_line, "ff64_gpu": ff_line, "solves": solves, "refinement": anchor,
+                "autotune": tuning,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     plan.close()

@@ -211,14 +211,6 @@ __device__ __forceinline__ uint64_t smem_desc_sbo(uint32_t saddr, uint32_t sbo) 
   return d;
 }
 
-__device__ __forceinline__ void put_row_a(unsigned char *tile, int row, int ko, const float x[8]) {
-  uint4 h, l;
-  split8(x, h, l);
-  const uint32_t o = (uint32_t)((row >> 3) * ASBO + ko * 128 + (row & 7) * 16);
-  *reinterpret_cast<uint4 *>(tile + o) = h;
-  *reinterpret_cast<uint4 *>(tile + ATILE + o) = l;
-}
-
 __device__ __forceinline__ void mma3_a(uint32_t d, const unsigned char *a, const unsigned char *b, int tile_b,
                                        uint32_t idesc, uint32_t acc) {
   const uint64_t ah = smem_desc_sbo(smem_u32(a), ASBO), al = smem_desc_sbo(smem_u32(a + ATILE), ASBO);
@@ -259,46 +251,118 @@ __device__ __forceinline__ void convert_b_pq(int b, int ko, unsigned char *B1, u
   }
 }
 
-// The 32 rows of this parity in one checkpoint block, for 8 consecutive ring
-// pairs (one lane of a worker warp); f selects the spin-2 function (p or q).
-template <int PART, bool DF>
-__device__ __forceinline__ void ana_block(unsigned char *At, int q, int g, int par, int ls, int l0, int lmax, int f,
-                                          const bool act[8], float v0[8], float v1[8], const Xs xs[8], float sc[8],
-                                          int Sk[8], int anyS, const float4 *__restrict__ rq0,
-                                          const float4 *__restrict__ rq2, const float2 *__restrict__ rq2d,
-                                          int64_t base) {
-  for (int t = 0; t < CKL; ++t) {
-    const int l = l0 + t;
-    if ((t & 1) == par) {
-      float x[8];
+// BF16 hi / lo of N consecutive values (N = 1, 2, 4, 8 ring pairs of one
+// core-matrix row), stored at byte offset o of the hi tile and of the lo tile.
+template <int N>
+__device__ __forceinline__ void put_vals(unsigned char *tile, uint32_t o, const float *x) {
+  if (N == 1) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x[0]);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x[0] - __bfloat162float(h));
+    *reinterpret_cast<__nv_bfloat16 *>(tile + o) = h;
+    *reinterpret_cast<__nv_bfloat16 *>(tile + ATILE + o) = l;
+  } else {
+    constexpr int H = N > 1 ? N / 2 : 1;
+    uint32_t h[H], l[H];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) x[i] = (act[i] && l <= lmax && l >= ls) ? v0[i] * sc[i] : 0.f;
-      put_row_a(At, 32 * q + (t >> 1), g, x);
+    for (int i = 0; i < N / 2; ++i) {
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+      const float2 hf = __bfloat1622float2(h2);
+      const __nv_bfloat162 l2 = __floats2bfloat162_rn(x[2 * i] - hf.x, x[2 * i + 1] - hf.y);
+      h[i] = *reinterpret_cast<const uint32_t *>(&h2);
+      l[i] = *reinterpret_cast<const uint32_t *>(&l2);
     }
-    if (l < lmax && l >= ls) {
-      float c, k, b, d = 0.f;
-      if (PART == 0) {
-        const float4 cf = rq0[base + l + 1];
-        c = cf.x;
-        k = 0.f;
-        b = cf.y;
-        d = cf.z;
-      } else {
-        const float4 cf = rq2[base + l + 1];
-        c = cf.x;
-        k = f ? -cf.y : cf.y;
-        b = cf.z;
-        if (DF) {
-          const float2 dd = rq2d[base + l + 1];
-          d = f ? dd.y : dd.x;
-        }
-      }
+    if (N == 2) {
+      *reinterpret_cast<uint32_t *>(tile + o) = h[0];
+      *reinterpret_cast<uint32_t *>(tile + ATILE + o) = l[0];
+    } else if (N == 4) {
+      *reinterpret_cast<uint2 *>(tile + o) = make_uint2(h[0], h[1]);
+      *reinterpret_cast<uint2 *>(tile + ATILE + o) = make_uint2(l[0], l[1]);
+    } else {
+      *reinterpret_cast<uint4 *>(tile + o) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4 *>(tile + ATILE + o) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t arow(int row) { return (uint32_t)((row >> 3) * ASBO + (row & 7) * 16); }
+
+// One lane's share of a K step's A operand: the rows of parity PAR of
+// checkpoint block J (l0 = its first multipole, tile rows 32 q ..) for the
+// PPL ring pairs p0 .. p0 + PPL - 1, at byte offset obase of each row; f
+// selects the spin-2 function (p or q).  Rows past lmax are left as they
+// are: they only reach accumulator rows that the epilogue drops.  The
+// coefficients of the next step are loaded one step ahead.
+template <int PART, bool DF, int PAR, int PPL>
+__device__ __forceinline__ void ana_task(unsigned char *At, int q, uint32_t obase, int l0, int lmax, int ls, int f,
+                                         const float4 *__restrict__ ck0, const float4 *__restrict__ ck2,
+                                         int64_t orow, const PairDev *__restrict__ pairs, int p0, int npairs,
+                                         const float4 *__restrict__ rq0, const float4 *__restrict__ rq2,
+                                         const float2 *__restrict__ rq2d, int64_t base) {
+  float v0[PPL], v1[PPL], sc[PPL];
+  Xs xs[PPL];
+  int Sk[PPL];
+  int anyS = 0;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) step<DF>(v0[i], v1[i], c, k, b, d, xs[i]);
+  for (int i = 0; i < PPL; ++i) {
+    const int pp = min(p0 + i, npairs - 1);
+    xs[i] = xs_of(pairs, pp);
+    const float4 r0 = ck0[orow + pp];
+    if (PART == 0) {
+      v0[i] = r0.x;
+      v1[i] = r0.y;
+      Sk[i] = __float_as_int(r0.z);
+    } else {
+      const float4 r2 = ck2[orow + pp];
+      v0[i] = f == 0 ? r2.x : r2.z;
+      v1[i] = f == 0 ? r2.y : r2.w;
+      Sk[i] = __float_as_int(r0.w);
+    }
+    sc[i] = scale_of(Sk[i]);
+    anyS |= Sk[i];
+  }
+  const int nv = min(CKL, lmax - l0 + 1);  // multipoles of the block up to lmax
+  const int t0 = max(0, ls - l0);          // spin 2 starts at l = 2
+  for (int t = PAR; t < t0 && t < nv; t += 2) {
+    const float z[PPL] = {};
+    put_vals<PPL>(At, arow(32 * q + (t >> 1)) + obase, z);
+  }
+  auto coef = [&](int l, float &c, float &k, float &b, float &d) {  // coefficients of target l + 1
+    if (PART == 0) {
+      const float4 cf = rq0[base + l + 1];
+      c = cf.x;
+      k = 0.f;
+      b = cf.y;
+      d = cf.z;
+    } else {
+      const float4 cf = rq2[base + l + 1];
+      c = cf.x;
+      k = f ? -cf.y : cf.y;
+      b = cf.z;
+      d = 0.f;
+      if (DF) {
+        const float2 dd = rq2d[base + l + 1];
+        d = f ? dd.y : dd.x;
+      }
+    }
+  };
+  float c = 0.f, k = 0.f, b = 0.f, d = 0.f;
+  if (t0 + 1 < nv) coef(l0 + t0, c, k, b, d);
+  for (int t = t0; t < nv; ++t) {
+    float cn = 0.f, kn = 0.f, bn = 0.f, dn = 0.f;
+    if (t + 2 < nv) coef(l0 + t + 1, cn, kn, bn, dn);
+    if ((t & 1) == PAR) {
+      float x[PPL];
+#pragma unroll
+      for (int i = 0; i < PPL; ++i) x[i] = v0[i] * sc[i];
+      put_vals<PPL>(At, arow(32 * q + (t >> 1)) + obase, x);
+    }
+    if (t + 1 < nv) {
+#pragma unroll
+      for (int i = 0; i < PPL; ++i) step<DF>(v0[i], v1[i], c, k, b, d, xs[i]);
       if (anyS) {
         anyS = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < PPL; ++i) {
           if (Sk[i] > 0 && fabsf(v0[i]) > 0x1p32f) {
             float d0 = 0.f, d1 = 0.f;
             rescale(v0[i], v1[i], d0, d1, Sk[i], sc[i]);
@@ -307,6 +371,34 @@ __device__ __forceinline__ void ana_block(unsigned char *At, int q, int g, int p
         }
       }
     }
+    c = cn;
+    k = kn;
+    b = bn;
+    d = dn;
+  }
+}
+
+template <int PART, bool DF, int PAR>
+__device__ __forceinline__ void ana_task_ppl(int PPL, unsigned char *At, int q, uint32_t obase, int l0, int lmax,
+                                             int ls, int f, const float4 *ck0, const float4 *ck2, int64_t orow,
+                                             const PairDev *pairs, int p0, int npairs, const float4 *rq0,
+                                             const float4 *rq2, const float2 *rq2d, int64_t base) {
+  switch (PPL) {
+    case 8:
+      ana_task<PART, DF, PAR, 8>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0, rq2, rq2d,
+                                 base);
+      break;
+    case 4:
+      ana_task<PART, DF, PAR, 4>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0, rq2, rq2d,
+                                 base);
+      break;
+    case 2:
+      ana_task<PART, DF, PAR, 2>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0, rq2, rq2d,
+                                 base);
+      break;
+    default:
+      ana_task<PART, DF, PAR, 1>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0, rq2, rq2d,
+                                 base);
   }
 }
 
@@ -353,15 +445,21 @@ __global__ void __launch_bounds__(AGEN_THREADS, 1) k_ana_gen(
   const int nsteps = (npairs + 15) / 16;
   const int nblk = (lmax - m + 1 + CKL - 1) / CKL;
   if (warp < S) {
-    // this lane's generation task
-    const int j = PART == 0 ? lane >> 3 : lane >> 4;
-    const int g = PART == 0 ? (lane >> 2) & 1 : (lane >> 3) & 1;
-    const int q = PART == 0 ? lane & 3 : (lane >> 1) & 3;
-    const int f = PART == 0 ? 0 : lane & 1;
-    const int J = 4 * (lt0 + j) + q;       // checkpoint block
-    const bool gen = j < nt;
-    const bool blk = gen && J < nblk;
+    // This CTA's checkpoint blocks: J = 4 lt0 + bi for bi < nvalid.  A lane
+    // takes PPL pairs of one octet g of one block bi (and one spin-2 function
+    // f); PPL is the fewest pairs per lane that still covers every block with
+    // the warp's 32 lanes: 8 at low m, down to 1 when few blocks remain.
+    constexpr int nf = PART == 0 ? 1 : 2;
+    const int nvalid = max(0, min(4 * nt, nblk - 4 * lt0));
+    int PPL = 1;
+    while (PPL < 8 && nvalid * 2 * (8 / PPL) * nf > 32) PPL *= 2;
+    const int sub = 8 / PPL;
+    const int sl = lane % sub, g = (lane / sub) & 1, f = PART == 0 ? 0 : (lane / (2 * sub)) & 1;
+    const int bi = lane / (2 * sub * nf);
+    const bool gen = bi < nvalid;
+    const int J = 4 * lt0 + bi, j = bi >> 2, q = bi & 3;
     const int ls = (PART == 1 && m < 2 && J == 0) ? 2 : 0;
+    const uint32_t obase = (uint32_t)(g * 128 + sl * PPL * 2);
     for (int c = warp; c < nsteps; c += S) {
       const int s = warp, k = c / S;
       if (k > 0 && !mbar_wait(&done[s], (k - 1) & 1, err)) break;
@@ -384,46 +482,27 @@ __global__ void __launch_bounds__(AGEN_THREADS, 1) k_ana_gen(
           convert_b_pq(b, ko, Bst, Bst + 2 * tileB, tileB, par, vq, vu);
         }
       }
-      // A tile rows of block J, pairs 16 c + 8 g + 0..7
+      // A tile rows of block J, pairs 16 c + 8 g + PPL sl ..
       if (gen) {
         unsigned char *At = Ast + (j * nA + f) * ATS;
-        if (!blk) {
-          const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          for (int r = 0; r < 32; ++r) put_row_a(At, 32 * q + r, g, z);
-        } else {
-          float v0[8], v1[8], sc[8];
-          Xs xs[8];
-          int Sk[8];
-          bool act[8];
-          int anyS = 0;
-          const int64_t orow = (cko[m] + J) * (int64_t)npairs;
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int pr = 16 * c + 8 * g + i;
-            act[i] = pr < npairs;
-            const int pp = act[i] ? pr : npairs - 1;
-            xs[i] = xs_of(pairs, pp);
-            const float4 r0 = ck0[orow + pp];
-            if (PART == 0) {
-              v0[i] = r0.x;
-              v1[i] = r0.y;
-              Sk[i] = __float_as_int(r0.z);
-            } else {
-              const float4 r2 = ck2[orow + pp];
-              v0[i] = f == 0 ? r2.x : r2.z;
-              v1[i] = f == 0 ? r2.y : r2.w;
-              Sk[i] = __float_as_int(r0.w);
-            }
-            sc[i] = scale_of(Sk[i]);
-            anyS |= Sk[i];
-          }
-          const int p8 = min(16 * c + 8 * g, npairs - 1);
-          if (pair_dform(pairs, p8))
-            ana_block<PART, true>(At, q, g, par, ls, m + CKL * J, lmax, f, act, v0, v1, xs, sc, Sk, anyS, rq0, rq2,
-                                  rq2d, base);
+        const int p0 = 16 * c + 8 * g + PPL * sl;
+        const int64_t orow = (cko[m] + J) * (int64_t)npairs;
+        const bool df = pair_dform(pairs, min(16 * c + 8 * g, npairs - 1));
+        const int l0 = m + CKL * J;
+        if (df) {
+          if (par == 0)
+            ana_task_ppl<PART, true, 0>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0,
+                                        rq2, rq2d, base);
           else
-            ana_block<PART, false>(At, q, g, par, ls, m + CKL * J, lmax, f, act, v0, v1, xs, sc, Sk, anyS, rq0,
-                                   rq2, rq2d, base);
+            ana_task_ppl<PART, true, 1>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0,
+                                        rq2, rq2d, base);
+        } else {
+          if (par == 0)
+            ana_task_ppl<PART, false, 0>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0,
+                                         rq2, rq2d, base);
+          else
+            ana_task_ppl<PART, false, 1>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0,
+                                         rq2, rq2d, base);
         }
       }
       fence_proxy_async();  // generic-proxy writes -> tensor-core reads
@@ -489,10 +568,10 @@ constexpr int SGEN_MAX_NS = 8;
 // multipoles l = lb .. lb + 31, stored as the rows of the parity tiles (spin 0:
 // lambda e, o in unit Ae; spin 2: {lam+ e, lam- o} in Ae, {lam+ o, lam- e} in
 // Ao), the recurrence state carried on to the next step.
-template <int PART, bool DF>
+template <int PART>
 __device__ __forceinline__ void syn_step(unsigned char *Ae, unsigned char *Ao, int r, int lb, int lmax, int ls,
                                          bool act, float &a0, float &a1, float &b0, float &b1, int &S, float &sc,
-                                         const Xs &xs, float4 cA, float2 cD) {
+                                         const Xs &xs, bool df, float4 cA, float2 cD) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     float ve[8], vo[8], we[8], wo[8];  // spin 0: lambda; spin 2: v = lam+, w = lam-
@@ -514,24 +593,32 @@ __device__ __forceinline__ void syn_step(unsigned char *Ae, unsigned char *Ao, i
         ve[t >> 1] = v;
         we[t >> 1] = w;
       }
-      // the coefficients of target l + 1, held by lane 16 h + t of the warp
+      // the coefficients of target l + 1, held by lane 16 h + t of the warp;
+      // every lane takes part in the shuffles (the form is chosen after them,
+      // per lane: a warp can hold ring pairs of both forms)
       const int src = 16 * h + t;
       const float c0 = __shfl_sync(0xffffffffu, cA.x, src), c1 = __shfl_sync(0xffffffffu, cA.y, src);
       const float c2 = __shfl_sync(0xffffffffu, cA.z, src);
-      float dp = 0.f, dq = 0.f;
-      if (PART == 0 && DF) dp = c2;
-      if (PART == 1 && DF) {
+      float dp = c2, dq = 0.f;
+      if (PART == 1) {
         dp = __shfl_sync(0xffffffffu, cD.x, src);
         dq = __shfl_sync(0xffffffffu, cD.y, src);
       }
       if (l < lmax && l >= ls) {
         if (PART == 0) {
-          step<DF>(a0, a1, c0, 0.f, c1, dp, xs);
+          if (df)
+            step<true>(a0, a1, c0, 0.f, c1, dp, xs);
+          else
+            step<false>(a0, a1, c0, 0.f, c1, 0.f, xs);
           if (S > 0 && fabsf(a0) > 0x1p32f) rescale(a0, a1, b0, b1, S, sc);
         } else {
-          const float4 cf = make_float4(c0, c1, c2, 0.f);
-          step<DF>(a0, a1, cf.x, cf.y, cf.z, dp, xs);
-          step<DF>(b0, b1, cf.x, -cf.y, cf.z, dq, xs);
+          if (df) {
+            step<true>(a0, a1, c0, c1, c2, dp, xs);
+            step<true>(b0, b1, c0, -c1, c2, dq, xs);
+          } else {
+            step<false>(a0, a1, c0, c1, c2, 0.f, xs);
+            step<false>(b0, b1, c0, -c1, c2, 0.f, xs);
+          }
           if (S > 0 && fabsf(a0) + fabsf(b0) > 0x1p32f) rescale(a0, a1, b0, b1, S, sc);
         }
       }
@@ -645,10 +732,7 @@ __global__ void __launch_bounds__(160, 1) k_syn_gen(
       }
       unsigned char *Ae = sm + ((c * UPS) % NS) * stage;
       unsigned char *Ao = PART == 0 ? Ae : sm + ((c * UPS + 1) % NS) * stage;
-      if (df)
-        syn_step<PART, true>(Ae, Ao, r, m + 32 * c, lmax, ls, act, a0, a1, b0, b1, S, sc, xs, cA, cD);
-      else
-        syn_step<PART, false>(Ae, Ao, r, m + 32 * c, lmax, ls, act, a0, a1, b0, b1, S, sc, xs, cA, cD);
+      syn_step<PART>(Ae, Ao, r, m + 32 * c, lmax, ls, act, a0, a1, b0, b1, S, sc, xs, df, cA, cD);
       cA = nA;
       cD = nD;
       fence_proxy_async();
