@@ -268,6 +268,15 @@ dm_status dm_set_tc_tiles(dm_plan *plan, int generate);
  * plan or bytes < 1, DM_EBUSY during a solve session. */
 dm_status dm_set_ff_slab_bytes(dm_plan *plan, int64_t bytes);
 
+/* Memory for the partial sums of the FP64 and float-float analysis: one
+ * slot per RHS and chunk of 64 ring pairs (3 nalm FP64 complex values).  By
+ * default a plan holds every chunk while that takes at most 24 GiB, else as
+ * many slots as fit in it (at least 2); with fewer slots than chunks the
+ * analysis runs the chunks in waves, slot 0 keeping the running sum.  slots:
+ * 2 .. chunks (clamped).  Reallocates the partial-sum buffer; DM_EINVAL for a
+ * null plan or slots < 2, DM_EBUSY during a solve session. */
+dm_status dm_set_analysis_slots(dm_plan *plan, int slots);
+
 /* Tuning: the ring transforms of an iteration for rings whose FFT size M is a
  * power of two in [512, 4096] run as fixed-size kernels of radix 2^lr with
  * M / 2^lr threads per ring and (RHS, field) lane; lr = 3 (radix 8, the

@@ -447,7 +447,14 @@ dm_status plan_workspace(dm_plan *p, dm_plan **out) {
   p->t_h.assign(B, 0.0);
   if ((e = dalloc(p, &p->rc, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return bad(e, "alloc rc");
   if ((e = dalloc(p, &p->a, (size_t)B * 3 * p->nalm))) return bad(e, "alloc a");
-  if (!p->flat && (e = dalloc(p, &p->apart, (size_t)B * p->nchunk * 3 * p->nalm))) return bad(e, "alloc apart");
+  // FP64 analysis partials: every pair chunk at once while that takes at most
+  // 24 GiB, else a few slots and the chunks in waves (legendre_analysis)
+  {
+    const double per_slot = (double)B * 3 * p->nalm * sizeof(double2);
+    const int fit = (int)std::max(2.0, std::floor(24.0 * (1u << 30) / per_slot));
+    p->nslot = std::min(p->nchunk, fit);
+  }
+  if (!p->flat && (e = dalloc(p, &p->apart, (size_t)B * p->nslot * 3 * p->nalm))) return bad(e, "alloc apart");
   if ((e = dalloc(p, &p->wd, (size_t)B * n3))) return bad(e, "alloc wd");
   if ((e = dalloc(p, &p->norms, (size_t)B * 3 * p->nrings * 2))) return bad(e, "alloc norms");
   if ((e = dalloc(p, &p->state, (size_t)B))) return bad(e, "alloc state");
@@ -921,6 +928,23 @@ dm_status dm_set_ff_slab_bytes(dm_plan *p, int64_t bytes) {
   if (p->ffs_lo) cudaFree(p->ffs_lo);
   p->ffs = p->ffs_lo = nullptr;
   p->ffs_m.clear();
+  return DM_OK;
+}
+
+dm_status dm_set_analysis_slots(dm_plan *p, int slots) {
+  if (!p || slots < 2) return DM_EINVAL;
+  if (p->session) return DM_EBUSY;
+  if (p->flat) return DM_OK;
+  const int ns = std::min(slots, p->nchunk);
+  if (ns == p->nslot) return DM_OK;
+  prog_release(p);
+  const size_t n = (size_t)p->batch * ns * 3 * p->nalm;
+  double2 *a = nullptr;
+  if (cudaMalloc(&a, sizeof(double2) * n) != cudaSuccess) return fail(p, DM_ENOMEM, "analysis slots");
+  cudaFree(p->apart);
+  p->bytes += (int64_t)sizeof(double2) * ((int64_t)n - (int64_t)p->batch * p->nslot * 3 * p->nalm);
+  p->apart = a;
+  p->nslot = ns;
   return DM_OK;
 }
 

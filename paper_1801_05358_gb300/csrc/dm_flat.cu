@@ -195,6 +195,7 @@ dm_status dm_plan_create_flat(int N, double L, int batch, dm_plan **out) {
   p->mmax = p->lmax = N / 2 - 1;
   p->nmodes = p->nalm = (int64_t)(N / 2) * N;
   p->nchunk = 1;
+  p->nslot = 1;
   cudaError_t e = build_tables_flat(p);
   if (e) {
     p->err = std::string("build flat tables: ") + cudaGetErrorString(e);

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/dmwf.h"
@@ -138,6 +139,8 @@ struct dm_plan {
   double2 *a = nullptr;         // [B][3][nalm] harmonic iterate
   double2 *apart = nullptr;     // [B][nchunk][3][nalm] analysis partial sums
   int nchunk = 0;               // pair chunks of the analysis
+  int nslot = 0;                // chunk slots of apart per RHS (nslot < nchunk: the analysis runs in waves)
+  int nchunk32 = 0;             // chunks of apart32 per RHS: nchunk, or 1 (tensor-core analysis only) when that is over 24 GiB
   double *wd = nullptr;         // [B][3][npix] w * d
   double *norms = nullptr;      // [B][3][nrings][2] Cauchy partial sums
   dmwf::SolveState *state = nullptr;   // [B]
@@ -319,7 +322,34 @@ cudaError_t ana_gen_launch(dm_plan *p, cudaStream_t st);
 cudaError_t legendre_synthesis_ff(dm_plan *p, const double2 *alm, cudaStream_t st);
 cudaError_t anchor_c32(dm_plan *p, cudaStream_t st);     // c = F (a_hi + g_hi) - a_hi, e = 0
 cudaError_t materialize_a(dm_plan *p, cudaStream_t st);  // a = a_hi + e
-cudaError_t legendre_analysis_ff_parts(dm_plan *p, cudaStream_t st);
+cudaError_t legendre_analysis_ff_parts(dm_plan *p, cudaStream_t st, int *used);
+cudaError_t fold_slots(dm_plan *p, int nused, int m0, int m1, cudaStream_t st);
+// Partial sums of the FP64-class analysis over every pair chunk into apart,
+// in waves of at most nslot chunks when the plan holds fewer slots than
+// chunks: slot 0 keeps the running sum, each later wave fills slots 1 ..
+// and is folded into it.  launch(c0, slot0, n, m0, m1) runs the chunks
+// [c0, c0 + n) into the slots [slot0, slot0 + n) for the orders [m0, m1).
+// Returns the slots that hold the orders' sum (nchunk without waves, else 1).
+template <class F>
+inline cudaError_t chunk_waves(dm_plan *p, int m0, int m1, cudaStream_t st, F launch, int *used_out) {
+  if (p->nslot >= p->nchunk) {
+    *used_out = p->nchunk;
+    return launch(0, 0, p->nchunk, m0, m1);
+  }
+  int c0 = 0, used = 0;
+  while (c0 < p->nchunk) {
+    const int slot0 = used == 0 ? 0 : 1;
+    const int n = std::min(p->nslot - slot0, p->nchunk - c0);
+    if (cudaError_t e = launch(c0, slot0, n, m0, m1)) return e;
+    c0 += n;
+    used = slot0 + n;
+    if (cudaError_t e = fold_slots(p, used, m0, m1, st)) return e;
+    used = 1;
+  }
+  *used_out = 1;
+  return cudaSuccess;
+}
+
 
 // driver (dm_api.cu), shared with the server (dm_serve.cu)
 dm_status upload_levels(dm_plan *p);

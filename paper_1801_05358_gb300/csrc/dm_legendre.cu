@@ -129,14 +129,14 @@ __global__ void __launch_bounds__(ANA_P) k_leg_ana64(const PairDev *__restrict__
                                                      const double *__restrict__ seed,
                                                      const int *__restrict__ seed_exp,
                                                      const double2 *__restrict__ rc, double2 *__restrict__ apart,
-                                                     int lmax, int mmax, int npairs, int64_t nalm, int nchunk,
-                                                     const SolveState *__restrict__ state) {
+                                                     int lmax, int mmax, int npairs, int64_t nalm, int c0,
+                                                     int slot0, int nslot, const SolveState *__restrict__ state) {
   __shared__ double P0[ANA_P][ANA_L + 1], Pp[ANA_P][ANA_L + 1], Pq[ANA_P][ANA_L + 1];
   // per pair: GT even, GT odd, GQ even, GQ odd, GU even, GU odd (complex)
   __shared__ double2 G[ANA_P][6];
   __shared__ double red[ANA_PARTS][ANA_L][6];
   __shared__ RecCoef sc[ANA_L];
-  const int m = blockIdx.y, b = blockIdx.z, chunk = blockIdx.x;
+  const int m = blockIdx.y, b = blockIdx.z, chunk = c0 + blockIdx.x, slot = slot0 + blockIdx.x;
   if (state != nullptr && state[b].done) return;
   const int t = threadIdx.x;
   const int p = chunk * ANA_P + t;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(ANA_P) k_leg_ana64(const PairDev *__restrict__
         for (int q = 1; q < ANA_PARTS; ++q) a += red[q][lj][k];
         v[k] = a;
       }
-      double2 *o = apart + ((int64_t)b * nchunk + chunk) * 3 * nalm + base + l;
+      double2 *o = apart + ((int64_t)b * nslot + slot) * 3 * nalm + base + l;
       o[0] = make_double2(v[0], v[1]);
       o[nalm] = make_double2(v[2], v[3]);
       o[2 * nalm] = make_double2(v[4], v[5]);
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(ANA_P) k_leg_ana64(const PairDev *__restrict__
 //  ANA_DM_STEP : out = F_level (out + Omega sum)   (a <- F [a + A (t - s)])
 // grid: (l blocks, batch, m)
 __global__ void k_ana_reduce(const double2 *__restrict__ apart, double2 *out, int lmax, int64_t nalm, int nchunk,
-                             double omega, int epilogue, const double *__restrict__ filt, int nlev,
+                             int nslot, double omega, int epilogue, const double *__restrict__ filt, int nlev,
                              const SolveState *__restrict__ state, const double2 *__restrict__ src) {
   const int b = blockIdx.y, m = blockIdx.z;
   if (state != nullptr && state[b].done) return;
@@ -227,7 +227,7 @@ __global__ void k_ana_reduce(const double2 *__restrict__ apart, double2 *out, in
   double2 acc[3];
   for (int f = 0; f < 3; ++f) {
     double2 a = make_double2(0, 0);
-    for (int c = 0; c < nchunk; ++c) a = cadd(a, apart[(((int64_t)b * nchunk + c) * 3 + f) * nalm + i]);
+    for (int c = 0; c < nchunk; ++c) a = cadd(a, apart[(((int64_t)b * nslot + c) * 3 + f) * nalm + i]);
     acc[f] = make_double2(omega * a.x, omega * a.y);
   }
   double2 *o = out + (int64_t)b * 3 * nalm + i;
@@ -250,22 +250,52 @@ __global__ void k_ana_reduce(const double2 *__restrict__ apart, double2 *out, in
   o[2 * nalm] = make_double2(c[3] * bb.x, c[3] * bb.y);
 }
 
+// Slot 0 += slots 1 .. nused - 1 for the orders [m0, m0 + gridDim.z)
+// (grid: l blocks, batch, orders)
+__global__ void k_fold_slots(double2 *apart, int nslot, int nused, int lmax, int64_t nalm, int m0,
+                             const SolveState *__restrict__ state) {
+  const int b = blockIdx.y, m = m0 + blockIdx.z;
+  if (state != nullptr && state[b].done) return;
+  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
+  if (l > lmax) return;
+  const int64_t i = alm_base(lmax, m) + l;
+  for (int f = 0; f < 3; ++f) {
+    double2 a = apart[(((int64_t)b * nslot) * 3 + f) * nalm + i];
+    for (int c = 1; c < nused; ++c) a = cadd(a, apart[(((int64_t)b * nslot + c) * 3 + f) * nalm + i]);
+    apart[(((int64_t)b * nslot) * 3 + f) * nalm + i] = a;
+  }
+}
+
+cudaError_t fold_slots(dm_plan *p, int nused, int m0, int m1, cudaStream_t st) {
+  if (nused <= 1 || m1 <= m0) return cudaSuccess;
+  dim3 g((unsigned)((p->lmax + 1 + 127) / 128), p->batch, m1 - m0);
+  k_fold_slots<<<g, 128, 0, st>>>(p->apart, p->nslot, nused, p->lmax, p->nalm, m0,
+                                  p->state_active ? p->state : nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t analysis64_parts(dm_plan *p, cudaStream_t st, int *used) {
+  const SolveState *stp = p->state_active ? p->state : nullptr;
+  return chunk_waves(p, 0, p->mmax + 1, st, [&](int c0, int slot0, int n, int m0, int m1) {
+    dim3 grid(n, m1 - m0, p->batch);
+    k_leg_ana64<<<grid, ANA_P, 0, st>>>(p->pairs, p->rec, p->seed, p->seed_exp, p->rc, p->apart, p->lmax, p->mmax,
+                                        p->npairs, p->nalm, c0, slot0, p->nslot, stp);
+    return cudaGetLastError();
+  }, used);
+}
+
 cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid) {
   if (p->flat) return flat_analysis(p, epilogue, out, st, mid);
   if (p->prec != DM_FP64) return legendre_analysis32(p, epilogue, out, st, mid);
-  dim3 grid(p->nchunk, p->mmax + 1, p->batch);
   const SolveState *stp = p->state_active ? p->state : nullptr;
-  if (p->ff_legendre || p->ff_now) {
-    cudaError_t e = legendre_analysis_ff_parts(p, st);
-    if (e) return e;
-  } else {
-    k_leg_ana64<<<grid, ANA_P, 0, st>>>(p->pairs, p->rec, p->seed, p->seed_exp, p->rc, p->apart, p->lmax, p->mmax,
-                                        p->npairs, p->nalm, p->nchunk, stp);
-  }
+  int used = p->nchunk;
+  cudaError_t e = (p->ff_legendre || p->ff_now) ? legendre_analysis_ff_parts(p, st, &used)
+                                                : analysis64_parts(p, st, &used);
+  if (e) return e;
   if (mid) cudaEventRecord(mid, st);
   double omega = 4.0 * M_PI / (double)p->npix;
   dim3 g2((unsigned)((p->lmax + 1 + 127) / 128), p->batch, p->mmax + 1);
-  k_ana_reduce<<<g2, 128, 0, st>>>(p->apart, out, p->lmax, p->nalm, p->nchunk, omega, epilogue, p->filt,
+  k_ana_reduce<<<g2, 128, 0, st>>>(p->apart, out, p->lmax, p->nalm, used, p->nslot, omega, epilogue, p->filt,
                                    p->filt_levels,
                                    epilogue == ANA_DM_STEP ? p->state : stp,
                                    (epilogue == ANA_DM_STEP && p->src_active) ? p->jsrc : nullptr);
@@ -720,6 +750,8 @@ cudaError_t legendre_analysis32(dm_plan *p, int epilogue, double2 *out, cudaStre
     cudaError_t e = legendre_analysis_tc(p, st);
     if (e) return e;
     nchunk = 1;
+  } else if (p->nchunk32 < p->nchunk) {
+    return cudaErrorInvalidValue;  // the CUDA-core FP32 analysis needs every chunk (see setup_fp32)
   } else if (cudaError_t e = ensure_ptab(p)) {
     return e;
   } else if (p->batch % 4 == 0) {

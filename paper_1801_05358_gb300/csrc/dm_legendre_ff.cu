@@ -173,14 +173,15 @@ template <int NB>
 __global__ void __launch_bounds__(FF_ANA_P) k_leg_ana_ff(const float *__restrict__ ptab,
                                                         const float *__restrict__ ptab_lo,
                                                         const double2 *__restrict__ rc, double2 *__restrict__ apart,
-                                                        int lmax, int mmax, int npairs, int64_t nalm, int nchunk,
-                                                        int batch, const SolveState *__restrict__ state, int m0,
-                                                        int64_t base0, int64_t plane) {
+                                                        int lmax, int mmax, int npairs, int64_t nalm, int c0,
+                                                        int slot0, int nslot, int batch,
+                                                        const SolveState *__restrict__ state, int m0, int64_t base0,
+                                                        int64_t plane) {
   __shared__ ff P[3][FF_ANA_P][FF_ANA_L + 1];
   // per pair and RHS: (T, Q, U) x (even, odd) x (re, im)
   __shared__ ff G[FF_ANA_P][NB][12];
   __shared__ ff red[FF_ANA_PARTS][FF_ANA_L][NB][6];
-  const int b0 = blockIdx.x * NB, chunk = blockIdx.y, m = m0 + blockIdx.z;
+  const int b0 = blockIdx.x * NB, chunk = c0 + blockIdx.y, slot = slot0 + blockIdx.y, m = m0 + blockIdx.z;
   bool any = false;
   for (int k = 0; k < NB; ++k) any = any || (b0 + k < batch && (state == nullptr || !state[b0 + k].done));
   if (!any) return;
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(FF_ANA_P) k_leg_ana_ff(const float *__restrict
           for (int q = 1; q < FF_ANA_PARTS; ++q) ff_add(a, red[q][lj][k][i]);
           v[i] = ff_to_double(a);
         }
-        double2 *o = apart + ((int64_t)b * nchunk + chunk) * 3 * nalm + base + l;
+        double2 *o = apart + ((int64_t)b * nslot + slot) * 3 * nalm + base + l;
         o[0] = make_double2(v[0], v[1]);
         o[nalm] = make_double2(v[2], v[3]);
         o[2 * nalm] = make_double2(v[4], v[5]);
@@ -326,25 +327,33 @@ cudaError_t legendre_synthesis_ff(dm_plan *p, const double2 *alm, cudaStream_t s
   return cudaGetLastError();
 }
 
-// partial sums per chunk of 64 ring pairs into p->apart (the FP64 reduction follows)
-cudaError_t legendre_analysis_ff_parts(dm_plan *p, cudaStream_t st) {
+// partial sums per chunk of 64 ring pairs into p->apart (the FP64 reduction
+// follows), in chunk waves when the plan holds fewer slots than chunks
+// (chunk_waves); *used = the slots holding the sums
+cudaError_t legendre_analysis_ff_parts(dm_plan *p, cudaStream_t st, int *used) {
   const SolveState *stp = p->state_active ? p->state : nullptr;
   if (p->ptab) {
-    dim3 g((p->batch + FF_NB - 1) / FF_NB, p->nchunk, p->mmax + 1);
-    k_leg_ana_ff<FF_NB><<<g, FF_ANA_P, 0, st>>>(p->ptab, p->ptab_lo, p->rc, p->apart, p->lmax, p->mmax, p->npairs,
-                                                p->nalm, p->nchunk, p->batch, stp, 0, 0,
-                                                p->nalm * (int64_t)p->npairs);
-    return cudaGetLastError();
+    return chunk_waves(p, 0, p->mmax + 1, st, [&](int c0, int slot0, int n, int m0, int m1) {
+      dim3 g((p->batch + FF_NB - 1) / FF_NB, n, m1 - m0);
+      k_leg_ana_ff<FF_NB><<<g, FF_ANA_P, 0, st>>>(p->ptab, p->ptab_lo, p->rc, p->apart, p->lmax, p->mmax,
+                                                  p->npairs, p->nalm, c0, slot0, p->nslot, p->batch, stp, m0, 0,
+                                                  p->nalm * (int64_t)p->npairs);
+      return cudaGetLastError();
+    }, used);
   }
   if (cudaError_t e = ff_slabs(p)) return e;
   for (size_t k = 0; k + 1 < p->ffs_m.size(); ++k) {
-    const int m0 = p->ffs_m[k], m1 = p->ffs_m[k + 1];
-    if (cudaError_t e = gen_tables32_slab(p, p->ffs, p->ffs_lo, m0, m1, st)) return e;
-    const int64_t b0 = alm_start_h(p->lmax, m0), b1 = alm_start_h(p->lmax, m1);
-    dim3 g((p->batch + FF_NB - 1) / FF_NB, p->nchunk, m1 - m0);
-    k_leg_ana_ff<FF_NB><<<g, FF_ANA_P, 0, st>>>(p->ffs, p->ffs_lo, p->rc, p->apart, p->lmax, p->mmax, p->npairs,
-                                                p->nalm, p->nchunk, p->batch, stp, m0, b0,
-                                                (b1 - b0) * (int64_t)p->npairs);
+    const int s0 = p->ffs_m[k], s1 = p->ffs_m[k + 1];
+    if (cudaError_t e = gen_tables32_slab(p, p->ffs, p->ffs_lo, s0, s1, st)) return e;
+    const int64_t b0 = alm_start_h(p->lmax, s0), b1 = alm_start_h(p->lmax, s1);
+    cudaError_t e = chunk_waves(p, s0, s1, st, [&](int c0, int slot0, int n, int m0, int m1) {
+      dim3 g((p->batch + FF_NB - 1) / FF_NB, n, m1 - m0);
+      k_leg_ana_ff<FF_NB><<<g, FF_ANA_P, 0, st>>>(p->ffs, p->ffs_lo, p->rc, p->apart, p->lmax, p->mmax, p->npairs,
+                                                  p->nalm, c0, slot0, p->nslot, p->batch, stp, m0, b0,
+                                                  (b1 - b0) * (int64_t)p->npairs);
+      return cudaGetLastError();
+    }, used);
+    if (e) return e;
   }
   return cudaGetLastError();
 }

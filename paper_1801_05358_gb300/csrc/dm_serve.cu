@@ -96,7 +96,7 @@ dm_plan make_view(const dm_plan *p, int b) {
   const size_t nrc = 3 * (size_t)(p->mmax + 1) * p->npairs * 2;
   v.rc += b * nrc;
   v.a += b * na;
-  v.apart += (size_t)b * p->nchunk * na;
+  v.apart += (size_t)b * p->nslot * na;
   v.wd += b * n3;
   v.norms += (size_t)b * 3 * p->nrings * 2;
   v.state += b;
@@ -113,7 +113,7 @@ dm_plan make_view(const dm_plan *p, int b) {
   v.filt += (size_t)b * p->filt_levels * 4 * (p->lmax + 1);
   if (p->fp32_ready) {
     v.rc32 += b * nrc;
-    v.apart32 += (size_t)b * p->nchunk * na;
+    v.apart32 += (size_t)b * p->nchunk32 * na;
     v.s32 += b * n3;
     v.w32 += b * n3;
     v.wd32 += b * n3;

@@ -623,7 +623,11 @@ cudaError_t setup_fp32(dm_plan *p) {
   if ((e = al(&p->twid32, p->fft_M_max - 1))) return undo(e);
   if ((e = al(&p->twr32, p->twr_words))) return undo(e);
   if ((e = al(&p->rc32, (size_t)B * 3 * (p->mmax + 1) * p->npairs * 2))) return undo(e);
-  if ((e = al(&p->apart32, (size_t)B * p->nchunk * 3 * p->nalm))) return undo(e);
+  {
+    const double full = (double)B * p->nchunk * 3 * p->nalm * sizeof(float2);
+    p->nchunk32 = full <= 24.0 * (1u << 30) ? p->nchunk : 1;
+  }
+  if ((e = al(&p->apart32, (size_t)B * p->nchunk32 * 3 * p->nalm))) return undo(e);
   if ((e = al(&p->s32, (size_t)B * n3))) return undo(e);
   if ((e = al(&p->w32, (size_t)B * n3))) return undo(e);
   if ((e = al(&p->wd32, (size_t)B * n3))) return undo(e);

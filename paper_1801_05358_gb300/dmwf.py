@@ -26,7 +26,7 @@ EXPORTS = [
     "dm_ring_fft_inverse", "dm_legendre_synthesis", "dm_legendre_analysis", "dm_apply_filter", "dm_noise_info",
     "dm_profile_enable", "dm_profile_read", "dm_measure_alu_peaks", "dm_solve_begin", "dm_solve_iterate",
     "dm_solve_end", "dm_set_refinement", "dm_set_noise_mask_rhs", "dm_server_create", "dm_serve_submit",
-    "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores", "dm_set_tc_tiles", "dm_set_ff_slab_bytes", "dm_set_ring_radix",
+    "dm_serve_poll", "dm_serve_cancel", "dm_server_info", "dm_server_destroy", "dm_set_tensor_cores", "dm_set_tc_tiles", "dm_set_ff_slab_bytes", "dm_set_analysis_slots", "dm_set_ring_radix",
     "dm_set_anchor_precision", "dm_set_noise_cov",
     "dm_legendre_analysis_noalloc", "dm_set_diagnostics", "dm_autotune", "dm_get_tuning", "dm_set_tuning",
     "dm_jacobi_refine", "dm_test_tc_withhold", "dm_plan_create_flat", "dm_set_spectra_flat", "dm_set_noise_flat",
@@ -139,6 +139,7 @@ def lib():
         L.dm_set_tensor_cores.argtypes = [vp, ctypes.c_int]
         L.dm_set_tc_tiles.argtypes = [vp, ctypes.c_int]
         L.dm_set_ff_slab_bytes.argtypes = [vp, ctypes.c_int64]
+        L.dm_set_analysis_slots.argtypes = [vp, ctypes.c_int]
         L.dm_set_diagnostics.argtypes = [vp, ctypes.c_int]
         L.dm_autotune.argtypes = [vp, ctypes.c_int, vp]
         L.dm_jacobi_refine.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
@@ -355,6 +356,10 @@ class Plan:
         """Tensor-core Legendre operand generated in the kernels (True), streamed from stored
         tables (False) or chosen by size (None)."""
         self._check(lib().dm_set_tc_tiles(self.h, -1 if generate is None else (1 if generate else 0)))
+
+    def set_analysis_slots(self, slots):
+        """Chunk slots of the FP64-class analysis partial sums per RHS (fewer than chunks: waves)."""
+        self._check(lib().dm_set_analysis_slots(self.h, int(slots)))
 
     def set_ff_slab_bytes(self, nbytes):
         """Largest per-slab table of the float-float stages when the plan keeps no full FP32 tables."""

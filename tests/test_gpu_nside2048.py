@@ -1,12 +1,15 @@
-"""Configuration nside 2048 / lmax 4096 (FP64 path) against the oracle on
-sampled outputs.
+"""Configuration nside 2048 / lmax 4096 (FP64 path, and the mixed path with
+the tensor-core Legendre operand generated in the kernels) against the oracle
+on sampled outputs.
 
 A full oracle transform at this size takes far too long, so the oracle
 computes whole rings of alm2map and whole orders m of map2alm one at a time
 (oracle.ring_alm2map / map2alm_m, pinned to the full transforms at small
 sizes).  The GPU runs the full transforms and one dual messenger iteration in
-the FP64 mode; the mixed mode's tables do not fit this size (3 x nalm x npairs
-FP32 values, about 412 GB).  The data map of the iteration is the nside 2048
+the FP64 mode.  The mixed mode's stored tables would not fit this size
+(about 1 TB of tiles and FP32 tables), so its plans generate the tensor-core
+tiles in the kernels and the float-float anchors' tables per slab; its
+transforms and first iteration are held to the mixed bar, 2e-5 and 1e-5.  The data map of the iteration is the nside 2048
 recipe's noise realisation on the observed pixels of its mask (no GPU result
 enters an expected value).  Bar: the FP64 one, 1e-10 relative L2 per sample,
 except on the two rings nearest each pole (theta < 1e-3): there the oracle's
@@ -91,3 +94,66 @@ def test_first_iteration_sampled_orders(orc):
     for m in ORDERS:
         idx = [orc.almidx(LMAX, l, m) for l in range(m, LMAX + 1)]
         assert rel(ga[:, idx], ref[:, idx]) < 1e-10, m
+
+
+MB = 8  # a tensor-core batch
+
+
+def test_mixed_alm2map_sampled_rings(orc):
+    alm = W.random_alm(LMAX, MB, 53)
+    p = dmwf.Plan(NSIDE, LMAX, MB)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    m_out = torch.zeros((MB, 3, NPIX), dtype=torch.float64, device="cuda")
+    p.alm2map(alm_dev(alm), m_out)
+    torch.cuda.synchronize()
+    p.close()
+    for b in (0, MB - 1):
+        for i in RINGS:
+            nr, st = orc.ring_info(NSIDE, i)[:2]
+            got = m_out[b, :, st:st + nr].cpu().numpy()
+            assert rel(got, orc.ring_alm2map(NSIDE, LMAX, alm[b], i)) < 2e-5, (b, i)
+
+
+def test_mixed_map2alm_sampled_orders(orc):
+    maps = W.random_maps(NSIDE, MB, 54)
+    p = dmwf.Plan(NSIDE, LMAX, MB)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    a_out = torch.zeros((MB, 3, NALM, 2), dtype=torch.float64, device="cuda")
+    p.map2alm(dev(maps), a_out)
+    ga = alm_host(a_out, (MB, 3, -1))
+    p.close()
+    for b in (0, MB - 1):
+        for m in ORDERS:
+            idx = [orc.almidx(LMAX, l, m) for l in range(m, LMAX + 1)]
+            ref = orc.map2alm_m(NSIDE, LMAX, maps[b], m)[:, m:]
+            assert rel(ga[b][:, idx], ref) < 2e-5, (b, m)
+
+
+def test_mixed_first_iteration_sampled_orders(orc):
+    """The first mixed iteration (float-float anchor at the start, one
+    tensor-core iteration) on the same data in every RHS, against the oracle's
+    a_1 = F_0 A t_0 on sampled orders."""
+    wl = W.make_workload("nside2048", [0])
+    d = (wl.noise[0] * wl.mask[None, :]).astype(np.float64)
+    p = dmwf.Plan(NSIDE, LMAX, MB)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    p.set_spectra(wl.cl)
+    p.set_noise_mask(wl.sigma, wl.mask)
+    p.set_schedule(lambda0=1000.0, n_levels=2, iters_per_level=0, check_every=1)
+    p.set_forced_iters([1, 0])
+    s = torch.zeros((MB, 3, NPIX), dtype=torch.float64, device="cuda")
+    a = torch.zeros((MB, 3, NALM, 2), dtype=torch.float64, device="cuda")
+    st, stats = p.wiener_filter(dev(np.broadcast_to(d[None], (MB,) + d.shape)), s, a)
+    assert stats[0]["iters_total"] == 1
+    ga = alm_host(a[0:1], (1, 3, -1))[0]
+    p.close()
+    th = orc.alpha(wl.sigma, wl.mask) * 4.0 * np.pi / NPIX
+    coef = orc.filter_coefs(LMAX, wl.cl, (1000.0 - 1.0) * th, th)
+    cols = np.zeros((3, NALM), dtype=np.complex128)
+    for m in ORDERS:
+        idx = [orc.almidx(LMAX, l, m) for l in range(m, LMAX + 1)]
+        cols[:, idx] = orc.map2alm_m(NSIDE, LMAX, d, m)[:, m:]
+    ref = orc.apply_filter(LMAX, coef, cols)
+    for m in ORDERS:
+        idx = [orc.almidx(LMAX, l, m) for l in range(m, LMAX + 1)]
+        assert rel(ga[:, idx], ref[:, idx]) < 1e-5, m
