@@ -170,7 +170,9 @@ cudaError_t enqueue_iteration(dm_plan *p, cudaStream_t st, cudaEvent_t *E) {
   if (E) cudaEventRecord(E[2], st);
   if ((e = legendre_synthesis(p, p->a, st))) return e;
   if (E) cudaEventRecord(E[3], st);
-  if ((e = p->cov ? cov_ring_stage(p, st) : ring_stage(p, RING_ITER, nullptr, p->s64, st))) return e;
+  if ((e = p->cov ? (p->prec == DM_FP64 ? cov_ring_stage(p, st) : cov_ring_stage32(p, st))
+                  : ring_stage(p, RING_ITER, nullptr, p->s64, st)))
+    return e;
   if (E) cudaEventRecord(E[4], st);
   if ((e = control_step(p, st))) return e;
   if (E) cudaEventRecord(E[5], st);
@@ -205,7 +207,7 @@ dm_status anchor(dm_plan *p, cudaStream_t st, bool initial, const double *d, boo
     if (!e) e = cudaMemcpyAsync(p->a_hi, p->a, an, cudaMemcpyDeviceToDevice, st);
     if (!e) e = legendre_synthesis(p, p->a_hi, st);
     if (!e) e = ring_stage(p, RING_INV_MAP, nullptr, p->s64, st);
-    if (!e) e = anchor_residual_wd(p, p->s64, st);
+    if (!e) e = p->cov ? anchor_residual_wd_cov(p, p->s64, st) : anchor_residual_wd(p, p->s64, st);
     p->launches += 3;
   }
   if (need_g) {
@@ -238,8 +240,6 @@ dm_status anchor(dm_plan *p, cudaStream_t st, bool initial, const double *d, boo
 }
 
 dm_status solve_begin(dm_plan *p, const double *d, cudaStream_t st) {
-  if (p->cov && p->prec != DM_FP64)
-    return fail(p, DM_EINVAL, "correlated noise (dm_set_noise_cov) runs in DM_FP64 or DM_FLOAT_FLOAT");
   // a tensor-core wait that gave up in an earlier solve does not count against this one
   if (p->tc_err) DM_CU(cudaMemsetAsync(p->tc_err, 0, sizeof(int), st), "clear wait flag");
   DM_CU(cudaMemsetAsync(p->a, 0, sizeof(double2) * 3 * p->nalm * p->batch, st), "zero a");

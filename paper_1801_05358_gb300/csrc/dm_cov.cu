@@ -89,6 +89,74 @@ __global__ void __launch_bounds__(256) k_cov_update(const RingDev *__restrict__ 
   }
 }
 
+// Mixed mode, between anchors: the state is the FP32 map Y e (s32), the full
+// map s = s_anchor + Y e (s_anchor in FP32 in shi32), and the data part
+// W (d - s_anchor) is carried in FP64 by the anchor, so the correction is
+// r = -W (Y e).  One block per (ring, RHS): Cauchy partials of s (the change
+// of Y e is the change of s), s32 <- the new Y e (from the inverse ring
+// transform, in sn), and r written over sn.  Finished RHS are left untouched.
+__global__ void __launch_bounds__(256) k_cov_update32(const RingDev *__restrict__ rings, float *__restrict__ s32,
+                                                      double *__restrict__ sn, const float *__restrict__ shi32,
+                                                      const double *__restrict__ wc, double *__restrict__ norms,
+                                                      const SolveState *__restrict__ state, int64_t npix,
+                                                      int nrings) {
+  const int r = blockIdx.x, b = blockIdx.y;
+  if (state[b].done) return;  // uniform over the block
+  const RingDev R = rings[r];
+  float acc[6] = {0, 0, 0, 0, 0, 0};  // per thread in FP32, the sums over threads in FP64
+  const int64_t base = (int64_t)b * 3 * npix;
+  for (int j = threadIdx.x; j < R.n; j += blockDim.x) {
+    const int64_t p = R.start + j;
+    float x[3];
+    for (int f = 0; f < 3; ++f) {
+      const int64_t i = base + f * npix + p;
+      const float v = (float)sn[i], dv = v - s32[i], full = shi32[i] + v;
+      acc[2 * f] += dv * dv;
+      acc[2 * f + 1] += full * full;
+      s32[i] = v;
+      x[f] = v;
+    }
+    const double *w = wc + 6 * p;
+    sn[base + p] = -(w[0] * x[0] + w[3] * x[1] + w[4] * x[2]);
+    sn[base + npix + p] = -(w[3] * x[0] + w[1] * x[1] + w[5] * x[2]);
+    sn[base + 2 * npix + p] = -(w[4] * x[0] + w[5] * x[1] + w[2] * x[2]);
+  }
+  __shared__ double red[8][6];
+  double a[6];
+  for (int k = 0; k < 6; ++k) {
+    a[k] = acc[k];
+    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+  }
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 6; ++k) red[threadIdx.x >> 5][k] = a[k];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double t = 0.0;
+    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) t += red[wv][threadIdx.x];
+    const int f = threadIdx.x >> 1, k = threadIdx.x & 1;
+    norms[(((int64_t)b * 3 + f) * nrings + r) * 2 + k] = t;
+  }
+}
+
+// An anchor's residual under correlated noise: r = W d - W s_hi (W d stored in
+// FP64 by cov_prepare_wd), shi32 = s_hi in FP32
+__global__ void k_anchor_resid_wd_cov(const double *__restrict__ wd, const double *__restrict__ s_hi,
+                                      const double *__restrict__ wc, double *__restrict__ r,
+                                      float *__restrict__ shi32, int64_t npix, int batch) {
+  const int64_t total = npix * batch;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / npix, p = i - b * npix, base = b * 3 * npix;
+    const double *w = wc + 6 * p;
+    const double x0 = s_hi[base + p], x1 = s_hi[base + npix + p], x2 = s_hi[base + 2 * npix + p];
+    r[base + p] = wd[base + p] - (w[0] * x0 + w[3] * x1 + w[4] * x2);
+    r[base + npix + p] = wd[base + npix + p] - (w[3] * x0 + w[1] * x1 + w[5] * x2);
+    r[base + 2 * npix + p] = wd[base + 2 * npix + p] - (w[4] * x0 + w[5] * x1 + w[2] * x2);
+    shi32[base + p] = (float)x0;
+    shi32[base + npix + p] = (float)x1;
+    shi32[base + 2 * npix + p] = (float)x2;
+  }
+}
+
 cudaError_t cov_prepare_wd(dm_plan *p, const double *d, cudaStream_t st) {
   k_wd_cov<<<2048, 256, 0, st>>>(d, p->wcov, p->wd, p->npix, p->batch);
   return cudaGetLastError();
@@ -104,6 +172,23 @@ cudaError_t cov_ring_stage(dm_plan *p, cudaStream_t st) {
                                                           p->state, p->npix, p->nrings);
   if ((e = cudaGetLastError())) return e;
   return ring_stage(p, RING_FWD_MAP, p->rhi, nullptr, st);
+}
+
+// The same in the mixed mode (FP32 ring transforms of the FP32 state; rhi,
+// which holds an anchor's residual only until that anchor's analysis, is the
+// scratch map between anchors)
+cudaError_t cov_ring_stage32(dm_plan *p, cudaStream_t st) {
+  cudaError_t e = ring_stage(p, RING_INV_MAP, nullptr, p->rhi, st);
+  if (e) return e;
+  k_cov_update32<<<dim3(p->nrings, p->batch), 256, 0, st>>>(p->rings, p->s32, p->rhi, p->shi32, p->wcov, p->norms,
+                                                            p->state, p->npix, p->nrings);
+  if ((e = cudaGetLastError())) return e;
+  return ring_stage(p, RING_FWD_MAP, p->rhi, nullptr, st);
+}
+
+cudaError_t anchor_residual_wd_cov(dm_plan *p, const double *s_hi, cudaStream_t st) {
+  k_anchor_resid_wd_cov<<<2048, 256, 0, st>>>(p->wd, s_hi, p->wcov, p->rhi, p->shi32, p->npix, p->batch);
+  return cudaGetLastError();
 }
 
 // Largest eigenvalue of a symmetric 3x3 matrix from the roots of its

@@ -296,6 +296,8 @@ cudaError_t control_step(dm_plan *p, cudaStream_t st);
 cudaError_t prepare_wd(dm_plan *p, const double *d, cudaStream_t st);
 cudaError_t cov_prepare_wd(dm_plan *p, const double *d, cudaStream_t st);  // dm_cov.cu
 cudaError_t cov_ring_stage(dm_plan *p, cudaStream_t st);
+cudaError_t cov_ring_stage32(dm_plan *p, cudaStream_t st);      // the mixed mode's (FP32 state)
+cudaError_t anchor_residual_wd_cov(dm_plan *p, const double *s_hi, cudaStream_t st);
 cudaError_t setup_fp32(dm_plan *p);
 cudaError_t ensure_ptab(dm_plan *p);  // the full FP32 tables, built on first use
 // first alm index of order m (m = mmax + 1 = lmax + 1 gives nalm): idx(l, m) = start(m) + l - m

@@ -1,9 +1,11 @@
 """Correlated 3x3 per-pixel noise with distinct temperature and polarisation
 masks (dm_set_noise_cov; Section 2.1 and Appendix B) against the oracle's
 orc_dm_solve_cov, through the C ABI: FP64 and float-float solves at the FP64
-bar (relative L2 <= 1e-10), batches, the free-running Cauchy schedule,
-constrained realisations (their conditional noise draws, Eq. 18 and 19) and
-the calls the mode rejects."""
+bar (relative L2 <= 1e-10) and mixed solves (FP32 ring stage with the 3x3
+weights per pixel, FP64-class anchors every few iterations) at the mixed bar
+1e-5, on the CUDA-core and the tensor-core Legendre stages; batches, the
+free-running Cauchy schedule, constrained realisations (their conditional
+noise draws, Eq. 18 and 19) and the calls the mode rejects."""
 import numpy as np
 import pytest
 
@@ -36,24 +38,29 @@ def _data(orc, wl):
 
 
 @pytest.mark.parametrize("nside,B,prec", [(8, 1, dmwf.DM_FP64), (16, 3, dmwf.DM_FP64),
-                                          (16, 2, dmwf.DM_FLOAT_FLOAT)])
+                                          (16, 2, dmwf.DM_FLOAT_FLOAT), (16, 2, dmwf.DM_MIXED_FP32),
+                                          (16, 8, dmwf.DM_MIXED_FP32)])
 def test_cov_fixed_schedule_matches_oracle(orc, nside, B, prec):
     wl = W.make_cov_workload(list(range(20, 20 + B)), nside, 2 * nside)
     d = _data(orc, wl)
     lam = W.lambda_schedule(1000.0, 4)
     p = _plan(wl, B, lambda0=1000.0, n_levels=4, iters_per_level=4)
     p.set_precision(prec)
+    bar = 1e-10
+    if prec == dmwf.DM_MIXED_FP32:
+        p.set_refinement(6)  # anchors inside the 16 iterations
+        bar = 1e-5
     s = torch.zeros((B, 3, wl.npix), dtype=torch.float64, device="cuda")
     a = torch.zeros((B, 3, (wl.lmax + 1) * (wl.lmax + 2) // 2, 2), dtype=torch.float64, device="cuda")
     st, stats = p.wiener_filter(dev(d), s, a)
     p.close()
     assert all(x["iters_total"] == 16 for x in stats)
     gs, ga = s.cpu().numpy(), alm_host(a, (B, 3, -1))
-    for b in range(B):
+    for b in range(0, B, max(1, B // 3)):
         ref = orc.dm_solve_cov(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d[b], lam,
                                forced_iters=[4, 4, 4, 4])
-        assert rel(gs[b], ref["s"]) < 1e-10
-        assert rel(ga[b], ref["alm"]) < 1e-10
+        assert rel(gs[b], ref["s"]) < bar
+        assert rel(ga[b], ref["alm"]) < bar
 
 
 def test_cov_cauchy_schedule_matches_oracle(orc):
@@ -81,9 +88,10 @@ def test_cov_rejections():
     with pytest.raises(RuntimeError):
         p.set_noise_cov(wl.sigma, bad, wl.mask, wl.mask_p)
     p.set_noise_cov(wl.sigma, wl.rho, wl.mask, wl.mask_p)
-    p.set_precision(dmwf.DM_MIXED_FP32)
-    d = torch.zeros((1, 3, wl.npix), dtype=torch.float64, device="cuda")
-    with pytest.raises(RuntimeError):
+    with pytest.raises(RuntimeError):  # the working resolution needs the diagonal model
+        p.set_progressive(0.25, 2)
+        p.set_schedule(lambda0=10.0, n_levels=2, iters_per_level=1)
+        d = torch.zeros((1, 3, wl.npix), dtype=torch.float64, device="cuda")
         p.wiener_filter(d, torch.zeros_like(d))
     p.close()
 
@@ -109,7 +117,7 @@ def test_cov_cr_inputs_match_oracle(orc):
         assert np.all(gd[b][0][wl.mask == 0] == 0.0) and np.all(gd[b][1:][:, wl.mask_p == 0] == 0.0)
 
 
-@pytest.mark.parametrize("prec", [dmwf.DM_FP64, dmwf.DM_FLOAT_FLOAT])
+@pytest.mark.parametrize("prec", [dmwf.DM_FP64, dmwf.DM_FLOAT_FLOAT, dmwf.DM_MIXED_FP32])
 def test_cov_constrained_realization_matches_oracle(orc, prec):
     """s_CR = W(d - dhat) + shat (Eq. 19) under correlated noise, one dual
     messenger run per realisation, against the oracle at the FP64 bar."""
@@ -119,6 +127,10 @@ def test_cov_constrained_realization_matches_oracle(orc, prec):
     seeds = [5, 6]
     p = _plan(wl, 2, lambda0=100.0, n_levels=3, iters_per_level=4)
     p.set_precision(prec)
+    bar = 1e-10
+    if prec == dmwf.DM_MIXED_FP32:
+        p.set_refinement(5)
+        bar = 1e-5
     s = torch.zeros((2, 3, wl.npix), dtype=torch.float64, device="cuda")
     a = torch.zeros((2, 3, (wl.lmax + 1) * (wl.lmax + 2) // 2, 2), dtype=torch.float64, device="cuda")
     st, stats = p.constrained_realization(dev(d), seeds, s, a)
@@ -127,5 +139,5 @@ def test_cov_constrained_realization_matches_oracle(orc, prec):
     for b, sd in enumerate(seeds):
         ref = orc.constrained_realization_cov(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d[b],
                                               sd, lam, forced_iters=[4, 4, 4])
-        assert rel(gs[b], ref["s_cr"]) < 1e-10
-        assert rel(ga[b], ref["alm_cr"]) < 1e-10
+        assert rel(gs[b], ref["s_cr"]) < bar
+        assert rel(ga[b], ref["alm_cr"]) < bar
