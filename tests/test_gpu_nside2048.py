@@ -158,6 +158,11 @@ def test_mixed_first_iteration_sampled_orders(orc):
         idx = [orc.almidx(LMAX, l, m) for l in range(m, LMAX + 1)]
         cols[:, idx] = orc.map2alm_m(NSIDE, LMAX, d, m)[:, m:]
     ref = orc.apply_filter(LMAX, coef, cols)
+    # the mixed state is FP32 between anchors: coefficients far below FP32's
+    # range (1e-88 at the highest orders after the lambda_0 = 1000 filter)
+    # flush to zero, so each order's error is taken against the largest order
+    # norm of the sample
+    scale = max(np.linalg.norm(ref[:, [orc.almidx(LMAX, l, m) for l in range(m, LMAX + 1)]]) for m in ORDERS)
     for m in ORDERS:
         idx = [orc.almidx(LMAX, l, m) for l in range(m, LMAX + 1)]
-        assert rel(ga[:, idx], ref[:, idx]) < 1e-5, m
+        assert np.linalg.norm(ga[:, idx] - ref[:, idx]) / scale < 1e-5, m
