@@ -10,9 +10,12 @@
 //               alone through a one-RHS view of the plan (its own noise, mask,
 //               alpha, filters, tolerance, data, and for a constrained
 //               realisation its Philox draws), including its first iteration;
-//   rounds    : every pool with busy slots advances iters_per_round dual
-//               messenger iterations on its own stream (pools overlap on the
-//               device); free or finished slots are skipped by the kernels;
+//   rounds    : every pool with busy slots and no round in flight enqueues
+//               iters_per_round dual messenger iterations on its own stream
+//               and a copy of its solver states behind them; the worker polls
+//               the rounds' events, so pools of different sizes run
+//               concurrently and a small pool is not held to a large one's
+//               pace; free or finished slots are skipped by the kernels;
 //   retirement: a slot whose last level met its stopping rule writes its map
 //               to the caller's buffer and frees the slot for the queue.
 // The messenger state of a request stays on the device from admission to
@@ -69,6 +72,11 @@ struct Pool {
   dm_plan *plan = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<Slot> slots;
+  // a round in flight: its iterations and the copy of the solver states into
+  // hs (pinned) are enqueued, done_ev is recorded after them
+  bool inflight = false;
+  cudaEvent_t done_ev = nullptr;
+  SolveState *hs = nullptr;
   int busy() const {
     int n = 0;
     for (auto &s : slots) n += s.busy ? 1 : 0;
@@ -209,6 +217,13 @@ dm_precision request_prec(const dm_server *S, const Request &r) {
   return (S->cfg.strict_tol > 0.0 && r.tol < S->cfg.strict_tol) ? S->cfg.strict_prec : S->cfg.prec;
 }
 
+void release_pool(Pool *q) {
+  if (q->done_ev) cudaEventDestroy(q->done_ev);
+  if (q->hs) cudaFreeHost(q->hs);
+  cudaStreamDestroy(q->stream);
+  dm_plan_destroy(q->plan);
+}
+
 // A new pool for r, or nullptr with *why = DM_ENOMEM when the budget (or the
 // device) has no room for it, else the status of the call that rejected r.
 Pool *make_pool(dm_server *S, const Request &r, dm_status *why) {
@@ -223,8 +238,7 @@ Pool *make_pool(dm_server *S, const Request &r, dm_status *why) {
       Pool *q = S->pools[i].get();
       if (q->busy() == 0) {
         S->used -= estimate_bytes(q->nside, q->lmax, slots, q->prec);
-        cudaStreamDestroy(q->stream);
-        dm_plan_destroy(q->plan);
+        release_pool(q);
         S->pools.erase(S->pools.begin() + i);
       } else {
         ++i;
@@ -258,6 +272,14 @@ Pool *make_pool(dm_server *S, const Request &r, dm_status *why) {
     *why = DM_ECUDA;
     return nullptr;
   }
+  if (cudaEventCreateWithFlags(&pool->done_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost(&pool->hs, sizeof(SolveState) * slots) != cudaSuccess) {
+    if (pool->done_ev) cudaEventDestroy(pool->done_ev);
+    cudaStreamDestroy(pool->stream);
+    dm_plan_destroy(p);
+    *why = DM_ECUDA;
+    return nullptr;
+  }
   pool->slots.resize(slots);
   k_mark_done<<<(slots + 127) / 128, 128, 0, pool->stream>>>(p->state, slots);
   p->session = true;
@@ -276,7 +298,9 @@ Pool *find_pool(dm_server *S, const Request &r, bool *full) {
   *full = false;
   for (auto &q : S->pools)
     if (q->nside == r.nside && q->lmax == r.lmax && q->cl_hash == h && q->prec == prec) {
-      if (q->busy() < (int)q->slots.size()) return q.get();
+      // a pool with a round in flight takes new requests when the round ends
+      // (setting a slot up waits on the pool's stream)
+      if (!q->inflight && q->busy() < (int)q->slots.size()) return q.get();
       *full = true;
     }
   return nullptr;
@@ -435,28 +459,31 @@ void worker_main(dm_server *S) {
         pool->slots[b].req.reset();
       }
     }
-    // ---- one round: every pool with busy slots advances N iterations
-    std::vector<Pool *> act;
-    for (auto &q : S->pools)
-      if (q->busy() > 0) act.push_back(q.get());
-    for (Pool *q : act)
+    // ---- rounds: every pool with busy slots and no round in flight starts
+    // one of N iterations; pools of different sizes run concurrently, each
+    // on its own stream, and each is retired as soon as its own round ends
+    bool progressed = !fresh.empty();
+    for (auto &qq : S->pools) {
+      Pool *q = qq.get();
+      if (q->inflight || q->busy() == 0) continue;
       for (int k = 0; k < N; ++k) enqueue_iteration(q->plan, q->stream, nullptr);
-    std::vector<std::vector<SolveState>> hs(act.size());
-    for (size_t i = 0; i < act.size(); ++i) {
-      hs[i].resize(act[i]->slots.size());
-      cudaMemcpyAsync(hs[i].data(), act[i]->plan->state, sizeof(SolveState) * hs[i].size(), cudaMemcpyDeviceToHost,
-                      act[i]->stream);
+      cudaMemcpyAsync(q->hs, q->plan->state, sizeof(SolveState) * q->slots.size(), cudaMemcpyDeviceToHost,
+                      q->stream);
+      cudaEventRecord(q->done_ev, q->stream);
+      q->inflight = true;
     }
-    for (Pool *q : act) cudaStreamSynchronize(q->stream);
-    S->rounds++;
-    // ---- retirement and anchors
-    for (size_t i = 0; i < act.size(); ++i) {
-      Pool *q = act[i];
+    // ---- retirement and anchors of the pools whose round has ended
+    for (auto &qq : S->pools) {
+      Pool *q = qq.get();
+      if (!q->inflight || cudaEventQuery(q->done_ev) != cudaSuccess) continue;
+      q->inflight = false;
+      progressed = true;
+      S->rounds++;
       for (int b = 0; b < (int)q->slots.size(); ++b) {
         Slot &sl = q->slots[b];
         if (!sl.busy) continue;
-        if (hs[i][b].done) {
-          slot_end(S, q, b, hs[i][b]);
+        if (q->hs[b].done) {
+          slot_end(S, q, b, q->hs[b]);
           continue;
         }
         sl.since_anchor += N;
@@ -467,6 +494,7 @@ void worker_main(dm_server *S) {
         }
       }
     }
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
 }
 
@@ -581,8 +609,8 @@ void dm_server_destroy(dm_server *S) {
   S->cv.notify_all();
   if (S->worker.joinable()) S->worker.join();
   for (auto &q : S->pools) {
-    cudaStreamDestroy(q->stream);
-    dm_plan_destroy(q->plan);
+    if (q->inflight) cudaEventSynchronize(q->done_ev);
+    release_pool(q.get());
   }
   delete S;
 }
