@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--lmax", type=int, default=None)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--fp64-steps", type=int, default=2,
+    ap.add_argument("--fp64-steps", type=int, default=10,
                     help="iterations of the plain FP64 GPU path timed beside (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-solve", action="store_true",
@@ -201,6 +201,24 @@ def oracle_data(O, nside, lmax, wl):
     """Data map of RHS 0 made on the host: the oracle's synthesis of the drawn
     signal plus the drawn noise, masked (no value from the CUDA path)."""
     return wl.data([O.alm2map(nside, lmax, wl.alm_true[0])])[0]
+
+
+def timed_single_steps(plan, d, nf, torch):
+    """Median device time (ms) of nf iterations, each timed on its own with
+    CUDA events after one warm-up iteration of the session."""
+    plan.solve_begin(d)
+    plan.solve_iterate(1)            # warm
+    times = []
+    for _ in range(nf):
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        f0.record()
+        plan.solve_iterate(1)
+        f1.record()
+        torch.cuda.synchronize()
+        times.append(f0.elapsed_time(f1))
+    plan.solve_end()
+    return float(np.median(times))
 
 
 def cpu_baseline(nside, lmax, wl, d0):
@@ -579,36 +597,19 @@ def main():
     if args.fp64_steps > 0 and prec != dmwf.DM_FP64:
         nf = args.fp64_steps
         real_schedule(nf)
-        plan.solve_begin(d)
-        plan.solve_iterate(1)            # warm
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        f0.record()
-        plan.solve_iterate(nf)
-        f1.record()
-        torch.cuda.synchronize()
-        plan.solve_end()
-        fms = f0.elapsed_time(f1)
-        fp64_line = {"value": B * nf / (fms * 1e-3), "unit": "DM iterations/s", "steps": nf,
-                     "ms_per_step": fms / nf}
+        fms = timed_single_steps(plan, d, nf, torch)
+        fp64_line = {"value": B / (fms * 1e-3), "unit": "DM iterations/s", "steps": nf,
+                     "ms_per_step": fms, "note": f"median of {nf} single timed iterations"}
     # ---- the float-float Legendre path (FP64-class results on the FP32 pipe) ----
     ff_line = None
     if args.fp64_steps > 0 and prec != dmwf.DM_FP64:
         nf = args.fp64_steps
         plan.set_precision(dmwf.DM_FLOAT_FLOAT)
         real_schedule(nf)
-        plan.solve_begin(d)
-        plan.solve_iterate(1)            # warm
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        f0.record()
-        plan.solve_iterate(nf)
-        f1.record()
-        torch.cuda.synchronize()
-        plan.solve_end()
-        fms = f0.elapsed_time(f1)
-        ff_line = {"value": B * nf / (fms * 1e-3), "unit": "DM iterations/s", "steps": nf,
-                   "ms_per_step": fms / nf, "precision": "DM_FLOAT_FLOAT"}
+        fms = timed_single_steps(plan, d, nf, torch)
+        ff_line = {"value": B / (fms * 1e-3), "unit": "DM iterations/s", "steps": nf,
+                   "ms_per_step": fms, "precision": "DM_FLOAT_FLOAT",
+                   "note": f"median of {nf} single timed iterations"}
     plan.set_tc_tiles({"auto": None, "stored": False, "generated": True}[args.tc_tiles])
     plan.set_precision(prec)
     tuning = None

@@ -267,7 +267,13 @@ Pool *make_pool(dm_server *S, const Request &r, dm_status *why) {
     return nullptr;
   }
   p->anchor_every = S->cfg.anchor_every > 0 ? S->cfg.anchor_every : 256;
-  if (cudaStreamCreateWithFlags(&pool->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  // Pools run their rounds concurrently; the strict-precision pools, whose
+  // requests are the long ones, take the higher stream priority so that the
+  // short rounds of the default pools fill the gaps instead of delaying them.
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  const int prio = (prec == S->cfg.strict_prec && S->cfg.strict_prec != S->cfg.prec) ? prio_hi : prio_lo;
+  if (cudaStreamCreateWithPriority(&pool->stream, cudaStreamNonBlocking, prio) != cudaSuccess) {
     dm_plan_destroy(p);
     *why = DM_ECUDA;
     return nullptr;

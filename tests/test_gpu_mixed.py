@@ -188,3 +188,31 @@ def test_tc_generated_tiles_solve(orc):
     for b in [0, 5]:
         ref = orc.dm_solve(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.mask, d[b], lam, forced_iters=[10] * 10)
         assert rel(got[b], ref["s"]) < 1e-5
+
+
+@pytest.mark.parametrize("B", [1, 8])
+def test_mixed_cauchy_partials_bounded(orc, B):
+    """The mixed mode sums each thread's Cauchy partials in FP32 (its maps are
+    FP32) and everything above in FP64.  Under a free-running schedule
+    (Cauchy 1e-2 -> 1e-4, checked every iteration) its per-level counts stay
+    within one iteration of the FP64 oracle's, and where the totals agree its
+    final Cauchy ratio within 1 % of the oracle's at that iteration: the FP32
+    partial sums move the stopping decisions by at most one step."""
+    wl = W.make_workload("nside16", list(range(11, 11 + B)), nside=32, lmax=64)
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(100.0, 3)
+    eps = W.eps_schedule(3, 1e-2, 1e-4)
+    p = make_plan(wl, B, lambda0=100.0, n_levels=3, iters_per_level=0, eps0=1e-2, eps_final=1e-4, eta=0.0,
+                  check_every=1)
+    p.set_precision(dmwf.DM_MIXED_FP32)
+    s = torch.zeros((B, 3, wl.npix), dtype=torch.float64, device="cuda")
+    st, stats = p.wiener_filter(dev(d), s)
+    p.close()
+    for b in range(0, B, max(1, B // 2)):
+        ref = orc.dm_solve(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.mask, d[b], lam, eps=eps)
+        got = list(stats[b]["iters_per_level"][:3])
+        want = list(ref["iters_per_level"])
+        assert all(abs(g - w) <= 1 for g, w in zip(got, want)), (got, want)
+        if sum(got) == sum(want):
+            c_ref = ref["cauchy"][sum(want) - 1]
+            assert abs(stats[b]["cauchy_final"] - c_ref) <= 1e-2 * c_ref, (stats[b]["cauchy_final"], c_ref)
