@@ -166,8 +166,8 @@ KERNEL_SOURCES = {
     "k_ring_iter": ["dm_ring.cu", "dm_fft.cuh"],
     "k_leg_syn64": ["dm_legendre.cu", "dm_rec.cuh"],
     "k_leg_ana64": ["dm_legendre.cu", "dm_rec.cuh"],
-    "k_syn_tc": ["dm_legendre_tc.cu", "dm_tc.cuh"],
-    "k_ana_tc": ["dm_legendre_tc.cu", "dm_tc.cuh"],
+    "k_syn_tc": ["dm_legendre_tc.cu", "dm_tc.cuh", "dm_tc_tiles.cuh"],
+    "k_ana_tc": ["dm_legendre_tc.cu", "dm_tc.cuh", "dm_tc_tiles.cuh"],
     "k_reduce": ["dm_legendre.cu"],
 }
 
@@ -693,6 +693,9 @@ def main():
                 if "bf16_tflops_sustained" in peaks else "fallback 1700 TFLOP/s sustained (of fallback)")
     mixed = prec != dmwf.DM_FP64
     use_tc = mixed and B in (8, 16, 32, 64)
+    # the tensor-core operand: generated tiles when asked, or by the library's size rule (stored tiles and
+    # their FP32 tables within 40 GiB; nside 1024 and above generate them)
+    gen_tiles = args.tc_tiles == "generated" or (args.tc_tiles == "auto" and nside >= 1024)
     # ring stage (k_ring<RING_ITER>, one launch per FFT-size class).
     # Algorithmic bytes (the map bytes of the hot-path scope): per pixel and
     # RHS-field w d (the anchor map in the mixed mode), s_prev and s, in the
@@ -741,9 +744,9 @@ def main():
     stages = {
         "ring": hbm_line("k_ring<RING_ITER> (one launch per FFT-size class)", ring_bytes, stage["ms_ring"],
                          "k_ring_iter", ring_impl_bytes),
-        "synthesis": leg_line("k_syn_b + k_syn_tc<0,1>" if use_tc else ("k_leg_syn32" if mixed else "k_leg_syn64"),
+        "synthesis": leg_line(("k_syn_b + k_syn_gen<0,1>" if gen_tiles else "k_syn_b + k_syn_tc<0,1>") if use_tc else ("k_leg_syn32" if mixed else "k_leg_syn64"),
                               stage["ms_synthesis"], "k_syn_tc" if use_tc else "k_leg_syn64"),
-        "analysis": leg_line("k_ana_tc<0,1>" if use_tc else ("k_leg_ana32" if mixed else "k_leg_ana64"),
+        "analysis": leg_line(("k_ana_gen<0,1>" if gen_tiles else "k_ana_tc<0,1>") if use_tc else ("k_leg_ana32" if mixed else "k_leg_ana64"),
                              stage["ms_analysis"], "k_ana_tc" if use_tc else "k_leg_ana64"),
         "reduce": hbm_line("k_ana_step_e32" if mixed else "k_ana_reduce", red_bytes, stage["ms_reduce"], "k_reduce"),
     }

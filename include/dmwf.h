@@ -264,7 +264,9 @@ dm_status dm_set_tc_tiles(dm_plan *plan, int generate);
  * with generated tiles): each stage call generates the tables of one slab of
  * orders m (FP64 recurrence, hi and lo in FP32) and contracts it before the
  * next.  bytes: the largest slab (default 1 GiB; at least one order m is
- * always taken).  Takes effect at the next stage call; DM_EINVAL for a null
+ * always taken).  By default a plan keeps the full tables instead when they
+ * fit in one slab, and in DM_FLOAT_FLOAT when they take at most 32 GiB;
+ * after this call only the first rule applies.  Takes effect at the next stage call; DM_EINVAL for a null
  * plan or bytes < 1, DM_EBUSY during a solve session. */
 dm_status dm_set_ff_slab_bytes(dm_plan *plan, int64_t bytes);
 

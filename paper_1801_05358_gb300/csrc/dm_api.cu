@@ -924,6 +924,7 @@ dm_status dm_set_ff_slab_bytes(dm_plan *p, int64_t bytes) {
   if (!p || bytes < 1) return DM_EINVAL;
   if (p->session) return DM_EBUSY;
   p->ffs_cap = bytes;
+  p->ffs_cap_set = true;
   if (p->ffs) cudaFree(p->ffs);
   if (p->ffs_lo) cudaFree(p->ffs_lo);
   p->ffs = p->ffs_lo = nullptr;

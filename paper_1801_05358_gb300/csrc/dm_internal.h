@@ -164,6 +164,7 @@ struct dm_plan {
   float *ffs = nullptr, *ffs_lo = nullptr;  // slab tables of the float-float stages
   std::vector<int> ffs_m;       // slab boundaries in m (first orders, then mmax + 1)
   int64_t ffs_cap = (int64_t)1 << 30;  // bytes of the largest slab (hi and lo)
+  bool ffs_cap_set = false;     // dm_set_ff_slab_bytes was called: slabs of that size, no full tables
   bool ff_legendre = false;     // DM_FLOAT_FLOAT: Legendre stages in float-float
   bool anchor_ff = true;        // mixed-mode anchors in float-float (else FP64)
   bool ff_now = false;          // inside a float-float anchor

@@ -306,8 +306,21 @@ static cudaError_t ff_slabs(dm_plan *p) {
   return cudaSuccess;
 }
 
+// Full tables instead of slabs when they are cheap to keep: when they fit in
+// one slab, and, unless the slab size was set (dm_set_ff_slab_bytes), in
+// DM_FLOAT_FLOAT (which reads them every iteration, not only at the mixed
+// mode's anchors) when they take at most 32 GiB.
+static cudaError_t ff_tables(dm_plan *p) {
+  if (p->ptab) return cudaSuccess;
+  const double full = 6.0 * sizeof(float) * (double)p->nalm * p->npairs;
+  if (full <= (double)p->ffs_cap || (p->ff_legendre && !p->ffs_cap_set && full <= 32.0 * (1u << 30)))
+    return ensure_ptab(p);
+  return cudaSuccess;
+}
+
 cudaError_t legendre_synthesis_ff(dm_plan *p, const double2 *alm, cudaStream_t st) {
   const SolveState *stp = p->state_active ? p->state : nullptr;
+  if (cudaError_t e = ff_tables(p)) return e;
   if (p->ptab) {
     dim3 g((p->batch + FF_NB - 1) / FF_NB, (p->npairs + FF_SYN_THREADS - 1) / FF_SYN_THREADS, p->mmax + 1);
     k_leg_syn_ff<FF_NB><<<g, FF_SYN_THREADS, 0, st>>>(p->ptab, p->ptab_lo, alm, p->rc, p->lmax, p->mmax, p->npairs,
@@ -332,6 +345,7 @@ cudaError_t legendre_synthesis_ff(dm_plan *p, const double2 *alm, cudaStream_t s
 // (chunk_waves); *used = the slots holding the sums
 cudaError_t legendre_analysis_ff_parts(dm_plan *p, cudaStream_t st, int *used) {
   const SolveState *stp = p->state_active ? p->state : nullptr;
+  if (cudaError_t e = ff_tables(p)) return e;
   if (p->ptab) {
     return chunk_waves(p, 0, p->mmax + 1, st, [&](int c0, int slot0, int n, int m0, int m1) {
       dim3 g((p->batch + FF_NB - 1) / FF_NB, n, m1 - m0);

@@ -162,8 +162,10 @@ size_t estimate_bytes(int nside, int lmax, int S, dm_precision prec) {
   const bool tc = prec == DM_MIXED_FP32 && dmwf::tc_batch_ok(S);
   const bool stored = tc && dmwf::tc_tables_fit(lmax, lmax, (int)npairs, S);
   if (prec != DM_FP64) {                         // DM_MIXED_FP32 and DM_FLOAT_FLOAT
-    if (stored || (prec == DM_MIXED_FP32 && !tc))
-      b += 3 * nalm * npairs * 4 * 2;            // FP32 tables, hi and lo
+    const double full = 3 * nalm * npairs * 4 * 2;  // FP32 tables, hi and lo
+    if (stored || (prec == DM_MIXED_FP32 && !tc) || (prec == DM_FLOAT_FLOAT && full <= 32.0 * (1u << 30)) ||
+        full <= (double)(1u << 30))
+      b += full;
     else
       b += (double)(1u << 30);                   // per-slab tables of the float-float stages
     b += S * 3 * (lmax + 1.0) * npairs * 2 * 8;  // rc32
