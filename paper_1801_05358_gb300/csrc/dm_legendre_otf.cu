@@ -256,21 +256,15 @@ __device__ __forceinline__ void convert_b_pq(int b, int ko, unsigned char *B1, u
 template <int N>
 __device__ __forceinline__ void put_vals(unsigned char *tile, uint32_t o, const float *x) {
   if (N == 1) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x[0]);
-    const __nv_bfloat16 l = __float2bfloat16_rn(x[0] - __bfloat162float(h));
-    *reinterpret_cast<__nv_bfloat16 *>(tile + o) = h;
-    *reinterpret_cast<__nv_bfloat16 *>(tile + ATILE + o) = l;
+    uint16_t h, l;
+    split1(x[0], h, l);
+    *reinterpret_cast<uint16_t *>(tile + o) = h;
+    *reinterpret_cast<uint16_t *>(tile + ATILE + o) = l;
   } else {
     constexpr int H = N > 1 ? N / 2 : 1;
     uint32_t h[H], l[H];
 #pragma unroll
-    for (int i = 0; i < N / 2; ++i) {
-      const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
-      const float2 hf = __bfloat1622float2(h2);
-      const __nv_bfloat162 l2 = __floats2bfloat162_rn(x[2 * i] - hf.x, x[2 * i + 1] - hf.y);
-      h[i] = *reinterpret_cast<const uint32_t *>(&h2);
-      l[i] = *reinterpret_cast<const uint32_t *>(&l2);
-    }
+    for (int i = 0; i < N / 2; ++i) split2(x[2 * i], x[2 * i + 1], h[i], l[i]);
     if (N == 2) {
       *reinterpret_cast<uint32_t *>(tile + o) = h[0];
       *reinterpret_cast<uint32_t *>(tile + ATILE + o) = l[0];
@@ -286,6 +280,12 @@ __device__ __forceinline__ void put_vals(unsigned char *tile, uint32_t o, const 
 
 __device__ __forceinline__ uint32_t arow(int row) { return (uint32_t)((row >> 3) * ASBO + (row & 7) * 16); }
 
+// Slot of the k-th staged coefficient: one slot of padding every 64, so that
+// lanes on different checkpoint blocks (64 targets apart) read different
+// bank groups.
+__device__ __forceinline__ int cpad(int k) { return k + (k >> 6); }
+__host__ __device__ inline int coef_slots(int LT) { return 256 * LT + 4 * LT + 1; }
+
 // One lane's share of a K step's A operand: the rows of parity PAR of
 // checkpoint block J (l0 = its first multipole, tile rows 32 q ..) for the
 // PPL ring pairs p0 .. p0 + PPL - 1, at byte offset obase of each row; f
@@ -296,8 +296,7 @@ template <int PART, bool DF, int PAR, int PPL>
 __device__ __forceinline__ void ana_task(unsigned char *At, int q, uint32_t obase, int l0, int lmax, int ls, int f,
                                          const float4 *__restrict__ ck0, const float4 *__restrict__ ck2,
                                          int64_t orow, const PairDev *__restrict__ pairs, int p0, int npairs,
-                                         const float4 *__restrict__ rq0, const float4 *__restrict__ rq2,
-                                         const float2 *__restrict__ rq2d, int64_t base) {
+                                         const float4 *sA, const float2 *sD, int tlo) {
   float v0[PPL], v1[PPL], sc[PPL];
   Xs xs[PPL];
   int Sk[PPL];
@@ -326,21 +325,21 @@ __device__ __forceinline__ void ana_task(unsigned char *At, int q, uint32_t obas
     const float z[PPL] = {};
     put_vals<PPL>(At, arow(32 * q + (t >> 1)) + obase, z);
   }
-  auto coef = [&](int l, float &c, float &k, float &b, float &d) {  // coefficients of target l + 1
+  auto coef = [&](int l, float &c, float &k, float &b, float &d) {  // coefficients of target l + 1 (shared memory)
+    const int q = cpad(l + 1 - tlo);
+    const float4 cf = sA[q];
     if (PART == 0) {
-      const float4 cf = rq0[base + l + 1];
       c = cf.x;
       k = 0.f;
       b = cf.y;
       d = cf.z;
     } else {
-      const float4 cf = rq2[base + l + 1];
       c = cf.x;
       k = f ? -cf.y : cf.y;
       b = cf.z;
       d = 0.f;
       if (DF) {
-        const float2 dd = rq2d[base + l + 1];
+        const float2 dd = sD[q];
         d = f ? dd.y : dd.x;
       }
     }
@@ -381,24 +380,24 @@ __device__ __forceinline__ void ana_task(unsigned char *At, int q, uint32_t obas
 template <int PART, bool DF, int PAR>
 __device__ __forceinline__ void ana_task_ppl(int PPL, unsigned char *At, int q, uint32_t obase, int l0, int lmax,
                                              int ls, int f, const float4 *ck0, const float4 *ck2, int64_t orow,
-                                             const PairDev *pairs, int p0, int npairs, const float4 *rq0,
-                                             const float4 *rq2, const float2 *rq2d, int64_t base) {
+                                             const PairDev *pairs, int p0, int npairs, const float4 *sA,
+                                             const float2 *sD, int tlo) {
   switch (PPL) {
     case 8:
-      ana_task<PART, DF, PAR, 8>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0, rq2, rq2d,
-                                 base);
+      ana_task<PART, DF, PAR, 8>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, sA, sD,
+                                 tlo);
       break;
     case 4:
-      ana_task<PART, DF, PAR, 4>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0, rq2, rq2d,
-                                 base);
+      ana_task<PART, DF, PAR, 4>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, sA, sD,
+                                 tlo);
       break;
     case 2:
-      ana_task<PART, DF, PAR, 2>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0, rq2, rq2d,
-                                 base);
+      ana_task<PART, DF, PAR, 2>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, sA, sD,
+                                 tlo);
       break;
     default:
-      ana_task<PART, DF, PAR, 1>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0, rq2, rq2d,
-                                 base);
+      ana_task<PART, DF, PAR, 1>(At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, sA, sD,
+                                 tlo);
   }
 }
 
@@ -428,6 +427,27 @@ __global__ void __launch_bounds__(AGEN_THREADS, 1) k_ana_gen(
   const int a_area = ((LT * nA * ATS) + 1023) & ~1023;
   const int stage = a_area + nA * 2 * tileB;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the recurrence coefficients of this CTA's multipoles, staged once: every
+  // worker walks the same range for every K step (targets tlo .. tlo + 256 nt - 1)
+  const int ncs = coef_slots(LT);
+  float4 *sA = reinterpret_cast<float4 *>(sm);
+  float2 *sD = reinterpret_cast<float2 *>(sm + 16 * ncs);
+  const int coef_bytes = ((ncs * (PART == 0 ? 16 : 24)) + 1023) & ~1023;
+  unsigned char *stg = sm + coef_bytes;
+  const int tlo = m + 256 * lt0 + 1;
+  {
+    const int64_t b0 = abase(lmax, m);
+    for (int k = tid; k < 256 * nt; k += blockDim.x) {
+      const int T = tlo + k;
+      if (T > lmax) break;
+      if (PART == 0) {
+        sA[cpad(k)] = rq0[b0 + T];
+      } else {
+        sA[cpad(k)] = rq2[b0 + T];
+        sD[cpad(k)] = rq2d[b0 + T];
+      }
+    }
+  }
   if (tid == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&full[i], 32);
@@ -463,7 +483,7 @@ __global__ void __launch_bounds__(AGEN_THREADS, 1) k_ana_gen(
     for (int c = warp; c < nsteps; c += S) {
       const int s = warp, k = c / S;
       if (k > 0 && !mbar_wait(&done[s], (k - 1) & 1, err)) break;
-      unsigned char *Ast = sm + s * stage, *Bst = Ast + a_area;
+      unsigned char *Ast = stg + s * stage, *Bst = Ast + a_area;
       // B operand of this K step
       if (PART == 0) {
         for (int task = lane; task < 2 * B; task += 32) {
@@ -491,18 +511,18 @@ __global__ void __launch_bounds__(AGEN_THREADS, 1) k_ana_gen(
         const int l0 = m + CKL * J;
         if (df) {
           if (par == 0)
-            ana_task_ppl<PART, true, 0>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0,
-                                        rq2, rq2d, base);
+            ana_task_ppl<PART, true, 0>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, sA,
+                                        sD, tlo);
           else
-            ana_task_ppl<PART, true, 1>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0,
-                                        rq2, rq2d, base);
+            ana_task_ppl<PART, true, 1>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, sA,
+                                        sD, tlo);
         } else {
           if (par == 0)
-            ana_task_ppl<PART, false, 0>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0,
-                                         rq2, rq2d, base);
+            ana_task_ppl<PART, false, 0>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, sA,
+                                         sD, tlo);
           else
-            ana_task_ppl<PART, false, 1>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, rq0,
-                                         rq2, rq2d, base);
+            ana_task_ppl<PART, false, 1>(PPL, At, q, obase, l0, lmax, ls, f, ck0, ck2, orow, pairs, p0, npairs, sA,
+                                         sD, tlo);
         }
       }
       fence_proxy_async();  // generic-proxy writes -> tensor-core reads
@@ -518,7 +538,7 @@ __global__ void __launch_bounds__(AGEN_THREADS, 1) k_ana_gen(
       const int s = c % S, k = c / S;
       if (!mbar_wait(&full[s], k & 1, err)) break;
       fence_after_sync();
-      const unsigned char *Ast = sm + s * stage, *Bst = Ast + a_area;
+      const unsigned char *Ast = stg + s * stage, *Bst = Ast + a_area;
       const uint32_t acc = c > 0 ? 1u : 0u;
       for (int j = 0; j < nt; ++j) {
         const uint32_t dj = tbase + (uint32_t)(j * NC);
@@ -955,14 +975,15 @@ cudaError_t ana_gen_launch(dm_plan *p, cudaStream_t st) {
     const int ltmax = std::max(1, std::min(part == 0 ? 4 : 2, 512 / (int)pow2_cols(NC)));
     const int LT = p->tune_ana_lt[part] > 0 ? std::min(p->tune_ana_lt[part], ltmax) : ltmax;
     const int stage = agen_stage_bytes(part, LT, B);
-    const int fit = (int)(((227u << 10) - 1024u) / (unsigned)stage);
+    const int coef_bytes = ((coef_slots(LT) * (part == 0 ? 16 : 24)) + 1023) & ~1023;
+    const int fit = (int)(((227u << 10) - 1024u - (unsigned)coef_bytes) / (unsigned)stage);
     const int want = p->tune_ana_S[part] > 0 ? p->tune_ana_S[part] : AGEN_MAX_S;
     const int S = std::max(1, std::min(want, std::min(fit, AGEN_MAX_S)));
     if (fit < 1) return cudaErrorInvalidConfiguration;
     p->ana_lt_used[part] = LT;
     p->ana_S_used[part] = S;
     const uint32_t nc = pow2_cols(LT * NC);
-    const size_t sm = tc_smem_n(stage, S, nc);
+    const size_t sm = tc_smem_n(stage, S, nc) + coef_bytes;
     dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
     if (part == 0) {
       cudaFuncSetAttribute(k_ana_gen<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
