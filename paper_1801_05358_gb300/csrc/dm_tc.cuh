@@ -162,26 +162,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// BF16 rounding on the integer pipe: the bits of a finite x rounded to
-// nearest (ties to even) at bit 16.  The upper half is the BF16 value and
-// r & 0xFFFF0000 the same value as an FP32.  (The conversion instructions run
-// on a narrow unit of this GPU; the tile generators convert every value they
-// produce, so they round with integer adds instead.)
-__device__ __forceinline__ uint32_t bf16_round_bits(float x) {
-  const uint32_t u = __float_as_uint(x);
-  return u + 0x7FFFu + ((u >> 16) & 1u);
-}
-
-// hi = rn_bf16(x), lo = rn_bf16(x - hi) for two values, packed as BF16x2
-// (x0 in the low half); x - hi is exact in FP32
-__device__ __forceinline__ void split2(float x0, float x1, uint32_t &h, uint32_t &l) {
-  const uint32_t r0 = bf16_round_bits(x0), r1 = bf16_round_bits(x1);
-  const float d0 = x0 - __uint_as_float(r0 & 0xFFFF0000u), d1 = x1 - __uint_as_float(r1 & 0xFFFF0000u);
-  h = __byte_perm(r0, r1, 0x7632);
-  l = __byte_perm(bf16_round_bits(d0), bf16_round_bits(d1), 0x7632);
-}
-
 // split 8 FP32 values into 8 BF16 hi and 8 BF16 lo packed as 16-byte rows
+// (packed conversions: two values per cvt.rn.bf16x2.f32; the widening back to
+// FP32 is exact)
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t &h, uint32_t &l) {
+  const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+  const float2 hf = __bfloat1622float2(h2);
+  const __nv_bfloat162 l2 = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+  h = *reinterpret_cast<const uint32_t *>(&h2);
+  l = *reinterpret_cast<const uint32_t *>(&l2);
+}
+
 __device__ __forceinline__ void split8(const float x[8], uint4 &hi, uint4 &lo) {
   uint32_t h[4], l[4];
 #pragma unroll
@@ -192,9 +183,10 @@ __device__ __forceinline__ void split8(const float x[8], uint4 &hi, uint4 &lo) {
 
 // split an FP32 value into BF16 hi + lo bit patterns (x ~ hi + lo to ~16 bits)
 __device__ __forceinline__ void split1(float x, uint16_t &hi, uint16_t &lo) {
-  const uint32_t r = bf16_round_bits(x);
-  hi = (uint16_t)(r >> 16);
-  lo = (uint16_t)(bf16_round_bits(x - __uint_as_float(r & 0xFFFF0000u)) >> 16);
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  hi = *reinterpret_cast<const uint16_t *>(&h);
+  lo = *reinterpret_cast<const uint16_t *>(&l);
 }
 
 }  // namespace tc
