@@ -148,7 +148,7 @@ size_t flat_smem(int N) { return sizeof(double2) * ((size_t)(N - 1) + 3 * (size_
 cudaError_t flat_synthesis(dm_plan *p, const double2 *alm, cudaStream_t st) {
   const int N = p->flatN;
   const size_t sm = flat_smem(N);
-  cudaError_t e = cudaFuncSetAttribute(k_flat_syn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = dyn_smem_allow(k_flat_syn, sm);
   if (e) return e;
   const int T = std::min(256, std::max(32, N / 4));
   k_flat_syn<<<dim3(N / 2, p->batch), dim3(T, 3), sm, st>>>(alm, p->rc, p->twid, N, p->mmax,
@@ -160,7 +160,7 @@ cudaError_t flat_synthesis(dm_plan *p, const double2 *alm, cudaStream_t st) {
 cudaError_t flat_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid) {
   const int N = p->flatN;
   const size_t sm = flat_smem(N);
-  cudaError_t e = cudaFuncSetAttribute(k_flat_ana, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = dyn_smem_allow(k_flat_ana, sm);
   if (e) return e;
   const int T = std::min(256, std::max(32, N / 4));
   const double h = p->flatL / N;

@@ -301,6 +301,16 @@ cudaError_t cov_ring_stage32(dm_plan *p, cudaStream_t st);      // the mixed mod
 cudaError_t anchor_residual_wd_cov(dm_plan *p, const double *s_hi, cudaStream_t st);
 cudaError_t setup_fp32(dm_plan *p);
 cudaError_t ensure_ptab(dm_plan *p);  // the full FP32 tables, built on first use
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`, never lowering it.  The limit is a process-wide attribute of
+// the function: set per launch, a smaller value set by a plan on another host
+// thread between this thread's set and launch would fail the launch; raised
+// monotonically under a lock, every launch of at most the granted size holds.
+cudaError_t dyn_smem_allow_fn(const void *func, size_t bytes);
+template <typename F>
+inline cudaError_t dyn_smem_allow(F *func, size_t bytes) {
+  return dyn_smem_allow_fn((const void *)func, bytes);
+}
 // first alm index of order m (m = mmax + 1 = lmax + 1 gives nalm): idx(l, m) = start(m) + l - m
 inline int64_t alm_start_h(int lmax, int m) { return (int64_t)m * (2 * lmax + 3 - m) / 2; }
 cudaError_t gen_tables32_slab(dm_plan *p, float *hi, float *lo, int m0, int m1, cudaStream_t st);                          // tables and buffers of DM_MIXED_FP32

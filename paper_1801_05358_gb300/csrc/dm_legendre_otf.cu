@@ -939,7 +939,7 @@ cudaError_t syn_gen_launch(dm_plan *p, bool run0, bool run1, cudaStream_t st) {
     const int ns = sgen_stages(p->tune_syn_ns[0], stage, nc);
     p->syn_ns_used[0] = ns;
     const size_t sm = tc_smem_n(stage, ns, nc);
-    cudaFuncSetAttribute(k_syn_gen<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dyn_smem_allow(k_syn_gen<0>, sm);
     k_syn_gen<0><<<g, 160, sm, st>>>(p->ck0, p->ck2, p->cko, p->rq0, p->rq2, p->rq2d, p->pairs, p->tc_synB[0], p->tc_soff,
                                      p->rc32, p->lmax, p->mmax, p->npairs, B, ns, nc, p->tc_err);
   }
@@ -949,7 +949,7 @@ cudaError_t syn_gen_launch(dm_plan *p, bool run0, bool run1, cudaStream_t st) {
     const int ns = sgen_stages(p->tune_syn_ns[1], stage, nc);
     p->syn_ns_used[1] = ns;
     const size_t sm = tc_smem_n(stage, ns, nc);
-    cudaFuncSetAttribute(k_syn_gen<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dyn_smem_allow(k_syn_gen<1>, sm);
     k_syn_gen<1><<<g, 160, sm, st>>>(p->ck0, p->ck2, p->cko, p->rq0, p->rq2, p->rq2d, p->pairs, p->tc_synB[1], p->tc_soff,
                                      p->rc32, p->lmax, p->mmax, p->npairs, B, ns, nc, p->tc_err);
   }
@@ -986,12 +986,12 @@ cudaError_t ana_gen_launch(dm_plan *p, cudaStream_t st) {
     const size_t sm = tc_smem_n(stage, S, nc) + coef_bytes;
     dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
     if (part == 0) {
-      cudaFuncSetAttribute(k_ana_gen<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      dyn_smem_allow(k_ana_gen<0>, sm);
       k_ana_gen<0><<<g, AGEN_THREADS, sm, st>>>(p->ck0, p->ck2, p->cko, p->rq0, p->rq2, p->rq2d, p->pairs, p->rc32,
                                                 p->apart32, p->lmax, p->mmax, p->npairs, p->nalm, B, LT, nc, S,
                                                 p->tc_err, p->tc_withhold);
     } else {
-      cudaFuncSetAttribute(k_ana_gen<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      dyn_smem_allow(k_ana_gen<1>, sm);
       k_ana_gen<1><<<g, AGEN_THREADS, sm, st>>>(p->ck0, p->ck2, p->cko, p->rq0, p->rq2, p->rq2d, p->pairs, p->rc32,
                                                 p->apart32, p->lmax, p->mmax, p->npairs, p->nalm, B, LT, nc, S,
                                                 p->tc_err, 0);

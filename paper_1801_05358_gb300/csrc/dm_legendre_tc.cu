@@ -599,7 +599,7 @@ cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t s
     const int ns = syn_stages_pick(p->tune_syn_ns[0], stage, nc);
     p->syn_ns_used[0] = ns;
     const size_t sm = tc_smem_n(stage, ns, nc);
-    cudaFuncSetAttribute(k_syn_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dyn_smem_allow(k_syn_tc<0>, sm);
     k_syn_tc<0><<<g, 128, sm, st>>>(p->tc_synA[0], p->tc_synB[0], p->tc_soff, p->rc32, p->lmax, p->mmax,
                                     p->npairs, B, ns, nc, p->tc_err);
   }
@@ -609,7 +609,7 @@ cudaError_t legendre_synthesis_tc(dm_plan *p, const double2 *alm, cudaStream_t s
     const int ns = syn_stages_pick(p->tune_syn_ns[1], stage, nc);
     p->syn_ns_used[1] = ns;
     const size_t sm = tc_smem_n(stage, ns, nc);
-    cudaFuncSetAttribute(k_syn_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dyn_smem_allow(k_syn_tc<1>, sm);
     k_syn_tc<1><<<g, 128, sm, st>>>(p->tc_synA[1], p->tc_synB[1], p->tc_soff, p->rc32, p->lmax, p->mmax,
                                     p->npairs, B, ns, nc, p->tc_err);
   }
@@ -657,7 +657,7 @@ cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st) {
     p->ana_S_used[0] = S;
     const size_t sm = tc_smem_n(stage, S, nc);
     dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
-    cudaFuncSetAttribute(k_ana_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dyn_smem_allow(k_ana_tc<0>, sm);
     k_ana_tc<0><<<g, ANA_THREADS, sm, st>>>(p->tc_anaA[0], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
                                             p->npairs, p->nalm, B, LT, nc, S, p->tc_err, p->tc_withhold);
   }
@@ -670,7 +670,7 @@ cudaError_t legendre_analysis_tc(dm_plan *p, cudaStream_t st) {
     p->ana_S_used[1] = S;
     const size_t sm = tc_smem_n(stage, S, nc);
     dim3 g((ltiles + LT - 1) / LT, 2, p->mmax + 1);
-    cudaFuncSetAttribute(k_ana_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dyn_smem_allow(k_ana_tc<1>, sm);
     k_ana_tc<1><<<g, ANA_THREADS, sm, st>>>(p->tc_anaA[1], p->tc_aoff, p->rc32, p->apart32, p->lmax, p->mmax,
                                             p->npairs, p->nalm, B, LT, nc, S, p->tc_err, 0);
   }

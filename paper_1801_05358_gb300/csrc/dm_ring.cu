@@ -676,7 +676,7 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
     const size_t smem = sizeof(C) * ((size_t)tw_words + ph_words + (size_t)G * lane_words);
     dim3 grid(paired ? rc_cls.pcount : rc_cls.count, (vlanes + G - 1) / G);
     dim3 block(T, G);
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = dyn_smem_allow(kern, smem);
     if (e != cudaSuccess) return e;
     const int *order = paired ? p->pair_order + rc_cls.poff : p->ring_order + rc_cls.off;
     // the fixed-size kernels read the Bluestein spectra transposed

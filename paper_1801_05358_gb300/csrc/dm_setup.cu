@@ -5,11 +5,28 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "dm_fft.cuh"
 #include "dm_internal.h"
 
 namespace dmwf {
+
+cudaError_t dyn_smem_allow_fn(const void *func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, size_t> granted;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t &g = granted[{dev, func}];
+  if (bytes <= g) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (!e) g = bytes;
+  return e;
+}
 
 // ---------------------------------------------------------------- geometry
 // Pair p joins northern ring i = p + 1 (1 <= i <= 2 nside) with its mirror.
@@ -553,7 +570,7 @@ cudaError_t build_tables(dm_plan *p) {
     if ((e = cudaMalloc(&ids, sizeof(int) * bl_ring.size()))) return e;
     cudaMemcpy(ids, bl_ring.data(), sizeof(int) * bl_ring.size(), cudaMemcpyHostToDevice);
     size_t smem = sizeof(double2) * (p->fft_M_max + p->fft_M_max / 32 + 1);  // slots spad(0..M-1)
-    cudaFuncSetAttribute(k_bhat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dyn_smem_allow(k_bhat, smem);
     k_bhat<<<(unsigned)bl_ring.size(), 256, smem>>>(p->rings, ids, p->phase, p->bhat, p->twid);
     k_chirp<<<(unsigned)bl_ring.size(), 256>>>(p->rings, ids, p->chirp);
     for (int lr = 3; lr <= 4 && !e; ++lr) {  // transposed copies for the fixed-size kernels of radix 2^lr
