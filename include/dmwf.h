@@ -410,7 +410,9 @@ typedef struct {
   int ring_lanes[DM_TUNE_MAX_CLASSES];
   int ring_fused[DM_TUNE_MAX_CLASSES];  /* fixed-size kernels: 1 = last inverse pass, messenger update and
                                            first forward pass fused in registers, 0 = separate passes,
-                                           -1 = default (separate) */
+                                           2 = separate passes with the FP32 radix-16 kernels of up to 2048
+                                           points compiled for 80 registers a thread (three blocks of 256
+                                           threads per SM; other launches take 0), -1 = default (separate) */
   int syn_stages[2];
   int ana_ltiles[2];
   int ana_stages[2];

@@ -221,7 +221,8 @@ struct dm_plan {
   int tune_ring_G[DM_TUNE_MAX_CLASSES];    // 0: heuristic lanes per block
   int ring_G_used[DM_TUNE_MAX_CLASSES];    // what the last iteration launch used
   int ring_lr_used[DM_TUNE_MAX_CLASSES];
-  int tune_ring_fuse[DM_TUNE_MAX_CLASSES];  // fixed-size kernels: 1 fused update pass (default), 0 separate
+  int tune_ring_fuse[DM_TUNE_MAX_CLASSES];  // fixed-size kernels: 1 fused update pass, 0 separate (default),
+                                            // 2 separate with the register-capped radix-16 kernels
   int ring_fuse_used[DM_TUNE_MAX_CLASSES];
   int tune_syn_ns[2] = {0, 0};             // k_syn_tc<PART> stages
   int tune_ana_lt[2] = {0, 0};             // k_ana_tc<PART> l tiles per CTA

@@ -192,8 +192,9 @@ __device__ __forceinline__ C dft_out(const C *buf, int k, int bluestein, const C
 // memory.  A lane works in place on M + 1 entries: the real-FFT packing and
 // unpacking handle k and h - k in the same thread.  Lanes of finished RHS
 // compute but write nothing.
-template <typename R, typename C, int MODE, bool COMPACT, int LOGM, int LR, bool FUSE = false>
-__global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) ? 2 : 1) k_ring(const RingDev *__restrict__ rings, const int *__restrict__ order,
+template <typename R, typename C, int MODE, bool COMPACT, int LOGM, int LR, bool FUSE = false, bool CAPREG = false>
+__global__ void __launch_bounds__(CAPREG ? 256 : 512,
+                                  CAPREG ? 3 : ((LR == 0 || (LR == 3 && sizeof(R) == 4)) ? 2 : 1)) k_ring(const RingDev *__restrict__ rings, const int *__restrict__ order,
                                               const C *__restrict__ phase, const C *__restrict__ bhat,
                                               const C *__restrict__ twid, int tw_words, int ph_words,
                                               int buf_words, int lane_words, int nlanes, C *__restrict__ rc,
@@ -591,16 +592,16 @@ __global__ void __launch_bounds__(512, (LR == 0 || (LR == 3 && sizeof(R) == 4)) 
 // Iteration launches of classes with one FFT size M in [512, 4096] take the
 // fixed-size kernel (LOGM = log2 M, radix 2^ring_lr, M / 2^ring_lr threads
 // per lane) unless the plan's ring_lr is 0.
-template <typename R, typename C, int MODE, int LR, bool FUSE>
+template <typename R, typename C, int MODE, int LR, bool FUSE, bool CAPREG = false>
 static void pick_fixed(int logm, void (*&kern)(const RingDev *, const int *, const C *, const C *, const C *, int,
                                                int, int, int, int, C *, int, int, int64_t, int, const double *,
                                                double *, R *, const R *, const R *, double *, const SolveState *,
                                                const R *, const C *)) {
   switch (logm) {
-    case 9: kern = k_ring<R, C, MODE, false, 9, LR, FUSE>; break;
-    case 10: kern = k_ring<R, C, MODE, false, 10, LR, FUSE>; break;
-    case 11: kern = k_ring<R, C, MODE, false, 11, LR, FUSE>; break;
-    default: kern = k_ring<R, C, MODE, false, 12, LR, FUSE>; break;
+    case 9: kern = k_ring<R, C, MODE, false, 9, LR, FUSE, CAPREG>; break;
+    case 10: kern = k_ring<R, C, MODE, false, 10, LR, FUSE, CAPREG>; break;
+    case 11: kern = k_ring<R, C, MODE, false, 11, LR, FUSE, CAPREG>; break;
+    default: kern = k_ring<R, C, MODE, false, 12, LR, FUSE, CAPREG>; break;
   }
 }
 
@@ -642,11 +643,18 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
         // separate passes unless tuned otherwise (measured faster on the
         // bench workload: the fused pass spills at the 64-register cap)
         const bool fuse = tcls && p->tune_ring_fuse[ci] == 1;
-        if (lr == 3)
+        // variant 2: the FP32 radix-16 kernels of up to 2048 points compiled
+        // for three blocks of 256 threads per SM (80 registers a thread)
+        // instead of 128 registers and two blocks
+        const bool cap = sizeof(R) == 4 && tcls && p->tune_ring_fuse[ci] == 2 && lr == 4 && logm <= 11;
+        if (lr == 3) {
           fuse ? pick_fixed<R, C, MODE, 3, true>(logm, kern) : pick_fixed<R, C, MODE, 3, false>(logm, kern);
-        else
+        } else if (cap) {
+          if constexpr (sizeof(R) == 4) pick_fixed<R, C, MODE, 4, false, true>(logm, kern);
+        } else {
           fuse ? pick_fixed<R, C, MODE, 4, true>(logm, kern) : pick_fixed<R, C, MODE, 4, false>(logm, kern);
-        if (tcls) p->ring_fuse_used[ci] = fuse ? 1 : 0;
+        }
+        if (tcls) p->ring_fuse_used[ci] = cap ? 2 : (fuse ? 1 : 0);
         T = rc_cls.M >> lr;
         tw_words = fftr_tw_words(logm, lr);
         tws = twr + p->twr_off[lr - 3][logm];
@@ -668,6 +676,7 @@ static cudaError_t launch_ring(dm_plan *p, const C *phase, const C *bhat, const 
         ++gmax;
       G = std::min(std::min(p->tune_ring_G[ci], gmax), vlanes);
     }
+    while (G > 1 && G * T > fa.maxThreadsPerBlock) --G;  // the register-capped kernels take 256 threads
     if (paired) G = std::max(2, G & ~1);
     if (MODE == RING_ITER && tcls) {
       p->ring_G_used[ci] = G;

@@ -42,7 +42,7 @@ void apply(dm_plan *p, const dm_tuning &t) {
     const int g = in ? t.ring_lanes[i] : 0;
     p->tune_ring_G[i] = (g >= 1 && g <= 16) ? g : 0;
     const int fu = in ? t.ring_fused[i] : -1;
-    p->tune_ring_fuse[i] = (fu == 0 || fu == 1) ? fu : -1;
+    p->tune_ring_fuse[i] = (fu >= 0 && fu <= 2) ? fu : -1;
   }
   for (int k = 0; k < 2; ++k) {
     p->tune_syn_ns[k] = (t.syn_stages[k] >= 2 && t.syn_stages[k] <= 8) ? t.syn_stages[k] : 0;
@@ -105,8 +105,9 @@ dm_status autotune(dm_plan *p, cudaStream_t st, std::string &err) {
       rs = DM_ECUDA;
       break;
     }
-    // a candidate is (radix, lanes per block, fused update pass); the
-    // generic kernels have no fused variant
+    // a candidate is (radix, lanes per block, pass variant: 1 fused update
+    // pass, 0 separate passes, 2 separate passes with the register-capped
+    // radix-16 kernels); the generic kernels have no variants
     auto used_now = [&]() {
       const int lr = p->ring_lr_used[ci];
       return std::array<int, 3>{lr, p->ring_G_used[ci], lr > 0 ? p->ring_fuse_used[ci] : 0};
@@ -116,8 +117,9 @@ dm_status autotune(dm_plan *p, cudaStream_t st, std::string &err) {
     std::vector<std::array<int, 3>> seen{bestc};
     const int lrs[3] = {3, 4, 0};
     for (int li = 0; li < 3; ++li)
-      for (int fu = 1; fu >= 0; --fu) {
-        if (lrs[li] == 0 && fu == 0) continue;
+      for (int fu : {1, 0, 2}) {
+        if (lrs[li] == 0 && fu != 1) continue;
+        if (fu == 2 && (lrs[li] != 4 || p->prec == DM_FP64)) continue;
         for (int g = 1; g <= 16; ++g) {
           p->tune_ring_lr[ci] = lrs[li];
           p->tune_ring_G[ci] = g;

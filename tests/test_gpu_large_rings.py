@@ -35,7 +35,7 @@ def _case(orc, nside, seeds):
     return wl, d
 
 
-def _run(orc, wl, d, iters, prec, lr=None):
+def _run(orc, wl, d, iters, prec, lr=None, tuning=None):
     B = d.shape[0]
     lam = W.lambda_schedule(1000.0, len(iters)) if len(iters) > 1 else np.array([1000.0])
     if len(iters) == 1:  # iters[0] iterations at lambda = 1000, none at lambda = 1
@@ -46,6 +46,8 @@ def _run(orc, wl, d, iters, prec, lr=None):
     p.set_precision(prec)
     if lr is not None:
         p.set_ring_radix(lr)
+    if tuning is not None:
+        p.set_tuning(tuning)
     s = torch.zeros((B, 3, wl.npix), dtype=torch.float64, device="cuda")
     a = torch.zeros((B, 3, (wl.lmax + 1) * (wl.lmax + 2) // 2, 2), dtype=torch.float64, device="cuda")
     st, stats = p.wiener_filter(dev(d), s, a)
@@ -72,6 +74,18 @@ def test_fp64_iterations_large_rings(orc, nside, iters, B, lr):
 def test_mixed_iterations_nside128(orc, lr):
     wl, d = _case(orc, 128, [80, 81])
     for es, ea in _run(orc, wl, d, [3, 3], dmwf.DM_MIXED_FP32, lr):
+        assert es < 1e-5 and ea < 1e-5, (es, ea)
+
+
+@pytest.mark.parametrize("nside", [128, 256])
+def test_mixed_iterations_register_capped_radix16(orc, nside):
+    """Tuning variant 2 (the FP32 radix-16 kernels compiled for 80 registers a
+    thread) on every class it serves: 512 points at nside 128, 512 and 1024
+    at nside 256; the generic classes keep their kernels."""
+    wl, d = _case(orc, nside, [82])
+    n = dmwf.DM_TUNE_MAX_CLASSES
+    tuning = {"ring_radix_lr": [4] * n, "ring_lanes": [0] * n, "ring_fused": [2] * n}
+    for es, ea in _run(orc, wl, d, [3, 3], dmwf.DM_MIXED_FP32, tuning=tuning):
         assert es < 1e-5 and ea < 1e-5, (es, ea)
 
 
