@@ -30,6 +30,8 @@
  *    that stream; a call returns once its work is enqueued unless it says it
  *    synchronises.  The caller owns every buffer it passes; the plan owns its
  *    workspace.  A plan is not thread-safe: one host thread at a time.
+ *    Distinct plans may be driven from different host threads at once, each
+ *    on its own stream.
  *
  * Errors: every call returns a dm_status.  DM_EINVAL for bad arguments (the
  * plan is left unchanged), DM_ECUDA for a CUDA failure, DM_ENOMEM when device
