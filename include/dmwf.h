@@ -106,8 +106,9 @@ typedef struct {
  *               A = Omega Y^T standing in for Y^T, as in the iteration);
  *  chi2       = (d - s)^T N^-1 (d - s) + a^T S^+ a  (Eq. 3; observed
  *               pixel-components only, S^+ the per-l pseudo-inverse).
- * Both are NaN when dm_set_diagnostics turned them off or under correlated
- * noise (dm_set_noise_cov).  For a constrained realisation they describe its
+ * Under correlated noise (dm_set_noise_cov) N^-1 is the per-pixel 3 x 3 block
+ * on the observed components.  Both are NaN when dm_set_diagnostics turned
+ * them off, and on flat-sky plans.  For a constrained realisation they describe its
  * Wiener-filter solve W(d - dhat).  ms_total is the device time of the call
  * (or from dm_solve_begin to dm_solve_end), diagnostics excluded. */
 typedef struct {

@@ -13,7 +13,9 @@
 //
 // Both reuse the FP64 (or float-float) stages of the plan: one ring analysis
 // of w d and one of the residual map w (d - Y a), where s = Y a is the final
-// map the solve already holds.  Sums run per block in FP64 and are added on
+// map the solve already holds.  Under correlated noise (Appendix B) w is the
+// 3 x 3 block W = alpha N^-1 of each pixel, and the data term of chi^2 is
+// formed from r = W (d - s) by the inverse of W's observed block.  Sums run per block in FP64 and are added on
 // the host in a fixed order.
 #include <math.h>
 
@@ -45,6 +47,70 @@ __global__ void __launch_bounds__(DG_THREADS) k_diag_resid_map(const double *__r
     const double ri = wd[off + i] - ww * s[off + i];
     r[off + i] = ri;
     if (ww > 0.0) acc += ri * ri / ww;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < DG_THREADS / 32; ++k) t += red[k];
+    part[(int64_t)b * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// r_o^T M^-1 r_o for the block M of the symmetric 3 x 3 w (xx, yy, zz, xy,
+// xz, yz) over the components o whose diagonal entry is positive (the
+// observed ones: masked components have zero rows and columns), by the
+// Cholesky factor of that block; 0 when none is observed.
+__device__ __forceinline__ double quad_inv_observed(const double *w, const double r[3]) {
+  int idx[3], k = 0;
+  for (int i = 0; i < 3; ++i)
+    if (w[i] > 0.0) idx[k++] = i;
+  auto W = [&](int a, int b) -> double {
+    if (a == b) return w[a];
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo == 0 ? (hi == 1 ? w[3] : w[4]) : w[5];
+  };
+  double L[3][3], y[3], out = 0.0;
+  for (int i = 0; i < k; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double v = W(idx[i], idx[j]);
+      for (int q = 0; q < j; ++q) v -= L[i][q] * L[j][q];
+      L[i][j] = (i == j) ? sqrt(v) : v / L[j][j];
+    }
+    double v = r[idx[i]];
+    for (int q = 0; q < i; ++q) v -= L[i][q] * y[q];
+    y[i] = v / L[i][i];
+    out += y[i] * y[i];
+  }
+  return out;
+}
+
+// The same under correlated noise (Appendix B): W = alpha N^-1 is a symmetric
+// 3 x 3 block per pixel (wc[p][6] = xx, yy, zz, xy, xz, yz, shared by every
+// RHS), r = W d - W s, and per block the sum over pixels of r_o^T W_oo^-1 r_o
+// over the observed components o; since r_o = W_oo (d - s)_o this is
+// alpha (d - s)^T N^-1 (d - s).  grid (DG_MAP_BLOCKS, batch).
+__global__ void __launch_bounds__(DG_THREADS) k_diag_resid_map_cov(const double *__restrict__ wd,
+                                                                   const double *__restrict__ wc,
+                                                                   const double *__restrict__ s,
+                                                                   double *__restrict__ r, int64_t npix,
+                                                                   double *__restrict__ part) {
+  __shared__ double red[DG_THREADS / 32];
+  const int b = blockIdx.y;
+  const int64_t off = (int64_t)b * 3 * npix;
+  double acc = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)DG_THREADS + threadIdx.x; p < npix; p += (int64_t)gridDim.x * DG_THREADS) {
+    const double *w = wc + 6 * p;
+    const double x0 = s[off + p], x1 = s[off + npix + p], x2 = s[off + 2 * npix + p];
+    double rr[3];
+    rr[0] = wd[off + p] - (w[0] * x0 + w[3] * x1 + w[4] * x2);
+    rr[1] = wd[off + npix + p] - (w[3] * x0 + w[1] * x1 + w[5] * x2);
+    rr[2] = wd[off + 2 * npix + p] - (w[4] * x0 + w[5] * x1 + w[2] * x2);
+    r[off + p] = rr[0];
+    r[off + npix + p] = rr[1];
+    r[off + 2 * npix + p] = rr[2];
+    acc += quad_inv_observed(w, rr);
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -179,7 +245,7 @@ cudaError_t diagnostics(dm_plan *p, cudaStream_t st, std::vector<double> &resid,
   const int B = p->batch;
   resid.assign(B, NAN);
   chi2.assign(B, NAN);
-  if (p->cov || !p->diag_tab) return cudaSuccess;  // diagonal noise only
+  if (!p->diag_tab) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   const size_t an = sizeof(double2) * 3 * (size_t)p->nalm * B;
   const int nm = p->mmax + 1;
@@ -211,8 +277,13 @@ cudaError_t diagnostics(dm_plan *p, cudaStream_t st, std::vector<double> &resid,
     p->ff_now = p->anchor_ff;
   }
   const int64_t n3 = 3 * p->npix;
-  // r = w (d - Y a) into tmpmap2, and the data term of chi^2
-  k_diag_resid_map<<<dim3(DG_MAP_BLOCKS, B), DG_THREADS, 0, st>>>(p->wd, p->w, p->s64, p->tmpmap2, n3, part_map);
+  // r = w (d - Y a) (W (d - Y a) under correlated noise) into tmpmap2, and
+  // the data term of chi^2
+  if (p->cov)
+    k_diag_resid_map_cov<<<dim3(DG_MAP_BLOCKS, B), DG_THREADS, 0, st>>>(p->wd, p->wcov, p->s64, p->tmpmap2,
+                                                                        p->npix, part_map);
+  else
+    k_diag_resid_map<<<dim3(DG_MAP_BLOCKS, B), DG_THREADS, 0, st>>>(p->wd, p->w, p->s64, p->tmpmap2, n3, part_map);
   e = cudaGetLastError();
   // den: A(w d)
   if (!e) e = ring_stage(p, RING_FWD_MAP, p->wd, nullptr, st);

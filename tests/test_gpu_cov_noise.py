@@ -63,6 +63,34 @@ def test_cov_fixed_schedule_matches_oracle(orc, nside, B, prec):
         assert rel(ga[b], ref["alm"]) < bar
 
 
+@pytest.mark.parametrize("prec,B,bar", [(dmwf.DM_FP64, 2, 1e-10), (dmwf.DM_MIXED_FP32, 8, 1e-5)])
+def test_cov_diagnostics_match_oracle(orc, prec, B, bar):
+    """The true residual and chi^2 in dm_stats under correlated noise with
+    distinct T/P masks, against orc_wf_residual_cov / orc_chi2_cov on the
+    oracle's own solve at the same counts (bars as for the diagonal model:
+    chi^2 relative, the residual absolute)."""
+    wl = W.make_cov_workload(list(range(50, 50 + B)), 16, 32)
+    d = _data(orc, wl)
+    lam = W.lambda_schedule(1000.0, 4)
+    p = _plan(wl, B, lambda0=1000.0, n_levels=4, iters_per_level=4)
+    p.set_precision(prec)
+    if prec == dmwf.DM_MIXED_FP32:
+        p.set_refinement(6)
+    s = torch.zeros((B, 3, wl.npix), dtype=torch.float64, device="cuda")
+    st, stats = p.wiener_filter(dev(d), s)
+    p.close()
+    for b in [0, B - 1]:
+        ref = orc.dm_solve_cov(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d[b], lam,
+                               forced_iters=[4, 4, 4, 4])
+        r_ref = orc.wf_residual_cov(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d[b],
+                                    ref["alm"])
+        c_ref = orc.chi2_cov(wl.nside, wl.lmax, wl.cl, wl.sigma, wl.rho, wl.mask, wl.mask_p, d[b], ref["s"],
+                             ref["alm"])
+        assert 1e-4 < r_ref < 1.0  # 16 iterations: far from converged, well away from zero
+        assert abs(stats[b]["true_resid"] - r_ref) < bar, (b, stats[b]["true_resid"], r_ref)
+        assert abs(stats[b]["chi2"] - c_ref) < bar * c_ref, (b, stats[b]["chi2"], c_ref)
+
+
 def test_cov_cauchy_schedule_matches_oracle(orc):
     """Free-running levels (Cauchy 1e-3 -> 1e-5): the same per-level counts."""
     wl = W.make_cov_workload([30], 8, 16)
