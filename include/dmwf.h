@@ -107,8 +107,9 @@ typedef struct {
  *  chi2       = (d - s)^T N^-1 (d - s) + a^T S^+ a  (Eq. 3; observed
  *               pixel-components only, S^+ the per-l pseudo-inverse).
  * Under correlated noise (dm_set_noise_cov) N^-1 is the per-pixel 3 x 3 block
- * on the observed components.  Both are NaN when dm_set_diagnostics turned
- * them off, and on flat-sky plans.  For a constrained realisation they describe its
+ * on the observed components.  On flat-sky plans S is the per-mode block
+ * (<|a_l|^2> = L^2 S) and Omega the pixel area.  Both are NaN when
+ * dm_set_diagnostics turned them off.  For a constrained realisation they describe its
  * Wiener-filter solve W(d - dhat).  ms_total is the device time of the call
  * (or from dm_solve_begin to dm_solve_end), diagnostics excluded. */
 typedef struct {

@@ -125,22 +125,26 @@ __global__ void __launch_bounds__(DG_THREADS) k_diag_resid_map_cov(const double 
 // Per (m, RHS) block, over l: mode 0 sums fac |C^1/2 g|^2 (den); mode 1 sums
 // fac |C^1/2 (g - alpha Omega C^+ a)|^2 (num) and fac a^T C^+ a (prior).
 // tab[l][DIAG_TAB_W] = C^1/2, C^+ and the range projector P, each (tt, te, ee,
-// bb).  grid (mmax+1, batch).
+// bb).  grid (mmax+1, batch).  Flat-sky plans (flatN = N > 0): the block is
+// the column kx = m of modes (kx, ky), ky = 0 .. N-1 stored at kx N + ky, the
+// table is per mode, and fac = 2 for kx > 0 stands for the Hermitian partner
+// (-kx, -ky) that is not stored.
 __global__ void __launch_bounds__(DG_THREADS) k_diag_alm(const double2 *__restrict__ g,
                                                          const double2 *__restrict__ a,
                                                          const double *__restrict__ tab,
                                                          const double *__restrict__ aomega, int lmax, int64_t nalm,
-                                                         int mode, double *__restrict__ part) {
+                                                         int mode, int flatN, double *__restrict__ part) {
   __shared__ double red[2][DG_THREADS / 32];
   const int m = blockIdx.x, b = blockIdx.y;
-  const int64_t base = dg_alm_base(lmax, m);
+  const int64_t base = flatN ? (int64_t)m * flatN : dg_alm_base(lmax, m);
+  const int lo = flatN ? 0 : m, hi = flatN ? flatN - 1 : lmax;
   const double fac = (m == 0) ? 1.0 : 2.0;
   const double ao = mode ? aomega[b] : 0.0;
   const double2 *gb = g + (int64_t)b * 3 * nalm + base;
   const double2 *ab = a + (int64_t)b * 3 * nalm + base;
   double acc = 0.0, pri = 0.0;
-  for (int l = m + threadIdx.x; l <= lmax; l += DG_THREADS) {
-    const double *h = tab + DIAG_TAB_W * (int64_t)l, *q = h + 4;
+  for (int l = lo + threadIdx.x; l <= hi; l += DG_THREADS) {
+    const double *h = tab + DIAG_TAB_W * (flatN ? base + l : (int64_t)l), *q = h + 4;
     double2 gt = gb[l], ge = gb[nalm + l], gbb = gb[2 * nalm + l];
     if (mode) {
       const double2 at = ab[l], ae = ab[nalm + l], abb = ab[2 * nalm + l];
@@ -202,40 +206,58 @@ void eig_sym2(double tt, double te, double ee, double &e1, double &e2, double &c
 
 }  // namespace
 
+// One table row: C^1/2, C^+ and the range projector of the block
+// [[tt, te], [te, ee]] and of bb, each as (tt, te, ee, bb).
+static void diag_row(double tt, double te, double ee, double bb, double *h) {
+  double e1, e2, c, s;
+  eig_sym2(tt, te, ee, e1, e2, c, s);
+  const double r1 = e1 > 0.0 ? sqrt(e1) : 0.0, r2 = e2 > 0.0 ? sqrt(e2) : 0.0;
+  const double i1 = e1 > 0.0 ? 1.0 / e1 : 0.0, i2 = e2 > 0.0 ? 1.0 / e2 : 0.0;
+  // f(C) = f(e1) v1 v1^T + f(e2) v2 v2^T, v1 = (c, s), v2 = (-s, c)
+  double *q = h + 4, *pr = h + 8;
+  h[0] = r1 * c * c + r2 * s * s;
+  h[1] = (r1 - r2) * c * s;
+  h[2] = r1 * s * s + r2 * c * c;
+  h[3] = bb > 0.0 ? sqrt(bb) : 0.0;
+  q[0] = i1 * c * c + i2 * s * s;
+  q[1] = (i1 - i2) * c * s;
+  q[2] = i1 * s * s + i2 * c * c;
+  q[3] = bb > 0.0 ? 1.0 / bb : 0.0;
+  const double p1 = e1 > 0.0 ? 1.0 : 0.0, p2 = e2 > 0.0 ? 1.0 : 0.0;
+  pr[0] = p1 * c * c + p2 * s * s;
+  pr[1] = (p1 - p2) * c * s;
+  pr[2] = p1 * s * s + p2 * c * c;
+  pr[3] = bb > 0.0 ? 1.0 : 0.0;
+}
+
+static cudaError_t upload_diag_tab(dm_plan *p, const std::vector<double> &t, size_t rows) {
+  cudaError_t e = cudaSuccess;
+  if (!p->diag_tab) {
+    e = cudaMalloc((void **)&p->diag_tab, sizeof(double) * DIAG_TAB_W * rows);
+    if (e) return e;
+    p->bytes += (int64_t)(sizeof(double) * DIAG_TAB_W * rows);
+  }
+  return cudaMemcpy(p->diag_tab, t.data(), sizeof(double) * DIAG_TAB_W * rows, cudaMemcpyHostToDevice);
+}
+
 // C^1/2, C^+ and the range projector per l on the host (FP64), uploaded
 // beside the spectra.
 cudaError_t diag_tables(dm_plan *p) {
   const int L = p->lmax + 1;
   std::vector<double> t(DIAG_TAB_W * (size_t)L, 0.0);
-  for (int l = 0; l < L; ++l) {
-    const double tt = p->cl_h[l], ee = p->cl_h[L + l], bb = p->cl_h[2 * L + l], te = p->cl_h[3 * L + l];
-    double e1, e2, c, s;
-    eig_sym2(tt, te, ee, e1, e2, c, s);
-    const double r1 = e1 > 0.0 ? sqrt(e1) : 0.0, r2 = e2 > 0.0 ? sqrt(e2) : 0.0;
-    const double i1 = e1 > 0.0 ? 1.0 / e1 : 0.0, i2 = e2 > 0.0 ? 1.0 / e2 : 0.0;
-    // f(C) = f(e1) v1 v1^T + f(e2) v2 v2^T, v1 = (c, s), v2 = (-s, c)
-    double *h = &t[DIAG_TAB_W * (size_t)l], *q = h + 4, *pr = h + 8;
-    h[0] = r1 * c * c + r2 * s * s;
-    h[1] = (r1 - r2) * c * s;
-    h[2] = r1 * s * s + r2 * c * c;
-    h[3] = bb > 0.0 ? sqrt(bb) : 0.0;
-    q[0] = i1 * c * c + i2 * s * s;
-    q[1] = (i1 - i2) * c * s;
-    q[2] = i1 * s * s + i2 * c * c;
-    q[3] = bb > 0.0 ? 1.0 / bb : 0.0;
-    const double p1 = e1 > 0.0 ? 1.0 : 0.0, p2 = e2 > 0.0 ? 1.0 : 0.0;
-    pr[0] = p1 * c * c + p2 * s * s;
-    pr[1] = (p1 - p2) * c * s;
-    pr[2] = p1 * s * s + p2 * c * c;
-    pr[3] = bb > 0.0 ? 1.0 : 0.0;
-  }
-  cudaError_t e = cudaSuccess;
-  if (!p->diag_tab) {
-    e = cudaMalloc((void **)&p->diag_tab, sizeof(double) * DIAG_TAB_W * (size_t)L);
-    if (e) return e;
-    p->bytes += (int64_t)(sizeof(double) * DIAG_TAB_W * (size_t)L);
-  }
-  return cudaMemcpy(p->diag_tab, t.data(), sizeof(double) * DIAG_TAB_W * (size_t)L, cudaMemcpyHostToDevice);
+  for (int l = 0; l < L; ++l)
+    diag_row(p->cl_h[l], p->cl_h[3 * L + l], p->cl_h[L + l], p->cl_h[2 * L + l], &t[DIAG_TAB_W * (size_t)l]);
+  return upload_diag_tab(p, t, (size_t)L);
+}
+
+// The same per mode of a flat-sky plan, from its spectra in the stored mode
+// order (cl[4][nmodes]: TT, EE, BB, TE).
+cudaError_t diag_tables_flat(dm_plan *p, const std::vector<double> &cl) {
+  const int64_t nm = p->nmodes;
+  std::vector<double> t(DIAG_TAB_W * (size_t)nm, 0.0);
+  for (int64_t k = 0; k < nm; ++k)
+    diag_row(cl[k], cl[3 * nm + k], cl[nm + k], cl[2 * nm + k], &t[DIAG_TAB_W * (size_t)k]);
+  return upload_diag_tab(p, t, (size_t)nm);
 }
 
 // The diagnostics of every RHS of the plan's final iterate (p->a, with
@@ -262,7 +284,8 @@ cudaError_t diagnostics(dm_plan *p, cudaStream_t st, std::vector<double> &resid,
     if ((e = cudaMalloc((void **)&p->diag_ao, sizeof(double) * B))) return e;
     p->bytes += (int64_t)(sizeof(double) * B);
   }
-  const double omega = 4.0 * M_PI / (double)p->npix;
+  const double hpix = p->flat ? p->flatL / p->flatN : 0.0;
+  const double omega = p->flat ? hpix * hpix : 4.0 * M_PI / (double)p->npix;  // Omega_p on a flat patch
   std::vector<double> ao(B);
   for (int b = 0; b < B; ++b) ao[b] = p->alpha[b] * omega;
   if ((e = cudaMemcpyAsync(p->diag_ao, ao.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st))) return e;
@@ -290,7 +313,7 @@ cudaError_t diagnostics(dm_plan *p, cudaStream_t st, std::vector<double> &resid,
   if (!e) e = legendre_analysis(p, ANA_PLAIN, p->diag_alm, st);
   if (!e) {
     k_diag_alm<<<dim3(nm, B), DG_THREADS, 0, st>>>(p->diag_alm, p->a, p->diag_tab, p->diag_ao, p->lmax, p->nalm, 0,
-                                                    part_den);
+                                                    p->flat ? p->flatN : 0, part_den);
     e = cudaGetLastError();
   }
   // num and prior: A(r) - alpha Omega C^+ a
@@ -298,7 +321,7 @@ cudaError_t diagnostics(dm_plan *p, cudaStream_t st, std::vector<double> &resid,
   if (!e) e = legendre_analysis(p, ANA_PLAIN, p->diag_alm, st);
   if (!e) {
     k_diag_alm<<<dim3(nm, B), DG_THREADS, 0, st>>>(p->diag_alm, p->a, p->diag_tab, p->diag_ao, p->lmax, p->nalm, 1,
-                                                    part_num);
+                                                    p->flat ? p->flatN : 0, part_num);
     e = cudaGetLastError();
   }
   p->prec = prec;
@@ -319,7 +342,8 @@ cudaError_t diagnostics(dm_plan *p, cudaStream_t st, std::vector<double> &resid,
       pri += h[2 * npart + ((size_t)b * nm + m) * 2 + 1];
     }
     resid[b] = den > 0.0 ? sqrt(num / den) : 0.0;
-    chi2[b] = dat / p->alpha[b] + pri;
+    // flat sky: the prior is a^H (L^2 S)^+ a, <|a_l|^2> = L^2 S per mode
+    chi2[b] = dat / p->alpha[b] + pri * (p->flat ? 1.0 / (p->flatL * p->flatL) : 1.0);
   }
   return cudaSuccess;
 }

@@ -235,6 +235,7 @@ dm_status dm_set_spectra_flat(dm_plan *p, const double *S) {
       cl[3 * nm + dst] = te;
     }
   cudaError_t e = cudaMemcpy(p->cl, cl.data(), sizeof(double) * 4 * nm, cudaMemcpyHostToDevice);
+  if (!e) e = diag_tables_flat(p, cl);  // the end-of-solve diagnostics' per-mode tables
   if (e) {
     p->err = "upload spectra";
     return DM_ECUDA;

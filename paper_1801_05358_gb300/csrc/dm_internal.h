@@ -410,6 +410,7 @@ dm_status autotune(dm_plan *p, cudaStream_t st, std::string &err);
 
 // end-of-solve diagnostics (dm_diag.cu)
 cudaError_t diag_tables(dm_plan *p);
+cudaError_t diag_tables_flat(dm_plan *p, const std::vector<double> &cl);  // per mode, cl[4][nmodes]
 cudaError_t diagnostics(dm_plan *p, cudaStream_t st, std::vector<double> &resid, std::vector<double> &chi2);
 
 }  // namespace dmwf

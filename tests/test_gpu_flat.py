@@ -7,7 +7,8 @@ oracle (oracle/flat.py), element by element through the C ABI:
   distinct temperature and polarisation masks, on grids of 64, 256 and
   1024 pixels (the paper's 1024^2, where the row transforms take the
   fixed-size ring kernels);
-- the free-running Cauchy schedule: the same per-level counts.
+- the free-running Cauchy schedule: the same per-level counts;
+- the end-of-solve true residual and chi^2 against the oracle's definitions.
 
 Layouts: the oracle's modes are [3, N, N] in numpy order (axis 0 = ky); the
 library keeps kx = 0 .. N/2 - 1 with every ky, [3, N/2, N].  Bar: the FP64
@@ -92,6 +93,29 @@ def test_flat_solve_matches_oracle(N, B):
         ref = F.dm_solve(d[b], wl.sigma, wl.mask_t, wl.mask_p, wl.S, wl.L, lam, forced_iters=counts)
         assert rel(gs[b], ref["s"]) < 1e-10
         assert rel(ga[b], _ours(ref["alm"])) < 1e-10
+
+
+def test_flat_diagnostics_match_oracle():
+    """The true residual and chi^2 in dm_stats of a flat-sky solve against the
+    flat oracle's definitions (flat.wf_residual, flat.chi2) on the oracle's
+    own solve at the same counts: the residual absolute, chi^2 relative, at
+    the FP64 bar."""
+    N, B = 64, 2
+    wl = W.make_flat_workload([11, 12], N=N)
+    d = np.stack(wl.data([F.synthesis(a, wl.L) for a in wl.alm_true]))
+    lam = W.lambda_schedule(1000.0, 3)
+    counts = [3, 3, 3]
+    p = _plan(wl, B, lambda0=1000.0, n_levels=3, iters_per_level=3, check_every=4)
+    s = torch.zeros((B, 3, N * N), dtype=torch.float64, device="cuda")
+    st, stats = p.wiener_filter(dev(d.reshape(B, 3, -1)), s)
+    p.close()
+    for b in range(B):
+        ref = F.dm_solve(d[b], wl.sigma, wl.mask_t, wl.mask_p, wl.S, wl.L, lam, forced_iters=counts)
+        r_ref = F.wf_residual(ref["alm"], d[b], wl.sigma, wl.mask_t, wl.mask_p, wl.S, wl.L)
+        c_ref = F.chi2(ref["alm"], d[b], wl.sigma, wl.mask_t, wl.mask_p, wl.S, wl.L)
+        assert 1e-4 < r_ref < 1.0  # 9 iterations: far from converged, well away from zero
+        assert abs(stats[b]["true_resid"] - r_ref) < 1e-10, (b, stats[b]["true_resid"], r_ref)
+        assert abs(stats[b]["chi2"] - c_ref) < 1e-10 * c_ref, (b, stats[b]["chi2"], c_ref)
 
 
 def test_flat_cauchy_schedule_matches_oracle():
