@@ -69,3 +69,18 @@ def test_whole_job_value_and_schedule_split():
     for k in [1, 7, 10, 256]:
         s = bench.iters_split(k)
         assert sum(s) == k and max(s) - min(s) <= 1 and len(s) == 10
+
+
+def test_single_thread_baseline_leg():
+    """The bench's single-core oracle leg: one iteration at a quarter of the
+    nside (here the nside 16 floor) in a child process with one OpenMP
+    thread, scaled by the ratio of (l, m, ring pair) triples."""
+    out = bench.single_thread_baseline(32, 64)
+    assert "error" not in out, out
+    assert out["cores"] == 1
+    assert out["seconds_per_iteration_sample"] > 0.0
+    ns, lm = 16, 32
+    triples = lambda n, l: (l + 1) * (l + 2) // 2 * 2 * n  # noqa: E731
+    scale = triples(32, 64) / triples(ns, lm)
+    assert out["value_extrapolated"] == pytest.approx(1.0 / (out["seconds_per_iteration_sample"] * scale))
+    assert "nside 16, lmax 32" in out["sample"]
