@@ -486,10 +486,17 @@ dm_status dm_measure_alu_peaks(double *fp64_tflops, double *fp32_tflops);
  * the complex conjugates of (-kx, -ky).  The pair is exact (F^dagger F = 1),
  * so the iteration is Algorithm 1 as printed.  Solves (dm_wiener_filter,
  * dm_wiener_filter_host, dm_solve_*), the transform stages (dm_alm2map,
- * dm_map2alm, the ring and column stages), the schedule calls and
- * dm_autotune work on it, in DM_FP64; the sphere-only calls (spectra per l,
- * HEALPix noise setters, constrained realisations, the Jacobi refinement,
- * dm_apply_filter, the diagnostics, which are NaN) return DM_EINVAL. */
+ * dm_map2alm, the ring and column stages), the schedule calls,
+ * dm_autotune, the end-of-solve diagnostics and constrained realisations
+ * (dm_constrained_realization, dm_draw_cr_inputs) work on it, in DM_FP64.
+ * Its constrained-realisation signal draw takes unit white-noise maps z
+ * instead of per-mode normals: for pixel p = y N + x, counters (p, 0, 2, 0)
+ * -> (I, Q) and (p, 1, 2, 0) -> (U, -), Box-Muller as at dm_draw_cr_inputs;
+ * ahat = (L/N) FFT2(z), unrotated, times the per-mode Cholesky factor of the
+ * TE block and sqrt(BB), zero on the Nyquist row (so <a a^H> = L^2 S); the
+ * noise draw is that of dm_draw_cr_inputs, zero on each masked component.
+ * The sphere-only calls (spectra per l, HEALPix noise setters, the Jacobi
+ * refinement, dm_apply_filter) return DM_EINVAL. */
 dm_status dm_plan_create_flat(int N, double L, int batch, dm_plan **out);
 /* Spectra per Fourier mode, host S[4][N][N] (TT, EE, BB, TE) in numpy FFT
  * order (axis 0 = ky, axis 1 = kx), <|a_l|^2> = L^2 C per mode; each 2x2 TE

@@ -721,12 +721,12 @@ dm_status dm_wiener_filter_host(dm_plan *p, const double *d_host, double *s_host
 
 dm_status dm_draw_cr_inputs(dm_plan *p, const uint64_t *seeds, double *ahat, double *shat, double *dhat,
                             void *stream) {
-  if (p && p->flat) return fail(p, DM_EINVAL, "constrained realisations are built for sphere plans");
   if (!p || !seeds) return DM_EINVAL;
   if (!p->have_cl || !p->have_noise) return fail(p, DM_EINVAL, "spectra and noise must be set");
   cudaStream_t st = (cudaStream_t)stream;
   DM_CU(cudaMemcpyAsync(p->seeds_dev, seeds, sizeof(uint64_t) * p->batch, cudaMemcpyHostToDevice, st), "seeds");
-  DM_CU(draw_signal(p, p->seeds_dev, p->tmpalm, st), "draw signal");
+  DM_CU(p->flat ? flat_draw_signal(p, p->seeds_dev, p->tmpalm, st) : draw_signal(p, p->seeds_dev, p->tmpalm, st),
+        "draw signal");
   DM_CU(legendre_synthesis(p, p->tmpalm, st), "synthesis");
   DM_CU(ring_stage(p, RING_INV_MAP, nullptr, p->tmpmap, st), "ring inverse");
   if (dhat) DM_CU(draw_noise_add(p, p->seeds_dev, p->tmpmap, dhat, st), "draw noise");
@@ -741,7 +741,6 @@ dm_status dm_draw_cr_inputs(dm_plan *p, const uint64_t *seeds, double *ahat, dou
 
 dm_status dm_constrained_realization(dm_plan *p, const double *d, const uint64_t *seeds, double *s_cr_out,
                                      double *alm_cr_out, dm_stats *stats, void *stream) {
-  if (p && p->flat) return fail(p, DM_EINVAL, "constrained realisations are built for sphere plans");
   dm_status r = check_ready(p);
   if (r != DM_OK) return r;
   if (!d || !seeds || !s_cr_out) return fail(p, DM_EINVAL, "null buffer");
@@ -750,7 +749,8 @@ dm_status dm_constrained_realization(dm_plan *p, const double *d, const uint64_t
   // shat -> tmpmap, ahat -> tmpalm, dhat -> tmpmap2, then tmpmap2 = d - dhat
   DM_CU(cudaEventRecord(p->ev_begin, st), "event");
   DM_CU(cudaMemcpyAsync(p->seeds_dev, seeds, sizeof(uint64_t) * p->batch, cudaMemcpyHostToDevice, st), "seeds");
-  DM_CU(draw_signal(p, p->seeds_dev, p->tmpalm, st), "draw signal");
+  DM_CU(p->flat ? flat_draw_signal(p, p->seeds_dev, p->tmpalm, st) : draw_signal(p, p->seeds_dev, p->tmpalm, st),
+        "draw signal");
   DM_CU(legendre_synthesis(p, p->tmpalm, st), "synthesis");
   DM_CU(ring_stage(p, RING_INV_MAP, nullptr, p->tmpmap, st), "ring inverse");
   DM_CU(draw_noise_add(p, p->seeds_dev, p->tmpmap, p->tmpmap2, st), "draw noise");

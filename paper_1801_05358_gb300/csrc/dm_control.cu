@@ -246,10 +246,12 @@ cudaError_t draw_signal(dm_plan *p, const uint64_t *seeds_dev, double2 *ahat, cu
   return cudaGetLastError();
 }
 
-// dhat = shat + sigma z on observed pixels, 0 on masked ones.
+// dhat = shat + sigma z on observed pixels, 0 on masked ones; with w given
+// (flat plans, whose temperature and polarisation masks differ) a component
+// is observed where its weight is positive.
 __global__ void k_draw_noise(const uint64_t *__restrict__ seeds, const double *__restrict__ sigma,
-                             const uint8_t *__restrict__ mask, const double *__restrict__ shat, double *dhat,
-                             int64_t npix) {
+                             const uint8_t *__restrict__ mask, const double *__restrict__ w,
+                             const double *__restrict__ shat, double *dhat, int64_t npix) {
   const int b = blockIdx.y;
   const uint64_t seed = seeds[b];
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
@@ -260,7 +262,8 @@ __global__ void k_draw_noise(const uint64_t *__restrict__ seeds, const double *_
     const double zz[3] = {z01.x, z01.y, z2.x};
     for (int f = 0; f < 3; ++f) {
       const int64_t i = o + f * npix;
-      dhat[i] = obs ? shat[i] + sigma[i] * zz[f] : 0.0;
+      const bool ob = (w != nullptr) ? (w[i] > 0.0) : obs;
+      dhat[i] = ob ? shat[i] + sigma[i] * zz[f] : 0.0;
     }
   }
 }
@@ -286,13 +289,35 @@ __global__ void k_draw_noise_cov(const uint64_t *__restrict__ seeds, const doubl
   }
 }
 
+// Unit white-noise maps z [batch][3][npix] for the flat constrained-realisation
+// signal draw: per RHS seed and pixel p, the pair (p, 0, 2) gives the I and Q
+// values and the first normal of (p, 1, 2) the U value (the third counter word
+// is 0 for the sphere's signal draw and 1 for the noise draws).
+__global__ void k_white_maps(const uint64_t *__restrict__ seeds, double *__restrict__ z, int64_t npix) {
+  const int b = blockIdx.y;
+  const uint64_t seed = seeds[b];
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+    const double2 z01 = gauss2(seed, (unsigned)p, 0u, 2u);
+    const double2 z2 = gauss2(seed, (unsigned)p, 1u, 2u);
+    const int64_t o = (int64_t)b * 3 * npix + p;
+    z[o] = z01.x;
+    z[o + npix] = z01.y;
+    z[o + 2 * npix] = z2.x;
+  }
+}
+
+cudaError_t draw_white_maps(dm_plan *p, const uint64_t *seeds_dev, double *z, cudaStream_t st) {
+  k_white_maps<<<dim3(256, p->batch), 256, 0, st>>>(seeds_dev, z, p->npix);
+  return cudaGetLastError();
+}
+
 cudaError_t draw_noise_add(dm_plan *p, const uint64_t *seeds_dev, const double *shat, double *dhat,
                            cudaStream_t st) {
   dim3 g(1024, p->batch);
   if (p->cov)
     k_draw_noise_cov<<<g, 256, 0, st>>>(seeds_dev, p->covdraw, p->w, shat, dhat, p->npix);
   else
-    k_draw_noise<<<g, 256, 0, st>>>(seeds_dev, p->sigma, p->mask, shat, dhat, p->npix);
+    k_draw_noise<<<g, 256, 0, st>>>(seeds_dev, p->sigma, p->mask, p->flat ? p->w : nullptr, shat, dhat, p->npix);
   return cudaGetLastError();
 }
 

@@ -90,6 +90,24 @@ __global__ void __launch_bounds__(768) k_flat_ana(const double2 *__restrict__ rc
     double2 aB = make_double2(w * (-g1.x * s + g2.x * c), w * (-g1.y * s + g2.y * c));
     const int64_t mode = (int64_t)kx * N + ky;
     double2 *o = out + (int64_t)b * 3 * nmodes + mode;
+    if (epilogue == ANA_FLAT_DRAW) {
+      // the signal draw of a constrained realisation: the 2-D FFT of white
+      // noise maps, unrotated and scaled by L/N (passed as omega), times the
+      // per-mode Cholesky factor of the TE block and sqrt(BB) (filt holds the
+      // spectra, [4][nmodes]: TT, EE, BB, TE), so that <a a^H> = L^2 S
+      const double tt = filt[mode], ee = filt[nmodes + mode], bb = filt[2 * nmodes + mode],
+                   te = filt[3 * nmodes + mode];
+      const double l11 = sqrt(fmax(tt, 0.0));
+      const double l21 = (l11 > 0.0) ? te / l11 : 0.0;
+      const double l22 = sqrt(fmax(ee - l21 * l21, 0.0));
+      const double lbb = sqrt(fmax(bb, 0.0));
+      const double2 h0 = make_double2(w * g0.x, w * g0.y), h1 = make_double2(w * g1.x, w * g1.y),
+                    h2 = make_double2(w * g2.x, w * g2.y);
+      o[0] = make_double2(l11 * h0.x, l11 * h0.y);
+      o[nmodes] = make_double2(l21 * h0.x + l22 * h1.x, l21 * h0.y + l22 * h1.y);
+      o[2 * nmodes] = make_double2(lbb * h2.x, lbb * h2.y);
+      continue;
+    }
     if (epilogue == ANA_DM_STEP) {
       const double *cf = filt + ((int64_t)state[b].level * nmodes + mode) * 4;
       const double2 t = cadd(o[0], aT), e = cadd(o[nmodes], aE), bb = cadd(o[2 * nmodes], aB);
@@ -164,11 +182,25 @@ cudaError_t flat_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t s
   if (e) return e;
   const int T = std::min(256, std::max(32, N / 4));
   const double h = p->flatL / N;
-  const SolveState *stp = (epilogue == ANA_DM_STEP || p->state_active) ? p->state : nullptr;
-  k_flat_ana<<<dim3(N / 2, p->batch), dim3(T, 3), sm, st>>>(p->rc, out, p->twid, N, p->mmax, h * h, epilogue,
-                                                            p->filt, p->nmodes, stp);
+  const bool draw = epilogue == ANA_FLAT_DRAW;
+  const SolveState *stp = (epilogue == ANA_DM_STEP || (p->state_active && !draw)) ? p->state : nullptr;
+  k_flat_ana<<<dim3(N / 2, p->batch), dim3(T, 3), sm, st>>>(p->rc, out, p->twid, N, p->mmax, draw ? h : h * h,
+                                                            epilogue, draw ? p->cl : p->filt, p->nmodes, stp);
   if (mid) cudaEventRecord(mid, st);
   return cudaGetLastError();
+}
+
+// a_hat of a constrained realisation on a flat plan: white noise maps z,
+// their row transforms (the ring kernels) and the draw epilogue of the column
+// transforms, into ahat [batch][3][nmodes].  The maps pass through tmpmap.
+cudaError_t flat_draw_signal(dm_plan *p, const uint64_t *seeds_dev, double2 *ahat, cudaStream_t st) {
+  cudaError_t e = draw_white_maps(p, seeds_dev, p->tmpmap, st);
+  const bool sa = p->state_active;
+  p->state_active = false;
+  if (!e) e = ring_stage(p, RING_FWD_MAP, p->tmpmap, nullptr, st);
+  if (!e) e = flat_analysis(p, ANA_FLAT_DRAW, ahat, st, nullptr);
+  p->state_active = sa;
+  return e;
 }
 
 }  // namespace dmwf

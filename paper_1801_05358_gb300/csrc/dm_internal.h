@@ -287,7 +287,11 @@ cudaError_t rc_from_public(dm_plan *p, const double2 *pub, cudaStream_t st);
 // Legendre stages on the plan's rc buffer
 cudaError_t legendre_synthesis(dm_plan *p, const double2 *alm, cudaStream_t st);
 // analysis into apart, then reduce: out = (accumulate ? a_prev : 0) + Omega sum, then filter
-enum AnaEpilogue { ANA_PLAIN = 0, ANA_DM_STEP = 1 };
+enum AnaEpilogue {
+  ANA_PLAIN = 0,
+  ANA_DM_STEP = 1,
+  ANA_FLAT_DRAW = 2  // flat sky only: the constrained-realisation signal draw (dm_flat.cu)
+};
 cudaError_t legendre_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t st, cudaEvent_t mid = nullptr);
 cudaError_t apply_filter_level(dm_plan *p, const double *coef, const double2 *in, double2 *out, cudaStream_t st);
 cudaError_t build_filter_one(dm_plan *p, double lambda, double th, double *coef, cudaStream_t st);
@@ -376,6 +380,8 @@ dm_status run_dm(dm_plan *p, const double *d, cudaStream_t st);
 
 // constrained realisations
 cudaError_t draw_signal(dm_plan *p, const uint64_t *seeds_dev, double2 *ahat, cudaStream_t st);
+cudaError_t draw_white_maps(dm_plan *p, const uint64_t *seeds_dev, double *z, cudaStream_t st);
+cudaError_t flat_draw_signal(dm_plan *p, const uint64_t *seeds_dev, double2 *ahat, cudaStream_t st);
 cudaError_t draw_noise_add(dm_plan *p, const uint64_t *seeds_dev, const double *shat, double *dhat,
                            cudaStream_t st);
 cudaError_t axpy_maps(int64_t n, const double *x, double alpha, double *y, cudaStream_t st);

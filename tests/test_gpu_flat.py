@@ -8,7 +8,9 @@ oracle (oracle/flat.py), element by element through the C ABI:
   1024 pixels (the paper's 1024^2, where the row transforms take the
   fixed-size ring kernels);
 - the free-running Cauchy schedule: the same per-level counts;
-- the end-of-solve true residual and chi^2 against the oracle's definitions.
+- the end-of-solve true residual and chi^2 against the oracle's definitions;
+- constrained realisations (the drawn inputs and the whole realisation),
+  with the oracle fed the same Philox normals.
 
 Layouts: the oracle's modes are [3, N, N] in numpy order (axis 0 = ky); the
 library keeps kx = 0 .. N/2 - 1 with every ky, [3, N/2, N].  Bar: the FP64
@@ -132,6 +134,54 @@ def test_flat_cauchy_schedule_matches_oracle():
     p.close()
     assert list(stats[0]["iters_per_level"][:3]) == list(ref["iters_per_level"])
     assert rel(s.cpu().numpy().reshape(3, N, N), ref["s"]) < 1e-10
+
+
+def _flat_normals(orc, seed, N):
+    """The unit normals the library draws for a flat constrained realisation,
+    from the oracle's own Philox4x32-10 and Box-Muller (orc_gauss_pair):
+    per pixel p = y N + x, signal maps (I, Q) from counter (p, 0, 2) and U
+    from (p, 1, 2); noise (I, Q) from (p, 0, 1) and U from (p, 1, 1)."""
+    zs = np.zeros((3, N * N))
+    zn = np.zeros((3, N * N))
+    for q in range(N * N):
+        zs[0, q], zs[1, q] = orc.gauss_pair(seed, q, 0, 2)
+        zs[2, q] = orc.gauss_pair(seed, q, 1, 2)[0]
+        zn[0, q], zn[1, q] = orc.gauss_pair(seed, q, 0, 1)
+        zn[2, q] = orc.gauss_pair(seed, q, 1, 1)[0]
+    return zs.reshape(3, N, N), zn.reshape(3, N, N)
+
+
+def test_flat_constrained_realization_matches_oracle(orc):
+    """Constrained realisations on the flat patch (Section 2.2, Eq. 19): the
+    drawn inputs (a_hat, s_hat, d_hat) at 1e-12 and the whole realisation at
+    the oracle's per-level counts at 1e-10, distinct T/P masks, 2 RHS."""
+    N, B = 64, 2
+    seeds = [501, 502]
+    wl = W.make_flat_workload([13, 14], N=N)
+    d = np.stack(wl.data([F.synthesis(a, wl.L) for a in wl.alm_true]))
+    lam = W.lambda_schedule(1000.0, 3)
+    counts = [3, 3, 3]
+    p = _plan(wl, B, lambda0=1000.0, n_levels=3, iters_per_level=3, check_every=4)
+    ah = torch.zeros((B, 3, N * N // 2, 2), dtype=torch.float64, device="cuda")
+    sh = torch.zeros((B, 3, N * N), dtype=torch.float64, device="cuda")
+    dh = torch.zeros((B, 3, N * N), dtype=torch.float64, device="cuda")
+    p.draw_cr_inputs(seeds, ahat=ah, shat=sh, dhat=dh)
+    s = torch.zeros((B, 3, N * N), dtype=torch.float64, device="cuda")
+    a = torch.zeros((B, 3, N * N // 2, 2), dtype=torch.float64, device="cuda")
+    st, stats = p.constrained_realization(dev(d.reshape(B, 3, -1)), seeds, s, a)
+    p.close()
+    g_ah, g_sh, g_dh = _alm_of(ah, B, N), sh.cpu().numpy().reshape(B, 3, N, N), dh.cpu().numpy().reshape(B, 3, N, N)
+    gs, ga = s.cpu().numpy().reshape(B, 3, N, N), _alm_of(a, B, N)
+    for b in range(B):
+        zs, zn = _flat_normals(orc, seeds[b], N)
+        ref = F.constrained_realization(d[b], zs, zn, wl.sigma, wl.mask_t, wl.mask_p, wl.S, wl.L, lam,
+                                        forced_iters=counts)
+        assert rel(g_ah[b], _ours(ref["a_hat"])) < 1e-12
+        assert rel(g_sh[b], ref["s_hat"]) < 1e-12
+        assert rel(g_dh[b], ref["d_hat"]) < 1e-12
+        assert stats[b]["iters_per_level"][:3] == counts
+        assert rel(gs[b], ref["s_cr"]) < 1e-10
+        assert rel(ga[b], _ours(ref["alm_cr"])) < 1e-10
 
 
 def test_flat_plan_refuses_sphere_calls():
