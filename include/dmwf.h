@@ -495,8 +495,9 @@ dm_status dm_measure_alu_peaks(double *fp64_tflops, double *fp32_tflops);
  * ahat = (L/N) FFT2(z), unrotated, times the per-mode Cholesky factor of the
  * TE block and sqrt(BB), zero on the Nyquist row (so <a a^H> = L^2 S); the
  * noise draw is that of dm_draw_cr_inputs, zero on each masked component.
- * The sphere-only calls (spectra per l, HEALPix noise setters, the Jacobi
- * refinement, dm_apply_filter) return DM_EINVAL. */
+ * dm_jacobi_refine works on it too (the source with per-mode spectra and
+ * the pixel area for Omega).  The sphere-only calls (spectra per l, HEALPix
+ * noise setters, dm_apply_filter) return DM_EINVAL. */
 dm_status dm_plan_create_flat(int N, double L, int batch, dm_plan **out);
 /* Spectra per Fourier mode, host S[4][N][N] (TT, EE, BB, TE) in numpy FFT
  * order (axis 0 = ky, axis 1 = kx), <|a_l|^2> = L^2 C per mode; each 2x2 TE

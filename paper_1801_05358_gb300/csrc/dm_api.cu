@@ -857,7 +857,6 @@ dm_status dm_solve_end(dm_plan *p, double *s_out, double *alm_out, dm_stats *sta
 
 dm_status dm_jacobi_refine(dm_plan *p, const double *d, int n_refine, double *s_out, double *alm_out,
                            dm_stats *stats, void *stream) {
-  if (p && p->flat) return fail(p, DM_EINVAL, "the Jacobi refinement is built for sphere plans");
   dm_status r = check_ready(p);
   if (r != DM_OK) return r;
   if (!d || !s_out || n_refine < 0) return fail(p, DM_EINVAL, "null buffer or negative refinement count");

@@ -63,7 +63,8 @@ __device__ __forceinline__ void rot2(int kx, int ky, double &c, double &s) {
 __global__ void __launch_bounds__(768) k_flat_ana(const double2 *__restrict__ rc, double2 *out,
                                                   const double2 *__restrict__ twid, int N, int mmax, double omega,
                                                   int epilogue, const double *__restrict__ filt, int64_t nmodes,
-                                                  const SolveState *__restrict__ state) {
+                                                  const SolveState *__restrict__ state,
+                                                  const double2 *__restrict__ src) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int kx = blockIdx.x, b = blockIdx.y, f = threadIdx.y, tx = threadIdx.x, T = blockDim.x;
   if (state != nullptr && state[b].done) return;  // uniform over the block
@@ -110,7 +111,13 @@ __global__ void __launch_bounds__(768) k_flat_ana(const double2 *__restrict__ rc
     }
     if (epilogue == ANA_DM_STEP) {
       const double *cf = filt + ((int64_t)state[b].level * nmodes + mode) * 4;
-      const double2 t = cadd(o[0], aT), e = cadd(o[nmodes], aE), bb = cadd(o[2 * nmodes], aB);
+      double2 t = cadd(o[0], aT), e = cadd(o[nmodes], aE), bb = cadd(o[2 * nmodes], aB);
+      if (src != nullptr) {  // the harmonic source of a Jacobi refinement's W~ run, before the filter
+        const double2 *g = src + (int64_t)b * 3 * nmodes + mode;
+        t = cadd(t, g[0]);
+        e = cadd(e, g[nmodes]);
+        bb = cadd(bb, g[2 * nmodes]);
+      }
       aT = make_double2(cf[0] * t.x + cf[1] * e.x, cf[0] * t.y + cf[1] * e.y);
       aE = make_double2(cf[1] * t.x + cf[2] * e.x, cf[1] * t.y + cf[2] * e.y);
       aB = make_double2(cf[3] * bb.x, cf[3] * bb.y);
@@ -184,8 +191,9 @@ cudaError_t flat_analysis(dm_plan *p, int epilogue, double2 *out, cudaStream_t s
   const double h = p->flatL / N;
   const bool draw = epilogue == ANA_FLAT_DRAW;
   const SolveState *stp = (epilogue == ANA_DM_STEP || (p->state_active && !draw)) ? p->state : nullptr;
+  const double2 *src = (epilogue == ANA_DM_STEP && p->src_active) ? p->jsrc : nullptr;
   k_flat_ana<<<dim3(N / 2, p->batch), dim3(T, 3), sm, st>>>(p->rc, out, p->twid, N, p->mmax, draw ? h : h * h,
-                                                            epilogue, draw ? p->cl : p->filt, p->nmodes, stp);
+                                                            epilogue, draw ? p->cl : p->filt, p->nmodes, stp, src);
   if (mid) cudaEventRecord(mid, st);
   return cudaGetLastError();
 }

@@ -1,5 +1,6 @@
 // dm_jacobi.cu -- the modified Jacobi refinement of Appendix A on the device,
-// in the harmonic form the sphere allows:
+// in the harmonic form the sphere allows (and the flat patch, whose transform
+// pair is exact, with per-mode spectra and the pixel area for Omega):
 //
 //   a <- a + W~(P g(a)),   g(a) = A(w (d - Y a)) - alpha Omega C^+ a,
 //
@@ -32,15 +33,19 @@ __global__ void k_jacobi_resid(const double *__restrict__ wd, const double *__re
 }
 
 // g <- P (g - alpha Omega C^+ a) per (l, m), in place.  tab[l] holds C^1/2,
-// C^+ and P (each tt, te, ee, bb).  grid (mmax + 1, batch).
+// C^+ and P (each tt, te, ee, bb).  grid (mmax + 1, batch).  Flat-sky plans
+// (flatN = N > 0): block m is the column kx of modes kx N + ky, ky < N, with
+// the tables per mode and Omega the pixel area.
 __global__ void k_jacobi_source(double2 *__restrict__ g, const double2 *__restrict__ a,
                                 const double *__restrict__ tab, const double *__restrict__ aomega, int lmax,
-                                int64_t nalm) {
+                                int64_t nalm, int flatN) {
   const int m = blockIdx.x, b = blockIdx.y;
   const double ao = aomega[b];
-  const int64_t base = (int64_t)b * 3 * nalm + jb_alm_base(lmax, m);
-  for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
-    const double *q = tab + DIAG_TAB_W * (int64_t)l + 4, *pr = q + 4;
+  const int64_t col = flatN ? (int64_t)m * flatN : jb_alm_base(lmax, m);
+  const int64_t base = (int64_t)b * 3 * nalm + col;
+  const int lo = flatN ? 0 : m, hi = flatN ? flatN - 1 : lmax;
+  for (int l = lo + threadIdx.x; l <= hi; l += blockDim.x) {
+    const double *q = tab + DIAG_TAB_W * (flatN ? col + l : (int64_t)l) + 4, *pr = q + 4;
     const int64_t i = base + l;
     const double2 at = a[i], ae = a[i + nalm], ab = a[i + 2 * nalm];
     double2 gt = g[i], ge = g[i + nalm], gb = g[i + 2 * nalm];
@@ -98,7 +103,8 @@ cudaError_t jacobi_alloc(dm_plan *p) {
 
 // jsrc = P g(jacc) for every RHS, from the data d (device, [B][3][npix]).
 cudaError_t jacobi_source(dm_plan *p, const double *d, cudaStream_t st) {
-  const double omega = 4.0 * M_PI / (double)p->npix;
+  const double hpix = p->flat ? p->flatL / p->flatN : 0.0;
+  const double omega = p->flat ? hpix * hpix : 4.0 * M_PI / (double)p->npix;
   std::vector<double> ao(p->batch);
   for (int b = 0; b < p->batch; ++b) ao[b] = p->alpha[b] * omega;
   cudaError_t e = cudaMemcpyAsync(p->diag_ao, ao.data(), sizeof(double) * p->batch, cudaMemcpyHostToDevice, st);
@@ -117,7 +123,7 @@ cudaError_t jacobi_source(dm_plan *p, const double *d, cudaStream_t st) {
   });
   if (e) return e;
   k_jacobi_source<<<dim3(p->mmax + 1, p->batch), 128, 0, st>>>(p->jsrc, p->jacc, p->diag_tab, p->diag_ao, p->lmax,
-                                                               p->nalm);
+                                                               p->nalm, p->flat ? p->flatN : 0);
   // a synchronous copy keeps ao alive until the upload has run
   e = cudaGetLastError();
   if (!e) e = cudaStreamSynchronize(st);

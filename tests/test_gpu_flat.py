@@ -10,7 +10,8 @@ oracle (oracle/flat.py), element by element through the C ABI:
 - the free-running Cauchy schedule: the same per-level counts;
 - the end-of-solve true residual and chi^2 against the oracle's definitions;
 - constrained realisations (the drawn inputs and the whole realisation),
-  with the oracle fed the same Philox normals.
+  with the oracle fed the same Philox normals;
+- the modified Jacobi refinement (Appendix A).
 
 Layouts: the oracle's modes are [3, N, N] in numpy order (axis 0 = ky); the
 library keeps kx = 0 .. N/2 - 1 with every ky, [3, N/2, N].  Bar: the FP64
@@ -182,6 +183,31 @@ def test_flat_constrained_realization_matches_oracle(orc):
         assert stats[b]["iters_per_level"][:3] == counts
         assert rel(gs[b], ref["s_cr"]) < 1e-10
         assert rel(ga[b], _ours(ref["alm_cr"])) < 1e-10
+
+
+def test_flat_jacobi_refine_matches_oracle():
+    """The modified Jacobi refinement (Appendix A) on the flat patch against
+    flat.jacobi_refine: the solve at the oracle's counts, then two refinement
+    steps at those counts, at the FP64 bar; the true residual drops."""
+    N, B = 64, 2
+    wl = W.make_flat_workload([15, 16], N=N)
+    d = np.stack(wl.data([F.synthesis(a, wl.L) for a in wl.alm_true]))
+    lam = W.lambda_schedule(1000.0, 3)
+    counts = [3, 3, 3]
+    p = _plan(wl, B, lambda0=1000.0, n_levels=3, iters_per_level=3, check_every=4)
+    s = torch.zeros((B, 3, N * N), dtype=torch.float64, device="cuda")
+    a = torch.zeros((B, 3, N * N // 2, 2), dtype=torch.float64, device="cuda")
+    st, base = p.wiener_filter(dev(d.reshape(B, 3, -1)), s)
+    st, stats = p.jacobi_refine(dev(d.reshape(B, 3, -1)), 2, s, a)
+    gs, ga = s.cpu().numpy().reshape(B, 3, N, N), _alm_of(a, B, N)
+    p.close()
+    for b in range(B):
+        assert stats[b]["iters_total"] == 3 * sum(counts)
+        assert stats[b]["true_resid"] < 0.5 * base[b]["true_resid"]
+        ref = F.jacobi_refine(d[b], wl.sigma, wl.mask_t, wl.mask_p, wl.S, wl.L, lam, forced_iters=counts,
+                              n_refine=2)
+        assert rel(gs[b], ref["s"]) < 1e-10
+        assert rel(ga[b], _ours(ref["alm"])) < 1e-10
 
 
 def test_flat_plan_refuses_sphere_calls():
